@@ -1,0 +1,640 @@
+// FP64 CPU oracle for the multiple-shooting SVGD hot path.
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load, call or
+// link this file: only the test suite, the smoke check and the benchmark's
+// CPU-baseline leg use it.  It shares no code, header or constant with the
+// CUDA library; its only common ground with that library is the seeded input
+// generator, which holds none of the method's arithmetic.
+//
+// Everything here is plain, slow and double precision, written to be checked
+// against the paper by eye:
+//   * planar articulated-body forward dynamics (ABA, Featherstone's
+//     articulated-body recursion in link-local Plucker frames), the step of
+//     Appendix B-A, Eq. (dynamics);
+//   * CRBA + Cholesky, a second forward-dynamics algorithm used only as a
+//     cross-check of the ABA;
+//   * semi-implicit Euler exactly as Eq. (dynamics): acceleration, then
+//     velocity, then position with the new velocity;
+//   * the multiple-shooting log-likelihood of Sec. IV-C (Eqs. 2, 4, 5) plus
+//     the parameter-limit prior of Sec. IV-D;
+//   * its gradient by forward-mode dual numbers, one window at a time
+//     (exact up to rounding, independent of the GPU's reverse adjoint);
+//   * the SVGD update of Eq. (1) with an RBF kernel and the median heuristic
+//     (Sec. IV-A), driven by Adam (Algorithm 1's "learning rate scheduler").
+//
+// Readings taken where the paper is silent (all documented in the design doc):
+//   window w covers steps t_w+1 .. t_{w+1}, t_w = floor(w*T/W); window 0
+//   starts at the known s_0, window w>0 at the shooting state s^s_w; every
+//   observation x_1..x_T is compared once; Gaussian constants are included;
+//   the uniform limit prior is log U = -sum log(hi-lo) plus the smooth
+//   penalty -(c_lim/2)||clamp(u,0,1)-u||^2 in the unit box u; the kernel acts
+//   on the unit-box coordinates u of theta; bandwidth = lower median of the
+//   pairwise squared distances over i<j divided by log N.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace orc {
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers (value + up to MAXD directional derivatives).
+// The number of live directions is a per-thread setting.
+// ---------------------------------------------------------------------------
+constexpr int MAXD = 72;
+static thread_local int g_nd = 0;
+
+struct Dual {
+  double v;
+  double d[MAXD];
+  Dual() : v(0.0) { std::memset(d, 0, sizeof(d)); }
+  Dual(double x) : v(x) { std::memset(d, 0, sizeof(d)); }
+};
+static inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r(a.v + b.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+static inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r(a.v - b.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+static inline Dual operator-(const Dual& a) {
+  Dual r(-a.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+static inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r(a.v * b.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+static inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r(a.v / b.v);
+  const double inv = 1.0 / b.v;
+  for (int k = 0; k < g_nd; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * inv;
+  return r;
+}
+static inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
+static inline Dual& operator-=(Dual& a, const Dual& b) { a = a - b; return a; }
+static inline Dual sin(const Dual& a) {
+  Dual r(std::sin(a.v));
+  const double c = std::cos(a.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = c * a.d[k];
+  return r;
+}
+static inline Dual cos(const Dual& a) {
+  Dual r(std::cos(a.v));
+  const double s = -std::sin(a.v);
+  for (int k = 0; k < g_nd; ++k) r.d[k] = s * a.d[k];
+  return r;
+}
+static inline double val(double x) { return x; }
+static inline double val(const Dual& x) { return x.v; }
+using std::sin;
+using std::cos;
+
+// ---------------------------------------------------------------------------
+// Planar spatial algebra (3-vectors (omega, vx, vy) / (n, fx, fy)).
+// ---------------------------------------------------------------------------
+template <class T> struct V3 { T a[3]; };
+template <class T> struct M3 { T a[3][3]; };
+
+template <class T> static V3<T> vzero() { V3<T> r; for (int i = 0; i < 3; ++i) r.a[i] = T(0.0); return r; }
+template <class T> static M3<T> mzero() { M3<T> r; for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) r.a[i][j] = T(0.0); return r; }
+
+template <class T> static V3<T> mul(const M3<T>& m, const V3<T>& v) {
+  V3<T> r;
+  for (int i = 0; i < 3; ++i) r.a[i] = m.a[i][0] * v.a[0] + m.a[i][1] * v.a[1] + m.a[i][2] * v.a[2];
+  return r;
+}
+template <class T> static V3<T> mulT(const M3<T>& m, const V3<T>& v) {  // m^T v
+  V3<T> r;
+  for (int i = 0; i < 3; ++i) r.a[i] = m.a[0][i] * v.a[0] + m.a[1][i] * v.a[1] + m.a[2][i] * v.a[2];
+  return r;
+}
+template <class T> static M3<T> mul(const M3<T>& x, const M3<T>& y) {
+  M3<T> r;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) r.a[i][j] = x.a[i][0] * y.a[0][j] + x.a[i][1] * y.a[1][j] + x.a[i][2] * y.a[2][j];
+  return r;
+}
+template <class T> static M3<T> transpose(const M3<T>& x) {
+  M3<T> r;
+  for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) r.a[i][j] = x.a[j][i];
+  return r;
+}
+template <class T> static V3<T> add(const V3<T>& x, const V3<T>& y) { V3<T> r; for (int i = 0; i < 3; ++i) r.a[i] = x.a[i] + y.a[i]; return r; }
+template <class T> static V3<T> sub(const V3<T>& x, const V3<T>& y) { V3<T> r; for (int i = 0; i < 3; ++i) r.a[i] = x.a[i] - y.a[i]; return r; }
+template <class T> static M3<T> add(const M3<T>& x, const M3<T>& y) { M3<T> r; for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) r.a[i][j] = x.a[i][j] + y.a[i][j]; return r; }
+
+// Plucker transform of motion vectors from frame A to frame B, where B's
+// origin sits at r (A coordinates) and B is rotated by th relative to A.
+template <class T> static M3<T> plnr(const T& th, const T& rx, const T& ry) {
+  T c = cos(th), s = sin(th);
+  M3<T> X;
+  X.a[0][0] = T(1.0); X.a[0][1] = T(0.0); X.a[0][2] = T(0.0);
+  X.a[1][0] = s * rx - c * ry; X.a[1][1] = c; X.a[1][2] = s;
+  X.a[2][0] = c * rx + s * ry; X.a[2][1] = -s; X.a[2][2] = c;
+  return X;
+}
+// motion cross product v x m
+template <class T> static V3<T> crm(const V3<T>& v, const V3<T>& m) {
+  V3<T> r;
+  r.a[0] = T(0.0);
+  r.a[1] = v.a[2] * m.a[0] - v.a[0] * m.a[2];
+  r.a[2] = v.a[0] * m.a[1] - v.a[1] * m.a[0];
+  return r;
+}
+// force cross product v x* f
+template <class T> static V3<T> crf(const V3<T>& v, const V3<T>& f) {
+  V3<T> r;
+  r.a[0] = v.a[1] * f.a[2] - v.a[2] * f.a[1];
+  r.a[1] = -v.a[0] * f.a[2];
+  r.a[2] = v.a[0] * f.a[1];
+  return r;
+}
+// Planar spatial inertia of a point mass m at (cx, cy) in the link frame.
+template <class T> static M3<T> point_inertia(const T& m, const T& cx, const T& cy) {
+  M3<T> I;
+  I.a[0][0] = m * (cx * cx + cy * cy); I.a[0][1] = -(m * cy); I.a[0][2] = m * cx;
+  I.a[1][0] = -(m * cy);               I.a[1][1] = m;         I.a[1][2] = T(0.0);
+  I.a[2][0] = m * cx;                  I.a[2][1] = T(0.0);    I.a[2][2] = m;
+  return I;
+}
+
+// ---------------------------------------------------------------------------
+// Planar serial chain of revolute joints, point mass m_i at the tip of link i,
+// relative joint angles, q = 0 hanging straight down, gravity -g y.
+// Joint torque is viscous damping tau_i = -b_i qd_i (no actuation).
+// Link frame i: origin at joint i, rotated by the absolute link angle; the
+// link runs along its local -y axis, so its tip (and mass) is at (0, -l_i).
+// ---------------------------------------------------------------------------
+template <class T> struct Chain {
+  int n;
+  const T* m;
+  const T* l;
+  const T* b;
+  double g;
+};
+
+template <class T> static M3<T> joint_xup(const Chain<T>& ch, int i, const T& qi) {
+  // Joint i sits at the tip of link i-1, i.e. at (0, -l_{i-1}) in frame i-1.
+  if (i == 0) return plnr<T>(qi, T(0.0), T(0.0));
+  return plnr<T>(qi, T(0.0), -ch.l[i - 1]);
+}
+
+// Articulated-body algorithm (three passes: velocities outward, articulated
+// inertias inward, accelerations outward).  Appendix B-A names ABA as the
+// forward dynamics inside f_step.
+template <class T>
+static void aba(const Chain<T>& ch, const T* q, const T* qd, const T* tau, T* qdd) {
+  const int n = ch.n;
+  std::vector<M3<T>> Xup(n), IA(n);
+  std::vector<V3<T>> v(n), c(n), pA(n), U(n), a(n);
+  std::vector<T> d(n), u(n);
+  for (int i = 0; i < n; ++i) {
+    Xup[i] = joint_xup(ch, i, q[i]);
+    V3<T> vJ = vzero<T>();
+    vJ.a[0] = qd[i];
+    v[i] = (i == 0) ? vJ : add(mul(Xup[i], v[i - 1]), vJ);
+    c[i] = crm(v[i], vJ);
+    M3<T> I = point_inertia<T>(ch.m[i], T(0.0), -ch.l[i]);
+    IA[i] = I;
+    pA[i] = crf(v[i], mul(I, v[i]));
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    U[i].a[0] = IA[i].a[0][0]; U[i].a[1] = IA[i].a[1][0]; U[i].a[2] = IA[i].a[2][0];
+    d[i] = U[i].a[0];
+    u[i] = tau[i] - pA[i].a[0];
+    if (i > 0) {
+      M3<T> Ia;
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) Ia.a[r][s] = IA[i].a[r][s] - U[i].a[r] * U[i].a[s] / d[i];
+      V3<T> pa = mul(Ia, c[i]);
+      for (int r = 0; r < 3; ++r) pa.a[r] = pA[i].a[r] + pa.a[r] + U[i].a[r] * u[i] / d[i];
+      IA[i - 1] = add(IA[i - 1], mul(transpose(Xup[i]), mul(Ia, Xup[i])));
+      pA[i - 1] = add(pA[i - 1], mulT(Xup[i], pa));
+    }
+  }
+  V3<T> a0 = vzero<T>();
+  a0.a[2] = T(ch.g);  // fictitious base acceleration = -gravity
+  for (int i = 0; i < n; ++i) {
+    a[i] = add(mul(Xup[i], (i == 0) ? a0 : a[i - 1]), c[i]);
+    qdd[i] = (u[i] - (U[i].a[0] * a[i].a[0] + U[i].a[1] * a[i].a[1] + U[i].a[2] * a[i].a[2])) / d[i];
+    a[i].a[0] = a[i].a[0] + qdd[i];
+  }
+}
+
+// Composite-rigid-body algorithm + recursive Newton-Euler bias; used only to
+// cross-check the ABA.  H qdd = tau - C.
+static void crba_bias(const Chain<double>& ch, const double* q, const double* qd, double* H, double* C) {
+  const int n = ch.n;
+  std::vector<M3<double>> Xup(n), IC(n), I(n);
+  std::vector<V3<double>> v(n), a(n), f(n);
+  for (int i = 0; i < n; ++i) {
+    Xup[i] = joint_xup(ch, i, q[i]);
+    I[i] = point_inertia<double>(ch.m[i], 0.0, -ch.l[i]);
+    V3<double> vJ = vzero<double>();
+    vJ.a[0] = qd[i];
+    V3<double> a0 = vzero<double>();
+    a0.a[2] = ch.g;
+    v[i] = (i == 0) ? vJ : add(mul(Xup[i], v[i - 1]), vJ);
+    a[i] = add(mul(Xup[i], (i == 0) ? a0 : a[i - 1]), crm(v[i], vJ));
+    f[i] = add(mul(I[i], a[i]), crf(v[i], mul(I[i], v[i])));
+    IC[i] = I[i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    C[i] = f[i].a[0];
+    if (i > 0) {
+      f[i - 1] = add(f[i - 1], mulT(Xup[i], f[i]));
+      IC[i - 1] = add(IC[i - 1], mul(transpose(Xup[i]), mul(IC[i], Xup[i])));
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    V3<double> F;
+    F.a[0] = IC[i].a[0][0]; F.a[1] = IC[i].a[1][0]; F.a[2] = IC[i].a[2][0];
+    H[i * n + i] = F.a[0];
+    int j = i;
+    while (j > 0) {
+      F = mulT(Xup[j], F);
+      --j;
+      H[i * n + j] = F.a[0];
+      H[j * n + i] = F.a[0];
+    }
+  }
+}
+
+static bool cholesky_solve(int n, const double* H, const double* rhs, double* x) {
+  std::vector<double> L(n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      double s = H[i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[i * n + k] * L[j * n + k];
+      if (i == j) {
+        if (s <= 0.0) return false;
+        L[i * n + i] = std::sqrt(s);
+      } else {
+        L[i * n + j] = s / L[j * n + j];
+      }
+    }
+  }
+  std::vector<double> y(n);
+  for (int i = 0; i < n; ++i) {
+    double s = rhs[i];
+    for (int k = 0; k < i; ++k) s -= L[i * n + k] * y[k];
+    y[i] = s / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];
+    x[i] = s / L[i * n + i];
+  }
+  return true;
+}
+
+// One semi-implicit Euler step, Eq. (dynamics): qdd from (q_t, qd_t), then
+// qd_{t+1} = qd_t + qdd dt, then q_{t+1} = q_t + qd_{t+1} dt.
+// State layout s = [q_0..q_{n-1}, qd_0..qd_{n-1}].
+template <class T>
+static void step(const Chain<T>& ch, double dt, const T* s, T* s_next) {
+  const int n = ch.n;
+  std::vector<T> tau(n), qdd(n);
+  for (int i = 0; i < n; ++i) tau[i] = -(ch.b[i] * s[n + i]);
+  aba(ch, s, s + n, tau.data(), qdd.data());
+  for (int i = 0; i < n; ++i) {
+    T qd_new = s[n + i] + qdd[i] * T(dt);
+    s_next[n + i] = qd_new;
+    s_next[i] = s[i] + qd_new * T(dt);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Problem description shared by the likelihood functions.
+// ---------------------------------------------------------------------------
+struct Problem {
+  int n;                   // links
+  double g;
+  const double* mass;      // [n] values used where theta does not override
+  const double* length;    // [n]
+  const double* damping;   // [n]
+  int M;                   // dim theta
+  const int* theta_kind;   // [M] 0 mass, 1 length, 2 damping
+  const int* theta_link;   // [M]
+  double dt;
+  int T, W, D;
+  const int* obs_index;    // [D] indices into the state
+  const double* obs;       // [T][D], row t-1 holds x_t
+  double sigma_obs, sigma_def;
+  const double* s0;        // [2n]
+  const double* lo;        // [M]
+  const double* hi;        // [M]
+  double c_lim;
+};
+
+static inline int window_start(const Problem& P, int w) { return (int)(((long long)w * P.T) / P.W); }
+
+// log N(x | mu, sigma^2 I) for a single scalar component, without the
+// constant (the constant is added once per vector below).
+// The window's log-likelihood: observation terms for t = t_w+1 .. t_{w+1}
+// (Eq. 2 over the window, Eq. 5's inner factor) and, for w < W-1, the
+// defect term log N(s^s_{w+1} | s_end, sigma_def^2 I) (Eq. 4).
+template <class T>
+static T window_loglik(const Problem& P, const T* m, const T* l, const T* b, const T* s_start, const T* s_next, int w) {
+  const int n = P.n, S = 2 * n;
+  Chain<T> ch{n, m, l, b, P.g};
+  std::vector<T> s(s_start, s_start + S), sn(S);
+  const int t0 = window_start(P, w), t1 = window_start(P, w + 1);
+  const double so2 = P.sigma_obs * P.sigma_obs;
+  const double obs_const = -0.5 * P.D * std::log(2.0 * M_PI * so2);
+  T ll(0.0);
+  for (int t = t0 + 1; t <= t1; ++t) {
+    step(ch, P.dt, s.data(), sn.data());
+    s.swap(sn);
+    T acc(0.0);
+    for (int k = 0; k < P.D; ++k) {
+      T r = T(P.obs[(size_t)(t - 1) * P.D + k]) - s[P.obs_index[k]];
+      acc += r * r;
+    }
+    ll += acc * T(-0.5 / so2) + T(obs_const);
+  }
+  if (w < P.W - 1) {
+    const double sd2 = P.sigma_def * P.sigma_def;
+    T acc(0.0);
+    for (int k = 0; k < S; ++k) {
+      T d = s_next[k] - s[k];
+      acc += d * d;
+    }
+    ll += acc * T(-0.5 / sd2) + T(-0.5 * S * std::log(2.0 * M_PI * sd2));
+  }
+  return ll;
+}
+
+// Physical link parameters for one particle: defaults overridden by theta.
+template <class T>
+static void physical_params(const Problem& P, const T* theta, std::vector<T>& m, std::vector<T>& l, std::vector<T>& b) {
+  m.assign(P.n, T(0.0)); l.assign(P.n, T(0.0)); b.assign(P.n, T(0.0));
+  for (int i = 0; i < P.n; ++i) { m[i] = T(P.mass[i]); l[i] = T(P.length[i]); b[i] = T(P.damping[i]); }
+  for (int k = 0; k < P.M; ++k) {
+    const int i = P.theta_link[k];
+    if (P.theta_kind[k] == 0) m[i] = theta[k];
+    else if (P.theta_kind[k] == 1) l[i] = theta[k];
+    else b[i] = theta[k];
+  }
+}
+
+// log p_lim: uniform density on the box plus the smooth limit penalty.
+static double limit_logprior(const Problem& P, const double* theta, double* grad_theta) {
+  double lp = 0.0;
+  for (int k = 0; k < P.M; ++k) {
+    const double w = P.hi[k] - P.lo[k];
+    const double u = (theta[k] - P.lo[k]) / w;
+    const double cu = std::min(1.0, std::max(0.0, u));
+    lp += -std::log(w) - 0.5 * P.c_lim * (cu - u) * (cu - u);
+    if (grad_theta) grad_theta[k] += P.c_lim * (cu - u) / w;
+  }
+  return lp;
+}
+
+// log p_ms for one particle (Eq. 5 summed in log space) plus log p_lim, and
+// its gradient over the augmented vector [theta, s^s_1 .. s^s_{W-1}].
+static double particle_loglik_grad(const Problem& P, const double* x, double* grad) {
+  const int n = P.n, S = 2 * n, M = P.M, W = P.W;
+  const int Pdim = M + (W - 1) * S;
+  if (grad) std::fill(grad, grad + Pdim, 0.0);
+  double total = 0.0;
+  for (int w = 0; w < W; ++w) {
+    const double* ss = (w == 0) ? P.s0 : x + M + (w - 1) * S;
+    const double* sn = (w < W - 1) ? x + M + w * S : nullptr;
+    if (!grad) {
+      std::vector<double> m, l, b;
+      physical_params<double>(P, x, m, l, b);
+      total += window_loglik<double>(P, m.data(), l.data(), b.data(), ss, sn, w);
+      continue;
+    }
+    // Directions: theta (M), start state (S, only for w>0), next state (S).
+    g_nd = M + 2 * S;
+    std::vector<Dual> th(M), s_start(S), s_next(S);
+    for (int k = 0; k < M; ++k) { th[k] = Dual(x[k]); th[k].d[k] = 1.0; }
+    for (int k = 0; k < S; ++k) {
+      s_start[k] = Dual(ss[k]);
+      if (w > 0) s_start[k].d[M + k] = 1.0;
+      if (sn) { s_next[k] = Dual(sn[k]); s_next[k].d[M + S + k] = 1.0; }
+    }
+    std::vector<Dual> m, l, b;
+    physical_params<Dual>(P, th.data(), m, l, b);
+    Dual ll = window_loglik<Dual>(P, m.data(), l.data(), b.data(), s_start.data(), sn ? s_next.data() : nullptr, w);
+    total += ll.v;
+    for (int k = 0; k < M; ++k) grad[k] += ll.d[k];
+    if (w > 0)
+      for (int k = 0; k < S; ++k) grad[M + (w - 1) * S + k] += ll.d[M + k];
+    if (sn)
+      for (int k = 0; k < S; ++k) grad[M + w * S + k] += ll.d[M + S + k];
+  }
+  total += limit_logprior(P, x, grad);
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// SVGD (Eq. 1) with RBF kernel on unit-box coordinates and Adam ascent.
+// ---------------------------------------------------------------------------
+// Lower median of the N(N-1)/2 squared distances d_ij (i<j).
+static double median_sqdist(int N, int M, const double* u /*[N][M]*/) {
+  if (N < 2) return 0.0;
+  std::vector<double> d;
+  d.reserve((size_t)N * (N - 1) / 2);
+  for (int i = 0; i < N; ++i)
+    for (int j = i + 1; j < N; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < M; ++k) {
+        const double e = u[(size_t)i * M + k] - u[(size_t)j * M + k];
+        s += e * e;
+      }
+      d.push_back(s);
+    }
+  const size_t r = (d.size() - 1) / 2;
+  std::nth_element(d.begin(), d.begin() + r, d.end());
+  return d[r];
+}
+
+static double bandwidth_from_median(int N, double med) {
+  if (N < 2 || !(med > 0.0)) return 1.0;
+  return med / std::log((double)N);
+}
+
+// phi_i = 1/N sum_j [ k(u_j,u_i) g_j + grad_{u_j} k(u_j,u_i) ],
+// k(a,b) = exp(-||a-b||^2 / bw), grad_{u_j} k(u_j,u_i) = (2/bw)(u_i-u_j) k.
+static void svgd_phi(int N, int M, const double* u, const double* g, double bw, double* phi) {
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < M; ++k) phi[(size_t)i * M + k] = 0.0;
+    for (int j = 0; j < N; ++j) {
+      double d = 0.0;
+      for (int k = 0; k < M; ++k) {
+        const double e = u[(size_t)i * M + k] - u[(size_t)j * M + k];
+        d += e * e;
+      }
+      const double kij = std::exp(-d / bw);
+      for (int k = 0; k < M; ++k)
+        phi[(size_t)i * M + k] += kij * g[(size_t)j * M + k] +
+                                  (2.0 / bw) * (u[(size_t)i * M + k] - u[(size_t)j * M + k]) * kij;
+    }
+    for (int k = 0; k < M; ++k) phi[(size_t)i * M + k] /= N;
+  }
+}
+
+// Adam ascent on x with direction g (Kingma & Ba): bias-corrected moments.
+static void adam_ascent(double& x, double& m, double& v, double g, int t, double lr, double b1, double b2, double eps) {
+  m = b1 * m + (1.0 - b1) * g;
+  v = b2 * v + (1.0 - b2) * g * g;
+  const double mh = m / (1.0 - std::pow(b1, t));
+  const double vh = v / (1.0 - std::pow(b2, t));
+  x += lr * mh / (std::sqrt(vh) + eps);
+}
+
+}  // namespace orc
+
+using namespace orc;
+
+// ---------------------------------------------------------------------------
+// C API (ctypes).  All arrays are row-major doubles unless stated.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int orc_version() { return 1; }
+
+// ABA: qdd for a chain with per-link mass/length/damping, torques given.
+int orc_aba(int n, double g, const double* m, const double* l, const double* b,
+            const double* q, const double* qd, const double* tau, double* qdd) {
+  Chain<double> ch{n, m, l, b, g};
+  aba(ch, q, qd, tau, qdd);
+  return 0;
+}
+
+// CRBA mass matrix H [n][n] and bias C [n] (Coriolis + gravity).
+int orc_crba(int n, double g, const double* m, const double* l, const double* b,
+             const double* q, const double* qd, double* H, double* C) {
+  Chain<double> ch{n, m, l, b, g};
+  crba_bias(ch, q, qd, H, C);
+  return 0;
+}
+
+// Forward dynamics by CRBA + Cholesky: qdd = H^-1 (tau - C).
+int orc_fd_crba(int n, double g, const double* m, const double* l, const double* b,
+                const double* q, const double* qd, const double* tau, double* qdd) {
+  std::vector<double> H(n * n), C(n), rhs(n);
+  Chain<double> ch{n, m, l, b, g};
+  crba_bias(ch, q, qd, H.data(), C.data());
+  for (int i = 0; i < n; ++i) rhs[i] = tau[i] - C[i];
+  return cholesky_solve(n, H.data(), rhs.data(), qdd) ? 0 : -1;
+}
+
+// Total mechanical energy (kinetic + gravitational potential) of the chain.
+double orc_energy(int n, double g, const double* m, const double* l, const double* q, const double* qd) {
+  double px = 0, py = 0, vx = 0, vy = 0, phi = 0, om = 0, E = 0;
+  for (int i = 0; i < n; ++i) {
+    phi += q[i];
+    om += qd[i];
+    px += l[i] * std::sin(phi);
+    py += -l[i] * std::cos(phi);
+    vx += l[i] * std::cos(phi) * om;
+    vy += l[i] * std::sin(phi) * om;
+    E += 0.5 * m[i] * (vx * vx + vy * vy) + m[i] * g * py;
+  }
+  return E;
+}
+
+// f_sim: roll out T semi-implicit Euler steps from s0.  states [T+1][2n].
+int orc_simulate(int n, double g, const double* m, const double* l, const double* b,
+                 double dt, int T, const double* s0, double* states) {
+  Chain<double> ch{n, m, l, b, g};
+  const int S = 2 * n;
+  std::copy(s0, s0 + S, states);
+  for (int t = 0; t < T; ++t) step(ch, dt, states + (size_t)t * S, states + (size_t)(t + 1) * S);
+  return 0;
+}
+
+// One step's Jacobian-free check helper: s_next = f_step(s).
+int orc_step(int n, double g, const double* m, const double* l, const double* b,
+             double dt, const double* s, double* s_next) {
+  Chain<double> ch{n, m, l, b, g};
+  step(ch, dt, s, s_next);
+  return 0;
+}
+
+// Batched log p_ms + log p_lim and gradient.  particles [N][P] with
+// P = M + (W-1)*2n; logp [N]; grad [N][P] or NULL.  Parallel over particles
+// with `threads` OpenMP threads (<=0: library default).
+int orc_loglik_grad(const Problem* prob, const double* particles, int N, double* logp, double* grad, int threads) {
+  const Problem& P = *prob;
+  // M theta directions plus 2S state directions must fit the dual width.
+  if (P.n < 1 || P.M < 0 || P.W < 1 || P.T < P.W || P.M + 4 * P.n > MAXD) return -1;
+  const int Pdim = P.M + (P.W - 1) * 2 * P.n;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i) {
+    logp[i] = particle_loglik_grad(P, particles + (size_t)i * Pdim, grad ? grad + (size_t)i * Pdim : nullptr);
+  }
+  return 0;
+}
+
+int orc_max_threads() {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+double orc_median_sqdist(int N, int M, const double* u) { return median_sqdist(N, M, u); }
+double orc_bandwidth(int N, double med) { return bandwidth_from_median(N, med); }
+
+int orc_svgd_phi(int N, int M, const double* u, const double* g, double bw, double* phi) {
+  svgd_phi(N, M, u, g, bw, phi);
+  return 0;
+}
+
+// One SVGD + Adam iteration on particles [N][P] (first M entries theta,
+// the rest shooting states), given grad = d log p / d x [N][P].
+// adam_m, adam_v [N][P] hold theta moments in unit-box coordinates and
+// shooting-state moments in state units; *t is the step count (incremented).
+// phi_out [N][M] (unit-box coordinates) and bw_out may be NULL.
+int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
+                  double* particles, const double* grad, double* adam_m, double* adam_v, int* t,
+                  double lr, double b1, double b2, double eps, int clamp,
+                  double* phi_out, double* bw_out) {
+  std::vector<double> u((size_t)N * M), gu((size_t)N * M), phi((size_t)N * M);
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < M; ++k) {
+      const double w = hi[k] - lo[k];
+      u[(size_t)i * M + k] = (particles[(size_t)i * P + k] - lo[k]) / w;
+      gu[(size_t)i * M + k] = grad[(size_t)i * P + k] * w;  // chain rule through u
+    }
+  const double med = median_sqdist(N, M, u.data());
+  const double bw = bandwidth_from_median(N, med);
+  svgd_phi(N, M, u.data(), gu.data(), bw, phi.data());
+  *t += 1;
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < M; ++k) {
+      double x = u[(size_t)i * M + k];
+      adam_ascent(x, adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k], phi[(size_t)i * M + k], *t, lr, b1, b2, eps);
+      if (clamp) x = std::min(1.0, std::max(0.0, x));
+      particles[(size_t)i * P + k] = lo[k] + x * (hi[k] - lo[k]);
+    }
+    for (int k = M; k < P; ++k)
+      adam_ascent(particles[(size_t)i * P + k], adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k],
+                  grad[(size_t)i * P + k], *t, lr, b1, b2, eps);
+  }
+  if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
+  if (bw_out) *bw_out = bw;
+  return 0;
+}
+
+}  // extern "C"

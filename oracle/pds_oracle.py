@@ -1,0 +1,260 @@
+"""ctypes binding of the FP64 CPU oracle (``oracle/oracle.cpp``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg may import this module; the product library never does.
+
+The oracle restates, in double precision and plain loops, what the hot path
+computes: planar articulated-body dynamics with semi-implicit Euler
+(Appendix B-A, Eq. dynamics), the multiple-shooting likelihood (Sec. IV-C,
+Eqs. 2, 4, 5) with the limit prior (Sec. IV-D), its gradient by forward-mode
+dual numbers, and the SVGD update (Sec. IV-A, Eq. 1) driven by Adam
+(Algorithm 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.cpp")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (g++, -O2, OpenMP)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int),
+        ("g", ctypes.c_double),
+        ("mass", _dp),
+        ("length", _dp),
+        ("damping", _dp),
+        ("M", ctypes.c_int),
+        ("theta_kind", _ip),
+        ("theta_link", _ip),
+        ("dt", ctypes.c_double),
+        ("T", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("D", ctypes.c_int),
+        ("obs_index", _ip),
+        ("obs", _dp),
+        ("sigma_obs", ctypes.c_double),
+        ("sigma_def", ctypes.c_double),
+        ("s0", _dp),
+        ("lo", _dp),
+        ("hi", _dp),
+        ("c_lim", ctypes.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.orc_aba.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_crba.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_fd_crba.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp, _dp, _dp, _dp]
+            L.orc_energy.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, _dp]
+            L.orc_energy.restype = ctypes.c_double
+            L.orc_simulate.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_double,
+                                       ctypes.c_int, _dp, _dp]
+            L.orc_step.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp, ctypes.c_double, _dp, _dp]
+            L.orc_loglik_grad.argtypes = [ctypes.POINTER(_Problem), _dp, ctypes.c_int, _dp, _dp, ctypes.c_int]
+            L.orc_max_threads.restype = ctypes.c_int
+            L.orc_median_sqdist.argtypes = [ctypes.c_int, ctypes.c_int, _dp]
+            L.orc_median_sqdist.restype = ctypes.c_double
+            L.orc_bandwidth.argtypes = [ctypes.c_int, ctypes.c_double]
+            L.orc_bandwidth.restype = ctypes.c_double
+            L.orc_svgd_phi.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _dp]
+            L.orc_svgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(_ip)
+
+
+# --------------------------------------------------------------------------
+# dynamics
+# --------------------------------------------------------------------------
+def aba(m, l, b, q, qd, tau, g=9.81):
+    """Forward dynamics qdd of the planar point-mass chain by the ABA."""
+    n = len(m)
+    bufs = [_d(x) for x in (m, l, b, q, qd, tau)]
+    out = np.zeros(n)
+    lib().orc_aba(n, g, *[p for _, p in bufs], out.ctypes.data_as(_dp))
+    return out
+
+
+def fd_crba(m, l, b, q, qd, tau, g=9.81):
+    """Forward dynamics by CRBA + Cholesky (independent of the ABA)."""
+    n = len(m)
+    bufs = [_d(x) for x in (m, l, b, q, qd, tau)]
+    out = np.zeros(n)
+    rc = lib().orc_fd_crba(n, g, *[p for _, p in bufs], out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise RuntimeError("mass matrix not positive definite")
+    return out
+
+
+def crba(m, l, b, q, qd, g=9.81):
+    n = len(m)
+    bufs = [_d(x) for x in (m, l, b, q, qd)]
+    H = np.zeros((n, n))
+    C = np.zeros(n)
+    lib().orc_crba(n, g, *[p for _, p in bufs], H.ctypes.data_as(_dp), C.ctypes.data_as(_dp))
+    return H, C
+
+
+def energy(m, l, q, qd, g=9.81):
+    bufs = [_d(x) for x in (m, l, q, qd)]
+    return lib().orc_energy(len(m), g, *[p for _, p in bufs])
+
+
+def simulate(m, l, b, s0, dt, T, g=9.81):
+    """f_sim: states [T+1][2n] from s0 by T semi-implicit Euler steps."""
+    n = len(m)
+    bufs = [_d(x) for x in (m, l, b, s0)]
+    out = np.zeros((T + 1, 2 * n))
+    p = [p for _, p in bufs]
+    lib().orc_simulate(n, g, p[0], p[1], p[2], dt, T, p[3], out.ctypes.data_as(_dp))
+    return out
+
+
+def step(m, l, b, s, dt, g=9.81):
+    n = len(m)
+    bufs = [_d(x) for x in (m, l, b, s)]
+    out = np.zeros(2 * n)
+    p = [p for _, p in bufs]
+    lib().orc_step(n, g, p[0], p[1], p[2], dt, p[3], out.ctypes.data_as(_dp))
+    return out
+
+
+# --------------------------------------------------------------------------
+# likelihood
+# --------------------------------------------------------------------------
+class Problem:
+    """Multiple-shooting problem for the oracle (all arrays float64/int32).
+
+    ``obs`` is [T][D]: row t-1 holds observation x_t.  Particles are
+    [N][P] with P = M + (W-1)*2n: theta first, then s^s_1 .. s^s_{W-1}.
+    """
+
+    def __init__(self, *, mass, length, damping, theta_kind, theta_link, dt, T, W, obs, obs_index,
+                 sigma_obs, sigma_def, s0, lo, hi, g=9.81, c_lim=1e4):
+        self._keep = []
+
+        def d(x):
+            a, p = _d(x)
+            self._keep.append(a)
+            return p
+
+        def i(x):
+            a, p = _i(x)
+            self._keep.append(a)
+            return p
+
+        self.n = len(mass)
+        self.M = len(theta_kind)
+        self.W = int(W)
+        self.T = int(T)
+        self.S = 2 * self.n
+        self.P = self.M + (self.W - 1) * self.S
+        obs = np.asarray(obs, dtype=np.float64)
+        self.D = obs.shape[1]
+        self.c = _Problem(
+            n=self.n, g=float(g), mass=d(mass), length=d(length), damping=d(damping), M=self.M,
+            theta_kind=i(theta_kind), theta_link=i(theta_link), dt=float(dt), T=self.T, W=self.W, D=self.D,
+            obs_index=i(obs_index), obs=d(obs), sigma_obs=float(sigma_obs), sigma_def=float(sigma_def),
+            s0=d(s0), lo=d(lo), hi=d(hi), c_lim=float(c_lim))
+
+    def loglik_grad(self, particles, grad=True, threads=1):
+        x, xp = _d(np.atleast_2d(particles))
+        N = x.shape[0]
+        assert x.shape[1] == self.P, (x.shape, self.P)
+        logp = np.zeros(N)
+        g = np.zeros((N, self.P)) if grad else None
+        rc = lib().orc_loglik_grad(ctypes.byref(self.c), xp, N, logp.ctypes.data_as(_dp),
+                                   g.ctypes.data_as(_dp) if grad else None, int(threads))
+        if rc != 0:
+            raise RuntimeError(f"orc_loglik_grad failed ({rc})")
+        return (logp, g) if grad else logp
+
+
+def max_threads() -> int:
+    return int(lib().orc_max_threads())
+
+
+# --------------------------------------------------------------------------
+# SVGD
+# --------------------------------------------------------------------------
+def median_sqdist(u):
+    u, up = _d(np.atleast_2d(u))
+    return lib().orc_median_sqdist(u.shape[0], u.shape[1], up)
+
+
+def bandwidth(N, med):
+    return lib().orc_bandwidth(int(N), float(med))
+
+
+def svgd_phi(u, g, bw):
+    u, up = _d(u)
+    g, gp = _d(g)
+    out = np.zeros_like(u)
+    lib().orc_svgd_phi(u.shape[0], u.shape[1], up, gp, float(bw), out.ctypes.data_as(_dp))
+    return out
+
+
+class SvgdState:
+    """Adam moments and step count of the oracle's SVGD iteration."""
+
+    def __init__(self, N, P, lo, hi, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, clamp=True):
+        self.N, self.P = N, P
+        self.M = len(lo)
+        self.lo = np.ascontiguousarray(lo, dtype=np.float64)
+        self.hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.m = np.zeros((N, P))
+        self.v = np.zeros((N, P))
+        self.t = ctypes.c_int(0)
+        self.lr, self.beta1, self.beta2, self.eps, self.clamp = lr, beta1, beta2, eps, clamp
+
+    def step(self, particles, grad):
+        """In-place SVGD+Adam update of particles [N][P]; returns (phi, bw)."""
+        assert particles.dtype == np.float64 and particles.flags.c_contiguous
+        g, gp = _d(grad)
+        phi = np.zeros((self.N, self.M))
+        bw = ctypes.c_double(0.0)
+        lib().orc_svgd_step(self.N, self.M, self.P, self.lo.ctypes.data_as(_dp), self.hi.ctypes.data_as(_dp),
+                            particles.ctypes.data_as(_dp), gp, self.m.ctypes.data_as(_dp),
+                            self.v.ctypes.data_as(_dp), ctypes.byref(self.t), self.lr, self.beta1, self.beta2,
+                            self.eps, int(self.clamp), phi.ctypes.data_as(_dp), ctypes.byref(bw))
+        return phi, bw.value

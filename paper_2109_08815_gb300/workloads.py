@@ -1,0 +1,215 @@
+"""Seeded synthetic workloads shaped like the paper's experiments.
+
+This module holds random draws and configuration constants only: no dynamics,
+no likelihood, no SVGD arithmetic.  It is the one module that both the CUDA
+path (through the Python binding) and the FP64 oracle (in the tests) take
+their inputs from, so that the two sides see identical arrays.
+
+Observations are produced by whoever rolls out the true parameters (the
+oracle in tests, the library's own ``simulate`` in the benchmark); this module
+only supplies the true parameters, the initial state and the standard-normal
+noise draws that are scaled by sigma_obs.
+
+Workloads (synthetic stand-ins; the paper's real datasets are not available):
+
+* ``double_pendulum`` -- the paper's double-pendulum setting (Sec. V-A, V-B):
+  2 revolute links, theta = (m1, m2, l1, l2), 200 steps at dt = 0.01,
+  angles observed with sigma 0.01, 10 shooting windows, 100 particles.
+* ``chain5`` -- a 5-link planar chain with point masses at the link tips and
+  viscous joint damping, theta = 5 masses + 5 damping coefficients, 1000 steps
+  at dt = 0.005, angles and velocities observed with sigma 0.02, 20 windows.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+PARAM_MASS = 0
+PARAM_LENGTH = 1
+PARAM_DAMPING = 2
+
+GRAVITY = 9.81
+SIGMA_DEF = 0.1          # sigma_def^2 = 1e-2, the "small variance" of Eq. 4
+C_LIM = 1.0e4            # stiffness of the smooth parameter-limit penalty
+
+
+@dataclasses.dataclass
+class PlanarWorkload:
+    name: str
+    n: int
+    mass: np.ndarray            # [n] true masses (theta entries override)
+    length: np.ndarray          # [n]
+    damping: np.ndarray         # [n]
+    theta_kind: np.ndarray      # [M] int32, PARAM_*
+    theta_link: np.ndarray      # [M] int32
+    theta_true: np.ndarray      # [M]
+    lo: np.ndarray              # [M] prior box
+    hi: np.ndarray              # [M]
+    dt: float
+    T: int
+    W: int
+    obs_index: np.ndarray       # [D] int32 indices into s = [q, qd]
+    sigma_obs: float
+    sigma_def: float
+    s0: np.ndarray              # [2n]
+    noise: np.ndarray           # [T][D] standard normal draws
+    theta_init: np.ndarray      # [N][M] initial particles, uniform in the box
+    lr: float = 1e-2
+    iterations: int = 100
+    g: float = GRAVITY
+    c_lim: float = C_LIM
+    seed: int = 0
+
+    @property
+    def M(self) -> int:
+        return len(self.theta_kind)
+
+    @property
+    def S(self) -> int:
+        return 2 * self.n
+
+    @property
+    def D(self) -> int:
+        return len(self.obs_index)
+
+    @property
+    def N(self) -> int:
+        return self.theta_init.shape[0]
+
+    @property
+    def P(self) -> int:
+        return self.M + (self.W - 1) * self.S
+
+    def window_start(self, w: int) -> int:
+        return (w * self.T) // self.W
+
+
+def double_pendulum(N: int = 100, seed: int = 1000) -> PlanarWorkload:
+    """Double pendulum, theta = (m1, m2, l1, l2).
+
+    True masses ~ U[0.5, 2], lengths ~ U[0.5, 1.5]; q0 ~ U(-pi/2, pi/2),
+    zero velocity; no damping.  The prior box is the sampling box.
+    """
+    rng = np.random.default_rng(seed)
+    lo = np.array([0.5, 0.5, 0.5, 0.5])
+    hi = np.array([2.0, 2.0, 1.5, 1.5])
+    theta_true = rng.uniform(lo, hi)
+    q0 = rng.uniform(-math.pi / 2, math.pi / 2, size=2)
+    T, D = 200, 2
+    noise = rng.standard_normal((T, D))
+    theta_init = rng.uniform(lo, hi, size=(N, 4))
+    return PlanarWorkload(
+        name="double_pendulum", n=2,
+        mass=theta_true[:2].copy(), length=theta_true[2:].copy(), damping=np.zeros(2),
+        theta_kind=np.array([PARAM_MASS, PARAM_MASS, PARAM_LENGTH, PARAM_LENGTH], dtype=np.int32),
+        theta_link=np.array([0, 1, 0, 1], dtype=np.int32),
+        theta_true=theta_true, lo=lo, hi=hi, dt=0.01, T=T, W=10,
+        obs_index=np.array([0, 1], dtype=np.int32), sigma_obs=0.01, sigma_def=SIGMA_DEF,
+        s0=np.concatenate([q0, np.zeros(2)]), noise=noise, theta_init=theta_init,
+        lr=1e-2, iterations=100, seed=seed)
+
+
+CHAIN5_LENGTH = 0.5      # fixed link length [m]; lengths are not inferred
+
+
+def chain5(N: int = 1024, seed: int | None = None, T: int = 1000, W: int = 20) -> PlanarWorkload:
+    """5-link damped chain, theta = 5 masses + 5 damping coefficients ~ U[0.1, 2].
+
+    Fixed link lengths 0.5 m; q0 ~ U(-pi/2, pi/2) relative angles, zero
+    velocity; angles and velocities observed with sigma 0.02.
+    """
+    if seed is None:
+        seed = 2000 + N
+    rng = np.random.default_rng(seed)
+    n = 5
+    lo = np.full(2 * n, 0.1)
+    hi = np.full(2 * n, 2.0)
+    theta_true = rng.uniform(lo, hi)
+    q0 = rng.uniform(-math.pi / 2, math.pi / 2, size=n)
+    D = 2 * n
+    noise = rng.standard_normal((T, D))
+    theta_init = rng.uniform(lo, hi, size=(N, 2 * n))
+    kind = np.array([PARAM_MASS] * n + [PARAM_DAMPING] * n, dtype=np.int32)
+    link = np.array(list(range(n)) * 2, dtype=np.int32)
+    return PlanarWorkload(
+        name="chain5", n=n,
+        mass=theta_true[:n].copy(), length=np.full(n, CHAIN5_LENGTH), damping=theta_true[n:].copy(),
+        theta_kind=kind, theta_link=link, theta_true=theta_true, lo=lo, hi=hi, dt=0.005, T=T, W=W,
+        obs_index=np.arange(D, dtype=np.int32), sigma_obs=0.02, sigma_def=SIGMA_DEF,
+        s0=np.concatenate([q0, np.zeros(n)]), noise=noise, theta_init=theta_init,
+        lr=1e-2, iterations=100, seed=seed)
+
+
+def random_chain(n: int, N: int, seed: int, T: int = 40, W: int = 4, kinds=(PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING),
+                 dt: float = 0.005, observe_velocity: bool = True) -> PlanarWorkload:
+    """Small random chain used by parity tests (all three parameter kinds)."""
+    rng = np.random.default_rng(seed)
+    ranges = {PARAM_MASS: (0.3, 2.0), PARAM_LENGTH: (0.3, 1.2), PARAM_DAMPING: (0.0, 0.8)}
+    kind, link, lo, hi = [], [], [], []
+    for k in kinds:
+        for i in range(n):
+            kind.append(k)
+            link.append(i)
+            lo.append(ranges[k][0])
+            hi.append(ranges[k][1])
+    lo, hi = np.array(lo), np.array(hi)
+    theta_true = rng.uniform(lo, hi)
+    mass = rng.uniform(0.3, 2.0, n)
+    length = rng.uniform(0.3, 1.2, n)
+    damping = rng.uniform(0.0, 0.8, n)
+    for j, (k, i) in enumerate(zip(kind, link)):
+        {PARAM_MASS: mass, PARAM_LENGTH: length, PARAM_DAMPING: damping}[k][i] = theta_true[j]
+    q0 = rng.uniform(-math.pi / 2, math.pi / 2, size=n)
+    qd0 = rng.uniform(-1.0, 1.0, size=n)
+    obs_index = np.arange(2 * n if observe_velocity else n, dtype=np.int32)
+    noise = rng.standard_normal((T, len(obs_index)))
+    theta_init = rng.uniform(lo, hi, size=(N, len(kind)))
+    return PlanarWorkload(
+        name=f"chain{n}", n=n, mass=mass, length=length, damping=damping,
+        theta_kind=np.array(kind, dtype=np.int32), theta_link=np.array(link, dtype=np.int32),
+        theta_true=theta_true, lo=lo, hi=hi, dt=dt, T=T, W=W, obs_index=obs_index,
+        sigma_obs=0.02, sigma_def=SIGMA_DEF, s0=np.concatenate([q0, qd0]), noise=noise,
+        theta_init=theta_init, seed=seed)
+
+
+def observations(wl: PlanarWorkload, states: np.ndarray) -> np.ndarray:
+    """x_t = (observed components of s_t) + sigma_obs * noise_t, t = 1..T.
+
+    ``states`` is the true rollout [T+1][2n] (row 0 = s_0).  Returns [T][D].
+    """
+    return states[1:, wl.obs_index] + wl.sigma_obs * wl.noise
+
+
+def initial_particles(wl: PlanarWorkload, obs: np.ndarray, N: int | None = None, rng_seed: int | None = None
+                      ) -> np.ndarray:
+    """Initial augmented particles [N][P] (theta, then s^s_1..s^s_{W-1}).
+
+    theta: the workload's uniform draws in the prior box.  Shooting states:
+    the observed components at t_w; unobserved velocities from central
+    differences of the observed angles (as for the real pendulum data in
+    Appendix B-B).  Identical for all particles.
+    """
+    theta = wl.theta_init if N is None else wl.theta_init[:N]
+    N = theta.shape[0]
+    S, n = wl.S, wl.n
+    shoot = np.zeros((wl.W - 1, S))
+    for w in range(1, wl.W):
+        t = wl.window_start(w)
+        row = obs[t - 1]
+        for d, idx in enumerate(wl.obs_index):
+            shoot[w - 1, idx] = row[d]
+        for i in range(n):
+            if (n + i) not in set(int(x) for x in wl.obs_index):
+                d = list(int(x) for x in wl.obs_index).index(i)
+                nxt = obs[min(t, wl.T - 1), d]
+                prv = obs[max(t - 2, 0), d]
+                shoot[w - 1, n + i] = (nxt - prv) / (2.0 * wl.dt)
+    x = np.zeros((N, wl.P))
+    x[:, :wl.M] = theta
+    x[:, wl.M:] = shoot.reshape(-1)[None, :]
+    if rng_seed is not None:
+        rng = np.random.default_rng(rng_seed)
+        x[:, wl.M:] += 0.05 * rng.standard_normal((N, wl.P - wl.M))
+    return x

@@ -1,0 +1,165 @@
+"""Pins of the oracle's multiple-shooting likelihood and gradient (CPU only).
+
+Sec. IV-B/IV-C: the single-shooting likelihood (Eq. 3) is a product of
+Gaussians over observations (Eq. 2); multiple shooting (Eq. 5) splits the
+trajectory into windows tied by Gaussian defect terms (Eq. 4); Sec. IV-D adds
+a uniform prior on the parameter box.  Special cases fix the oracle:
+one window is single shooting; shooting states placed on the true rollout
+give zero defects; the Gaussian and uniform densities come from scipy; the
+gradient matches central finite differences.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import pds_oracle as orc
+from paper_2109_08815_gb300 import workloads as wlmod
+
+
+def _physical(wl, theta):
+    m, l, b = wl.mass.copy(), wl.length.copy(), wl.damping.copy()
+    for k, (kind, i) in enumerate(zip(wl.theta_kind, wl.theta_link)):
+        {0: m, 1: l, 2: b}[int(kind)][i] = theta[k]
+    return m, l, b
+
+
+def _problem(wl, obs, W=None, c_lim=wlmod.C_LIM):
+    return orc.Problem(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
+                       theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W if W is None else W, obs=obs,
+                       obs_index=wl.obs_index, sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0,
+                       lo=wl.lo, hi=wl.hi, g=wl.g, c_lim=c_lim)
+
+
+def _obs(wl):
+    m, l, b = _physical(wl, wl.theta_true)
+    return wlmod.observations(wl, orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g))
+
+
+def _scipy_single_shooting(wl, obs, theta):
+    """log p_ss (Eq. 3) + log U(theta | box) with scipy's densities."""
+    m, l, b = _physical(wl, theta)
+    st = orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g)
+    pred = st[1:, wl.obs_index]
+    lp = stats.norm.logpdf(obs, loc=pred, scale=wl.sigma_obs).sum()
+    lp += stats.uniform.logpdf(theta, loc=wl.lo, scale=wl.hi - wl.lo).sum()
+    return lp, st
+
+
+@pytest.mark.parametrize("maker", [lambda: wlmod.double_pendulum(N=4), lambda: wlmod.random_chain(3, 4, seed=5)])
+def test_one_window_is_single_shooting(maker):
+    wl = maker()
+    obs = _obs(wl)
+    prob = _problem(wl, obs, W=1)
+    for theta in wl.theta_init:
+        ref, _ = _scipy_single_shooting(wl, obs, theta)
+        got = prob.loglik_grad(theta[None, :], grad=False)[0]
+        assert abs(got - ref) <= 1e-9 * max(1.0, abs(ref))
+
+
+@pytest.mark.parametrize("W", [2, 3, 7, 10])
+def test_zero_defects_reduce_to_single_shooting(W):
+    """Shooting states on the particle's own rollout: p_ms = p_ss * prod N(0|0, sd^2)."""
+    wl = wlmod.double_pendulum(N=3)
+    obs = _obs(wl)
+    prob = _problem(wl, obs, W=W)
+    for theta in wl.theta_init:
+        ref, st = _scipy_single_shooting(wl, obs, theta)
+        x = np.concatenate([theta] + [st[(w * wl.T) // W] for w in range(1, W)])
+        got = prob.loglik_grad(x[None, :], grad=False)[0]
+        ref_ms = ref + (W - 1) * stats.norm.logpdf(np.zeros(wl.S), 0.0, wl.sigma_def).sum()
+        assert abs(got - ref_ms) <= 1e-9 * max(1.0, abs(ref_ms))
+
+
+def test_uneven_windows_cover_every_observation_once():
+    """T not divisible by W: each x_t still enters exactly once."""
+    wl = wlmod.random_chain(2, 2, seed=11, T=37, W=5)
+    obs = _obs(wl)
+    theta = wl.theta_init[0]
+    ref, st = _scipy_single_shooting(wl, obs, theta)
+    x = np.concatenate([theta] + [st[(w * wl.T) // wl.W] for w in range(1, wl.W)])
+    got = _problem(wl, obs).loglik_grad(x[None, :], grad=False)[0]
+    ref_ms = ref + (wl.W - 1) * stats.norm.logpdf(np.zeros(wl.S), 0.0, wl.sigma_def).sum()
+    assert abs(got - ref_ms) <= 1e-9 * max(1.0, abs(ref_ms))
+
+
+def test_noise_free_truth_gives_normalising_constants():
+    wl = wlmod.double_pendulum(N=1)
+    m, l, b = _physical(wl, wl.theta_true)
+    st = orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g)
+    obs = st[1:, wl.obs_index]
+    x = np.concatenate([wl.theta_true] + [st[wl.window_start(w)] for w in range(1, wl.W)])
+    got = _problem(wl, obs).loglik_grad(x[None, :], grad=False)[0]
+    ref = (wl.T * wl.D * stats.norm.logpdf(0.0, 0.0, wl.sigma_obs)
+           + (wl.W - 1) * wl.S * stats.norm.logpdf(0.0, 0.0, wl.sigma_def)
+           - np.log(wl.hi - wl.lo).sum())
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+
+
+def test_defect_term_is_gaussian_in_the_gap():
+    """Moving one shooting state by delta changes only its window's start and
+    the previous window's defect; with W=2 and an unobserved-free check via
+    two evaluations the defect enters as -||d||^2 / (2 sd^2)."""
+    wl = wlmod.double_pendulum(N=1)
+    wl.W = 2
+    obs = _obs(wl)
+    prob = _problem(wl, obs)
+    theta = wl.theta_true
+    m, l, b = _physical(wl, theta)
+    st = orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g)
+    s_end = st[wl.window_start(1)]
+    # Evaluate window 0's defect alone: log p(W=2, x) - [window-1 obs terms
+    # at start x] is independent of x except through the defect.
+    x0 = np.concatenate([theta, s_end])
+    base = prob.loglik_grad(x0[None, :], grad=False)[0]
+    # window-1 part for a shifted start, from single shooting of window 1 only
+    delta = np.array([0.01, -0.02, 0.03, 0.0])
+    x1 = np.concatenate([theta, s_end + delta])
+    shifted = prob.loglik_grad(x1[None, :], grad=False)[0]
+    st1 = orc.simulate(m, l, b, s_end + delta, wl.dt, wl.T - wl.window_start(1), g=wl.g)
+    st0 = st[wl.window_start(1):]
+    t1 = wl.window_start(1)
+    obs1 = obs[t1:]
+    w1_shift = stats.norm.logpdf(obs1, st1[1:, wl.obs_index], wl.sigma_obs).sum()
+    w1_base = stats.norm.logpdf(obs1, st0[1:, wl.obs_index], wl.sigma_obs).sum()
+    defect_change = (stats.norm.logpdf(delta, 0.0, wl.sigma_def).sum()
+                     - stats.norm.logpdf(np.zeros(4), 0.0, wl.sigma_def).sum())
+    assert abs((shifted - base) - (w1_shift - w1_base + defect_change)) < 1e-8 * max(1, abs(shifted))
+
+
+def _fd_grad(prob, x, h):
+    g = np.zeros_like(x)
+    for k in range(len(x)):
+        xp, xm = x.copy(), x.copy()
+        xp[k] += h
+        xm[k] -= h
+        g[k] = (prob.loglik_grad(xp[None], grad=False)[0] - prob.loglik_grad(xm[None], grad=False)[0]) / (2 * h)
+    return g
+
+
+@pytest.mark.parametrize("n,kinds", [(2, (0, 1)), (3, (0, 1, 2)), (5, (0, 2))])
+def test_dual_gradient_matches_central_differences(n, kinds):
+    wl = wlmod.random_chain(n, 3, seed=20 + n, T=16, W=4, kinds=kinds)
+    obs = _obs(wl)
+    prob = _problem(wl, obs)
+    x = wlmod.initial_particles(wl, obs, rng_seed=3)
+    logp, grad = prob.loglik_grad(x)
+    for i in range(x.shape[0]):
+        fd = _fd_grad(prob, x[i], 1e-5)
+        err = np.max(np.abs(grad[i] - fd)) / np.max(np.abs(fd))
+        assert err < 1e-6, err
+
+
+def test_limit_prior_gradient_outside_box():
+    wl = wlmod.double_pendulum(N=1)
+    obs = _obs(wl)
+    prob = _problem(wl, obs, c_lim=50.0)
+    wl.W = 10
+    x = wlmod.initial_particles(wl, obs)[0]
+    x[0] = wl.hi[0] + 0.05      # above the box
+    x[3] = wl.lo[3] - 0.02      # below the box
+    _, g = prob.loglik_grad(x[None])
+    fd = _fd_grad(prob, x, 1e-6)
+    np.testing.assert_allclose(g[0, :4], fd[:4], rtol=1e-5, atol=1e-4)
+    # the penalty part alone: -(c/2)(clamp(u)-u)^2 per coordinate
+    lp_in = prob.loglik_grad(np.concatenate([np.clip(x[:4], wl.lo, wl.hi), x[4:]])[None], grad=False)[0]
+    assert prob.loglik_grad(x[None], grad=False)[0] < lp_in

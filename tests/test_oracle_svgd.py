@@ -1,0 +1,82 @@
+"""Pins of the oracle's SVGD step (Sec. IV-A, Eq. 1) (CPU only).
+
+* N = 1: the kernel is 1 and the repulsion vanishes, so phi is the gradient.
+* The median heuristic's median equals a brute-force sort of all pairwise
+  squared distances (lower middle element for an even count).
+* On a linear-Gaussian target N(mu, Sigma), iterating SVGD + Adam recovers
+  the closed-form mean and covariance (an approximate pin: SVGD's particle
+  approximation with N = 400 particles, stated tolerance).
+"""
+import numpy as np
+import pytest
+
+from oracle import pds_oracle as orc
+
+
+def test_single_particle_phi_is_gradient():
+    rng = np.random.default_rng(0)
+    u = rng.uniform(size=(1, 6))
+    g = rng.normal(size=(1, 6))
+    assert orc.bandwidth(1, orc.median_sqdist(u)) == 1.0
+    np.testing.assert_array_equal(orc.svgd_phi(u, g, 0.37), g)
+
+
+@pytest.mark.parametrize("N,M", [(2, 3), (3, 1), (4, 2), (17, 5), (64, 10)])
+def test_median_is_lower_middle_of_sorted_pairs(N, M):
+    rng = np.random.default_rng(N * 31 + M)
+    u = rng.uniform(size=(N, M))
+    d = np.sort([np.sum((u[i] - u[j]) ** 2) for i in range(N) for j in range(i + 1, N)])
+    assert orc.median_sqdist(u) == d[(len(d) - 1) // 2]
+
+
+def test_bandwidth_rule():
+    assert orc.bandwidth(100, 0.5) == pytest.approx(0.5 / np.log(100), rel=1e-15)
+    assert orc.bandwidth(50, 0.0) == 1.0
+    assert orc.bandwidth(1, 3.0) == 1.0
+
+
+def test_two_particles_repel_symmetrically():
+    """With zero gradient, two particles move apart along their difference."""
+    u = np.array([[0.4, 0.5], [0.6, 0.5]])
+    g = np.zeros_like(u)
+    bw = 0.3
+    phi = orc.svgd_phi(u, g, bw)
+    k = np.exp(-0.04 / bw)
+    # (1/N) * (2/bw) * (u_i - u_j) * k for the one other particle
+    np.testing.assert_allclose(phi[0], 0.5 * (2 / bw) * (u[0] - u[1]) * k, rtol=1e-14)
+    np.testing.assert_allclose(phi[1], -phi[0], rtol=1e-14)
+
+
+@pytest.mark.slow
+def test_linear_gaussian_posterior_recovered():
+    mu = np.array([0.3, -0.2])
+    Sig = np.array([[0.04, 0.018], [0.018, 0.025]])
+    Prec = np.linalg.inv(Sig)
+    lo, hi = np.array([-2.0, -2.0]), np.array([2.0, 2.0])
+    N = 400
+    rng = np.random.default_rng(42)
+    x = np.ascontiguousarray(rng.uniform(-1.0, 1.0, size=(N, 2)))
+    st = orc.SvgdState(N, 2, lo, hi, lr=2e-2, clamp=False)
+    for _ in range(1500):
+        grad = -(x - mu) @ Prec          # closed-form d log N(x | mu, Sigma) / dx
+        st.step(x, grad)
+    sd = np.sqrt(np.diag(Sig))
+    assert np.all(np.abs(x.mean(0) - mu) < 0.05 * sd)
+    C = np.cov(x.T)
+    assert np.all(np.abs(np.diag(C) - np.diag(Sig)) < 0.1 * np.diag(Sig))
+    assert abs(C[0, 1] - Sig[0, 1]) < 0.1 * np.sqrt(Sig[0, 0] * Sig[1, 1])
+
+
+def test_adam_step_on_shooting_states_and_clamp():
+    """Shooting rows follow plain Adam ascent on their own gradient; theta
+    rows are clamped to the box after the update."""
+    N, M, P = 3, 2, 4
+    lo, hi = np.array([0.0, 1.0]), np.array([1.0, 3.0])
+    x = np.ascontiguousarray([[0.999, 2.0, 0.1, 0.2], [0.5, 1.5, -0.3, 0.0], [0.2, 2.9, 1.0, 1.0]], dtype=float)
+    g = np.array([[50.0, 0.0, 1.0, -2.0], [0.0, 0.0, 0.5, 0.0], [0.0, 80.0, -1.0, 3.0]])
+    st = orc.SvgdState(N, P, lo, hi, lr=0.1)
+    x_before = x.copy()
+    st.step(x, g)
+    # first Adam step moves by lr * sign(g) (|g| >> eps)
+    np.testing.assert_allclose(x[:, 2:], x_before[:, 2:] + 0.1 * np.sign(g[:, 2:]), atol=1e-7)
+    assert np.all(x[:, :M] >= lo) and np.all(x[:, :M] <= hi)
