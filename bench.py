@@ -1,0 +1,362 @@
+#!/usr/bin/env python3
+"""Benchmark: one SVGD iteration of multiple-shooting inference per step.
+
+Workload: the 5-link damped planar chain (theta = 5 masses + 5 damping
+coefficients), T = 1000 steps at dt = 0.005, W = 20 shooting windows,
+N = 16384 particles, adjoint checkpoint stride K = 10 -- the largest particle
+count of the chain workload.  A step is log p + gradient of every particle
+(rollout + adjoint + window reduction) followed by the SVGD + Adam update
+(median bandwidth, phi, Adam).  Metric: particle-step-gradients per second =
+N * T / step time (one unit = one particle x one time step, forward and
+adjoint, with the SVGD update's time included).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pds|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Under torchrun each rank runs an independent
+replica (the chain problems are independent; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2109_08815_gb300 import workloads as wlmod  # noqa: E402
+
+METRIC = "particle-step-gradients/sec"
+UNIT = "particle-steps/s"
+N_DEFAULT = 16384
+K_CKPT = 10
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
+    """Algorithmic FP32 flops of one time step (FMA = 2): forward step with
+    its observation term, and the reverse (adjoint) step, counted from the
+    arithmetic of the specialised articulated-body recursion and its
+    hand-written reverse (recomputation for checkpointing excluded)."""
+    fwd = 69 * n + 3 * D + 1
+    rev = 148 * n + 3 * D
+    return fwd, rev
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_problem_inputs(N: int):
+    wl = wlmod.chain5(N=N)
+    return wl
+
+
+def oracle_rate(wl, obs, x, sample: int, threads: int):
+    """FP64 oracle: log p + gradient of `sample` particles (full T)."""
+    from oracle import pds_oracle as orc
+    op = orc.Problem(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
+                     theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs.astype(np.float64),
+                     obs_index=wl.obs_index, sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo,
+                     hi=wl.hi, g=wl.g, c_lim=wl.c_lim)
+    xs = np.ascontiguousarray(x[:sample].astype(np.float64))
+    t0 = time.perf_counter()
+    op.loglik_grad(xs, threads=threads)
+    dt = time.perf_counter() - t0
+    return sample * wl.T / dt, dt
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import pds_oracle as orc
+    orc.build()
+    wl = wlmod.chain5(N=args.n)
+    # true trajectory: the oracle's own FP64 rollout of the true parameters
+    st = orc.simulate(wl.mass, wl.length, wl.damping, wl.s0, wl.dt, wl.T, g=wl.g)
+    obs = wlmod.observations(wl, st).astype(np.float32)
+    x = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
+    threads = os.cpu_count() or 1
+    sample = args.ref_sample
+    op = orc.Problem(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
+                     theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs.astype(np.float64),
+                     obs_index=wl.obs_index, sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo,
+                     hi=wl.hi, g=wl.g, c_lim=wl.c_lim)
+    xs = np.ascontiguousarray(x[:sample].astype(np.float64))
+    svgd = orc.SvgdState(sample, wl.P, wl.lo, wl.hi, lr=wl.lr)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, g = op.loglik_grad(xs, threads=threads)
+        svgd.step(xs, g)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    value = sample * wl.T / step_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(wl, args.n, note=f"FP64 CPU oracle, {sample}-particle sample per step"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{sample} particles x T={wl.T} (log p + gradient) + SVGD step on the sample"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(wl, N, note=None):
+    c = {"workload": f"chain5 planar damped chain, N={N} particles, T={wl.T}, W={wl.W}, K={K_CKPT}",
+         "system": "5-link planar chain, point masses, viscous damping", "N": N, "T": wl.T, "W": wl.W,
+         "K": K_CKPT, "M": wl.M, "P": wl.P, "dt": wl.dt,
+         "l2": "flushed between timed steps (256 MiB device write outside the timed events)"}
+    if note:
+        c["note"] = note
+    return c
+
+
+def run_pds(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2109_08815_gb300 import api
+    world, rank, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = args.n
+    wl = wlmod.chain5(N=N)
+    stream = torch.cuda.Stream(device=dev)
+
+    # --- synthetic observations: roll out the true parameters with f_sim
+    with torch.cuda.stream(stream):
+        gen = api.Problem.from_workload(wl, np.zeros((wl.T, wl.D), np.float32), stream=stream)
+        th = torch.tensor(wl.theta_true, dtype=torch.float32, device=dev).reshape(wl.M, 1).contiguous()
+        states = gen.simulate(th)
+    stream.synchronize()
+    obs = wlmod.observations(wl, states[:, :, 0].cpu().numpy().astype(np.float64)).astype(np.float32)
+    gen.close()
+    x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
+
+    prob = api.Problem.from_workload(wl, obs, stream=stream, checkpoint_stride=K_CKPT)
+    prob.reserve(N)
+    svgd = api.Svgd(N, wl.M, wl.P, wl.lo, wl.hi, lr=wl.lr, stream=stream)
+    X = torch.from_numpy(np.ascontiguousarray(x0.T, dtype=np.float32)).to(dev)
+    logp = torch.empty(N, device=dev)
+    grad = torch.empty_like(X)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    L = api.lib()
+
+    def step():
+        rc = L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(grad), None)
+        api._check(rc, "pds_loglik_grad")
+        n1 = L.pds_last_launch_count()
+        return n1
+
+    def update():
+        rc = L.pds_svgd_step(svgd.handle, api._ptr(X), api._ptr(grad), None, None)
+        api._check(rc, "pds_svgd_step")
+        return L.pds_last_launch_count()
+
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+            update()
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches = 0
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    t_wall0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()
+            e0, e1, e2 = evs[k]
+            e0.record(stream)
+            launches += step()
+            e1.record(stream)
+            launches += update()
+            e2.record(stream)
+    stream.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    step_ms = [evs[k][0].elapsed_time(evs[k][2]) for k in range(args.steps)]
+    lg_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+        dist.barrier()
+    ms_per_step = t_total * 1e3 / args.steps
+    value = world * N * wl.T * args.steps / t_total
+
+    # --- end to end through the public C ABI with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        xh_t = torch.empty((wl.P, N), dtype=torch.float32, pin_memory=True)
+        lh_t = torch.empty(N, dtype=torch.float32, pin_memory=True)
+        xh, lh = xh_t.numpy(), lh_t.numpy()
+        xh[...] = X.cpu().numpy()
+        api.iterate_host(prob, svgd, xh, 1, lh)  # warm
+        ts = []
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            api.iterate_host(prob, svgd, xh, 1, lh)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = sum(ts) / len(ts)
+        if world > 1:
+            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * N * wl.T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": wl.P * N * 4,
+               "d2h_bytes_per_step": wl.P * N * 4 + N * 4}
+
+    # --- roofline of the dominant kernel (the fused rollout + adjoint)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_count = props.multi_processor_count
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    fwd, rev = flops_per_particle_step(wl.n, wl.D)
+    flops_launch = N * wl.T * (fwd + rev)
+    lg_s = statistics.mean(lg_ms) / 1e3
+    achieved = flops_launch / lg_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                "kernel": "rollout_kernel<5> (+ window_reduce, <1%)",
+                "peak_basis": f"FP32 {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max_mhz:.0f} MHz "
+                              "(MEASURED_PEAKS sm_max_mhz)",
+                "flops_per_particle_step": fwd + rev,
+                "loglik_grad_ms": statistics.mean(lg_ms), "svgd_step_ms": statistics.mean(step_ms) - statistics.mean(lg_ms)}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_measured_clock"] = achieved / (sm_count * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import pds_oracle as orc
+        orc.build()
+        threads = os.cpu_count() or 1
+        rate, secs = oracle_rate(wl, obs, x0, args.ref_sample_baseline, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.ref_sample_baseline} particles x T={wl.T} log p + gradient (FP64, forward-mode "
+                         f"duals), {secs:.1f} s on {threads} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(wl, N),
+            "svgd_iters_per_sec": 1e3 / ms_per_step, "gpu_launches": launches, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed": t_wall,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+# dram bytes per rollout launch from the committed ncu capture of this kernel
+# (None until a capture of the current kernel exists)
+TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pds", choices=["pds", "reference"])
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
+    ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pds(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

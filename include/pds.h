@@ -1,0 +1,186 @@
+/*
+ * pds.h -- C ABI of the GB300 (sm_103a) library for probabilistic inference
+ * of simulation parameters by multiple-shooting SVGD over a differentiable
+ * planar articulated-body simulator.
+ *
+ * The operations follow the paper's problem statement (Sec. III, Algorithm 1
+ * inputs): a differentiable simulator f_sim, an observation function f_obs,
+ * the start state of the measured trajectory, the measured trajectory, a
+ * step-size rule (Adam) and a kernel (RBF).  The library evaluates, for every
+ * particle, the multiple-shooting log-likelihood (Sec. IV-C, Eqs. 2, 4, 5)
+ * plus the parameter-limit prior (Sec. IV-D) and its gradient, and applies the
+ * SVGD update of Eq. (1).
+ *
+ * Conventions shared by every entry point:
+ *  - Return PDS_OK (0) on success, a negative PDS_ERR_* code otherwise;
+ *    pds_last_error() gives a message for the calling thread.  No C++
+ *    exception crosses the ABI.
+ *  - Pointers documented "device" must be CUDA device (or managed) memory
+ *    owned by the caller; "host" pointers are read during the call only.
+ *  - Particle arrays are structure-of-arrays: element (row r, particle i)
+ *    lives at [r * N + i] (particle index fastest).
+ *  - Calls are asynchronous on the CUDA stream given at creation unless
+ *    stated otherwise; the caller synchronises before reading results.
+ *  - Objects are not thread-safe: one host thread drives one object at a time.
+ */
+#ifndef PDS_H_
+#define PDS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDS_OK 0
+#define PDS_ERR_ARG (-1)         /* invalid argument (NULL, size out of range) */
+#define PDS_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed       */
+#define PDS_ERR_OOM (-3)         /* device allocation failed                   */
+#define PDS_ERR_NONFINITE (-4)   /* reserved: non-finite result reported       */
+#define PDS_ERR_UNSUPPORTED (-7) /* configuration outside the compiled range   */
+
+#define PDS_SYSTEM_PLANAR_CHAIN 1
+
+#define PDS_PARAM_MASS 0    /* point mass at the tip of a link [kg]          */
+#define PDS_PARAM_LENGTH 1  /* link length [m]                               */
+#define PDS_PARAM_DAMPING 2 /* viscous joint damping [N m s / rad]           */
+
+#define PDS_MAX_LINKS 8
+#define PDS_MAX_THETA 16
+#define PDS_MAX_WINDOW_STEPS 4096
+
+/* Articulated system (Appendix B-A: the simulator computes joint
+ * accelerations with the articulated-body algorithm and integrates them with
+ * semi-implicit Euler).  PDS_SYSTEM_PLANAR_CHAIN: a planar serial chain of
+ * revolute joints with relative joint angles, q = 0 hanging straight down
+ * along -y, a point mass at the tip of each link and joint torque
+ * tau_i = -damping_i * qd_i.  State s = [q_0..q_{n-1}, qd_0..qd_{n-1}]. */
+typedef struct pds_system_desc {
+  int kind;               /* PDS_SYSTEM_PLANAR_CHAIN                        */
+  int n_links;            /* 1..PDS_MAX_LINKS                                */
+  const double* mass;     /* host [n_links]; used where theta does not override */
+  const double* length;   /* host [n_links]                                  */
+  const double* damping;  /* host [n_links]                                  */
+  double gravity;         /* magnitude of gravity along -y [m/s^2]           */
+  int n_theta;            /* M = dim theta, 1..PDS_MAX_THETA                 */
+  const int* theta_kind;  /* host [M], PDS_PARAM_*                           */
+  const int* theta_link;  /* host [M], 0-based link index; each (kind, link) at most once */
+} pds_system_desc;
+
+typedef struct pds_problem* pds_problem_t;
+typedef struct pds_svgd* pds_svgd_t;
+
+/* Create a multiple-shooting inference problem (Sec. IV-C).
+ *  dt, T      : time step and number of steps of the measured trajectory.
+ *  windows    : number of shooting windows W, 1 <= W <= T.  Window w covers
+ *               steps t_w+1..t_{w+1} with t_w = floor(w*T/W); window 0 starts
+ *               at s0, window w > 0 at the particle's shooting state s^s_w.
+ *               At most PDS_MAX_WINDOW_STEPS steps per window.
+ *  obs        : host [T][D] float; row t-1 is the observation x_t (Eq. 2).
+ *  obs_index  : host [D]; observation column d is state component obs_index[d]
+ *               (f_obs selects state components; each at most once).
+ *  sigma_obs  : observation noise std (Eq. 2); sigma_def: defect std (Eq. 4).
+ *  s0         : host [2n] known start state s_0 (Sec. III).
+ *  theta_lo/hi: host [M] parameter box of the uniform prior (Sec. IV-D).
+ *  c_lim      : stiffness of the smooth limit penalty added to log p_lim,
+ *               -(c_lim/2) * ||clamp(u,0,1) - u||^2 with u the unit-box
+ *               coordinates of theta (0 disables it).
+ *  cuda_stream: cudaStream_t the problem's work is queued on (NULL = legacy
+ *               default stream).
+ * The problem copies everything it needs to the device; it owns that memory
+ * and its workspace.  Particle layout: P = M + (W-1)*2n rows: theta first,
+ * then s^s_1 .. s^s_{W-1}, each 2n rows. */
+int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows,
+                       const float* obs, int D, const int* obs_index,
+                       double sigma_obs, double sigma_def, const float* s0,
+                       const float* theta_lo, const float* theta_hi, double c_lim,
+                       void* cuda_stream, pds_problem_t* out);
+
+/* Release the problem and all device memory it owns (synchronises its stream). */
+int pds_problem_destroy(pds_problem_t p);
+
+/* Report M (= dim theta), S (= 2n, state size) and P (= M + (W-1)*S). */
+int pds_problem_layout(pds_problem_t p, int* M, int* S, int* P);
+
+/* Adjoint checkpoint stride K (default 10): the reverse sweep keeps one
+ * state every K steps and recomputes the states in between (the gradient is
+ * the same for every K up to rounding).  1 <= K <= PDS_MAX_WINDOW_STEPS. */
+int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
+
+/* Allocate the workspace for up to N_max particles now, so that later calls
+ * with N <= N_max allocate nothing (e.g. before capturing a CUDA graph).
+ * Calls with a larger N grow the workspace (synchronising the stream). */
+int pds_problem_reserve(pds_problem_t p, int N_max);
+
+/* log p(theta_bar) and its gradient for N particles (Sec. IV-C, Eq. 5 in log
+ * space, plus log p_lim of Sec. IV-D):
+ *   log p = sum_t log N(x_t | f_obs(s_t), sigma_obs^2 I)
+ *         + sum_{w=1}^{W-1} log N(s^s_w | s_end(w-1), sigma_def^2 I)
+ *         - sum_k log(hi_k - lo_k) - (c_lim/2) ||clamp(u,0,1) - u||^2
+ *  particles: device [P][N] float (read only).
+ *  logp     : device [N] float (written).
+ *  grad     : device [P][N] float, d log p / d particles (ascent direction),
+ *             or NULL to evaluate log p only.
+ *  status   : device [N] int32 or NULL; 0 = finite, 1 = log p or a gradient
+ *             entry was not finite (the particle's values are then
+ *             meaningless).
+ * 1 <= N <= 1<<20. */
+int pds_loglik_grad(pds_problem_t p, const float* particles, int N, float* logp,
+                    float* grad, int32_t* status);
+
+/* f_sim (Sec. III): roll out T steps from s0 for N parameter vectors.
+ *  theta : device [M][N]; states: device [T+1][2n][N] (row 0 = s0). */
+int pds_simulate(pds_problem_t p, const float* theta, int N, float* states);
+
+/* SVGD state for N particles of P rows whose first M rows are theta
+ * (Eq. 1 / Algorithm 1).  The kernel is the RBF kernel
+ * k(a, b) = exp(-||u_a - u_b||^2 / bw) on unit-box coordinates
+ * u = (theta - lo) / (hi - lo); bw is the lower median of the N(N-1)/2
+ * pairwise squared distances divided by log N (1 if N < 2 or the median is
+ * 0), the median heuristic of Sec. IV-A.  theta moves by Adam ascent
+ * (lr, beta1, beta2, eps) on phi in u coordinates, then (if clamp) is clipped
+ * to the box; rows M..P-1 (shooting states) move by Adam ascent on their own
+ * gradient.  theta_lo/hi: host [M].  1 <= N <= 65536, 1 <= M <= 16. */
+int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* theta_hi,
+                    double lr, double beta1, double beta2, double eps, int clamp,
+                    void* cuda_stream, pds_svgd_t* out);
+int pds_svgd_destroy(pds_svgd_t s);
+
+/* One SVGD + Adam update in place.
+ *  particles    : device [P][N] float (read and written).
+ *  grad         : device [P][N] float, d log p / d particles.
+ *  bandwidth_out: device float scalar or NULL (the bandwidth bw used).
+ *  phi_out      : device [M][N] float or NULL (phi in u coordinates). */
+int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad,
+                  float* bandwidth_out, float* phi_out);
+
+/* Reset Adam moments and the step count to zero. */
+int pds_svgd_reset(pds_svgd_t s);
+
+/* Algorithm 1 loop on the device: `iters` times { log p and gradient of all
+ * particles; SVGD + Adam update }.  particles: device [P][N] in/out;
+ * logp: device [N] or NULL, receives log p evaluated in the last iteration
+ * (before its update).  N must equal the SVGD state's N. */
+int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, float* logp);
+
+/* Same as pds_iterate for host-resident data: copies particles (host [P][N])
+ * to the device, runs `iters` iterations, copies the updated particles and
+ * the last log p (host [N] or NULL) back, and synchronises the stream.
+ * Pinned host memory gives the fastest copies. */
+int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters,
+                     float* logp_host);
+
+/* Number of kernel launches the last pds_loglik_grad / pds_svgd_step /
+ * pds_iterate call made (for launch accounting). */
+int pds_last_launch_count(void);
+
+/* Human-readable name of a status code; message of the last error on the
+ * calling thread. */
+const char* pds_strerror(int code);
+const char* pds_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PDS_H_ */

@@ -1,0 +1,288 @@
+"""Thin Python binding of libpds (include/pds.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch only
+supplies device memory and streams.  If ``libpds.so`` is missing or no CUDA
+device is present, the calls raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpds.so")
+
+PDS_SYSTEM_PLANAR_CHAIN = 1
+PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
+
+_lib = None
+_lock = threading.Lock()
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class _SystemDesc(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("n_links", ctypes.c_int),
+        ("mass", _dp),
+        ("length", _dp),
+        ("damping", _dp),
+        ("gravity", ctypes.c_double),
+        ("n_theta", ctypes.c_int),
+        ("theta_kind", _ip),
+        ("theta_link", _ip),
+    ]
+
+
+EXPORTS = {
+    "pds_problem_create": ([ctypes.POINTER(_SystemDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
+                            ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
+                            _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_problem_destroy": ([_vp], ctypes.c_int),
+    "pds_problem_layout": ([_vp, _ip, _ip, _ip], ctypes.c_int),
+    "pds_problem_set_checkpoint_stride": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pds_problem_reserve": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
+    "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pds_svgd_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_svgd_destroy": ([_vp], ctypes.c_int),
+    "pds_svgd_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "pds_svgd_reset": ([_vp], ctypes.c_int),
+    "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pds_iterate_host": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pds_last_launch_count": ([], ctypes.c_int),
+    "pds_strerror": ([ctypes.c_int], ctypes.c_char_p),
+    "pds_last_error": ([], ctypes.c_char_p),
+}
+
+
+class PdsError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load libpds.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise PdsError(f"{LIB_PATH} is missing: build the CUDA library first "
+                               "(python -c 'import __graft_entry__ as g; g.build()')")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in EXPORTS.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        L = lib()
+        raise PdsError(f"{what}: {L.pds_strerror(rc).decode()} ({rc}): {L.pds_last_error().decode()}")
+
+
+def last_launch_count() -> int:
+    return int(lib().pds_last_launch_count())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t: torch.Tensor, dtype, name):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise PdsError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream), stream
+
+
+class Problem:
+    """A multiple-shooting inference problem (pds_problem_create).
+
+    Arguments mirror :c:func:`pds_problem_create`; host arrays are numpy.
+    ``obs`` is [T][D] with row t-1 = x_t.
+    """
+
+    def __init__(self, *, mass, length, damping, theta_kind, theta_link, dt, T, W, obs, obs_index, sigma_obs,
+                 sigma_def, s0, lo, hi, g=9.81, c_lim=1e4, stream=None, checkpoint_stride=None):
+        L = lib()
+        self._keep = []
+
+        def d(x):
+            a = np.ascontiguousarray(x, dtype=np.float64)
+            self._keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        def i(x):
+            a = np.ascontiguousarray(x, dtype=np.int32)
+            self._keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        def f(x):
+            a = np.ascontiguousarray(x, dtype=np.float32)
+            self._keep.append(a)
+            return a.ctypes.data_as(_fp)
+
+        n = len(mass)
+        obs = np.ascontiguousarray(obs, dtype=np.float32)
+        self.T, self.W, self.n = int(T), int(W), n
+        sysd = _SystemDesc(kind=PDS_SYSTEM_PLANAR_CHAIN, n_links=n, mass=d(mass), length=d(length),
+                           damping=d(damping), gravity=float(g), n_theta=len(theta_kind), theta_kind=i(theta_kind),
+                           theta_link=i(theta_link))
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_problem_create(ctypes.byref(sysd), float(dt), self.T, self.W, f(obs), obs.shape[1],
+                                    i(obs_index), float(sigma_obs), float(sigma_def), f(s0), f(lo), f(hi),
+                                    float(c_lim), self._stream_h, ctypes.byref(h)), "pds_problem_create")
+        self._h = h
+        self._keep = []
+        M, S, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.pds_problem_layout(h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
+        self.M, self.S, self.P = M.value, S.value, P.value
+        if checkpoint_stride is not None:
+            self.set_checkpoint_stride(checkpoint_stride)
+
+    @classmethod
+    def from_workload(cls, wl, obs, **kw):
+        return cls(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
+                   theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs, obs_index=wl.obs_index,
+                   sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo, hi=wl.hi, g=wl.g,
+                   c_lim=wl.c_lim, **kw)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pds_problem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_checkpoint_stride(self, K: int):
+        _check(lib().pds_problem_set_checkpoint_stride(self._h, int(K)), "pds_problem_set_checkpoint_stride")
+
+    def reserve(self, N: int):
+        _check(lib().pds_problem_reserve(self._h, int(N)), "pds_problem_reserve")
+
+    def loglik_grad(self, particles: torch.Tensor, grad: bool = True, out=None):
+        """log p and (optionally) d log p / d particles for particles [P][N]."""
+        _need_cuda(particles, torch.float32, "particles")
+        assert particles.dim() == 2 and particles.shape[0] == self.P, (particles.shape, self.P)
+        N = particles.shape[1]
+        if out is None:
+            logp = torch.empty(N, device=particles.device, dtype=torch.float32)
+            g = torch.empty_like(particles) if grad else None
+            status = torch.empty(N, device=particles.device, dtype=torch.int32)
+        else:
+            logp, g, status = out
+        _check(lib().pds_loglik_grad(self._h, _ptr(particles), N, _ptr(logp), _ptr(g), _ptr(status)),
+               "pds_loglik_grad")
+        return logp, g, status
+
+    def simulate(self, theta: torch.Tensor) -> torch.Tensor:
+        """f_sim for theta [M][N]; returns states [T+1][S][N]."""
+        _need_cuda(theta, torch.float32, "theta")
+        N = theta.shape[1]
+        states = torch.empty((self.T + 1, self.S, N), device=theta.device, dtype=torch.float32)
+        _check(lib().pds_simulate(self._h, _ptr(theta), N, _ptr(states)), "pds_simulate")
+        return states
+
+
+class Svgd:
+    """SVGD + Adam state (pds_svgd_create)."""
+
+    def __init__(self, N, M, P, lo, hi, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, clamp=True, stream=None):
+        L = lib()
+        lo = np.ascontiguousarray(lo, dtype=np.float32)
+        hi = np.ascontiguousarray(hi, dtype=np.float32)
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_svgd_create(int(N), int(M), int(P), lo.ctypes.data_as(_fp), hi.ctypes.data_as(_fp), float(lr),
+                                 float(beta1), float(beta2), float(eps), int(bool(clamp)), self._stream_h,
+                                 ctypes.byref(h)), "pds_svgd_create")
+        self._h = h
+        self.N, self.M, self.P = int(N), int(M), int(P)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pds_svgd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check(lib().pds_svgd_reset(self._h), "pds_svgd_reset")
+
+    def step(self, particles: torch.Tensor, grad: torch.Tensor, return_phi: bool = False):
+        """In-place update of particles [P][N]; returns (bandwidth tensor, phi or None)."""
+        _need_cuda(particles, torch.float32, "particles")
+        _need_cuda(grad, torch.float32, "grad")
+        bw = torch.empty(1, device=particles.device, dtype=torch.float32)
+        phi = torch.empty((self.M, self.N), device=particles.device, dtype=torch.float32) if return_phi else None
+        _check(lib().pds_svgd_step(self._h, _ptr(particles), _ptr(grad), _ptr(bw), _ptr(phi)), "pds_svgd_step")
+        return bw, phi
+
+
+def iterate(problem: Problem, svgd: Svgd, particles: torch.Tensor, iters: int, logp: torch.Tensor | None = None):
+    """Algorithm 1 on the device: iters x (log p + gradient, SVGD update)."""
+    _need_cuda(particles, torch.float32, "particles")
+    _check(lib().pds_iterate(problem.handle, svgd.handle, _ptr(particles), int(iters), _ptr(logp)), "pds_iterate")
+
+
+def iterate_host(problem: Problem, svgd: Svgd, particles: np.ndarray, iters: int, logp: np.ndarray | None = None):
+    """Algorithm 1 on host-resident float32 arrays (copies inside the call)."""
+    assert particles.dtype == np.float32 and particles.flags.c_contiguous
+    lp = None if logp is None else ctypes.c_void_p(logp.ctypes.data)
+    _check(lib().pds_iterate_host(problem.handle, svgd.handle, ctypes.c_void_p(particles.ctypes.data), int(iters),
+                                  lp), "pds_iterate_host")
+
+
+class LogLik(torch.autograd.Function):
+    """log p(particles) as a differentiable torch op: the backward pass uses
+    the hand-written adjoint computed by the same kernel launch."""
+
+    @staticmethod
+    def forward(ctx, particles, problem):
+        logp, g, _ = problem.loglik_grad(particles.detach().contiguous(), grad=True)
+        ctx.save_for_backward(g)
+        return logp
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return g * grad_out[None, :], None
+
+
+def loglik(particles: torch.Tensor, problem: Problem) -> torch.Tensor:
+    return LogLik.apply(particles, problem)

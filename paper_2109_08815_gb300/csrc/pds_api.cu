@@ -1,0 +1,420 @@
+// C ABI of libpds (declared in include/pds.h): argument checking, device
+// memory ownership and kernel dispatch.  No torch types cross this boundary.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "pds_internal.cuh"
+
+namespace pds {
+template <int NL>
+cudaError_t launch_rollout_nl(const ChainParams&, const float*, int, const Partials&, int, cudaStream_t);
+template <int NL>
+cudaError_t launch_simulate_nl(const ChainParams&, const float*, int, float*, cudaStream_t);
+
+static thread_local std::string g_err;
+static thread_local int g_launches = 0;
+
+static int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(e == cudaErrorMemoryAllocation ? PDS_ERR_OOM : PDS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
+                           cudaStream_t st) {
+  switch (c.n) {
+    case 1: return launch_rollout_nl<1>(c, X, N, parts, grad, st);
+    case 2: return launch_rollout_nl<2>(c, X, N, parts, grad, st);
+    case 3: return launch_rollout_nl<3>(c, X, N, parts, grad, st);
+    case 4: return launch_rollout_nl<4>(c, X, N, parts, grad, st);
+    case 5: return launch_rollout_nl<5>(c, X, N, parts, grad, st);
+    case 6: return launch_rollout_nl<6>(c, X, N, parts, grad, st);
+    case 7: return launch_rollout_nl<7>(c, X, N, parts, grad, st);
+    case 8: return launch_rollout_nl<8>(c, X, N, parts, grad, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st) {
+  switch (c.n) {
+    case 1: return launch_simulate_nl<1>(c, theta, N, states, st);
+    case 2: return launch_simulate_nl<2>(c, theta, N, states, st);
+    case 3: return launch_simulate_nl<3>(c, theta, N, states, st);
+    case 4: return launch_simulate_nl<4>(c, theta, N, states, st);
+    case 5: return launch_simulate_nl<5>(c, theta, N, states, st);
+    case 6: return launch_simulate_nl<6>(c, theta, N, states, st);
+    case 7: return launch_simulate_nl<7>(c, theta, N, states, st);
+    case 8: return launch_simulate_nl<8>(c, theta, N, states, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace pds
+
+using namespace pds;
+
+struct pds_problem {
+  ChainParams c;
+  cudaStream_t stream;
+  float* d_obs = nullptr;
+  int cap_N = 0;          // workspace capacity in particles
+  int cap_K = 0;          // checkpoint stride the tape was sized for
+  Partials parts{};
+  // buffers used by pds_iterate / pds_iterate_host
+  int it_N = 0;
+  float* d_grad = nullptr;
+  float* d_logp = nullptr;
+  float* d_x = nullptr;
+};
+
+struct pds_svgd {
+  SvgdParams sp;
+  SvgdWork w{};
+  cudaStream_t stream;
+};
+
+static void free_parts(Partials& p) {
+  cudaFree(p.lp);
+  cudaFree(p.th);
+  cudaFree(p.start);
+  cudaFree(p.next);
+  cudaFree(p.tape);
+  p = Partials{};
+}
+
+static int ensure_workspace(pds_problem* p, int N) {
+  if (N <= p->cap_N && p->cap_K == p->c.K) return PDS_OK;
+  const int newN = N > p->cap_N ? N : p->cap_N;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  free_parts(p->parts);
+  p->cap_N = 0;
+  const ChainParams& c = p->c;
+  const size_t Nn = (size_t)newN, W = (size_t)c.W, S = (size_t)c.S, M = (size_t)c.M;
+  const size_t U = Nn * W;
+  const size_t tape = ((size_t)c.max_seg + (size_t)c.K) * S * U;
+  if ((e = cudaMalloc(&p->parts.lp, W * Nn * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->parts.th, W * (M ? M : 1) * Nn * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->parts.start, W * S * Nn * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->parts.next, W * S * Nn * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->parts.tape, tape * sizeof(float))) != cudaSuccess) {
+    free_parts(p->parts);
+    return cuda_fail(e, "workspace allocation");
+  }
+  p->cap_N = newN;
+  p->cap_K = c.K;
+  return PDS_OK;
+}
+
+static void update_segments(ChainParams& c) {
+  int hmax = 0;
+  for (int w = 0; w < c.W; ++w) {
+    const int h = (int)(((long long)(w + 1) * c.T) / c.W - ((long long)w * c.T) / c.W);
+    if (h > hmax) hmax = h;
+  }
+  c.max_seg = (hmax + c.K - 1) / c.K;
+}
+
+extern "C" {
+
+const char* pds_strerror(int code) {
+  switch (code) {
+    case PDS_OK: return "ok";
+    case PDS_ERR_ARG: return "invalid argument";
+    case PDS_ERR_CUDA: return "CUDA error";
+    case PDS_ERR_OOM: return "out of device memory";
+    case PDS_ERR_NONFINITE: return "non-finite value";
+    case PDS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+const char* pds_last_error(void) { return g_err.c_str(); }
+
+int pds_last_launch_count(void) { return g_launches; }
+
+int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows, const float* obs, int D,
+                       const int* obs_index, double sigma_obs, double sigma_def, const float* s0,
+                       const float* theta_lo, const float* theta_hi, double c_lim, void* cuda_stream,
+                       pds_problem_t* out) {
+  if (!out) return fail(PDS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!sys || !obs || !obs_index || !s0 || !theta_lo || !theta_hi)
+    return fail(PDS_ERR_ARG, "NULL argument");
+  if (sys->kind != PDS_SYSTEM_PLANAR_CHAIN) return fail(PDS_ERR_UNSUPPORTED, "unknown system kind %d", sys->kind);
+  const int n = sys->n_links;
+  if (n < 1 || n > PDS_MAX_LINKS) return fail(PDS_ERR_UNSUPPORTED, "n_links %d outside 1..%d", n, PDS_MAX_LINKS);
+  if (!sys->mass || !sys->length || !sys->damping) return fail(PDS_ERR_ARG, "NULL link parameter array");
+  const int M = sys->n_theta;
+  if (M < 1 || M > PDS_MAX_THETA) return fail(PDS_ERR_UNSUPPORTED, "n_theta %d outside 1..%d", M, PDS_MAX_THETA);
+  if (M > 0 && (!sys->theta_kind || !sys->theta_link)) return fail(PDS_ERR_ARG, "NULL theta map");
+  if (!(dt > 0.0) || T < 1 || windows < 1 || windows > T) return fail(PDS_ERR_ARG, "bad dt/T/windows");
+  if (D < 1 || D > 2 * n) return fail(PDS_ERR_ARG, "D %d outside 1..%d", D, 2 * n);
+  if (!(sigma_obs > 0.0) || !(sigma_def > 0.0) || !(c_lim >= 0.0)) return fail(PDS_ERR_ARG, "bad sigma or c_lim");
+
+  ChainParams c;
+  memset(&c, 0, sizeof(c));
+  c.n = n; c.M = M; c.T = T; c.W = windows; c.D = D; c.S = 2 * n; c.P = M + (windows - 1) * 2 * n;
+  c.K = 10;
+  c.dt = (float)dt;
+  c.g = (float)sys->gravity;
+  c.inv_so2 = (float)(1.0 / (sigma_obs * sigma_obs));
+  c.obs_const = (float)(-0.5 * D * log(2.0 * M_PI * sigma_obs * sigma_obs));
+  c.inv_sd2 = (float)(1.0 / (sigma_def * sigma_def));
+  c.def_const = (float)(-0.5 * (2 * n) * log(2.0 * M_PI * sigma_def * sigma_def));
+  c.c_lim = (float)c_lim;
+  for (int j = 0; j < PDS_MAX_LINKS; ++j) { c.mass_theta[j] = c.length_theta[j] = c.damp_theta[j] = -1; }
+  for (int j = 0; j < 2 * PDS_MAX_LINKS; ++j) c.obs_col[j] = -1;
+  for (int j = 0; j < n; ++j) {
+    c.mass[j] = (float)sys->mass[j];
+    c.length[j] = (float)sys->length[j];
+    c.damping[j] = (float)sys->damping[j];
+  }
+  double lim = 0.0;
+  for (int k = 0; k < M; ++k) {
+    const int kind = sys->theta_kind[k], link = sys->theta_link[k];
+    if (link < 0 || link >= n) return fail(PDS_ERR_ARG, "theta_link[%d] = %d out of range", k, link);
+    int* slot = kind == PDS_PARAM_MASS ? c.mass_theta : kind == PDS_PARAM_LENGTH ? c.length_theta
+              : kind == PDS_PARAM_DAMPING ? c.damp_theta : nullptr;
+    if (!slot) return fail(PDS_ERR_ARG, "theta_kind[%d] = %d unknown", k, kind);
+    if (slot[link] >= 0) return fail(PDS_ERR_ARG, "theta entry %d duplicates a parameter", k);
+    slot[link] = k;
+    if (!(theta_hi[k] > theta_lo[k])) return fail(PDS_ERR_ARG, "theta box %d empty", k);
+    c.lo[k] = theta_lo[k];
+    c.hi[k] = theta_hi[k];
+    lim -= log((double)theta_hi[k] - (double)theta_lo[k]);
+  }
+  c.lim_const = (float)lim;
+  for (int d = 0; d < D; ++d) {
+    const int idx = obs_index[d];
+    if (idx < 0 || idx >= 2 * n) return fail(PDS_ERR_ARG, "obs_index[%d] = %d out of range", d, idx);
+    if (c.obs_col[idx] >= 0) return fail(PDS_ERR_ARG, "obs_index repeats state %d", idx);
+    c.obs_col[idx] = d;
+  }
+  for (int j = 0; j < 2 * n; ++j) c.s0[j] = s0[j];
+  int hmax = 0;
+  for (int w = 0; w < windows; ++w) {
+    const int h = (int)(((long long)(w + 1) * T) / windows - ((long long)w * T) / windows);
+    if (h > hmax) hmax = h;
+  }
+  if (hmax > PDS_MAX_WINDOW_STEPS) return fail(PDS_ERR_UNSUPPORTED, "window of %d steps > %d", hmax,
+                                                PDS_MAX_WINDOW_STEPS);
+  update_segments(c);
+
+  pds_problem* p = new pds_problem();
+  p->c = c;
+  p->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaMalloc(&p->d_obs, (size_t)T * D * sizeof(float));
+  if (e != cudaSuccess) { delete p; return cuda_fail(e, "cudaMalloc obs"); }
+  e = cudaMemcpyAsync(p->d_obs, obs, (size_t)T * D * sizeof(float), cudaMemcpyHostToDevice, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) { cudaFree(p->d_obs); delete p; return cuda_fail(e, "copy obs"); }
+  p->c.obs = p->d_obs;
+  *out = p;
+  return PDS_OK;
+}
+
+int pds_problem_destroy(pds_problem_t p) {
+  if (!p) return PDS_OK;
+  cudaStreamSynchronize(p->stream);
+  free_parts(p->parts);
+  cudaFree(p->d_obs);
+  cudaFree(p->d_grad);
+  cudaFree(p->d_logp);
+  cudaFree(p->d_x);
+  delete p;
+  return PDS_OK;
+}
+
+int pds_problem_layout(pds_problem_t p, int* M, int* S, int* P) {
+  if (!p) return fail(PDS_ERR_ARG, "NULL problem");
+  if (M) *M = p->c.M;
+  if (S) *S = p->c.S;
+  if (P) *P = p->c.P;
+  return PDS_OK;
+}
+
+int pds_problem_set_checkpoint_stride(pds_problem_t p, int K) {
+  if (!p) return fail(PDS_ERR_ARG, "NULL problem");
+  if (K < 1 || K > PDS_MAX_WINDOW_STEPS) return fail(PDS_ERR_ARG, "K %d outside 1..%d", K, PDS_MAX_WINDOW_STEPS);
+  p->c.K = K;
+  update_segments(p->c);
+  return PDS_OK;
+}
+
+int pds_problem_reserve(pds_problem_t p, int N_max) {
+  if (!p) return fail(PDS_ERR_ARG, "NULL problem");
+  if (N_max < 1 || N_max > (1 << 20)) return fail(PDS_ERR_ARG, "N_max %d outside 1..2^20", N_max);
+  return ensure_workspace(p, N_max);
+}
+
+int pds_loglik_grad(pds_problem_t p, const float* particles, int N, float* logp, float* grad, int32_t* status) {
+  g_launches = 0;
+  if (!p || !particles || !logp) return fail(PDS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
+  int rc = ensure_workspace(p, N);
+  if (rc != PDS_OK) return rc;
+  cudaError_t e = launch_rollout(p->c, particles, N, p->parts, grad != nullptr, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
+  e = launch_window_reduce(p->c, particles, N, p->parts, logp, grad, status, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "window reduce launch");
+  g_launches = 2;
+  return PDS_OK;
+}
+
+int pds_simulate(pds_problem_t p, const float* theta, int N, float* states) {
+  g_launches = 0;
+  if (!p || !theta || !states) return fail(PDS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
+  cudaError_t e = launch_simulate(p->c, theta, N, states, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "simulate launch");
+  g_launches = 1;
+  return PDS_OK;
+}
+
+int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* theta_hi, double lr, double beta1,
+                    double beta2, double eps, int clamp, void* cuda_stream, pds_svgd_t* out) {
+  if (!out) return fail(PDS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (N < 1 || N > 65536) return fail(PDS_ERR_ARG, "N %d outside 1..65536", N);
+  if (M < 1 || M > PDS_MAX_THETA || P < M) return fail(PDS_ERR_ARG, "bad M %d / P %d", M, P);
+  if (!theta_lo || !theta_hi) return fail(PDS_ERR_ARG, "NULL box");
+  if (!(lr > 0.0) || !(beta1 >= 0.0 && beta1 < 1.0) || !(beta2 >= 0.0 && beta2 < 1.0) || !(eps >= 0.0))
+    return fail(PDS_ERR_ARG, "bad Adam constants");
+  pds_svgd* s = new pds_svgd();
+  memset(&s->sp, 0, sizeof(s->sp));
+  s->sp.N = N; s->sp.M = M; s->sp.P = P;
+  for (int k = 0; k < M; ++k) {
+    if (!(theta_hi[k] > theta_lo[k])) { delete s; return fail(PDS_ERR_ARG, "theta box %d empty", k); }
+    s->sp.lo[k] = theta_lo[k];
+    s->sp.hi[k] = theta_hi[k];
+  }
+  s->sp.lr = (float)lr; s->sp.b1 = (float)beta1; s->sp.b2 = (float)beta2; s->sp.eps = (float)eps;
+  s->sp.clamp = clamp ? 1 : 0;
+  s->stream = (cudaStream_t)cuda_stream;
+  s->w.chunks = svgd_phi_chunks(N);
+  const size_t MN = (size_t)M * N, PN = (size_t)P * N;
+  cudaError_t e;
+  if ((e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->w.gu, MN * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->w.phi_part, (size_t)s->w.chunks * MN * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->w.adam_m, PN * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->w.adam_v, PN * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->w.ctl, sizeof(SvgdCtl))) != cudaSuccess) {
+    pds_svgd_destroy(s);
+    return cuda_fail(e, "svgd allocation");
+  }
+  *out = s;
+  return pds_svgd_reset(s);
+}
+
+int pds_svgd_reset(pds_svgd_t s) {
+  if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
+  const size_t PN = (size_t)s->sp.P * s->sp.N;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(s->w.adam_m, 0, PN * sizeof(float), s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->w.adam_v, 0, PN * sizeof(float), s->stream)) != cudaSuccess ||
+      (e = cudaMemsetAsync(s->w.ctl, 0, sizeof(SvgdCtl), s->stream)) != cudaSuccess)
+    return cuda_fail(e, "svgd reset");
+  return PDS_OK;
+}
+
+int pds_svgd_destroy(pds_svgd_t s) {
+  if (!s) return PDS_OK;
+  cudaStreamSynchronize(s->stream);
+  cudaFree(s->w.u);
+  cudaFree(s->w.gu);
+  cudaFree(s->w.phi_part);
+  cudaFree(s->w.adam_m);
+  cudaFree(s->w.adam_v);
+  cudaFree(s->w.ctl);
+  delete s;
+  return PDS_OK;
+}
+
+int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* bandwidth_out, float* phi_out) {
+  g_launches = 0;
+  if (!s || !particles || !grad) return fail(PDS_ERR_ARG, "NULL argument");
+  int n = 0;
+  cudaError_t e = launch_svgd_step(s->sp, s->w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
+  g_launches = n;
+  if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
+  return PDS_OK;
+}
+
+static int ensure_iter_buffers(pds_problem* p, int N) {
+  if (p->it_N >= N) return PDS_OK;
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->d_grad);
+  cudaFree(p->d_logp);
+  cudaFree(p->d_x);
+  p->d_grad = p->d_logp = p->d_x = nullptr;
+  p->it_N = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_grad, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_logp, (size_t)N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_x, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess)
+    return cuda_fail(e, "iteration buffers");
+  p->it_N = N;
+  return PDS_OK;
+}
+
+int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, float* logp) {
+  if (!p || !s || !particles) return fail(PDS_ERR_ARG, "NULL argument");
+  if (iters < 0) return fail(PDS_ERR_ARG, "iters < 0");
+  if (s->sp.M != p->c.M || s->sp.P != p->c.P) return fail(PDS_ERR_ARG, "SVGD state does not match the problem");
+  const int N = s->sp.N;
+  int rc = ensure_iter_buffers(p, N);
+  if (rc != PDS_OK) return rc;
+  rc = ensure_workspace(p, N);
+  if (rc != PDS_OK) return rc;
+  int total = 0;
+  for (int it = 0; it < iters; ++it) {
+    float* lp = (logp && it == iters - 1) ? logp : p->d_logp;
+    rc = pds_loglik_grad(p, particles, N, lp, p->d_grad, nullptr);
+    if (rc != PDS_OK) return rc;
+    total += g_launches;
+    rc = pds_svgd_step(s, particles, p->d_grad, nullptr, nullptr);
+    if (rc != PDS_OK) return rc;
+    total += g_launches;
+  }
+  g_launches = total;
+  return PDS_OK;
+}
+
+int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters, float* logp_host) {
+  if (!p || !s || !particles_host) return fail(PDS_ERR_ARG, "NULL argument");
+  const int N = s->sp.N;
+  int rc = ensure_iter_buffers(p, N);
+  if (rc != PDS_OK) return rc;
+  const size_t bytes = (size_t)p->c.P * N * sizeof(float);
+  cudaError_t e = cudaMemcpyAsync(p->d_x, particles_host, bytes, cudaMemcpyHostToDevice, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy particles to device");
+  rc = pds_iterate(p, s, p->d_x, iters, p->d_logp);
+  if (rc != PDS_OK) return rc;
+  const int launches = g_launches;
+  e = cudaMemcpyAsync(particles_host, p->d_x, bytes, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess && logp_host)
+    e = cudaMemcpyAsync(logp_host, p->d_logp, (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "copy results to host");
+  g_launches = launches;
+  return PDS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the CUDA translation units of libpds.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pds.h"
+
+namespace pds {
+
+constexpr int kMaxLinks = PDS_MAX_LINKS;
+constexpr int kMaxState = 2 * PDS_MAX_LINKS;
+constexpr int kMaxTheta = PDS_MAX_THETA;
+
+// Everything a rollout thread needs about the problem; passed by value as a
+// kernel parameter (constant bank, broadcast to all threads).
+struct ChainParams {
+  int n, M, T, W, D, S, P;
+  int K;            // adjoint checkpoint stride
+  int max_seg;      // checkpoint slots per unit = ceil(max window length / K)
+  float dt, g;
+  float inv_so2;    // 1 / sigma_obs^2
+  float obs_const;  // -(D/2) log(2 pi sigma_obs^2), once per observed step
+  float inv_sd2;    // 1 / sigma_def^2
+  float def_const;  // -(S/2) log(2 pi sigma_def^2), once per defect
+  float c_lim;
+  float lim_const;  // -sum_k log(hi_k - lo_k)
+  float mass[kMaxLinks], length[kMaxLinks], damping[kMaxLinks];
+  int mass_theta[kMaxLinks], length_theta[kMaxLinks], damp_theta[kMaxLinks];  // theta row or -1
+  int obs_col[kMaxState];  // observation column of each state component or -1
+  float s0[kMaxState];
+  float lo[kMaxTheta], hi[kMaxTheta];
+  const float* obs;        // device [T][D]
+};
+
+// Per-window partial results written by the rollout kernel, reduced over
+// windows by the window-reduction kernel.  All [row][N] slabs.
+struct Partials {
+  float* lp;      // [W][N] window log-likelihood (observation + defect terms)
+  float* th;      // [W][M][N] d/dtheta
+  float* start;   // [W][S][N] d/d(window start state)
+  float* next;    // [W][S][N] d/d(next shooting state) from the defect term
+  float* tape;    // checkpoints [max_seg][S][U] then segment states [K][S][U]
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
+                           cudaStream_t st);
+cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
+                                 float* grad, int32_t* status, cudaStream_t st);
+cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st);
+
+struct SvgdParams {
+  int N, M, P;
+  float lo[kMaxTheta], hi[kMaxTheta];
+  float lr, b1, b2, eps;
+  int clamp;
+};
+
+// Device-resident SVGD control block (no host round trip inside a step).
+struct SvgdCtl {
+  unsigned int hist[2048];   // radix-select histogram
+  unsigned int prefix;       // resolved high bits of the median's bit pattern
+  unsigned int rank;         // rank of the median within the current bucket
+  int step;                  // Adam step count
+  float bc1, bc2;            // Adam bias corrections 1 - beta^t
+  float bw;                  // bandwidth of the current step
+  float med;                 // median squared distance
+};
+
+struct SvgdWork {
+  float* u;        // [M][N] unit-box coordinates
+  float* gu;       // [M][N] gradient in unit-box coordinates
+  float* phi_part; // [chunks][M][N] partial phi sums
+  float* adam_m;   // [P][N]
+  float* adam_v;   // [P][N]
+  SvgdCtl* ctl;
+  int chunks;
+};
+
+cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
+                             float* phi_out, cudaStream_t st, int* launches);
+int svgd_phi_chunks(int N);
+
+}  // namespace pds

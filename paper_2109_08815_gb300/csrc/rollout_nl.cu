@@ -1,0 +1,14 @@
+// Explicit instantiation of the rollout kernels for one chain length.  The
+// build compiles this file once per link count (-DPDS_NL=1..8) so that the
+// instantiations compile in parallel.
+#include "rollout.cuh"
+
+#ifndef PDS_NL
+#error "compile with -DPDS_NL=<links>"
+#endif
+
+namespace pds {
+template cudaError_t launch_rollout_nl<PDS_NL>(const ChainParams&, const float*, int, const Partials&, int,
+                                               cudaStream_t);
+template cudaError_t launch_simulate_nl<PDS_NL>(const ChainParams&, const float*, int, float*, cudaStream_t);
+}  // namespace pds

@@ -1,0 +1,128 @@
+"""GPU parity of the SVGD step (pds_svgd_step: median-heuristic bandwidth,
+Eq. 1's phi, Adam update) against the FP64 oracle, through the C ABI.
+
+Tolerances: bandwidth rel 1e-5 (the median of FP32 distances is within
+rounding of the FP64 median); phi per particle max-norm rel 2e-3 of the
+largest |phi| (FP32 sums of N kernel-weighted terms); updated particles
+abs 1e-4 of the box width (one Adam step moves at most lr).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pds_oracle as orc
+from paper_2109_08815_gb300 import api
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(x).T, dtype=np.float32)).cuda()
+
+
+def _case(N, M, P, seed, spread=1.0):
+    rng = np.random.default_rng(seed)
+    lo = rng.uniform(-2, 0, M).astype(np.float32).astype(np.float64)
+    hi = (lo + rng.uniform(0.5, 3, M)).astype(np.float32).astype(np.float64)
+    x = np.zeros((N, P))
+    x[:, :M] = lo + (hi - lo) * np.clip(0.5 + spread * (rng.uniform(size=(N, M)) - 0.5), 0, 1)
+    x[:, M:] = rng.normal(size=(N, P - M))
+    g = rng.normal(size=(N, P)) * rng.uniform(0.1, 10, P)
+    return lo, hi, x.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64)
+
+
+def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2):
+    lo, hi, x, g = _case(N, M, P, seed, spread)
+    sv = api.Svgd(N, M, P, lo, hi, lr=lr)
+    X, G = _gpu(x), _gpu(g)
+    ost = orc.SvgdState(N, P, lo, hi, lr=lr)
+    xo = np.ascontiguousarray(x.copy())
+    for _ in range(steps):
+        bw, phi = sv.step(X, G, return_phi=True)
+        phi_ref, bw_ref = ost.step(xo, g)
+    torch.cuda.synchronize()
+    assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref, (bw.item(), bw_ref)
+    phi = phi.cpu().numpy().T
+    scale = np.max(np.abs(phi_ref))
+    assert np.max(np.abs(phi - phi_ref)) <= 2e-3 * scale, np.max(np.abs(phi - phi_ref)) / scale
+    xg = X.cpu().numpy().T
+    width = np.concatenate([hi - lo, np.ones(P - M)])
+    assert np.max(np.abs(xg - xo) / width) <= 1e-4 * steps, np.max(np.abs(xg - xo) / width)
+
+
+@pytest.mark.parametrize("N,M,P", [(2, 1, 1), (3, 2, 5), (100, 4, 76), (129, 10, 30), (1000, 7, 7), (257, 16, 40)])
+def test_svgd_step_matches_oracle(N, M, P):
+    _compare(N, M, P, seed=N + 10 * M)
+
+
+def test_svgd_five_steps_match_oracle():
+    _compare(300, 4, 12, seed=5, steps=5)
+
+
+def test_single_particle_phi_is_gradient():
+    lo, hi, x, g = _case(1, 3, 3, seed=1)
+    sv = api.Svgd(1, 3, 3, lo, hi)
+    bw, phi = sv.step(_gpu(x), _gpu(g), return_phi=True)
+    torch.cuda.synchronize()
+    assert bw.item() == 1.0
+    np.testing.assert_allclose(phi.cpu().numpy().T, g * (hi - lo), rtol=1e-6)
+
+
+def test_exact_median_on_integer_grid():
+    """Distances that FP32 represents exactly: the radix select must return
+    the same median as a brute-force sort, bit for bit."""
+    rng = np.random.default_rng(3)
+    N, M = 513, 3
+    lo, hi = np.zeros(M), np.full(M, 64.0)
+    pts = rng.integers(0, 64, size=(N, M)).astype(np.float64)
+    u = pts / 64.0  # exact in binary: (theta - 0) / 64
+    d = np.sort([np.sum((u[i] - u[j]) ** 2) for i in range(N) for j in range(i + 1, N)])
+    med = d[(len(d) - 1) // 2]
+    sv = api.Svgd(N, M, M, lo, hi)
+    bw, _ = sv.step(_gpu(pts), _gpu(np.zeros_like(pts)))
+    torch.cuda.synchronize()
+    # neighbouring distances on this grid differ by >= 2^-12 (relative 5e-4
+    # near the median), so 1e-6 agreement pins the exact order statistic
+    assert abs(bw.item() - med / np.log(N)) <= 1e-6 * med / np.log(N)
+
+
+def test_coincident_particles_give_unit_bandwidth():
+    N, M = 50, 2
+    lo, hi = np.zeros(M), np.ones(M)
+    x = np.full((N, M), 0.5)
+    sv = api.Svgd(N, M, M, lo, hi)
+    bw, phi = sv.step(_gpu(x), _gpu(np.ones_like(x)), return_phi=True)
+    torch.cuda.synchronize()
+    assert bw.item() == 1.0
+    np.testing.assert_allclose(phi.cpu().numpy(), 1.0, rtol=1e-6)
+
+
+@pytest.mark.slow
+def test_full_size_bandwidth_and_phi():
+    """N = 16384, M = 10 (the benchmark's particle set): bandwidth over all
+    1.3e8 pairs and phi of every particle against the oracle."""
+    N, M, P = 16384, 10, 10
+    lo, hi, x, g = _case(N, M, P, seed=11)
+    sv = api.Svgd(N, M, P, lo, hi)
+    bw, phi = sv.step(_gpu(x), _gpu(g), return_phi=True)
+    torch.cuda.synchronize()
+    u = (x[:, :M] - lo) / (hi - lo)
+    bw_ref = orc.bandwidth(N, orc.median_sqdist(u))
+    assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref
+    rng = np.random.default_rng(0)
+    idx = rng.choice(N, 64, replace=False)
+    gu = g[:, :M] * (hi - lo)
+    # phi rows for sampled particles: the oracle's phi over all j, evaluated row by row
+    full = orc.svgd_phi(u, gu, bw_ref)
+    phi = phi.cpu().numpy().T
+    scale = np.max(np.abs(full))
+    assert np.max(np.abs(phi[idx] - full[idx])) <= 2e-3 * scale
+
+
+def test_svgd_rejects_bad_sizes():
+    with pytest.raises(api.PdsError):
+        api.Svgd(0, 2, 2, [0, 0], [1, 1])
+    with pytest.raises(api.PdsError):
+        api.Svgd(10, 17, 17, np.zeros(17), np.ones(17))
+    with pytest.raises(api.PdsError):
+        api.Svgd(10, 2, 2, [0, 1], [1, 1])
