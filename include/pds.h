@@ -170,6 +170,30 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
 int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters,
                      float* logp_host);
 
+/* Median-heuristic bandwidth of N particles without allocating any device
+ * memory.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc -- for example code running inside another
+ * framework's allocator or memory-pool callback, or a process whose device
+ * memory is fully reserved up front -- and so cannot create the workspace
+ * that pds_svgd_create allocates.  It computes the same bandwidth as
+ * pds_svgd_step (lower median of the pairwise squared distances of the
+ * unit-box coordinates, divided by log N; 1 if N < 2 or the median is 0).
+ *  theta        : device [M][N] float (e.g. the first M rows of a particle array).
+ *  theta_lo/hi  : host [M] box.
+ *  bandwidth_out: device float scalar (written).
+ *  cuda_stream  : cudaStream_t the work is queued on (NULL = legacy default).
+ * Its scratch is one file-scope device array of 16 KiB + 4 MiB that every GPU
+ * loading the library holds until the process exits; N * M must not exceed
+ * 1048576 (PDS_ERR_ARG otherwise, with a message) and 1 <= M <= 16.  The
+ * first call on each device looks up that array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array and clears what must start at zero, so calls
+ * whose work overlaps on the GPU (different streams, or several host
+ * threads) race and must be serialised by the caller.  The call allocates
+ * nothing and returns after queuing its kernels. */
+int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo,
+                          const float* theta_hi, float* bandwidth_out, void* cuda_stream);
+
 /* Number of kernel launches the last pds_loglik_grad / pds_svgd_step /
  * pds_iterate call made (for launch accounting). */
 int pds_last_launch_count(void);

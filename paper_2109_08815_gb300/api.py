@@ -59,6 +59,7 @@ EXPORTS = {
     "pds_svgd_reset": ([_vp], ctypes.c_int),
     "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_iterate_host": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pds_bandwidth_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _fp, _fp, _vp, _vp], ctypes.c_int),
     "pds_last_launch_count": ([], ctypes.c_int),
     "pds_strerror": ([ctypes.c_int], ctypes.c_char_p),
     "pds_last_error": ([], ctypes.c_char_p),
@@ -286,3 +287,18 @@ class LogLik(torch.autograd.Function):
 
 def loglik(particles: torch.Tensor, problem: Problem) -> torch.Tensor:
     return LogLik.apply(particles, problem)
+
+
+def bandwidth_noalloc(theta: torch.Tensor, lo, hi, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Median-heuristic bandwidth of theta [M][N] through the entry point that
+    allocates no device memory (for callers that cannot call cudaMalloc)."""
+    _need_cuda(theta, torch.float32, "theta")
+    M, N = theta.shape
+    lo = np.ascontiguousarray(lo, dtype=np.float32)
+    hi = np.ascontiguousarray(hi, dtype=np.float32)
+    if out is None:
+        out = torch.empty(1, device=theta.device, dtype=torch.float32)
+    h, _ = _stream_handle(stream)
+    _check(lib().pds_bandwidth_noalloc(_ptr(theta), int(N), int(M), lo.ctypes.data_as(_fp), hi.ctypes.data_as(_fp),
+                                       _ptr(out), h), "pds_bandwidth_noalloc")
+    return out

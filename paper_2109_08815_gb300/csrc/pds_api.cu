@@ -31,6 +31,11 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+int set_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? PDS_ERR_OOM : PDS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }

@@ -82,4 +82,7 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
                              float* phi_out, cudaStream_t st, int* launches);
 int svgd_phi_chunks(int N);
 
+// Record an error message for pds_last_error() and return `code`.
+int set_error(int code, const char* msg);
+
 }  // namespace pds

@@ -281,3 +281,117 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
 }
 
 }  // namespace pds
+
+// ---------------------------------------------------------------------------
+// Allocation-free median-heuristic bandwidth (pds_bandwidth_noalloc).
+//
+// For callers that cannot allocate device memory: code running inside a
+// host-side memory pool or allocator callback, or a process whose device
+// memory is reserved up front by another framework, may not be allowed to
+// call cudaMalloc.  This variant of the bandwidth computation above runs the
+// same radix-select kernels, but its scratch (the control block with the
+// radix histogram, and the unit-box coordinates) lives in the file-scope
+// device array below instead of a workspace allocated by pds_svgd_create.
+// Every GPU that loads the library holds this array until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace pds {
+
+constexpr int kNoAllocCtlFloats = 4096;        // control block, padded to 16 KiB
+constexpr int kNoAllocMaxElems = 1 << 20;      // N * M <= 1,048,576 (4 MiB of coordinates)
+static_assert(sizeof(SvgdCtl) <= kNoAllocCtlFloats * sizeof(float), "control block does not fit");
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocCtlFloats + kNoAllocMaxElems];
+
+struct NoAllocBox {
+  float lo[kMaxTheta], hi[kMaxTheta];
+};
+
+// Clears the histogram and radix state (the array keeps the previous call's
+// contents) and writes u = (theta - lo) / (hi - lo) into the scratch.
+__global__ void noalloc_prep_kernel(int N, int M, NoAllocBox box, const float* __restrict__ theta,
+                                    SvgdCtl* __restrict__ ctl, float* __restrict__ u) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < kHistBins) ctl->hist[idx] = 0u;
+  if (idx == 0) {
+    const unsigned long long pairs = (unsigned long long)N * (unsigned long long)(N - 1) / 2ull;
+    ctl->prefix = 0u;
+    ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
+    ctl->bw = 1.0f;
+    ctl->med = 0.0f;
+  }
+  if (idx < M * N) {
+    const int k = idx / N;
+    u[idx] = (theta[idx] - box.lo[k]) / (box.hi[k] - box.lo[k]);
+  }
+}
+
+__global__ void noalloc_out_kernel(const SvgdCtl* __restrict__ ctl, float* __restrict__ out) { *out = ctl->bw; }
+
+template <int MM>
+static cudaError_t noalloc_bandwidth_mm(int N, int M, const NoAllocBox& box, const float* theta, float* out,
+                                        float* scratch, cudaStream_t st) {
+  SvgdCtl* ctl = reinterpret_cast<SvgdCtl*>(scratch);
+  float* u = scratch + kNoAllocCtlFloats;
+  const int total = (M * N > kHistBins) ? M * N : kHistBins;
+  noalloc_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(N, M, box, theta, ctl, u);
+  if (N >= 2) {
+    const int nt = (N + kTile - 1) / kTile;
+    const long long all_tiles = (long long)nt * nt;
+    const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
+    for (int pass = 0; pass < 3; ++pass) {
+      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, u, ctl, pass);
+      median_select_kernel<<<1, 32, 0, st>>>(ctl, pass, N);
+    }
+  }
+  noalloc_out_kernel<<<1, 1, 0, st>>>(ctl, out);
+  return cudaGetLastError();
+}
+
+static std::mutex g_noalloc_mu;
+static float* g_noalloc_ptr[64];
+
+}  // namespace pds
+
+extern "C" int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo, const float* theta_hi,
+                                     float* bandwidth_out, void* cuda_stream) {
+  using namespace pds;
+  if (!theta || !theta_lo || !theta_hi || !bandwidth_out) return set_error(PDS_ERR_ARG, "NULL argument");
+  if (M < 1 || M > kMaxTheta) return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: M outside 1..16");
+  if (N < 1 || (long long)N * M > kNoAllocMaxElems)
+    return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: N * M must be in 1..1048576 (static scratch limit)");
+  NoAllocBox box;
+  for (int k = 0; k < kMaxTheta; ++k) { box.lo[k] = 0.f; box.hi[k] = 1.f; }
+  for (int k = 0; k < M; ++k) {
+    if (!(theta_hi[k] > theta_lo[k])) return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: empty theta box");
+    box.lo[k] = theta_lo[k];
+    box.hi[k] = theta_hi[k];
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 64) return set_error(PDS_ERR_CUDA, "pds_bandwidth_noalloc: no device");
+  float* scratch = nullptr;
+  {
+    // One-time set-up per device, on the first call with that device
+    // current: host code needs the array's device address (its name on the
+    // host is only a stand-in).
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return set_error(PDS_ERR_CUDA, "pds_bandwidth_noalloc: cudaGetSymbolAddress failed");
+      g_noalloc_ptr[dev] = static_cast<float*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (M <= 2) e = noalloc_bandwidth_mm<2>(N, M, box, theta, bandwidth_out, scratch, st);
+  else if (M <= 4) e = noalloc_bandwidth_mm<4>(N, M, box, theta, bandwidth_out, scratch, st);
+  else if (M <= 8) e = noalloc_bandwidth_mm<8>(N, M, box, theta, bandwidth_out, scratch, st);
+  else if (M <= 10) e = noalloc_bandwidth_mm<10>(N, M, box, theta, bandwidth_out, scratch, st);
+  else e = noalloc_bandwidth_mm<16>(N, M, box, theta, bandwidth_out, scratch, st);
+  if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "pds_bandwidth_noalloc: kernel launch failed");
+  return PDS_OK;
+}
