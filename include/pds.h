@@ -107,6 +107,16 @@ int pds_problem_layout(pds_problem_t p, int* M, int* S, int* P);
  * the same for every K up to rounding).  1 <= K <= PDS_MAX_WINDOW_STEPS. */
 int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
 
+/* Tuning options of a problem (pds_problem_set_option / _get_option):
+ *  PDS_OPT_CHECKPOINT_STRIDE: K as in pds_problem_set_checkpoint_stride.
+ *  PDS_OPT_FAST_MATH: 0 (default) = CUDA's sinf/cosf and IEEE division in the
+ *    rollout; 1 = the hardware approximations __sincosf / __fdividef (results
+ *    stay within the tolerances the parity tests state). */
+#define PDS_OPT_CHECKPOINT_STRIDE 1
+#define PDS_OPT_FAST_MATH 2
+int pds_problem_set_option(pds_problem_t p, int option, int value);
+int pds_problem_get_option(pds_problem_t p, int option, int* value);
+
 /* Allocate the workspace for up to N_max particles now, so that later calls
  * with N <= N_max allocate nothing (e.g. before capturing a CUDA graph).
  * Calls with a larger N grow the workspace (synchronising the stream). */
@@ -145,6 +155,15 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
                     double lr, double beta1, double beta2, double eps, int clamp,
                     void* cuda_stream, pds_svgd_t* out);
 int pds_svgd_destroy(pds_svgd_t s);
+
+/* SVGD options: PDS_OPT_FAST_MATH 0 (default) = expf for the kernel values,
+ * 1 = the hardware approximation __expf.  PDS_OPT_MEDIAN_FULL_PASSES 0
+ * (default) = for N >= 2048 bracket the median from a sample of pairs and
+ * select among the pairs inside the bracket (falling back to the full passes
+ * if the bracket misses); 1 = always three radix passes over all pairs.
+ * Both give the same exact median. */
+#define PDS_OPT_MEDIAN_FULL_PASSES 3
+int pds_svgd_set_option(pds_svgd_t s, int option, int value);
 
 /* One SVGD + Adam update in place.
  *  particles    : device [P][N] float (read and written).

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libpds.so")
 
 PDS_SYSTEM_PLANAR_CHAIN = 1
 PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
+OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES = 1, 2, 3
 
 _lib = None
 _lock = threading.Lock()
@@ -50,6 +51,8 @@ EXPORTS = {
     "pds_problem_layout": ([_vp, _ip, _ip, _ip], ctypes.c_int),
     "pds_problem_set_checkpoint_stride": ([_vp, ctypes.c_int], ctypes.c_int),
     "pds_problem_reserve": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pds_problem_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "pds_problem_get_option": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
     "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_svgd_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, ctypes.c_double,
@@ -57,6 +60,7 @@ EXPORTS = {
     "pds_svgd_destroy": ([_vp], ctypes.c_int),
     "pds_svgd_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pds_svgd_reset": ([_vp], ctypes.c_int),
+    "pds_svgd_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_iterate_host": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_bandwidth_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _fp, _fp, _vp, _vp], ctypes.c_int),
@@ -122,7 +126,7 @@ class Problem:
     """
 
     def __init__(self, *, mass, length, damping, theta_kind, theta_link, dt, T, W, obs, obs_index, sigma_obs,
-                 sigma_def, s0, lo, hi, g=9.81, c_lim=1e4, stream=None, checkpoint_stride=None):
+                 sigma_def, s0, lo, hi, g=9.81, c_lim=1e4, stream=None, checkpoint_stride=None, fast_math=None):
         L = lib()
         self._keep = []
 
@@ -159,6 +163,8 @@ class Problem:
         self.M, self.S, self.P = M.value, S.value, P.value
         if checkpoint_stride is not None:
             self.set_checkpoint_stride(checkpoint_stride)
+        if fast_math is not None:
+            self.set_option(OPT_FAST_MATH, int(bool(fast_math)))
 
     @classmethod
     def from_workload(cls, wl, obs, **kw):
@@ -188,6 +194,14 @@ class Problem:
     def reserve(self, N: int):
         _check(lib().pds_problem_reserve(self._h, int(N)), "pds_problem_reserve")
 
+    def set_option(self, option: int, value: int):
+        _check(lib().pds_problem_set_option(self._h, int(option), int(value)), "pds_problem_set_option")
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int()
+        _check(lib().pds_problem_get_option(self._h, int(option), ctypes.byref(v)), "pds_problem_get_option")
+        return v.value
+
     def loglik_grad(self, particles: torch.Tensor, grad: bool = True, out=None):
         """log p and (optionally) d log p / d particles for particles [P][N]."""
         _need_cuda(particles, torch.float32, "particles")
@@ -215,7 +229,8 @@ class Problem:
 class Svgd:
     """SVGD + Adam state (pds_svgd_create)."""
 
-    def __init__(self, N, M, P, lo, hi, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, clamp=True, stream=None):
+    def __init__(self, N, M, P, lo, hi, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, clamp=True, stream=None,
+                 fast_math=False):
         L = lib()
         lo = np.ascontiguousarray(lo, dtype=np.float32)
         hi = np.ascontiguousarray(hi, dtype=np.float32)
@@ -226,6 +241,8 @@ class Svgd:
                                  ctypes.byref(h)), "pds_svgd_create")
         self._h = h
         self.N, self.M, self.P = int(N), int(M), int(P)
+        if fast_math:
+            _check(L.pds_svgd_set_option(h, OPT_FAST_MATH, 1), "pds_svgd_set_option")
 
     @property
     def handle(self):
@@ -244,6 +261,9 @@ class Svgd:
 
     def reset(self):
         _check(lib().pds_svgd_reset(self._h), "pds_svgd_reset")
+
+    def set_option(self, option: int, value: int):
+        _check(lib().pds_svgd_set_option(self._h, int(option), int(value)), "pds_svgd_set_option")
 
     def step(self, particles: torch.Tensor, grad: torch.Tensor, return_phi: bool = False):
         """In-place update of particles [P][N]; returns (bandwidth tensor, phi or None)."""

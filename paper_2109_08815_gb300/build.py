@@ -46,16 +46,22 @@ def _sources_mtime() -> float:
     return t
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
-        return LIB
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None, defines=(),
+          lib_path: str | None = None, build_dir: str | None = None) -> str:
+    """Compile and link the library; ``defines`` (e.g. ["PDS_ROLLOUT_MINB=2"])
+    and ``lib_path``/``build_dir`` build a variant without touching the
+    default library."""
+    lib_out = lib_path or LIB
+    bdir = build_dir or BUILD
+    if not force and os.path.exists(lib_out) and os.path.getmtime(lib_out) >= _sources_mtime():
+        return lib_out
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
-    extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    os.makedirs(bdir, exist_ok=True)
+    extra = (["-Xptxas", "-v"] if verbose_ptxas else []) + [f"-D{d}" for d in defines]
 
     def compile_unit(u):
         name, src, defs = u
-        obj = os.path.join(BUILD, name + ".o")
+        obj = os.path.join(bdir, name + ".o")
         cmd = [nvcc, *NVFLAGS, *extra, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -68,13 +74,13 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
     if verbose_ptxas:
         for (obj, log) in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_out + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_out)
+    return lib_out
 
 
 if __name__ == "__main__":

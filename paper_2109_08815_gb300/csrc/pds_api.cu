@@ -13,7 +13,7 @@
 
 namespace pds {
 template <int NL>
-cudaError_t launch_rollout_nl(const ChainParams&, const float*, int, const Partials&, int, cudaStream_t);
+cudaError_t launch_rollout_nl(const ChainParams&, const float*, int, const Partials&, int, int32_t*, cudaStream_t);
 template <int NL>
 cudaError_t launch_simulate_nl(const ChainParams&, const float*, int, float*, cudaStream_t);
 
@@ -41,16 +41,16 @@ static int cuda_fail(cudaError_t e, const char* what) {
 }
 
 cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                           cudaStream_t st) {
+                           int32_t* status, cudaStream_t st) {
   switch (c.n) {
-    case 1: return launch_rollout_nl<1>(c, X, N, parts, grad, st);
-    case 2: return launch_rollout_nl<2>(c, X, N, parts, grad, st);
-    case 3: return launch_rollout_nl<3>(c, X, N, parts, grad, st);
-    case 4: return launch_rollout_nl<4>(c, X, N, parts, grad, st);
-    case 5: return launch_rollout_nl<5>(c, X, N, parts, grad, st);
-    case 6: return launch_rollout_nl<6>(c, X, N, parts, grad, st);
-    case 7: return launch_rollout_nl<7>(c, X, N, parts, grad, st);
-    case 8: return launch_rollout_nl<8>(c, X, N, parts, grad, st);
+    case 1: return launch_rollout_nl<1>(c, X, N, parts, grad, status, st);
+    case 2: return launch_rollout_nl<2>(c, X, N, parts, grad, status, st);
+    case 3: return launch_rollout_nl<3>(c, X, N, parts, grad, status, st);
+    case 4: return launch_rollout_nl<4>(c, X, N, parts, grad, status, st);
+    case 5: return launch_rollout_nl<5>(c, X, N, parts, grad, status, st);
+    case 6: return launch_rollout_nl<6>(c, X, N, parts, grad, status, st);
+    case 7: return launch_rollout_nl<7>(c, X, N, parts, grad, status, st);
+    case 8: return launch_rollout_nl<8>(c, X, N, parts, grad, status, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -91,6 +91,7 @@ struct pds_svgd {
   SvgdParams sp;
   SvgdWork w{};
   cudaStream_t stream;
+  int full_passes = 0;
 };
 
 static void free_parts(Partials& p) {
@@ -262,6 +263,27 @@ int pds_problem_set_checkpoint_stride(pds_problem_t p, int K) {
   return PDS_OK;
 }
 
+int pds_problem_set_option(pds_problem_t p, int option, int value) {
+  if (!p) return fail(PDS_ERR_ARG, "NULL problem");
+  switch (option) {
+    case PDS_OPT_CHECKPOINT_STRIDE: return pds_problem_set_checkpoint_stride(p, value);
+    case PDS_OPT_FAST_MATH:
+      if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "fast math must be 0 or 1");
+      p->c.fast_math = value;
+      return PDS_OK;
+    default: return fail(PDS_ERR_ARG, "unknown option %d", option);
+  }
+}
+
+int pds_problem_get_option(pds_problem_t p, int option, int* value) {
+  if (!p || !value) return fail(PDS_ERR_ARG, "NULL argument");
+  switch (option) {
+    case PDS_OPT_CHECKPOINT_STRIDE: *value = p->c.K; return PDS_OK;
+    case PDS_OPT_FAST_MATH: *value = p->c.fast_math; return PDS_OK;
+    default: return fail(PDS_ERR_ARG, "unknown option %d", option);
+  }
+}
+
 int pds_problem_reserve(pds_problem_t p, int N_max) {
   if (!p) return fail(PDS_ERR_ARG, "NULL problem");
   if (N_max < 1 || N_max > (1 << 20)) return fail(PDS_ERR_ARG, "N_max %d outside 1..2^20", N_max);
@@ -274,7 +296,7 @@ int pds_loglik_grad(pds_problem_t p, const float* particles, int N, float* logp,
   if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
   int rc = ensure_workspace(p, N);
   if (rc != PDS_OK) return rc;
-  cudaError_t e = launch_rollout(p->c, particles, N, p->parts, grad != nullptr, p->stream);
+  cudaError_t e = launch_rollout(p->c, particles, N, p->parts, grad != nullptr, status, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
   e = launch_window_reduce(p->c, particles, N, p->parts, logp, grad, status, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "window reduce launch");
@@ -313,9 +335,12 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   s->sp.clamp = clamp ? 1 : 0;
   s->stream = (cudaStream_t)cuda_stream;
   s->w.chunks = svgd_phi_chunks(N);
+  s->w.cand_cap = svgd_cand_capacity(N);
   const size_t MN = (size_t)M * N, PN = (size_t)P * N;
-  cudaError_t e;
-  if ((e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
+  cudaError_t e = cudaSuccess;
+  if ((s->w.cand_cap && (e = cudaMalloc(&s->w.cand, s->w.cand_cap * sizeof(float))) != cudaSuccess) ||
+      (s->w.cand_cap && (e = cudaMalloc(&s->w.samp, svgd_sample_size() * sizeof(float))) != cudaSuccess) ||
+      (e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.gu, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.phi_part, (size_t)s->w.chunks * MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.adam_m, PN * sizeof(float))) != cudaSuccess ||
@@ -326,6 +351,16 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   }
   *out = s;
   return pds_svgd_reset(s);
+}
+
+int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
+  if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
+  if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "option value must be 0 or 1");
+  switch (option) {
+    case PDS_OPT_FAST_MATH: s->sp.fast_math = value; return PDS_OK;
+    case PDS_OPT_MEDIAN_FULL_PASSES: s->full_passes = value; return PDS_OK;
+    default: return fail(PDS_ERR_ARG, "unknown option %d", option);
+  }
 }
 
 int pds_svgd_reset(pds_svgd_t s) {
@@ -342,6 +377,8 @@ int pds_svgd_reset(pds_svgd_t s) {
 int pds_svgd_destroy(pds_svgd_t s) {
   if (!s) return PDS_OK;
   cudaStreamSynchronize(s->stream);
+  cudaFree(s->w.cand);
+  cudaFree(s->w.samp);
   cudaFree(s->w.u);
   cudaFree(s->w.gu);
   cudaFree(s->w.phi_part);
@@ -356,7 +393,9 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   g_launches = 0;
   if (!s || !particles || !grad) return fail(PDS_ERR_ARG, "NULL argument");
   int n = 0;
-  cudaError_t e = launch_svgd_step(s->sp, s->w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
+  SvgdWork w = s->w;
+  if (s->full_passes) w.cand_cap = 0;
+  cudaError_t e = launch_svgd_step(s->sp, w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
   g_launches = n;
   if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
   return PDS_OK;

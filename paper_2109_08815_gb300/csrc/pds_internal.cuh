@@ -17,6 +17,7 @@ constexpr int kMaxTheta = PDS_MAX_THETA;
 struct ChainParams {
   int n, M, T, W, D, S, P;
   int K;            // adjoint checkpoint stride
+  int fast_math;    // 1: hardware sin/cos and reciprocal approximations
   int max_seg;      // checkpoint slots per unit = ceil(max window length / K)
   float dt, g;
   float inv_so2;    // 1 / sigma_obs^2
@@ -45,7 +46,7 @@ struct Partials {
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                           cudaStream_t st);
+                           int32_t* status, cudaStream_t st);
 cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
                                  float* grad, int32_t* status, cudaStream_t st);
 cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st);
@@ -55,6 +56,7 @@ struct SvgdParams {
   float lo[kMaxTheta], hi[kMaxTheta];
   float lr, b1, b2, eps;
   int clamp;
+  int fast_math;   // 1: __expf for the kernel values
 };
 
 // Device-resident SVGD control block (no host round trip inside a step).
@@ -66,9 +68,17 @@ struct SvgdCtl {
   float bc1, bc2;            // Adam bias corrections 1 - beta^t
   float bw;                  // bandwidth of the current step
   float med;                 // median squared distance
+  // sampled bracket [lo, hi] around the median (large N)
+  float lo, hi;
+  unsigned long long below;  // pairs with d < lo
+  unsigned long long inside; // pairs with lo <= d <= hi (= candidates)
+  int mode;                  // 0: select among candidates; 1: full radix passes over all pairs
 };
 
 struct SvgdWork {
+  float* samp;     // sampled pair distances (bracket estimate)
+  float* cand;     // candidate distances inside the sampled bracket
+  unsigned long long cand_cap;
   float* u;        // [M][N] unit-box coordinates
   float* gu;       // [M][N] gradient in unit-box coordinates
   float* phi_part; // [chunks][M][N] partial phi sums
@@ -81,6 +91,8 @@ struct SvgdWork {
 cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
                              float* phi_out, cudaStream_t st, int* launches);
 int svgd_phi_chunks(int N);
+unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
+int svgd_sample_size();
 
 // Record an error message for pds_last_error() and return `code`.
 int set_error(int code, const char* msg);

@@ -29,14 +29,26 @@
 
 #include "pds_internal.cuh"
 
+#ifndef PDS_ROLLOUT_MINB
+#define PDS_ROLLOUT_MINB 3
+#endif
+
 namespace pds {
 
-struct LinkParams {
-  float m, l, b;
-};
+// sin/cos and reciprocal: CUDA's accurate functions, or (FAST) the hardware
+// approximations __sincosf / __fdividef, which the parity tests also cover.
+template <bool FAST>
+__device__ __forceinline__ void sc(float x, float* s, float* c) {
+  if (FAST) __sincosf(x, s, c);
+  else sincosf(x, s, c);
+}
+template <bool FAST>
+__device__ __forceinline__ float rcp(float x) {
+  return FAST ? __fdividef(1.0f, x) : 1.0f / x;
+}
 
 // Forward step in place.
-template <int NL>
+template <int NL, bool FAST>
 __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const float (&m)[NL],
                                            const float (&l)[NL], const float (&b)[NL], float g, float dt) {
   float sn[NL], cs[NL], w2[NL], tau[NL];
@@ -46,7 +58,7 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
     for (int i = 0; i < NL; ++i) {
       phi += q[i];
       om += v[i];
-      sincosf(phi, &sn[i], &cs[i]);
+      sc<FAST>(phi, &sn[i], &cs[i]);
       w2[i] = om * om;
       tau[i] = -b[i] * v[i];
     }
@@ -62,7 +74,7 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
     const float D = px * yx + py * yy;
     const float zx = Axx * rx + Axy * ry, zy = Axy * rx + Ayy * ry;
     const float bx = Bx - w2[i] * zx, by = By + m[i] * g - w2[i] * zy;
-    const float id = 1.0f / D;
+    const float id = rcp<FAST>(D);
     const float t = (tau[i] - tnext - (px * bx + py * by)) * id;
     Bx = bx + t * yx;
     By = by + t * yy;
@@ -90,7 +102,7 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
 // Reverse of one step.  On entry (qb, vb) is the adjoint of the step's
 // output state; on exit it is the adjoint of the input state (q, v).  The
 // adjoints of the link parameters are accumulated into mb, lb, bb.
-template <int NL>
+template <int NL, bool FAST>
 __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const float (&m)[NL],
                                                const float (&l)[NL], const float (&b)[NL], float g, float dt,
                                                float (&qb)[NL], float (&vb)[NL], float (&mb)[NL], float (&lb)[NL],
@@ -103,7 +115,7 @@ __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float
     for (int i = 0; i < NL; ++i) {
       phi += q[i];
       o += v[i];
-      sincosf(phi, &sn[i], &cs[i]);
+      sc<FAST>(phi, &sn[i], &cs[i]);
       om[i] = o;
       tau[i] = -b[i] * v[i];
     }
@@ -122,7 +134,7 @@ __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float
       const float w2 = om[i] * om[i];
       bx[i] = Bx - w2 * zx;
       by[i] = By + m[i] * g - w2 * zy;
-      iD[i] = 1.0f / D;
+      iD[i] = rcp<FAST>(D);
       tt[i] = (tau[i] - tnext - (px * bx[i] + py * by[i])) * iD[i];
       Bx = bx[i] + tt[i] * yx;
       By = by[i] + tt[i] * yy;
@@ -320,14 +332,16 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
 // One thread per unit u = w * N + i (window w, particle i): the window's
 // forward rollout with its observation and defect terms (Eqs. 2, 4, 5), then
 // (grad != 0) the reverse sweep from checkpoints every K steps.
-template <int NL>
-__global__ void __launch_bounds__(128) rollout_kernel(const ChainParams c, const float* __restrict__ X, int N,
-                                                      Partials parts, int grad) {
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const ChainParams c, const float* __restrict__ X, int N,
+                                                      Partials parts, int grad, int32_t* __restrict__ status) {
   const size_t U = (size_t)N * c.W;
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   const int w = (int)(u / N);
   const int i = (int)(u - (size_t)w * N);
+  // the window-reduction kernel (next on the stream) ORs in non-finite flags
+  if (status && w == 0) status[i] = 0;
 
   float m[NL], l[NL], b[NL];
   load_params<NL>(c, X, N, i, m, l, b);
@@ -354,7 +368,7 @@ __global__ void __launch_bounds__(128) rollout_kernel(const ChainParams c, const
   float rss = 0.f;
   for (int k = 0; k < h; ++k) {
     if (grad && (k % K) == 0) tape_store<NL>(ckpt, k / K, U, u, q, v);
-    chain_step<NL>(q, v, m, l, b, c.g, c.dt);
+    chain_step<NL, FAST>(q, v, m, l, b, c.g, c.dt);
     rss += obs_residual<NL>(c, t0 + k + 1, q, v, qb, vb, false);
   }
   float lp = -0.5f * c.inv_so2 * rss + (float)h * c.obs_const;
@@ -400,13 +414,13 @@ __global__ void __launch_bounds__(128) rollout_kernel(const ChainParams c, const
     // recompute s_a .. s_{e-1} into the segment buffer
     for (int k = a; k < e; ++k) {
       tape_store<NL>(segbuf, k - a, U, u, qs, vs);
-      if (k + 1 < e) chain_step<NL>(qs, vs, m, l, b, c.g, c.dt);
+      if (k + 1 < e) chain_step<NL, FAST>(qs, vs, m, l, b, c.g, c.dt);
     }
     for (int k = e - 1; k >= a; --k) {
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL>(c, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, U, u, qs, vs);
-      chain_step_vjp<NL>(qs, vs, m, l, b, c.g, c.dt, qb, vb, mb, lb, bb);
+      chain_step_vjp<NL, FAST>(qs, vs, m, l, b, c.g, c.dt, qb, vb, mb, lb, bb);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -444,7 +458,7 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
   for (int j = 0; j < NL; ++j) { q[j] = c.s0[j]; v[j] = c.s0[NL + j]; }
   const size_t SN = (size_t)2 * NL * N;
   for (int t = 0; t <= c.T; ++t) {
-    if (t > 0) chain_step<NL>(q, v, m, l, b, c.g, c.dt);
+    if (t > 0) chain_step<NL, false>(q, v, m, l, b, c.g, c.dt);
     float* out = states + (size_t)t * SN + i;
 #pragma unroll
     for (int j = 0; j < NL; ++j) { out[(size_t)j * N] = q[j]; out[(size_t)(NL + j) * N] = v[j]; }
@@ -453,10 +467,13 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
 
 template <int NL>
 cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                              cudaStream_t st) {
+                              int32_t* status, cudaStream_t st) {
   const size_t U = (size_t)N * c.W;
   const unsigned blocks = (unsigned)((U + 127) / 128);
-  rollout_kernel<NL><<<blocks, 128, 0, st>>>(c, X, N, parts, grad);
+  if (c.fast_math)
+    rollout_kernel<NL, true><<<blocks, 128, 0, st>>>(c, X, N, parts, grad, status);
+  else
+    rollout_kernel<NL, false><<<blocks, 128, 0, st>>>(c, X, N, parts, grad, status);
   return cudaGetLastError();
 }
 

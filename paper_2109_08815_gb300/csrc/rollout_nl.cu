@@ -8,7 +8,7 @@
 #endif
 
 namespace pds {
-template cudaError_t launch_rollout_nl<PDS_NL>(const ChainParams&, const float*, int, const Partials&, int,
+template cudaError_t launch_rollout_nl<PDS_NL>(const ChainParams&, const float*, int, const Partials&, int, int32_t*,
                                                cudaStream_t);
 template cudaError_t launch_simulate_nl<PDS_NL>(const ChainParams&, const float*, int, float*, cudaStream_t);
 }  // namespace pds

@@ -19,7 +19,8 @@ constexpr int kTile = 128;        // particles per tile (threads per block)
 constexpr int kHistBins = 2048;   // 11-bit radix digits
 
 __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const float* __restrict__ X,
-                                 const float* __restrict__ G, float* __restrict__ u, float* __restrict__ gu) {
+                                 const float* __restrict__ G, float* __restrict__ u, float* __restrict__ gu,
+                                 int mode) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < kHistBins) ctl->hist[idx] = 0u;
   if (idx == 0) {
@@ -32,6 +33,9 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
     ctl->bw = 1.0f;
     ctl->med = 0.0f;
+    ctl->below = 0ull;
+    ctl->inside = 0ull;
+    ctl->mode = mode;
   }
   const int total = sp.M * sp.N;
   if (idx < total) {
@@ -43,54 +47,122 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
 }
 
 template <int MM>
+struct Pad4 {
+  static constexpr int Q = (MM + 3) / 4;  // float4 groups per particle
+};
+
+template <int MM>
 __device__ __forceinline__ void load_row(const float* __restrict__ u, int M, int N, int i, float (&r)[MM]) {
 #pragma unroll
   for (int k = 0; k < MM; ++k) r[k] = (k < M && i < N) ? u[(size_t)k * N + i] : 0.f;
 }
 
+// Unpack a shared-memory row of float4 into MM scalars (the padding lanes of
+// the last float4 are loaded but never used).
+template <int MM>
+__device__ __forceinline__ void unpack_row(const float4* __restrict__ src, float (&v)[MM]) {
+#pragma unroll
+  for (int q = 0; q < Pad4<MM>::Q; ++q) {
+    const float4 t = src[q];
+    if (4 * q + 0 < MM) v[4 * q + 0] = t.x;
+    if (4 * q + 1 < MM) v[4 * q + 1] = t.y;
+    if (4 * q + 2 < MM) v[4 * q + 2] = t.z;
+    if (4 * q + 3 < MM) v[4 * q + 3] = t.w;
+  }
+}
+
+// Stage particle j's coordinates (zero padded to a multiple of 4) into a
+// shared-memory row of float4 so the inner loops read them with 128-bit
+// broadcast loads.
+template <int MM>
+__device__ __forceinline__ void stage_row(const float* __restrict__ u, int M, int N, int j, bool ok,
+                                          float4* __restrict__ dst) {
+  constexpr int Q = Pad4<MM>::Q;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    float v[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int k = 4 * q + r;
+      v[r] = (ok && k < M) ? u[(size_t)k * N + j] : 0.f;
+    }
+    dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+  }
+}
+
+template <int MM>
+__device__ __forceinline__ float sqdist(const float (&a)[MM], const float4* __restrict__ b) {
+  float v[MM];
+  unpack_row<MM>(b, v);
+  float d = 0.f;
+#pragma unroll
+  for (int k = 0; k < MM; ++k) {
+    const float e = a[k] - v[k];
+    d = fmaf(e, e, d);
+  }
+  return d;
+}
+
+constexpr int kRows = 2;                 // rows (particles i) per thread
+constexpr int kSpan = kTile * kRows;     // particles per square tile
+
+__device__ __forceinline__ void hist_add(unsigned int* hist, float d, int pass, unsigned int prefix) {
+  const unsigned int bits = __float_as_uint(d);
+  if (pass == 0) {
+    atomicAdd(&hist[bits >> 21], 1u);
+  } else if (pass == 1) {
+    if ((bits >> 21) == prefix) atomicAdd(&hist[(bits >> 10) & 2047u], 1u);
+  } else {
+    if ((bits >> 10) == prefix) atomicAdd(&hist[bits & 1023u], 1u);
+  }
+}
+
 // One radix-select pass over all pairs i < j.  pass 0 histograms bits
 // [31:21]; pass 1 bits [20:10] of the pairs whose bits [31:21] equal the
 // resolved prefix; pass 2 bits [9:0] of those whose bits [31:10] match.
+// Square tiles of kSpan x kSpan particles; a thread owns kRows rows.
 template <int MM>
 __global__ void __launch_bounds__(kTile) median_hist_kernel(int N, int M, const float* __restrict__ u,
-                                                            SvgdCtl* __restrict__ ctl, int pass) {
+                                                            SvgdCtl* __restrict__ ctl, int pass,
+                                                            int only_in_fallback) {
+  constexpr int Q = Pad4<MM>::Q;
   __shared__ unsigned int hist[kHistBins];
-  __shared__ float uj[MM][kTile];
+  __shared__ float4 uj[kSpan][Q];
+  if (only_in_fallback && ctl->mode != 1) return;  // the sampled bracket held the median
   for (int b = threadIdx.x; b < kHistBins; b += kTile) hist[b] = 0u;
   const unsigned int prefix = ctl->prefix;
-  const int nt = (N + kTile - 1) / kTile;
+  const int nt = (N + kSpan - 1) / kSpan;
   const long long ntiles = (long long)nt * nt;
   __syncthreads();
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int I = (int)(tile / nt), J = (int)(tile - (long long)I * nt);
     if (I > J) continue;  // uniform across the block
-    const int i = I * kTile + threadIdx.x;
-    float ui[MM];
-    load_row<MM>(u, M, N, i, ui);
-    {
-      const int j = J * kTile + threadIdx.x;
+    const int i0 = I * kSpan + threadIdx.x, i1 = i0 + kTile;
+    float a0[MM], a1[MM];
+    load_row<MM>(u, M, N, i0, a0);
+    load_row<MM>(u, M, N, i1, a1);
 #pragma unroll
-      for (int k = 0; k < MM; ++k) uj[k][threadIdx.x] = (k < M && j < N) ? u[(size_t)k * N + j] : 0.f;
+    for (int r = 0; r < kRows; ++r) {
+      const int jl = threadIdx.x + r * kTile;
+      const int j = J * kSpan + jl;
+      stage_row<MM>(u, M, N, j, j < N, uj[jl]);
     }
     __syncthreads();
-    if (i < N) {
-      const int jn = min(kTile, N - J * kTile);
-      const int jstart = (I == J) ? (threadIdx.x + 1) : 0;
-      for (int jj = jstart; jj < jn; ++jj) {
-        float d = 0.f;
-#pragma unroll
-        for (int k = 0; k < MM; ++k) {
-          const float e = ui[k] - uj[k][jj];
-          d = fmaf(e, e, d);
-        }
-        const unsigned int bits = __float_as_uint(d);
-        if (pass == 0) {
-          atomicAdd(&hist[bits >> 21], 1u);
-        } else if (pass == 1) {
-          if ((bits >> 21) == prefix) atomicAdd(&hist[(bits >> 10) & 2047u], 1u);
-        } else {
-          if ((bits >> 10) == prefix) atomicAdd(&hist[bits & 1023u], 1u);
-        }
+    const int jn = min(kSpan, N - J * kSpan);
+    if (I < J) {
+      for (int jj = 0; jj < jn; ++jj) {
+        const float d0 = sqdist<MM>(a0, uj[jj]);
+        const float d1 = sqdist<MM>(a1, uj[jj]);
+        if (i0 < N) hist_add(hist, d0, pass, prefix);
+        if (i1 < N) hist_add(hist, d1, pass, prefix);
+      }
+    } else {
+      // diagonal tile: only j > i
+      const int l0 = threadIdx.x, l1 = threadIdx.x + kTile;
+      for (int jj = l0 + 1; jj < jn; ++jj) {
+        const float d0 = sqdist<MM>(a0, uj[jj]);
+        if (i0 < N) hist_add(hist, d0, pass, prefix);
+        if (jj > l1 && i1 < N) hist_add(hist, sqdist<MM>(a1, uj[jj]), pass, prefix);
       }
     }
     __syncthreads();
@@ -103,7 +175,8 @@ __global__ void __launch_bounds__(kTile) median_hist_kernel(int N, int M, const 
 
 // Resolve one radix digit: find the bin holding the rank-th element, narrow
 // the prefix and the rank, clear the histogram.  One warp.
-__global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N) {
+__global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N, int required_mode) {
+  if (required_mode >= 0 && ctl->mode != required_mode) return;
   const int lane = threadIdx.x;  // 32 lanes x 64 bins
   unsigned int local = 0u;
   for (int b = 0; b < 64; ++b) local += ctl->hist[lane * 64 + b];
@@ -139,56 +212,257 @@ __global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N)
   for (int b = 0; b < 64; ++b) ctl->hist[lane * 64 + b] = 0u;
 }
 
+// ---- sampled bracket around the median (large N) -------------------------
+// A sample of kSample ordered pairs (i != j, from a counter-based hash) is
+// sorted in shared memory; the order statistics at ranks kSample/2 -+ 2
+// sqrt(kSample) (4 standard deviations of the sample median's rank) bracket
+// the median of all pairs with high probability.  One pass over all pairs
+// then counts the pairs below the bracket and collects those inside it; the
+// radix select finishes on the candidates only.  If the bracket missed the
+// median, or the candidates overflow their buffer, the three full passes
+// over all pairs run instead, so the result is always the exact median.
+constexpr int kSample = 16384;
+constexpr int kSampleThreads = 1024;
+constexpr int kSampleMargin = 256;     // 2 sqrt(kSample)
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+  // SplitMix64 finaliser (Steele, Lea and Flood, 2014)
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  return x ^ (x >> 31);
+}
+
+// Distances of kSample hashed ordered pairs (one per thread, many blocks).
+template <int MM>
+__global__ void __launch_bounds__(256) median_sample_dist_kernel(int N, int M, const float* __restrict__ u,
+                                                                 float* __restrict__ samp) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= kSample) return;
+  const unsigned long long h = mix64((unsigned long long)s);
+  const int i = (int)((h & 0xffffffffull) % (unsigned long long)N);
+  int j = (int)((h >> 32) % (unsigned long long)(N - 1));
+  if (j >= i) ++j;
+  float d = 0.f;
+#pragma unroll
+  for (int k = 0; k < MM; ++k) {
+    if (k < M) {
+      const float e = u[(size_t)k * N + i] - u[(size_t)k * N + j];
+      d = fmaf(e, e, d);
+    }
+  }
+  samp[s] = d;
+}
+
+// Sort the sample in shared memory (bitonic, one block) and keep the two
+// order statistics that bracket the median.
+__global__ void __launch_bounds__(kSampleThreads) median_sample_sort_kernel(const float* __restrict__ samp,
+                                                                            SvgdCtl* __restrict__ ctl) {
+  extern __shared__ float smp[];  // kSample floats
+  for (int s = threadIdx.x; s < kSample; s += kSampleThreads) smp[s] = samp[s];
+  __syncthreads();
+  for (int k = 2; k <= kSample; k <<= 1) {
+    for (int jd = k >> 1; jd > 0; jd >>= 1) {
+      for (int idx = threadIdx.x; idx < kSample; idx += kSampleThreads) {
+        const int ixj = idx ^ jd;
+        if (ixj > idx) {
+          const float a = smp[idx], b = smp[ixj];
+          const bool up = (idx & k) == 0;
+          if ((a > b) == up) { smp[idx] = b; smp[ixj] = a; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    ctl->lo = smp[kSample / 2 - kSampleMargin];
+    ctl->hi = smp[kSample / 2 + kSampleMargin];
+  }
+}
+
+constexpr int kCandBuf = 8192;       // per-block shared candidate buffer (floats)
+constexpr int kCandFlushEvery = 16;  // j steps between flush checks (adds <= 16 * kSpan)
+
+__device__ __forceinline__ void cand_flush(float* __restrict__ buf, unsigned int* __restrict__ count,
+                                           SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
+                                           unsigned long long cap) {
+  __shared__ unsigned long long base;
+  const unsigned int n = *count;
+  if (threadIdx.x == 0) base = n ? atomicAdd(&ctl->inside, (unsigned long long)n) : 0ull;
+  __syncthreads();
+  for (unsigned int k = threadIdx.x; k < n; k += blockDim.x)
+    if (base + k < cap) cand[base + k] = buf[k];
+  __syncthreads();
+  if (threadIdx.x == 0) *count = 0u;
+  __syncthreads();
+}
+
+// One pass over all pairs i < j: count d < lo, collect lo <= d <= hi.
+template <int MM>
+__global__ void __launch_bounds__(kTile) median_bracket_kernel(int N, int M, const float* __restrict__ u,
+                                                               SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
+                                                               unsigned long long cap) {
+  constexpr int Q = Pad4<MM>::Q;
+  __shared__ float4 uj[kSpan][Q];
+  __shared__ float buf[kCandBuf];
+  __shared__ unsigned int count;
+  __shared__ unsigned long long below_blk;
+  if (threadIdx.x == 0) { count = 0u; below_blk = 0ull; }
+  const float lo = ctl->lo, hi = ctl->hi;
+  const int nt = (N + kSpan - 1) / kSpan;
+  const long long ntiles = (long long)nt * nt;
+  unsigned int below = 0u;
+  __syncthreads();
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int I = (int)(tile / nt), J = (int)(tile - (long long)I * nt);
+    if (I > J) continue;  // uniform across the block
+    const int i0 = I * kSpan + threadIdx.x, i1 = i0 + kTile;
+    float a0[MM], a1[MM];
+    load_row<MM>(u, M, N, i0, a0);
+    load_row<MM>(u, M, N, i1, a1);
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int jl = threadIdx.x + r * kTile;
+      const int j = J * kSpan + jl;
+      stage_row<MM>(u, M, N, j, j < N, uj[jl]);
+    }
+    __syncthreads();
+    const int jn = min(kSpan, N - J * kSpan);
+    const bool diag = (I == J);
+    const int l0 = threadIdx.x, l1 = threadIdx.x + kTile;
+    for (int jb = 0; jb < jn; jb += kCandFlushEvery) {
+      const int je = min(jn, jb + kCandFlushEvery);
+      for (int jj = jb; jj < je; ++jj) {
+        const float d0 = sqdist<MM>(a0, uj[jj]);
+        const float d1 = sqdist<MM>(a1, uj[jj]);
+        const bool v0 = (i0 < N) && (!diag || jj > l0);
+        const bool v1 = (i1 < N) && (!diag || jj > l1);
+        below += (v0 && d0 < lo) + (v1 && d1 < lo);
+        const bool c0 = v0 && d0 >= lo && d0 <= hi;
+        const bool c1 = v1 && d1 >= lo && d1 <= hi;
+        const unsigned int m0 = __ballot_sync(0xffffffffu, c0);
+        const unsigned int m1 = __ballot_sync(0xffffffffu, c1);
+        const int lane = threadIdx.x & 31;
+        if (m0 | m1) {
+          unsigned int wbase = 0u;
+          if (lane == 0) wbase = atomicAdd(&count, (unsigned int)(__popc(m0) + __popc(m1)));
+          wbase = __shfl_sync(0xffffffffu, wbase, 0);
+          const unsigned int lt = (1u << lane) - 1u;
+          if (c0) buf[wbase + __popc(m0 & lt)] = d0;
+          if (c1) buf[wbase + __popc(m0) + __popc(m1 & lt)] = d1;
+        }
+      }
+      __syncthreads();
+      if (count > kCandBuf - kCandFlushEvery * kSpan) cand_flush(buf, &count, ctl, cand, cap);
+    }
+    __syncthreads();
+  }
+  cand_flush(buf, &count, ctl, cand, cap);
+  atomicAdd(&below_blk, (unsigned long long)below);
+  __syncthreads();
+  if (threadIdx.x == 0 && below_blk) atomicAdd(&ctl->below, below_blk);
+}
+
+// Decide between the candidate path and the full passes.
+__global__ void median_resolve_kernel(SvgdCtl* __restrict__ ctl, unsigned long long cap) {
+  const unsigned long long rank = ctl->rank;
+  const unsigned long long below = ctl->below, inside = ctl->inside;
+  if (below <= rank && rank < below + inside && inside <= cap) {
+    ctl->mode = 0;
+    ctl->rank = (unsigned int)(rank - below);
+  } else {
+    ctl->mode = 1;
+  }
+}
+
+// Radix pass over the candidates (mode 0 only).
+__global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __restrict__ cand,
+                                                               SvgdCtl* __restrict__ ctl, int pass) {
+  __shared__ unsigned int hist[kHistBins];
+  if (ctl->mode != 0) return;
+  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  const unsigned long long n = ctl->inside;
+  const unsigned int prefix = ctl->prefix;
+  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (unsigned long long)gridDim.x * blockDim.x)
+    hist_add(hist, cand[k], pass, prefix);
+  __syncthreads();
+  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
+    const unsigned int h = hist[b];
+    if (h) atomicAdd(&ctl->hist[b], h);
+  }
+}
+
+int svgd_sample_size() { return kSample; }
+
+unsigned long long svgd_cand_capacity(int N) {
+  if (N < 2048) return 0ull;
+  const unsigned long long pairs = (unsigned long long)N * (unsigned long long)(N - 1) / 2ull;
+  unsigned long long cap = pairs / 12ull;  // 8 % of the pairs; the bracket expects 3.1 %
+  if (cap < (1ull << 20)) cap = 1ull << 20;
+  return cap;
+}
+
 // Partial phi over one chunk of j: phi_part[c][k][i] =
 //   sum_j k_ij g_j[k] + (2/bw) sum_j k_ij (u_i[k] - u_j[k]).
-template <int MM>
+// A block owns kSpan rows (kRows per thread); j is staged kTile at a time.
+template <int MM, bool FAST>
 __global__ void __launch_bounds__(kTile) svgd_phi_kernel(int N, int M, const float* __restrict__ u,
                                                          const float* __restrict__ gu, const SvgdCtl* __restrict__ ctl,
                                                          float* __restrict__ phi_part, int chunk_len) {
-  __shared__ float uj[MM][kTile];
-  __shared__ float gj[MM][kTile];
-  const int i = blockIdx.x * kTile + threadIdx.x;
+  constexpr int Q = Pad4<MM>::Q;
+  __shared__ float4 uj[kTile][Q];
+  __shared__ float4 gj[kTile][Q];
+  const int i0 = blockIdx.x * kSpan + threadIdx.x, i1 = i0 + kTile;
   const int c = blockIdx.y;
   const int j0 = c * chunk_len;
   const int j1 = min(N, j0 + chunk_len);
   const float bw = ctl->bw;
   const float inv_bw = 1.0f / bw;
-  float ui[MM], ag[MM], ar[MM];
-  load_row<MM>(u, M, N, i, ui);
+  float a0[MM], a1[MM], g0[MM], g1[MM], r0[MM], r1[MM];
+  load_row<MM>(u, M, N, i0, a0);
+  load_row<MM>(u, M, N, i1, a1);
 #pragma unroll
-  for (int k = 0; k < MM; ++k) { ag[k] = 0.f; ar[k] = 0.f; }
+  for (int k = 0; k < MM; ++k) { g0[k] = 0.f; g1[k] = 0.f; r0[k] = 0.f; r1[k] = 0.f; }
   for (int jt = j0; jt < j1; jt += kTile) {
     const int j = jt + threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < MM; ++k) {
-      const bool ok = (k < M) && (j < j1);
-      uj[k][threadIdx.x] = ok ? u[(size_t)k * N + j] : 0.f;
-      gj[k][threadIdx.x] = ok ? gu[(size_t)k * N + j] : 0.f;
-    }
+    stage_row<MM>(u, M, N, j, j < j1, uj[threadIdx.x]);
+    stage_row<MM>(gu, M, N, j, j < j1, gj[threadIdx.x]);
     __syncthreads();
     const int jn = min(kTile, j1 - jt);
     for (int jj = 0; jj < jn; ++jj) {
-      float e[MM];
-      float d = 0.f;
+      float v[MM], e0[MM], e1[MM];
+      unpack_row<MM>(uj[jj], v);
+      float d0 = 0.f, d1 = 0.f;
 #pragma unroll
       for (int k = 0; k < MM; ++k) {
-        e[k] = ui[k] - uj[k][jj];
-        d = fmaf(e[k], e[k], d);
+        e0[k] = a0[k] - v[k];
+        e1[k] = a1[k] - v[k];
+        d0 = fmaf(e0[k], e0[k], d0);
+        d1 = fmaf(e1[k], e1[k], d1);
       }
-      const float kij = expf(-d * inv_bw);
+      const float k0 = FAST ? __expf(-d0 * inv_bw) : expf(-d0 * inv_bw);
+      const float k1 = FAST ? __expf(-d1 * inv_bw) : expf(-d1 * inv_bw);
+      float gg[MM];
+      unpack_row<MM>(gj[jj], gg);
 #pragma unroll
       for (int k = 0; k < MM; ++k) {
-        ag[k] = fmaf(kij, gj[k][jj], ag[k]);
-        ar[k] = fmaf(kij, e[k], ar[k]);
+        g0[k] = fmaf(k0, gg[k], g0[k]);
+        g1[k] = fmaf(k1, gg[k], g1[k]);
+        r0[k] = fmaf(k0, e0[k], r0[k]);
+        r1[k] = fmaf(k1, e1[k], r1[k]);
       }
     }
     __syncthreads();
   }
-  if (i < N) {
-    const float two_over_bw = 2.0f * inv_bw;
+  const float two_over_bw = 2.0f * inv_bw;
 #pragma unroll
-    for (int k = 0; k < MM; ++k)
-      if (k < M) phi_part[((size_t)c * M + k) * N + i] = fmaf(two_over_bw, ar[k], ag[k]);
+  for (int k = 0; k < MM; ++k) {
+    if (k < M) {
+      if (i0 < N) phi_part[((size_t)c * M + k) * N + i0] = fmaf(two_over_bw, r0[k], g0[k]);
+      if (i1 < N) phi_part[((size_t)c * M + k) * N + i1] = fmaf(two_over_bw, r1[k], g1[k]);
+    }
   }
 }
 
@@ -228,7 +502,7 @@ __global__ void svgd_adam_kernel(SvgdParams sp, const SvgdCtl* __restrict__ ctl,
 }
 
 int svgd_phi_chunks(int N) {
-  const int row_blocks = (N + kTile - 1) / kTile;
+  const int row_blocks = (N + kSpan - 1) / kSpan;
   int chunks = (8 * 152 + row_blocks - 1) / row_blocks;
   const int max_chunks = (N + kTile - 1) / kTile;
   if (chunks > max_chunks) chunks = max_chunks;
@@ -241,27 +515,56 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
                                   float* phi_out, cudaStream_t st, int* launches) {
   const int N = sp.N, M = sp.M;
   int n = 0;
+  const bool bracket = (N >= 2) && w.cand && w.cand_cap > 0;
   {
     const int total = (M * N > kHistBins) ? M * N : kHistBins;
-    svgd_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(sp, w.ctl, X, G, w.u, w.gu);
+    svgd_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
     ++n;
   }
   if (N >= 2) {
-    const int nt = (N + kTile - 1) / kTile;
-    const long long tiles = (long long)nt * (nt + 1) / 2;
-    int grid = 152 * 8;
-    if (tiles < grid) grid = (int)((long long)nt * nt);
+    const int nt = (N + kSpan - 1) / kSpan;
+    const long long all_tiles = (long long)nt * nt;
+    const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
+    if (bracket) {
+      // 64 KiB of dynamic shared memory for the sample: opt in once per device
+      static bool smem_ok[64];
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !smem_ok[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(median_sample_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(kSample * sizeof(float)));
+        if (e != cudaSuccess) return e;
+        smem_ok[dev] = true;
+      }
+      median_sample_dist_kernel<MM><<<kSample / 256, 256, 0, st>>>(N, M, w.u, w.samp);
+      median_sample_sort_kernel<<<1, kSampleThreads, kSample * sizeof(float), st>>>(w.samp, w.ctl);
+      n += 1;
+      median_bracket_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, w.cand, w.cand_cap);
+      median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);
+      n += 3;
+      for (int pass = 0; pass < 3; ++pass) {
+        median_cand_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, pass);
+        median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 0);
+        n += 2;
+      }
+    }
+    // full passes over all pairs: always for small N, otherwise only if the
+    // bracket missed (the kernels return at once in that case)
     for (int pass = 0; pass < 3; ++pass) {
-      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, pass);
-      median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N);
+      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, pass, bracket ? 1 : 0);
+      median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 1);
       n += 2;
     }
   }
   {
-    const int chunk_len = ((N + w.chunks - 1) / w.chunks + kTile - 1) / kTile * kTile;
+    const int chunks0 = svgd_phi_chunks(N);
+    const int chunk_len = ((N + chunks0 - 1) / chunks0 + kTile - 1) / kTile * kTile;
     const int chunks = (N + chunk_len - 1) / chunk_len;
-    dim3 grid((N + kTile - 1) / kTile, chunks);
-    svgd_phi_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+    dim3 grid((N + kSpan - 1) / kSpan, chunks);
+    if (sp.fast_math)
+      svgd_phi_kernel<MM, true><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+    else
+      svgd_phi_kernel<MM, false><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
     const size_t total = (size_t)sp.P * N;
     svgd_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, w.ctl, X, G, w.phi_part, chunks, w.adam_m,
                                                                       w.adam_v, bw_out, phi_out);
@@ -320,6 +623,7 @@ __global__ void noalloc_prep_kernel(int N, int M, NoAllocBox box, const float* _
     ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
     ctl->bw = 1.0f;
     ctl->med = 0.0f;
+    ctl->mode = 1;
   }
   if (idx < M * N) {
     const int k = idx / N;
@@ -337,12 +641,12 @@ static cudaError_t noalloc_bandwidth_mm(int N, int M, const NoAllocBox& box, con
   const int total = (M * N > kHistBins) ? M * N : kHistBins;
   noalloc_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(N, M, box, theta, ctl, u);
   if (N >= 2) {
-    const int nt = (N + kTile - 1) / kTile;
+    const int nt = (N + kSpan - 1) / kSpan;
     const long long all_tiles = (long long)nt * nt;
     const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
     for (int pass = 0; pass < 3; ++pass) {
-      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, u, ctl, pass);
-      median_select_kernel<<<1, 32, 0, st>>>(ctl, pass, N);
+      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, u, ctl, pass, 0);
+      median_select_kernel<<<1, 32, 0, st>>>(ctl, pass, N, -1);
     }
   }
   noalloc_out_kernel<<<1, 1, 0, st>>>(ctl, out);

@@ -31,9 +31,9 @@ def _case(N, M, P, seed, spread=1.0):
     return lo, hi, x.astype(np.float32).astype(np.float64), g.astype(np.float32).astype(np.float64)
 
 
-def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2):
+def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2, fast=False):
     lo, hi, x, g = _case(N, M, P, seed, spread)
-    sv = api.Svgd(N, M, P, lo, hi, lr=lr)
+    sv = api.Svgd(N, M, P, lo, hi, lr=lr, fast_math=fast)
     X, G = _gpu(x), _gpu(g)
     ost = orc.SvgdState(N, P, lo, hi, lr=lr)
     xo = np.ascontiguousarray(x.copy())
@@ -50,9 +50,11 @@ def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2):
     assert np.max(np.abs(xg - xo) / width) <= 1e-4 * steps, np.max(np.abs(xg - xo) / width)
 
 
-@pytest.mark.parametrize("N,M,P", [(2, 1, 1), (3, 2, 5), (100, 4, 76), (129, 10, 30), (1000, 7, 7), (257, 16, 40)])
-def test_svgd_step_matches_oracle(N, M, P):
-    _compare(N, M, P, seed=N + 10 * M)
+@pytest.mark.parametrize("fast", [False, True])
+@pytest.mark.parametrize("N,M,P", [(2, 1, 1), (3, 2, 5), (100, 4, 76), (129, 10, 30), (1000, 7, 7), (257, 16, 40),
+                                   (600, 3, 9), (1031, 9, 9)])
+def test_svgd_step_matches_oracle(N, M, P, fast):
+    _compare(N, M, P, seed=N + 10 * M, fast=fast)
 
 
 def test_svgd_five_steps_match_oracle():
@@ -126,3 +128,39 @@ def test_svgd_rejects_bad_sizes():
         api.Svgd(10, 17, 17, np.zeros(17), np.ones(17))
     with pytest.raises(api.PdsError):
         api.Svgd(10, 2, 2, [0, 1], [1, 1])
+
+
+def _bw(x, lo, hi, full):
+    N, M = x.shape
+    sv = api.Svgd(N, M, M, lo, hi)
+    sv.set_option(api.OPT_MEDIAN_FULL_PASSES, int(full))
+    bw, _ = sv.step(_gpu(x), _gpu(np.zeros_like(x)))
+    torch.cuda.synchronize()
+    out = float(bw.item())
+    sv.close()
+    return out
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clusters", "grid_ties"])
+def test_sampled_bracket_median_equals_full_passes(kind):
+    """N >= 2048 selects the median among the pairs inside a sampled bracket;
+    it must equal the three full radix passes bit for bit."""
+    rng = np.random.default_rng(17)
+    N, M = 4099, 5
+    lo, hi = np.zeros(M), np.ones(M)
+    if kind == "uniform":
+        x = rng.uniform(size=(N, M))
+    elif kind == "clusters":
+        c = rng.uniform(size=(3, M))
+        x = np.clip(c[rng.integers(0, 3, N)] + 0.01 * rng.normal(size=(N, M)), 0, 1)
+    else:
+        x = rng.integers(0, 4, size=(N, M)) / 4.0  # few distinct distances, many ties
+    x = x.astype(np.float32).astype(np.float64)
+    b_bracket = _bw(x, lo, hi, False)
+    b_full = _bw(x, lo, hi, True)
+    assert b_bracket == b_full
+    if kind == "grid_ties":
+        u = x
+        d = ((u[:, None, :] - u[None, :, :]) ** 2).sum(-1)[np.triu_indices(N, 1)]
+        med = np.partition(d, (len(d) - 1) // 2)[(len(d) - 1) // 2]
+        assert abs(b_full - med / np.log(N)) <= 1e-6 * med / np.log(N)
