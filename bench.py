@@ -321,6 +321,12 @@ def run_pds(args):
                "sample": f"{args.ref_sample_baseline} particles x T={wl.T} log p + gradient (FP64, forward-mode "
                          f"duals), {secs:.1f} s on {threads} threads"}
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_batched:
+        extra["batched"] = run_batched(api, dev, stream)
+    if rank == 0 and world == 1 and not args.no_serving:
+        extra["serving"] = run_serving(api, dev, stream)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -329,10 +335,98 @@ def run_pds(args):
             "svgd_iters_per_sec": 1e3 / ms_per_step, "gpu_launches": launches, "e2e": e2e,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed": t_wall,
         }
+        line.update(extra)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def _gen_obs(api, wl, dev, stream):
+    """Observations from the library's own f_sim of the true parameters."""
+    import torch
+    with torch.cuda.stream(stream):
+        gen = api.Problem.from_workload(wl, np.zeros((wl.T, wl.D), np.float32), stream=stream)
+        th = torch.tensor(wl.theta_true, dtype=torch.float32, device=dev).reshape(wl.M, 1).contiguous()
+        states = gen.simulate(th)
+    stream.synchronize()
+    obs = wlmod.observations(wl, states[:, :, 0].cpu().numpy().astype(np.float64)).astype(np.float32)
+    gen.close()
+    return obs
+
+
+def run_batched(api, dev, stream, n_jobs=64, iters=10):
+    """64 uneven problems: batched (persistent launches + graph, autotuned)
+    against the plain path (each problem's iteration launched separately)."""
+    import torch
+    wls = wlmod.batched_problems(n_jobs=n_jobs, seed=4000)
+    obs = [_gen_obs(api, w, dev, stream) for w in wls]
+    x0 = [np.ascontiguousarray(wlmod.initial_particles(w, o.astype(np.float64), rng_seed=1).T, dtype=np.float32)
+          for w, o in zip(wls, obs)]
+    units = sum(w.N * w.T for w in wls)
+    probs = [api.Problem.from_workload(w, o, stream=stream, checkpoint_stride=K_CKPT, fast_math=FAST_MATH)
+             for w, o in zip(wls, obs)]
+    svgds = [api.Svgd(w.N, w.M, w.P, w.lo, w.hi, lr=w.lr, stream=stream) for w in wls]
+    Xs = [torch.from_numpy(x).to(dev) for x in x0]
+    b = api.Batch(probs, svgds, Xs, stream=stream)
+    t_tune = time.perf_counter()
+    choices = b.autotune(allow_fast_math=bool(FAST_MATH))
+    t_tune = time.perf_counter() - t_tune
+    b.iterate(3)
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.iterate(iters)
+    e1.record(stream)
+    e1.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3 / iters
+    ng, lpi = b.info()
+    b.close()
+    # plain: same problems, one after another, separate launches per iteration
+    Xp = [torch.from_numpy(x).to(dev) for x in x0]
+    for p, s, x in zip(probs, svgds, Xp):
+        s.reset()
+        api.iterate(p, s, x, 1)
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(2):
+        for p, s, x in zip(probs, svgds, Xp):
+            api.iterate(p, s, x, 1)
+    e1.record(stream)
+    e1.synchronize()
+    t_p = e0.elapsed_time(e1) / 1e3 / 2
+    for o in probs + svgds:
+        o.close()
+    return {"workload": f"{n_jobs} uneven problems: chains of 2-8 links, T 100-2000, W 5-50, N 64-4096 "
+                        "(log-uniform), pendulum/damped parameter types 50/50",
+            "particle_steps_per_iter": units, "value": units / t_b, "unit": UNIT, "ms_per_iter": t_b * 1e3,
+            "plain_value": units / t_p, "plain_ms_per_iter": t_p * 1e3, "speedup_vs_plain": t_p / t_b,
+            "chain_length_groups": ng, "launches_per_iter_in_graph": lpi,
+            "autotune": [{"links": c[0], "K": c[1], "fast_math": c[2], "grid_blocks": c[3]} for c in choices],
+            "autotune_s": t_tune}
+
+
+def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300):
+    """Poisson arrivals of jobs from the uneven-problem distribution, each
+    run to `iters` SVGD iterations: continuous batching against one job at a
+    time with plain launches."""
+    from paper_2109_08815_gb300 import serve
+    wls = wlmod.batched_problems(n_jobs=n_jobs, seed=5000)
+    jobs = []
+    for w in wls:
+        o = _gen_obs(api, w, dev, stream)
+        jobs.append((w, o, wlmod.initial_particles(w, o.astype(np.float64), rng_seed=1), iters))
+    arrivals = serve.poisson_arrivals(n_jobs, rate, seed=5000)
+    units = sum(w.N * w.T for w in wls) * iters
+    lat_s, _, wall_s = serve.run_server(jobs, arrivals, mem_budget=64 << 30, stream=stream,
+                                        checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH))
+    lat_p, _, wall_p = serve.run_plain(jobs, arrivals, checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH),
+                                       stream=stream)
+    return {"workload": f"{n_jobs} jobs, Poisson arrivals at {rate:g}/s, {iters} SVGD iterations each, "
+                        "uneven-problem distribution",
+            "served": {**serve.percentiles(lat_s), "value": units / wall_s, "wall_s": wall_s},
+            "plain_sequential": {**serve.percentiles(lat_p), "value": units / wall_p, "wall_s": wall_p},
+            "unit": UNIT, "time_to_posterior": "arrival to final particles on the host"}
 
 
 # dram bytes per rollout launch from the committed ncu capture of this kernel
@@ -349,6 +443,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-problems measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
     ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
     args = ap.parse_args()

@@ -26,6 +26,7 @@
 #ifndef PDS_H_
 #define PDS_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -37,6 +38,7 @@ extern "C" {
 #define PDS_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed       */
 #define PDS_ERR_OOM (-3)         /* device allocation failed                   */
 #define PDS_ERR_NONFINITE (-4)   /* reserved: non-finite result reported       */
+#define PDS_ERR_BUDGET (-6)      /* job larger than the server's memory budget */
 #define PDS_ERR_UNSUPPORTED (-7) /* configuration outside the compiled range   */
 
 #define PDS_SYSTEM_PLANAR_CHAIN 1
@@ -188,6 +190,85 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
  * Pinned host memory gives the fastest copies. */
 int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters,
                      float* logp_host);
+
+/* ---- Batched execution of many problems (uneven chain length, trajectory
+ * length, window count and particle count).  Every iteration runs one
+ * persistent rollout launch per chain length over all problems' (particle,
+ * window) units -- work items ordered longest window first and taken through
+ * an atomic counter -- then each problem's window reduction and SVGD update
+ * on parallel CUDA-graph branches.  The iteration is captured once into a
+ * CUDA graph (on the first pds_batch_iterate after creation or autotuning)
+ * and replayed (the first iteration after creation or autotuning runs with
+ * plain launches).  Results equal those of running each problem alone with the
+ * same settings, up to rounding.  No counterpart in the paper, which runs one
+ * problem at a time; this is Algorithm 1 applied to many problems at once. */
+typedef struct pds_batch* pds_batch_t;
+
+/* problems/svgds/particles: arrays of n_jobs handles and device particle
+ * buffers ([P_j][N_j], owned by the caller, updated in place every
+ * iteration).  logp: NULL or n_jobs device pointers ([N_j] each), written
+ * with log p of the particles before each update.  The batch takes over the
+ * problems' checkpoint-stride and fast-math settings (per chain length) and
+ * queues its work on cuda_stream; do not use the problems or SVGD states
+ * elsewhere while the batch exists. */
+int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const* svgds,
+                     float* const* particles, float* const* logp, void* cuda_stream,
+                     pds_batch_t* out);
+int pds_batch_destroy(pds_batch_t b);
+
+/* Autotuner: for every chain length present, time the batched rollout for
+ * checkpoint strides K in {5, 10, 25, 50}, exact or (allow_fast_math) fast
+ * math, and the two largest persistent grid sizes, and keep the fastest.
+ * choices: NULL or [4 * number of chain lengths] ints receiving
+ * (links, K, fast_math, grid blocks) per chain length.  Synchronises. */
+int pds_batch_autotune(pds_batch_t b, int allow_fast_math, int* choices);
+
+/* Run `iters` iterations of every problem (graph replays; asynchronous). */
+int pds_batch_iterate(pds_batch_t b, int iters);
+
+/* Number of chain-length groups and kernel launches per iteration (inside
+ * the graph). */
+int pds_batch_info(pds_batch_t b, int* n_groups, int* launches_per_iter);
+
+/* ---- Serving with continuous batching.  Jobs (one problem, its initial
+ * particles, an iteration count) enter a FIFO queue.  Each pds_server_tick
+ * admits queued jobs while their estimated device memory (problem workspace,
+ * adjoint tape, SVGD state, particles) fits the budget and the active-job
+ * limit, runs one SVGD iteration of every active job in one batched launch
+ * (pds_batch over the active set, rebuilt when it changes), copies the
+ * particles and last log p of jobs that reached their iteration count to the
+ * host and releases their device memory.  Every job's state stays on the
+ * device between ticks.  Jobs use SVGD with Adam (beta1 0.9, beta2 0.999,
+ * eps 1e-8) and clamping to the box, as pds_svgd_create.  The server queues
+ * its work on cuda_stream and synchronises it at the end of every tick.  No
+ * counterpart in the paper (Algorithm 1 for a stream of requests). */
+#define PDS_JOB_QUEUED 0
+#define PDS_JOB_ACTIVE 1
+#define PDS_JOB_DONE 2
+typedef struct pds_server* pds_server_t;
+int pds_server_create(size_t mem_budget_bytes, int max_active, void* cuda_stream, pds_server_t* out);
+int pds_server_destroy(pds_server_t s);
+/* Checkpoint stride and math variant of the rollouts of jobs admitted from
+ * now on (defaults 5 and fast math). */
+int pds_server_set_rollout_options(pds_server_t s, int checkpoint_stride, int fast_math);
+/* Arguments as pds_problem_create plus N particles (host [P][N], copied),
+ * the Adam learning rate and the number of SVGD iterations.  Fails with
+ * PDS_ERR_BUDGET if the job alone exceeds the memory budget. */
+int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int T, int windows,
+                      const float* obs, int D, const int* obs_index, double sigma_obs,
+                      double sigma_def, const float* s0, const float* theta_lo,
+                      const float* theta_hi, double c_lim, int N, const float* particles,
+                      double lr, int iterations, long long* job_id);
+/* One scheduling step (admit, iterate, retire); synchronises the stream. */
+int pds_server_tick(pds_server_t s, int* n_active, int* n_retired);
+/* PDS_JOB_* state and iterations done so far. */
+int pds_server_status(pds_server_t s, long long job_id, int* state, int* iterations_done);
+/* Copy a finished job's particles (host [P][N]) and last log p (host [N] or
+ * NULL) and forget the job. */
+int pds_server_result(pds_server_t s, long long job_id, float* particles, float* logp);
+/* Remove a queued or active job (its device memory is released). */
+int pds_server_cancel(pds_server_t s, long long job_id);
+int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_use);
 
 /* Median-heuristic bandwidth of N particles without allocating any device
  * memory.  The paper has no counterpart: this entry point exists for callers

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libpds.so")
 PDS_SYSTEM_PLANAR_CHAIN = 1
 PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
 OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES = 1, 2, 3
+JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()
@@ -63,6 +64,24 @@ EXPORTS = {
     "pds_svgd_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_iterate_host": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
+    "pds_batch_create": ([ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                          ctypes.POINTER(_vp), _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_batch_destroy": ([_vp], ctypes.c_int),
+    "pds_batch_autotune": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
+    "pds_batch_iterate": ([_vp, ctypes.c_int], ctypes.c_int),
+    "pds_batch_info": ([_vp, _ip, _ip], ctypes.c_int),
+    "pds_server_create": ([ctypes.c_size_t, ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_server_destroy": ([_vp], ctypes.c_int),
+    "pds_server_set_rollout_options": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "pds_server_submit": ([_vp, ctypes.POINTER(_SystemDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
+                           ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
+                           ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
+                          ctypes.c_int),
+    "pds_server_tick": ([_vp, _ip, _ip], ctypes.c_int),
+    "pds_server_status": ([_vp, ctypes.c_longlong, _ip, _ip], ctypes.c_int),
+    "pds_server_result": ([_vp, ctypes.c_longlong, _fp, _fp], ctypes.c_int),
+    "pds_server_cancel": ([_vp, ctypes.c_longlong], ctypes.c_int),
+    "pds_server_stats": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "pds_bandwidth_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _fp, _fp, _vp, _vp], ctypes.c_int),
     "pds_last_launch_count": ([], ctypes.c_int),
     "pds_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -287,6 +306,147 @@ def iterate_host(problem: Problem, svgd: Svgd, particles: np.ndarray, iters: int
     lp = None if logp is None else ctypes.c_void_p(logp.ctypes.data)
     _check(lib().pds_iterate_host(problem.handle, svgd.handle, ctypes.c_void_p(particles.ctypes.data), int(iters),
                                   lp), "pds_iterate_host")
+
+
+class Batch:
+    """Many problems iterated together (pds_batch_*): one persistent rollout
+    launch per chain length plus per-problem SVGD branches, replayed from a
+    captured CUDA graph."""
+
+    def __init__(self, problems, svgds, particles, logp=None, stream=None):
+        L = lib()
+        n = len(problems)
+        assert len(svgds) == n and len(particles) == n
+        for x in particles:
+            _need_cuda(x, torch.float32, "particles")
+        self._problems, self._svgds, self._particles = list(problems), list(svgds), list(particles)
+        self._logp = list(logp) if logp is not None else None
+        arr = lambda xs: (_vp * n)(*[ctypes.c_void_p(x) for x in xs])  # noqa: E731
+        ph = arr([p.handle.value for p in problems])
+        sh = arr([s.handle.value for s in svgds])
+        xh = arr([x.data_ptr() for x in particles])
+        lh = arr([t.data_ptr() for t in logp]) if logp is not None else None
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_batch_create(n, ph, sh, xh, lh, self._stream_h, ctypes.byref(h)), "pds_batch_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pds_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def autotune(self, allow_fast_math=True):
+        """Returns [(links, K, fast_math, grid_blocks)] per chain length."""
+        ch = (ctypes.c_int * (4 * 8))()
+        _check(lib().pds_batch_autotune(self._h, int(bool(allow_fast_math)), ch), "pds_batch_autotune")
+        ng, _ = self.info()
+        return [tuple(ch[4 * g:4 * g + 4]) for g in range(ng)]
+
+    def iterate(self, iters=1):
+        _check(lib().pds_batch_iterate(self._h, int(iters)), "pds_batch_iterate")
+
+    def info(self):
+        ng, lpi = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pds_batch_info(self._h, ctypes.byref(ng), ctypes.byref(lpi)), "pds_batch_info")
+        return ng.value, lpi.value
+
+
+class Server:
+    """Serving loop with continuous batching (pds_server_*)."""
+
+    def __init__(self, mem_budget_bytes: int, max_active: int = 256, stream=None, checkpoint_stride=None,
+                 fast_math=None):
+        L = lib()
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_server_create(int(mem_budget_bytes), int(max_active), self._stream_h, ctypes.byref(h)),
+               "pds_server_create")
+        self._h = h
+        if checkpoint_stride is not None or fast_math is not None:
+            _check(L.pds_server_set_rollout_options(h, int(checkpoint_stride or 5), int(1 if fast_math is None
+                                                                                         else bool(fast_math))),
+                   "pds_server_set_rollout_options")
+        self._shapes = {}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pds_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, wl, obs, particles: np.ndarray, iterations: int) -> int:
+        """Submit a workload-shaped job; particles [N][P] (host)."""
+        keep = []
+
+        def d(x):
+            a = np.ascontiguousarray(x, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        def i(x):
+            a = np.ascontiguousarray(x, dtype=np.int32)
+            keep.append(a)
+            return a.ctypes.data_as(_ip)
+
+        def f(x):
+            a = np.ascontiguousarray(x, dtype=np.float32)
+            keep.append(a)
+            return a.ctypes.data_as(_fp)
+
+        obs = np.ascontiguousarray(obs, dtype=np.float32)
+        sysd = _SystemDesc(kind=PDS_SYSTEM_PLANAR_CHAIN, n_links=wl.n, mass=d(wl.mass), length=d(wl.length),
+                           damping=d(wl.damping), gravity=float(wl.g), n_theta=wl.M, theta_kind=i(wl.theta_kind),
+                           theta_link=i(wl.theta_link))
+        x = np.ascontiguousarray(np.asarray(particles).T, dtype=np.float32)  # [P][N]
+        jid = ctypes.c_longlong()
+        _check(lib().pds_server_submit(self._h, ctypes.byref(sysd), float(wl.dt), int(wl.T), int(wl.W), f(obs),
+                                       obs.shape[1], i(wl.obs_index), float(wl.sigma_obs), float(wl.sigma_def),
+                                       f(wl.s0), f(wl.lo), f(wl.hi), float(wl.c_lim), x.shape[1], f(x),
+                                       float(wl.lr), int(iterations), ctypes.byref(jid)), "pds_server_submit")
+        self._shapes[jid.value] = (x.shape[0], x.shape[1])
+        return jid.value
+
+    def tick(self):
+        a, r = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pds_server_tick(self._h, ctypes.byref(a), ctypes.byref(r)), "pds_server_tick")
+        return a.value, r.value
+
+    def status(self, job_id):
+        st, it = ctypes.c_int(), ctypes.c_int()
+        _check(lib().pds_server_status(self._h, ctypes.c_longlong(job_id), ctypes.byref(st), ctypes.byref(it)),
+               "pds_server_status")
+        return st.value, it.value
+
+    def result(self, job_id):
+        """(particles [N][P], logp [N]) of a finished job; forgets the job."""
+        P, N = self._shapes.pop(job_id)
+        x = np.empty((P, N), np.float32)
+        lp = np.empty(N, np.float32)
+        _check(lib().pds_server_result(self._h, ctypes.c_longlong(job_id), x.ctypes.data_as(_fp),
+                                       lp.ctypes.data_as(_fp)), "pds_server_result")
+        return x.T.copy(), lp
+
+    def cancel(self, job_id):
+        _check(lib().pds_server_cancel(self._h, ctypes.c_longlong(job_id)), "pds_server_cancel")
+        self._shapes.pop(job_id, None)
+
+    def stats(self):
+        q, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(lib().pds_server_stats(self._h, ctypes.byref(q), ctypes.byref(a), ctypes.byref(b)),
+               "pds_server_stats")
+        return q.value, a.value, b.value
 
 
 class LogLik(torch.autograd.Function):

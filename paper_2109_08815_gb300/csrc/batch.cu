@@ -1,0 +1,402 @@
+// Batched execution of many inference problems: one persistent rollout
+// launch per chain length over all problems' (particle, window) units, then
+// each problem's window reduction and SVGD update on parallel graph
+// branches; the whole iteration is captured once in a CUDA graph and
+// replayed.  An autotuner picks, per chain length, the adjoint checkpoint
+// stride, the math variant and the persistent grid size by timing the
+// batched rollout itself.
+#include <cuda_runtime.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pds_internal.cuh"
+
+namespace pds {
+
+cudaError_t launch_batch_rollout(int NL, const BatchJob* jobs, const WorkItem* items, int n_items,
+                                 unsigned int* counter, int grad, int fast, int blocks, cudaStream_t st) {
+  switch (NL) {
+    case 1: return launch_batch_rollout_nl<1>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 2: return launch_batch_rollout_nl<2>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 3: return launch_batch_rollout_nl<3>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 4: return launch_batch_rollout_nl<4>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 5: return launch_batch_rollout_nl<5>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 6: return launch_batch_rollout_nl<6>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 7: return launch_batch_rollout_nl<7>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 8: return launch_batch_rollout_nl<8>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+static int blocks_per_sm(int NL, int fast) {
+  switch (NL) {
+    case 1: return batch_rollout_blocks_per_sm_nl<1>(fast);
+    case 2: return batch_rollout_blocks_per_sm_nl<2>(fast);
+    case 3: return batch_rollout_blocks_per_sm_nl<3>(fast);
+    case 4: return batch_rollout_blocks_per_sm_nl<4>(fast);
+    case 5: return batch_rollout_blocks_per_sm_nl<5>(fast);
+    case 6: return batch_rollout_blocks_per_sm_nl<6>(fast);
+    case 7: return batch_rollout_blocks_per_sm_nl<7>(fast);
+    case 8: return batch_rollout_blocks_per_sm_nl<8>(fast);
+    default: return 1;
+  }
+}
+
+// All problems of one chain length.
+struct Group {
+  int NL = 0;
+  std::vector<int> jobs;          // indices into the batch
+  int K = 10, fast = 0, blocks = 0;
+  BatchJob* d_jobs = nullptr;
+  WorkItem* d_items = nullptr;
+  int n_items = 0;
+  unsigned int* d_counter = nullptr;
+};
+
+}  // namespace pds
+
+using namespace pds;
+
+struct pds_batch {
+  std::vector<pds_problem*> probs;
+  std::vector<pds_svgd*> svgds;
+  std::vector<float*> X;
+  std::vector<float*> logp;       // caller's per-problem log p outputs (may be NULL)
+  std::vector<Group> groups;
+  cudaStream_t stream = nullptr;  // the batch's own stream (captured into the graph)
+  cudaStream_t user = nullptr;    // the caller's stream; joined through events
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;    // [0] fork, [1..] joins
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  bool dirty = true;              // tables or settings changed since the graph was captured
+  bool eager_done = false;        // the first iteration after a rebuild runs without a graph
+  int sm_count = 0;
+  int launches_per_iter = 0;
+};
+
+static constexpr int kSideStreams = 8;
+
+static void free_group(Group& g) {
+  cudaFree(g.d_jobs);
+  cudaFree(g.d_items);
+  cudaFree(g.d_counter);
+  g.d_jobs = nullptr;
+  g.d_items = nullptr;
+  g.d_counter = nullptr;
+}
+
+static void drop_graph(pds_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// (Re)build a group's device job table and cost-ordered work list.
+static int build_group(pds_batch* b, Group& g) {
+  free_group(g);
+  std::vector<BatchJob> jobs;
+  struct Item { WorkItem w; int cost; };
+  std::vector<Item> items;
+  for (size_t a = 0; a < g.jobs.size(); ++a) {
+    pds_problem* p = b->probs[g.jobs[a]];
+    p->c.K = g.K;
+    p->c.fast_math = g.fast;
+    // checkpoint slots depend on K
+    int hmax = 0;
+    for (int w = 0; w < p->c.W; ++w) {
+      const int h = (int)(((long long)(w + 1) * p->c.T) / p->c.W - ((long long)w * p->c.T) / p->c.W);
+      hmax = std::max(hmax, h);
+    }
+    p->c.max_seg = (hmax + p->c.K - 1) / p->c.K;
+    const int N = b->svgds[g.jobs[a]]->sp.N;
+    int rc = ensure_workspace(p, N);
+    if (rc != PDS_OK) return rc;
+    rc = ensure_iter_buffers(p, N);
+    if (rc != PDS_OK) return rc;
+    BatchJob bj;
+    memset(&bj, 0, sizeof(bj));
+    bj.c = p->c;
+    bj.X = b->X[g.jobs[a]];
+    bj.N = N;
+    bj.parts = p->parts;
+    bj.status = nullptr;
+    jobs.push_back(bj);
+    const long long U = (long long)N * p->c.W;
+    for (long long u0 = 0; u0 < U; u0 += 128) {
+      const long long u1 = std::min(U, u0 + 128) - 1;
+      int cost = 0;
+      for (long long w = u0 / N; w <= u1 / N; ++w) {
+        const int h = (int)(((w + 1) * p->c.T) / p->c.W - (w * p->c.T) / p->c.W);
+        cost = std::max(cost, h);
+      }
+      items.push_back({{(int)a, (int)u0}, cost});
+    }
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item& x, const Item& y) { return x.cost > y.cost; });
+  std::vector<WorkItem> w(items.size());
+  for (size_t k = 0; k < items.size(); ++k) w[k] = items[k].w;
+  g.n_items = (int)w.size();
+  cudaError_t e;
+  if ((e = cudaMalloc(&g.d_jobs, jobs.size() * sizeof(BatchJob))) != cudaSuccess ||
+      (e = cudaMalloc(&g.d_items, std::max<size_t>(1, w.size()) * sizeof(WorkItem))) != cudaSuccess ||
+      (e = cudaMalloc(&g.d_counter, sizeof(unsigned int))) != cudaSuccess) {
+    free_group(g);
+    return set_error(PDS_ERR_OOM, "batch table allocation failed");
+  }
+  if ((e = cudaMemcpy(g.d_jobs, jobs.data(), jobs.size() * sizeof(BatchJob), cudaMemcpyHostToDevice)) !=
+          cudaSuccess ||
+      (w.size() && (e = cudaMemcpy(g.d_items, w.data(), w.size() * sizeof(WorkItem), cudaMemcpyHostToDevice)) !=
+                       cudaSuccess))
+    return set_error(PDS_ERR_CUDA, "batch table upload failed");
+  if (g.blocks <= 0) g.blocks = b->sm_count * std::max(1, blocks_per_sm(g.NL, g.fast));
+  return PDS_OK;
+}
+
+static cudaError_t launch_group_rollout(Group& g, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  return launch_batch_rollout(g.NL, g.d_jobs, g.d_items, g.n_items, g.d_counter, 1, g.fast, g.blocks, st);
+}
+
+// One iteration of every problem, queued on b->stream with per-problem
+// branches on the side streams.
+static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
+  int n = 0;
+  cudaError_t e;
+  for (Group& g : b->groups) {
+    if ((e = launch_group_rollout(g, b->stream)) != cudaSuccess) return e;
+    ++n;
+  }
+  if ((e = cudaEventRecord(b->ev[0], b->stream)) != cudaSuccess) return e;
+  for (int s = 0; s < kSideStreams; ++s)
+    if ((e = cudaStreamWaitEvent(b->side[s], b->ev[0], 0)) != cudaSuccess) return e;
+  for (size_t j = 0; j < b->probs.size(); ++j) {
+    pds_problem* p = b->probs[j];
+    pds_svgd* s = b->svgds[j];
+    cudaStream_t st = b->side[j % kSideStreams];
+    const int N = s->sp.N;
+    float* lp = b->logp[j] ? b->logp[j] : p->d_logp;
+    if ((e = launch_window_reduce(p->c, b->X[j], N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess)
+      return e;
+    SvgdWork w = s->w;
+    if (s->full_passes) w.cand_cap = 0;
+    int k = 0;
+    if ((e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k)) != cudaSuccess) return e;
+    n += 1 + k;
+  }
+  for (int s = 0; s < kSideStreams; ++s) {
+    if ((e = cudaEventRecord(b->ev[1 + s], b->side[s])) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(b->stream, b->ev[1 + s], 0)) != cudaSuccess) return e;
+  }
+  if (launches) *launches = n;
+  return cudaSuccess;
+}
+
+// Rebuild the job tables if anything changed (drops the captured graph).
+static int rebuild(pds_batch* b) {
+  if (!b->dirty) return PDS_OK;
+  drop_graph(b);
+  for (Group& g : b->groups) {
+    int rc = build_group(b, g);
+    if (rc != PDS_OK) return rc;
+  }
+  b->dirty = false;
+  b->eager_done = false;
+  return PDS_OK;
+}
+
+static int capture(pds_batch* b) {
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "batch: begin capture failed");
+  int n = 0;
+  cudaError_t el = enqueue_iteration(b, &n);
+  e = cudaStreamEndCapture(b->stream, &b->graph);
+  if (el != cudaSuccess || e != cudaSuccess) {
+    drop_graph(b);
+    return set_error(PDS_ERR_CUDA, "batch: capture of the iteration failed");
+  }
+  e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+  if (e != cudaSuccess) {
+    drop_graph(b);
+    return set_error(PDS_ERR_CUDA, "batch: graph instantiation failed");
+  }
+  b->launches_per_iter = n;
+  return PDS_OK;
+}
+
+extern "C" {
+
+int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const* svgds, float* const* particles,
+                     float* const* logp, void* cuda_stream, pds_batch_t* out) {
+  if (!out) return set_error(PDS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_jobs < 1 || !problems || !svgds || !particles) return set_error(PDS_ERR_ARG, "bad batch arguments");
+  pds_batch* b = new pds_batch();
+  b->user = (cudaStream_t)cuda_stream;
+  // a stream of its own: the caller's may be the legacy default stream,
+  // which cannot be captured
+  if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return set_error(PDS_ERR_CUDA, "batch: stream creation failed");
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  for (int j = 0; j < n_jobs; ++j) {
+    pds_problem* p = problems[j];
+    pds_svgd* s = svgds[j];
+    if (!p || !s || !particles[j]) {
+      delete b;
+      return set_error(PDS_ERR_ARG, "NULL problem, SVGD state or particle buffer in the batch");
+    }
+    if (s->sp.M != p->c.M || s->sp.P != p->c.P) {
+      delete b;
+      return set_error(PDS_ERR_ARG, "SVGD state does not match its problem");
+    }
+    b->probs.push_back(p);
+    b->svgds.push_back(s);
+    b->X.push_back(particles[j]);
+    b->logp.push_back(logp ? logp[j] : nullptr);
+  }
+  for (int nl = 1; nl <= PDS_MAX_LINKS; ++nl) {
+    Group g;
+    g.NL = nl;
+    for (int j = 0; j < n_jobs; ++j)
+      if (b->probs[j]->c.n == nl) g.jobs.push_back(j);
+    if (!g.jobs.empty()) {
+      g.K = b->probs[g.jobs[0]]->c.K;
+      g.fast = b->probs[g.jobs[0]]->c.fast_math;
+      b->groups.push_back(g);
+    }
+  }
+  b->side.resize(kSideStreams);
+  b->ev.resize(1 + kSideStreams);
+  for (int s = 0; s < kSideStreams; ++s) cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking);
+  for (auto& e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  *out = b;
+  return PDS_OK;
+}
+
+int pds_batch_destroy(pds_batch_t b) {
+  if (!b) return PDS_OK;
+  cudaStreamSynchronize(b->stream);
+  drop_graph(b);
+  for (Group& g : b->groups) free_group(g);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->ev) cudaEventDestroy(e);
+  cudaEventDestroy(b->ev_in);
+  cudaEventDestroy(b->ev_out);
+  cudaStreamDestroy(b->stream);
+  delete b;
+  return PDS_OK;
+}
+
+int pds_batch_autotune(pds_batch_t b, int allow_fast_math, int* choices) {
+  if (!b) return set_error(PDS_ERR_ARG, "NULL batch");
+  cudaStreamSynchronize(b->user);
+  cudaEvent_t t0, t1;
+  cudaEventCreate(&t0);
+  cudaEventCreate(&t1);
+  const int Ks[] = {5, 10, 25, 50};
+  int gi = 0;
+  for (Group& g : b->groups) {
+    int best_K = g.K, best_fast = g.fast, best_blocks = 0;
+    float best = 1e30f;
+    for (int fast = 0; fast <= (allow_fast_math ? 1 : 0); ++fast) {
+      const int occ = std::max(1, blocks_per_sm(g.NL, fast));
+      for (int K : Ks) {
+        for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
+          g.K = K;
+          g.fast = fast;
+          g.blocks = b->sm_count * per_sm;
+          int rc = build_group(b, g);
+          if (rc != PDS_OK) return rc;
+          float ms = 0.f, tot = 0.f;
+          for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(t0, b->stream);
+            if (launch_group_rollout(g, b->stream) != cudaSuccess)
+              return set_error(PDS_ERR_CUDA, "autotune launch failed");
+            cudaEventRecord(t1, b->stream);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (r > 0) tot += ms;  // the first run warms up
+          }
+          if (tot < best) {
+            best = tot;
+            best_K = K;
+            best_fast = fast;
+            best_blocks = g.blocks;
+          }
+        }
+      }
+    }
+    g.K = best_K;
+    g.fast = best_fast;
+    g.blocks = best_blocks;
+    if (choices) {
+      choices[4 * gi + 0] = g.NL;
+      choices[4 * gi + 1] = g.K;
+      choices[4 * gi + 2] = g.fast;
+      choices[4 * gi + 3] = g.blocks;
+    }
+    ++gi;
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  b->dirty = true;
+  return PDS_OK;
+}
+
+int pds_batch_iterate(pds_batch_t b, int iters) {
+  if (!b) return set_error(PDS_ERR_ARG, "NULL batch");
+  if (iters < 0) return set_error(PDS_ERR_ARG, "iters < 0");
+  int rc = rebuild(b);
+  if (rc != PDS_OK) return rc;
+  cudaError_t e = svgd_setup_device();
+  if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "batch: device set-up failed");
+  // order after the caller's earlier work, and the caller's later work after ours
+  if ((e = cudaEventRecord(b->ev_in, b->user)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(b->stream, b->ev_in, 0)) != cudaSuccess)
+    return set_error(PDS_ERR_CUDA, "batch: stream join failed");
+  int launches = 0;
+  for (int it = 0; it < iters; ++it) {
+    if (!b->exec && !b->eager_done) {
+      // first iteration after a (re)build: plain launches, no capture cost
+      int n = 0;
+      if ((e = enqueue_iteration(b, &n)) != cudaSuccess) return set_error(PDS_ERR_CUDA, "batch: launch failed");
+      b->launches_per_iter = n;
+      b->eager_done = true;
+      launches += n;
+      continue;
+    }
+    if (!b->exec) {
+      rc = capture(b);
+      if (rc != PDS_OK) return rc;
+    }
+    if ((e = cudaGraphLaunch(b->exec, b->stream)) != cudaSuccess)
+      return set_error(PDS_ERR_CUDA, "batch: graph launch failed");
+    launches += b->launches_per_iter;
+  }
+  if ((e = cudaEventRecord(b->ev_out, b->stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(b->user, b->ev_out, 0)) != cudaSuccess)
+    return set_error(PDS_ERR_CUDA, "batch: stream join failed");
+  set_launch_count(launches);
+  return PDS_OK;
+}
+
+int pds_batch_info(pds_batch_t b, int* n_groups, int* launches_per_iter) {
+  if (!b) return set_error(PDS_ERR_ARG, "NULL batch");
+  if (n_groups) *n_groups = (int)b->groups.size();
+  if (launches_per_iter) *launches_per_iter = b->launches_per_iter;
+  return PDS_OK;
+}
+
+}  // extern "C"

@@ -36,6 +36,8 @@ int set_error(int code, const char* msg) {
   return code;
 }
 
+void set_launch_count(int n) { g_launches = n; }
+
 static int cuda_fail(cudaError_t e, const char* what) {
   return fail(e == cudaErrorMemoryAllocation ? PDS_ERR_OOM : PDS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -73,27 +75,6 @@ cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, flo
 
 using namespace pds;
 
-struct pds_problem {
-  ChainParams c;
-  cudaStream_t stream;
-  float* d_obs = nullptr;
-  int cap_N = 0;          // workspace capacity in particles
-  int cap_K = 0;          // checkpoint stride the tape was sized for
-  Partials parts{};
-  // buffers used by pds_iterate / pds_iterate_host
-  int it_N = 0;
-  float* d_grad = nullptr;
-  float* d_logp = nullptr;
-  float* d_x = nullptr;
-};
-
-struct pds_svgd {
-  SvgdParams sp;
-  SvgdWork w{};
-  cudaStream_t stream;
-  int full_passes = 0;
-};
-
 static void free_parts(Partials& p) {
   cudaFree(p.lp);
   cudaFree(p.th);
@@ -103,7 +84,7 @@ static void free_parts(Partials& p) {
   p = Partials{};
 }
 
-static int ensure_workspace(pds_problem* p, int N) {
+int pds::ensure_workspace(pds_problem* p, int N) {
   if (N <= p->cap_N && p->cap_K == p->c.K) return PDS_OK;
   const int newN = N > p->cap_N ? N : p->cap_N;
   cudaError_t e = cudaStreamSynchronize(p->stream);
@@ -136,6 +117,23 @@ static void update_segments(ChainParams& c) {
   c.max_seg = (hmax + c.K - 1) / c.K;
 }
 
+int pds::ensure_iter_buffers(pds_problem* p, int N) {
+  if (p->it_N >= N) return PDS_OK;
+  cudaStreamSynchronize(p->stream);
+  cudaFree(p->d_grad);
+  cudaFree(p->d_logp);
+  cudaFree(p->d_x);
+  p->d_grad = p->d_logp = p->d_x = nullptr;
+  p->it_N = 0;
+  cudaError_t e;
+  if ((e = cudaMalloc(&p->d_grad, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_logp, (size_t)N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&p->d_x, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess)
+    return cuda_fail(e, "iteration buffers");
+  p->it_N = N;
+  return PDS_OK;
+}
+
 extern "C" {
 
 const char* pds_strerror(int code) {
@@ -145,6 +143,7 @@ const char* pds_strerror(int code) {
     case PDS_ERR_CUDA: return "CUDA error";
     case PDS_ERR_OOM: return "out of device memory";
     case PDS_ERR_NONFINITE: return "non-finite value";
+    case PDS_ERR_BUDGET: return "over the memory budget";
     case PDS_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown status";
   }
@@ -398,23 +397,6 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   cudaError_t e = launch_svgd_step(s->sp, w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
   g_launches = n;
   if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
-  return PDS_OK;
-}
-
-static int ensure_iter_buffers(pds_problem* p, int N) {
-  if (p->it_N >= N) return PDS_OK;
-  cudaStreamSynchronize(p->stream);
-  cudaFree(p->d_grad);
-  cudaFree(p->d_logp);
-  cudaFree(p->d_x);
-  p->d_grad = p->d_logp = p->d_x = nullptr;
-  p->it_N = 0;
-  cudaError_t e;
-  if ((e = cudaMalloc(&p->d_grad, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_logp, (size_t)N * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&p->d_x, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess)
-    return cuda_fail(e, "iteration buffers");
-  p->it_N = N;
   return PDS_OK;
 }
 

@@ -44,6 +44,22 @@ struct Partials {
   float* tape;    // checkpoints [max_seg][S][U] then segment states [K][S][U]
 };
 
+// One problem of a batched launch (device-side job table entry).
+struct BatchJob {
+  ChainParams c;
+  const float* X;    // particles [P][N]
+  int N;
+  int pad_;
+  Partials parts;
+  int32_t* status;   // [N] or NULL
+};
+
+// 128 consecutive units of one problem.
+struct WorkItem {
+  int job;
+  int unit0;
+};
+
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
                            int32_t* status, cudaStream_t st);
@@ -93,8 +109,41 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
 int svgd_phi_chunks(int N);
 unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
 int svgd_sample_size();
+cudaError_t svgd_setup_device();
 
 // Record an error message for pds_last_error() and return `code`.
 int set_error(int code, const char* msg);
+void set_launch_count(int n);
 
+}  // namespace pds
+
+// Objects behind the opaque handles of pds.h.
+struct pds_problem {
+  pds::ChainParams c;
+  cudaStream_t stream;
+  float* d_obs = nullptr;
+  int cap_N = 0;          // workspace capacity in particles
+  int cap_K = 0;          // checkpoint stride the tape was sized for
+  pds::Partials parts{};
+  // buffers used by pds_iterate / pds_iterate_host / batches
+  int it_N = 0;
+  float* d_grad = nullptr;
+  float* d_logp = nullptr;
+  float* d_x = nullptr;
+};
+
+struct pds_svgd {
+  pds::SvgdParams sp;
+  pds::SvgdWork w{};
+  cudaStream_t stream;
+  int full_passes = 0;
+};
+
+namespace pds {
+int ensure_workspace(pds_problem* p, int N);
+int ensure_iter_buffers(pds_problem* p, int N);
+template <int NL>
+cudaError_t launch_batch_rollout_nl(const BatchJob*, const WorkItem*, int, unsigned int*, int, int, int, cudaStream_t);
+template <int NL>
+int batch_rollout_blocks_per_sm_nl(int fast);
 }  // namespace pds

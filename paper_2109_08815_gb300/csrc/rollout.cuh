@@ -333,11 +333,10 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
 // forward rollout with its observation and defect terms (Eqs. 2, 4, 5), then
 // (grad != 0) the reverse sweep from checkpoints every K steps.
 template <int NL, bool FAST>
-__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const ChainParams c, const float* __restrict__ X, int N,
-                                                      Partials parts, int grad, int32_t* __restrict__ status) {
+__device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
+                                             const Partials& parts, int grad, int32_t* __restrict__ status,
+                                             size_t u) {
   const size_t U = (size_t)N * c.W;
-  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= U) return;
   const int w = (int)(u / N);
   const int i = (int)(u - (size_t)w * N);
   // the window-reduction kernel (next on the stream) ORs in non-finite flags
@@ -443,6 +442,70 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const Ch
     nx[(size_t)j * N] = nb[j];
     nx[(size_t)(NL + j) * N] = nb[NL + j];
   }
+}
+
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const ChainParams c, const float* __restrict__ X,
+                                                                        int N, Partials parts, int grad,
+                                                                        int32_t* __restrict__ status) {
+  const size_t U = (size_t)N * c.W;
+  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= U) return;
+  rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u);
+}
+
+// Persistent rollout over several problems with the same chain length
+// (batched execution): blocks take work items -- 128 consecutive units of
+// one problem -- from a list sorted by decreasing cost (longest windows
+// first), through an atomic counter, so problems of uneven size and window
+// length share the launch and balance across SMs.  The problem's parameters
+// are staged in shared memory for the item.
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) batch_rollout_kernel(const BatchJob* __restrict__ jobs,
+                                                                              const WorkItem* __restrict__ items,
+                                                                              int n_items,
+                                                                              unsigned int* __restrict__ counter,
+                                                                              int grad) {
+  __shared__ ChainParams cs;
+  __shared__ int item;
+  constexpr int kWords = sizeof(ChainParams) / sizeof(int);
+  static_assert(sizeof(ChainParams) % sizeof(int) == 0, "ChainParams must be word sized");
+  for (;;) {
+    if (threadIdx.x == 0) item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item;
+    if (it >= n_items) break;
+    const WorkItem wi = items[it];
+    const BatchJob* job = jobs + wi.job;
+    const int* src = reinterpret_cast<const int*>(&job->c);
+    int* dst = reinterpret_cast<int*>(&cs);
+    for (int k = threadIdx.x; k < kWords; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    const size_t u = (size_t)wi.unit0 + threadIdx.x;
+    const int N = job->N;
+    if (u < (size_t)N * cs.W) rollout_unit<NL, FAST>(cs, job->X, N, job->parts, grad, job->status, u);
+    __syncthreads();
+  }
+}
+
+template <int NL>
+int batch_rollout_blocks_per_sm_nl(int fast) {
+  int nb = 0;
+  if (fast)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_kernel<NL, true>, 128, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_kernel<NL, false>, 128, 0);
+  return nb;
+}
+
+template <int NL>
+cudaError_t launch_batch_rollout_nl(const BatchJob* jobs, const WorkItem* items, int n_items, unsigned int* counter,
+                                    int grad, int fast, int blocks, cudaStream_t st) {
+  if (fast)
+    batch_rollout_kernel<NL, true><<<blocks, 128, 0, st>>>(jobs, items, n_items, counter, grad);
+  else
+    batch_rollout_kernel<NL, false><<<blocks, 128, 0, st>>>(jobs, items, n_items, counter, grad);
+  return cudaGetLastError();
 }
 
 // f_sim for N parameter vectors from s0: states [T+1][S][N].

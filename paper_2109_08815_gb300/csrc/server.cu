@@ -1,0 +1,317 @@
+// Serving loop with continuous batching.
+//
+// Jobs (a problem, its initial particles and an iteration count) are
+// submitted to a FIFO queue.  Every tick admits queued jobs while their
+// estimated device memory fits the budget (and the active-job limit), runs
+// one SVGD iteration of every active job in one batched launch (pds_batch,
+// rebuilt when the active set changes), and retires the jobs that reached
+// their iteration count: their particles and last log p are copied to the
+// host and their device memory is released, so waiting jobs can enter on the
+// next tick.  Every job's state stays resident on the device between ticks.
+#include <cuda_runtime.h>
+#include <string.h>
+
+#include <deque>
+#include <map>
+#include <vector>
+
+#include "pds_internal.cuh"
+
+using namespace pds;
+
+namespace {
+
+struct Job {
+  long long id = 0;
+  int state = 0;  // PDS_JOB_*
+  // creation arguments (host copies)
+  pds_system_desc sys{};
+  std::vector<double> mass, length, damping;
+  std::vector<int> theta_kind, theta_link, obs_index;
+  std::vector<float> obs, s0, lo, hi, x0;
+  double dt = 0, sigma_obs = 0, sigma_def = 0, c_lim = 0, lr = 0;
+  int T = 0, W = 0, D = 0, N = 0, P = 0, iterations = 0, done_iters = 0;
+  size_t bytes = 0;
+  // device state while active
+  pds_problem_t prob = nullptr;
+  pds_svgd_t svgd = nullptr;
+  float* d_x = nullptr;
+  float* d_logp = nullptr;
+  // results
+  std::vector<float> x_out, logp_out;
+};
+
+}  // namespace
+
+struct pds_server {
+  size_t budget = 0, in_use = 0;
+  int max_active = 0;
+  int K = 5, fast = 1;
+  cudaStream_t stream = nullptr;
+  long long next_id = 1;
+  std::deque<long long> queue;
+  std::vector<long long> active;
+  std::map<long long, Job> jobs;
+  pds_batch_t batch = nullptr;
+  bool batch_dirty = true;
+};
+
+// Device bytes a job holds while active (problem workspace and buffers,
+// SVGD state, particles).
+static size_t job_bytes(int n, int M, int T, int W, int D, int N, int K) {
+  const size_t S = 2 * (size_t)n, P = (size_t)M + (size_t)(W - 1) * S, U = (size_t)N * W;
+  int hmax = 0;
+  for (int w = 0; w < W; ++w) {
+    const int h = (int)(((long long)(w + 1) * T) / W - ((long long)w * T) / W);
+    if (h > hmax) hmax = h;
+  }
+  const size_t segs = (size_t)((hmax + K - 1) / K);
+  size_t b = 0;
+  b += (size_t)T * D * 4;                                   // observations
+  b += (size_t)W * (1 + M + 2 * S) * N * 4;                 // per-window partials
+  b += (segs + (size_t)K) * S * U * 4;                      // adjoint tape
+  b += (2 * P * N + N) * 4;                                 // iteration buffers (grad, x, logp)
+  b += (size_t)svgd_phi_chunks(N) * M * N * 4 + 2 * (size_t)M * N * 4 + 2 * P * N * 4;  // SVGD state
+  b += svgd_cand_capacity(N) * 4 + (svgd_cand_capacity(N) ? (size_t)svgd_sample_size() * 4 : 0);
+  b += P * N * 4 + (size_t)N * 4;                           // particles, log p
+  return b + (64u << 10);
+}
+
+static void release(Job& j) {
+  if (j.prob) pds_problem_destroy(j.prob);
+  if (j.svgd) pds_svgd_destroy(j.svgd);
+  cudaFree(j.d_x);
+  cudaFree(j.d_logp);
+  j.prob = nullptr;
+  j.svgd = nullptr;
+  j.d_x = nullptr;
+  j.d_logp = nullptr;
+}
+
+static int activate(pds_server* s, Job& j) {
+  pds_system_desc sys = j.sys;
+  sys.mass = j.mass.data();
+  sys.length = j.length.data();
+  sys.damping = j.damping.data();
+  sys.theta_kind = j.theta_kind.data();
+  sys.theta_link = j.theta_link.data();
+  int rc = pds_problem_create(&sys, j.dt, j.T, j.W, j.obs.data(), j.D, j.obs_index.data(), j.sigma_obs, j.sigma_def,
+                              j.s0.data(), j.lo.data(), j.hi.data(), j.c_lim, s->stream, &j.prob);
+  if (rc != PDS_OK) return rc;
+  pds_problem_set_option(j.prob, PDS_OPT_CHECKPOINT_STRIDE, s->K);
+  pds_problem_set_option(j.prob, PDS_OPT_FAST_MATH, s->fast);
+  rc = pds_svgd_create(j.N, sys.n_theta, j.P, j.lo.data(), j.hi.data(), j.lr, 0.9, 0.999, 1e-8, 1, s->stream,
+                       &j.svgd);
+  if (rc != PDS_OK) { release(j); return rc; }
+  cudaError_t e;
+  if ((e = cudaMalloc(&j.d_x, (size_t)j.P * j.N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&j.d_logp, (size_t)j.N * sizeof(float))) != cudaSuccess) {
+    release(j);
+    return set_error(PDS_ERR_OOM, "server: particle allocation failed");
+  }
+  e = cudaMemcpyAsync(j.d_x, j.x0.data(), (size_t)j.P * j.N * sizeof(float), cudaMemcpyHostToDevice, s->stream);
+  if (e != cudaSuccess) { release(j); return set_error(PDS_ERR_CUDA, "server: particle upload failed"); }
+  rc = pds_problem_reserve(j.prob, j.N);
+  if (rc != PDS_OK) { release(j); return rc; }
+  j.x0.clear();
+  j.x0.shrink_to_fit();
+  return PDS_OK;
+}
+
+extern "C" {
+
+int pds_server_create(size_t mem_budget_bytes, int max_active, void* cuda_stream, pds_server_t* out) {
+  if (!out) return set_error(PDS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (mem_budget_bytes == 0 || max_active < 1) return set_error(PDS_ERR_ARG, "bad server budget or limit");
+  pds_server* s = new pds_server();
+  s->budget = mem_budget_bytes;
+  s->max_active = max_active;
+  s->stream = (cudaStream_t)cuda_stream;
+  *out = s;
+  return PDS_OK;
+}
+
+int pds_server_set_rollout_options(pds_server_t s, int checkpoint_stride, int fast_math) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  if (checkpoint_stride < 1 || checkpoint_stride > PDS_MAX_WINDOW_STEPS || (fast_math != 0 && fast_math != 1))
+    return set_error(PDS_ERR_ARG, "bad rollout options");
+  s->K = checkpoint_stride;
+  s->fast = fast_math;
+  return PDS_OK;
+}
+
+int pds_server_destroy(pds_server_t s) {
+  if (!s) return PDS_OK;
+  cudaStreamSynchronize(s->stream);
+  if (s->batch) pds_batch_destroy(s->batch);
+  for (auto& kv : s->jobs) release(kv.second);
+  delete s;
+  return PDS_OK;
+}
+
+int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int T, int windows, const float* obs,
+                      int D, const int* obs_index, double sigma_obs, double sigma_def, const float* s0,
+                      const float* theta_lo, const float* theta_hi, double c_lim, int N, const float* particles,
+                      double lr, int iterations, long long* job_id) {
+  if (!s || !sys || !obs || !obs_index || !s0 || !theta_lo || !theta_hi || !particles || !job_id)
+    return set_error(PDS_ERR_ARG, "NULL argument");
+  *job_id = 0;
+  const int n = sys->n_links, M = sys->n_theta;
+  if (n < 1 || n > PDS_MAX_LINKS || M < 1 || M > PDS_MAX_THETA || T < 1 || windows < 1 || windows > T || D < 1 ||
+      D > 2 * n || N < 1 || N > 65536 || iterations < 1 || !(lr > 0.0))
+    return set_error(PDS_ERR_ARG, "job outside the supported sizes");
+  const size_t bytes = job_bytes(n, M, T, windows, D, N, s->K);
+  if (bytes > s->budget) return set_error(PDS_ERR_BUDGET, "job needs more device memory than the server budget");
+  Job j;
+  j.id = s->next_id++;
+  j.sys = *sys;
+  j.mass.assign(sys->mass, sys->mass + n);
+  j.length.assign(sys->length, sys->length + n);
+  j.damping.assign(sys->damping, sys->damping + n);
+  j.theta_kind.assign(sys->theta_kind, sys->theta_kind + M);
+  j.theta_link.assign(sys->theta_link, sys->theta_link + M);
+  j.obs_index.assign(obs_index, obs_index + D);
+  j.obs.assign(obs, obs + (size_t)T * D);
+  j.s0.assign(s0, s0 + 2 * n);
+  j.lo.assign(theta_lo, theta_lo + M);
+  j.hi.assign(theta_hi, theta_hi + M);
+  j.dt = dt; j.T = T; j.W = windows; j.D = D; j.N = N; j.P = M + (windows - 1) * 2 * n;
+  j.sigma_obs = sigma_obs; j.sigma_def = sigma_def; j.c_lim = c_lim; j.lr = lr; j.iterations = iterations;
+  j.x0.assign(particles, particles + (size_t)j.P * N);
+  j.bytes = bytes;
+  j.state = PDS_JOB_QUEUED;
+  *job_id = j.id;
+  s->queue.push_back(j.id);
+  s->jobs.emplace(j.id, std::move(j));
+  return PDS_OK;
+}
+
+int pds_server_tick(pds_server_t s, int* n_active, int* n_retired) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  int retired = 0;
+  // admission, first in first out
+  while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+    Job& j = s->jobs[s->queue.front()];
+    if (s->in_use + j.bytes > s->budget) break;
+    int rc = activate(s, j);
+    if (rc != PDS_OK) return rc;
+    s->in_use += j.bytes;
+    j.state = PDS_JOB_ACTIVE;
+    s->active.push_back(j.id);
+    s->queue.pop_front();
+    s->batch_dirty = true;
+  }
+  if (!s->active.empty()) {
+    if (s->batch_dirty) {
+      if (s->batch) pds_batch_destroy(s->batch);
+      s->batch = nullptr;
+      std::vector<pds_problem_t> probs;
+      std::vector<pds_svgd_t> svgds;
+      std::vector<float*> xs, lps;
+      for (long long id : s->active) {
+        Job& j = s->jobs[id];
+        probs.push_back(j.prob);
+        svgds.push_back(j.svgd);
+        xs.push_back(j.d_x);
+        lps.push_back(j.d_logp);
+      }
+      int rc = pds_batch_create((int)probs.size(), probs.data(), svgds.data(), xs.data(), lps.data(), s->stream,
+                                &s->batch);
+      if (rc != PDS_OK) return rc;
+      s->batch_dirty = false;
+    }
+    int rc = pds_batch_iterate(s->batch, 1);
+    if (rc != PDS_OK) return rc;
+    std::vector<long long> still;
+    std::vector<long long> finishing;
+    for (long long id : s->active) {
+      Job& j = s->jobs[id];
+      if (++j.done_iters >= j.iterations) finishing.push_back(id);
+      else still.push_back(id);
+    }
+    for (long long id : finishing) {
+      Job& j = s->jobs[id];
+      j.x_out.resize((size_t)j.P * j.N);
+      j.logp_out.resize(j.N);
+      cudaMemcpyAsync(j.x_out.data(), j.d_x, j.x_out.size() * sizeof(float), cudaMemcpyDeviceToHost, s->stream);
+      cudaMemcpyAsync(j.logp_out.data(), j.d_logp, j.logp_out.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                      s->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "server: tick failed");
+    if (!finishing.empty()) {
+      for (long long id : finishing) {
+        Job& j = s->jobs[id];
+        release(j);
+        s->in_use -= j.bytes;
+        j.state = PDS_JOB_DONE;
+        ++retired;
+      }
+      s->active = still;
+      s->batch_dirty = true;
+      if (s->batch) pds_batch_destroy(s->batch);
+      s->batch = nullptr;
+    }
+  }
+  if (n_active) *n_active = (int)s->active.size();
+  if (n_retired) *n_retired = retired;
+  return PDS_OK;
+}
+
+int pds_server_status(pds_server_t s, long long job_id, int* state, int* iterations_done) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return set_error(PDS_ERR_ARG, "unknown job");
+  if (state) *state = it->second.state;
+  if (iterations_done) *iterations_done = it->second.done_iters;
+  return PDS_OK;
+}
+
+int pds_server_result(pds_server_t s, long long job_id, float* particles, float* logp) {
+  if (!s || !particles) return set_error(PDS_ERR_ARG, "NULL argument");
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return set_error(PDS_ERR_ARG, "unknown job");
+  Job& j = it->second;
+  if (j.state != PDS_JOB_DONE) return set_error(PDS_ERR_ARG, "job not finished");
+  memcpy(particles, j.x_out.data(), j.x_out.size() * sizeof(float));
+  if (logp) memcpy(logp, j.logp_out.data(), j.logp_out.size() * sizeof(float));
+  s->jobs.erase(it);
+  return PDS_OK;
+}
+
+int pds_server_cancel(pds_server_t s, long long job_id) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return set_error(PDS_ERR_ARG, "unknown job");
+  Job& j = it->second;
+  if (j.state == PDS_JOB_QUEUED) {
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+      if (*q == job_id) { s->queue.erase(q); break; }
+  } else if (j.state == PDS_JOB_ACTIVE) {
+    cudaStreamSynchronize(s->stream);
+    if (s->batch) pds_batch_destroy(s->batch);
+    s->batch = nullptr;
+    s->batch_dirty = true;
+    std::vector<long long> still;
+    for (long long id : s->active)
+      if (id != job_id) still.push_back(id);
+    s->active = still;
+    release(j);
+    s->in_use -= j.bytes;
+  } else {
+    return set_error(PDS_ERR_ARG, "job already finished");
+  }
+  s->jobs.erase(it);
+  return PDS_OK;
+}
+
+int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_use) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  if (queued) *queued = (int)s->queue.size();
+  if (active) *active = (int)s->active.size();
+  if (bytes_in_use) *bytes_in_use = s->in_use;
+  return PDS_OK;
+}
+
+}  // extern "C"

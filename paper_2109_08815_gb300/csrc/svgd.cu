@@ -396,6 +396,22 @@ __global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __re
 
 int svgd_sample_size() { return kSample; }
 
+// 64 KiB of dynamic shared memory for the sample sort: opt in once per
+// device (before any stream capture that launches it).
+cudaError_t svgd_setup_device() {
+  static bool smem_ok[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < 64 && !smem_ok[dev]) {
+    e = cudaFuncSetAttribute(median_sample_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(kSample * sizeof(float)));
+    if (e != cudaSuccess) return e;
+    smem_ok[dev] = true;
+  }
+  return cudaSuccess;
+}
+
 unsigned long long svgd_cand_capacity(int N) {
   if (N < 2048) return 0ull;
   const unsigned long long pairs = (unsigned long long)N * (unsigned long long)(N - 1) / 2ull;
@@ -526,16 +542,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     const long long all_tiles = (long long)nt * nt;
     const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
     if (bracket) {
-      // 64 KiB of dynamic shared memory for the sample: opt in once per device
-      static bool smem_ok[64];
-      int dev = 0;
-      cudaGetDevice(&dev);
-      if (dev >= 0 && dev < 64 && !smem_ok[dev]) {
-        cudaError_t e = cudaFuncSetAttribute(median_sample_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(kSample * sizeof(float)));
-        if (e != cudaSuccess) return e;
-        smem_ok[dev] = true;
-      }
+      cudaError_t e = svgd_setup_device();
+      if (e != cudaSuccess) return e;
       median_sample_dist_kernel<MM><<<kSample / 256, 256, 0, st>>>(N, M, w.u, w.samp);
       median_sample_sort_kernel<<<1, kSampleThreads, kSample * sizeof(float), st>>>(w.samp, w.ctl);
       n += 1;

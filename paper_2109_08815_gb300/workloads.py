@@ -213,3 +213,52 @@ def initial_particles(wl: PlanarWorkload, obs: np.ndarray, N: int | None = None,
         rng = np.random.default_rng(rng_seed)
         x[:, wl.M:] += 0.05 * rng.standard_normal((N, wl.P - wl.M))
     return x
+
+
+def batched_problems(n_jobs: int = 64, seed: int = 4000, n_range=(2, 8), T_range=(100, 2000), W_range=(5, 50),
+                     N_range=(64, 4096)) -> list[PlanarWorkload]:
+    """Independent problems of uneven size for batched execution.
+
+    Chain length n ~ U{2..8}; T, W and N log-uniform in their ranges (W at
+    most T/2); parameter types of the double pendulum (masses + lengths,
+    dt = 0.01, angles observed, sigma 0.01) or of the damped chain (masses +
+    damping, dt = 0.005, angles and velocities observed, sigma 0.02), 50/50.
+    """
+    rng = np.random.default_rng(seed)
+
+    def logu(lo, hi):
+        return int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+
+    out = []
+    for j in range(n_jobs):
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        T = logu(*T_range)
+        W = max(1, min(logu(*W_range), T // 2))
+        N = logu(*N_range)
+        pend = bool(rng.uniform() < 0.5)
+        if pend:
+            lo = np.concatenate([np.full(n, 0.5), np.full(n, 0.5)])
+            hi = np.concatenate([np.full(n, 2.0), np.full(n, 1.5)])
+            kind = [PARAM_MASS] * n + [PARAM_LENGTH] * n
+            dt, sig = 0.01, 0.01
+            obs_index = np.arange(n, dtype=np.int32)
+        else:
+            lo = np.full(2 * n, 0.1)
+            hi = np.full(2 * n, 2.0)
+            kind = [PARAM_MASS] * n + [PARAM_DAMPING] * n
+            dt, sig = 0.005, 0.02
+            obs_index = np.arange(2 * n, dtype=np.int32)
+        theta_true = rng.uniform(lo, hi)
+        mass = theta_true[:n].copy()
+        length = theta_true[n:].copy() if pend else np.full(n, CHAIN5_LENGTH)
+        damping = np.zeros(n) if pend else theta_true[n:].copy()
+        q0 = rng.uniform(-math.pi / 2, math.pi / 2, size=n)
+        noise = rng.standard_normal((T, len(obs_index)))
+        theta_init = rng.uniform(lo, hi, size=(N, 2 * n))
+        out.append(PlanarWorkload(
+            name=f"batch{j}_{'pend' if pend else 'damped'}{n}", n=n, mass=mass, length=length, damping=damping,
+            theta_kind=np.array(kind, dtype=np.int32), theta_link=np.array(list(range(n)) * 2, dtype=np.int32),
+            theta_true=theta_true, lo=lo, hi=hi, dt=dt, T=T, W=W, obs_index=obs_index, sigma_obs=sig,
+            sigma_def=SIGMA_DEF, s0=np.concatenate([q0, np.zeros(n)]), noise=noise, theta_init=theta_init,
+            lr=1e-2, seed=seed + j))
+    return out
