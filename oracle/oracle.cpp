@@ -497,6 +497,319 @@ static void adam_ascent(double& x, double& m, double& v, double g, int t, double
   x += lr * mh / (std::sqrt(vh) + eps);
 }
 
+
+// ---------------------------------------------------------------------------
+// Arm shaking a box (Sec. V-C, Panda arm experiment, synthetic analogue).
+// A serial arm of revolute joints with prescribed motion carries, at its
+// end, a box hanging on two passive revolute joints (a U-joint: axis x, then
+// axis y, both at the same point).  The box is a solid cube plus two point
+// weights whose (x, y) positions are theta.  Only the two box joints are
+// simulated; the arm is a moving base whose velocity and acceleration follow
+// from its prescribed joint trajectories.
+// 6-D spatial algebra (Featherstone): motion (w; v), force (n; f).
+// ---------------------------------------------------------------------------
+template <class T> struct V6 { T a[6]; };
+template <class T> struct M6 { T a[6][6]; };
+template <class T> struct R3 { T a[3][3]; };
+
+template <class T> static V6<T> v6zero() { V6<T> r; for (int i = 0; i < 6; ++i) r.a[i] = T(0.0); return r; }
+template <class T> static M6<T> m6zero() { M6<T> r; for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) r.a[i][j] = T(0.0); return r; }
+
+template <class T> static V6<T> mul6(const M6<T>& m, const V6<T>& v) {
+  V6<T> r;
+  for (int i = 0; i < 6; ++i) { T s(0.0); for (int j = 0; j < 6; ++j) s += m.a[i][j] * v.a[j]; r.a[i] = s; }
+  return r;
+}
+template <class T> static V6<T> mul6T(const M6<T>& m, const V6<T>& v) {
+  V6<T> r;
+  for (int i = 0; i < 6; ++i) { T s(0.0); for (int j = 0; j < 6; ++j) s += m.a[j][i] * v.a[j]; r.a[i] = s; }
+  return r;
+}
+template <class T> static M6<T> mm6(const M6<T>& x, const M6<T>& y) {
+  M6<T> r;
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) { T s(0.0); for (int k = 0; k < 6; ++k) s += x.a[i][k] * y.a[k][j]; r.a[i][j] = s; }
+  return r;
+}
+template <class T> static M6<T> tr6(const M6<T>& x) { M6<T> r; for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) r.a[i][j] = x.a[j][i]; return r; }
+template <class T> static V6<T> add6(const V6<T>& x, const V6<T>& y) { V6<T> r; for (int i = 0; i < 6; ++i) r.a[i] = x.a[i] + y.a[i]; return r; }
+template <class T> static M6<T> madd6(const M6<T>& x, const M6<T>& y) { M6<T> r; for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) r.a[i][j] = x.a[i][j] + y.a[i][j]; return r; }
+
+// coordinate rotation about a principal axis (Featherstone's rx, ry, rz)
+template <class T> static R3<T> rot_axis(int axis, const T& q) {
+  T c = cos(q), s = sin(q);
+  R3<T> E;
+  for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) E.a[i][j] = T(i == j ? 1.0 : 0.0);
+  const int i1 = (axis + 1) % 3, i2 = (axis + 2) % 3;
+  E.a[i1][i1] = c; E.a[i1][i2] = s;
+  E.a[i2][i1] = -s; E.a[i2][i2] = c;
+  return E;
+}
+// Plucker transform for a frame rotated by E (coordinate transform) and
+// translated by r (in the parent frame): X = [E 0; -E rx E].
+template <class T> static M6<T> plux(const R3<T>& E, const T* r) {
+  M6<T> X = m6zero<T>();
+  T rx[3][3] = {{T(0.0), -r[2], r[1]}, {r[2], T(0.0), -r[0]}, {-r[1], r[0], T(0.0)}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      X.a[i][j] = E.a[i][j];
+      X.a[3 + i][3 + j] = E.a[i][j];
+      T s(0.0);
+      for (int k = 0; k < 3; ++k) s += E.a[i][k] * rx[k][j];
+      X.a[3 + i][j] = -s;
+    }
+  return X;
+}
+template <class T> static V6<T> crm6(const V6<T>& v, const V6<T>& m) {  // v x m
+  V6<T> r;
+  const T *w = v.a, *vo = v.a + 3, *mw = m.a, *mv = m.a + 3;
+  r.a[0] = w[1] * mw[2] - w[2] * mw[1];
+  r.a[1] = w[2] * mw[0] - w[0] * mw[2];
+  r.a[2] = w[0] * mw[1] - w[1] * mw[0];
+  r.a[3] = w[1] * mv[2] - w[2] * mv[1] + vo[1] * mw[2] - vo[2] * mw[1];
+  r.a[4] = w[2] * mv[0] - w[0] * mv[2] + vo[2] * mw[0] - vo[0] * mw[2];
+  r.a[5] = w[0] * mv[1] - w[1] * mv[0] + vo[0] * mw[1] - vo[1] * mw[0];
+  return r;
+}
+template <class T> static V6<T> crf6(const V6<T>& v, const V6<T>& f) {  // v x* f
+  V6<T> r;
+  const T *w = v.a, *vo = v.a + 3, *n = f.a, *fo = f.a + 3;
+  r.a[0] = w[1] * n[2] - w[2] * n[1] + vo[1] * fo[2] - vo[2] * fo[1];
+  r.a[1] = w[2] * n[0] - w[0] * n[2] + vo[2] * fo[0] - vo[0] * fo[2];
+  r.a[2] = w[0] * n[1] - w[1] * n[0] + vo[0] * fo[1] - vo[1] * fo[0];
+  r.a[3] = w[1] * fo[2] - w[2] * fo[1];
+  r.a[4] = w[2] * fo[0] - w[0] * fo[2];
+  r.a[5] = w[0] * fo[1] - w[1] * fo[0];
+  return r;
+}
+// rigid-body inertia of mass m with COM c and rotational inertia Ic (about the COM)
+template <class T> static M6<T> mcI(const T& m, const T* c, const T (&Ic)[3][3]) {
+  M6<T> I = m6zero<T>();
+  T cx[3][3] = {{T(0.0), -c[2], c[1]}, {c[2], T(0.0), -c[0]}, {-c[1], c[0], T(0.0)}};
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      T s(0.0);
+      for (int k = 0; k < 3; ++k) s += cx[i][k] * cx[j][k];  // cx cx^T
+      I.a[i][j] = Ic[i][j] + m * s;
+      I.a[i][3 + j] = m * cx[i][j];
+      I.a[3 + i][j] = m * cx[j][i];
+      I.a[3 + i][3 + j] = T(i == j ? 1.0 : 0.0) * m;
+    }
+  return I;
+}
+
+struct ArmBox {
+  int n_arm;              // prescribed arm joints; axes alternate z, y, z, ...
+  const double* arm_len;  // [n_arm] offset to the next joint along the local z axis
+  const double* amp;      // [n_arm][3] sinusoid amplitudes [rad]
+  const double* freq;     // [n_arm][3] [Hz]
+  const double* phase;    // [n_arm][3] [rad]
+  double box_mass, box_side, box_com_depth;
+  double weight_mass0, weight_mass1, weight_depth;
+  double g, damping;
+};
+
+// Prescribed arm joint angle and its first two time derivatives.
+static void arm_joint(const ArmBox& A, int j, double t, double* q, double* qd, double* qdd) {
+  *q = *qd = *qdd = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double a = A.amp[3 * j + k], w = 2.0 * M_PI * A.freq[3 * j + k], ph = A.phase[3 * j + k];
+    *q += a * std::sin(w * t + ph);
+    *qd += a * w * std::cos(w * t + ph);
+    *qdd += -a * w * w * std::sin(w * t + ph);
+  }
+}
+
+// Spatial velocity and acceleration (acceleration offset by -gravity, as
+// the articulated-body algorithm's base acceleration) of the box pivot frame
+// at time t, in pivot coordinates, by the recursive kinematics of the arm.
+static void arm_pivot_motion(const ArmBox& A, double t, V6<double>* v_out, V6<double>* a_out) {
+  V6<double> v = v6zero<double>(), a = v6zero<double>();
+  a.a[5] = A.g;  // -gravity (gravity along -z of the world)
+  double zero3[3] = {0.0, 0.0, 0.0};
+  for (int j = 0; j < A.n_arm; ++j) {
+    double q, qd, qdd;
+    arm_joint(A, j, t, &q, &qd, &qdd);
+    const int axis = (j % 2 == 0) ? 2 : 1;  // z, y, z, y, ...
+    double r[3] = {0.0, 0.0, j == 0 ? 0.0 : A.arm_len[j - 1]};
+    M6<double> Xup = mm6(plux<double>(rot_axis<double>(axis, q), zero3), plux<double>(rot_axis<double>(0, 0.0), r));
+    V6<double> S = v6zero<double>();
+    S.a[axis] = 1.0;
+    V6<double> vJ = S;
+    for (int i = 0; i < 6; ++i) vJ.a[i] *= qd;
+    v = add6(mul6(Xup, v), vJ);
+    V6<double> aJ = S;
+    for (int i = 0; i < 6; ++i) aJ.a[i] *= qdd;
+    a = add6(add6(mul6(Xup, a), aJ), crm6(v, vJ));
+  }
+  // pivot: the tip of the last link
+  double r[3] = {0.0, 0.0, A.arm_len[A.n_arm - 1]};
+  M6<double> X = plux<double>(rot_axis<double>(0, 0.0), r);
+  *v_out = mul6(X, v);
+  *a_out = mul6(X, a);
+}
+
+// Spatial inertia of the box (cube + two point weights at (x_k, y_k, -depth)).
+template <class T>
+static M6<T> box_inertia(const ArmBox& A, const T* th) {
+  const double side = A.box_side, m = A.box_mass;
+  T Ic[3][3];
+  for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) Ic[i][j] = T(i == j ? m * side * side / 6.0 : 0.0);
+  T c[3] = {T(0.0), T(0.0), T(-A.box_com_depth)};
+  M6<T> I = mcI<T>(T(m), c, Ic);
+  T Z[3][3];
+  for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) Z[i][j] = T(0.0);
+  T p0[3] = {th[0], th[1], T(-A.weight_depth)};
+  T p1[3] = {th[2], th[3], T(-A.weight_depth)};
+  I = madd6(I, mcI<T>(T(A.weight_mass0), p0, Z));
+  I = madd6(I, mcI<T>(T(A.weight_mass1), p1, Z));
+  return I;
+}
+
+// ABA for the two box joints (body 1: massless, joint about x; body 2: the
+// box, joint about y, same origin) on a base with spatial velocity v0 and
+// acceleration a0 (a0 already offset by -gravity).
+template <class T>
+static void box_aba(const ArmBox& A, const M6<T>& Ibox, const T* q, const T* qd, const T* tau, const V6<double>& v0,
+                    const V6<double>& a0, T* qdd) {
+  T zero3[3] = {T(0.0), T(0.0), T(0.0)};
+  M6<T> Xup[2];
+  Xup[0] = plux<T>(rot_axis<T>(0, q[0]), zero3);
+  Xup[1] = plux<T>(rot_axis<T>(1, q[1]), zero3);
+  V6<T> S[2];
+  S[0] = v6zero<T>(); S[0].a[0] = T(1.0);
+  S[1] = v6zero<T>(); S[1].a[1] = T(1.0);
+  V6<T> vb, ab;
+  for (int i = 0; i < 6; ++i) { vb.a[i] = T(v0.a[i]); ab.a[i] = T(a0.a[i]); }
+  V6<T> v[2], c[2], pA[2], U[2], a[2];
+  M6<T> IA[2];
+  T d[2], u[2];
+  for (int i = 0; i < 2; ++i) {
+    V6<T> vJ = S[i];
+    for (int k = 0; k < 6; ++k) vJ.a[k] = vJ.a[k] * qd[i];
+    v[i] = add6(mul6(Xup[i], i == 0 ? vb : v[i - 1]), vJ);
+    c[i] = crm6(v[i], vJ);
+    IA[i] = (i == 1) ? Ibox : m6zero<T>();
+    pA[i] = crf6(v[i], mul6(IA[i], v[i]));
+  }
+  for (int i = 1; i >= 0; --i) {
+    U[i] = mul6(IA[i], S[i]);
+    d[i] = S[i].a[0] * U[i].a[0] + S[i].a[1] * U[i].a[1];  // S has one non-zero entry
+    T sp(0.0);
+    for (int k = 0; k < 6; ++k) sp += S[i].a[k] * pA[i].a[k];
+    u[i] = tau[i] - sp;
+    if (i > 0) {
+      M6<T> Ia;
+      for (int r = 0; r < 6; ++r) for (int s2 = 0; s2 < 6; ++s2) Ia.a[r][s2] = IA[i].a[r][s2] - U[i].a[r] * U[i].a[s2] / d[i];
+      V6<T> pa = mul6(Ia, c[i]);
+      for (int r = 0; r < 6; ++r) pa.a[r] = pA[i].a[r] + pa.a[r] + U[i].a[r] * u[i] / d[i];
+      IA[i - 1] = madd6(IA[i - 1], mm6(tr6(Xup[i]), mm6(Ia, Xup[i])));
+      pA[i - 1] = add6(pA[i - 1], mul6T(Xup[i], pa));
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    a[i] = add6(mul6(Xup[i], i == 0 ? ab : a[i - 1]), c[i]);
+    T ua(0.0);
+    for (int k = 0; k < 6; ++k) ua += U[i].a[k] * a[i].a[k];
+    qdd[i] = (u[i] - ua) / d[i];
+    for (int k = 0; k < 6; ++k) a[i].a[k] = a[i].a[k] + S[i].a[k] * qdd[i];
+  }
+}
+
+// One semi-implicit Euler step of the box at time t (state [q1, q2, qd1, qd2]).
+template <class T>
+static void box_step(const ArmBox& A, const M6<T>& Ibox, double t, double dt, const T* s, T* sn) {
+  V6<double> v0, a0;
+  arm_pivot_motion(A, t, &v0, &a0);
+  T tau[2] = {-(T(A.damping) * s[2]), -(T(A.damping) * s[3])};
+  T qdd[2];
+  box_aba<T>(A, Ibox, s, s + 2, tau, v0, a0, qdd);
+  for (int i = 0; i < 2; ++i) {
+    T v = s[2 + i] + qdd[i] * T(dt);
+    sn[2 + i] = v;
+    sn[i] = s[i] + v * T(dt);
+  }
+}
+
+struct ArmBoxProblem {
+  ArmBox ab;
+  double dt;
+  int T, W, D;
+  const int* obs_index;   // [D] into the box state [q1, q2, qd1, qd2]
+  const double* obs;      // [T][D], row t-1 holds x_t
+  double sigma_obs, sigma_def;
+  const double* s0;       // [4]
+  const double* lo;       // [4]
+  const double* hi;       // [4]
+  double c_lim;
+};
+
+template <class T>
+static T armbox_window(const ArmBoxProblem& P, const T* th, const T* s_start, const T* s_next, int w) {
+  const M6<T> Ibox = box_inertia<T>(P.ab, th);
+  std::vector<T> s(s_start, s_start + 4), sn(4);
+  const int t0 = (int)(((long long)w * P.T) / P.W), t1 = (int)(((long long)(w + 1) * P.T) / P.W);
+  const double so2 = P.sigma_obs * P.sigma_obs;
+  const double obs_const = -0.5 * P.D * std::log(2.0 * M_PI * so2);
+  T ll(0.0);
+  for (int t = t0 + 1; t <= t1; ++t) {
+    box_step<T>(P.ab, Ibox, (t - 1) * P.dt, P.dt, s.data(), sn.data());
+    s.swap(sn);
+    T acc(0.0);
+    for (int k = 0; k < P.D; ++k) {
+      T r = T(P.obs[(size_t)(t - 1) * P.D + k]) - s[P.obs_index[k]];
+      acc += r * r;
+    }
+    ll += acc * T(-0.5 / so2) + T(obs_const);
+  }
+  if (w < P.W - 1) {
+    const double sd2 = P.sigma_def * P.sigma_def;
+    T acc(0.0);
+    for (int k = 0; k < 4; ++k) {
+      T d = s_next[k] - s[k];
+      acc += d * d;
+    }
+    ll += acc * T(-0.5 / sd2) + T(-0.5 * 4 * std::log(2.0 * M_PI * sd2));
+  }
+  return ll;
+}
+
+static double armbox_particle(const ArmBoxProblem& P, const double* x, double* grad) {
+  const int M = 4, S = 4, W = P.W, Pdim = M + (W - 1) * S;
+  if (grad) std::fill(grad, grad + Pdim, 0.0);
+  double total = 0.0;
+  for (int w = 0; w < W; ++w) {
+    const double* ss = (w == 0) ? P.s0 : x + M + (w - 1) * S;
+    const double* sn = (w < W - 1) ? x + M + w * S : nullptr;
+    if (!grad) {
+      total += armbox_window<double>(P, x, ss, sn, w);
+      continue;
+    }
+    g_nd = M + 2 * S;
+    std::vector<Dual> th(M), a(S), b(S);
+    for (int k = 0; k < M; ++k) { th[k] = Dual(x[k]); th[k].d[k] = 1.0; }
+    for (int k = 0; k < S; ++k) {
+      a[k] = Dual(ss[k]);
+      if (w > 0) a[k].d[M + k] = 1.0;
+      if (sn) { b[k] = Dual(sn[k]); b[k].d[M + S + k] = 1.0; }
+    }
+    Dual ll = armbox_window<Dual>(P, th.data(), a.data(), sn ? b.data() : nullptr, w);
+    total += ll.v;
+    for (int k = 0; k < M; ++k) grad[k] += ll.d[k];
+    if (w > 0) for (int k = 0; k < S; ++k) grad[M + (w - 1) * S + k] += ll.d[M + k];
+    if (sn) for (int k = 0; k < S; ++k) grad[M + w * S + k] += ll.d[M + S + k];
+  }
+  // limit prior, as for the chain problems
+  for (int k = 0; k < M; ++k) {
+    const double wd = P.hi[k] - P.lo[k];
+    const double u = (x[k] - P.lo[k]) / wd;
+    const double cu = std::min(1.0, std::max(0.0, u));
+    total += -std::log(wd) - 0.5 * P.c_lim * (cu - u) * (cu - u);
+    if (grad) grad[k] += P.c_lim * (cu - u) / wd;
+  }
+  return total;
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -634,6 +947,54 @@ int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
   }
   if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
   if (bw_out) *bw_out = bw;
+  return 0;
+}
+
+// ---- arm + box -------------------------------------------------------------
+// Spatial velocity and acceleration (minus gravity) of the box pivot at t.
+int orc_armbox_pivot(const ArmBox* A, double t, double* v6, double* a6) {
+  V6<double> v, a;
+  arm_pivot_motion(*A, t, &v, &a);
+  for (int i = 0; i < 6; ++i) { v6[i] = v.a[i]; a6[i] = a.a[i]; }
+  return 0;
+}
+
+// Box joint accelerations for state s = [q1, q2, qd1, qd2] at time t.
+int orc_armbox_qdd(const ArmBox* A, const double* theta, double t, const double* s, double* qdd) {
+  M6<double> I = box_inertia<double>(*A, theta);
+  V6<double> v0, a0;
+  arm_pivot_motion(*A, t, &v0, &a0);
+  double tau[2] = {-A->damping * s[2], -A->damping * s[3]};
+  box_aba<double>(*A, I, s, s + 2, tau, v0, a0, qdd);
+  return 0;
+}
+
+// Spatial inertia of the box (6x6, row-major) for weight positions theta.
+int orc_armbox_inertia(const ArmBox* A, const double* theta, double* I66) {
+  M6<double> I = box_inertia<double>(*A, theta);
+  for (int i = 0; i < 6; ++i) for (int j = 0; j < 6; ++j) I66[6 * i + j] = I.a[i][j];
+  return 0;
+}
+
+// f_sim of the box: states [T+1][4] from s0.
+int orc_armbox_simulate(const ArmBox* A, const double* theta, double dt, int T, const double* s0, double* states) {
+  M6<double> I = box_inertia<double>(*A, theta);
+  std::copy(s0, s0 + 4, states);
+  for (int t = 0; t < T; ++t) box_step<double>(*A, I, t * dt, dt, states + (size_t)t * 4, states + (size_t)(t + 1) * 4);
+  return 0;
+}
+
+int orc_armbox_loglik_grad(const ArmBoxProblem* prob, const double* particles, int N, double* logp, double* grad,
+                           int threads) {
+  const ArmBoxProblem& P = *prob;
+  if (P.W < 1 || P.T < P.W) return -1;
+  const int Pdim = 4 + (P.W - 1) * 4;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i)
+    logp[i] = armbox_particle(P, particles + (size_t)i * Pdim, grad ? grad + (size_t)i * Pdim : nullptr);
   return 0;
 }
 

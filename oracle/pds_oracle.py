@@ -65,6 +65,42 @@ class _Problem(ctypes.Structure):
     ]
 
 
+class _ArmBox(ctypes.Structure):
+    _fields_ = [
+        ("n_arm", ctypes.c_int),
+        ("arm_len", _dp),
+        ("amp", _dp),
+        ("freq", _dp),
+        ("phase", _dp),
+        ("box_mass", ctypes.c_double),
+        ("box_side", ctypes.c_double),
+        ("box_com_depth", ctypes.c_double),
+        ("weight_mass0", ctypes.c_double),
+        ("weight_mass1", ctypes.c_double),
+        ("weight_depth", ctypes.c_double),
+        ("g", ctypes.c_double),
+        ("damping", ctypes.c_double),
+    ]
+
+
+class _ArmBoxProblem(ctypes.Structure):
+    _fields_ = [
+        ("ab", _ArmBox),
+        ("dt", ctypes.c_double),
+        ("T", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("D", ctypes.c_int),
+        ("obs_index", _ip),
+        ("obs", _dp),
+        ("sigma_obs", ctypes.c_double),
+        ("sigma_def", ctypes.c_double),
+        ("s0", _dp),
+        ("lo", _dp),
+        ("hi", _dp),
+        ("c_lim", ctypes.c_double),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -89,6 +125,12 @@ def lib():
             L.orc_svgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_armbox_pivot.argtypes = [ctypes.POINTER(_ArmBox), ctypes.c_double, _dp, _dp]
+            L.orc_armbox_qdd.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, _dp, _dp]
+            L.orc_armbox_inertia.argtypes = [ctypes.POINTER(_ArmBox), _dp, _dp]
+            L.orc_armbox_simulate.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_armbox_loglik_grad.argtypes = [ctypes.POINTER(_ArmBoxProblem), _dp, ctypes.c_int, _dp, _dp,
+                                                 ctypes.c_int]
             _lib = L
     return _lib
 
@@ -258,3 +300,87 @@ class SvgdState:
                             self.v.ctypes.data_as(_dp), ctypes.byref(self.t), self.lr, self.beta1, self.beta2,
                             self.eps, int(self.clamp), phi.ctypes.data_as(_dp), ctypes.byref(bw))
         return phi, bw.value
+
+
+# --------------------------------------------------------------------------
+# arm shaking a box
+# --------------------------------------------------------------------------
+class ArmBox:
+    """Prescribed arm + U-joint box description (see oracle.cpp)."""
+
+    def __init__(self, *, arm_len, amp, freq, phase, box_mass=1.0, box_side=0.3, box_com_depth=0.15,
+                 weight_mass=(0.5, 0.5), weight_depth=0.3, g=9.81, damping=0.0):
+        self._keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (arm_len, amp, freq, phase)]
+        a, b, c, d = self._keep
+        self.c = _ArmBox(n_arm=len(a), arm_len=a.ctypes.data_as(_dp), amp=b.ctypes.data_as(_dp),
+                         freq=c.ctypes.data_as(_dp), phase=d.ctypes.data_as(_dp), box_mass=box_mass,
+                         box_side=box_side, box_com_depth=box_com_depth, weight_mass0=weight_mass[0],
+                         weight_mass1=weight_mass[1], weight_depth=weight_depth, g=g, damping=damping)
+
+    @classmethod
+    def from_workload(cls, wl):
+        return cls(arm_len=wl.arm_len, amp=wl.amp, freq=wl.freq, phase=wl.phase, box_mass=wl.box_mass,
+                   box_side=wl.box_side, box_com_depth=wl.box_com_depth, weight_mass=wl.weight_mass,
+                   weight_depth=wl.weight_depth, g=wl.g, damping=wl.box_damping)
+
+    def pivot(self, t):
+        v, a = np.zeros(6), np.zeros(6)
+        lib().orc_armbox_pivot(ctypes.byref(self.c), float(t), v.ctypes.data_as(_dp), a.ctypes.data_as(_dp))
+        return v, a
+
+    def qdd(self, theta, t, s):
+        th, tp = _d(theta)
+        st, sp = _d(s)
+        out = np.zeros(2)
+        lib().orc_armbox_qdd(ctypes.byref(self.c), tp, float(t), sp, out.ctypes.data_as(_dp))
+        return out
+
+    def inertia(self, theta):
+        th, tp = _d(theta)
+        out = np.zeros((6, 6))
+        lib().orc_armbox_inertia(ctypes.byref(self.c), tp, out.ctypes.data_as(_dp))
+        return out
+
+    def simulate(self, theta, dt, T, s0):
+        th, tp = _d(theta)
+        s, sp = _d(s0)
+        out = np.zeros((T + 1, 4))
+        lib().orc_armbox_simulate(ctypes.byref(self.c), tp, float(dt), int(T), sp, out.ctypes.data_as(_dp))
+        return out
+
+
+class ArmBoxProblem:
+    """Multiple-shooting problem of the box (theta = (x1, y1, x2, y2))."""
+
+    def __init__(self, armbox: ArmBox, *, dt, T, W, obs, obs_index, sigma_obs, sigma_def, s0, lo, hi, c_lim=1e4):
+        self.armbox = armbox
+        self._keep = []
+
+        def d(x):
+            a, p = _d(x)
+            self._keep.append(a)
+            return p
+
+        def i(x):
+            a, p = _i(x)
+            self._keep.append(a)
+            return p
+
+        obs = np.asarray(obs, dtype=np.float64)
+        self.T, self.W, self.M, self.S = int(T), int(W), 4, 4
+        self.P = 4 + (self.W - 1) * 4
+        self.c = _ArmBoxProblem(ab=armbox.c, dt=float(dt), T=self.T, W=self.W, D=obs.shape[1], obs_index=i(obs_index),
+                                obs=d(obs), sigma_obs=float(sigma_obs), sigma_def=float(sigma_def), s0=d(s0),
+                                lo=d(lo), hi=d(hi), c_lim=float(c_lim))
+
+    def loglik_grad(self, particles, grad=True, threads=1):
+        x, xp = _d(np.atleast_2d(particles))
+        N = x.shape[0]
+        assert x.shape[1] == self.P
+        logp = np.zeros(N)
+        g = np.zeros((N, self.P)) if grad else None
+        rc = lib().orc_armbox_loglik_grad(ctypes.byref(self.c), xp, N, logp.ctypes.data_as(_dp),
+                                          g.ctypes.data_as(_dp) if grad else None, int(threads))
+        if rc != 0:
+            raise RuntimeError("orc_armbox_loglik_grad failed")
+        return (logp, g) if grad else logp

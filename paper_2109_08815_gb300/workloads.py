@@ -262,3 +262,86 @@ def batched_problems(n_jobs: int = 64, seed: int = 4000, n_range=(2, 8), T_range
             sigma_def=SIGMA_DEF, s0=np.concatenate([q0, np.zeros(n)]), noise=noise, theta_init=theta_init,
             lr=1e-2, seed=seed + j))
     return out
+
+
+@dataclasses.dataclass
+class ArmBoxWorkload:
+    """Arm shaking a box (the paper's Panda-arm experiment, Sec. V-C, synthetic).
+
+    A serial arm of revolute joints (axes alternate z, y, z, ...; link i
+    offset l_i along its local z) follows prescribed joint trajectories
+    q_j(t) = sum_k amp_jk sin(2 pi f_jk t + phase_jk).  A cube of side 0.3 m
+    and mass 1 kg (COM 0.15 m below the joint) hangs from the arm's tip on a
+    U-joint (axis x, then y); two 0.5 kg point weights sit on its floor at
+    (x_k, y_k, -0.3).  theta = (x1, y1, x2, y2).  The box joint angles are
+    observed.
+    """
+    name: str
+    arm_len: np.ndarray        # [n_arm]
+    arm_mass: np.ndarray       # [n_arm] (the arm's motion is prescribed; kept for completeness)
+    amp: np.ndarray            # [n_arm][3]
+    freq: np.ndarray           # [n_arm][3]
+    phase: np.ndarray          # [n_arm][3]
+    theta_true: np.ndarray     # [4]
+    lo: np.ndarray
+    hi: np.ndarray
+    dt: float
+    T: int
+    W: int
+    obs_index: np.ndarray
+    sigma_obs: float
+    sigma_def: float
+    s0: np.ndarray             # [4]
+    noise: np.ndarray          # [T][D]
+    theta_init: np.ndarray     # [N][4]
+    box_mass: float = 1.0
+    box_side: float = 0.3
+    box_com_depth: float = 0.15
+    weight_mass: tuple = (0.5, 0.5)
+    weight_depth: float = 0.3
+    box_damping: float = 0.0
+    g: float = GRAVITY
+    c_lim: float = C_LIM
+    lr: float = 1e-2
+    iterations: int = 500
+    seed: int = 0
+    n: int = 2
+    M: int = 4
+    S: int = 4
+
+    @property
+    def D(self) -> int:
+        return len(self.obs_index)
+
+    @property
+    def N(self) -> int:
+        return self.theta_init.shape[0]
+
+    @property
+    def P(self) -> int:
+        return self.M + (self.W - 1) * self.S
+
+    def window_start(self, w: int) -> int:
+        return (w * self.T) // self.W
+
+
+def arm_box(N: int = 2048, seed: int = 3000, T: int = 2000, W: int = 40, n_arm: int = 7) -> ArmBoxWorkload:
+    """7-joint arm (lengths U[0.1, 0.4] m, masses U[1, 4] kg), each joint a sum
+    of 3 sinusoids of amplitude 0.3 rad and frequency U[0.2, 1] Hz; weight
+    positions ~ U[-0.15, 0.15]; T = 2000 at dt = 0.002, 40 windows, box
+    angles observed with sigma 0.01; the box starts at rest in the tip frame."""
+    rng = np.random.default_rng(seed)
+    arm_len = rng.uniform(0.1, 0.4, n_arm)
+    arm_mass = rng.uniform(1.0, 4.0, n_arm)
+    amp = np.full((n_arm, 3), 0.3)
+    freq = rng.uniform(0.2, 1.0, (n_arm, 3))
+    phase = rng.uniform(0.0, 2 * math.pi, (n_arm, 3))
+    lo, hi = np.full(4, -0.15), np.full(4, 0.15)
+    theta_true = rng.uniform(lo, hi)
+    obs_index = np.array([0, 1], dtype=np.int32)
+    noise = rng.standard_normal((T, 2))
+    theta_init = rng.uniform(lo, hi, size=(N, 4))
+    return ArmBoxWorkload(name="arm_box", arm_len=arm_len, arm_mass=arm_mass, amp=amp, freq=freq, phase=phase,
+                          theta_true=theta_true, lo=lo, hi=hi, dt=0.002, T=T, W=W, obs_index=obs_index,
+                          sigma_obs=0.01, sigma_def=SIGMA_DEF, s0=np.zeros(4), noise=noise, theta_init=theta_init,
+                          seed=seed)
