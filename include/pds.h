@@ -42,6 +42,7 @@ extern "C" {
 #define PDS_ERR_UNSUPPORTED (-7) /* configuration outside the compiled range   */
 
 #define PDS_SYSTEM_PLANAR_CHAIN 1
+#define PDS_SYSTEM_ARM_BOX 2
 
 #define PDS_PARAM_MASS 0    /* point mass at the tip of a link [kg]          */
 #define PDS_PARAM_LENGTH 1  /* link length [m]                               */
@@ -68,6 +69,30 @@ typedef struct pds_system_desc {
   const int* theta_kind;  /* host [M], PDS_PARAM_*                           */
   const int* theta_link;  /* host [M], 0-based link index; each (kind, link) at most once */
 } pds_system_desc;
+
+/* Arm shaking a box (the paper's Panda-arm experiment, Sec. V-C, as a
+ * synthetic system).  A serial arm of n_arm revolute joints (axes alternate
+ * z, y, z, ... of the link frames; joint j+1 sits arm_len[j] along the local
+ * z axis of link j; joint 1 at the world origin; gravity along -z) follows
+ * prescribed trajectories q_j(t) = sum_k amp[j][k] sin(2 pi freq[j][k] t +
+ * phase[j][k]).  At the tip of the last link a box hangs on two passive
+ * revolute joints at the same point (axis x, then axis y: a U-joint) with
+ * viscous damping.  The box is a solid cube (box_mass, box_side, its centre
+ * box_com_depth below the joint) plus two point weights (weight_mass[k]) at
+ * (x_k, y_k, -weight_depth) in the box frame.  theta = (x1, y1, x2, y2);
+ * state s = [q1, q2, qd1, qd2] of the box joints. */
+typedef struct pds_armbox_desc {
+  int n_arm;             /* 1..8 */
+  const double* arm_len; /* host [n_arm] */
+  const double* amp;     /* host [n_arm][3] rad */
+  const double* freq;    /* host [n_arm][3] Hz */
+  const double* phase;   /* host [n_arm][3] rad */
+  double box_mass, box_side, box_com_depth;
+  double weight_mass[2];
+  double weight_depth;
+  double gravity;
+  double damping;        /* box joint damping [N m s / rad] */
+} pds_armbox_desc;
 
 typedef struct pds_problem* pds_problem_t;
 typedef struct pds_svgd* pds_svgd_t;
@@ -97,6 +122,18 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
                        double sigma_obs, double sigma_def, const float* s0,
                        const float* theta_lo, const float* theta_hi, double c_lim,
                        void* cuda_stream, pds_problem_t* out);
+
+/* Multiple-shooting problem of the arm-and-box system; arguments as
+ * pds_problem_create (obs_index indexes the box state [q1, q2, qd1, qd2];
+ * theta box and particles have M = 4, S = 4).  The arm's pivot motion is
+ * tabulated on the host for every time step and kept on the device.  The
+ * gradient comes from tangents propagated forward through each window
+ * (theta and the window's start state: 8 directions). */
+int pds_problem_create_armbox(const pds_armbox_desc* sys, double dt, int T, int windows,
+                              const float* obs, int D, const int* obs_index, double sigma_obs,
+                              double sigma_def, const float* s0, const float* theta_lo,
+                              const float* theta_hi, double c_lim, void* cuda_stream,
+                              pds_problem_t* out);
 
 /* Release the problem and all device memory it owns (synchronises its stream). */
 int pds_problem_destroy(pds_problem_t p);

@@ -44,10 +44,30 @@ class _SystemDesc(ctypes.Structure):
     ]
 
 
+class _ArmBoxDesc(ctypes.Structure):
+    _fields_ = [
+        ("n_arm", ctypes.c_int),
+        ("arm_len", _dp),
+        ("amp", _dp),
+        ("freq", _dp),
+        ("phase", _dp),
+        ("box_mass", ctypes.c_double),
+        ("box_side", ctypes.c_double),
+        ("box_com_depth", ctypes.c_double),
+        ("weight_mass", ctypes.c_double * 2),
+        ("weight_depth", ctypes.c_double),
+        ("gravity", ctypes.c_double),
+        ("damping", ctypes.c_double),
+    ]
+
+
 EXPORTS = {
     "pds_problem_create": ([ctypes.POINTER(_SystemDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
                             ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
                             _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_problem_create_armbox": ([ctypes.POINTER(_ArmBoxDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
+                                   ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
+                                   ctypes.c_double, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "pds_problem_destroy": ([_vp], ctypes.c_int),
     "pds_problem_layout": ([_vp, _ip, _ip, _ip], ctypes.c_int),
     "pds_problem_set_checkpoint_stride": ([_vp, ctypes.c_int], ctypes.c_int),
@@ -186,7 +206,41 @@ class Problem:
             self.set_option(OPT_FAST_MATH, int(bool(fast_math)))
 
     @classmethod
+    def armbox(cls, wl, obs, stream=None, checkpoint_stride=None, fast_math=None):
+        """Arm-and-box problem (pds_problem_create_armbox) from an ArmBoxWorkload."""
+        self = cls.__new__(cls)
+        L = lib()
+        keep = [np.ascontiguousarray(a, dtype=np.float64) for a in (wl.arm_len, wl.amp, wl.freq, wl.phase)]
+        d = _ArmBoxDesc(n_arm=len(keep[0]), arm_len=keep[0].ctypes.data_as(_dp), amp=keep[1].ctypes.data_as(_dp),
+                        freq=keep[2].ctypes.data_as(_dp), phase=keep[3].ctypes.data_as(_dp),
+                        box_mass=wl.box_mass, box_side=wl.box_side, box_com_depth=wl.box_com_depth,
+                        weight_mass=(ctypes.c_double * 2)(*wl.weight_mass), weight_depth=wl.weight_depth,
+                        gravity=wl.g, damping=wl.box_damping)
+        f = [np.ascontiguousarray(x, dtype=np.float32) for x in (obs, wl.s0, wl.lo, wl.hi)]
+        oi = np.ascontiguousarray(wl.obs_index, dtype=np.int32)
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_problem_create_armbox(ctypes.byref(d), float(wl.dt), int(wl.T), int(wl.W),
+                                           f[0].ctypes.data_as(_fp), f[0].shape[1], oi.ctypes.data_as(_ip),
+                                           float(wl.sigma_obs), float(wl.sigma_def), f[1].ctypes.data_as(_fp),
+                                           f[2].ctypes.data_as(_fp), f[3].ctypes.data_as(_fp), float(wl.c_lim),
+                                           self._stream_h, ctypes.byref(h)), "pds_problem_create_armbox")
+        self._h = h
+        self._keep = []
+        self.T, self.W, self.n = int(wl.T), int(wl.W), 2
+        M, S, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.pds_problem_layout(h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
+        self.M, self.S, self.P = M.value, S.value, P.value
+        if checkpoint_stride is not None:
+            self.set_checkpoint_stride(checkpoint_stride)
+        if fast_math is not None:
+            self.set_option(OPT_FAST_MATH, int(bool(fast_math)))
+        return self
+
+    @classmethod
     def from_workload(cls, wl, obs, **kw):
+        if hasattr(wl, "arm_len"):
+            return cls.armbox(wl, obs, **kw)
         return cls(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
                    theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs, obs_index=wl.obs_index,
                    sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo, hi=wl.hi, g=wl.g,

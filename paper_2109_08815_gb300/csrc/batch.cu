@@ -182,6 +182,11 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     cudaStream_t st = b->side[j % kSideStreams];
     const int N = s->sp.N;
     float* lp = b->logp[j] ? b->logp[j] : p->d_logp;
+    if (p->kind == PDS_SYSTEM_ARM_BOX) {
+      // not part of the chain-length groups: its own rollout on the branch
+      if ((e = launch_armbox_rollout(p->c, p->ab, b->X[j], N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
+      ++n;
+    }
     if ((e = launch_window_reduce(p->c, b->X[j], N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess)
       return e;
     SvgdWork w = s->w;
@@ -204,6 +209,12 @@ static int rebuild(pds_batch* b) {
   drop_graph(b);
   for (Group& g : b->groups) {
     int rc = build_group(b, g);
+    if (rc != PDS_OK) return rc;
+  }
+  for (size_t j = 0; j < b->probs.size(); ++j) {
+    if (b->probs[j]->kind != PDS_SYSTEM_ARM_BOX) continue;
+    int rc = ensure_workspace(b->probs[j], b->svgds[j]->sp.N);
+    if (rc == PDS_OK) rc = ensure_iter_buffers(b->probs[j], b->svgds[j]->sp.N);
     if (rc != PDS_OK) return rc;
   }
   b->dirty = false;
@@ -270,7 +281,7 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
     Group g;
     g.NL = nl;
     for (int j = 0; j < n_jobs; ++j)
-      if (b->probs[j]->c.n == nl) g.jobs.push_back(j);
+      if (b->probs[j]->kind == PDS_SYSTEM_PLANAR_CHAIN && b->probs[j]->c.n == nl) g.jobs.push_back(j);
     if (!g.jobs.empty()) {
       g.K = b->probs[g.jobs[0]]->c.K;
       g.fast = b->probs[g.jobs[0]]->c.fast_math;

@@ -34,6 +34,13 @@ struct ChainParams {
   const float* obs;        // device [T][D]
 };
 
+// Arm-and-box system parameters (added to ChainParams-based problems with
+// kind == PDS_SYSTEM_ARM_BOX; ChainParams then has n = 2, M = 4, S = 4).
+struct ArmBoxParams {
+  float box_mass, box_side, box_com_depth, w_mass0, w_mass1, w_depth, damping;
+  const float* base;  // device [T][9]: pivot omega, alpha, (a - g), pivot coordinates
+};
+
 // Per-window partial results written by the rollout kernel, reduced over
 // windows by the window-reduction kernel.  All [row][N] slabs.
 struct Partials {
@@ -66,6 +73,10 @@ cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Pa
 cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
                                  float* grad, int32_t* status, cudaStream_t st);
 cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st);
+cudaError_t launch_armbox_rollout(const ChainParams& c, const ArmBoxParams& ab, const float* X, int N,
+                                  const Partials& parts, int grad, int32_t* status, cudaStream_t st);
+cudaError_t launch_armbox_simulate(const ChainParams& c, const ArmBoxParams& ab, const float* theta, int N,
+                                   float* states, cudaStream_t st);
 
 struct SvgdParams {
   int N, M, P;
@@ -119,7 +130,10 @@ void set_launch_count(int n);
 
 // Objects behind the opaque handles of pds.h.
 struct pds_problem {
+  int kind = PDS_SYSTEM_PLANAR_CHAIN;
   pds::ChainParams c;
+  pds::ArmBoxParams ab{};
+  float* d_base = nullptr;  // arm-and-box pivot motion table
   cudaStream_t stream;
   float* d_obs = nullptr;
   int cap_N = 0;          // workspace capacity in particles
