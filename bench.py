@@ -109,6 +109,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Maximum of a per-rank float over all ranks (the job's time is the
+    slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -261,11 +273,8 @@ def run_pds(args):
     torch.cuda.synchronize()
     step_ms = [evs[k][0].elapsed_time(evs[k][2]) for k in range(args.steps)]
     lg_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
-    t_total = sum(step_ms) / 1e3
+    t_total = max_over_ranks(sum(step_ms) / 1e3, dev)
     if world > 1:
-        tt = torch.tensor([t_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
         dist.barrier()
     ms_per_step = t_total * 1e3 / args.steps
     value = world * N * wl.T * args.steps / t_total
@@ -283,11 +292,7 @@ def run_pds(args):
             t0 = time.perf_counter()
             api.iterate_host(prob, svgd, xh, 1, lh)
             ts.append(time.perf_counter() - t0)
-        e2e_s = sum(ts) / len(ts)
-        if world > 1:
-            tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(sum(ts) / len(ts), dev)
         e2e = {"value": world * N * wl.T / e2e_s, "unit": UNIT, "h2d_bytes_per_step": wl.P * N * 4,
                "d2h_bytes_per_step": wl.P * N * 4 + N * 4}
 
@@ -411,7 +416,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300):
     run to `iters` SVGD iterations: continuous batching against one job at a
     time with plain launches."""
     from paper_2109_08815_gb300 import serve
-    wls = wlmod.batched_problems(n_jobs=n_jobs, seed=5000)
+    wls = wlmod.serving_mix(n_jobs=n_jobs, seed=5000)
     jobs = []
     for w in wls:
         o = _gen_obs(api, w, dev, stream)
@@ -422,8 +427,9 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300):
                                         checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH))
     lat_p, _, wall_p = serve.run_plain(jobs, arrivals, checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH),
                                        stream=stream)
-    return {"workload": f"{n_jobs} jobs, Poisson arrivals at {rate:g}/s, {iters} SVGD iterations each, "
-                        "uneven-problem distribution",
+    n_arm = sum(1 for w in wls if hasattr(w, "arm_len"))
+    return {"workload": f"{n_jobs} jobs, Poisson arrivals at {rate:g}/s, {iters} SVGD iterations each: "
+                        f"{n_jobs - n_arm} uneven chain problems, {n_arm} arm-box jobs at 512 particles",
             "served": {**serve.percentiles(lat_s), "value": units / wall_s, "wall_s": wall_s},
             "plain_sequential": {**serve.percentiles(lat_p), "value": units / wall_p, "wall_s": wall_p},
             "unit": UNIT, "time_to_posterior": "arrival to final particles on the host"}

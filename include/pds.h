@@ -296,6 +296,12 @@ int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int
                       double sigma_def, const float* s0, const float* theta_lo,
                       const float* theta_hi, double c_lim, int N, const float* particles,
                       double lr, int iterations, long long* job_id);
+/* Same for an arm-and-box job (arguments as pds_problem_create_armbox). */
+int pds_server_submit_armbox(pds_server_t s, const pds_armbox_desc* sys, double dt, int T,
+                             int windows, const float* obs, int D, const int* obs_index,
+                             double sigma_obs, double sigma_def, const float* s0,
+                             const float* theta_lo, const float* theta_hi, double c_lim, int N,
+                             const float* particles, double lr, int iterations, long long* job_id);
 /* One scheduling step (admit, iterate, retire); synchronises the stream. */
 int pds_server_tick(pds_server_t s, int* n_active, int* n_retired);
 /* PDS_JOB_* state and iterations done so far. */

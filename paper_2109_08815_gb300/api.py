@@ -97,6 +97,10 @@ EXPORTS = {
                            ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
                            ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
                           ctypes.c_int),
+    "pds_server_submit_armbox": ([_vp, ctypes.POINTER(_ArmBoxDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  _fp, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
+                                  ctypes.c_double, ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "pds_server_tick": ([_vp, _ip, _ip], ctypes.c_int),
     "pds_server_status": ([_vp, ctypes.c_longlong, _ip, _ip], ctypes.c_int),
     "pds_server_result": ([_vp, ctypes.c_longlong, _fp, _fp], ctypes.c_int),
@@ -460,15 +464,27 @@ class Server:
             return a.ctypes.data_as(_fp)
 
         obs = np.ascontiguousarray(obs, dtype=np.float32)
-        sysd = _SystemDesc(kind=PDS_SYSTEM_PLANAR_CHAIN, n_links=wl.n, mass=d(wl.mass), length=d(wl.length),
-                           damping=d(wl.damping), gravity=float(wl.g), n_theta=wl.M, theta_kind=i(wl.theta_kind),
-                           theta_link=i(wl.theta_link))
         x = np.ascontiguousarray(np.asarray(particles).T, dtype=np.float32)  # [P][N]
         jid = ctypes.c_longlong()
-        _check(lib().pds_server_submit(self._h, ctypes.byref(sysd), float(wl.dt), int(wl.T), int(wl.W), f(obs),
-                                       obs.shape[1], i(wl.obs_index), float(wl.sigma_obs), float(wl.sigma_def),
-                                       f(wl.s0), f(wl.lo), f(wl.hi), float(wl.c_lim), x.shape[1], f(x),
-                                       float(wl.lr), int(iterations), ctypes.byref(jid)), "pds_server_submit")
+        if hasattr(wl, "arm_len"):
+            ad = _ArmBoxDesc(n_arm=len(wl.arm_len), arm_len=d(wl.arm_len), amp=d(wl.amp), freq=d(wl.freq),
+                             phase=d(wl.phase), box_mass=wl.box_mass, box_side=wl.box_side,
+                             box_com_depth=wl.box_com_depth, weight_mass=(ctypes.c_double * 2)(*wl.weight_mass),
+                             weight_depth=wl.weight_depth, gravity=wl.g, damping=wl.box_damping)
+            _check(lib().pds_server_submit_armbox(self._h, ctypes.byref(ad), float(wl.dt), int(wl.T), int(wl.W),
+                                                  f(obs), obs.shape[1], i(wl.obs_index), float(wl.sigma_obs),
+                                                  float(wl.sigma_def), f(wl.s0), f(wl.lo), f(wl.hi),
+                                                  float(wl.c_lim), x.shape[1], f(x), float(wl.lr), int(iterations),
+                                                  ctypes.byref(jid)), "pds_server_submit_armbox")
+        else:
+            sysd = _SystemDesc(kind=PDS_SYSTEM_PLANAR_CHAIN, n_links=wl.n, mass=d(wl.mass), length=d(wl.length),
+                               damping=d(wl.damping), gravity=float(wl.g), n_theta=wl.M,
+                               theta_kind=i(wl.theta_kind), theta_link=i(wl.theta_link))
+            _check(lib().pds_server_submit(self._h, ctypes.byref(sysd), float(wl.dt), int(wl.T), int(wl.W),
+                                           f(obs), obs.shape[1], i(wl.obs_index), float(wl.sigma_obs),
+                                           float(wl.sigma_def), f(wl.s0), f(wl.lo), f(wl.hi), float(wl.c_lim),
+                                           x.shape[1], f(x), float(wl.lr), int(iterations), ctypes.byref(jid)),
+                   "pds_server_submit")
         self._shapes[jid.value] = (x.shape[0], x.shape[1])
         return jid.value
 

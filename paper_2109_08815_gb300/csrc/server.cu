@@ -24,8 +24,11 @@ namespace {
 struct Job {
   long long id = 0;
   int state = 0;  // PDS_JOB_*
+  int kind = PDS_SYSTEM_PLANAR_CHAIN;
   // creation arguments (host copies)
   pds_system_desc sys{};
+  pds_armbox_desc arm{};
+  std::vector<double> arm_len, amp, freq, phase;
   std::vector<double> mass, length, damping;
   std::vector<int> theta_kind, theta_link, obs_index;
   std::vector<float> obs, s0, lo, hi, x0;
@@ -89,19 +92,31 @@ static void release(Job& j) {
 }
 
 static int activate(pds_server* s, Job& j) {
-  pds_system_desc sys = j.sys;
-  sys.mass = j.mass.data();
-  sys.length = j.length.data();
-  sys.damping = j.damping.data();
-  sys.theta_kind = j.theta_kind.data();
-  sys.theta_link = j.theta_link.data();
-  int rc = pds_problem_create(&sys, j.dt, j.T, j.W, j.obs.data(), j.D, j.obs_index.data(), j.sigma_obs, j.sigma_def,
-                              j.s0.data(), j.lo.data(), j.hi.data(), j.c_lim, s->stream, &j.prob);
+  int rc;
+  int M = 4;
+  if (j.kind == PDS_SYSTEM_ARM_BOX) {
+    pds_armbox_desc a = j.arm;
+    a.arm_len = j.arm_len.data();
+    a.amp = j.amp.data();
+    a.freq = j.freq.data();
+    a.phase = j.phase.data();
+    rc = pds_problem_create_armbox(&a, j.dt, j.T, j.W, j.obs.data(), j.D, j.obs_index.data(), j.sigma_obs,
+                                   j.sigma_def, j.s0.data(), j.lo.data(), j.hi.data(), j.c_lim, s->stream, &j.prob);
+  } else {
+    pds_system_desc sys = j.sys;
+    sys.mass = j.mass.data();
+    sys.length = j.length.data();
+    sys.damping = j.damping.data();
+    sys.theta_kind = j.theta_kind.data();
+    sys.theta_link = j.theta_link.data();
+    M = sys.n_theta;
+    rc = pds_problem_create(&sys, j.dt, j.T, j.W, j.obs.data(), j.D, j.obs_index.data(), j.sigma_obs, j.sigma_def,
+                            j.s0.data(), j.lo.data(), j.hi.data(), j.c_lim, s->stream, &j.prob);
+  }
   if (rc != PDS_OK) return rc;
   pds_problem_set_option(j.prob, PDS_OPT_CHECKPOINT_STRIDE, s->K);
   pds_problem_set_option(j.prob, PDS_OPT_FAST_MATH, s->fast);
-  rc = pds_svgd_create(j.N, sys.n_theta, j.P, j.lo.data(), j.hi.data(), j.lr, 0.9, 0.999, 1e-8, 1, s->stream,
-                       &j.svgd);
+  rc = pds_svgd_create(j.N, M, j.P, j.lo.data(), j.hi.data(), j.lr, 0.9, 0.999, 1e-8, 1, s->stream, &j.svgd);
   if (rc != PDS_OK) { release(j); return rc; }
   cudaError_t e;
   if ((e = cudaMalloc(&j.d_x, (size_t)j.P * j.N * sizeof(float))) != cudaSuccess ||
@@ -177,6 +192,44 @@ int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int
   j.lo.assign(theta_lo, theta_lo + M);
   j.hi.assign(theta_hi, theta_hi + M);
   j.dt = dt; j.T = T; j.W = windows; j.D = D; j.N = N; j.P = M + (windows - 1) * 2 * n;
+  j.sigma_obs = sigma_obs; j.sigma_def = sigma_def; j.c_lim = c_lim; j.lr = lr; j.iterations = iterations;
+  j.x0.assign(particles, particles + (size_t)j.P * N);
+  j.bytes = bytes;
+  j.state = PDS_JOB_QUEUED;
+  *job_id = j.id;
+  s->queue.push_back(j.id);
+  s->jobs.emplace(j.id, std::move(j));
+  return PDS_OK;
+}
+
+int pds_server_submit_armbox(pds_server_t s, const pds_armbox_desc* sys, double dt, int T, int windows,
+                             const float* obs, int D, const int* obs_index, double sigma_obs, double sigma_def,
+                             const float* s0, const float* theta_lo, const float* theta_hi, double c_lim, int N,
+                             const float* particles, double lr, int iterations, long long* job_id) {
+  if (!s || !sys || !sys->arm_len || !sys->amp || !sys->freq || !sys->phase || !obs || !obs_index || !s0 ||
+      !theta_lo || !theta_hi || !particles || !job_id)
+    return set_error(PDS_ERR_ARG, "NULL argument");
+  *job_id = 0;
+  const int na = sys->n_arm;
+  if (na < 1 || na > PDS_MAX_LINKS || T < 1 || windows < 1 || windows > T || D < 1 || D > 4 || N < 1 ||
+      N > 65536 || iterations < 1 || !(lr > 0.0))
+    return set_error(PDS_ERR_ARG, "job outside the supported sizes");
+  const size_t bytes = job_bytes(2, 4, T, windows, D, N, s->K) + (size_t)T * 9 * 4;
+  if (bytes > s->budget) return set_error(PDS_ERR_BUDGET, "job needs more device memory than the server budget");
+  Job j;
+  j.id = s->next_id++;
+  j.kind = PDS_SYSTEM_ARM_BOX;
+  j.arm = *sys;
+  j.arm_len.assign(sys->arm_len, sys->arm_len + na);
+  j.amp.assign(sys->amp, sys->amp + 3 * na);
+  j.freq.assign(sys->freq, sys->freq + 3 * na);
+  j.phase.assign(sys->phase, sys->phase + 3 * na);
+  j.obs_index.assign(obs_index, obs_index + D);
+  j.obs.assign(obs, obs + (size_t)T * D);
+  j.s0.assign(s0, s0 + 4);
+  j.lo.assign(theta_lo, theta_lo + 4);
+  j.hi.assign(theta_hi, theta_hi + 4);
+  j.dt = dt; j.T = T; j.W = windows; j.D = D; j.N = N; j.P = 4 + (windows - 1) * 4;
   j.sigma_obs = sigma_obs; j.sigma_def = sigma_def; j.c_lim = c_lim; j.lr = lr; j.iterations = iterations;
   j.x0.assign(particles, particles + (size_t)j.P * N);
   j.bytes = bytes;

@@ -345,3 +345,17 @@ def arm_box(N: int = 2048, seed: int = 3000, T: int = 2000, W: int = 40, n_arm: 
                           theta_true=theta_true, lo=lo, hi=hi, dt=0.002, T=T, W=W, obs_index=obs_index,
                           sigma_obs=0.01, sigma_def=SIGMA_DEF, s0=np.zeros(4), noise=noise, theta_init=theta_init,
                           seed=seed)
+
+
+def serving_mix(n_jobs: int, seed: int = 5000, armbox_fraction: float = 0.1, armbox_N: int = 512):
+    """Jobs of the serving workload: uneven chain problems, with a fraction of
+    arm-shaking-a-box jobs at armbox_N particles (T = 2000, W = 40)."""
+    rng = np.random.default_rng(seed)
+    chains = batched_problems(n_jobs=n_jobs, seed=seed)
+    out = []
+    for j in range(n_jobs):
+        if rng.uniform() < armbox_fraction:
+            out.append(arm_box(N=armbox_N, seed=seed + 7919 * (j + 1)))
+        else:
+            out.append(chains[j])
+    return out

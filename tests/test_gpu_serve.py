@@ -105,3 +105,20 @@ def test_admission_by_memory_budget():
     for r in results[1:]:
         np.testing.assert_array_equal(r, results[0])   # same job, same result, whenever it ran
     srv.close()
+
+
+def test_armbox_job_in_the_mix_equals_alone():
+    jobs = _jobs(3, seed=55, iters=3, T_range=(30, 90), W_range=(2, 5), N_range=(30, 200))
+    wl = wlmod.arm_box(N=256, seed=77, T=200, W=5)
+    from oracle import pds_oracle as orc
+    st = orc.ArmBox.from_workload(wl).simulate(wl.theta_true, wl.dt, wl.T, wl.s0)
+    obs = (st[1:, wl.obs_index] + wl.sigma_obs * wl.noise[:wl.T]).astype(np.float32)
+    shoot = st[[wl.window_start(w) for w in range(1, wl.W)]].ravel()
+    x = np.concatenate([wl.theta_init, np.tile(shoot, (wl.N, 1))], 1)
+    jobs.insert(1, (wl, obs, x, 3))
+    arrivals = np.array([0.0, 0.0, 0.005, 0.01])
+    _, res, _ = serve.run_server(jobs, arrivals, mem_budget=8 << 30)
+    _, alone, _ = serve.run_plain(jobs, np.zeros(len(jobs)))
+    for k, (w, _, _, _) in enumerate(jobs):
+        width = np.concatenate([w.hi - w.lo, np.ones(w.P - w.M)])
+        assert np.max(np.abs(res[k][0] - alone[k][0]) / width) <= 1e-5, k
