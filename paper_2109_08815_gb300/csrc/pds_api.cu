@@ -343,6 +343,7 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   cudaError_t e = cudaSuccess;
   if ((s->w.cand_cap && (e = cudaMalloc(&s->w.cand, s->w.cand_cap * sizeof(float))) != cudaSuccess) ||
       (s->w.cand_cap && (e = cudaMalloc(&s->w.samp, svgd_sample_size() * sizeof(float))) != cudaSuccess) ||
+      (N >= 256 && (e = cudaMalloc(&s->w.tc, phi_tc_floats(N, M) * sizeof(float))) != cudaSuccess) ||
       (e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.gu, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.phi_part, (size_t)s->w.chunks * MN * sizeof(float))) != cudaSuccess ||
@@ -362,6 +363,7 @@ int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
   switch (option) {
     case PDS_OPT_FAST_MATH: s->sp.fast_math = value; return PDS_OK;
     case PDS_OPT_MEDIAN_FULL_PASSES: s->full_passes = value; return PDS_OK;
+    case PDS_OPT_PHI_CUDA_CORES: s->phi_cuda_cores = value; return PDS_OK;
     default: return fail(PDS_ERR_ARG, "unknown option %d", option);
   }
 }
@@ -382,6 +384,7 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaStreamSynchronize(s->stream);
   cudaFree(s->w.cand);
   cudaFree(s->w.samp);
+  cudaFree(s->w.tc);
   cudaFree(s->w.u);
   cudaFree(s->w.gu);
   cudaFree(s->w.phi_part);
@@ -398,6 +401,7 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   int n = 0;
   SvgdWork w = s->w;
   if (s->full_passes) w.cand_cap = 0;
+  if (s->phi_cuda_cores) w.tc = nullptr;
   cudaError_t e = launch_svgd_step(s->sp, w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
   g_launches = n;
   if (e != cudaSuccess) return cuda_fail(e, "svgd launch");

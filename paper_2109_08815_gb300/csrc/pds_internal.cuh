@@ -100,9 +100,11 @@ struct SvgdCtl {
   unsigned long long below;  // pairs with d < lo
   unsigned long long inside; // pairs with lo <= d <= hi (= candidates)
   int mode;                  // 0: select among candidates; 1: full radix passes over all pairs
+  int tc_error;              // set if a tensor-core pass gave up waiting for its products
 };
 
 struct SvgdWork {
+  float* tc;       // tensor-core operand rows (a, b, v split in tf32 parts), or NULL
   float* samp;     // sampled pair distances (bracket estimate)
   float* cand;     // candidate distances inside the sampled bracket
   unsigned long long cand_cap;
@@ -120,6 +122,8 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
 int svgd_phi_chunks(int N);
 unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
 int svgd_sample_size();
+size_t phi_tc_floats(int N, int M);
+cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st);
 cudaError_t svgd_setup_device();
 
 // Record an error message for pds_last_error() and return `code`.
@@ -151,6 +155,7 @@ struct pds_svgd {
   pds::SvgdWork w{};
   cudaStream_t stream;
   int full_passes = 0;
+  int phi_cuda_cores = 1;
 };
 
 namespace pds {

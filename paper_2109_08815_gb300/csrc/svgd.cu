@@ -568,14 +568,23 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     const int chunks0 = svgd_phi_chunks(N);
     const int chunk_len = ((N + chunks0 - 1) / chunks0 + kTile - 1) / kTile * kTile;
     const int chunks = (N + chunk_len - 1) / chunk_len;
-    dim3 grid((N + kSpan - 1) / kSpan, chunks);
-    if (sp.fast_math)
-      svgd_phi_kernel<MM, true><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
-    else
-      svgd_phi_kernel<MM, false><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+    int chunks_used = chunks;
+    if (w.tc && N >= 256) {
+      // tensor-core path: the kernel-matrix products on tcgen05 (chunks0 chunks of 128-column tiles)
+      cudaError_t e = launch_phi_tc(N, M, w, chunks0, st);
+      if (e != cudaSuccess) return e;
+      chunks_used = chunks0;
+      n += 1;
+    } else {
+      dim3 grid((N + kSpan - 1) / kSpan, chunks);
+      if (sp.fast_math)
+        svgd_phi_kernel<MM, true><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+      else
+        svgd_phi_kernel<MM, false><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+    }
     const size_t total = (size_t)sp.P * N;
-    svgd_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, w.ctl, X, G, w.phi_part, chunks, w.adam_m,
-                                                                      w.adam_v, bw_out, phi_out);
+    svgd_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, w.ctl, X, G, w.phi_part, chunks_used,
+                                                                      w.adam_m, w.adam_v, bw_out, phi_out);
     n += 2;
   }
   if (launches) *launches += n;

@@ -41,13 +41,20 @@ def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2, fast=False):
         bw, phi = sv.step(X, G, return_phi=True)
         phi_ref, bw_ref = ost.step(xo, g)
     torch.cuda.synchronize()
-    assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref, (bw.item(), bw_ref)
+    # after several steps the two particle sets differ by the rare sign flips
+    # below, which moves the median slightly
+    assert abs(bw.item() - bw_ref) <= (1e-5 if steps == 1 else 1e-3) * bw_ref, (bw.item(), bw_ref)
     phi = phi.cpu().numpy().T
     scale = np.max(np.abs(phi_ref))
     assert np.max(np.abs(phi - phi_ref)) <= 2e-3 * scale, np.max(np.abs(phi - phi_ref)) / scale
     xg = X.cpu().numpy().T
     width = np.concatenate([hi - lo, np.ones(P - M)])
-    assert np.max(np.abs(xg - xo) / width) <= 1e-4 * steps, np.max(np.abs(xg - xo) / width)
+    dx = np.abs(xg - xo) / width
+    # Adam's first steps move each entry by about lr * sign(direction): entries
+    # agree to rounding except where the FP32 and FP64 directions straddle
+    # zero, which must stay rare
+    assert np.mean(dx > 1e-4 * steps) <= 2e-3, np.mean(dx > 1e-4 * steps)
+    assert dx.max() <= 2.5 * lr * steps, dx.max()
 
 
 @pytest.mark.parametrize("fast", [False, True])
@@ -164,3 +171,24 @@ def test_sampled_bracket_median_equals_full_passes(kind):
         d = ((u[:, None, :] - u[None, :, :]) ** 2).sum(-1)[np.triu_indices(N, 1)]
         med = np.partition(d, (len(d) - 1) // 2)[(len(d) - 1) // 2]
         assert abs(b_full - med / np.log(N)) <= 1e-6 * med / np.log(N)
+
+
+@pytest.mark.parametrize("N,M", [(256, 1), (300, 4), (1000, 10), (777, 16), (4096, 10), (2500, 8)])
+def test_tensor_core_phi_matches_cuda_cores(N, M):
+    """phi's kernel-matrix products on tcgen05 (split tf32 operands, fp32
+    accumulation; the kernel values themselves rounded to tf32) against the
+    fp32 CUDA-core kernel."""
+    lo, hi, x, g = _case(N, M, M + 3, seed=N + M)
+    out = []
+    for cuda_cores in (1, 0):
+        sv = api.Svgd(N, M, M + 3, lo, hi)
+        sv.set_option(api.OPT_PHI_CUDA_CORES, cuda_cores)
+        bw, phi = sv.step(_gpu(x), _gpu(g), return_phi=True)
+        torch.cuda.synchronize()
+        out.append((bw.item(), phi.cpu().numpy().T))
+        sv.close()
+    assert out[0][0] == out[1][0]
+    ref, tcp = out[0][1], out[1][1]
+    # the kernel values enter the second product rounded to tf32 (relative
+    # 2^-11 at most, unbiased): about 1e-4 of the largest |phi|
+    assert np.max(np.abs(tcp - ref)) <= 1e-3 * np.max(np.abs(ref)), np.max(np.abs(tcp - ref)) / np.max(np.abs(ref))
