@@ -200,9 +200,9 @@ int pds_svgd_destroy(pds_svgd_t s);
  * (default) = for N >= 2048 bracket the median from a sample of pairs and
  * select among the pairs inside the bracket (falling back to the full passes
  * if the bracket misses); 1 = always three radix passes over all pairs.
- * Both give the same exact median.  PDS_OPT_PHI_CUDA_CORES 0 = for N >= 256
- * the kernel-matrix products of phi run on the tensor cores (tcgen05, tf32
- * with split operands, fp32 accumulation); 1 (default) = CUDA cores. */
+ * Both give the same exact median.  PDS_OPT_PHI_CUDA_CORES 0 (default) = for
+ * N >= 256 the kernel-matrix products of phi run on the tensor cores
+ * (tcgen05, tf32 with split operands, fp32 accumulation); 1 = CUDA cores. */
 #define PDS_OPT_MEDIAN_FULL_PASSES 3
 #define PDS_OPT_PHI_CUDA_CORES 4
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);

@@ -155,7 +155,7 @@ struct pds_svgd {
   pds::SvgdWork w{};
   cudaStream_t stream;
   int full_passes = 0;
-  int phi_cuda_cores = 1;
+  int phi_cuda_cores = 0;
 };
 
 namespace pds {

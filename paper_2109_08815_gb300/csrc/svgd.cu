@@ -254,29 +254,68 @@ __global__ void __launch_bounds__(256) median_sample_dist_kernel(int N, int M, c
   samp[s] = d;
 }
 
-// Sort the sample in shared memory (bitonic, one block) and keep the two
-// order statistics that bracket the median.
+// The two order statistics of the sample that bracket the median, by a
+// radix select in one block (three passes of 11, 11 and 10 bits; both ranks
+// resolved together with one histogram each).
 __global__ void __launch_bounds__(kSampleThreads) median_sample_sort_kernel(const float* __restrict__ samp,
                                                                             SvgdCtl* __restrict__ ctl) {
-  extern __shared__ float smp[];  // kSample floats
-  for (int s = threadIdx.x; s < kSample; s += kSampleThreads) smp[s] = samp[s];
-  __syncthreads();
-  for (int k = 2; k <= kSample; k <<= 1) {
-    for (int jd = k >> 1; jd > 0; jd >>= 1) {
-      for (int idx = threadIdx.x; idx < kSample; idx += kSampleThreads) {
-        const int ixj = idx ^ jd;
-        if (ixj > idx) {
-          const float a = smp[idx], b = smp[ixj];
-          const bool up = (idx & k) == 0;
-          if ((a > b) == up) { smp[idx] = b; smp[ixj] = a; }
-        }
+  constexpr int kPer = kSample / kSampleThreads;
+  __shared__ unsigned int hist[2][kHistBins];
+  __shared__ unsigned int prefix[2], rank[2];
+  unsigned int v[kPer];
+#pragma unroll
+  for (int k = 0; k < kPer; ++k) v[k] = __float_as_uint(samp[threadIdx.x + k * kSampleThreads]);
+  if (threadIdx.x < 2) {
+    prefix[threadIdx.x] = 0u;
+    rank[threadIdx.x] = threadIdx.x == 0 ? (unsigned)(kSample / 2 - kSampleMargin) : (unsigned)(kSample / 2 + kSampleMargin);
+  }
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int b = threadIdx.x; b < 2 * kHistBins; b += kSampleThreads) hist[b / kHistBins][b % kHistBins] = 0u;
+    __syncthreads();
+    const unsigned int shift = pass == 0 ? 21u : pass == 1 ? 10u : 0u;
+    const unsigned int mask = pass == 2 ? 1023u : 2047u;
+    const unsigned int hi_shift = pass == 0 ? 32u : pass == 1 ? 21u : 10u;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const unsigned int pf = prefix[q];
+#pragma unroll
+      for (int k = 0; k < kPer; ++k) {
+        const bool match = hi_shift == 32u || (v[k] >> hi_shift) == pf;
+        if (match) atomicAdd(&hist[q][(v[k] >> shift) & mask], 1u);
       }
-      __syncthreads();
     }
+    __syncthreads();
+    // warp q resolves order statistic q
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+      const unsigned int* h = hist[warp];
+      unsigned int local = 0u;
+      for (int b = 0; b < 64; ++b) local += h[lane * 64 + b];
+      unsigned int incl = local;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      const unsigned int excl = incl - local;
+      const unsigned int r = rank[warp];
+      if (r >= excl && r < incl) {
+        unsigned int cum = excl;
+        int bin = lane * 64;
+        for (int b = 0; b < 64; ++b) {
+          const unsigned int c = h[lane * 64 + b];
+          if (r < cum + c) { bin = lane * 64 + b; break; }
+          cum += c;
+        }
+        rank[warp] = r - cum;
+        prefix[warp] = (prefix[warp] << (pass == 2 ? 10u : 11u)) | (unsigned int)bin;
+      }
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    ctl->lo = smp[kSample / 2 - kSampleMargin];
-    ctl->hi = smp[kSample / 2 + kSampleMargin];
+    ctl->lo = __uint_as_float(prefix[0]);
+    ctl->hi = __uint_as_float(prefix[1]);
   }
 }
 
@@ -396,21 +435,9 @@ __global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __re
 
 int svgd_sample_size() { return kSample; }
 
-// 64 KiB of dynamic shared memory for the sample sort: opt in once per
-// device (before any stream capture that launches it).
-cudaError_t svgd_setup_device() {
-  static bool smem_ok[64];
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64 && !smem_ok[dev]) {
-    e = cudaFuncSetAttribute(median_sample_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(kSample * sizeof(float)));
-    if (e != cudaSuccess) return e;
-    smem_ok[dev] = true;
-  }
-  return cudaSuccess;
-}
+// One-time per-device set-up of the SVGD kernels (none needed at present;
+// kept as the place to do it before any stream capture).
+cudaError_t svgd_setup_device() { return cudaSuccess; }
 
 unsigned long long svgd_cand_capacity(int N) {
   if (N < 2048) return 0ull;
@@ -545,7 +572,7 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
       cudaError_t e = svgd_setup_device();
       if (e != cudaSuccess) return e;
       median_sample_dist_kernel<MM><<<kSample / 256, 256, 0, st>>>(N, M, w.u, w.samp);
-      median_sample_sort_kernel<<<1, kSampleThreads, kSample * sizeof(float), st>>>(w.samp, w.ctl);
+      median_sample_sort_kernel<<<1, kSampleThreads, 0, st>>>(w.samp, w.ctl);
       n += 1;
       median_bracket_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, w.cand, w.cand_cap);
       median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);

@@ -38,14 +38,26 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = __uint_as_float(tc::to_tf32(x - hi));
 }
 
-// Operand rows for every particle (rows N .. Npad-1 are zero: their v is 0,
-// so they add nothing).
+template <int MM>
+struct TcSmem {
+  static constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
+  static constexpr int kA = kTcRows * KA * 4;   // one operand tile (128 rows x KA), bytes
+  static constexpr int kV = NV * kTcRows * 4;   // one v^T tile, bytes
+  static constexpr int kStage = 2 * kA + 2 * kV;  // b (hi, lo) + v^T (hi, lo) of one column tile
+  static constexpr int kBytes = 2 * kA + 2 * kStage + 128;
+};
+
+// Operand tiles for every particle, written directly in the shared-memory
+// image the products read (K-major core-matrix layout), one image per tile
+// of 128 particles: imgA[tile] = (a hi, a lo), imgBV[tile] = (b hi, b lo,
+// v^T hi, v^T lo).  Rows N .. Npad-1 are zero (their v is 0, so they add
+// nothing).
 template <int MM>
 __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restrict__ u, const float* __restrict__ gu,
-                                   const SvgdCtl* __restrict__ ctl, float* __restrict__ ah, float* __restrict__ al,
-                                   float* __restrict__ bh, float* __restrict__ bl, float* __restrict__ vh,
-                                   float* __restrict__ vl) {
+                                   const SvgdCtl* __restrict__ ctl, float* __restrict__ imgA,
+                                   float* __restrict__ imgBV) {
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
+  using SM = TcSmem<MM>;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= Npad) return;
   float x[MM], g[MM];
@@ -59,59 +71,49 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
     g[k] = on ? gu[(size_t)k * N + j] : 0.f;
     n = fmaf(x[k], x[k], n);
   }
-  float a[KA], b[KA], v[NV];
+  const int tile = j / kTcRows, r = j % kTcRows;
+  float* A = imgA + (size_t)tile * (2 * SM::kA / 4);
+  float* BV = imgBV + (size_t)tile * (SM::kStage / 4);
+  float* Bh = BV;
+  float* Bl = BV + SM::kA / 4;
+  float* Vh = BV + 2 * SM::kA / 4;
+  float* Vl = BV + 2 * SM::kA / 4 + SM::kV / 4;
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
-    a[k] = k < MM ? 2.f * L * x[k] : (k == MM ? -L * n : (k == MM + 1 ? -L : 0.f));
-    b[k] = k < MM ? x[k] : (k == MM ? (live ? 1.f : 0.f) : (k == MM + 1 ? n : 0.f));
+    const float a = k < MM ? 2.f * L * x[k] : (k == MM ? -L * n : (k == MM + 1 ? -L : 0.f));
+    const float b = k < MM ? x[k] : (k == MM ? (live ? 1.f : 0.f) : (k == MM + 1 ? n : 0.f));
+    const uint32_t o = tc::kmajor_offset(r, k, KA) >> 2;
+    float h, l;
+    split_tf32(a, h, l);
+    A[o] = h;
+    A[SM::kA / 4 + o] = l;
+    split_tf32(b, h, l);
+    Bh[o] = h;
+    Bl[o] = l;
   }
 #pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = k < MM ? g[k] : (k < 2 * MM ? x[k - MM] : (k == 2 * MM && live ? 1.f : 0.f));
-#pragma unroll
-  for (int k = 0; k < KA; ++k) {
+  for (int c = 0; c < NV; ++c) {
+    const float v = c < MM ? g[c] : (c < 2 * MM ? x[c - MM] : (c == 2 * MM && live ? 1.f : 0.f));
+    const uint32_t o = tc::kmajor_offset(c, r, kTcRows) >> 2;
     float h, l;
-    split_tf32(a[k], h, l);
-    ah[(size_t)j * KA + k] = h;
-    al[(size_t)j * KA + k] = l;
-    split_tf32(b[k], h, l);
-    bh[(size_t)j * KA + k] = h;
-    bl[(size_t)j * KA + k] = l;
-  }
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    float h, l;
-    split_tf32(v[k], h, l);
-    vh[(size_t)j * NV + k] = h;
-    vl[(size_t)j * NV + k] = l;
+    split_tf32(v, h, l);
+    Vh[o] = h;
+    Vl[o] = l;
   }
 }
 
 template <int MM>
-struct TcSmem {
-  static constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
-  static constexpr int kA = kTcRows * KA * 4;   // one operand tile of rows x KA
-  static constexpr int kV = NV * kTcRows * 4;   // v^T tile
-  static constexpr int kBytes = 4 * kA + 2 * kV + 64;
-};
-
-template <int MM>
-__global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, const float* __restrict__ ah,
-                                                        const float* __restrict__ al, const float* __restrict__ bh,
-                                                        const float* __restrict__ bl, const float* __restrict__ vh,
-                                                        const float* __restrict__ vl, const float* __restrict__ u,
+__global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, const float* __restrict__ imgA,
+                                                        const float* __restrict__ imgBV, const float* __restrict__ u,
                                                         SvgdCtl* __restrict__ ctl, float* __restrict__ phi_part,
                                                         int tiles_per_chunk) {
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   using SM = TcSmem<MM>;
   extern __shared__ __align__(1024) unsigned char smem[];
-  float* sAh = (float*)(smem);
-  float* sAl = (float*)(smem + SM::kA);
-  float* sBh = (float*)(smem + 2 * SM::kA);
-  float* sBl = (float*)(smem + 3 * SM::kA);
-  float* sVh = (float*)(smem + 4 * SM::kA);
-  float* sVl = (float*)(smem + 4 * SM::kA + SM::kV);
-  uint64_t* mbar = (uint64_t*)(smem + 4 * SM::kA + 2 * SM::kV);
-  uint32_t* tslot = (uint32_t*)(smem + 4 * SM::kA + 2 * SM::kV + 16);
+  unsigned char* sA = smem;                              // a hi | a lo
+  unsigned char* sStage[2] = {smem + 2 * SM::kA, smem + 2 * SM::kA + SM::kStage};
+  uint64_t* bars = (uint64_t*)(smem + 2 * SM::kA + 2 * SM::kStage);  // full[0], full[1], a, mma
+  uint32_t* tslot = (uint32_t*)(bars + 4);
 
   const int t = threadIdx.x, warp = t >> 5;
   const int i0 = blockIdx.x * kTcRows;
@@ -120,58 +122,55 @@ __global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, 
   const int jt1 = min(ntiles, jt0 + tiles_per_chunk);
   const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
 
-  // this CTA's rows of a (the exponent product's A operand)
-#pragma unroll
-  for (int k = 0; k < KA; ++k) {
-    const uint32_t o = tc::kmajor_offset(t, k, KA) >> 2;
-    sAh[o] = ah[(size_t)(i0 + t) * KA + k];
-    sAl[o] = al[(size_t)(i0 + t) * KA + k];
+  if (t == 0) {
+    for (int b = 0; b < 4; ++b) tc::mbar_init(bars + b, 1);
   }
-  if (t == 0) tc::mbar_init(mbar, 1);
   if (warp == 0) tc::tmem_alloc(tslot, 256);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
   const uint32_t tE = tbase, tO = tbase + 128;
-  uint32_t phase = 0;
+
+  // prologue: this CTA's a tile and the first two column tiles
+  if (t == 0 && jt1 > jt0) {
+    tc::mbar_expect_tx(bars + 2, 2 * SM::kA);
+    tc::bulk_g2s(sA, imgA + (size_t)blockIdx.x * (2 * SM::kA / 4), 2 * SM::kA, bars + 2);
+    for (int s = 0; s < 2 && jt0 + s < jt1; ++s) {
+      tc::mbar_expect_tx(bars + s, SM::kStage);
+      tc::bulk_g2s(sStage[s], imgBV + (size_t)(jt0 + s) * (SM::kStage / 4), SM::kStage, bars + s);
+    }
+  }
   bool ok = true;
+  if (jt1 > jt0) ok = __syncthreads_and(tc::mbar_wait(bars + 2, 0, 1 << 24)) != 0;
+  uint32_t ph_full[2] = {0u, 0u}, ph_mma = 0u;
 
   for (int jt = jt0; jt < jt1 && ok; ++jt) {
-    const int j0 = jt * kTcRows;
-    // stage b (rows j) and v^T of this tile
-#pragma unroll
-    for (int k = 0; k < KA; ++k) {
-      const uint32_t o = tc::kmajor_offset(t, k, KA) >> 2;
-      sBh[o] = bh[(size_t)(j0 + t) * KA + k];
-      sBl[o] = bl[(size_t)(j0 + t) * KA + k];
-    }
-#pragma unroll
-    for (int c = 0; c < NV; ++c) {
-      const uint32_t o = tc::kmajor_offset(c, t, kTcRows) >> 2;
-      sVh[o] = vh[(size_t)(j0 + t) * NV + c];
-      sVl[o] = vl[(size_t)(j0 + t) * NV + c];
-    }
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
+    const int s = (jt - jt0) & 1;
+    ok = __syncthreads_and(tc::mbar_wait(bars + s, ph_full[s], 1 << 24)) != 0;
+    ph_full[s] ^= 1;
+    if (!ok) break;
+    const unsigned char* sB = sStage[s];
+    const unsigned char* sV = sStage[s] + 2 * SM::kA;
     // exponents E = a b^T (three split products)
     if (t == 0) {
       tc::fence_after();
       constexpr uint32_t id = tc::idesc_tf32(128, 128);
       const uint32_t sbo = 32 * KA;
-      const float* Aop[3] = {sAh, sAh, sAl};
-      const float* Bop[3] = {sBh, sBl, sBh};
+      const uint32_t a_h = tc::smem_u32(sA), a_l = a_h + SM::kA;
+      const uint32_t b_h = tc::smem_u32(sB), b_l = b_h + SM::kA;
+      const uint32_t Aop[3] = {a_h, a_h, a_l};
+      const uint32_t Bop[3] = {b_h, b_l, b_h};
 #pragma unroll
       for (int p = 0; p < 3; ++p)
 #pragma unroll
         for (int ks = 0; ks < KA / 8; ++ks)
-          tc::mma_ss(tE, tc::smem_desc(tc::smem_u32(Aop[p]) + ks * 256, 128, sbo),
-                     tc::smem_desc(tc::smem_u32(Bop[p]) + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
-      tc::mma_commit(mbar);
+          tc::mma_ss(tE, tc::smem_desc(Aop[p] + ks * 256, 128, sbo), tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id,
+                     (p > 0 || ks > 0) ? 1u : 0u);
+      tc::mma_commit(bars + 3);
     }
-    ok = __syncthreads_and(tc::mbar_wait(mbar, phase, 1 << 24)) != 0;
-    phase ^= 1;
+    ok = __syncthreads_and(tc::mbar_wait(bars + 3, ph_mma, 1 << 24)) != 0;
+    ph_mma ^= 1;
     tc::fence_after();
     if (!ok) break;
     // kernel values k = 2^E, rounded to tf32, written back in place
@@ -187,27 +186,31 @@ __global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, 
     tc::tmem_wait_st();
     tc::fence_before();
     __syncthreads();
-    // O += K v (v split in two)
+    // O += K v (v split in two); then refill this stage with tile jt + 2
     if (t == 0) {
       tc::fence_after();
       constexpr uint32_t id = tc::idesc_tf32(128, NV);
       const uint32_t sbo = 32 * kTcRows;
+      const uint32_t v_h = tc::smem_u32(sV), v_l = v_h + SM::kV;
 #pragma unroll
       for (int ks = 0; ks < kTcRows / 8; ++ks)
-        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(tc::smem_u32(sVh) + ks * 256, 128, sbo), id,
-                   (jt > jt0 || ks > 0) ? 1u : 0u);
+        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_h + ks * 256, 128, sbo), id, (jt > jt0 || ks > 0) ? 1u : 0u);
 #pragma unroll
       for (int ks = 0; ks < kTcRows / 8; ++ks)
-        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(tc::smem_u32(sVl) + ks * 256, 128, sbo), id, 1u);
-      tc::mma_commit(mbar);
+        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_l + ks * 256, 128, sbo), id, 1u);
+      tc::mma_commit(bars + 3);
     }
-    ok = __syncthreads_and(tc::mbar_wait(mbar, phase, 1 << 24)) != 0;  // tiles and E free again
-    phase ^= 1;
+    ok = __syncthreads_and(tc::mbar_wait(bars + 3, ph_mma, 1 << 24)) != 0;
+    ph_mma ^= 1;
     tc::fence_after();
+    if (t == 0 && ok && jt + 2 < jt1) {
+      tc::mbar_expect_tx(bars + s, SM::kStage);
+      tc::bulk_g2s(sStage[s], imgBV + (size_t)(jt + 2) * (SM::kStage / 4), SM::kStage, bars + s);
+    }
   }
 
-  if (ok && jt1 > jt0) {
-    // O row of this thread: columns [0, NV)
+  const int i = i0 + t;
+  if (jt1 > jt0 && ok) {
     float o[64];
 #pragma unroll
     for (int c0 = 0; c0 < NV; c0 += 32) {
@@ -217,7 +220,6 @@ __global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, 
 #pragma unroll
       for (int k = 0; k < 32; ++k) o[c0 + k] = __uint_as_float(r[k]);
     }
-    const int i = i0 + t;
     if (i < N) {
       const float two_over_bw = 2.0f / ctl->bw;
       const float o1 = o[2 * MM];
@@ -229,14 +231,11 @@ __global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, 
         }
       }
     }
-  } else if (jt1 > jt0 && t == 0) {
-    ctl->tc_error = 1;
-  }
-  if (jt1 <= jt0) {
-    // empty chunk: contribute zeros
-    const int i = i0 + t;
-    if (i < N)
-      for (int k = 0; k < M; ++k) phi_part[((size_t)blockIdx.y * M + k) * N + i] = 0.f;
+  } else if (jt1 > jt0) {
+    if (t == 0) ctl->tc_error = 1;
+  } else if (i < N) {
+    // empty chunk: contributes zeros
+    for (int k = 0; k < M; ++k) phi_part[((size_t)blockIdx.y * M + k) * N + i] = 0.f;
   }
   tc::fence_before();
   __syncthreads();
@@ -245,19 +244,14 @@ __global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, 
 
 template <int MM>
 static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st) {
+  using SM = TcSmem<MM>;
   const int Npad = (N + kTcRows - 1) / kTcRows * kTcRows;
   const int ntiles = Npad / kTcRows;
   const int tiles_per_chunk = (ntiles + chunks - 1) / chunks;
-  constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
-  float* ah = w.tc;
-  float* al = ah + (size_t)Npad * KA;
-  float* bh = al + (size_t)Npad * KA;
-  float* bl = bh + (size_t)Npad * KA;
-  float* vh = bl + (size_t)Npad * KA;
-  float* vl = vh + (size_t)Npad * NV;
-  phi_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, w.u, w.gu, w.ctl, ah, al, bh, bl, vh, vl);
-  // at most two CTAs per SM: their tensor-memory allocations (256 columns each) always fit
-  const int smem = TcSmem<MM>::kBytes < 100 * 1024 ? 100 * 1024 : TcSmem<MM>::kBytes;
+  float* imgA = w.tc;
+  float* imgBV = imgA + (size_t)ntiles * (2 * SM::kA / 4);
+  phi_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, w.u, w.gu, w.ctl, imgA, imgBV);
+  const int smem = SM::kBytes;
   static bool attr[64];
   int dev = 0;
   cudaGetDevice(&dev);
@@ -267,8 +261,7 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int chunks,
     attr[dev] = true;
   }
   dim3 grid(ntiles, chunks);
-  phi_tc_kernel<MM><<<grid, 128, smem, st>>>(N, Npad, M, ah, al, bh, bl, vh, vl, w.u, w.ctl, w.phi_part,
-                                             tiles_per_chunk);
+  phi_tc_kernel<MM><<<grid, 128, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, tiles_per_chunk);
   return cudaGetLastError();
 }
 
