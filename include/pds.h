@@ -205,6 +205,10 @@ int pds_svgd_destroy(pds_svgd_t s);
  * (tcgen05, tf32 with split operands, fp32 accumulation); 1 = CUDA cores. */
 #define PDS_OPT_MEDIAN_FULL_PASSES 3
 #define PDS_OPT_PHI_CUDA_CORES 4
+/* PDS_OPT_MEDIAN_CUDA_CORES 0 (default) = for N >= 2048 the pair distances of
+ * the median passes come from tensor-core products (split tf32, fp32
+ * accumulation, clamped at 0); 1 = CUDA cores. */
+#define PDS_OPT_MEDIAN_CUDA_CORES 5
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);
 
 /* One SVGD + Adam update in place.

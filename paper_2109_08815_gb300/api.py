@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libpds.so")
 
 PDS_SYSTEM_PLANAR_CHAIN = 1
 PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
-OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES = 1, 2, 3, 4
+OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES, OPT_MEDIAN_CUDA_CORES = 1, 2, 3, 4, 5
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
 
 _lib = None

@@ -192,6 +192,7 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     SvgdWork w = s->w;
     if (s->full_passes) w.cand_cap = 0;
     if (s->phi_cuda_cores) w.tc = nullptr;
+    if (s->median_cuda_cores) w.mimg = nullptr;
     int k = 0;
     if ((e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k)) != cudaSuccess) return e;
     n += 1 + k;

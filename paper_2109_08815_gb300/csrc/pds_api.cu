@@ -8,6 +8,7 @@
 #include <string.h>
 
 #include <string>
+#include <vector>
 
 #include "pds_internal.cuh"
 
@@ -344,6 +345,7 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   if ((s->w.cand_cap && (e = cudaMalloc(&s->w.cand, s->w.cand_cap * sizeof(float))) != cudaSuccess) ||
       (s->w.cand_cap && (e = cudaMalloc(&s->w.samp, svgd_sample_size() * sizeof(float))) != cudaSuccess) ||
       (N >= 256 && (e = cudaMalloc(&s->w.tc, phi_tc_floats(N, M) * sizeof(float))) != cudaSuccess) ||
+      (N >= 2048 && (e = cudaMalloc(&s->w.mimg, median_tc_floats(N, M) * sizeof(float))) != cudaSuccess) ||
       (e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.gu, MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.phi_part, (size_t)s->w.chunks * MN * sizeof(float))) != cudaSuccess ||
@@ -352,6 +354,19 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
       (e = cudaMalloc(&s->w.ctl, sizeof(SvgdCtl))) != cudaSuccess) {
     pds_svgd_destroy(s);
     return cuda_fail(e, "svgd allocation");
+  }
+  if (N >= 2048) {
+    const int chunk = 8;  // column tiles per work item
+    const int n_items = median_tc_work_items(N, chunk, nullptr);
+    std::vector<int> items(3 * (size_t)n_items);
+    median_tc_work_items(N, chunk, items.data());
+    if ((e = cudaMalloc(&s->w.mwork, items.size() * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemcpy(s->w.mwork, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+      pds_svgd_destroy(s);
+      return cuda_fail(e, "svgd allocation");
+    }
+    s->w.n_mwork = n_items;
   }
   *out = s;
   return pds_svgd_reset(s);
@@ -364,6 +379,7 @@ int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
     case PDS_OPT_FAST_MATH: s->sp.fast_math = value; return PDS_OK;
     case PDS_OPT_MEDIAN_FULL_PASSES: s->full_passes = value; return PDS_OK;
     case PDS_OPT_PHI_CUDA_CORES: s->phi_cuda_cores = value; return PDS_OK;
+    case PDS_OPT_MEDIAN_CUDA_CORES: s->median_cuda_cores = value; return PDS_OK;
     default: return fail(PDS_ERR_ARG, "unknown option %d", option);
   }
 }
@@ -385,6 +401,8 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaFree(s->w.cand);
   cudaFree(s->w.samp);
   cudaFree(s->w.tc);
+  cudaFree(s->w.mimg);
+  cudaFree(s->w.mwork);
   cudaFree(s->w.u);
   cudaFree(s->w.gu);
   cudaFree(s->w.phi_part);
@@ -402,6 +420,7 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   SvgdWork w = s->w;
   if (s->full_passes) w.cand_cap = 0;
   if (s->phi_cuda_cores) w.tc = nullptr;
+  if (s->median_cuda_cores) w.mimg = nullptr;
   cudaError_t e = launch_svgd_step(s->sp, w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
   g_launches = n;
   if (e != cudaSuccess) return cuda_fail(e, "svgd launch");

@@ -105,6 +105,9 @@ struct SvgdCtl {
 
 struct SvgdWork {
   float* tc;       // tensor-core operand rows (a, b, v split in tf32 parts), or NULL
+  float* mimg;     // tensor-core distance tiles for the median passes, or NULL
+  int* mwork;      // their work items (row tile, column tile range)
+  int n_mwork;
   float* samp;     // sampled pair distances (bracket estimate)
   float* cand;     // candidate distances inside the sampled bracket
   unsigned long long cand_cap;
@@ -123,6 +126,11 @@ int svgd_phi_chunks(int N);
 unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
 int svgd_sample_size();
 size_t phi_tc_floats(int N, int M);
+size_t median_tc_floats(int N, int M);
+int median_tc_work_items(int N, int chunk, int* out);
+cudaError_t launch_median_tc(int N, int M, const float* u, float* img, const int* work, int n_work, SvgdCtl* ctl,
+                             float* cand, unsigned long long cap, int mode, int only_in_fallback, bool prep,
+                             cudaStream_t st);
 cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st);
 cudaError_t svgd_setup_device();
 
@@ -156,6 +164,7 @@ struct pds_svgd {
   cudaStream_t stream;
   int full_passes = 0;
   int phi_cuda_cores = 0;
+  int median_cuda_cores = 0;
 };
 
 namespace pds {

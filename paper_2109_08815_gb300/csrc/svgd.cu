@@ -568,27 +568,48 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     const int nt = (N + kSpan - 1) / kSpan;
     const long long all_tiles = (long long)nt * nt;
     const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
+    // pair distances on the tensor cores (N >= 2048): every pass over the
+    // pairs then sees the same distances
+    const bool tcm = w.mimg && w.mwork && N >= 2048;
+    bool prepped = false;
     if (bracket) {
       cudaError_t e = svgd_setup_device();
       if (e != cudaSuccess) return e;
       median_sample_dist_kernel<MM><<<kSample / 256, 256, 0, st>>>(N, M, w.u, w.samp);
       median_sample_sort_kernel<<<1, kSampleThreads, 0, st>>>(w.samp, w.ctl);
-      n += 1;
-      median_bracket_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, w.cand, w.cand_cap);
+      n += 2;
+      if (tcm) {
+        e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, w.cand, w.cand_cap, 0, 0, true, st);
+        if (e != cudaSuccess) return e;
+        prepped = true;
+        n += 2;
+      } else {
+        median_bracket_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, w.cand, w.cand_cap);
+        n += 1;
+      }
       median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);
-      n += 3;
+      n += 1;
       for (int pass = 0; pass < 3; ++pass) {
         median_cand_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, pass);
         median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 0);
         n += 2;
       }
     }
-    // full passes over all pairs: always for small N, otherwise only if the
-    // bracket missed (the kernels return at once in that case)
+    // full passes over all pairs: always for small N or when asked, otherwise
+    // only if the bracket missed (the kernels return at once in that case)
     for (int pass = 0; pass < 3; ++pass) {
-      median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, pass, bracket ? 1 : 0);
+      if (tcm) {
+        cudaError_t e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, nullptr, 0ull, pass + 1,
+                                         bracket ? 1 : 0, !prepped, st);
+        if (e != cudaSuccess) return e;
+        n += prepped ? 1 : 2;
+        prepped = true;
+      } else {
+        median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, pass, bracket ? 1 : 0);
+        n += 1;
+      }
       median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 1);
-      n += 2;
+      n += 1;
     }
   }
   {

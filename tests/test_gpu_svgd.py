@@ -192,3 +192,25 @@ def test_tensor_core_phi_matches_cuda_cores(N, M):
     # the kernel values enter the second product rounded to tf32 (relative
     # 2^-11 at most, unbiased): about 1e-4 of the largest |phi|
     assert np.max(np.abs(tcp - ref)) <= 1e-3 * np.max(np.abs(ref)), np.max(np.abs(tcp - ref)) / np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("N,M", [(2048, 2), (3001, 10), (4096, 16)])
+def test_tensor_core_median_matches_cuda_cores(N, M):
+    """Pair distances of the median passes from tensor-core products against
+    the CUDA-core distances: the same bandwidth within 1e-5."""
+    rng = np.random.default_rng(N)
+    lo, hi = np.zeros(M), np.ones(M)
+    x = rng.uniform(size=(N, M))
+    out = []
+    for cc in (1, 0):
+        sv = api.Svgd(N, M, M, lo, hi)
+        sv.set_option(api.OPT_MEDIAN_CUDA_CORES, cc)
+        bw, _ = sv.step(_gpu(x), _gpu(np.zeros_like(x)))
+        torch.cuda.synchronize()
+        out.append(bw.item())
+        sv.close()
+    assert abs(out[0] - out[1]) <= 1e-5 * out[0], out
+    u = x
+    d = ((u[:, None, :] - u[None, :, :]) ** 2).sum(-1)[np.triu_indices(N, 1)]
+    med = np.partition(d, (len(d) - 1) // 2)[(len(d) - 1) // 2]
+    assert abs(out[1] - med / np.log(N)) <= 1e-5 * med / np.log(N)
