@@ -45,12 +45,15 @@ FP32_LANES_PER_SM = 128
 
 
 def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
-    """Algorithmic FP32 flops of one time step (FMA = 2): forward step with
-    its observation term, and the reverse (adjoint) step, counted from the
-    arithmetic of the specialised articulated-body recursion and its
-    hand-written reverse (recomputation for checkpointing excluded)."""
-    fwd = 69 * n + 3 * D + 1
-    rev = 148 * n + 3 * D
+    """Algorithmic FP32 flops of one time step (FMA = 2; sincos and
+    reciprocals run on the MUFU and are not counted): forward step with its
+    observation term, and the reverse (adjoint) step, counted from the
+    arithmetic of the rank-1 link-frame articulated-body recursion and its
+    hand-written reverse.  No recomputation of any kind is counted: the
+    checkpoint segment recompute and the re-forward inside the reverse step
+    are implementation costs."""
+    fwd = 58 * n + 3 * D - 25
+    rev = 130 * n + 3 * D - 51
     return fwd, rev
 
 

@@ -2,29 +2,40 @@
 // chains (one thread per particle-window unit).
 //
 // Forward dynamics (Appendix B-A, Eq. dynamics): the articulated-body
-// recursion specialised to a planar chain whose links are massless rods with
-// a point mass at the tip.  Every frame is world-aligned and sits at the
-// joint, so the joint motion subspace is (1, 0, 0) and the articulated
-// inertia passed from link i to its parent has only a 2x2 translational
-// block K (a revolute joint transmits no moment).  With
-//   r_i   = l_i (sin phi_i, -cos phi_i)   link vector p_i - p_{i-1}
-//   rho_i = l_i (cos phi_i,  sin phi_i)   its derivative d r_i / d phi_i
-//   phi_i = q_1 + .. + q_i, omega_i = qd_1 + .. + qd_i  (absolute angle, rate)
-// the inward pass (i = n..1, K_{n+1} = 0, B_{n+1} = 0, tau_{n+1} = 0) is
-//   A_i = K_{i+1} + m_i I,  Y_i = A_i rho_i,  D_i = rho_i . Y_i,
-//   beta_i = B_{i+1} + m_i g e_y - omega_i^2 A_i r_i,
-//   t_i = (tau_i - tau_{i+1} - rho_i . beta_i) / D_i,
-//   B_i = beta_i + t_i Y_i,  K_i = A_i - Y_i Y_i^T / D_i,
-// where the force link i's parent applies at joint i is K_i a_{i-1} + B_i
-// (a_{i-1} = acceleration of joint i).  The outward pass (a_0 = 0) gives the
-// absolute angular accelerations
-//   alpha_i = t_i - Y_i . a_{i-1} / D_i,  a_i = a_{i-1} - omega_i^2 r_i + alpha_i rho_i,
-// and qdd_i = alpha_i - alpha_{i-1}.  Semi-implicit Euler then updates
-// qd += qdd dt, q += qd dt (the new velocity).
+// recursion specialised to a planar chain whose links are massless rods of
+// length l_i with a point mass m_i at the tip.  Each link carries a frame
+// whose first axis e_i runs along the rod (joint i to mass i) and whose second
+// axis p_i is the direction the mass moves when joint i turns; in world
+// coordinates e_i = (sin phi_i, -cos phi_i), p_i = (cos phi_i, sin phi_i) with
+// phi_i = q_1 + .. + q_i, and the frame of link i+1 is that of link i turned by
+// q_{i+1}.  Because a revolute joint carries no moment and the rod is
+// massless, the articulated inertia that link i passes to its parent is rank
+// one along its own rod: K_i = k_i e_i e_i^T.  With link i+1's axis at
+// (c, s) = (cos q_{i+1}, sin q_{i+1}) in link i's frame, the general step
+// A_i = K_{i+1} + m_i I, K_i = A_i - A_i p p^T A_i / (p^T A_i p) reduces to
+//   h_i = m_i + k_{i+1} s^2,   k_i = m_i (m_i + k_{i+1}) / h_i,
+// so the inward pass (i = n..1, k_{n+1} = 0, bias B_{n+1} = 0, tau_{n+1} = 0)
+// needs one reciprocal per link:
+//   (Be, Bp) = B_{i+1} turned into link i's frame,
+//   y_i = k_{i+1} s c,   z_i = m_i + k_{i+1} c^2,   w_i = omega_i^2 l_i,
+//   be = Be - w_i z_i - m_i g cos phi_i,   bp = Bp - w_i y_i + m_i g sin phi_i,
+//   f_i = ((tau_i - tau_{i+1}) / l_i - bp) / h_i,
+//   B_i = (be + f_i y_i, (tau_i - tau_{i+1}) / l_i),
+// (B_i is the force link i's parent applies at joint i less K_i a_{i-1}).  The
+// outward pass (a_0 = 0) turns the joint acceleration a_{i-1} into link i's
+// frame, (ae, ap), and gives the tip acceleration and absolute angular
+// acceleration
+//   a_i = (ae - w_i, f_i - (y_i / h_i) ae),   alpha_i = (a_i,p - ap) / l_i,
+// with qdd_i = alpha_i - alpha_{i-1}.  Semi-implicit Euler then updates
+// qd += qdd dt, q += qd dt (the new velocity).  The recursion is the
+// textbook one written in link frames; the oracle runs the general spatial
+// algorithm, so the two agree only through the dynamics.
 //
 // The adjoint of one step is the exact reverse-mode derivative of the same
 // arithmetic (Appendix B-A: gradients through f_step by the chain rule /
 // adjoint method), written by hand statement by statement in reverse order.
+// cos / sin of the absolute angles are built by composing the joint
+// rotations; their adjoint is taken with respect to phi_i directly.
 #pragma once
 
 #include "pds_internal.cuh"
@@ -47,55 +58,86 @@ __device__ __forceinline__ float rcp(float x) {
   return FAST ? __fdividef(1.0f, x) : 1.0f / x;
 }
 
-// Forward step in place.
+// Per-particle link parameters, with the loop-invariant 1 / l and m g.
+template <int NL>
+struct Links {
+  float m[NL], l[NL], b[NL];
+  float il[NL], mg[NL];
+};
+
+// Joint rotations (sin q_i, cos q_i) and absolute-angle (sin, cos) by
+// composing them along the chain.
 template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const float (&m)[NL],
-                                           const float (&l)[NL], const float (&b)[NL], float g, float dt) {
-  float sn[NL], cs[NL], w2[NL], tau[NL];
-  {
-    float phi = 0.f, om = 0.f;
-#pragma unroll
-    for (int i = 0; i < NL; ++i) {
-      phi += q[i];
-      om += v[i];
-      sc<FAST>(phi, &sn[i], &cs[i]);
-      w2[i] = om * om;
-      tau[i] = -b[i] * v[i];
-    }
-  }
-  float Yx[NL], Yy[NL], iD[NL], tt[NL];
-  float Kxx = 0.f, Kxy = 0.f, Kyy = 0.f, Bx = 0.f, By = 0.f, tnext = 0.f;
-#pragma unroll
-  for (int i = NL - 1; i >= 0; --i) {
-    const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-    const float px = l[i] * cs[i], py = l[i] * sn[i];
-    const float Axx = Kxx + m[i], Axy = Kxy, Ayy = Kyy + m[i];
-    const float yx = Axx * px + Axy * py, yy = Axy * px + Ayy * py;
-    const float D = px * yx + py * yy;
-    const float zx = Axx * rx + Axy * ry, zy = Axy * rx + Ayy * ry;
-    const float bx = Bx - w2[i] * zx, by = By + m[i] * g - w2[i] * zy;
-    const float id = rcp<FAST>(D);
-    const float t = (tau[i] - tnext - (px * bx + py * by)) * id;
-    Bx = bx + t * yx;
-    By = by + t * yy;
-    Kxx = Axx - yx * yx * id;
-    Kxy = Axy - yx * yy * id;
-    Kyy = Ayy - yy * yy * id;
-    tnext = tau[i];
-    Yx[i] = yx; Yy[i] = yy; iD[i] = id; tt[i] = t;
-  }
-  float ax = 0.f, ay = 0.f, aprev = 0.f;
+__device__ __forceinline__ void joint_trig(const float (&q)[NL], float (&sq)[NL], float (&cq)[NL], float (&S)[NL],
+                                           float (&C)[NL]) {
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
-    const float al = tt[i] - (Yx[i] * ax + Yy[i] * ay) * iD[i];
-    const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-    const float px = l[i] * cs[i], py = l[i] * sn[i];
-    ax = ax - w2[i] * rx + al * px;
-    ay = ay - w2[i] * ry + al * py;
-    const float qdd = al - aprev;
-    aprev = al;
-    v[i] = v[i] + qdd * dt;
-    q[i] = q[i] + v[i] * dt;
+    sc<FAST>(q[i], &sq[i], &cq[i]);
+    if (i == 0) {
+      S[0] = sq[0];
+      C[0] = cq[0];
+    } else {
+      S[i] = fmaf(S[i - 1], cq[i], C[i - 1] * sq[i]);
+      C[i] = fmaf(C[i - 1], cq[i], -S[i - 1] * sq[i]);
+    }
+  }
+}
+
+// Forward step in place.
+template <int NL, bool FAST>
+__device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const Links<NL>& P, float dt) {
+  float sq[NL], cq[NL], S[NL], C[NL], w[NL], tau[NL];
+  joint_trig<NL, FAST>(q, sq, cq, S, C);
+  {
+    float om = 0.f;
+#pragma unroll
+    for (int i = 0; i < NL; ++i) {
+      om += v[i];
+      w[i] = om * om * P.l[i];
+      tau[i] = -P.b[i] * v[i];
+    }
+  }
+  float f[NL], x[NL];
+  float Bce = 0.f, Bcp = 0.f, kc = 0.f;
+#pragma unroll
+  for (int i = NL - 1; i >= 0; --i) {
+    const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
+    float Be = 0.f, Bp = 0.f, h = P.m[i], y = 0.f, z = P.m[i];
+    if (i + 1 < NL) {
+      const float s1 = sq[i + 1], c1 = cq[i + 1];
+      Be = fmaf(Bce, c1, -Bcp * s1);
+      Bp = fmaf(Bce, s1, Bcp * c1);
+      const float ks = kc * s1;
+      h = fmaf(ks, s1, P.m[i]);
+      y = ks * c1;
+      z = fmaf(kc * c1, c1, P.m[i]);
+    }
+    const float ih = rcp<FAST>(h);
+    const float be = Be - w[i] * z - P.mg[i] * C[i];
+    const float bp = Bp - w[i] * y + P.mg[i] * S[i];
+    const float ft = (dtau * P.il[i] - bp) * ih;
+    f[i] = ft;
+    x[i] = y * ih;
+    Bce = fmaf(ft, y, be);
+    Bcp = dtau * P.il[i];
+    kc = P.m[i] * (P.m[i] + kc) * ih;
+  }
+  float Ae = 0.f, Ap = 0.f, alp = 0.f;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) {
+    float ae = 0.f, ap = 0.f;
+    if (i > 0) {
+      ae = fmaf(cq[i], Ae, sq[i] * Ap);
+      ap = fmaf(cq[i], Ap, -sq[i] * Ae);
+    }
+    const float An = fmaf(-x[i], ae, f[i]);
+    const float al = (An - ap) * P.il[i];
+    Ae = ae - w[i];
+    Ap = An;
+    const float qdd = al - alp;
+    alp = al;
+    v[i] = fmaf(qdd, dt, v[i]);
+    q[i] = fmaf(v[i], dt, q[i]);
   }
 }
 
@@ -103,183 +145,184 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
 // output state; on exit it is the adjoint of the input state (q, v).  The
 // adjoints of the link parameters are accumulated into mb, lb, bb.
 template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const float (&m)[NL],
-                                               const float (&l)[NL], const float (&b)[NL], float g, float dt,
-                                               float (&qb)[NL], float (&vb)[NL], float (&mb)[NL], float (&lb)[NL],
-                                               float (&bb)[NL]) {
+__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P, float g,
+                                               float dt, float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
+                                               float (&lb)[NL], float (&bb)[NL]) {
   // ---- recompute the forward intermediates at (q, v)
-  float sn[NL], cs[NL], om[NL], tau[NL];
+  float sq[NL], cq[NL], S[NL], C[NL], om[NL], tau[NL];
+  joint_trig<NL, FAST>(q, sq, cq, S, C);
   {
-    float phi = 0.f, o = 0.f;
+    float o = 0.f;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      phi += q[i];
       o += v[i];
-      sc<FAST>(phi, &sn[i], &cs[i]);
       om[i] = o;
-      tau[i] = -b[i] * v[i];
+      tau[i] = -P.b[i] * v[i];
     }
   }
-  float Axx[NL], Axy[NL], Ayy[NL], iD[NL], bx[NL], by[NL], tt[NL], al[NL], a0x[NL], a0y[NL];
+  float kc[NL], ih[NL], y[NL], f[NL], num[NL], Be[NL], Bp[NL], ae[NL], ap[NL];
   {
-    float Kxx = 0.f, Kxy = 0.f, Kyy = 0.f, Bx = 0.f, By = 0.f, tnext = 0.f;
+    float Bce = 0.f, Bcp = 0.f, k = 0.f;
 #pragma unroll
     for (int i = NL - 1; i >= 0; --i) {
-      const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-      const float px = l[i] * cs[i], py = l[i] * sn[i];
-      Axx[i] = Kxx + m[i]; Axy[i] = Kxy; Ayy[i] = Kyy + m[i];
-      const float yx = Axx[i] * px + Axy[i] * py, yy = Axy[i] * px + Ayy[i] * py;
-      const float D = px * yx + py * yy;
-      const float zx = Axx[i] * rx + Axy[i] * ry, zy = Axy[i] * rx + Ayy[i] * ry;
-      const float w2 = om[i] * om[i];
-      bx[i] = Bx - w2 * zx;
-      by[i] = By + m[i] * g - w2 * zy;
-      iD[i] = rcp<FAST>(D);
-      tt[i] = (tau[i] - tnext - (px * bx[i] + py * by[i])) * iD[i];
-      Bx = bx[i] + tt[i] * yx;
-      By = by[i] + tt[i] * yy;
-      Kxx = Axx[i] - yx * yx * iD[i];
-      Kxy = Axy[i] - yx * yy * iD[i];
-      Kyy = Ayy[i] - yy * yy * iD[i];
-      tnext = tau[i];
+      const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
+      const float w = om[i] * om[i] * P.l[i];
+      float h = P.m[i], yi = 0.f, z = P.m[i];
+      Be[i] = 0.f;
+      Bp[i] = 0.f;
+      if (i + 1 < NL) {
+        const float s1 = sq[i + 1], c1 = cq[i + 1];
+        Be[i] = fmaf(Bce, c1, -Bcp * s1);
+        Bp[i] = fmaf(Bce, s1, Bcp * c1);
+        const float ks = k * s1;
+        h = fmaf(ks, s1, P.m[i]);
+        yi = ks * c1;
+        z = fmaf(k * c1, c1, P.m[i]);
+      }
+      kc[i] = k;
+      ih[i] = rcp<FAST>(h);
+      y[i] = yi;
+      const float be = Be[i] - w * z - P.mg[i] * C[i];
+      const float bp = Bp[i] - w * yi + P.mg[i] * S[i];
+      num[i] = dtau * P.il[i] - bp;
+      f[i] = num[i] * ih[i];
+      Bce = fmaf(f[i], yi, be);
+      Bcp = dtau * P.il[i];
+      k = P.m[i] * (P.m[i] + k) * ih[i];
     }
-    float ax = 0.f, ay = 0.f;
+    float Ae = 0.f, Ap = 0.f;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-      const float px = l[i] * cs[i], py = l[i] * sn[i];
-      const float yx = Axx[i] * px + Axy[i] * py, yy = Axy[i] * px + Ayy[i] * py;
-      a0x[i] = ax; a0y[i] = ay;
-      al[i] = tt[i] - (yx * ax + yy * ay) * iD[i];
-      const float w2 = om[i] * om[i];
-      ax = ax - w2 * rx + al[i] * px;
-      ay = ay - w2 * ry + al[i] * py;
+      ae[i] = 0.f;
+      ap[i] = 0.f;
+      if (i > 0) {
+        ae[i] = fmaf(cq[i], Ae, sq[i] * Ap);
+        ap[i] = fmaf(cq[i], Ap, -sq[i] * Ae);
+      }
+      Ap = fmaf(-y[i] * ih[i], ae[i], f[i]);
+      Ae = ae[i] - om[i] * om[i] * P.l[i];
     }
   }
 
   // ---- Euler: qd' = qd + qdd dt, q' = q + qd' dt
-  float alb[NL];
 #pragma unroll
-  for (int i = 0; i < NL; ++i) vb[i] += qb[i] * dt;  // qb passes through unchanged
+  for (int i = 0; i < NL; ++i) vb[i] = fmaf(qb[i], dt, vb[i]);  // qb passes through unchanged
   // qdd_i = alpha_i - alpha_{i-1}  =>  alpha_i receives qdd_b[i] - qdd_b[i+1]
+  float alb[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) alb[i] = (vb[i] - ((i + 1 < NL) ? vb[i + 1] : 0.f)) * dt;
 
   // ---- reverse of the outward pass
-  float rxb[NL], ryb[NL], pxb[NL], pyb[NL], omb[NL], tb[NL], Yxb[NL], Yyb[NL], Db[NL];
+  float fb[NL], xb[NL], wb[NL], ilb[NL];
   {
-    float axb = 0.f, ayb = 0.f;
+    float Aeb = 0.f, Apb = 0.f;
 #pragma unroll
     for (int i = NL - 1; i >= 0; --i) {
-      const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-      const float px = l[i] * cs[i], py = l[i] * sn[i];
-      const float w2 = om[i] * om[i];
-      // a_i = a_{i-1} - w2 r + alpha rho
-      omb[i] = -2.f * om[i] * (rx * axb + ry * ayb);
-      rxb[i] = -w2 * axb;
-      ryb[i] = -w2 * ayb;
-      alb[i] += px * axb + py * ayb;
-      pxb[i] = al[i] * axb;
-      pyb[i] = al[i] * ayb;
-      // alpha_i = t_i - (Y . a_{i-1}) / D
-      const float yx = Axx[i] * px + Axy[i] * py, yy = Axy[i] * px + Ayy[i] * py;
-      tb[i] = alb[i];
-      const float f = alb[i] * iD[i];
-      Yxb[i] = -f * a0x[i];
-      Yyb[i] = -f * a0y[i];
-      Db[i] = f * (yx * a0x[i] + yy * a0y[i]) * iD[i];
-      axb -= f * yx;
-      ayb -= f * yy;
+      const float x = y[i] * ih[i];
+      // Ae = ae - w
+      float aeb = Aeb;
+      wb[i] = -Aeb;
+      // alpha = (An - ap) / l
+      const float ai = alb[i] * P.il[i];
+      const float Anb = Apb + ai;
+      const float apb = -ai;
+      const float An = fmaf(-x, ae[i], f[i]);
+      ilb[i] = alb[i] * (An - ap[i]);
+      // An = f - x ae
+      fb[i] = Anb;
+      xb[i] = -Anb * ae[i];
+      aeb = fmaf(-Anb, x, aeb);
+      if (i > 0) {
+        // (ae, ap) = a_{i-1} turned by -q_i
+        qb[i] += aeb * ap[i] - apb * ae[i];
+        Aeb = fmaf(cq[i], aeb, -sq[i] * apb);
+        Apb = fmaf(sq[i], aeb, cq[i] * apb);
+      }
     }
   }
 
   // ---- reverse of the inward pass (parent to child)
-  float taub[NL];
+  float taub[NL], phib[NL], omb[NL];
 #pragma unroll
   for (int i = 0; i < NL; ++i) taub[i] = 0.f;
   {
-    float Kxxb = 0.f, Kxyb = 0.f, Kyyb = 0.f, Bxb = 0.f, Byb = 0.f;
+    float Beob = 0.f, Bpob = 0.f, kob = 0.f;  // adjoints of link i's outputs B_i, k_i
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      const float rx = l[i] * sn[i], ry = -l[i] * cs[i];
-      const float px = l[i] * cs[i], py = l[i] * sn[i];
-      const float yx = Axx[i] * px + Axy[i] * py, yy = Axy[i] * px + Ayy[i] * py;
-      const float zx = Axx[i] * rx + Axy[i] * ry, zy = Axy[i] * rx + Ayy[i] * ry;
-      const float id = iD[i];
-      const float w2 = om[i] * om[i];
-      // K_i = A - Y Y^T / D
-      float Axxb = Kxxb, Axyb = Kxyb, Ayyb = Kyyb;
-      float yxb = Yxb[i] - (2.f * Kxxb * yx + Kxyb * yy) * id;
-      float yyb = Yyb[i] - (Kxyb * yx + 2.f * Kyyb * yy) * id;
-      float Dbar = Db[i] + (Kxxb * yx * yx + Kxyb * yx * yy + Kyyb * yy * yy) * id * id;
-      // B_i = beta + t Y
-      float bxb = Bxb, byb = Byb;
-      const float tbar = tb[i] + Bxb * yx + Byb * yy;
-      yxb += tt[i] * Bxb;
-      yyb += tt[i] * Byb;
-      // t = (tau_i - tau_{i+1} - rho . beta) / D
-      const float ft = tbar * id;
-      taub[i] += ft;
-      if (i + 1 < NL) taub[i + 1] -= ft;
-      float pxbar = pxb[i] - ft * bx[i];
-      float pybar = pyb[i] - ft * by[i];
-      bxb -= ft * px;
-      byb -= ft * py;
-      Dbar -= ft * tt[i];
-      // beta = B_{i+1} + m g e_y - w2 Z
-      mb[i] += g * byb;
-      float ombar = omb[i] - 2.f * om[i] * (zx * bxb + zy * byb);
-      const float zxb = -w2 * bxb, zyb = -w2 * byb;
-      // Z = A r
-      Axxb += zxb * rx;
-      Axyb += zxb * ry + zyb * rx;
-      Ayyb += zyb * ry;
-      float rxbar = rxb[i] + Axx[i] * zxb + Axy[i] * zyb;
-      float rybar = ryb[i] + Axy[i] * zxb + Ayy[i] * zyb;
-      // D = rho . Y
-      pxbar += Dbar * yx;
-      pybar += Dbar * yy;
-      yxb += Dbar * px;
-      yyb += Dbar * py;
-      // Y = A rho
-      Axxb += yxb * px;
-      Axyb += yxb * py + yyb * px;
-      Ayyb += yyb * py;
-      pxbar += Axx[i] * yxb + Axy[i] * yyb;
-      pybar += Axy[i] * yxb + Ayy[i] * yyb;
-      // A = K_{i+1} + m I
-      mb[i] += Axxb + Ayyb;
-      Kxxb = Axxb; Kxyb = Axyb; Kyyb = Ayyb;
-      Bxb = bxb; Byb = byb;
-      // kinematics: r = l (s, -c), rho = l (c, s); d r / d phi = rho, d rho / d phi = -r
-      const float phib = rxbar * px + rybar * py - (pxbar * rx + pybar * ry);
-      lb[i] += rxbar * sn[i] - rybar * cs[i] + pxbar * cs[i] + pybar * sn[i];
-      // stash phi / omega adjoints in rxb / ryb for the prefix-sum reverse
-      rxb[i] = phib;
-      ryb[i] = ombar;
+      const float m = P.m[i];
+      const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
+      const float w = om[i] * om[i] * P.l[i];
+      // k_i = m (m + k_{i+1}) / h
+      float mbi = kob * (2.f * m + kc[i]) * ih[i];
+      float kcb = kob * m * ih[i];
+      float ihb = kob * m * (m + kc[i]);
+      // B_i = (be + f y, dtau / l)
+      const float beb = Beob;
+      const float ftb = fmaf(Beob, y[i], fb[i]);
+      float yb = Beob * f[i];
+      // f = (dtau / l - bp) / h
+      const float gg = ftb * ih[i];
+      const float dtaub = (Bpob + gg) * P.il[i];
+      const float ilbi = fmaf(Bpob + gg, dtau, ilb[i]);
+      const float bpb = -gg;
+      ihb = fmaf(ftb, num[i], ihb);
+      // bp = Bp - w y + m g S ; be = Be - w z - m g C
+      float z = m;
+      if (i + 1 < NL) z = fmaf(kc[i] * cq[i + 1], cq[i + 1], m);
+      const float wbi = wb[i] - bpb * y[i] - beb * z;
+      yb = fmaf(-bpb, w, yb);
+      const float mgb = bpb * S[i] - beb * C[i];
+      const float Sb = bpb * P.mg[i], Cb = -beb * P.mg[i];
+      const float zb = -beb * w;
+      mbi += zb;
+      // x = y / h
+      yb = fmaf(xb[i], ih[i], yb);
+      ihb = fmaf(xb[i], y[i], ihb);
+      const float hb = -ihb * ih[i] * ih[i];
+      mbi += hb;
+      taub[i] += dtaub;
+      if (i + 1 < NL) {
+        const float s1 = sq[i + 1], c1 = cq[i + 1], k = kc[i];
+        // z = m + k c^2, y = k s c, h = m + k s^2
+        kcb += zb * c1 * c1 + yb * s1 * c1 + hb * s1 * s1;
+        const float c1b = 2.f * zb * k * c1 + yb * k * s1;
+        const float s1b = yb * k * c1 + 2.f * hb * k * s1;
+        // (Be, Bp) = B_{i+1} turned by q_{i+1}
+        qb[i + 1] += s1b * c1 - c1b * s1 - beb * Bp[i] + bpb * Be[i];
+        Beob = fmaf(beb, c1, bpb * s1);
+        Bpob = fmaf(bpb, c1, -beb * s1);
+        kob = kcb;
+        taub[i + 1] -= dtaub;
+      }
+      mb[i] += fmaf(mgb, g, mbi);
+      omb[i] = wbi * 2.f * om[i] * P.l[i];
+      lb[i] += wbi * om[i] * om[i] - ilbi * P.il[i] * P.il[i];
+      phib[i] = Sb * C[i] - Cb * S[i];
     }
   }
   // tau_i = -b_i v_i ; phi_i = sum_{j<=i} q_j ; omega_i = sum_{j<=i} v_j
   float sphi = 0.f, som = 0.f;
 #pragma unroll
   for (int i = NL - 1; i >= 0; --i) {
-    sphi += rxb[i];
-    som += ryb[i];
-    bb[i] += -taub[i] * v[i];
+    sphi += phib[i];
+    som += omb[i];
+    bb[i] = fmaf(-taub[i], v[i], bb[i]);
     qb[i] += sphi;
-    vb[i] += som - taub[i] * b[i];
+    vb[i] += fmaf(-taub[i], P.b[i], som);
   }
 }
 
 // Load the physical parameters of particle i (defaults overridden by theta).
-template <int NL>
+template <int NL, bool FAST>
 __device__ __forceinline__ void load_params(const ChainParams& c, const float* __restrict__ X, int N, int i,
-                                            float (&m)[NL], float (&l)[NL], float (&b)[NL]) {
+                                            Links<NL>& P) {
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
-    m[j] = (c.mass_theta[j] >= 0) ? __ldg(X + (size_t)c.mass_theta[j] * N + i) : c.mass[j];
-    l[j] = (c.length_theta[j] >= 0) ? __ldg(X + (size_t)c.length_theta[j] * N + i) : c.length[j];
-    b[j] = (c.damp_theta[j] >= 0) ? __ldg(X + (size_t)c.damp_theta[j] * N + i) : c.damping[j];
+    P.m[j] = (c.mass_theta[j] >= 0) ? __ldg(X + (size_t)c.mass_theta[j] * N + i) : c.mass[j];
+    P.l[j] = (c.length_theta[j] >= 0) ? __ldg(X + (size_t)c.length_theta[j] * N + i) : c.length[j];
+    P.b[j] = (c.damp_theta[j] >= 0) ? __ldg(X + (size_t)c.damp_theta[j] * N + i) : c.damping[j];
+    P.il[j] = rcp<FAST>(P.l[j]);
+    P.mg[j] = P.m[j] * c.g;
   }
 }
 
@@ -342,8 +385,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   // the window-reduction kernel (next on the stream) ORs in non-finite flags
   if (status && w == 0) status[i] = 0;
 
-  float m[NL], l[NL], b[NL];
-  load_params<NL>(c, X, N, i, m, l, b);
+  Links<NL> P;
+  load_params<NL, FAST>(c, X, N, i, P);
 
   float q[NL], v[NL];
   if (w == 0) {
@@ -367,7 +410,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   float rss = 0.f;
   for (int k = 0; k < h; ++k) {
     if (grad && (k % K) == 0) tape_store<NL>(ckpt, k / K, U, u, q, v);
-    chain_step<NL, FAST>(q, v, m, l, b, c.g, c.dt);
+    chain_step<NL, FAST>(q, v, P, c.dt);
     rss += obs_residual<NL>(c, t0 + k + 1, q, v, qb, vb, false);
   }
   float lp = -0.5f * c.inv_so2 * rss + (float)h * c.obs_const;
@@ -413,13 +456,13 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     // recompute s_a .. s_{e-1} into the segment buffer
     for (int k = a; k < e; ++k) {
       tape_store<NL>(segbuf, k - a, U, u, qs, vs);
-      if (k + 1 < e) chain_step<NL, FAST>(qs, vs, m, l, b, c.g, c.dt);
+      if (k + 1 < e) chain_step<NL, FAST>(qs, vs, P, c.dt);
     }
     for (int k = e - 1; k >= a; --k) {
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL>(c, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, U, u, qs, vs);
-      chain_step_vjp<NL, FAST>(qs, vs, m, l, b, c.g, c.dt, qb, vb, mb, lb, bb);
+      chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -514,14 +557,14 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
                                                        float* __restrict__ states) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  float m[NL], l[NL], b[NL];
-  load_params<NL>(c, theta, N, i, m, l, b);
+  Links<NL> P;
+  load_params<NL, false>(c, theta, N, i, P);
   float q[NL], v[NL];
 #pragma unroll
   for (int j = 0; j < NL; ++j) { q[j] = c.s0[j]; v[j] = c.s0[NL + j]; }
   const size_t SN = (size_t)2 * NL * N;
   for (int t = 0; t <= c.T; ++t) {
-    if (t > 0) chain_step<NL, false>(q, v, m, l, b, c.g, c.dt);
+    if (t > 0) chain_step<NL, false>(q, v, P, c.dt);
     float* out = states + (size_t)t * SN + i;
 #pragma unroll
     for (int j = 0; j < NL; ++j) { out[(size_t)j * N] = q[j]; out[(size_t)(NL + j) * N] = v[j]; }
