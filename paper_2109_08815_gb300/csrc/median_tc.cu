@@ -8,9 +8,20 @@
 // to a radix-digit histogram.  Only tiles with I <= J are visited and only
 // pairs i < j counted.  Every pass over the pairs (bracket, or the full radix
 // passes when the bracket misses) uses this kernel, so all see bit-identical
-// distances.  Tiles: A (row tile) loaded once per CTA, B (column tiles)
-// double-buffered by bulk async copies; two TMEM accumulators, so the
-// product of the next tile runs while the current one is read.
+// distances; a distance is clamped at zero by its bit pattern (negative
+// rounding residue, and -0, become +0).
+//
+// The grid is persistent: CTA b takes the contiguous run
+// [b T / G, (b+1) T / G) of the T upper-triangle tiles in row-major order,
+// so every CTA gets the same number of tiles to within one.  Two shared-memory
+// stages hold (row tile A, column tile B); A is copied only when the row
+// changes.  Two TMEM accumulators let the product of tile k+1 run while
+// tile k is read.  Eight warps read a tile: warp w owns TMEM lanes
+// 32 (w mod 4) .. + 31 (its rows) and column half w / 4, and releases the
+// accumulator through an mbarrier as soon as its loads are done, so warps
+// never wait for one another except through the accumulators.  In the
+// bracket pass each warp appends its candidates to its own shared buffer
+// and flushes it to global memory with one atomic when full.
 #include <math.h>
 
 #include "pds_internal.cuh"
@@ -20,14 +31,18 @@ namespace pds {
 
 constexpr int kMtRows = 128;
 constexpr int kMtBins = 2048;
-constexpr int kMtCand = 8192;  // shared candidate buffer (floats)
+constexpr int kMtWarps = 8;  // 4 lane quarters x 2 column halves
+constexpr int kMtThreads = 32 * kMtWarps;
+constexpr int kMtCandW = 1024;  // candidate buffer per warp (floats)
 
 template <int MM>
 struct MtDims {
   static constexpr int KA = ((MM + 2 + 7) / 8) * 8;
-  static constexpr int kA = kMtRows * KA * 4;          // one tile image (hi or lo), bytes
-  static constexpr int kTile = 2 * kA;                  // hi + lo
-  static constexpr int kBytes = kTile + 2 * kTile + kMtCand * 4 + 256;
+  static constexpr int kA = kMtRows * KA * 4;  // one tile image (hi or lo), bytes
+  static constexpr int kTile = 2 * kA;          // hi + lo
+  static constexpr int kStage = 2 * kTile;      // row tile A + column tile B
+  static constexpr int kCand = kMtWarps * kMtCandW * 4;
+  static constexpr int kBytes = 2 * kStage + kCand + 128;
 };
 
 __device__ __forceinline__ void mt_split(float x, float& hi, float& lo) {
@@ -71,67 +86,73 @@ __global__ void median_tc_prep_kernel(int N, int Npad, int M, const float* __res
 }
 
 // mode 0: bracket (count d < lo, collect lo <= d <= hi); mode 1..3: radix
-// pass 0..2 histogram.  Work item w: row tile I = work[3w], column tiles
-// [work[3w+1], work[3w+2]).
+// pass 0..2 histogram.  tiles[f] = (row tile I, column tile J), J >= I.
 template <int MM>
-__global__ void __launch_bounds__(128, 2) median_tc_kernel(int N, const float* __restrict__ imgA,
-                                                           const float* __restrict__ imgB,
-                                                           const int* __restrict__ work, SvgdCtl* __restrict__ ctl,
-                                                           float* __restrict__ cand, unsigned long long cap, int mode,
-                                                           int only_in_fallback) {
+__global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const float* __restrict__ imgA,
+                                                                  const float* __restrict__ imgB,
+                                                                  const int2* __restrict__ tiles, int n_tiles,
+                                                                  SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
+                                                                  unsigned long long cap, int mode,
+                                                                  int only_in_fallback) {
   using D = MtDims<MM>;
   constexpr int KA = D::KA;
+  constexpr int kLimit = 1 << 24;  // mbarrier polls before giving up
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;
-  unsigned char* sB[2] = {smem + D::kTile, smem + 2 * D::kTile};
-  float* buf = (float*)(smem + 3 * D::kTile);              // candidates, or the histogram in radix modes
-  uint64_t* bars = (uint64_t*)(smem + 3 * D::kTile + kMtCand * 4);  // full[0], full[1], a, mma[0], mma[1]
-  uint32_t* tslot = (uint32_t*)(bars + 5);
-  unsigned int* count = tslot + 1;
-  unsigned long long* below_blk = (unsigned long long*)(bars + 6);
-  unsigned long long* base_sh = below_blk + 1;
+  float* cbuf = (float*)(smem + 2 * D::kStage);  // per-warp candidates, or the histogram in radix modes
+  uint64_t* bars = (uint64_t*)(smem + 2 * D::kStage + D::kCand);  // full[2], mma[2], free[2]
+  uint32_t* tslot = (uint32_t*)(bars + 6);
 
   if (only_in_fallback && ctl->mode != 1) return;  // uniform: the bracket held the median
-  const int t = threadIdx.x, warp = t >> 5;
-  const int I = work[3 * blockIdx.x], J0 = work[3 * blockIdx.x + 1], J1 = work[3 * blockIdx.x + 2];
-  const int nJ = J1 - J0;
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
-  unsigned int* hist = (unsigned int*)buf;
-  const float lo = ctl->lo, hi = ctl->hi;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int f0 = (int)(((long long)blockIdx.x * n_tiles) / gridDim.x);
+  const int f1 = (int)(((long long)(blockIdx.x + 1) * n_tiles) / gridDim.x);
+  const int nk = f1 - f0;
+  unsigned int* hist = (unsigned int*)cbuf;
+  float* wbuf = cbuf + warp * kMtCandW;
+  // bracket on the clamped distance max(d, 0): with lo > 0, max(d, 0) < lo
+  // iff d < lo; with lo = 0 nothing is below and inside means d <= hi
+  const float lo = ctl->lo > 0.f ? ctl->lo : -INFINITY;
+  const float hi = ctl->hi;
   const unsigned int prefix = ctl->prefix;
   const int pass = mode - 1;
 
-  if (mode == 0) {
-    if (t == 0) { *count = 0u; *below_blk = 0ull; }
-  } else {
-    for (int b = t; b < kMtBins; b += 128) hist[b] = 0u;
+  if (mode != 0)
+    for (int b = t; b < kMtBins; b += kMtThreads) hist[b] = 0u;
+  if (t == 0) {
+    for (int b = 0; b < 4; ++b) tc::mbar_init(bars + b, 1);
+    tc::mbar_init(bars + 4, kMtWarps);
+    tc::mbar_init(bars + 5, kMtWarps);
   }
-  if (t == 0)
-    for (int b = 0; b < 5; ++b) tc::mbar_init(bars + b, 1);
   if (warp == 0) tc::tmem_alloc(tslot, 256);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
 
-  if (t == 0 && nJ > 0) {
-    tc::mbar_expect_tx(bars + 2, D::kTile);
-    tc::bulk_g2s(sA, imgA + (size_t)I * (D::kTile / 4), D::kTile, bars + 2);
-    for (int s = 0; s < 2 && s < nJ; ++s) {
-      tc::mbar_expect_tx(bars + s, D::kTile);
-      tc::bulk_g2s(sB[s], imgB + (size_t)(J0 + s) * (D::kTile / 4), D::kTile, bars + s);
-    }
-  }
-  uint32_t ph_full[2] = {0u, 0u}, ph_mma[2] = {0u, 0u};
-  bool ok = true;
-
-  auto issue_gram = [&](int k) {  // thread 0: product of column tile J0 + k into accumulator k % 2
+  // producer state (thread 0): row tile held by each stage, last tile
+  // loaded and last product issued
+  int a_row0 = -1, a_row1 = -1;
+  int last_loaded = -1, last_issued = -1;
+  auto load = [&](int k) {  // tile f0 + k into stage k & 1
+    const int s = k & 1;
+    unsigned char* stg = smem + s * D::kStage;
+    const int2 tj = tiles[f0 + k];
+    const bool needA = (s ? a_row1 : a_row0) != tj.x;
+    tc::mbar_expect_tx(bars + s, needA ? 2 * D::kTile : D::kTile);
+    if (needA) tc::bulk_g2s(stg, imgA + (size_t)tj.x * (D::kTile / 4), D::kTile, bars + s);
+    tc::bulk_g2s(stg + D::kTile, imgB + (size_t)tj.y * (D::kTile / 4), D::kTile, bars + s);
+    if (s) a_row1 = tj.x;
+    else a_row0 = tj.x;
+    last_loaded = k;
+  };
+  auto issue = [&](int k) {  // product of tile k into accumulator k & 1
     const int s = k & 1;
     tc::fence_after();
     constexpr uint32_t id = tc::idesc_tf32(128, 128);
     const uint32_t sbo = 32 * KA;
-    const uint32_t a_h = tc::smem_u32(sA), a_l = a_h + D::kA;
-    const uint32_t b_h = tc::smem_u32(sB[s]), b_l = b_h + D::kA;
+    const uint32_t a_h = tc::smem_u32(smem + s * D::kStage), a_l = a_h + D::kA;
+    const uint32_t b_h = a_h + D::kTile, b_l = b_h + D::kA;
     const uint32_t Aop[3] = {a_h, a_h, a_l};
     const uint32_t Bop[3] = {b_h, b_l, b_h};
 #pragma unroll
@@ -140,100 +161,112 @@ __global__ void __launch_bounds__(128, 2) median_tc_kernel(int N, const float* _
       for (int ks = 0; ks < KA / 8; ++ks)
         tc::mma_ss(tbase + 128 * s, tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
                    tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
-    tc::mma_commit(bars + 3 + s);
+    tc::mma_commit(bars + 2 + s);
+    last_issued = k;
   };
 
-  if (nJ > 0) {
-    bool w = true;
-    if (t == 0) {
-      w = tc::mbar_wait(bars + 2, 0, 1 << 24) && tc::mbar_wait(bars + 0, 0, 1 << 24);
-      if (w) issue_gram(0);
-    }
-    ok = __syncthreads_and(w) != 0;
-    ph_full[0] = 1u;
+  bool ok = true;
+  if (t == 0 && nk > 0) {
+    load(0);
+    if (nk > 1) load(1);
+    ok = tc::mbar_wait(bars + 0, 0, kLimit);
+    if (ok) issue(0);
   }
-  const int i = I * kMtRows + t;
-  unsigned int below = 0u;
 
-  for (int k = 0; k < nJ && ok; ++k) {
+  unsigned int below = 0u;  // pairs below the bracket (this thread)
+  unsigned int cnt = 0u;    // candidates in this warp's buffer (warp-uniform)
+  auto flush = [&]() {      // warp: move its buffer to the global candidates
+    unsigned long long base = 0ull;
+    if (lane == 0) base = atomicAdd(&ctl->inside, (unsigned long long)cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (unsigned int e = lane; e < cnt; e += 32)
+      if (base + e < cap) cand[base + e] = wbuf[e];
+    __syncwarp();
+    cnt = 0u;
+  };
+  const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+  const int c0 = half * 64;
+
+  for (int k = 0; k < nk; ++k) {
     const int s = k & 1;
-    // next tile's product while this one is read
-    bool w = true;
-    if (t == 0 && k + 1 < nJ) {
+    if (t == 0 && ok && k + 1 < nk) {
+      // next product: its tile is loaded and accumulator (k+1) & 1 has been
+      // read by every warp (tile k - 1)
       const int s1 = (k + 1) & 1;
-      w = tc::mbar_wait(bars + s1, ph_full[s1], 1 << 24);
-      if (w) issue_gram(k + 1);
+      ok = tc::mbar_wait(bars + s1, (uint32_t)((k + 1) >> 1) & 1u, kLimit);
+      if (ok && k >= 1) ok = tc::mbar_wait(bars + 4 + s1, (uint32_t)((k - 1) >> 1) & 1u, kLimit);
+      if (ok) issue(k + 1);
     }
-    if (k + 1 < nJ) ph_full[(k + 1) & 1] ^= 1u;
-    // this tile's product done: its B buffer may be refilled
-    w = w && tc::mbar_wait(bars + 3 + s, ph_mma[s], 1 << 24);
-    ph_mma[s] ^= 1u;
-    ok = __syncthreads_and(w) != 0;
-    tc::fence_after();
+    bool w = ok && tc::mbar_wait(bars + 2 + s, (uint32_t)(k >> 1) & 1u, kLimit);
+    ok = __all_sync(0xffffffffu, w) != 0;
     if (!ok) break;
-    if (t == 0 && k + 2 < nJ) {
-      tc::mbar_expect_tx(bars + s, D::kTile);
-      tc::bulk_g2s(sB[s], imgB + (size_t)(J0 + k + 2) * (D::kTile / 4), D::kTile, bars + s);
-    }
-    const int J = J0 + k;
-    const bool diag = (J == I);
-#pragma unroll 1
-    for (int c0 = 0; c0 < 128; c0 += 32) {
-      uint32_t r[32];
-      tc::tmem_ld32(tbase + 128 * s + lane_off + c0, r);
-      tc::tmem_wait_ld();
-      const int jb = J * kMtRows + c0;
-      if (mode == 0) {
-        // valid pairs of this chunk: j < N and (off the diagonal tile, or j > i)
-        const int jmax = min(32, N - jb);
-        const int jmin = diag ? (i - jb + 1) : 0;
-        unsigned int inmask = 0u;
+    tc::fence_after();
+    if (t == 0 && k + 2 < nk) load(k + 2);  // stage s is free: product k is done
+
+    uint32_t r0[32], r1[32];
+    tc::tmem_ld32(tbase + lane_off + 128 * s + c0, r0);
+    tc::tmem_ld32(tbase + lane_off + 128 * s + c0 + 32, r1);
+    tc::tmem_wait_ld();
+    tc::fence_before();
+    __syncwarp();
+    if (lane == 0) tc::mbar_arrive(bars + 4 + s);
+
+    const int2 tj = tiles[f0 + k];
+    const int i = tj.x * kMtRows + quarter * 32 + lane;
+    const bool diag = tj.x == tj.y;
+    const bool full = !diag && (tj.y + 1) * kMtRows <= N && (tj.x + 1) * kMtRows <= N;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const float d = fmaxf(__uint_as_float(r[q]), 0.f);
-          const bool valid = (q < jmax) && (q >= jmin) && (i < N);
-          below += (valid && d < lo) ? 1u : 0u;
-          inmask |= (valid && d >= lo && d <= hi) ? (1u << q) : 0u;
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t(&r)[32] = h ? r1 : r0;
+      const int jb = tj.y * kMtRows + c0 + 32 * h;
+      // valid columns q of this chunk: [jmin, jmax)
+      const int jmax = full ? 32 : (i < N ? min(32, N - jb) : 0);
+      const int jmin = diag ? (i - jb + 1) : 0;
+      if (mode == 0) {
+        unsigned int inmask = 0u;
+        if (full) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float d = __uint_as_float(r[q]);
+            const bool b = d < lo;
+            below += b ? 1u : 0u;
+            inmask |= (!b && d <= hi) ? (1u << q) : 0u;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const float d = __uint_as_float(r[q]);
+            const bool valid = q < jmax && q >= jmin;
+            const bool b = d < lo;
+            below += (valid && b) ? 1u : 0u;
+            inmask |= (valid && !b && d <= hi) ? (1u << q) : 0u;
+          }
         }
-        // warp-aggregated append: one shared atomic per warp
+        // warp-aggregated append to this warp's buffer
         const unsigned int mine = __popc(inmask);
         unsigned int incl = mine;
-        const int lane = t & 31;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
           const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
           if (lane >= off) incl += o;
         }
         const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
-        unsigned int base = 0u;
-        if (lane == 31 && total) base = atomicAdd(count, total);
-        base = __shfl_sync(0xffffffffu, base, 31) + (incl - mine);
-        if (inmask) {
+        if (total) {
+          if (cnt + total > (unsigned)kMtCandW) flush();
+          unsigned int pos = cnt + incl - mine;
+          if (inmask) {
 #pragma unroll
-          for (int q = 0; q < 32; ++q)
-            if (inmask & (1u << q)) buf[base++] = fmaxf(__uint_as_float(r[q]), 0.f);
-        }
-        __syncthreads();
-        if (*count > (unsigned)(kMtCand - 128 * 32)) {
-          // flush the shared candidates to the global buffer
-          const unsigned int nb = *count;
-          if (t == 0) *base_sh = atomicAdd(&ctl->inside, (unsigned long long)nb);
-          __syncthreads();
-          const unsigned long long base = *base_sh;
-          for (unsigned int e = t; e < nb; e += 128)
-            if (base + e < cap) cand[base + e] = buf[e];
-          __syncthreads();
-          if (t == 0) *count = 0u;
-          __syncthreads();
+            for (int q = 0; q < 32; ++q)
+              if (inmask & (1u << q)) wbuf[pos++] = __uint_as_float((unsigned int)max((int)r[q], 0));
+          }
+          __syncwarp();
+          cnt += total;
         }
       } else {
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const float d = fmaxf(__uint_as_float(r[q]), 0.f);
-          const int j = jb + q;
-          const bool valid = (i < N) && (j < N) && (!diag || j > i);
-          if (valid) {
-            const unsigned int bits = __float_as_uint(d);
+          const unsigned int bits = (unsigned int)max((int)r[q], 0);
+          if (q < jmax && q >= jmin) {
             if (pass == 0) atomicAdd(&hist[bits >> 21], 1u);
             else if (pass == 1) { if ((bits >> 21) == prefix) atomicAdd(&hist[(bits >> 10) & 2047u], 1u); }
             else if ((bits >> 10) == prefix) atomicAdd(&hist[bits & 1023u], 1u);
@@ -241,28 +274,25 @@ __global__ void __launch_bounds__(128, 2) median_tc_kernel(int N, const float* _
         }
       }
     }
-    tc::fence_before();
-    __syncthreads();  // accumulator s free for the product of tile k + 2
   }
-  if (!ok && t == 0) ctl->tc_error = 1;
+  if (!ok && lane == 0) ctl->tc_error = 1;
 
   if (mode == 0) {
-    // final flush and the below count
-    __syncthreads();
-    const unsigned int nb = *count;
-    if (t == 0 && nb) *base_sh = atomicAdd(&ctl->inside, (unsigned long long)nb);
-    __syncthreads();
-    if (nb) {
-      const unsigned long long base = *base_sh;
-      for (unsigned int e = t; e < nb; e += 128)
-        if (base + e < cap) cand[base + e] = buf[e];
-    }
-    atomicAdd(below_blk, (unsigned long long)below);
-    __syncthreads();
-    if (t == 0 && *below_blk) atomicAdd(&ctl->below, *below_blk);
-  } else {
-    __syncthreads();
-    for (int b = t; b < kMtBins; b += 128) {
+    if (cnt) flush();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) below += __shfl_xor_sync(0xffffffffu, below, off);
+    if (lane == 0 && below) atomicAdd(&ctl->below, (unsigned long long)below);
+  }
+  if (t == 0 && !ok) {
+    // gave up: let the copies and products already issued finish (bounded)
+    // before the shared memory and TMEM are released
+    for (int k = last_issued + 1; k <= last_loaded; ++k)
+      tc::mbar_wait(bars + (k & 1), (uint32_t)(k >> 1) & 1u, kLimit);
+    if (last_issued >= 0) tc::mbar_wait(bars + 2 + (last_issued & 1), (uint32_t)(last_issued >> 1) & 1u, kLimit);
+  }
+  __syncthreads();
+  if (mode != 0) {
+    for (int b = t; b < kMtBins; b += kMtThreads) {
       const unsigned int h = hist[b];
       if (h) atomicAdd(&ctl->hist[b], h);
     }
@@ -272,14 +302,14 @@ __global__ void __launch_bounds__(128, 2) median_tc_kernel(int N, const float* _
   if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
-// Work items over the upper triangle of tiles: (I, J0, J1) with J0 >= I,
-// at most `chunk` column tiles each.
-int median_tc_work_items(int N, int chunk, int* out) {
+// Upper-triangle tiles (I, J), J >= I, in row-major order; returns their
+// number and writes them to out (2 ints each) when out is not NULL.
+int median_tc_work_items(int N, int* out) {
   const int nt = (N + kMtRows - 1) / kMtRows;
   int n = 0;
   for (int I = 0; I < nt; ++I)
-    for (int J = I; J < nt; J += chunk) {
-      if (out) { out[3 * n] = I; out[3 * n + 1] = J; out[3 * n + 2] = J + chunk < nt ? J + chunk : nt; }
+    for (int J = I; J < nt; ++J) {
+      if (out) { out[2 * n] = I; out[2 * n + 1] = J; }
       ++n;
     }
   return n;
@@ -302,16 +332,39 @@ static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const 
   float* imgA = img;
   float* imgB = img + (size_t)nt * (D::kTile / 4);
   if (prep) median_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, u, imgA, imgB);
-  static bool attr[64];
+  // per device: shared-memory opt-in and the persistent grid (resident CTAs
+  // per SM, at most 2: each holds 256 of the SM's 512 TMEM columns)
+  static int grid_of[64];
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !attr[dev]) {
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  if (grid_of[dev] == 0) {
     cudaError_t e =
         cudaFuncSetAttribute(median_tc_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, D::kBytes);
     if (e != cudaSuccess) return e;
-    attr[dev] = true;
+    e = cudaFuncSetAttribute(median_tc_kernel<MM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    // resident CTAs per SM from the kernel's registers and shared memory
+    // (the maximum shared-memory carveout is requested above)
+    int sms = 0, smem_sm = 0, smem_rsv = 0;
+    cudaFuncAttributes fa;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, median_tc_kernel<MM>)) != cudaSuccess)
+      return e;
+    const int regs = (fa.numRegs + 7) / 8 * 8;
+    const int by_regs = 65536 / (regs * kMtThreads);
+    const int by_smem = smem_sm / (D::kBytes + smem_rsv);
+    int per_sm = by_regs < by_smem ? by_regs : by_smem;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    grid_of[dev] = sms * (per_sm < 2 ? per_sm : 2);
   }
-  median_tc_kernel<MM><<<n_work, 128, D::kBytes, st>>>(N, imgA, imgB, work, ctl, cand, cap, mode, only_in_fallback);
+  const int grid = n_work < grid_of[dev] ? n_work : grid_of[dev];
+  if (grid < 1) return cudaSuccess;
+  median_tc_kernel<MM><<<grid, kMtThreads, D::kBytes, st>>>(N, imgA, imgB, reinterpret_cast<const int2*>(work),
+                                                           n_work, ctl, cand, cap, mode, only_in_fallback);
   return cudaGetLastError();
 }
 

@@ -338,7 +338,7 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   s->sp.lr = (float)lr; s->sp.b1 = (float)beta1; s->sp.b2 = (float)beta2; s->sp.eps = (float)eps;
   s->sp.clamp = clamp ? 1 : 0;
   s->stream = (cudaStream_t)cuda_stream;
-  s->w.chunks = svgd_phi_chunks(N);
+  s->w.chunks = svgd_phi_partials(N);
   s->w.cand_cap = svgd_cand_capacity(N);
   const size_t MN = (size_t)M * N, PN = (size_t)P * N;
   cudaError_t e = cudaSuccess;
@@ -356,10 +356,9 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
     return cuda_fail(e, "svgd allocation");
   }
   if (N >= 2048) {
-    const int chunk = 8;  // column tiles per work item
-    const int n_items = median_tc_work_items(N, chunk, nullptr);
-    std::vector<int> items(3 * (size_t)n_items);
-    median_tc_work_items(N, chunk, items.data());
+    const int n_items = median_tc_work_items(N, nullptr);
+    std::vector<int> items(2 * (size_t)n_items);
+    median_tc_work_items(N, items.data());
     if ((e = cudaMalloc(&s->w.mwork, items.size() * sizeof(int))) != cudaSuccess ||
         (e = cudaMemcpy(s->w.mwork, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice)) !=
             cudaSuccess) {

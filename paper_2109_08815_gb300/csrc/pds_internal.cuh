@@ -106,7 +106,7 @@ struct SvgdCtl {
 struct SvgdWork {
   float* tc;       // tensor-core operand rows (a, b, v split in tf32 parts), or NULL
   float* mimg;     // tensor-core distance tiles for the median passes, or NULL
-  int* mwork;      // their work items (row tile, column tile range)
+  int* mwork;      // their tiles (row tile, column tile), upper triangle
   int n_mwork;
   float* samp;     // sampled pair distances (bracket estimate)
   float* cand;     // candidate distances inside the sampled bracket
@@ -127,11 +127,13 @@ unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not
 int svgd_sample_size();
 size_t phi_tc_floats(int N, int M);
 size_t median_tc_floats(int N, int M);
-int median_tc_work_items(int N, int chunk, int* out);
+int median_tc_work_items(int N, int* out);
 cudaError_t launch_median_tc(int N, int M, const float* u, float* img, const int* work, int n_work, SvgdCtl* ctl,
                              float* cand, unsigned long long cap, int mode, int only_in_fallback, bool prep,
                              cudaStream_t st);
-cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st);
+cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cudaStream_t st);
+int phi_tc_slots(int N);
+int svgd_phi_partials(int N);
 cudaError_t svgd_setup_device();
 
 // Record an error message for pds_last_error() and return `code`.

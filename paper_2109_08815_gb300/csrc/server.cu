@@ -74,10 +74,10 @@ static size_t job_bytes(int n, int M, int T, int W, int D, int N, int K) {
   b += (size_t)W * (1 + M + 2 * S) * N * 4;                 // per-window partials
   b += (segs + (size_t)K) * S * U * 4;                      // adjoint tape
   b += (2 * P * N + N) * 4;                                 // iteration buffers (grad, x, logp)
-  b += (size_t)svgd_phi_chunks(N) * M * N * 4 + 2 * (size_t)M * N * 4 + 2 * P * N * 4;  // SVGD state
+  b += (size_t)svgd_phi_partials(N) * M * N * 4 + 2 * (size_t)M * N * 4 + 2 * P * N * 4;  // SVGD state
   b += svgd_cand_capacity(N) * 4 + (svgd_cand_capacity(N) ? (size_t)svgd_sample_size() * 4 : 0);
   if (N >= 256) b += phi_tc_floats(N, M) * 4;
-  if (N >= 2048) b += median_tc_floats(N, M) * 4 + 64 * 1024;
+  if (N >= 2048) b += median_tc_floats(N, M) * 4 + (size_t)median_tc_work_items(N, nullptr) * 2 * sizeof(int);
   b += P * N * 4 + (size_t)N * 4;                           // particles, log p
   return b + (64u << 10);
 }

@@ -414,7 +414,10 @@ __global__ void median_resolve_kernel(SvgdCtl* __restrict__ ctl, unsigned long l
   }
 }
 
-// Radix pass over the candidates (mode 0 only).
+// Radix pass over the candidates (mode 0 only).  The candidates all lie in
+// the bracket, so runs of them share a bin (in the first pass nearly all of
+// them): each thread counts a run of equal bins in a register and adds it to
+// the shared histogram once.  Loads are float4, two in flight per thread.
 __global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __restrict__ cand,
                                                                SvgdCtl* __restrict__ ctl, int pass) {
   __shared__ unsigned int hist[kHistBins];
@@ -423,9 +426,38 @@ __global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __re
   __syncthreads();
   const unsigned long long n = ctl->inside;
   const unsigned int prefix = ctl->prefix;
-  for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-       k += (unsigned long long)gridDim.x * blockDim.x)
-    hist_add(hist, cand[k], pass, prefix);
+  unsigned int run_bin = 0u, run = 0u;
+  auto add = [&](float v) {
+    const unsigned int bits = __float_as_uint(v);
+    unsigned int bin;
+    if (pass == 0) bin = bits >> 21;
+    else if (pass == 1) bin = ((bits >> 21) == prefix) ? ((bits >> 10) & 2047u) : 0xFFFFFFFFu;
+    else bin = ((bits >> 10) == prefix) ? (bits & 1023u) : 0xFFFFFFFFu;
+    if (bin == 0xFFFFFFFFu) return;
+    if (run && bin == run_bin) {
+      ++run;
+    } else {
+      if (run) atomicAdd(&hist[run_bin], run);
+      run_bin = bin;
+      run = 1u;
+    }
+  };
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long n4 = n / 4;
+  const float4* c4 = reinterpret_cast<const float4*>(cand);
+  unsigned long long k = tid;
+  for (; k + stride < n4; k += 2 * stride) {
+    const float4 a = __ldg(c4 + k), b = __ldg(c4 + k + stride);
+    add(a.x); add(a.y); add(a.z); add(a.w);
+    add(b.x); add(b.y); add(b.z); add(b.w);
+  }
+  if (k < n4) {
+    const float4 a = __ldg(c4 + k);
+    add(a.x); add(a.y); add(a.z); add(a.w);
+  }
+  for (unsigned long long e = 4 * n4 + tid; e < n; e += stride) add(__ldg(cand + e));
+  if (run) atomicAdd(&hist[run_bin], run);
   __syncthreads();
   for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
     const unsigned int h = hist[b];
@@ -553,6 +585,14 @@ int svgd_phi_chunks(int N) {
   return chunks;
 }
 
+// Partial-phi buffers to allocate: enough for the CUDA-core chunks and the
+// tensor-core path's per-row slots.
+int svgd_phi_partials(int N) {
+  const int c = svgd_phi_chunks(N);
+  const int s = N >= 256 ? phi_tc_slots(N) : 0;
+  return c > s ? c : s;
+}
+
 template <int MM>
 static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
                                   float* phi_out, cudaStream_t st, int* launches) {
@@ -619,9 +659,10 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     int chunks_used = chunks;
     if (w.tc && N >= 256) {
       // tensor-core path: the kernel-matrix products on tcgen05 (chunks0 chunks of 128-column tiles)
-      cudaError_t e = launch_phi_tc(N, M, w, chunks0, st);
+      int slots = 0;
+      cudaError_t e = launch_phi_tc(N, M, w, &slots, st);
       if (e != cudaSuccess) return e;
-      chunks_used = chunks0;
+      chunks_used = slots;
       n += 1;
     } else {
       dim3 grid((N + kSpan - 1) / kSpan, chunks);

@@ -12,9 +12,20 @@
 // split into a tf32 high part and a tf32 remainder so the products keep
 // fp32-level accuracy (a.b = ah.bh + ah.bl + al.bh, v = vh + vl).  The
 // exponentials are taken on the CUDA cores between the two products, read
-// from and written back to tensor memory in place.  One CTA owns 128 rows i
-// and loops over a chunk of 128-column tiles j; partial sums per chunk are
-// added by the Adam kernel.
+// from and written back to tensor memory in place.
+//
+// The kernel is persistent and warp-specialised: one CTA per SM takes the
+// contiguous run [b T / G, (b+1) T / G) of the T = (N/128)^2 tiles (row tile
+// I, column tile J) in row-major order.  An issuer warp streams the column
+// tiles' operands through three shared-memory stages (bulk async copies),
+// issues the exponent product of tile k+1 into one of two TMEM exponent
+// buffers while sixteen exponent warps turn tile k into kernel values in the
+// other, and then issues the second product of tile k into one of two TMEM
+// output accumulators.  When a CTA's run leaves a row tile, four of the
+// exponent warps read that row's accumulator and write its partial phi to
+// the slot (CTA index - first CTA of the row); the last CTA of a row zeroes
+// the slots no CTA used, and the Adam kernel adds the slots in a fixed
+// order, so the result is deterministic.
 #include <math.h>
 
 #include "pds_internal.cuh"
@@ -38,13 +49,28 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = __uint_as_float(tc::to_tf32(x - hi));
 }
 
+// Tensor-memory plan (512 columns): NE exponent buffers of 128 columns, then
+// two output sets (one per row segment in flight) of 2 NV columns each: the
+// second product takes v's tf32 high and low parts as one operand of 2 NV
+// columns, so each 8-deep slice of K is a single instruction, and the
+// epilogue adds the two halves.  Three exponent buffers let the exponent
+// product of tile k+1 queue behind the second product of tile k-1 without
+// waiting for it; M = 16 (NV = 48) leaves room for two.
+template <int MM>
+struct TcAcc {
+  static constexpr int NV = TcDims<MM>::NV;
+  static constexpr int NE = (3 * 128 + 2 * 2 * NV <= 512) ? 3 : 2;
+  static constexpr int kOcol = 128 * NE;  // first output column
+};
+
 template <int MM>
 struct TcSmem {
   static constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
-  static constexpr int kA = kTcRows * KA * 4;   // one operand tile (128 rows x KA), bytes
-  static constexpr int kV = NV * kTcRows * 4;   // one v^T tile, bytes
+  static constexpr int kA = kTcRows * KA * 4;     // one operand tile (128 rows x KA), bytes
+  static constexpr int kV = NV * kTcRows * 4;     // one v^T tile, bytes
   static constexpr int kStage = 2 * kA + 2 * kV;  // b (hi, lo) + v^T (hi, lo) of one column tile
-  static constexpr int kBytes = 2 * kA + 2 * kStage + 128;
+  static constexpr int kStages = (2 * 2 * kA + 3 * kStage + 256 <= 220 * 1024) ? 3 : 2;
+  static constexpr int kBytes = 2 * 2 * kA + kStages * kStage + 256;  // two a slots, the stages, barriers
 };
 
 // Operand tiles for every particle, written directly in the shared-memory
@@ -102,166 +128,287 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
   }
 }
 
+constexpr int kPhiExpWarps = 16;                    // 4 lane quarters x 4 column quarters
+constexpr int kPhiThreads = 32 * (kPhiExpWarps + 1);  // + the issuer warp
+constexpr int kPhiEpiWarp0 = 12;                      // warps 12..15 (column quarter 3) read the outputs
+
+// First CTA whose run [b T / G, (b+1) T / G) contains tile x.
+__host__ __device__ inline int phi_tc_first_cta(long long x, long long T, int G) {
+  return (int)(((x + 1) * G + T - 1) / T) - 1;
+}
+
 template <int MM>
-__global__ void __launch_bounds__(128, 2) phi_tc_kernel(int N, int Npad, int M, const float* __restrict__ imgA,
-                                                        const float* __restrict__ imgBV, const float* __restrict__ u,
-                                                        SvgdCtl* __restrict__ ctl, float* __restrict__ phi_part,
-                                                        int tiles_per_chunk) {
+__global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad, int M, const float* __restrict__ imgA,
+                                                                const float* __restrict__ imgBV,
+                                                                const float* __restrict__ u,
+                                                                SvgdCtl* __restrict__ ctl, float* __restrict__ phi_part,
+                                                                int slots) {
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   using SM = TcSmem<MM>;
+  constexpr int S = SM::kStages;
+  constexpr int NE = TcAcc<MM>::NE;
+  constexpr int kLimit = 1 << 24;  // mbarrier polls before giving up
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sA = smem;                              // a hi | a lo
-  unsigned char* sStage[2] = {smem + 2 * SM::kA, smem + 2 * SM::kA + SM::kStage};
-  uint64_t* bars = (uint64_t*)(smem + 2 * SM::kA + 2 * SM::kStage);  // full[0], full[1], a, mma
-  uint32_t* tslot = (uint32_t*)(bars + 4);
+  unsigned char* sA = smem;                       // two a slots (hi | lo), by row parity
+  unsigned char* sStage = smem + 2 * 2 * SM::kA;  // S stages of (b hi | b lo | v hi | v lo)
+  uint64_t* bars = (uint64_t*)(sStage + S * SM::kStage);
+  uint64_t* full = bars;         // [S]   operands of a tile landed
+  uint64_t* g_done = bars + 3;   // [NE]  exponent product done
+  uint64_t* p_ready = bars + 6;  // [NE]  kernel values written (16 warps)
+  uint64_t* pv_done = bars + 9;  // [NE]  second product done
+  uint64_t* o_ready = bars + 12; // [2]   a row segment's outputs complete
+  uint64_t* o_free = bars + 14;  // [2]   a row segment's outputs read (4 warps)
+  uint32_t* tslot = (uint32_t*)(bars + 16);
 
-  const int t = threadIdx.x, warp = t >> 5;
-  const int i0 = blockIdx.x * kTcRows;
-  const int ntiles = Npad / kTcRows;
-  const int jt0 = blockIdx.y * tiles_per_chunk;
-  const int jt1 = min(ntiles, jt0 + tiles_per_chunk);
-  const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int nt = Npad / kTcRows;
+  const long long T = (long long)nt * nt;
+  const int G = gridDim.x;
+  const int f0 = (int)(((long long)blockIdx.x * T) / G);
+  const int f1 = (int)(((long long)(blockIdx.x + 1) * T) / G);
+  const int nk = f1 - f0;
 
   if (t == 0) {
-    for (int b = 0; b < 4; ++b) tc::mbar_init(bars + b, 1);
+    for (int b = 0; b < S; ++b) tc::mbar_init(full + b, 1);
+    for (int b = 0; b < NE; ++b) {
+      tc::mbar_init(g_done + b, 1);
+      tc::mbar_init(p_ready + b, kPhiExpWarps);
+      tc::mbar_init(pv_done + b, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(o_ready + b, 1);
+      tc::mbar_init(o_free + b, 4);
+    }
   }
-  if (warp == 0) tc::tmem_alloc(tslot, 256);
+  if (warp == 0) tc::tmem_alloc(tslot, 512);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *tslot;
-  const uint32_t tE = tbase, tO = tbase + 128;
-
-  // prologue: this CTA's a tile and the first two column tiles
-  if (t == 0 && jt1 > jt0) {
-    tc::mbar_expect_tx(bars + 2, 2 * SM::kA);
-    tc::bulk_g2s(sA, imgA + (size_t)blockIdx.x * (2 * SM::kA / 4), 2 * SM::kA, bars + 2);
-    for (int s = 0; s < 2 && jt0 + s < jt1; ++s) {
-      tc::mbar_expect_tx(bars + s, SM::kStage);
-      tc::bulk_g2s(sStage[s], imgBV + (size_t)(jt0 + s) * (SM::kStage / 4), SM::kStage, bars + s);
-    }
-  }
   bool ok = true;
-  if (jt1 > jt0) ok = __syncthreads_and(tc::mbar_wait(bars + 2, 0, 1 << 24)) != 0;
-  uint32_t ph_full[2] = {0u, 0u}, ph_mma = 0u;
 
-  for (int jt = jt0; jt < jt1 && ok; ++jt) {
-    const int s = (jt - jt0) & 1;
-    ok = __syncthreads_and(tc::mbar_wait(bars + s, ph_full[s], 1 << 24)) != 0;
-    ph_full[s] ^= 1;
-    if (!ok) break;
-    const unsigned char* sB = sStage[s];
-    const unsigned char* sV = sStage[s] + 2 * SM::kA;
-    // exponents E = a b^T (three split products)
-    if (t == 0) {
-      tc::fence_after();
-      constexpr uint32_t id = tc::idesc_tf32(128, 128);
-      const uint32_t sbo = 32 * KA;
-      const uint32_t a_h = tc::smem_u32(sA), a_l = a_h + SM::kA;
-      const uint32_t b_h = tc::smem_u32(sB), b_l = b_h + SM::kA;
-      const uint32_t Aop[3] = {a_h, a_h, a_l};
-      const uint32_t Bop[3] = {b_h, b_l, b_h};
+  if (warp == kPhiExpWarps) {
+    // ------------------------------------------------------------ issuer
+    if (lane == 0 && nk > 0) {
+      const int I0 = f0 / nt;
+      int next_load = 0, last_g = -1, last_pv = -1;
+      auto load = [&](int k) {  // operands of tile f0 + k into stage k % S (a with the row's first tile)
+        const int f = f0 + k, I = f / nt, J = f % nt;
+        unsigned char* stg = sStage + (k % S) * SM::kStage;
+        const bool needA = (k == 0) || (f % nt == 0);
+        tc::mbar_expect_tx(full + k % S, SM::kStage + (needA ? 2 * SM::kA : 0));
+        if (needA)
+          tc::bulk_g2s(sA + ((I - I0) & 1) * 2 * SM::kA, imgA + (size_t)I * (2 * SM::kA / 4), 2 * SM::kA, full + k % S);
+        tc::bulk_g2s(stg, imgBV + (size_t)J * (SM::kStage / 4), SM::kStage, full + k % S);
+        next_load = k + 1;
+      };
+      auto pv_wait = [&](int k) {  // second product of tile k done
+        return tc::mbar_wait(pv_done + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
+      };
+      auto gram = [&](int k) {  // E[k % NE] = a b^T (three split products)
+        const int f = f0 + k, I = f / nt;
+        tc::fence_after();
+        constexpr uint32_t id = tc::idesc_tf32(128, 128);
+        const uint32_t sbo = 32 * KA;
+        const uint32_t a_h = tc::smem_u32(sA + ((I - I0) & 1) * 2 * SM::kA), a_l = a_h + SM::kA;
+        const uint32_t b_h = tc::smem_u32(sStage + (k % S) * SM::kStage), b_l = b_h + SM::kA;
+        const uint32_t Aop[3] = {a_h, a_h, a_l};
+        const uint32_t Bop[3] = {b_h, b_l, b_h};
 #pragma unroll
-      for (int p = 0; p < 3; ++p)
+        for (int p = 0; p < 3; ++p)
 #pragma unroll
-        for (int ks = 0; ks < KA / 8; ++ks)
-          tc::mma_ss(tE, tc::smem_desc(Aop[p] + ks * 256, 128, sbo), tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id,
-                     (p > 0 || ks > 0) ? 1u : 0u);
-      tc::mma_commit(bars + 3);
+          for (int ks = 0; ks < KA / 8; ++ks)
+            tc::mma_ss(tbase + 128 * (k % NE), tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
+                       tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
+        tc::mma_commit(g_done + k % NE);
+        last_g = k;
+      };
+      for (int k = 0; k < S && k < nk; ++k) load(k);
+      ok = tc::mbar_wait(full + 0, 0u, kLimit);
+      if (ok) gram(0);
+      int seg = 0;  // row segment of tile k within this CTA's run
+      for (int k = 0; k < nk && ok; ++k) {
+        const int f = f0 + k;
+        if (k > 0 && f % nt == 0) ++seg;
+        if (k + 1 < nk) {
+          // exponent buffer (k+1) % NE was last read by the second product of tile k+1-NE
+          if (k + 1 - NE >= 0) ok = pv_wait(k + 1 - NE);
+          if (ok && next_load == k + 1) {  // fewer stages than needed to prefetch
+            if (k + 1 - S >= 0) ok = pv_wait(k + 1 - S);
+            if (ok) load(k + 1);
+          }
+          if (ok) ok = tc::mbar_wait(full + (k + 1) % S, (uint32_t)((k + 1) / S) & 1u, kLimit);
+          if (ok) gram(k + 1);
+        }
+        // stage (k-1) % S is free once the second product of tile k-1 is done
+        if (ok && k >= 1 && next_load == k - 1 + S && k - 1 + S < nk) {
+          ok = pv_wait(k - 1);
+          if (ok) load(k - 1 + S);
+        }
+        // kernel values of tile k written by every exponent warp
+        if (ok) ok = tc::mbar_wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
+        const bool first = (k == 0) || (f % nt == 0);
+        const bool last = (k == nk - 1) || ((f + 1) % nt == 0);
+        // output set seg & 1 was read for segment seg - 2
+        if (ok && first && seg >= 2) ok = tc::mbar_wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u, kLimit);
+        if (!ok) break;
+        tc::fence_after();
+        {
+          // O[seg & 1] (+)= K [v hi | v lo]: one instruction per 8-deep slice
+          constexpr uint32_t id = tc::idesc_tf32(128, 2 * NV);
+          const uint32_t sbo = 32 * kTcRows;
+          const uint32_t v_h = tc::smem_u32(sStage + (k % S) * SM::kStage + 2 * SM::kA);
+          const uint32_t tE = tbase + 128 * (k % NE), tO = tbase + TcAcc<MM>::kOcol + 2 * NV * (seg & 1);
+#pragma unroll
+          for (int ks = 0; ks < kTcRows / 8; ++ks)
+            tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_h + ks * 256, 128, sbo), id, (!first || ks > 0) ? 1u : 0u);
+          tc::mma_commit(pv_done + k % NE);
+          if (last) tc::mma_commit(o_ready + (seg & 1));
+          last_pv = k;
+        }
+      }
+      if (!ok) {
+        ctl->tc_error = 1;
+        // let the copies and products already issued finish (bounded) before
+        // shared memory and TMEM are released
+        for (int k = last_pv + 1; k < next_load; ++k) tc::mbar_wait(full + k % S, (uint32_t)(k / S) & 1u, kLimit);
+        if (last_g >= 0) tc::mbar_wait(g_done + last_g % NE, (uint32_t)(last_g / NE) & 1u, kLimit);
+        if (last_pv >= 0) pv_wait(last_pv);
+      }
     }
-    ok = __syncthreads_and(tc::mbar_wait(bars + 3, ph_mma, 1 << 24)) != 0;
-    ph_mma ^= 1;
-    tc::fence_after();
-    if (!ok) break;
-    // kernel values k = 2^E, rounded to tf32, written back in place
-#pragma unroll
-    for (int c0 = 0; c0 < 128; c0 += 32) {
+  } else {
+    // ------------------------------------------------------------ exponent warps
+    const int quarter = warp & 3, cq = warp >> 2;
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    const bool epi = warp >= kPhiEpiWarp0;
+    int seg = 0;
+    for (int k = 0; k < nk; ++k) {
+      const int f = f0 + k;
+      if (k > 0 && f % nt == 0) ++seg;
+      const bool w = tc::mbar_wait(g_done + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
+      ok = __all_sync(0xffffffffu, w) != 0;
+      if (!ok) break;
+      tc::fence_after();
+      const uint32_t tE = tbase + 128 * (k % NE) + lane_off + 32 * cq;
       uint32_t r[32];
-      tc::tmem_ld32(tE + lane_off + c0, r);
+      tc::tmem_ld32(tE, r);
       tc::tmem_wait_ld();
 #pragma unroll
-      for (int k = 0; k < 32; ++k) r[k] = tc::to_tf32(exp2f(__uint_as_float(r[k])));
-      tc::tmem_st32(tE + lane_off + c0, r);
-    }
-    tc::tmem_wait_st();
-    tc::fence_before();
-    __syncthreads();
-    // O += K v (v split in two); then refill this stage with tile jt + 2
-    if (t == 0) {
-      tc::fence_after();
-      constexpr uint32_t id = tc::idesc_tf32(128, NV);
-      const uint32_t sbo = 32 * kTcRows;
-      const uint32_t v_h = tc::smem_u32(sV), v_l = v_h + SM::kV;
+      for (int q = 0; q < 32; ++q) {
+        float e;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(__uint_as_float(r[q])));
+        r[q] = tc::to_tf32(e);
+      }
+      tc::tmem_st32(tE, r);
+      tc::tmem_wait_st();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(p_ready + k % NE);
+      const bool last = (k == nk - 1) || ((f + 1) % nt == 0);
+      if (epi && last) {
+        // this row segment's outputs: wait for its last second product, then read them
+        const bool w2 = tc::mbar_wait(o_ready + (seg & 1), (uint32_t)(seg >> 1) & 1u, kLimit);
+        ok = __all_sync(0xffffffffu, w2) != 0;
+        if (!ok) break;
+        tc::fence_after();
+        const uint32_t tO = tbase + TcAcc<MM>::kOcol + 2 * NV * (seg & 1) + lane_off;
+        float o[NV];
 #pragma unroll
-      for (int ks = 0; ks < kTcRows / 8; ++ks)
-        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_h + ks * 256, 128, sbo), id, (jt > jt0 || ks > 0) ? 1u : 0u);
+        for (int c0 = 0; c0 < 2 * NV; c0 += 32) {
+          uint32_t rr[32];
+          tc::tmem_ld32(tO + c0, rr);
+          tc::tmem_wait_ld();
 #pragma unroll
-      for (int ks = 0; ks < kTcRows / 8; ++ks)
-        tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_l + ks * 256, 128, sbo), id, 1u);
-      tc::mma_commit(bars + 3);
-    }
-    ok = __syncthreads_and(tc::mbar_wait(bars + 3, ph_mma, 1 << 24)) != 0;
-    ph_mma ^= 1;
-    tc::fence_after();
-    if (t == 0 && ok && jt + 2 < jt1) {
-      tc::mbar_expect_tx(bars + s, SM::kStage);
-      tc::bulk_g2s(sStage[s], imgBV + (size_t)(jt + 2) * (SM::kStage / 4), SM::kStage, bars + s);
-    }
-  }
-
-  const int i = i0 + t;
-  if (jt1 > jt0 && ok) {
-    float o[64];
+          for (int c = 0; c < 32; ++c) {
+            const int cc = c0 + c;  // hi half [0, NV), lo half [NV, 2 NV)
+            if (cc < NV) o[cc] = __uint_as_float(rr[c]);
+            else if (cc < 2 * NV) o[cc - NV] += __uint_as_float(rr[c]);
+          }
+        }
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(o_free + (seg & 1));
+        const int I = f / nt;
+        const int i = I * kTcRows + quarter * 32 + lane;
+        // slot of this CTA in row I; the row's last CTA zeroes the unused ones
+        const int b0 = phi_tc_first_cta((long long)I * nt, T, G);
+        const int slot = blockIdx.x - b0;
+        const bool row_end = (f + 1) % nt == 0;
+        if (i < N) {
+          const float two_over_bw = 2.0f / ctl->bw;
+          const float o1s = o[2 * MM];
 #pragma unroll
-    for (int c0 = 0; c0 < NV; c0 += 32) {
-      uint32_t r[32];
-      tc::tmem_ld32(tO + lane_off + c0, r);
-      tc::tmem_wait_ld();
-#pragma unroll
-      for (int k = 0; k < 32; ++k) o[c0 + k] = __uint_as_float(r[k]);
-    }
-    if (i < N) {
-      const float two_over_bw = 2.0f / ctl->bw;
-      const float o1 = o[2 * MM];
-#pragma unroll
-      for (int k = 0; k < MM; ++k) {
-        if (k < M) {
-          const float ui = u[(size_t)k * N + i];
-          phi_part[((size_t)blockIdx.y * M + k) * N + i] = o[k] + two_over_bw * (ui * o1 - o[MM + k]);
+          for (int c = 0; c < MM; ++c) {
+            if (c < M) {
+              const float ui = u[(size_t)c * N + i];
+              phi_part[((size_t)slot * M + c) * N + i] = o[c] + two_over_bw * (ui * o1s - o[MM + c]);
+            }
+          }
+          if (row_end)
+            for (int sl = slot + 1; sl < slots; ++sl)
+              for (int c = 0; c < M; ++c) phi_part[((size_t)sl * M + c) * N + i] = 0.f;
         }
       }
     }
-  } else if (jt1 > jt0) {
-    if (t == 0) ctl->tc_error = 1;
-  } else if (i < N) {
-    // empty chunk: contributes zeros
-    for (int k = 0; k < M; ++k) phi_part[((size_t)blockIdx.y * M + k) * N + i] = 0.f;
+    if (!ok && lane == 0) ctl->tc_error = 1;
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 256);
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
+// Persistent grid of the tensor-core phi: one CTA per SM (each holds all
+// 512 TMEM columns), at most one per tile.
+static int phi_tc_grid(int N) {
+  static int sms_of[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (sms_of[dev] == 0 && cudaDeviceGetAttribute(&sms_of[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  const long long nt = (N + kTcRows - 1) / kTcRows;
+  return (int)(nt * nt < sms_of[dev] ? nt * nt : sms_of[dev]);
+}
+
+// Number of partial-phi slots: the most CTAs whose runs meet one row tile.
+int phi_tc_slots(int N) {
+  const int G = phi_tc_grid(N);
+  if (G <= 0) return 0;
+  const long long nt = (N + kTcRows - 1) / kTcRows, T = nt * nt;
+  int most = 1;
+  for (long long I = 0; I < nt; ++I) {
+    const int n = phi_tc_first_cta((I + 1) * nt - 1, T, G) - phi_tc_first_cta(I * nt, T, G) + 1;
+    if (n > most) most = n;
+  }
+  return most;
 }
 
 template <int MM>
-static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st) {
+static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_used, cudaStream_t st) {
   using SM = TcSmem<MM>;
   const int Npad = (N + kTcRows - 1) / kTcRows * kTcRows;
   const int ntiles = Npad / kTcRows;
-  const int tiles_per_chunk = (ntiles + chunks - 1) / chunks;
   float* imgA = w.tc;
   float* imgBV = imgA + (size_t)ntiles * (2 * SM::kA / 4);
+  const int G = phi_tc_grid(N);
+  const int slots = phi_tc_slots(N);
+  if (G <= 0 || slots <= 0 || slots > w.chunks) return cudaErrorInvalidConfiguration;
   phi_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, w.u, w.gu, w.ctl, imgA, imgBV);
-  const int smem = SM::kBytes;
+  // at least 116 KB so that two CTAs never share an SM (each allocates all
+  // 512 TMEM columns)
+  const int smem = SM::kBytes > 116 * 1024 ? SM::kBytes : 116 * 1024;
   static bool attr[64];
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr[dev]) {
     cudaError_t e = cudaFuncSetAttribute(phi_tc_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(phi_tc_kernel<MM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  dim3 grid(ntiles, chunks);
-  phi_tc_kernel<MM><<<grid, 128, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, tiles_per_chunk);
+  phi_tc_kernel<MM><<<G, kPhiThreads, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, slots);
+  *slots_used = slots;
   return cudaGetLastError();
 }
 
@@ -272,12 +419,12 @@ size_t phi_tc_floats(int N, int M) {
   return Npad * (4 * (size_t)KA + 2 * (size_t)NV);
 }
 
-cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int chunks, cudaStream_t st) {
-  if (M <= 2) return launch_phi_tc_mm<2>(N, M, w, chunks, st);
-  if (M <= 4) return launch_phi_tc_mm<4>(N, M, w, chunks, st);
-  if (M <= 8) return launch_phi_tc_mm<8>(N, M, w, chunks, st);
-  if (M <= 10) return launch_phi_tc_mm<10>(N, M, w, chunks, st);
-  return launch_phi_tc_mm<16>(N, M, w, chunks, st);
+cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cudaStream_t st) {
+  if (M <= 2) return launch_phi_tc_mm<2>(N, M, w, slots_used, st);
+  if (M <= 4) return launch_phi_tc_mm<4>(N, M, w, slots_used, st);
+  if (M <= 8) return launch_phi_tc_mm<8>(N, M, w, slots_used, st);
+  if (M <= 10) return launch_phi_tc_mm<10>(N, M, w, slots_used, st);
+  return launch_phi_tc_mm<16>(N, M, w, slots_used, st);
 }
 
 }  // namespace pds

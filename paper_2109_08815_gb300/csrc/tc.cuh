@@ -40,6 +40,12 @@ __device__ __forceinline__ void mbar_init(uint64_t* m, uint32_t count) {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// One arrival on the barrier (release semantics for this thread's prior
+// shared-memory and, after tcgen05.fence::before_thread_sync, TMEM accesses).
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+
 // Wait for the given phase parity; gives up after `limit` polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int limit) {
   for (int it = 0; it < limit; ++it) {
