@@ -101,6 +101,7 @@ struct SvgdCtl {
   unsigned long long inside; // pairs with lo <= d <= hi (= candidates)
   int mode;                  // 0: select among candidates; 1: full radix passes over all pairs
   int tc_error;              // set if a tensor-core pass gave up waiting for its products
+  unsigned int gmax[16];     // max |g_u| per component (float bits); reset at the end of each step
 };
 
 struct SvgdWork {

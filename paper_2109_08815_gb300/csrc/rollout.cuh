@@ -375,10 +375,13 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
 // One thread per unit u = w * N + i (window w, particle i): the window's
 // forward rollout with its observation and defect terms (Eqs. 2, 4, 5), then
 // (grad != 0) the reverse sweep from checkpoints every K steps.
+// seg (may be NULL): the thread's K slots for the recomputed states of the
+// segment being reversed, seg[slot * 2 NL * seg_stride + var * seg_stride]
+// -- shared memory when they fit there, else the segment part of the tape.
 template <int NL, bool FAST>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
-                                             size_t u) {
+                                             size_t u, float* seg = nullptr, size_t seg_stride = 0) {
   const size_t U = (size_t)N * c.W;
   const int w = (int)(u / N);
   const int i = (int)(u - (size_t)w * N);
@@ -402,7 +405,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   const int h = t1 - t0;
 
   float* ckpt = parts.tape;
-  float* segbuf = parts.tape + (size_t)c.max_seg * (2 * NL) * U;
+  float* segbuf = seg ? seg : parts.tape + (size_t)c.max_seg * (2 * NL) * U + u;
+  const size_t sstride = seg ? seg_stride : U;
   const int K = c.K;
 
   // ---------------- forward
@@ -455,13 +459,13 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     tape_load<NL>(ckpt, sg, U, u, qs, vs);
     // recompute s_a .. s_{e-1} into the segment buffer
     for (int k = a; k < e; ++k) {
-      tape_store<NL>(segbuf, k - a, U, u, qs, vs);
+      tape_store<NL>(segbuf, k - a, sstride, 0, qs, vs);
       if (k + 1 < e) chain_step<NL, FAST>(qs, vs, P, c.dt);
     }
     for (int k = e - 1; k >= a; --k) {
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL>(c, t0 + k + 1, qh, vh, qb, vb, true);
-      tape_load<NL>(segbuf, k - a, U, u, qs, vs);
+      tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
       chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
@@ -487,14 +491,20 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   }
 }
 
+// seg_smem: the reverse sweep's recomputed segment states live in dynamic
+// shared memory (K x 2 NL x blockDim floats), else in the tape.
 template <int NL, bool FAST>
 __global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const ChainParams c, const float* __restrict__ X,
                                                                         int N, Partials parts, int grad,
-                                                                        int32_t* __restrict__ status) {
+                                                                        int32_t* __restrict__ status, int seg_smem) {
+  extern __shared__ float seg_sh[];
   const size_t U = (size_t)N * c.W;
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
-  rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u);
+  if (seg_smem)
+    rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+  else
+    rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u);
 }
 
 // Persistent rollout over several problems with the same chain length
@@ -576,10 +586,15 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
                               int32_t* status, cudaStream_t st) {
   const size_t U = (size_t)N * c.W;
   const unsigned blocks = (unsigned)((U + 127) / 128);
+  // the reverse sweep's K recomputed states in shared memory when they fit
+  // in the default 48 KB of a block
+  const size_t seg_bytes = (size_t)c.K * 2 * NL * 128 * sizeof(float);
+  const int seg_smem = (grad && seg_bytes <= 48 * 1024) ? 1 : 0;
+  const size_t smem = seg_smem ? seg_bytes : 0;
   if (c.fast_math)
-    rollout_kernel<NL, true><<<blocks, 128, 0, st>>>(c, X, N, parts, grad, status);
+    rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
   else
-    rollout_kernel<NL, false><<<blocks, 128, 0, st>>>(c, X, N, parts, grad, status);
+    rollout_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
   return cudaGetLastError();
 }
 

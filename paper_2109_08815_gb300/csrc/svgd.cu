@@ -38,11 +38,23 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     ctl->mode = mode;
   }
   const int total = sp.M * sp.N;
+  const int k = idx < total ? idx / sp.N : -1;
+  unsigned int gbits = 0u;
   if (idx < total) {
-    const int k = idx / sp.N;
     const float width = sp.hi[k] - sp.lo[k];
     u[idx] = (X[idx] - sp.lo[k]) / width;
-    gu[idx] = G[idx] * width;
+    const float g = G[idx] * width;
+    gu[idx] = g;
+    gbits = __float_as_uint(fabsf(g));
+  }
+  // per-component max |g_u| (scales of the fp16 second product of the
+  // tensor-core phi); one atomic per warp when the warp holds one component
+  const int k0 = __shfl_sync(0xffffffffu, k, 0);
+  if (__all_sync(0xffffffffu, k == k0)) {
+    const unsigned int m = __reduce_max_sync(0xffffffffu, gbits);
+    if ((threadIdx.x & 31) == 0 && k0 >= 0 && m) atomicMax(&ctl->gmax[k0], m);
+  } else if (k >= 0 && gbits) {
+    atomicMax(&ctl->gmax[k], gbits);
   }
 }
 
@@ -541,13 +553,14 @@ __global__ void __launch_bounds__(kTile) svgd_phi_kernel(int N, int M, const flo
   }
 }
 
-__global__ void svgd_adam_kernel(SvgdParams sp, const SvgdCtl* __restrict__ ctl, float* __restrict__ X,
+__global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float* __restrict__ X,
                                  const float* __restrict__ G, const float* __restrict__ phi_part, int chunks,
                                  float* __restrict__ am, float* __restrict__ av, float* __restrict__ bw_out,
                                  float* __restrict__ phi_out) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t total = (size_t)sp.P * sp.N;
   if (idx == 0 && bw_out) *bw_out = ctl->bw;
+  if (idx < 16) ctl->gmax[idx] = 0u;  // for the next step's prep kernel
   if (idx >= total) return;
   const int r = (int)(idx / sp.N);
   const int i = (int)(idx - (size_t)r * sp.N);

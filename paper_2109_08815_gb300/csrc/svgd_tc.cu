@@ -26,6 +26,7 @@
 // the slot (CTA index - first CTA of the row); the last CTA of a row zeroes
 // the slots no CTA used, and the Adam kernel adds the slots in a fixed
 // order, so the result is deterministic.
+#include <cuda_fp16.h>
 #include <math.h>
 
 #include "pds_internal.cuh"
@@ -37,11 +38,13 @@ constexpr int kTcRows = 128;
 
 // Column layout (compile-time, MM >= M; unused slots are zero):
 //   a, b: [0, MM) coordinates, MM and MM + 1 the norm terms;
-//   v:    [0, MM) gradient, [MM, 2 MM) coordinates, 2 MM the constant 1.
+//   v:    fp16 high parts [0, MM) scaled gradient, [MM, 2 MM) coordinates,
+//         2 MM the constant 1; low parts [2 MM + 1, 3 MM + 1) gradient and
+//         [3 MM + 1, 4 MM + 1) coordinates.
 template <int MM>
 struct TcDims {
-  static constexpr int KA = ((MM + 2 + 7) / 8) * 8;        // exponent product depth
-  static constexpr int NV = ((2 * MM + 1 + 15) / 16) * 16;  // columns of v
+  static constexpr int KA = ((MM + 2 + 7) / 8) * 8;         // exponent product depth
+  static constexpr int NV = ((4 * MM + 1 + 15) / 16) * 16;  // columns of v (high and low parts)
 };
 
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
@@ -50,16 +53,16 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
 }
 
 // Tensor-memory plan (512 columns): NE exponent buffers of 128 columns, then
-// two output sets (one per row segment in flight) of 2 NV columns each: the
-// second product takes v's tf32 high and low parts as one operand of 2 NV
-// columns, so each 8-deep slice of K is a single instruction, and the
-// epilogue adds the two halves.  Three exponent buffers let the exponent
+// two output sets (one per row segment in flight) of NV columns each: the
+// second product takes v's fp16 high and low parts as one operand of NV
+// columns, so each 16-deep slice of K is a single instruction, and the
+// epilogue adds the two parts.  Three exponent buffers let the exponent
 // product of tile k+1 queue behind the second product of tile k-1 without
-// waiting for it; M = 16 (NV = 48) leaves room for two.
+// waiting for it; M = 16 (NV = 80) leaves room for two.
 template <int MM>
 struct TcAcc {
   static constexpr int NV = TcDims<MM>::NV;
-  static constexpr int NE = (3 * 128 + 2 * 2 * NV <= 512) ? 3 : 2;
+  static constexpr int NE = (3 * 128 + 2 * NV <= 512) ? 3 : 2;
   static constexpr int kOcol = 128 * NE;  // first output column
 };
 
@@ -67,11 +70,26 @@ template <int MM>
 struct TcSmem {
   static constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   static constexpr int kA = kTcRows * KA * 4;     // one operand tile (128 rows x KA), bytes
-  static constexpr int kV = NV * kTcRows * 4;     // one v^T tile, bytes
-  static constexpr int kStage = 2 * kA + 2 * kV;  // b (hi, lo) + v^T (hi, lo) of one column tile
+  static constexpr int kV = NV * kTcRows * 2;  // one v^T tile in fp16 (high and low parts), bytes
+  static constexpr int kStage = 2 * kA + kV;  // b (hi, lo) + v^T of one column tile
   static constexpr int kStages = (2 * 2 * kA + 3 * kStage + 256 <= 220 * 1024) ? 3 : 2;
   static constexpr int kBytes = 2 * 2 * kA + kStages * kStage + 256;  // two a slots, the stages, barriers
 };
+
+// Byte offset of element (row, k) in a K-major fp16 tile of K_total
+// columns: core matrices of 8 rows x 8 elements (128 B), consecutive along K
+// (leading byte offset 128), then along rows (stride byte offset 16 K_total).
+__host__ __device__ __forceinline__ uint32_t kmajor_offset16(int row, int k, int K_total) {
+  return (uint32_t)((row >> 3) * (K_total >> 3) * 128 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Power-of-two scale of a gradient component for fp16: the exponent s with
+// max |g| 2^-s < 2^14 (0 for zero, subnormal or non-finite maxima).
+__device__ __forceinline__ int phi_g_shift(unsigned int gmax_bits) {
+  const int E = (int)((gmax_bits >> 23) & 0xFFu);
+  if (E == 0 || E == 255) return 0;
+  return E - 126 - 14;
+}
 
 // Operand tiles for every particle, written directly in the shared-memory
 // image the products read (K-major core-matrix layout), one image per tile
@@ -102,8 +120,7 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
   float* BV = imgBV + (size_t)tile * (SM::kStage / 4);
   float* Bh = BV;
   float* Bl = BV + SM::kA / 4;
-  float* Vh = BV + 2 * SM::kA / 4;
-  float* Vl = BV + 2 * SM::kA / 4 + SM::kV / 4;
+  __half* V = reinterpret_cast<__half*>(BV + 2 * SM::kA / 4);
 #pragma unroll
   for (int k = 0; k < KA; ++k) {
     const float a = k < MM ? 2.f * L * x[k] : (k == MM ? -L * n : (k == MM + 1 ? -L : 0.f));
@@ -117,15 +134,17 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
     Bh[o] = h;
     Bl[o] = l;
   }
+  // v = (g 2^-s, u, 1) in fp16 high parts, then the low parts of g 2^-s and u
 #pragma unroll
-  for (int c = 0; c < NV; ++c) {
-    const float v = c < MM ? g[c] : (c < 2 * MM ? x[c - MM] : (c == 2 * MM && live ? 1.f : 0.f));
-    const uint32_t o = tc::kmajor_offset(c, r, kTcRows) >> 2;
-    float h, l;
-    split_tf32(v, h, l);
-    Vh[o] = h;
-    Vl[o] = l;
+  for (int c = 0; c < 2 * MM; ++c) {
+    const float v = c < MM ? ldexpf(g[c], -phi_g_shift(ctl->gmax[c])) : x[c - MM];
+    const __half h = __float2half_rn(v);
+    V[kmajor_offset16(c, r, kTcRows) >> 1] = h;
+    V[kmajor_offset16(2 * MM + 1 + c, r, kTcRows) >> 1] = __float2half_rn(v - __half2float(h));
   }
+  V[kmajor_offset16(2 * MM, r, kTcRows) >> 1] = __float2half_rn(live ? 1.f : 0.f);
+#pragma unroll
+  for (int c = 4 * MM + 1; c < NV; ++c) V[kmajor_offset16(c, r, kTcRows) >> 1] = __float2half_rn(0.f);
 }
 
 constexpr int kPhiExpWarps = 16;                    // 4 lane quarters x 4 column quarters
@@ -202,9 +221,6 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         tc::bulk_g2s(stg, imgBV + (size_t)J * (SM::kStage / 4), SM::kStage, full + k % S);
         next_load = k + 1;
       };
-      auto pv_wait = [&](int k) {  // second product of tile k done
-        return tc::mbar_wait(pv_done + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
-      };
       auto gram = [&](int k) {  // E[k % NE] = a b^T (three split products)
         const int f = f0 + k, I = f / nt;
         tc::fence_after();
@@ -223,48 +239,58 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         tc::mma_commit(g_done + k % NE);
         last_g = k;
       };
+      // waits that are usually already complete test the barrier first
+      auto wait = [&](uint64_t* bar, uint32_t parity) {
+        return tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
+      };
       for (int k = 0; k < S && k < nk; ++k) load(k);
-      ok = tc::mbar_wait(full + 0, 0u, kLimit);
+      ok = wait(full + 0, 0u);
       if (ok) gram(0);
       int seg = 0;  // row segment of tile k within this CTA's run
       for (int k = 0; k < nk && ok; ++k) {
         const int f = f0 + k;
         if (k > 0 && f % nt == 0) ++seg;
+        // (a) exponent product of tile k+1: its exponent buffer was last read
+        // by the second product of tile k+1-NE (already waited for in (c)
+        // when NE = 3), its operands by now landed
         if (k + 1 < nk) {
-          // exponent buffer (k+1) % NE was last read by the second product of tile k+1-NE
-          if (k + 1 - NE >= 0) ok = pv_wait(k + 1 - NE);
+          if (NE == 2 && k >= 1) ok = wait(pv_done + (k - 1) % NE, (uint32_t)((k - 1) / NE) & 1u);
           if (ok && next_load == k + 1) {  // fewer stages than needed to prefetch
-            if (k + 1 - S >= 0) ok = pv_wait(k + 1 - S);
+            if (k + 1 - S >= 0) ok = wait(pv_done + (k + 1 - S) % NE, (uint32_t)((k + 1 - S) / NE) & 1u);
             if (ok) load(k + 1);
           }
-          if (ok) ok = tc::mbar_wait(full + (k + 1) % S, (uint32_t)((k + 1) / S) & 1u, kLimit);
+          if (ok) ok = wait(full + (k + 1) % S, (uint32_t)((k + 1) / S) & 1u);
           if (ok) gram(k + 1);
         }
-        // stage (k-1) % S is free once the second product of tile k-1 is done
-        if (ok && k >= 1 && next_load == k - 1 + S && k - 1 + S < nk) {
-          ok = pv_wait(k - 1);
-          if (ok) load(k - 1 + S);
-        }
-        // kernel values of tile k written by every exponent warp
-        if (ok) ok = tc::mbar_wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
+        // (b) second product of tile k once every exponent warp wrote its
+        // kernel values (and the output set was read for segment seg - 2)
+        if (ok) ok = wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u);
         const bool first = (k == 0) || (f % nt == 0);
         const bool last = (k == nk - 1) || ((f + 1) % nt == 0);
-        // output set seg & 1 was read for segment seg - 2
-        if (ok && first && seg >= 2) ok = tc::mbar_wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u, kLimit);
+        if (ok && first && seg >= 2) ok = wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u);
         if (!ok) break;
         tc::fence_after();
         {
-          // O[seg & 1] (+)= K [v hi | v lo]: one instruction per 8-deep slice
-          constexpr uint32_t id = tc::idesc_tf32(128, 2 * NV);
-          const uint32_t sbo = 32 * kTcRows;
+          // O[seg & 1] (+)= K v in fp16: one instruction per 16-deep slice of
+          // j; the kernel values of j = 16 ks .. 16 ks + 15 sit packed in
+          // columns 32 (ks / 2) + 8 (ks % 2) of the exponent buffer
+          constexpr uint32_t id = tc::idesc_f16(128, NV);
+          const uint32_t sbo = 16 * kTcRows;
           const uint32_t v_h = tc::smem_u32(sStage + (k % S) * SM::kStage + 2 * SM::kA);
-          const uint32_t tE = tbase + 128 * (k % NE), tO = tbase + TcAcc<MM>::kOcol + 2 * NV * (seg & 1);
+          const uint32_t tE = tbase + 128 * (k % NE), tO = tbase + TcAcc<MM>::kOcol + NV * (seg & 1);
 #pragma unroll
-          for (int ks = 0; ks < kTcRows / 8; ++ks)
-            tc::mma_ts(tO, tE + ks * 8, tc::smem_desc(v_h + ks * 256, 128, sbo), id, (!first || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < kTcRows / 16; ++ks)
+            tc::mma_ts_f16(tO, tE + 32 * (ks >> 1) + 8 * (ks & 1), tc::smem_desc(v_h + ks * 256, 128, sbo), id,
+                           (!first || ks > 0) ? 1u : 0u);
           tc::mma_commit(pv_done + k % NE);
           if (last) tc::mma_commit(o_ready + (seg & 1));
           last_pv = k;
+        }
+        // (c) the second product of tile k-1 frees exponent buffer (k-1) % NE
+        // and stage (k-1) % S, which takes tile k-1+S
+        if (k >= 1) {
+          ok = wait(pv_done + (k - 1) % NE, (uint32_t)((k - 1) / NE) & 1u);
+          if (ok && next_load == k - 1 + S && k - 1 + S < nk) load(k - 1 + S);
         }
       }
       if (!ok) {
@@ -273,7 +299,7 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         // shared memory and TMEM are released
         for (int k = last_pv + 1; k < next_load; ++k) tc::mbar_wait(full + k % S, (uint32_t)(k / S) & 1u, kLimit);
         if (last_g >= 0) tc::mbar_wait(g_done + last_g % NE, (uint32_t)(last_g / NE) & 1u, kLimit);
-        if (last_pv >= 0) pv_wait(last_pv);
+        if (last_pv >= 0) tc::mbar_wait(pv_done + last_pv % NE, (uint32_t)(last_pv / NE) & 1u, kLimit);
       }
     }
   } else {
@@ -293,13 +319,16 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
       uint32_t r[32];
       tc::tmem_ld32(tE, r);
       tc::tmem_wait_ld();
+      uint32_t pk[16];  // kernel values in fp16, two per column (even j in the low half)
 #pragma unroll
-      for (int q = 0; q < 32; ++q) {
-        float e;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(__uint_as_float(r[q])));
-        r[q] = tc::to_tf32(e);
+      for (int q = 0; q < 16; ++q) {
+        float e0, e1;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e0) : "f"(__uint_as_float(r[2 * q])));
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e1) : "f"(__uint_as_float(r[2 * q + 1])));
+        const __half2 h2 = __floats2half2_rn(e0, e1);
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h2);
       }
-      tc::tmem_st32(tE, r);
+      tc::tmem_st16(tE, pk);
       tc::tmem_wait_st();
       tc::fence_before();
       __syncwarp();
@@ -311,19 +340,16 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         ok = __all_sync(0xffffffffu, w2) != 0;
         if (!ok) break;
         tc::fence_after();
-        const uint32_t tO = tbase + TcAcc<MM>::kOcol + 2 * NV * (seg & 1) + lane_off;
+        const uint32_t tO = tbase + TcAcc<MM>::kOcol + NV * (seg & 1) + lane_off;
         float o[NV];
 #pragma unroll
-        for (int c0 = 0; c0 < 2 * NV; c0 += 32) {
+        for (int c0 = 0; c0 < NV; c0 += 32) {
           uint32_t rr[32];
           tc::tmem_ld32(tO + c0, rr);
           tc::tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const int cc = c0 + c;  // hi half [0, NV), lo half [NV, 2 NV)
-            if (cc < NV) o[cc] = __uint_as_float(rr[c]);
-            else if (cc < 2 * NV) o[cc - NV] += __uint_as_float(rr[c]);
-          }
+          for (int c = 0; c < 32; ++c)
+            if (c0 + c < NV) o[c0 + c] = __uint_as_float(rr[c]);
         }
         tc::fence_before();
         __syncwarp();
@@ -341,7 +367,9 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
           for (int c = 0; c < MM; ++c) {
             if (c < M) {
               const float ui = u[(size_t)c * N + i];
-              phi_part[((size_t)slot * M + c) * N + i] = o[c] + two_over_bw * (ui * o1s - o[MM + c]);
+              const float og = ldexpf(o[c] + o[2 * MM + 1 + c], phi_g_shift(ctl->gmax[c]));
+              const float ou = o[MM + c] + o[3 * MM + 1 + c];
+              phi_part[((size_t)slot * M + c) * N + i] = og + two_over_bw * (ui * o1s - ou);
             }
           }
           if (row_end)
@@ -415,8 +443,8 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_
 size_t phi_tc_floats(int N, int M) {
   const size_t Npad = (size_t)(N + kTcRows - 1) / kTcRows * kTcRows;
   const int MM = M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 10 ? 10 : 16;
-  const int KA = ((MM + 2 + 7) / 8) * 8, NV = ((2 * MM + 1 + 15) / 16) * 16;  // as TcDims<MM>
-  return Npad * (4 * (size_t)KA + 2 * (size_t)NV);
+  const int KA = ((MM + 2 + 7) / 8) * 8, NV = ((4 * MM + 1 + 15) / 16) * 16;  // as TcDims<MM>
+  return Npad * (4 * (size_t)KA + (size_t)NV / 2);  // a, b (tf32 hi, lo) and v (fp16) per particle
 }
 
 cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cudaStream_t st) {
