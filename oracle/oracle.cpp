@@ -20,7 +20,10 @@
 //   * its gradient by forward-mode dual numbers, one window at a time
 //     (exact up to rounding, independent of the GPU's reverse adjoint);
 //   * the SVGD update of Eq. (1) with an RBF kernel and the median heuristic
-//     (Sec. IV-A), driven by Adam (Algorithm 1's "learning rate scheduler").
+//     (Sec. IV-A), driven by Adam (Algorithm 1's "learning rate scheduler");
+//   * constrained SVGD (Sec. IV-E, Algorithm 1): the observation likelihood,
+//     the defect and limit constraints, their MDMM gradient with the
+//     per-particle multipliers held fixed, and the MDMM update.
 //
 // Readings taken where the paper is silent (all documented in the design doc):
 //   window w covers steps t_w+1 .. t_{w+1}, t_w = floor(w*T/W); window 0
@@ -438,6 +441,107 @@ static double particle_loglik_grad(const Problem& P, const double* x, double* gr
       for (int k = 0; k < S; ++k) grad[M + w * S + k] += ll.d[M + S + k];
   }
   total += limit_logprior(P, x, grad);
+  return total;
+}
+
+// ---------------------------------------------------------------------------
+// Constrained SVGD (Sec. IV-E, Eq. mdmm-loss, Algorithm 1): the likelihood is
+// the observation term only; the defect and limit terms become equality
+// constraints handled by MDMM with per-particle multipliers.
+//   g_def,w = ||s^s_w - s_end(w-1)||^2 / sigma_def^2      (w = 1..W-1)
+//   g_lim,k = clamp(u_k, 0, 1) - u_k,  u = (theta - lo) / (hi - lo)
+//   Psi     = sum_w (lam_def,w g_def,w + c/2 g_def,w^2)
+//           + sum_k (lam_lim,k g_lim,k + c/2 g_lim,k^2)
+// with the multipliers held fixed, so that the MDMM flow is
+//   theta' = phi(theta) - dPsi/dtheta,  s' = d(log p_obs - Psi)/ds,
+//   lam'   = g.
+// ---------------------------------------------------------------------------
+// The window's observation log-likelihood and, for w < W-1, the defect
+// constraint value g_def,w+1 (the two parts of window_loglik, kept apart).
+template <class T>
+static void window_obs_and_defect(const Problem& P, const T* m, const T* l, const T* b, const T* s_start,
+                                  const T* s_next, int w, T* obs_ll, T* gdef) {
+  const int n = P.n, S = 2 * n;
+  Chain<T> ch{n, m, l, b, P.g};
+  std::vector<T> s(s_start, s_start + S), sn(S);
+  const int t0 = window_start(P, w), t1 = window_start(P, w + 1);
+  const double so2 = P.sigma_obs * P.sigma_obs;
+  const double obs_const = -0.5 * P.D * std::log(2.0 * M_PI * so2);
+  T ll(0.0);
+  for (int t = t0 + 1; t <= t1; ++t) {
+    step(ch, P.dt, s.data(), sn.data());
+    s.swap(sn);
+    T acc(0.0);
+    for (int k = 0; k < P.D; ++k) {
+      T r = T(P.obs[(size_t)(t - 1) * P.D + k]) - s[P.obs_index[k]];
+      acc += r * r;
+    }
+    ll += acc * T(-0.5 / so2) + T(obs_const);
+  }
+  *obs_ll = ll;
+  T g(0.0);
+  if (w < P.W - 1) {
+    for (int k = 0; k < S; ++k) {
+      T d = s_next[k] - s[k];
+      g += d * d;
+    }
+    g = g * T(1.0 / (P.sigma_def * P.sigma_def));
+  }
+  *gdef = g;
+}
+
+// One particle x = [theta (M), s^s_1..s^s_{W-1} (S each), lam_def (W-1),
+// lam_lim (M)]: returns log p_obs and writes out[Pc + M]:
+//   [0, M)                  d log p_obs / d theta
+//   [M, M + (W-1) S)        d (log p_obs - Psi) / d s^s
+//   [.., + (W-1))           g_def,w        (the lam_def flow)
+//   [.., + M)               g_lim,k        (the lam_lim flow)
+//   [Pc, Pc + M)            - dPsi / d theta
+static double particle_csvgd(const Problem& P, double c, const double* x, double* out) {
+  const int n = P.n, S = 2 * n, M = P.M, W = P.W;
+  const int Pms = M + (W - 1) * S, Pc = Pms + (W - 1) + M;
+  std::fill(out, out + Pc + M, 0.0);
+  const double* lam_def = x + Pms;
+  const double* lam_lim = x + Pms + (W - 1);
+  double total = 0.0;
+  for (int w = 0; w < W; ++w) {
+    const double* ss = (w == 0) ? P.s0 : x + M + (w - 1) * S;
+    const double* sn = (w < W - 1) ? x + M + w * S : nullptr;
+    g_nd = M + 2 * S;
+    std::vector<Dual> th(M), s_start(S), s_next(S);
+    for (int k = 0; k < M; ++k) { th[k] = Dual(x[k]); th[k].d[k] = 1.0; }
+    for (int k = 0; k < S; ++k) {
+      s_start[k] = Dual(ss[k]);
+      if (w > 0) s_start[k].d[M + k] = 1.0;
+      if (sn) { s_next[k] = Dual(sn[k]); s_next[k].d[M + S + k] = 1.0; }
+    }
+    std::vector<Dual> m, l, b;
+    physical_params<Dual>(P, th.data(), m, l, b);
+    Dual ll, g;
+    window_obs_and_defect<Dual>(P, m.data(), l.data(), b.data(), s_start.data(), sn ? s_next.data() : nullptr, w,
+                                &ll, &g);
+    total += ll.v;
+    for (int k = 0; k < M; ++k) out[k] += ll.d[k];
+    if (w > 0)
+      for (int k = 0; k < S; ++k) out[M + (w - 1) * S + k] += ll.d[M + k];
+    if (sn) {
+      // constraint g_def,w+1 with multiplier lam_def[w]: -dPsi = -(lam + c g) dg
+      const double kappa = lam_def[w] + c * g.v;
+      out[Pms + w] = g.v;
+      for (int k = 0; k < M; ++k) out[Pc + k] -= kappa * g.d[k];
+      if (w > 0)
+        for (int k = 0; k < S; ++k) out[M + (w - 1) * S + k] -= kappa * g.d[M + k];
+      for (int k = 0; k < S; ++k) out[M + w * S + k] -= kappa * g.d[M + S + k];
+    }
+  }
+  for (int k = 0; k < M; ++k) {
+    const double wd = P.hi[k] - P.lo[k];
+    const double u = (x[k] - P.lo[k]) / wd;
+    const double gl = std::min(1.0, std::max(0.0, u)) - u;
+    const double dg_du = (u < 0.0 || u > 1.0) ? -1.0 : 0.0;  // d clamp / du is 0 outside the box
+    out[Pms + (W - 1) + k] = gl;
+    out[Pc + k] -= (lam_lim[k] + c * gl) * dg_du / wd;
+  }
   return total;
 }
 
@@ -944,6 +1048,62 @@ int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
     for (int k = M; k < P; ++k)
       adam_ascent(particles[(size_t)i * P + k], adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k],
                   grad[(size_t)i * P + k], *t, lr, b1, b2, eps);
+  }
+  if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
+  if (bw_out) *bw_out = bw;
+  return 0;
+}
+
+// CSVGD quantities of N particles [N][Pc] (Pc = M + (W-1) S + (W-1) + M) into
+// out [N][Pc + M] as particle_csvgd; logp_obs [N].
+int orc_csvgd_loglik_grad(const Problem* prob, double c, const double* particles, int N, double* logp_obs,
+                          double* out, int threads) {
+  const Problem& P = *prob;
+  if (P.n < 1 || P.M < 0 || P.W < 1 || P.T < P.W || P.M + 4 * P.n > MAXD) return -1;
+  const int S = 2 * P.n, Pc = P.M + (P.W - 1) * S + (P.W - 1) + P.M;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i)
+    logp_obs[i] = particle_csvgd(P, c, particles + (size_t)i * Pc, out + (size_t)i * (Pc + P.M));
+  return 0;
+}
+
+// One CSVGD iteration's update (Algorithm 1) from out = the rows above:
+// theta moves by Adam ascent in u coordinates on phi (Eq. 1 with the
+// observation gradient) plus the constraint direction -dPsi/du, without
+// clipping; the shooting states by Adam ascent on their rows; the
+// multipliers by a gradient-ascent step lam += lr g.
+int orc_csvgd_step(int N, int M, int Pc, int n_def, const double* lo, const double* hi, double* particles,
+                   const double* out, double* adam_m, double* adam_v, int* t, double lr, double b1, double b2,
+                   double eps, double* phi_out, double* bw_out) {
+  const int n_shoot = Pc - M - n_def - M;
+  if (n_shoot < 0) return -1;
+  const int G = Pc + M;
+  std::vector<double> u((size_t)N * M), gu((size_t)N * M), phi((size_t)N * M);
+  for (int i = 0; i < N; ++i)
+    for (int k = 0; k < M; ++k) {
+      const double w = hi[k] - lo[k];
+      u[(size_t)i * M + k] = (particles[(size_t)i * Pc + k] - lo[k]) / w;
+      gu[(size_t)i * M + k] = out[(size_t)i * G + k] * w;
+    }
+  const double bw = bandwidth_from_median(N, median_sqdist(N, M, u.data()));
+  svgd_phi(N, M, u.data(), gu.data(), bw, phi.data());
+  *t += 1;
+  for (int i = 0; i < N; ++i) {
+    const double* o = out + (size_t)i * G;
+    double* x = particles + (size_t)i * Pc;
+    for (int k = 0; k < M; ++k) {
+      const double w = hi[k] - lo[k];
+      double uk = u[(size_t)i * M + k];
+      adam_ascent(uk, adam_m[(size_t)i * Pc + k], adam_v[(size_t)i * Pc + k], phi[(size_t)i * M + k] + o[Pc + k] * w,
+                  *t, lr, b1, b2, eps);
+      x[k] = lo[k] + uk * w;
+    }
+    for (int k = M; k < M + n_shoot; ++k)
+      adam_ascent(x[k], adam_m[(size_t)i * Pc + k], adam_v[(size_t)i * Pc + k], o[k], *t, lr, b1, b2, eps);
+    for (int k = M + n_shoot; k < Pc; ++k) x[k] += lr * o[k];
   }
   if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
   if (bw_out) *bw_out = bw;

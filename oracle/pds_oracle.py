@@ -125,6 +125,11 @@ def lib():
             L.orc_svgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_csvgd_loglik_grad.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, _dp, ctypes.c_int, _dp,
+                                                _dp, ctypes.c_int]
+            L.orc_csvgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                         _dp, _dp, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, _dp, _dp]
             L.orc_armbox_pivot.argtypes = [ctypes.POINTER(_ArmBox), ctypes.c_double, _dp, _dp]
             L.orc_armbox_qdd.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, _dp, _dp]
             L.orc_armbox_inertia.argtypes = [ctypes.POINTER(_ArmBox), _dp, _dp]
@@ -239,6 +244,27 @@ class Problem:
             obs_index=i(obs_index), obs=d(obs), sigma_obs=float(sigma_obs), sigma_def=float(sigma_def),
             s0=d(s0), lo=d(lo), hi=d(hi), c_lim=float(c_lim))
 
+    @property
+    def Pc(self):
+        """Particle length of the constrained method: theta, shooting states,
+        the W-1 defect multipliers and the M limit multipliers."""
+        return self.P + (self.W - 1) + self.M
+
+    def csvgd_loglik_grad(self, particles, c=1.0, threads=1):
+        """Constrained SVGD (Sec. IV-E): returns (log p_obs [N], out [N][Pc+M])
+        with out's rows as orc_csvgd_loglik_grad documents: d log p_obs/d theta,
+        d(log p_obs - Psi)/d s^s, g_def, g_lim, -dPsi/d theta."""
+        x, xp = _d(np.atleast_2d(particles))
+        N = x.shape[0]
+        assert x.shape[1] == self.Pc, (x.shape, self.Pc)
+        logp = np.zeros(N)
+        out = np.zeros((N, self.Pc + self.M))
+        rc = lib().orc_csvgd_loglik_grad(ctypes.byref(self.c), float(c), xp, N, logp.ctypes.data_as(_dp),
+                                         out.ctypes.data_as(_dp), int(threads))
+        if rc != 0:
+            raise RuntimeError(f"orc_csvgd_loglik_grad failed ({rc})")
+        return logp, out
+
     def loglik_grad(self, particles, grad=True, threads=1):
         x, xp = _d(np.atleast_2d(particles))
         N = x.shape[0]
@@ -259,6 +285,36 @@ def max_threads() -> int:
 # --------------------------------------------------------------------------
 # SVGD
 # --------------------------------------------------------------------------
+class CsvgdState:
+    """Adam moments and step count of the oracle's constrained SVGD update
+    (Algorithm 1): particles [N][Pc] with Pc = M + n_shoot + n_def + M."""
+
+    def __init__(self, N, Pc, n_def, lo, hi, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+        self.N, self.Pc, self.n_def = N, Pc, n_def
+        self.M = len(lo)
+        self.lo = np.ascontiguousarray(lo, dtype=np.float64)
+        self.hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.m = np.zeros((N, Pc))
+        self.v = np.zeros((N, Pc))
+        self.t = ctypes.c_int(0)
+        self.lr, self.beta1, self.beta2, self.eps = lr, beta1, beta2, eps
+
+    def step(self, particles, out):
+        """In-place update of particles [N][Pc] from out [N][Pc+M]; returns (phi, bw)."""
+        assert particles.dtype == np.float64 and particles.flags.c_contiguous
+        o, op = _d(out)
+        assert o.shape == (self.N, self.Pc + self.M)
+        phi = np.zeros((self.N, self.M))
+        bw = ctypes.c_double(0.0)
+        rc = lib().orc_csvgd_step(self.N, self.M, self.Pc, self.n_def, self.lo.ctypes.data_as(_dp),
+                                  self.hi.ctypes.data_as(_dp), particles.ctypes.data_as(_dp), op,
+                                  self.m.ctypes.data_as(_dp), self.v.ctypes.data_as(_dp), ctypes.byref(self.t),
+                                  self.lr, self.beta1, self.beta2, self.eps, phi.ctypes.data_as(_dp),
+                                  ctypes.byref(bw))
+        if rc != 0:
+            raise RuntimeError("orc_csvgd_step failed")
+        return phi, bw.value
+
 def median_sqdist(u):
     u, up = _d(np.atleast_2d(u))
     return lib().orc_median_sqdist(u.shape[0], u.shape[1], up)
