@@ -156,6 +156,28 @@ int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
 int pds_problem_set_option(pds_problem_t p, int option, int value);
 int pds_problem_get_option(pds_problem_t p, int option, int* value);
 
+/* Constrained SVGD (Sec. IV-E, Eq. mdmm-loss, Algorithm 1).  With enable = 1
+ * the likelihood is the observation term only, and the defect terms and the
+ * parameter limits become equality constraints.  Each particle carries
+ * MDMM multipliers, which the modified differential multiplier method
+ * updates:
+ *   g_def,w = ||s^s_w - s_end(w-1)||^2 / sigma_def^2        (w = 1..W-1)
+ *   g_lim,k = clamp(u_k, 0, 1) - u_k,  u = (theta - lo) / (hi - lo)
+ *   Psi     = sum_w (lam_def,w g_def,w + c/2 g_def,w^2)
+ *           + sum_k (lam_lim,k g_lim,k + c/2 g_lim,k^2)
+ * The particle layout becomes P = M + (W-1)*S + (W-1) + M: theta, the
+ * shooting states, lam_def, lam_lim.  pds_loglik_grad then returns
+ * log p_obs and needs a grad buffer of P + M rows:
+ *   rows [0, M)        d log p_obs / d theta   (phi's input);
+ *   shooting rows      d (log p_obs - Psi) / d s^s;
+ *   lam_def rows       g_def;  lam_lim rows g_lim;
+ *   rows [P, P + M)    -dPsi/dtheta, with the multipliers held fixed.
+ * c >= 0 is the MDMM damping.  enable = 0 restores the multiple-shooting
+ * likelihood and layout.  Returns PDS_ERR_UNSUPPORTED for the arm-and-box
+ * system.  The iteration buffers are released (pds_iterate reallocates
+ * them). */
+int pds_problem_set_csvgd(pds_problem_t p, int enable, double c);
+
 /* Allocate the workspace for up to N_max particles now, so that later calls
  * with N <= N_max allocate nothing (e.g. before capturing a CUDA graph).
  * Calls with a larger N grow the workspace (synchronising the stream). */
@@ -210,6 +232,18 @@ int pds_svgd_destroy(pds_svgd_t s);
  * accumulation, clamped at 0); 1 = CUDA cores. */
 #define PDS_OPT_MEDIAN_CUDA_CORES 5
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);
+
+/* Constrained SVGD update (Algorithm 1) for particles laid out as
+ * pds_problem_set_csvgd describes; n_def = W - 1 defect multipliers, and the
+ * last M rows are the limit multipliers.  Each step then
+ *  - moves theta by Adam ascent in u on phi (Eq. 1, from grad rows [0, M))
+ *    plus the constraint direction (grad rows [P, P + M) times hi - lo),
+ *    without clipping to the box;
+ *  - moves the shooting states by Adam ascent on their rows;
+ *  - moves every multiplier by lam += lr * g (its grad row).
+ * grad must then have P + M rows.  enable = 0 restores the plain update.
+ * PDS_ERR_ARG if n_def does not fit the layout. */
+int pds_svgd_set_csvgd(pds_svgd_t s, int enable, int n_def);
 
 /* One SVGD + Adam update in place.
  *  particles    : device [P][N] float (read and written).

@@ -73,6 +73,7 @@ EXPORTS = {
     "pds_problem_set_checkpoint_stride": ([_vp, ctypes.c_int], ctypes.c_int),
     "pds_problem_reserve": ([_vp, ctypes.c_int], ctypes.c_int),
     "pds_problem_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "pds_problem_set_csvgd": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "pds_problem_get_option": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
     "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
@@ -82,6 +83,7 @@ EXPORTS = {
     "pds_svgd_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pds_svgd_reset": ([_vp], ctypes.c_int),
     "pds_svgd_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "pds_svgd_set_csvgd": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_iterate_host": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_batch_create": ([ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -279,14 +281,31 @@ class Problem:
         _check(lib().pds_problem_get_option(self._h, int(option), ctypes.byref(v)), "pds_problem_get_option")
         return v.value
 
+    def set_csvgd(self, enable: bool = True, c: float = 1.0):
+        """Constrained SVGD (pds_problem_set_csvgd): observation likelihood,
+        MDMM constraints; the layout grows by W-1 + M multiplier rows and the
+        gradient has P + M rows."""
+        L = lib()
+        _check(L.pds_problem_set_csvgd(self._h, int(bool(enable)), float(c)), "pds_problem_set_csvgd")
+        M, S, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.pds_problem_layout(self._h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
+        self.M, self.S, self.P = M.value, S.value, P.value
+        self.csvgd = bool(enable)
+
+    @property
+    def grad_rows(self) -> int:
+        return self.P + (self.M if getattr(self, "csvgd", False) else 0)
+
     def loglik_grad(self, particles: torch.Tensor, grad: bool = True, out=None):
-        """log p and (optionally) d log p / d particles for particles [P][N]."""
+        """log p and (optionally) d log p / d particles for particles [P][N]
+        (in constrained mode: log p_obs and the [P + M][N] rows of
+        pds_problem_set_csvgd)."""
         _need_cuda(particles, torch.float32, "particles")
         assert particles.dim() == 2 and particles.shape[0] == self.P, (particles.shape, self.P)
         N = particles.shape[1]
         if out is None:
             logp = torch.empty(N, device=particles.device, dtype=torch.float32)
-            g = torch.empty_like(particles) if grad else None
+            g = torch.empty((self.grad_rows, N), device=particles.device, dtype=torch.float32) if grad else None
             status = torch.empty(N, device=particles.device, dtype=torch.int32)
         else:
             logp, g, status = out
@@ -341,6 +360,10 @@ class Svgd:
 
     def set_option(self, option: int, value: int):
         _check(lib().pds_svgd_set_option(self._h, int(option), int(value)), "pds_svgd_set_option")
+
+    def set_csvgd(self, n_def: int, enable: bool = True):
+        """Constrained SVGD update (pds_svgd_set_csvgd) with n_def defect multipliers."""
+        _check(lib().pds_svgd_set_csvgd(self._h, int(bool(enable)), int(n_def)), "pds_svgd_set_csvgd")
 
     def step(self, particles: torch.Tensor, grad: torch.Tensor, return_phi: bool = False):
         """In-place update of particles [P][N]; returns (bandwidth tensor, phi or None)."""

@@ -274,6 +274,10 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       delete b;
       return set_error(PDS_ERR_ARG, "SVGD state does not match its problem");
     }
+    if (p->c.csvgd || s->sp.csvgd) {
+      delete b;
+      return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs the unconstrained method only");
+    }
     b->probs.push_back(p);
     b->svgds.push_back(s);
     b->X.push_back(particles[j]);

@@ -82,11 +82,13 @@ static void free_parts(Partials& p) {
   cudaFree(p.start);
   cudaFree(p.next);
   cudaFree(p.tape);
+  cudaFree(p.th2);
+  cudaFree(p.gdef);
   p = Partials{};
 }
 
 int pds::ensure_workspace(pds_problem* p, int N) {
-  if (N <= p->cap_N && p->cap_K == p->c.K) return PDS_OK;
+  if (N <= p->cap_N && p->cap_K == p->c.K && p->cap_cs == p->c.csvgd) return PDS_OK;
   const int newN = N > p->cap_N ? N : p->cap_N;
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
@@ -100,10 +102,13 @@ int pds::ensure_workspace(pds_problem* p, int N) {
       (e = cudaMalloc(&p->parts.th, W * (M ? M : 1) * Nn * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->parts.start, W * S * Nn * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->parts.next, W * S * Nn * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&p->parts.tape, tape * sizeof(float))) != cudaSuccess) {
+      (e = cudaMalloc(&p->parts.tape, tape * sizeof(float))) != cudaSuccess ||
+      (c.csvgd && (e = cudaMalloc(&p->parts.th2, W * (M ? M : 1) * Nn * sizeof(float))) != cudaSuccess) ||
+      (c.csvgd && (e = cudaMalloc(&p->parts.gdef, W * Nn * sizeof(float))) != cudaSuccess)) {
     free_parts(p->parts);
     return cuda_fail(e, "workspace allocation");
   }
+  p->cap_cs = c.csvgd;
   p->cap_N = newN;
   p->cap_K = c.K;
   return PDS_OK;
@@ -127,7 +132,9 @@ int pds::ensure_iter_buffers(pds_problem* p, int N) {
   p->d_grad = p->d_logp = p->d_x = nullptr;
   p->it_N = 0;
   cudaError_t e;
-  if ((e = cudaMalloc(&p->d_grad, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess ||
+  // the constrained method's gradient has M more rows (-dPsi/dtheta)
+  const size_t grows = (size_t)p->c.P + (p->c.csvgd ? (size_t)p->c.M : 0);
+  if ((e = cudaMalloc(&p->d_grad, grows * N * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_logp, (size_t)N * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&p->d_x, (size_t)p->c.P * N * sizeof(float))) != cudaSuccess)
     return cuda_fail(e, "iteration buffers");
@@ -285,6 +292,40 @@ int pds_problem_get_option(pds_problem_t p, int option, int* value) {
   }
 }
 
+int pds_problem_set_csvgd(pds_problem_t p, int enable, double c) {
+  if (!p) return fail(PDS_ERR_ARG, "NULL problem");
+  if (enable != 0 && enable != 1) return fail(PDS_ERR_ARG, "enable must be 0 or 1");
+  if (enable && p->kind != PDS_SYSTEM_PLANAR_CHAIN)
+    return fail(PDS_ERR_UNSUPPORTED, "constrained SVGD is built for planar chains");
+  if (enable && !(c >= 0.0 && c < 1e30)) return fail(PDS_ERR_ARG, "MDMM damping c must be finite and >= 0");
+  cudaStreamSynchronize(p->stream);
+  ChainParams& cp = p->c;
+  cp.csvgd = enable;
+  cp.c_mdmm = enable ? (float)c : 0.f;
+  cp.P = cp.M + (cp.W - 1) * cp.S + (enable ? (cp.W - 1) + cp.M : 0);
+  // the iteration buffers depend on P
+  cudaFree(p->d_grad);
+  cudaFree(p->d_logp);
+  cudaFree(p->d_x);
+  p->d_grad = p->d_logp = p->d_x = nullptr;
+  p->it_N = 0;
+  return PDS_OK;
+}
+
+int pds_svgd_set_csvgd(pds_svgd_t s, int enable, int n_def) {
+  if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
+  if (enable != 0 && enable != 1) return fail(PDS_ERR_ARG, "enable must be 0 or 1");
+  if (enable) {
+    const int lam0 = s->sp.P - n_def - s->sp.M;
+    if (n_def < 0 || lam0 < s->sp.M) return fail(PDS_ERR_ARG, "n_def %d does not fit P %d, M %d", n_def, s->sp.P, s->sp.M);
+    s->sp.lam0 = lam0;
+  } else {
+    s->sp.lam0 = 0;
+  }
+  s->sp.csvgd = enable;
+  return PDS_OK;
+}
+
 int pds_problem_reserve(pds_problem_t p, int N_max) {
   if (!p) return fail(PDS_ERR_ARG, "NULL problem");
   if (N_max < 1 || N_max > (1 << 20)) return fail(PDS_ERR_ARG, "N_max %d outside 1..2^20", N_max);
@@ -430,6 +471,9 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
   if (!p || !s || !particles) return fail(PDS_ERR_ARG, "NULL argument");
   if (iters < 0) return fail(PDS_ERR_ARG, "iters < 0");
   if (s->sp.M != p->c.M || s->sp.P != p->c.P) return fail(PDS_ERR_ARG, "SVGD state does not match the problem");
+  if (s->sp.csvgd != p->c.csvgd ||
+      (p->c.csvgd && s->sp.lam0 != p->c.M + (p->c.W - 1) * p->c.S))
+    return fail(PDS_ERR_ARG, "constrained SVGD set on one of problem and SVGD state only");
   const int N = s->sp.N;
   int rc = ensure_iter_buffers(p, N);
   if (rc != PDS_OK) return rc;

@@ -26,6 +26,8 @@ struct ChainParams {
   float def_const;  // -(S/2) log(2 pi sigma_def^2), once per defect
   float c_lim;
   float lim_const;  // -sum_k log(hi_k - lo_k)
+  int csvgd;        // 1: constrained SVGD (observation likelihood, MDMM constraints)
+  float c_mdmm;     // MDMM damping c
   float mass[kMaxLinks], length[kMaxLinks], damping[kMaxLinks];
   int mass_theta[kMaxLinks], length_theta[kMaxLinks], damp_theta[kMaxLinks];  // theta row or -1
   int obs_col[kMaxState];  // observation column of each state component or -1
@@ -49,6 +51,9 @@ struct Partials {
   float* start;   // [W][S][N] d/d(window start state)
   float* next;    // [W][S][N] d/d(next shooting state) from the defect term
   float* tape;    // checkpoints [max_seg][S][U] then segment states [K][S][U]
+  // constrained SVGD only (else NULL)
+  float* th2;     // [W][M][N] -dPsi_def/dtheta of the window's defect constraint
+  float* gdef;    // [W][N] defect constraint value g_def,w+1 (w < W-1)
 };
 
 // One problem of a batched launch (device-side job table entry).
@@ -84,6 +89,8 @@ struct SvgdParams {
   float lr, b1, b2, eps;
   int clamp;
   int fast_math;   // 1: __expf for the kernel values
+  int csvgd;       // 1: constrained SVGD; the gradient then has P + M rows
+  int lam0;        // constrained SVGD: first multiplier row (rows lam0..P-1 move by lr * g)
 };
 
 // Device-resident SVGD control block (no host round trip inside a step).
@@ -153,6 +160,7 @@ struct pds_problem {
   float* d_obs = nullptr;
   int cap_N = 0;          // workspace capacity in particles
   int cap_K = 0;          // checkpoint stride the tape was sized for
+  int cap_cs = 0;         // workspace has the constrained-SVGD partials
   pds::Partials parts{};
   // buffers used by pds_iterate / pds_iterate_host / batches
   int it_N = 0;

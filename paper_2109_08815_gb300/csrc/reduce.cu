@@ -5,7 +5,8 @@
 // Grid: x over particles, y over row groups.  y = 0: log p and the theta
 // gradient of the particle (sums over the W windows); y = w >= 1: the
 // gradient of shooting state s^s_w, the start-state adjoint of window w plus
-// the defect adjoint of window w-1.  Non-finite results are ORed into
+// the defect adjoint of window w-1.  In constrained-SVGD mode y = 0 also
+// writes the constraint values and the constraint gradient of theta.  Non-finite results are ORed into
 // status[i], which the rollout kernel zeroed for this call.
 #include <math.h>
 
@@ -20,7 +21,41 @@ __global__ void __launch_bounds__(256) window_reduce_kernel(const ChainParams c,
   if (i >= N) return;
   const int y = blockIdx.y;
   bool finite = true;
-  if (y == 0) {
+  if (c.csvgd && y == 0) {
+    // constrained SVGD (Sec. IV-E): log p_obs; theta rows d log p_obs/dtheta;
+    // multiplier rows g_def and g_lim; rows P..P+M-1 -dPsi/dtheta (defect and
+    // limit constraints, multipliers fixed)
+    const int Pms = c.M + (c.W - 1) * c.S;
+    double lp = 0.0;
+    for (int w = 0; w < c.W; ++w) lp += (double)parts.lp[(size_t)w * N + i];
+    const float lpf = (float)lp;
+    finite = isfinite(lpf);
+    logp[i] = lpf;
+    if (grad) {
+      for (int w = 0; w + 1 < c.W; ++w) {
+        const float g = parts.gdef[(size_t)w * N + i];
+        finite = finite && isfinite(g);
+        grad[(size_t)(Pms + w) * N + i] = g;
+      }
+      for (int k = 0; k < c.M; ++k) {
+        float go = 0.f, gc = 0.f;
+        for (int w = 0; w < c.W; ++w) {
+          go += parts.th[((size_t)w * c.M + k) * N + i];
+          gc += parts.th2[((size_t)w * c.M + k) * N + i];
+        }
+        const float width = c.hi[k] - c.lo[k];
+        const float uk = (X[(size_t)k * N + i] - c.lo[k]) / width;
+        const float gl = fminf(1.f, fmaxf(0.f, uk)) - uk;
+        const float dg_du = (uk < 0.f || uk > 1.f) ? -1.f : 0.f;  // d clamp / du is 0 outside the box
+        const float lam = X[(size_t)(Pms + c.W - 1 + k) * N + i];
+        gc -= (lam + c.c_mdmm * gl) * dg_du / width;
+        finite = finite && isfinite(go) && isfinite(gc);
+        grad[(size_t)k * N + i] = go;
+        grad[(size_t)(Pms + c.W - 1 + k) * N + i] = gl;
+        grad[(size_t)(c.P + k) * N + i] = gc;
+      }
+    }
+  } else if (y == 0) {
     // log-likelihood: windows summed in double, in window order
     double lp = 0.0;
     for (int w = 0; w < c.W; ++w) lp += (double)parts.lp[(size_t)w * N + i];

@@ -40,8 +40,13 @@
 
 #include "pds_internal.cuh"
 
-#ifndef PDS_ROLLOUT_MINB
-#define PDS_ROLLOUT_MINB 3
+// Resident 128-thread blocks per SM the rollout is compiled for: 3 keeps
+// chains of up to 5 links in registers; longer chains would spill at 168
+// registers and get 2 (255 registers).
+#ifdef PDS_ROLLOUT_MINB
+#define PDS_ROLLOUT_BLOCKS(NL) (PDS_ROLLOUT_MINB)
+#else
+#define PDS_ROLLOUT_BLOCKS(NL) ((NL) <= 5 ? 3 : 2)
 #endif
 
 namespace pds {
@@ -141,15 +146,20 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
   }
 }
 
-// Reverse of one step.  On entry (qb, vb) is the adjoint of the step's
-// output state; on exit it is the adjoint of the input state (q, v).  The
-// adjoints of the link parameters are accumulated into mb, lb, bb.
-template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P, float g,
-                                               float dt, float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
-                                               float (&lb)[NL], float (&bb)[NL]) {
-  // ---- recompute the forward intermediates at (q, v)
+// Forward intermediates of one step that its reverse needs.
+template <int NL>
+struct StepTape {
   float sq[NL], cq[NL], S[NL], C[NL], om[NL], tau[NL];
+  float kc[NL], ih[NL], y[NL], f[NL], num[NL], Be[NL], Bp[NL], ae[NL], ap[NL];
+  float v[NL];
+};
+
+// Recompute the forward intermediates of the step at (q, v).
+template <int NL, bool FAST>
+__device__ __forceinline__ void chain_step_recompute(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P,
+                                                     StepTape<NL>& F) {
+  // ---- recompute the forward intermediates at (q, v)
+  float (&sq)[NL] = F.sq, (&cq)[NL] = F.cq, (&S)[NL] = F.S, (&C)[NL] = F.C, (&om)[NL] = F.om, (&tau)[NL] = F.tau;
   joint_trig<NL, FAST>(q, sq, cq, S, C);
   {
     float o = 0.f;
@@ -160,7 +170,10 @@ __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float
       tau[i] = -P.b[i] * v[i];
     }
   }
-  float kc[NL], ih[NL], y[NL], f[NL], num[NL], Be[NL], Bp[NL], ae[NL], ap[NL];
+  float (&kc)[NL] = F.kc, (&ih)[NL] = F.ih, (&y)[NL] = F.y, (&f)[NL] = F.f, (&num)[NL] = F.num;
+  float (&Be)[NL] = F.Be, (&Bp)[NL] = F.Bp, (&ae)[NL] = F.ae, (&ap)[NL] = F.ap;
+#pragma unroll
+  for (int i = 0; i < NL; ++i) F.v[i] = v[i];
   {
     float Bce = 0.f, Bcp = 0.f, k = 0.f;
 #pragma unroll
@@ -203,7 +216,19 @@ __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float
       Ae = ae[i] - om[i] * om[i] * P.l[i];
     }
   }
+}
 
+// Reverse of one step from its intermediates.  On entry (qb, vb) is the
+// adjoint of the step's output state; on exit it is the adjoint of the input
+// state.  The adjoints of the link parameters are accumulated into mb, lb, bb.
+template <int NL>
+__device__ __forceinline__ void chain_step_reverse(const StepTape<NL>& F, const Links<NL>& P, float g, float dt,
+                                                   float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
+                                                   float (&lb)[NL], float (&bb)[NL]) {
+  const float (&sq)[NL] = F.sq, (&cq)[NL] = F.cq, (&S)[NL] = F.S, (&C)[NL] = F.C, (&om)[NL] = F.om, (&tau)[NL] = F.tau;
+  const float (&kc)[NL] = F.kc, (&ih)[NL] = F.ih, (&y)[NL] = F.y, (&f)[NL] = F.f, (&num)[NL] = F.num;
+  const float (&Be)[NL] = F.Be, (&Bp)[NL] = F.Bp, (&ae)[NL] = F.ae, (&ap)[NL] = F.ap;
+  const float (&v)[NL] = F.v;
   // ---- Euler: qd' = qd + qdd dt, q' = q + qd' dt
 #pragma unroll
   for (int i = 0; i < NL; ++i) vb[i] = fmaf(qb[i], dt, vb[i]);  // qb passes through unchanged
@@ -312,6 +337,16 @@ __device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float
   }
 }
 
+// Reverse of one step (recompute, then reverse).
+template <int NL, bool FAST>
+__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P, float g,
+                                               float dt, float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
+                                               float (&lb)[NL], float (&bb)[NL]) {
+  StepTape<NL> F;
+  chain_step_recompute<NL, FAST>(q, v, P, F);
+  chain_step_reverse<NL>(F, P, g, dt, qb, vb, mb, lb, bb);
+}
+
 // Load the physical parameters of particle i (defaults overridden by theta).
 template <int NL, bool FAST>
 __device__ __forceinline__ void load_params(const ChainParams& c, const float* __restrict__ X, int N, int i,
@@ -378,7 +413,15 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
 // seg (may be NULL): the thread's K slots for the recomputed states of the
 // segment being reversed, seg[slot * 2 NL * seg_stride + var * seg_stride]
 // -- shared memory when they fit there, else the segment part of the tape.
-template <int NL, bool FAST>
+//
+// CS (constrained SVGD, Sec. IV-E): the window's likelihood is the
+// observation term only; its defect g_def,w+1 = ||s^s_{w+1} - s_end||^2 /
+// sigma_def^2 is a constraint with multiplier lam = X[row M + (W-1) S + w].
+// A second adjoint, seeded only at the window's end with
+// -dPsi/ds_end = 2 (lam + c g) (s^s_{w+1} - s_end) / sigma_def^2, runs
+// through the same recomputed steps: th2 receives its theta part, start the
+// sum of both adjoints, next the direct -dPsi/ds^s_{w+1}, gdef the value g.
+template <int NL, bool FAST, bool CS = false>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
                                              size_t u, float* seg = nullptr, size_t seg_stride = 0) {
@@ -421,33 +464,56 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 
   // defect term against the next window's shooting state
   float nb[2 * NL];
+  float qb2[NL], vb2[NL];  // CS: adjoint of -Psi_def
 #pragma unroll
-  for (int j = 0; j < NL; ++j) { qb[j] = 0.f; vb[j] = 0.f; }
+  for (int j = 0; j < NL; ++j) { qb[j] = 0.f; vb[j] = 0.f; qb2[j] = 0.f; vb2[j] = 0.f; }
   if (w < c.W - 1) {
     const float* xs = X + (size_t)(c.M + w * 2 * NL) * N + i;
     float dss = 0.f;
+    float dd[2 * NL];
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
-      const float dq = __ldg(xs + (size_t)j * N) - q[j];
-      const float dv = __ldg(xs + (size_t)(NL + j) * N) - v[j];
-      dss += dq * dq + dv * dv;
-      qb[j] = dq * c.inv_sd2;        // d/ds_end of -|d|^2/(2 sd^2)
-      vb[j] = dv * c.inv_sd2;
-      nb[j] = -dq * c.inv_sd2;       // d/ds^s_{w+1}
-      nb[NL + j] = -dv * c.inv_sd2;
+      dd[j] = __ldg(xs + (size_t)j * N) - q[j];
+      dd[NL + j] = __ldg(xs + (size_t)(NL + j) * N) - v[j];
+      dss += dd[j] * dd[j] + dd[NL + j] * dd[NL + j];
     }
-    lp += -0.5f * c.inv_sd2 * dss + c.def_const;
+    if constexpr (CS) {
+      const float g = dss * c.inv_sd2;
+      const float lam = __ldg(X + (size_t)(c.M + (c.W - 1) * 2 * NL + w) * N + i);
+      const float kap2 = 2.f * (lam + c.c_mdmm * g) * c.inv_sd2;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        qb2[j] = kap2 * dd[j];  // -dPsi/ds_end
+        vb2[j] = kap2 * dd[NL + j];
+        nb[j] = -kap2 * dd[j];  // -dPsi/ds^s_{w+1}
+        nb[NL + j] = -kap2 * dd[NL + j];
+      }
+      if (grad) parts.gdef[(size_t)w * N + i] = g;
+    } else {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        qb[j] = dd[j] * c.inv_sd2;  // d/ds_end of -|d|^2/(2 sd^2)
+        vb[j] = dd[NL + j] * c.inv_sd2;
+        nb[j] = -dd[j] * c.inv_sd2;  // d/ds^s_{w+1}
+        nb[NL + j] = -dd[NL + j] * c.inv_sd2;
+      }
+      lp += -0.5f * c.inv_sd2 * dss + c.def_const;
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < 2 * NL; ++j) nb[j] = 0.f;
+    if constexpr (CS) {
+      if (grad) parts.gdef[(size_t)w * N + i] = 0.f;
+    }
   }
   parts.lp[(size_t)w * N + i] = lp;
   if (!grad) return;
 
   // ---------------- reverse sweep
   float mb[NL], lb[NL], bb[NL];
+  float mb2[NL], lb2[NL], bb2[NL];  // CS: theta adjoint of -Psi_def
 #pragma unroll
-  for (int j = 0; j < NL; ++j) { mb[j] = 0.f; lb[j] = 0.f; bb[j] = 0.f; }
+  for (int j = 0; j < NL; ++j) { mb[j] = 0.f; lb[j] = 0.f; bb[j] = 0.f; mb2[j] = 0.f; lb2[j] = 0.f; bb2[j] = 0.f; }
   float qh[NL], vh[NL];  // state s_{k+1} (output of the step being reversed)
 #pragma unroll
   for (int j = 0; j < NL; ++j) { qh[j] = q[j]; vh[j] = v[j]; }
@@ -466,7 +532,14 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL>(c, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
-      chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
+      if constexpr (CS) {
+        StepTape<NL> F;
+        chain_step_recompute<NL, FAST>(qs, vs, P, F);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
+      } else {
+        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
+      }
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -479,6 +552,17 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     if (c.mass_theta[j] >= 0) th[(size_t)c.mass_theta[j] * N] = mb[j];
     if (c.length_theta[j] >= 0) th[(size_t)c.length_theta[j] * N] = lb[j];
     if (c.damp_theta[j] >= 0) th[(size_t)c.damp_theta[j] * N] = bb[j];
+  }
+  if constexpr (CS) {
+    float* th2 = parts.th2 + (size_t)w * c.M * N + i;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      if (c.mass_theta[j] >= 0) th2[(size_t)c.mass_theta[j] * N] = mb2[j];
+      if (c.length_theta[j] >= 0) th2[(size_t)c.length_theta[j] * N] = lb2[j];
+      if (c.damp_theta[j] >= 0) th2[(size_t)c.damp_theta[j] * N] = bb2[j];
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) { qb[j] += qb2[j]; vb[j] += vb2[j]; }
   }
   float* st = parts.start + (size_t)w * 2 * NL * N + i;
   float* nx = parts.next + (size_t)w * 2 * NL * N + i;
@@ -494,7 +578,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 // seg_smem: the reverse sweep's recomputed segment states live in dynamic
 // shared memory (K x 2 NL x blockDim floats), else in the tape.
 template <int NL, bool FAST>
-__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const ChainParams c, const float* __restrict__ X,
+__global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(const ChainParams c, const float* __restrict__ X,
                                                                         int N, Partials parts, int grad,
                                                                         int32_t* __restrict__ status, int seg_smem) {
   extern __shared__ float seg_sh[];
@@ -507,6 +591,22 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const Ch
     rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u);
 }
 
+// Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
+                                                                           const float* __restrict__ X, int N,
+                                                                           Partials parts, int grad,
+                                                                           int32_t* __restrict__ status, int seg_smem) {
+  extern __shared__ float seg_sh[];
+  const size_t U = (size_t)N * c.W;
+  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= U) return;
+  if (seg_smem)
+    rollout_unit<NL, FAST, true>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+  else
+    rollout_unit<NL, FAST, true>(c, X, N, parts, grad, status, u);
+}
+
 // Persistent rollout over several problems with the same chain length
 // (batched execution): blocks take work items -- 128 consecutive units of
 // one problem -- from a list sorted by decreasing cost (longest windows
@@ -514,7 +614,7 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) rollout_kernel(const Ch
 // length share the launch and balance across SMs.  The problem's parameters
 // are staged in shared memory for the item.
 template <int NL, bool FAST>
-__global__ void __launch_bounds__(128, PDS_ROLLOUT_MINB) batch_rollout_kernel(const BatchJob* __restrict__ jobs,
+__global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_kernel(const BatchJob* __restrict__ jobs,
                                                                               const WorkItem* __restrict__ items,
                                                                               int n_items,
                                                                               unsigned int* __restrict__ counter,
@@ -591,10 +691,16 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
   const size_t seg_bytes = (size_t)c.K * 2 * NL * 128 * sizeof(float);
   const int seg_smem = (grad && seg_bytes <= 48 * 1024) ? 1 : 0;
   const size_t smem = seg_smem ? seg_bytes : 0;
-  if (c.fast_math)
+  if (c.csvgd) {
+    if (c.fast_math)
+      rollout_cs_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else
+      rollout_cs_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+  } else if (c.fast_math) {
     rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
-  else
+  } else {
     rollout_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+  }
   return cudaGetLastError();
 }
 

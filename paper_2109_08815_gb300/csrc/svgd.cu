@@ -565,6 +565,11 @@ __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float
   const int r = (int)(idx / sp.N);
   const int i = (int)(idx - (size_t)r * sp.N);
   const float bc1 = ctl->bc1, bc2 = ctl->bc2;
+  if (sp.csvgd && r >= sp.lam0) {
+    // MDMM multipliers: lambda' = g (Algorithm 1), a gradient-ascent step
+    X[idx] = X[idx] + sp.lr * G[idx];
+    return;
+  }
   float g;
   float x;
   if (r < sp.M) {
@@ -572,7 +577,10 @@ __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float
     for (int c = 0; c < chunks; ++c) s += phi_part[((size_t)c * sp.M + r) * sp.N + i];
     g = s / (float)sp.N;
     if (phi_out) phi_out[idx] = g;
-    x = (X[idx] - sp.lo[r]) / (sp.hi[r] - sp.lo[r]);
+    const float width = sp.hi[r] - sp.lo[r];
+    // constrained SVGD: plus the constraint direction -dPsi/dtheta, in u
+    if (sp.csvgd) g += G[(size_t)(sp.P + r) * sp.N + i] * width;
+    x = (X[idx] - sp.lo[r]) / width;
   } else {
     g = G[idx];
     x = X[idx];
@@ -583,7 +591,7 @@ __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float
   av[idx] = v;
   x += sp.lr * (m / bc1) / (sqrtf(v / bc2) + sp.eps);
   if (r < sp.M) {
-    if (sp.clamp) x = fminf(1.f, fmaxf(0.f, x));
+    if (sp.clamp && !sp.csvgd) x = fminf(1.f, fmaxf(0.f, x));
     x = sp.lo[r] + x * (sp.hi[r] - sp.lo[r]);
   }
   X[idx] = x;
