@@ -334,6 +334,9 @@ def run_pds(args):
         extra["batched"] = run_batched(api, dev, stream)
     if rank == 0 and world == 1 and not args.no_serving:
         extra["serving"] = run_serving(api, dev, stream)
+        extra["serving"]["other_rates"] = [run_serving(api, dev, stream, rate=r, brief=True) for r in (5.0, 200.0)]
+    if rank == 0 and world == 1 and not args.no_csvgd:
+        extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
 
     if rank == 0:
         line = {
@@ -414,7 +417,66 @@ def run_batched(api, dev, stream, n_jobs=64, iters=10):
             "autotune_s": t_tune}
 
 
-def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300):
+def run_csvgd(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
+    """Constrained SVGD (Sec. IV-E, Algorithm 1) on the benchmark workload:
+    log p_obs with the defect and limit constraints' MDMM gradient (second
+    adjoint), then the constrained update; multipliers start at zero."""
+    import torch
+    N = wl.N
+    prob = api.Problem.from_workload(wl, obs, stream=stream, checkpoint_stride=K_CKPT, fast_math=FAST_MATH)
+    prob.set_csvgd(True, 1.0)
+    prob.reserve(N)
+    sv = api.Svgd(N, wl.M, prob.P, wl.lo, wl.hi, lr=wl.lr, stream=stream)
+    sv.set_csvgd(wl.W - 1)
+    # the headline run's particles (shooting states from the observations),
+    # multipliers 0; particles whose rollout diverges sit out the SVGD steps
+    xa = np.concatenate([np.ascontiguousarray(x0.T, dtype=np.float32),
+                         np.zeros((prob.P - wl.P, N), np.float32)], axis=0)
+    X = torch.from_numpy(np.ascontiguousarray(xa)).to(dev)
+    logp = torch.empty(N, device=dev)
+    G = torch.empty((prob.grad_rows, N), device=dev)
+    status = torch.empty(N, dtype=torch.int32, device=dev)
+    L = api.lib()
+
+    def lg():
+        api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), None), "csvgd loglik")
+
+    def up():
+        api._check(L.pds_svgd_step(sv.handle, api._ptr(X), api._ptr(G), None, None), "csvgd step")
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lg()
+            up()
+    stream.synchronize()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(iters)]
+    with torch.cuda.stream(stream):
+        for k in range(iters):
+            flush.zero_()
+            evs[k][0].record(stream)
+            lg()
+            evs[k][1].record(stream)
+            up()
+            evs[k][2].record(stream)
+    stream.synchronize()
+    tot = sum(e[0].elapsed_time(e[2]) for e in evs) / iters
+    lgt = sum(e[0].elapsed_time(e[1]) for e in evs) / iters
+    with torch.cuda.stream(stream):
+        api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), api._ptr(status)),
+                   "csvgd loglik")
+    stream.synchronize()
+    nonfinite = int((status != 0).sum().item())
+    sv.close()
+    prob.close()
+    return {"workload": f"constrained SVGD (MDMM, c = 1) on the chain5 workload, N={N}, T={wl.T}, W={wl.W}, "
+                        f"K={K_CKPT}; particles carry {wl.W - 1} defect and {wl.M} limit multipliers",
+            "value": N * wl.T / (tot / 1e3), "unit": UNIT, "ms_per_iter": tot, "loglik_grad_ms": lgt,
+            "svgd_step_ms": tot - lgt, "iters": iters,
+            "init": "the headline run's particles; multipliers 0",
+            "nonfinite_particles_after": nonfinite}
+
+
+def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False):
     """Poisson arrivals of jobs from the uneven-problem distribution, each
     run to `iters` SVGD iterations: continuous batching against one job at a
     time with plain launches."""
@@ -431,6 +493,9 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300):
     lat_p, _, wall_p = serve.run_plain(jobs, arrivals, checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH),
                                        stream=stream)
     n_arm = sum(1 for w in wls if hasattr(w, "arm_len"))
+    if brief:
+        return {"rate_per_s": rate, "served": {**serve.percentiles(lat_s), "value": units / wall_s},
+                "plain_sequential": {**serve.percentiles(lat_p), "value": units / wall_p}}
     return {"workload": f"{n_jobs} jobs, Poisson arrivals at {rate:g}/s, {iters} SVGD iterations each: "
                         f"{n_jobs - n_arm} uneven chain problems, {n_arm} arm-box jobs at 512 particles",
             "served": {**serve.percentiles(lat_s), "value": units / wall_s, "wall_s": wall_s},
@@ -454,6 +519,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-problems measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-csvgd", action="store_true", help="skip the constrained-SVGD measurement")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
     ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
     args = ap.parse_args()

@@ -38,6 +38,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <limits>
 #include <vector>
 #ifdef _OPENMP
 #include <omp.h>
@@ -592,6 +593,42 @@ static void svgd_phi(int N, int M, const double* u, const double* g, double bw, 
   }
 }
 
+// Particles that sit out an SVGD step: any unit-box coordinate or gradient
+// component not finite.  They take no part in the median's pairs or in the
+// other particles' sums; the bandwidth and the 1/N of Eq. 1 count the live
+// particles only, and a particle that sits out gets the direction NaN.
+static int live_mask(int N, int M, const double* u, const double* g, std::vector<char>& live) {
+  live.assign(N, 1);
+  int n = 0;
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < M; ++k)
+      if (!std::isfinite(u[(size_t)i * M + k]) || !std::isfinite(g[(size_t)i * M + k])) live[i] = 0;
+    n += live[i];
+  }
+  return n;
+}
+
+// Median (as median_sqdist) and phi (as svgd_phi) over the live particles.
+static double live_step_phi(int N, int M, const double* u, const double* g, double* phi, double* bw_out) {
+  std::vector<char> live;
+  const int nl = live_mask(N, M, u, g, live);
+  std::vector<double> ul, gl;
+  std::vector<int> idx;
+  for (int i = 0; i < N; ++i)
+    if (live[i]) {
+      idx.push_back(i);
+      for (int k = 0; k < M; ++k) { ul.push_back(u[(size_t)i * M + k]); gl.push_back(g[(size_t)i * M + k]); }
+    }
+  const double bw = bandwidth_from_median(nl, median_sqdist(nl, M, ul.data()));
+  std::vector<double> pl((size_t)nl * M);
+  if (nl > 0) svgd_phi(nl, M, ul.data(), gl.data(), bw, pl.data());
+  for (size_t t = 0; t < (size_t)N * M; ++t) phi[t] = std::numeric_limits<double>::quiet_NaN();
+  for (int a = 0; a < nl; ++a)
+    for (int k = 0; k < M; ++k) phi[(size_t)idx[a] * M + k] = pl[(size_t)a * M + k];
+  *bw_out = bw;
+  return bw;
+}
+
 // Adam ascent on x with direction g (Kingma & Ba): bias-corrected moments.
 static void adam_ascent(double& x, double& m, double& v, double g, int t, double lr, double b1, double b2, double eps) {
   m = b1 * m + (1.0 - b1) * g;
@@ -1034,9 +1071,8 @@ int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
       u[(size_t)i * M + k] = (particles[(size_t)i * P + k] - lo[k]) / w;
       gu[(size_t)i * M + k] = grad[(size_t)i * P + k] * w;  // chain rule through u
     }
-  const double med = median_sqdist(N, M, u.data());
-  const double bw = bandwidth_from_median(N, med);
-  svgd_phi(N, M, u.data(), gu.data(), bw, phi.data());
+  double bw = 1.0;
+  live_step_phi(N, M, u.data(), gu.data(), phi.data(), &bw);
   *t += 1;
   for (int i = 0; i < N; ++i) {
     for (int k = 0; k < M; ++k) {
@@ -1088,8 +1124,8 @@ int orc_csvgd_step(int N, int M, int Pc, int n_def, const double* lo, const doub
       u[(size_t)i * M + k] = (particles[(size_t)i * Pc + k] - lo[k]) / w;
       gu[(size_t)i * M + k] = out[(size_t)i * G + k] * w;
     }
-  const double bw = bandwidth_from_median(N, median_sqdist(N, M, u.data()));
-  svgd_phi(N, M, u.data(), gu.data(), bw, phi.data());
+  double bw = 1.0;
+  live_step_phi(N, M, u.data(), gu.data(), phi.data(), &bw);
   *t += 1;
   for (int i = 0; i < N; ++i) {
     const double* o = out + (size_t)i * G;

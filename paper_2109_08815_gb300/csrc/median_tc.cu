@@ -266,7 +266,8 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
           const unsigned int bits = (unsigned int)max((int)r[q], 0);
-          if (q < jmax && q >= jmin) {
+          // pairs with a particle that sits out the step are NaN
+          if (q < jmax && q >= jmin && (r[q] & 0x7fffffffu) <= 0x7f800000u) {
             if (pass == 0) atomicAdd(&hist[bits >> 21], 1u);
             else if (pass == 1) { if ((bits >> 21) == prefix) atomicAdd(&hist[(bits >> 10) & 2047u], 1u); }
             else if ((bits >> 10) == prefix) atomicAdd(&hist[bits & 1023u], 1u);

@@ -109,6 +109,8 @@ struct SvgdCtl {
   int mode;                  // 0: select among candidates; 1: full radix passes over all pairs
   int tc_error;              // set if a tensor-core pass gave up waiting for its products
   unsigned int gmax[16];     // max |g_u| per component (float bits); reset at the end of each step
+  unsigned int n_live;       // particles with finite coordinates and gradient (the others sit out the step)
+  unsigned int live_blocks;  // blocks of the liveness pass that have finished
 };
 
 struct SvgdWork {

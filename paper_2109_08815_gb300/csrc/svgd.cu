@@ -36,6 +36,8 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     ctl->below = 0ull;
     ctl->inside = 0ull;
     ctl->mode = mode;
+    ctl->n_live = 0u;
+    ctl->live_blocks = 0u;
   }
   const int total = sp.M * sp.N;
   const int k = idx < total ? idx / sp.N : -1;
@@ -45,7 +47,7 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     u[idx] = (X[idx] - sp.lo[k]) / width;
     const float g = G[idx] * width;
     gu[idx] = g;
-    gbits = __float_as_uint(fabsf(g));
+    if (isfinite(g)) gbits = __float_as_uint(fabsf(g));  // particles that are not finite sit out
   }
   // per-component max |g_u| (scales of the fp16 second product of the
   // tensor-core phi); one atomic per warp when the warp holds one component
@@ -55,6 +57,40 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     if ((threadIdx.x & 31) == 0 && k0 >= 0 && m) atomicMax(&ctl->gmax[k0], m);
   } else if (k >= 0 && gbits) {
     atomicMax(&ctl->gmax[k], gbits);
+  }
+}
+
+// Liveness of each particle: a particle whose unit-box coordinates or
+// gradient are not all finite sits out this step (its coordinates in u become
+// NaN, so it takes no part in the median's pairs or in the other particles'
+// kernel sums, and its own direction is NaN).  Counts the live particles;
+// the last block sets the median's rank over the live pairs.
+__global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* __restrict__ ctl,
+                                                        float* __restrict__ u, const float* __restrict__ gu) {
+  __shared__ unsigned int blk;
+  __shared__ bool last;
+  if (threadIdx.x == 0) blk = 0u;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    bool live = true;
+    for (int k = 0; k < M; ++k) live = live && isfinite(u[(size_t)k * N + i]) && isfinite(gu[(size_t)k * N + i]);
+    if (live) atomicAdd(&blk, 1u);
+    else
+      for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (blk) atomicAdd(&ctl->n_live, blk);
+    __threadfence();
+    last = atomicAdd(&ctl->live_blocks, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long nl = atomicAdd(&ctl->n_live, 0u);
+    const unsigned long long pairs = nl * (nl > 0 ? nl - 1ull : 0ull) / 2ull;
+    ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
   }
 }
 
@@ -119,6 +155,7 @@ constexpr int kRows = 2;                 // rows (particles i) per thread
 constexpr int kSpan = kTile * kRows;     // particles per square tile
 
 __device__ __forceinline__ void hist_add(unsigned int* hist, float d, int pass, unsigned int prefix) {
+  if (!(d == d)) return;  // a pair with a particle that sits out the step
   const unsigned int bits = __float_as_uint(d);
   if (pass == 0) {
     atomicAdd(&hist[bits >> 21], 1u);
@@ -217,7 +254,8 @@ __global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N,
     if (pass == 2) {
       const float med = __uint_as_float(prefix);
       ctl->med = med;
-      ctl->bw = (med > 0.f && N > 1) ? med / logf((float)N) : 1.0f;
+      const unsigned int nl = ctl->n_live;
+      ctl->bw = (med > 0.f && nl > 1) ? med / logf((float)nl) : 1.0f;
     }
   }
   __syncwarp();
@@ -514,8 +552,19 @@ __global__ void __launch_bounds__(kTile) svgd_phi_kernel(int N, int M, const flo
   for (int k = 0; k < MM; ++k) { g0[k] = 0.f; g1[k] = 0.f; r0[k] = 0.f; r1[k] = 0.f; }
   for (int jt = j0; jt < j1; jt += kTile) {
     const int j = jt + threadIdx.x;
-    stage_row<MM>(u, M, N, j, j < j1, uj[threadIdx.x]);
-    stage_row<MM>(gu, M, N, j, j < j1, gj[threadIdx.x]);
+    // a particle that sits out the step (u is NaN) is staged far away (its
+    // kernel value underflows to 0) with a zero gradient
+    const bool live = j < j1 && isfinite(u[(size_t)(j < N ? j : 0)]);
+    if (live || j >= j1) {
+      stage_row<MM>(u, M, N, j, j < j1, uj[threadIdx.x]);
+      stage_row<MM>(gu, M, N, j, j < j1, gj[threadIdx.x]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < Pad4<MM>::Q; ++q) {
+        uj[threadIdx.x][q] = make_float4(1e18f, 1e18f, 1e18f, 1e18f);
+        gj[threadIdx.x][q] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
     __syncthreads();
     const int jn = min(kTile, j1 - jt);
     for (int jj = 0; jj < jn; ++jj) {
@@ -575,7 +624,8 @@ __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float
   if (r < sp.M) {
     float s = 0.f;
     for (int c = 0; c < chunks; ++c) s += phi_part[((size_t)c * sp.M + r) * sp.N + i];
-    g = s / (float)sp.N;
+    const unsigned int nl = ctl->n_live;  // the 1/N of Eq. 1 over the live particles
+    g = s / (float)(nl ? nl : 1u);
     if (phi_out) phi_out[idx] = g;
     const float width = sp.hi[r] - sp.lo[r];
     // constrained SVGD: plus the constraint direction -dPsi/dtheta, in u
@@ -623,7 +673,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
   {
     const int total = (M * N > kHistBins) ? M * N : kHistBins;
     svgd_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
-    ++n;
+    svgd_live_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, M, w.ctl, w.u, w.gu);
+    n += 2;
   }
   if (N >= 2) {
     const int nt = (N + kSpan - 1) / kSpan;
@@ -751,6 +802,7 @@ __global__ void noalloc_prep_kernel(int N, int M, NoAllocBox box, const float* _
     ctl->bw = 1.0f;
     ctl->med = 0.0f;
     ctl->mode = 1;
+    ctl->n_live = (unsigned int)N;
   }
   if (idx < M * N) {
     const int k = idx / N;

@@ -106,7 +106,8 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
   if (j >= Npad) return;
   float x[MM], g[MM];
   float n = 0.f, L = 0.f;
-  const bool live = j < N;
+  // a particle that sits out the step (u is NaN) is treated as padding
+  bool live = j < N && isfinite(u[(size_t)(j < N ? j : 0)]);
   if (live) L = 1.4426950408889634f / ctl->bw;
 #pragma unroll
   for (int k = 0; k < MM; ++k) {

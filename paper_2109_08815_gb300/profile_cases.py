@@ -6,6 +6,10 @@ at a time (for example under ``ncu -k``), on seeded synthetic inputs.
         fast math) with N particles: ``--calls`` launches of rollout_kernel
         and window_reduce_kernel.
 
+    python -m paper_2109_08815_gb300.profile_cases csvgd [--n 16384] [--steps 3]
+        constrained SVGD (Sec. IV-E) on the same chain: --steps iterations of
+        pds_loglik_grad (two adjoints) and pds_svgd_step, multipliers from 0.
+
     python -m paper_2109_08815_gb300.profile_cases svgd [--n 16384] [--m 10] [--steps 3]
         pds_svgd_step on N particles in the unit box with M kernel
         coordinates: per step the median passes (median_tc_kernel for
@@ -46,6 +50,35 @@ def rollout_case(n: int, calls: int) -> float:
     return out
 
 
+def csvgd_case(n: int, steps: int) -> float:
+    wl = wlmod.chain5(N=n)
+    dev = torch.device("cuda")
+    gen = api.Problem.from_workload(wl, np.zeros((wl.T, wl.D), np.float32))
+    th = torch.tensor(wl.theta_true, dtype=torch.float32, device=dev).reshape(wl.M, 1).contiguous()
+    states = gen.simulate(th)
+    torch.cuda.synchronize()
+    obs = wlmod.observations(wl, states[:, :, 0].cpu().numpy().astype(np.float64)).astype(np.float32)
+    gen.close()
+    x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
+    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=1)
+    prob.set_csvgd(True, 1.0)
+    sv = api.Svgd(n, wl.M, prob.P, wl.lo, wl.hi, lr=wl.lr)
+    sv.set_csvgd(wl.W - 1)
+    xa = np.concatenate([np.ascontiguousarray(x0.T, dtype=np.float32), np.zeros((prob.P - wl.P, n), np.float32)])
+    X = torch.from_numpy(np.ascontiguousarray(xa)).to(dev)
+    G = torch.empty((prob.grad_rows, n), device=dev)
+    logp = torch.empty(n, device=dev)
+    bw = None
+    for _ in range(steps):
+        prob.loglik_grad(X, out=(logp, G, None))
+        bw, _ = sv.step(X, G)
+    torch.cuda.synchronize()
+    out = float(bw.item())
+    sv.close()
+    prob.close()
+    return out
+
+
 def svgd_case(n: int, m: int, steps: int) -> float:
     P = 200 if m <= 200 else m
     rng = np.random.default_rng(0)
@@ -63,7 +96,7 @@ def svgd_case(n: int, m: int, steps: int) -> float:
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("case", choices=["rollout", "svgd"])
+    ap.add_argument("case", choices=["rollout", "svgd", "csvgd"])
     ap.add_argument("--n", type=int, default=None, help="particles (rollout 4096, svgd 16384 by default)")
     ap.add_argument("--m", type=int, default=10, help="kernel coordinates (svgd)")
     ap.add_argument("--calls", type=int, default=2, help="pds_loglik_grad calls (rollout)")
@@ -72,6 +105,9 @@ def main(argv=None) -> int:
     if a.case == "rollout":
         v = rollout_case(a.n or 4096, a.calls)
         print(f"rollout ok: sum log p = {v:.6e}")
+    elif a.case == "csvgd":
+        v = csvgd_case(a.n or 16384, a.steps)
+        print(f"csvgd ok: bandwidth = {v:.6e}")
     else:
         v = svgd_case(a.n or 16384, a.m, a.steps)
         print(f"svgd ok: bandwidth = {v:.6e}")

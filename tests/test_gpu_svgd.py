@@ -214,3 +214,37 @@ def test_tensor_core_median_matches_cuda_cores(N, M):
     d = ((u[:, None, :] - u[None, :, :]) ** 2).sum(-1)[np.triu_indices(N, 1)]
     med = np.partition(d, (len(d) - 1) // 2)[(len(d) - 1) // 2]
     assert abs(out[1] - med / np.log(N)) <= 1e-5 * med / np.log(N)
+
+
+@pytest.mark.parametrize("N,M,phi_cc,med_cc,full", [(300, 4, 0, 0, 0), (300, 4, 1, 1, 0), (2500, 6, 0, 0, 0),
+                                                      (2500, 6, 0, 0, 1), (2500, 6, 1, 1, 0)])
+def test_particles_that_are_not_finite_sit_out(N, M, phi_cc, med_cc, full):
+    """Particles with a non-finite gradient or coordinate take no part in the
+    median or the other particles' phi (tensor-core and CUDA-core paths,
+    bracket and full passes); against the oracle's step over the live set."""
+    rng = np.random.default_rng(N + M)
+    P = M + 2
+    lo, hi = np.zeros(M), np.ones(M)
+    x = rng.uniform(0.05, 0.95, size=(N, P)).astype(np.float32).astype(np.float64)
+    g = rng.normal(size=(N, P)).astype(np.float32).astype(np.float64)
+    dead = rng.choice(N, 7, replace=False)
+    g[dead[:3], 0] = np.inf
+    g[dead[3:5], M - 1] = np.nan
+    x[dead[5:], 1] = np.nan
+    live = np.setdiff1d(np.arange(N), dead)
+    sv = api.Svgd(N, M, P, lo, hi)
+    sv.set_option(api.OPT_PHI_CUDA_CORES, phi_cc)
+    sv.set_option(api.OPT_MEDIAN_CUDA_CORES, med_cc)
+    sv.set_option(api.OPT_MEDIAN_FULL_PASSES, full)
+    X = _gpu(x)
+    bw, phi = sv.step(X, _gpu(g), return_phi=True)
+    torch.cuda.synchronize()
+    ost = orc.SvgdState(N, P, lo, hi, lr=1e-2)
+    xo = np.ascontiguousarray(x.copy())
+    phi_ref, bw_ref = ost.step(xo, g)
+    assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref, (bw.item(), bw_ref)
+    phi = phi.cpu().numpy().T
+    assert np.all(np.isfinite(phi[live]))
+    assert np.max(np.abs(phi[live] - phi_ref[live])) <= 2e-3 * np.max(np.abs(phi_ref[live]))
+    assert np.all(np.isnan(phi[dead]))
+    sv.close()

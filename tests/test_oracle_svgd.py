@@ -80,3 +80,30 @@ def test_adam_step_on_shooting_states_and_clamp():
     # first Adam step moves by lr * sign(g) (|g| >> eps)
     np.testing.assert_allclose(x[:, 2:], x_before[:, 2:] + 0.1 * np.sign(g[:, 2:]), atol=1e-7)
     assert np.all(x[:, :M] >= lo) and np.all(x[:, :M] <= hi)
+
+
+def test_particles_that_are_not_finite_sit_out_the_step():
+    """A particle whose gradient or coordinates are not finite takes no part
+    in the step: the others move exactly as in a step over the live subset
+    alone (median, bandwidth and the 1/N of Eq. 1 over the live particles),
+    and its own direction is NaN."""
+    rng = np.random.default_rng(31)
+    N, M, P = 40, 3, 5
+    lo, hi = np.zeros(M), np.ones(M)
+    x = rng.uniform(0.1, 0.9, size=(N, P))
+    g = rng.normal(size=(N, P))
+    dead = [3, 17, 29]
+    g[3, 0] = np.inf
+    g[17, 2] = np.nan
+    x[29, 1] = np.nan
+    live = np.setdiff1d(np.arange(N), dead)
+    st = orc.SvgdState(N, P, lo, hi, lr=1e-2)
+    xa = x.copy()
+    phi, bw = st.step(xa, g)
+    sl = orc.SvgdState(len(live), P, lo, hi, lr=1e-2)
+    xl = np.ascontiguousarray(x[live])
+    phi_l, bw_l = sl.step(xl, np.ascontiguousarray(g[live]))
+    assert bw == bw_l
+    np.testing.assert_array_equal(phi[live], phi_l)
+    np.testing.assert_array_equal(xa[live], xl)
+    assert np.all(np.isnan(phi[dead]))
