@@ -340,6 +340,11 @@ struct Problem {
   const double* lo;        // [M]
   const double* hi;        // [M]
   double c_lim;
+  // a set of R trajectories (Sec. IV-C, Eqs. traj_likelihood_sum/_prod):
+  // obs is then [R][T][D] and s0 [R][2n]; each trajectory has its own
+  // shooting states.  combine: 0 sum (equally weighted mixture), 1 product.
+  int R;
+  int combine;
 };
 
 static inline int window_start(const Problem& P, int w) { return (int)(((long long)w * P.T) / P.W); }
@@ -443,6 +448,56 @@ static double particle_loglik_grad(const Problem& P, const double* x, double* gr
   }
   total += limit_logprior(P, x, grad);
   return total;
+}
+
+// A set of R trajectories, each with its own shooting states: particle x =
+// [theta, s^s of trajectory 0, .., s^s of trajectory R-1].  Each
+// trajectory's log p_ms,r (Eq. 5) comes from particle_loglik_grad on a
+// one-trajectory view of the problem; the parameter-limit prior is counted
+// once.  Sum (Eq. traj_likelihood_sum, equally weighted: the mixture's 1/R):
+//   log p = logsumexp_r(a_r) - log R + log p_lim,  a_r = log p_ms,r - log p_lim
+//   d log p = sum_r w_r d a_r + d log p_lim,        w = softmax(a)
+// Product (Eq. traj_likelihood_prod):  log p = sum_r a_r + log p_lim.
+static double set_loglik_grad(const Problem& P, const double* x, double* grad) {
+  const int S = 2 * P.n, M = P.M, W = P.W, R = P.R;
+  const int Ps = (W - 1) * S, P1 = M + Ps, Pdim = M + R * Ps;
+  Problem one = P;
+  one.R = 1;
+  std::vector<double> xr(P1), gr(P1), a(R), gprior(M, 0.0);
+  std::vector<std::vector<double>> grads(R);
+  const double prior = limit_logprior(P, x, gprior.data());
+  for (int r = 0; r < R; ++r) {
+    one.obs = P.obs + (size_t)r * P.T * P.D;
+    one.s0 = P.s0 + (size_t)r * S;
+    std::copy(x, x + M, xr.begin());
+    std::copy(x + M + r * Ps, x + M + (r + 1) * Ps, xr.begin() + M);
+    a[r] = particle_loglik_grad(one, xr.data(), grad ? gr.data() : nullptr) - prior;
+    if (grad) {
+      grads[r] = gr;
+      for (int k = 0; k < M; ++k) grads[r][k] -= gprior[k];
+    }
+  }
+  std::vector<double> w(R, 1.0);
+  double lp = 0.0;
+  if (P.combine == 0) {
+    const double amax = *std::max_element(a.begin(), a.end());
+    double z = 0.0;
+    for (int r = 0; r < R; ++r) z += std::exp(a[r] - amax);
+    lp = amax + std::log(z) - std::log((double)R);
+    for (int r = 0; r < R; ++r) w[r] = std::exp(a[r] - amax) / z;
+  } else {
+    for (int r = 0; r < R; ++r) lp += a[r];
+  }
+  if (grad) {
+    std::fill(grad, grad + Pdim, 0.0);
+    for (int k = 0; k < M; ++k) {
+      grad[k] = gprior[k];
+      for (int r = 0; r < R; ++r) grad[k] += w[r] * grads[r][k];
+    }
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < Ps; ++k) grad[M + r * Ps + k] = w[r] * grads[r][M + k];
+  }
+  return lp + prior;
 }
 
 // ---------------------------------------------------------------------------
@@ -1027,8 +1082,17 @@ int orc_step(int n, double g, const double* m, const double* l, const double* b,
 int orc_loglik_grad(const Problem* prob, const double* particles, int N, double* logp, double* grad, int threads) {
   const Problem& P = *prob;
   // M theta directions plus 2S state directions must fit the dual width.
-  if (P.n < 1 || P.M < 0 || P.W < 1 || P.T < P.W || P.M + 4 * P.n > MAXD) return -1;
-  const int Pdim = P.M + (P.W - 1) * 2 * P.n;
+  if (P.n < 1 || P.M < 0 || P.W < 1 || P.T < P.W || P.M + 4 * P.n > MAXD || P.R < 1) return -1;
+  const int Pdim = P.M + P.R * (P.W - 1) * 2 * P.n;
+  if (P.R > 1) {
+#ifdef _OPENMP
+    if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int i = 0; i < N; ++i)
+      logp[i] = set_loglik_grad(P, particles + (size_t)i * Pdim, grad ? grad + (size_t)i * Pdim : nullptr);
+    return 0;
+  }
 #ifdef _OPENMP
   if (threads > 0) omp_set_num_threads(threads);
 #pragma omp parallel for schedule(dynamic, 1)

@@ -62,6 +62,8 @@ class _Problem(ctypes.Structure):
         ("lo", _dp),
         ("hi", _dp),
         ("c_lim", ctypes.c_double),
+        ("R", ctypes.c_int),
+        ("combine", ctypes.c_int),
     ]
 
 
@@ -214,10 +216,13 @@ class Problem:
 
     ``obs`` is [T][D]: row t-1 holds observation x_t.  Particles are
     [N][P] with P = M + (W-1)*2n: theta first, then s^s_1 .. s^s_{W-1}.
+    A set of R trajectories: ``obs`` [R][T][D], ``s0`` [R][2n] and
+    ``combine`` "sum" (equally weighted mixture) or "product"; particles then
+    carry each trajectory's shooting states in turn, P = M + R (W-1) 2n.
     """
 
     def __init__(self, *, mass, length, damping, theta_kind, theta_link, dt, T, W, obs, obs_index,
-                 sigma_obs, sigma_def, s0, lo, hi, g=9.81, c_lim=1e4):
+                 sigma_obs, sigma_def, s0, lo, hi, g=9.81, c_lim=1e4, combine="sum"):
         self._keep = []
 
         def d(x):
@@ -235,14 +240,19 @@ class Problem:
         self.W = int(W)
         self.T = int(T)
         self.S = 2 * self.n
-        self.P = self.M + (self.W - 1) * self.S
         obs = np.asarray(obs, dtype=np.float64)
-        self.D = obs.shape[1]
+        s0 = np.asarray(s0, dtype=np.float64)
+        if obs.ndim == 2:
+            obs, s0 = obs[None], s0.reshape(1, -1)
+        self.R = obs.shape[0]
+        assert s0.shape == (self.R, self.S) and combine in ("sum", "product")
+        self.P = self.M + self.R * (self.W - 1) * self.S
+        self.D = obs.shape[2]
         self.c = _Problem(
             n=self.n, g=float(g), mass=d(mass), length=d(length), damping=d(damping), M=self.M,
             theta_kind=i(theta_kind), theta_link=i(theta_link), dt=float(dt), T=self.T, W=self.W, D=self.D,
             obs_index=i(obs_index), obs=d(obs), sigma_obs=float(sigma_obs), sigma_def=float(sigma_def),
-            s0=d(s0), lo=d(lo), hi=d(hi), c_lim=float(c_lim))
+            s0=d(s0), lo=d(lo), hi=d(hi), c_lim=float(c_lim), R=self.R, combine=0 if combine == "sum" else 1)
 
     @property
     def Pc(self):
@@ -254,6 +264,7 @@ class Problem:
         """Constrained SVGD (Sec. IV-E): returns (log p_obs [N], out [N][Pc+M])
         with out's rows as orc_csvgd_loglik_grad documents: d log p_obs/d theta,
         d(log p_obs - Psi)/d s^s, g_def, g_lim, -dPsi/d theta."""
+        assert self.R == 1, "constrained SVGD is built for one trajectory"
         x, xp = _d(np.atleast_2d(particles))
         N = x.shape[0]
         assert x.shape[1] == self.Pc, (x.shape, self.Pc)
