@@ -51,6 +51,7 @@ extern "C" {
 #define PDS_MAX_LINKS 8
 #define PDS_MAX_THETA 16
 #define PDS_MAX_WINDOW_STEPS 4096
+#define PDS_MAX_TRAJECTORIES 8
 
 /* Articulated system (Appendix B-A: the simulator computes joint
  * accelerations with the articulated-body algorithm and integrates them with
@@ -138,7 +139,8 @@ int pds_problem_create_armbox(const pds_armbox_desc* sys, double dt, int T, int 
 /* Release the problem and all device memory it owns (synchronises its stream). */
 int pds_problem_destroy(pds_problem_t p);
 
-/* Report M (= dim theta), S (= 2n, state size) and P (= M + (W-1)*S). */
+/* Report M (= dim theta), S (= 2n, state size) and P (= M + (W-1)*S, or as
+ * pds_problem_set_csvgd / pds_problem_set_trajectories change it). */
 int pds_problem_layout(pds_problem_t p, int* M, int* S, int* P);
 
 /* Adjoint checkpoint stride K (default 10): the reverse sweep keeps one
@@ -177,6 +179,24 @@ int pds_problem_get_option(pds_problem_t p, int option, int* value);
  * system.  The iteration buffers are released (pds_iterate reallocates
  * them). */
 int pds_problem_set_csvgd(pds_problem_t p, int enable, double c);
+
+/* A set of R trajectories (Sec. IV-C, Eqs. traj_likelihood_sum / _prod):
+ * replaces the problem's observations and start state.  Every trajectory
+ * has its own shooting states; the particle layout becomes
+ * P = M + R (W-1) S (theta, then trajectory 0's shooting states, ...).
+ *  obs     : host [R][T][D] float, copied to the device.
+ *  s0      : host [R][S] float.
+ *  combine : PDS_COMBINE_SUM, the equally weighted Gaussian mixture
+ *            log p = logsumexp_r(log p_ms,r) - log R (plus log p_lim once);
+ *            PDS_COMBINE_PRODUCT, log p = sum_r log p_ms,r (plus log p_lim
+ *            once).
+ * The gradient of the sum weights trajectory r by its responsibility
+ * softmax_r(log p_ms,r).  1 <= R <= PDS_MAX_TRAJECTORIES.
+ * PDS_ERR_UNSUPPORTED for the arm-and-box system, for constrained SVGD,
+ * and in batches. */
+#define PDS_COMBINE_SUM 0
+#define PDS_COMBINE_PRODUCT 1
+int pds_problem_set_trajectories(pds_problem_t p, int R, const float* obs, const float* s0, int combine);
 
 /* Allocate the workspace for up to N_max particles now, so that later calls
  * with N <= N_max allocate nothing (e.g. before capturing a CUDA graph).

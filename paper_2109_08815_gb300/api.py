@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "libpds.so")
 PDS_SYSTEM_PLANAR_CHAIN = 1
 PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
 OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES, OPT_MEDIAN_CUDA_CORES = 1, 2, 3, 4, 5
+COMBINE_SUM, COMBINE_PRODUCT = 0, 1
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
 
 _lib = None
@@ -74,6 +75,7 @@ EXPORTS = {
     "pds_problem_reserve": ([_vp, ctypes.c_int], ctypes.c_int),
     "pds_problem_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_problem_set_csvgd": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
+    "pds_problem_set_trajectories": ([_vp, ctypes.c_int, _fp, _fp, ctypes.c_int], ctypes.c_int),
     "pds_problem_get_option": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
     "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
@@ -291,6 +293,22 @@ class Problem:
         _check(L.pds_problem_layout(self._h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
         self.M, self.S, self.P = M.value, S.value, P.value
         self.csvgd = bool(enable)
+
+    def set_trajectories(self, obs, s0, combine: str = "sum"):
+        """A set of R trajectories (pds_problem_set_trajectories): obs [R][T][D],
+        s0 [R][S]; combine "sum" (equally weighted mixture) or "product"."""
+        obs = np.ascontiguousarray(obs, dtype=np.float32)
+        s0 = np.ascontiguousarray(s0, dtype=np.float32)
+        R = obs.shape[0]
+        assert obs.ndim == 3 and s0.shape == (R, self.S), (obs.shape, s0.shape)
+        mode = {"sum": COMBINE_SUM, "product": COMBINE_PRODUCT}[combine]
+        L = lib()
+        _check(L.pds_problem_set_trajectories(self._h, R, obs.ctypes.data_as(_fp), s0.ctypes.data_as(_fp), mode),
+               "pds_problem_set_trajectories")
+        M, S, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.pds_problem_layout(self._h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
+        self.M, self.S, self.P = M.value, S.value, P.value
+        self.R = R
 
     @property
     def grad_rows(self) -> int:

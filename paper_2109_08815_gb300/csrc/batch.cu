@@ -274,9 +274,9 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       delete b;
       return set_error(PDS_ERR_ARG, "SVGD state does not match its problem");
     }
-    if (p->c.csvgd || s->sp.csvgd) {
+    if (p->c.csvgd || s->sp.csvgd || p->c.R > 1) {
       delete b;
-      return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs the unconstrained method only");
+      return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs the unconstrained one-trajectory method only");
     }
     b->probs.push_back(p);
     b->svgds.push_back(s);

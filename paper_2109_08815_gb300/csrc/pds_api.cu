@@ -88,14 +88,15 @@ static void free_parts(Partials& p) {
 }
 
 int pds::ensure_workspace(pds_problem* p, int N) {
-  if (N <= p->cap_N && p->cap_K == p->c.K && p->cap_cs == p->c.csvgd) return PDS_OK;
+  if (N <= p->cap_N && p->cap_K == p->c.K && p->cap_cs == p->c.csvgd && p->cap_R == p->c.R) return PDS_OK;
   const int newN = N > p->cap_N ? N : p->cap_N;
   cudaError_t e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   free_parts(p->parts);
   p->cap_N = 0;
   const ChainParams& c = p->c;
-  const size_t Nn = (size_t)newN, W = (size_t)c.W, S = (size_t)c.S, M = (size_t)c.M;
+  // windows of all trajectories: the partials and the tape are per (trajectory, window)
+  const size_t Nn = (size_t)newN, W = (size_t)c.W * (size_t)c.R, S = (size_t)c.S, M = (size_t)c.M;
   const size_t U = Nn * W;
   const size_t tape = ((size_t)c.max_seg + (size_t)c.K) * S * U;
   if ((e = cudaMalloc(&p->parts.lp, W * Nn * sizeof(float))) != cudaSuccess ||
@@ -109,6 +110,7 @@ int pds::ensure_workspace(pds_problem* p, int N) {
     return cuda_fail(e, "workspace allocation");
   }
   p->cap_cs = c.csvgd;
+  p->cap_R = c.R;
   p->cap_N = newN;
   p->cap_K = c.K;
   return PDS_OK;
@@ -220,6 +222,8 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
     c.obs_col[idx] = d;
   }
   for (int j = 0; j < 2 * n; ++j) c.s0[j] = s0[j];
+  c.R = 1;
+  c.combine = 0;
   int hmax = 0;
   for (int w = 0; w < windows; ++w) {
     const int h = (int)(((long long)(w + 1) * T) / windows - ((long long)w * T) / windows);
@@ -297,12 +301,47 @@ int pds_problem_set_csvgd(pds_problem_t p, int enable, double c) {
   if (enable != 0 && enable != 1) return fail(PDS_ERR_ARG, "enable must be 0 or 1");
   if (enable && p->kind != PDS_SYSTEM_PLANAR_CHAIN)
     return fail(PDS_ERR_UNSUPPORTED, "constrained SVGD is built for planar chains");
+  if (enable && p->c.R > 1) return fail(PDS_ERR_UNSUPPORTED, "constrained SVGD is built for one trajectory");
   if (enable && !(c >= 0.0 && c < 1e30)) return fail(PDS_ERR_ARG, "MDMM damping c must be finite and >= 0");
   cudaStreamSynchronize(p->stream);
   ChainParams& cp = p->c;
   cp.csvgd = enable;
   cp.c_mdmm = enable ? (float)c : 0.f;
   cp.P = cp.M + (cp.W - 1) * cp.S + (enable ? (cp.W - 1) + cp.M : 0);
+  // the iteration buffers depend on P
+  cudaFree(p->d_grad);
+  cudaFree(p->d_logp);
+  cudaFree(p->d_x);
+  p->d_grad = p->d_logp = p->d_x = nullptr;
+  p->it_N = 0;
+  return PDS_OK;
+}
+
+int pds_problem_set_trajectories(pds_problem_t p, int R, const float* obs, const float* s0, int combine) {
+  if (!p || !obs || !s0) return fail(PDS_ERR_ARG, "NULL argument");
+  if (R < 1 || R > PDS_MAX_TRAJECTORIES) return fail(PDS_ERR_ARG, "R %d outside 1..%d", R, PDS_MAX_TRAJECTORIES);
+  if (combine != PDS_COMBINE_SUM && combine != PDS_COMBINE_PRODUCT) return fail(PDS_ERR_ARG, "unknown combine %d", combine);
+  if (p->kind != PDS_SYSTEM_PLANAR_CHAIN) return fail(PDS_ERR_UNSUPPORTED, "trajectory sets are built for planar chains");
+  if (p->c.csvgd) return fail(PDS_ERR_UNSUPPORTED, "constrained SVGD is built for one trajectory");
+  ChainParams& c = p->c;
+  const size_t bytes = (size_t)R * c.T * c.D * sizeof(float);
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  float* d = nullptr;
+  if ((e = cudaMalloc(&d, bytes)) != cudaSuccess) return cuda_fail(e, "cudaMalloc observations");
+  if ((e = cudaMemcpyAsync(d, obs, bytes, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(p->stream)) != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "copy observations");
+  }
+  cudaFree(p->d_obs);
+  p->d_obs = d;
+  c.obs = d;
+  for (int r = 0; r < R; ++r)
+    for (int j = 0; j < c.S; ++j) c.s0[r * kMaxState + j] = s0[(size_t)r * c.S + j];
+  c.R = R;
+  c.combine = combine;
+  c.P = c.M + R * (c.W - 1) * c.S;
   // the iteration buffers depend on P
   cudaFree(p->d_grad);
   cudaFree(p->d_logp);

@@ -11,6 +11,7 @@ namespace pds {
 constexpr int kMaxLinks = PDS_MAX_LINKS;
 constexpr int kMaxState = 2 * PDS_MAX_LINKS;
 constexpr int kMaxTheta = PDS_MAX_THETA;
+constexpr int kMaxTraj = PDS_MAX_TRAJECTORIES;
 
 // Everything a rollout thread needs about the problem; passed by value as a
 // kernel parameter (constant bank, broadcast to all threads).
@@ -31,9 +32,11 @@ struct ChainParams {
   float mass[kMaxLinks], length[kMaxLinks], damping[kMaxLinks];
   int mass_theta[kMaxLinks], length_theta[kMaxLinks], damp_theta[kMaxLinks];  // theta row or -1
   int obs_col[kMaxState];  // observation column of each state component or -1
-  float s0[kMaxState];
+  float s0[kMaxTraj * kMaxState];  // start state of trajectory r at s0[r * kMaxState]
   float lo[kMaxTheta], hi[kMaxTheta];
-  const float* obs;        // device [T][D]
+  const float* obs;        // device [R][T][D]
+  int R;                   // trajectories (each with its own shooting states)
+  int combine;             // R > 1: 0 equally weighted mixture (sum), 1 product
 };
 
 // Arm-and-box system parameters (added to ChainParams-based problems with
@@ -163,6 +166,7 @@ struct pds_problem {
   int cap_N = 0;          // workspace capacity in particles
   int cap_K = 0;          // checkpoint stride the tape was sized for
   int cap_cs = 0;         // workspace has the constrained-SVGD partials
+  int cap_R = 0;          // trajectories the workspace was sized for
   pds::Partials parts{};
   // buffers used by pds_iterate / pds_iterate_host / batches
   int it_N = 0;

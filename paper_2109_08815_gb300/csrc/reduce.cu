@@ -21,7 +21,67 @@ __global__ void __launch_bounds__(256) window_reduce_kernel(const ChainParams c,
   if (i >= N) return;
   const int y = blockIdx.y;
   bool finite = true;
-  if (c.csvgd && y == 0) {
+  if (c.R > 1) {
+    // a set of trajectories: a_r = sum_w lp of trajectory r; the mixture's
+    // responsibilities w_r = softmax(a) (sum) or 1 (product) weight each
+    // trajectory's gradients; the limit prior counts once
+    double a[kMaxTraj];
+    double amax = -INFINITY;
+    for (int r = 0; r < c.R; ++r) {
+      double s = 0.0;
+      for (int w = 0; w < c.W; ++w) s += (double)parts.lp[((size_t)r * c.W + w) * N + i];
+      a[r] = s;
+      amax = fmax(amax, s);
+    }
+    double wt[kMaxTraj];
+    double lp = 0.0;
+    if (c.combine == 0) {
+      double z = 0.0;
+      for (int r = 0; r < c.R; ++r) z += exp(a[r] - amax);
+      for (int r = 0; r < c.R; ++r) wt[r] = exp(a[r] - amax) / z;
+      lp = amax + log(z) - log((double)c.R);
+    } else {
+      for (int r = 0; r < c.R; ++r) { wt[r] = 1.0; lp += a[r]; }
+    }
+    if (y == 0) {
+      float pen = 0.f;
+      for (int k = 0; k < c.M; ++k) {
+        const float width = c.hi[k] - c.lo[k];
+        const float uk = (X[(size_t)k * N + i] - c.lo[k]) / width;
+        const float cu = fminf(1.f, fmaxf(0.f, uk));
+        pen += (cu - uk) * (cu - uk);
+        if (grad) {
+          double g = 0.0;
+          for (int r = 0; r < c.R; ++r) {
+            float gr = 0.f;
+            for (int w = 0; w < c.W; ++w) gr += parts.th[(((size_t)r * c.W + w) * c.M + k) * N + i];
+            g += wt[r] * (double)gr;
+          }
+          const float gf = (float)g + c.c_lim * (cu - uk) / width;
+          finite = finite && isfinite(gf);
+          grad[(size_t)k * N + i] = gf;
+        }
+      }
+      lp += (double)c.lim_const - 0.5 * (double)c.c_lim * (double)pen;
+      const float lpf = (float)lp;
+      finite = finite && isfinite(lpf);
+      logp[i] = lpf;
+    } else {
+      const int r = y / c.W, w = y - r * c.W;
+      if (w >= 1) {
+        const int S = c.S;
+        const float* st = parts.start + (size_t)y * S * N + i;
+        const float* nx = parts.next + (size_t)(y - 1) * S * N + i;
+        float* out = grad + ((size_t)c.M + (size_t)(r * (c.W - 1) + w - 1) * S) * N + i;
+        const float wr = (float)wt[r];
+        for (int s2 = 0; s2 < S; ++s2) {
+          const float g = wr * (st[(size_t)s2 * N] + nx[(size_t)s2 * N]);
+          finite = finite && isfinite(g);
+          out[(size_t)s2 * N] = g;
+        }
+      }
+    }
+  } else if (c.csvgd && y == 0) {
     // constrained SVGD (Sec. IV-E): log p_obs; theta rows d log p_obs/dtheta;
     // multiplier rows g_def and g_lim; rows P..P+M-1 -dPsi/dtheta (defect and
     // limit constraints, multipliers fixed)
@@ -95,7 +155,7 @@ __global__ void __launch_bounds__(256) window_reduce_kernel(const ChainParams c,
 
 cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
                                  float* grad, int32_t* status, cudaStream_t st) {
-  dim3 grid((N + 255) / 256, grad ? c.W : 1);
+  dim3 grid((N + 255) / 256, grad ? c.W * c.R : 1);
   window_reduce_kernel<<<grid, 256, 0, st>>>(c, X, N, parts, logp, grad, status);
   return cudaGetLastError();
 }

@@ -365,9 +365,10 @@ __device__ __forceinline__ void load_params(const ChainParams& c, const float* _
 // components of state (q, v) at time t (1-based), and if seed != nullptr adds
 // d/ds [-r^2 / (2 sigma^2)] = r / sigma^2 to the state adjoint.
 template <int NL>
-__device__ __forceinline__ float obs_residual(const ChainParams& c, int t, const float (&q)[NL], const float (&v)[NL],
-                                              float (&qb)[NL], float (&vb)[NL], bool seed) {
-  const float* row = c.obs + (size_t)(t - 1) * c.D;
+__device__ __forceinline__ float obs_residual(const ChainParams& c, const float* __restrict__ obs, int t,
+                                              const float (&q)[NL], const float (&v)[NL], float (&qb)[NL],
+                                              float (&vb)[NL], bool seed) {
+  const float* row = obs + (size_t)(t - 1) * c.D;
   float acc = 0.f;
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
@@ -425,11 +426,15 @@ template <int NL, bool FAST, bool CS = false>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
                                              size_t u, float* seg = nullptr, size_t seg_stride = 0) {
-  const size_t U = (size_t)N * c.W;
-  const int w = (int)(u / N);
-  const int i = (int)(u - (size_t)w * N);
+  // unit u = (r W + w) N + i: trajectory r, its window w, particle i
+  const size_t U = (size_t)N * c.W * c.R;
+  const int wg = (int)(u / N);
+  const int i = (int)(u - (size_t)wg * N);
+  const int r = wg / c.W, w = wg - r * c.W;
+  const float* obs = c.obs + (size_t)r * c.T * c.D;
+  const int shoot0 = c.M + r * (c.W - 1) * 2 * NL;  // first shooting-state row of trajectory r
   // the window-reduction kernel (next on the stream) ORs in non-finite flags
-  if (status && w == 0) status[i] = 0;
+  if (status && wg == 0) status[i] = 0;
 
   Links<NL> P;
   load_params<NL, FAST>(c, X, N, i, P);
@@ -437,9 +442,9 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   float q[NL], v[NL];
   if (w == 0) {
 #pragma unroll
-    for (int j = 0; j < NL; ++j) { q[j] = c.s0[j]; v[j] = c.s0[NL + j]; }
+    for (int j = 0; j < NL; ++j) { q[j] = c.s0[r * kMaxState + j]; v[j] = c.s0[r * kMaxState + NL + j]; }
   } else {
-    const float* xs = X + (size_t)(c.M + (w - 1) * 2 * NL) * N + i;
+    const float* xs = X + (size_t)(shoot0 + (w - 1) * 2 * NL) * N + i;
 #pragma unroll
     for (int j = 0; j < NL; ++j) { q[j] = __ldg(xs + (size_t)j * N); v[j] = __ldg(xs + (size_t)(NL + j) * N); }
   }
@@ -458,7 +463,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   for (int k = 0; k < h; ++k) {
     if (grad && (k % K) == 0) tape_store<NL>(ckpt, k / K, U, u, q, v);
     chain_step<NL, FAST>(q, v, P, c.dt);
-    rss += obs_residual<NL>(c, t0 + k + 1, q, v, qb, vb, false);
+    rss += obs_residual<NL>(c, obs, t0 + k + 1, q, v, qb, vb, false);
   }
   float lp = -0.5f * c.inv_so2 * rss + (float)h * c.obs_const;
 
@@ -468,7 +473,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 #pragma unroll
   for (int j = 0; j < NL; ++j) { qb[j] = 0.f; vb[j] = 0.f; qb2[j] = 0.f; vb2[j] = 0.f; }
   if (w < c.W - 1) {
-    const float* xs = X + (size_t)(c.M + w * 2 * NL) * N + i;
+    const float* xs = X + (size_t)(shoot0 + w * 2 * NL) * N + i;
     float dss = 0.f;
     float dd[2 * NL];
 #pragma unroll
@@ -488,7 +493,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
         nb[j] = -kap2 * dd[j];  // -dPsi/ds^s_{w+1}
         nb[NL + j] = -kap2 * dd[NL + j];
       }
-      if (grad) parts.gdef[(size_t)w * N + i] = g;
+      if (grad) parts.gdef[(size_t)wg * N + i] = g;
     } else {
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
@@ -503,10 +508,10 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 #pragma unroll
     for (int j = 0; j < 2 * NL; ++j) nb[j] = 0.f;
     if constexpr (CS) {
-      if (grad) parts.gdef[(size_t)w * N + i] = 0.f;
+      if (grad) parts.gdef[(size_t)wg * N + i] = 0.f;
     }
   }
-  parts.lp[(size_t)w * N + i] = lp;
+  parts.lp[(size_t)wg * N + i] = lp;
   if (!grad) return;
 
   // ---------------- reverse sweep
@@ -530,7 +535,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     }
     for (int k = e - 1; k >= a; --k) {
       // observation at time t0+k+1 depends on s_{k+1}
-      obs_residual<NL>(c, t0 + k + 1, qh, vh, qb, vb, true);
+      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
       if constexpr (CS) {
         StepTape<NL> F;
@@ -546,7 +551,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   }
 
   // ---------------- write partial gradients
-  float* th = parts.th + (size_t)w * c.M * N + i;
+  float* th = parts.th + (size_t)wg * c.M * N + i;
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
     if (c.mass_theta[j] >= 0) th[(size_t)c.mass_theta[j] * N] = mb[j];
@@ -554,7 +559,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     if (c.damp_theta[j] >= 0) th[(size_t)c.damp_theta[j] * N] = bb[j];
   }
   if constexpr (CS) {
-    float* th2 = parts.th2 + (size_t)w * c.M * N + i;
+    float* th2 = parts.th2 + (size_t)wg * c.M * N + i;
 #pragma unroll
     for (int j = 0; j < NL; ++j) {
       if (c.mass_theta[j] >= 0) th2[(size_t)c.mass_theta[j] * N] = mb2[j];
@@ -564,8 +569,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 #pragma unroll
     for (int j = 0; j < NL; ++j) { qb[j] += qb2[j]; vb[j] += vb2[j]; }
   }
-  float* st = parts.start + (size_t)w * 2 * NL * N + i;
-  float* nx = parts.next + (size_t)w * 2 * NL * N + i;
+  float* st = parts.start + (size_t)wg * 2 * NL * N + i;
+  float* nx = parts.next + (size_t)wg * 2 * NL * N + i;
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
     st[(size_t)j * N] = qb[j];
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
                                                                         int N, Partials parts, int grad,
                                                                         int32_t* __restrict__ status, int seg_smem) {
   extern __shared__ float seg_sh[];
-  const size_t U = (size_t)N * c.W;
+  const size_t U = (size_t)N * c.W * c.R;
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
                                                                            Partials parts, int grad,
                                                                            int32_t* __restrict__ status, int seg_smem) {
   extern __shared__ float seg_sh[];
-  const size_t U = (size_t)N * c.W;
+  const size_t U = (size_t)N * c.W * c.R;
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
@@ -684,7 +689,7 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
 template <int NL>
 cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
                               int32_t* status, cudaStream_t st) {
-  const size_t U = (size_t)N * c.W;
+  const size_t U = (size_t)N * c.W * c.R;
   const unsigned blocks = (unsigned)((U + 127) / 128);
   // the reverse sweep's K recomputed states in shared memory when they fit
   // in the default 48 KB of a block
