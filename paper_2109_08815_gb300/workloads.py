@@ -111,6 +111,34 @@ def double_pendulum(N: int = 100, seed: int = 1000) -> PlanarWorkload:
         lr=1e-2, iterations=100, seed=seed)
 
 
+def two_mode_pendulums(N: int = 100, seed: int = 6000):
+    """Two double-pendulum trajectories from two different link-length
+    settings (the setting of the paper's combination figure): unit masses,
+    theta = (l1, l2) in [0.5, 1.5]^2, both started at q0 = (90 deg, 0 deg) at
+    rest, 300 steps of 0.01 s, angles observed with sigma 0.01, 10 windows.
+
+    Returns (workload, [theta_a, theta_b], [noise_a, noise_b]): the workload
+    carries theta_a as theta_true and noise_a; noise_b is the second
+    trajectory's standard-normal observation noise [T][D].
+    """
+    rng = np.random.default_rng(seed)
+    lo = np.array([0.5, 0.5])
+    hi = np.array([1.5, 1.5])
+    theta_a = np.array([0.7, 1.2])
+    theta_b = np.array([1.2, 0.7])
+    T, D = 300, 2
+    noise = [rng.standard_normal((T, D)) for _ in range(2)]
+    theta_init = rng.uniform(lo, hi, size=(N, 2))
+    wl = PlanarWorkload(
+        name="two_mode_pendulums", n=2, mass=np.ones(2), length=theta_a.copy(), damping=np.zeros(2),
+        theta_kind=np.array([PARAM_LENGTH, PARAM_LENGTH], dtype=np.int32),
+        theta_link=np.array([0, 1], dtype=np.int32), theta_true=theta_a, lo=lo, hi=hi, dt=0.01, T=T, W=10,
+        obs_index=np.array([0, 1], dtype=np.int32), sigma_obs=0.01, sigma_def=SIGMA_DEF,
+        s0=np.array([math.pi / 2, 0.0, 0.0, 0.0]), noise=noise[0], theta_init=theta_init,
+        lr=1e-2, iterations=300, seed=seed)
+    return wl, [theta_a, theta_b], noise
+
+
 CHAIN5_LENGTH = 0.5      # fixed link length [m]; lengths are not inferred
 
 

@@ -122,3 +122,38 @@ def test_svgd_iterates_on_a_set_and_batches_refuse_it():
         prob.set_csvgd(True, 1.0)
     sv.close()
     prob.close()
+
+
+def test_sum_keeps_the_modes_and_product_averages_them():
+    """The paper's combination experiment, synthetically: two double-pendulum
+    trajectories from two link-length settings.  After 1000 iterations the
+    mixture (sum) leaves most particles at one of the two true settings,
+    while the product concentrates them at a compromise near neither."""
+    N = 200
+    wl, thetas, noises = wlmod.two_mode_pendulums(N=N)
+    dev = torch.device("cuda")
+    obs = []
+    for th, nz in zip(thetas, noises):
+        m, l, b = physical(wl, th)
+        roll = orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g)
+        obs.append((roll[1:, wl.obs_index] + wl.sigma_obs * nz).astype(np.float32))
+    obs = np.stack(obs)
+    s0s = np.stack([wl.s0, wl.s0])
+    near = {}
+    for combine in ("sum", "product"):
+        prob = api.Problem.from_workload(wl, obs[0])
+        prob.set_trajectories(obs, s0s, combine)
+        parts = [wlmod.initial_particles(wl, obs[r].astype(np.float64), rng_seed=1) for r in range(2)]
+        x = np.concatenate([parts[0][:, :2], parts[0][:, 2:], parts[1][:, 2:]], axis=1)
+        X = torch.from_numpy(np.ascontiguousarray(x.T, dtype=np.float32)).to(dev)
+        sv = api.Svgd(N, 2, prob.P, wl.lo, wl.hi, lr=1e-2)
+        api.iterate(prob, sv, X, 1000)
+        torch.cuda.synchronize()
+        th = X[:2].cpu().numpy().T
+        near[combine] = sum(float(np.mean(np.linalg.norm(th - t, axis=1) < 0.05)) for t in thetas)
+        if combine == "product":
+            assert np.all(th.std(axis=0) < 0.08), th.std(axis=0)
+        sv.close()
+        prob.close()
+    assert near["sum"] >= 0.5, near
+    assert near["product"] <= 0.05, near
