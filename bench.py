@@ -337,6 +337,8 @@ def run_pds(args):
         extra["serving"]["other_rates"] = [run_serving(api, dev, stream, rate=r, brief=True) for r in (5.0, 200.0)]
     if rank == 0 and world == 1 and not args.no_csvgd:
         extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
+    if rank == 0 and world == 1 and not args.no_trajset:
+        extra["trajectory_set"] = run_trajset(api, dev, stream, flush)
 
     if rank == 0:
         line = {
@@ -476,6 +478,62 @@ def run_csvgd(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
             "nonfinite_particles_after": nonfinite}
 
 
+def run_trajset(api, dev, stream, flush, N=8192, R=2, iters=10, warmup=3):
+    """Likelihood of a set of R trajectories (Sec. IV-C, the equally weighted
+    mixture) on the chain5 system: R trajectories from R parameter draws and
+    start states, N particles each carrying R sets of shooting states."""
+    import dataclasses
+
+    import torch
+    wl = wlmod.chain5(N=N)
+    rng = np.random.default_rng(7000)
+    wls = [wl] + [dataclasses.replace(wl, theta_true=rng.uniform(wl.lo, wl.hi),
+                                      s0=np.concatenate([rng.uniform(-1.0, 1.0, wl.n), np.zeros(wl.n)]),
+                                      noise=rng.standard_normal(wl.noise.shape)) for _ in range(R - 1)]
+    obs = np.stack([_gen_obs(api, w, dev, stream) for w in wls])
+    s0s = np.stack([w.s0 for w in wls]).astype(np.float32)
+    prob = api.Problem.from_workload(wl, obs[0], stream=stream, checkpoint_stride=K_CKPT, fast_math=FAST_MATH)
+    prob.set_trajectories(obs, s0s, "sum")
+    prob.reserve(N)
+    parts = [wlmod.initial_particles(w, o.astype(np.float64), rng_seed=1) for w, o in zip(wls, obs)]
+    x = np.concatenate([parts[0][:, :wl.M]] + [p[:, wl.M:] for p in parts], axis=1)
+    X = torch.from_numpy(np.ascontiguousarray(x.T, dtype=np.float32)).to(dev)
+    sv = api.Svgd(N, wl.M, prob.P, wl.lo, wl.hi, lr=wl.lr, stream=stream)
+    logp = torch.empty(N, device=dev)
+    G = torch.empty((prob.P, N), device=dev)
+    L = api.lib()
+
+    def lg():
+        api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), None), "set loglik")
+
+    def up():
+        api._check(L.pds_svgd_step(sv.handle, api._ptr(X), api._ptr(G), None, None), "set step")
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lg()
+            up()
+    stream.synchronize()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(iters)]
+    with torch.cuda.stream(stream):
+        for k in range(iters):
+            flush.zero_()
+            evs[k][0].record(stream)
+            lg()
+            evs[k][1].record(stream)
+            up()
+            evs[k][2].record(stream)
+    stream.synchronize()
+    tot = sum(e[0].elapsed_time(e[2]) for e in evs) / iters
+    lgt = sum(e[0].elapsed_time(e[1]) for e in evs) / iters
+    sv.close()
+    prob.close()
+    return {"workload": f"set of {R} chain5 trajectories (equally weighted mixture), N={N}, T={wl.T}, W={wl.W}, "
+                        f"K={K_CKPT}; each particle carries {R} sets of shooting states",
+            "value": N * R * wl.T / (tot / 1e3), "unit": UNIT, "ms_per_iter": tot, "loglik_grad_ms": lgt,
+            "svgd_step_ms": tot - lgt, "iters": iters}
+
+
 def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False):
     """Poisson arrivals of jobs from the uneven-problem distribution, each
     run to `iters` SVGD iterations: continuous batching against one job at a
@@ -520,6 +578,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-problems measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-csvgd", action="store_true", help="skip the constrained-SVGD measurement")
+    ap.add_argument("--no-trajset", action="store_true", help="skip the trajectory-set measurement")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
     ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
     args = ap.parse_args()
