@@ -398,6 +398,25 @@ int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_
 int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo,
                           const float* theta_hi, float* bandwidth_out, void* cuda_stream);
 
+/* ---- Posterior metrics (Sec. IV: Eq. knn-kl and the maximum mean
+ * discrepancy).  Sample sets are device arrays [d][n] float (coordinate-
+ * major, like particles), 1 <= d <= 64.  Both synchronise the stream and
+ * return the value on the host.
+ *
+ * pds_knn_kl: the k-nearest-neighbour estimate of KL(P || Q) with
+ * k_i = l_i = k (1 <= k <= 8; the paper uses 3):
+ *   (d / n) sum_i log( nu_k(i) / rho_k(i) ) + log( m / (n - 1) ),
+ * nu_k(i) the Euclidean distance from p_i to its k-th nearest neighbour in
+ * Q, rho_k(i) the same in P without p_i.  p [d][n], q [d][m], n >= k + 1,
+ * m >= k.  Coincident points make a ratio 0 or infinite.
+ *
+ * pds_mmd2: the unbiased estimate of the squared maximum mean discrepancy
+ * with the kernel exp(-||x - y||^2 / h), h > 0:
+ *   1/(n(n-1)) sum_{i!=j} k(x_i,x_j) + 1/(m(m-1)) sum_{i!=j} k(y_i,y_j)
+ *   - 2/(nm) sum_{i,j} k(x_i,y_j).   x [d][n], y [d][m], n, m >= 2. */
+int pds_knn_kl(const float* p, int n, const float* q, int m, int d, int k, double* kl, void* cuda_stream);
+int pds_mmd2(const float* x, int n, const float* y, int m, int d, double h, double* mmd2, void* cuda_stream);
+
 /* Number of kernel launches the last pds_loglik_grad / pds_svgd_step /
  * pds_iterate call made (for launch accounting). */
 int pds_last_launch_count(void);

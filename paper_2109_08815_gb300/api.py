@@ -76,6 +76,10 @@ EXPORTS = {
     "pds_problem_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_problem_set_csvgd": ([_vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
     "pds_problem_set_trajectories": ([_vp, ctypes.c_int, _fp, _fp, ctypes.c_int], ctypes.c_int),
+    "pds_knn_kl": ([_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                    ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
+    "pds_mmd2": ([_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                  ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
     "pds_problem_get_option": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
     "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
@@ -391,6 +395,30 @@ class Svgd:
         phi = torch.empty((self.M, self.N), device=particles.device, dtype=torch.float32) if return_phi else None
         _check(lib().pds_svgd_step(self._h, _ptr(particles), _ptr(grad), _ptr(bw), _ptr(phi)), "pds_svgd_step")
         return bw, phi
+
+
+def knn_kl(p: torch.Tensor, q: torch.Tensor, k: int = 3, stream=None) -> float:
+    """KNN estimate of KL(P || Q) (pds_knn_kl) for sample sets p [d][n], q [d][m]."""
+    _need_cuda(p, torch.float32, "p")
+    _need_cuda(q, torch.float32, "q")
+    assert p.dim() == 2 and q.dim() == 2 and p.shape[0] == q.shape[0]
+    h, _ = _stream_handle(stream)
+    out = ctypes.c_double()
+    _check(lib().pds_knn_kl(_ptr(p), p.shape[1], _ptr(q), q.shape[1], p.shape[0], int(k), ctypes.byref(out), h),
+           "pds_knn_kl")
+    return out.value
+
+
+def mmd2(x: torch.Tensor, y: torch.Tensor, h: float, stream=None) -> float:
+    """Unbiased MMD^2 with the RBF kernel exp(-|x - y|^2 / h) (pds_mmd2); x [d][n], y [d][m]."""
+    _need_cuda(x, torch.float32, "x")
+    _need_cuda(y, torch.float32, "y")
+    assert x.dim() == 2 and y.dim() == 2 and x.shape[0] == y.shape[0]
+    sh, _ = _stream_handle(stream)
+    out = ctypes.c_double()
+    _check(lib().pds_mmd2(_ptr(x), x.shape[1], _ptr(y), y.shape[1], x.shape[0], float(h), ctypes.byref(out), sh),
+           "pds_mmd2")
+    return out.value
 
 
 def iterate(problem: Problem, svgd: Svgd, particles: torch.Tensor, iters: int, logp: torch.Tensor | None = None):
