@@ -339,6 +339,8 @@ def run_pds(args):
         extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
     if rank == 0 and world == 1 and not args.no_trajset:
         extra["trajectory_set"] = run_trajset(api, dev, stream, flush)
+    if rank == 0 and world == 1 and not args.no_metrics:
+        extra["metrics"] = run_metrics(api, dev, X, wl)
 
     if rank == 0:
         line = {
@@ -534,6 +536,30 @@ def run_trajset(api, dev, stream, flush, N=8192, R=2, iters=10, warmup=3):
             "svgd_step_ms": tot - lgt, "iters": iters}
 
 
+def run_metrics(api, dev, X, wl, reps=5):
+    """Posterior metrics on the benchmark's particles: KNN-KL (k = 3) and the
+    unbiased MMD^2 of the N particles' theta against a reference sample of the
+    same size (particles jittered by 1 % of the box), event-timed."""
+    import torch
+    N = X.shape[1]
+    P = X[:wl.M].contiguous()
+    width = torch.tensor(wl.hi - wl.lo, dtype=torch.float32, device=dev).reshape(-1, 1)
+    g = torch.Generator(device=dev).manual_seed(8000)
+    Q = (P + 0.01 * width * torch.randn(P.shape, generator=g, device=dev)).contiguous()
+    h = float(np.mean((wl.hi - wl.lo) ** 2))
+    out = {}
+    for name, fn in (("knn_kl", lambda: api.knn_kl(P, Q, k=3)), ("mmd2", lambda: api.mmd2(P, Q, h))):
+        fn()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            v = fn()
+            ts.append(time.perf_counter() - t0)
+        out[name] = {"value": v, "ms": 1e3 * float(np.median(ts))}
+    out["workload"] = f"{N} particles' theta (d = {wl.M}) against {N} jittered copies"
+    return out
+
+
 def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False):
     """Poisson arrivals of jobs from the uneven-problem distribution, each
     run to `iters` SVGD iterations: continuous batching against one job at a
@@ -579,6 +605,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-csvgd", action="store_true", help="skip the constrained-SVGD measurement")
     ap.add_argument("--no-trajset", action="store_true", help="skip the trajectory-set measurement")
+    ap.add_argument("--no-metrics", action="store_true", help="skip the posterior-metric timing")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
     ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
     args = ap.parse_args()

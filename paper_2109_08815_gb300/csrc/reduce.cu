@@ -2,10 +2,10 @@
 // logs over windows, Sec. IV-D prior), fixed summation order over windows
 // (deterministic).
 //
-// Grid: x over particles, y over row groups.  y = 0: log p and the theta
-// gradient of the particle (sums over the W windows); y = w >= 1: the
-// gradient of shooting state s^s_w, the start-state adjoint of window w plus
-// the defect adjoint of window w-1.  In constrained-SVGD mode y = 0 also
+// Grid: x over particles, y over row groups.  y = 0: log p of the particle;
+// y = w in 1..W-1: the gradient of shooting state s^s_w, the start-state
+// adjoint of window w plus the defect adjoint of window w-1; y = W + k: the
+// gradient of theta_k (sum over the W windows plus the prior's).  In constrained-SVGD mode y = 0 also
 // writes the constraint values and the constraint gradient of theta.  Non-finite results are ORed into
 // status[i], which the rollout kernel zeroed for this call.
 #include <math.h>
@@ -126,18 +126,22 @@ __global__ void __launch_bounds__(256) window_reduce_kernel(const ChainParams c,
       const float uk = (X[(size_t)k * N + i] - c.lo[k]) / width;
       const float cu = fminf(1.f, fmaxf(0.f, uk));
       pen += (cu - uk) * (cu - uk);
-      if (grad) {
-        float g = 0.f;
-        for (int w = 0; w < c.W; ++w) g += parts.th[((size_t)w * c.M + k) * N + i];
-        g += c.c_lim * (cu - uk) / width;
-        finite = finite && isfinite(g);
-        grad[(size_t)k * N + i] = g;
-      }
     }
     lp += (double)c.lim_const - 0.5 * (double)c.c_lim * (double)pen;
     const float lpf = (float)lp;
     finite = finite && isfinite(lpf);
     logp[i] = lpf;
+  } else if (y >= c.W) {
+    // theta component k: sum over the windows plus the limit prior's gradient
+    const int k = y - c.W;
+    const float width = c.hi[k] - c.lo[k];
+    const float uk = (X[(size_t)k * N + i] - c.lo[k]) / width;
+    const float cu = fminf(1.f, fmaxf(0.f, uk));
+    float g = 0.f;
+    for (int w = 0; w < c.W; ++w) g += parts.th[((size_t)w * c.M + k) * N + i];
+    g += c.c_lim * (cu - uk) / width;
+    finite = isfinite(g);
+    grad[(size_t)k * N + i] = g;
   } else {
     const int w = y;
     const int S = c.S;
@@ -155,7 +159,9 @@ __global__ void __launch_bounds__(256) window_reduce_kernel(const ChainParams c,
 
 cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
                                  float* grad, int32_t* status, cudaStream_t st) {
-  dim3 grid((N + 255) / 256, grad ? c.W * c.R : 1);
+  // one trajectory, unconstrained: the theta rows get their own block rows
+  const int rows = !grad ? 1 : (c.R > 1 ? c.W * c.R : (c.csvgd ? c.W : c.W + c.M));
+  dim3 grid((N + 255) / 256, rows);
   window_reduce_kernel<<<grid, 256, 0, st>>>(c, X, N, parts, logp, grad, status);
   return cudaGetLastError();
 }

@@ -73,8 +73,9 @@ __global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* _
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < N) {
+    // all loads issued together: accumulate without short-circuiting
     bool live = true;
-    for (int k = 0; k < M; ++k) live = live && isfinite(u[(size_t)k * N + i]) && isfinite(gu[(size_t)k * N + i]);
+    for (int k = 0; k < M; ++k) live &= isfinite(u[(size_t)k * N + i]) & isfinite(gu[(size_t)k * N + i]);
     if (live) atomicAdd(&blk, 1u);
     else
       for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
