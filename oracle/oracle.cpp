@@ -1210,6 +1210,63 @@ int orc_csvgd_step(int N, int M, int Pc, int n_def, const double* lo, const doub
   return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Stochastic gradient Langevin dynamics with the multiple-shooting likelihood
+// (the second estimator of Sec. V-B's multiple-shooting comparison; Welling
+// and Teh 2011): every particle is an independent chain on the augmented
+// vector,
+//   u     <- u + (eps_t / 2) g_u + sqrt(eps_t) xi      (theta in unit-box u)
+//   s^s   <- s^s + (eps_t / 2) g_s + sqrt(eps_t) xi
+//   eps_t = a (b + t)^(-gamma),  t = 1, 2, ...
+// xi ~ N(0, 1) per (step, row, particle) from a counter-based generator:
+// SplitMix64 (Steele, Lea and Flood 2014) from `seed`, outputs 2k+1 and 2k+2
+// for k = (t-1) P N + r N + i, turned into one normal by Box-Muller
+// (u1 in (0, 1], u2 in [0, 1): sqrt(-2 ln u1) cos(2 pi u2)).
+// ---------------------------------------------------------------------------
+static uint64_t splitmix64_output(uint64_t seed, uint64_t index /* 1-based */) {
+  uint64_t z = seed + index * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static double langevin_normal(uint64_t seed, uint64_t k) {
+  const uint64_t z1 = splitmix64_output(seed, 2 * k + 1), z2 = splitmix64_output(seed, 2 * k + 2);
+  const double u1 = (double)((z1 >> 11) + 1) * 0x1.0p-53;
+  const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
+}
+
+// The generator's normal for (seed, k), and its underlying SplitMix64 output.
+double orc_langevin_normal(uint64_t seed, uint64_t k) { return langevin_normal(seed, k); }
+uint64_t orc_splitmix64(uint64_t seed, uint64_t index) { return splitmix64_output(seed, index); }
+
+// One SGLD step of N particles [N][P] (theta rows first, M of them) with
+// gradient grad [N][P]; t is the step count, incremented first.
+int orc_sgld_step(int N, int M, int P, const double* lo, const double* hi, double* particles, const double* grad,
+                  int* t, double a, double b, double gamma, uint64_t seed, int clamp) {
+  *t += 1;
+  const double eps = a * std::pow(b + *t, -gamma);
+  const double sq = std::sqrt(eps);
+  for (int i = 0; i < N; ++i)
+    for (int r = 0; r < P; ++r) {
+      const uint64_t k = ((uint64_t)(*t - 1) * P + r) * (uint64_t)N + i;
+      const double xi = langevin_normal(seed, k);
+      double& x = particles[(size_t)i * P + r];
+      const double g = grad[(size_t)i * P + r];
+      if (r < M) {
+        const double w = hi[r] - lo[r];
+        double u = (x - lo[r]) / w;
+        u += 0.5 * eps * g * w + sq * xi;
+        if (clamp) u = std::min(1.0, std::max(0.0, u));
+        x = lo[r] + u * w;
+      } else {
+        x += 0.5 * eps * g + sq * xi;
+      }
+    }
+  return 0;
+}
+
 // ---- arm + box -------------------------------------------------------------
 // Spatial velocity and acceleration (minus gravity) of the box pivot at t.
 int orc_armbox_pivot(const ArmBox* A, double t, double* v6, double* a6) {

@@ -132,6 +132,13 @@ def lib():
             L.orc_csvgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
                                          _dp, _dp, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double, ctypes.c_double, _dp, _dp]
+            L.orc_langevin_normal.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.orc_langevin_normal.restype = ctypes.c_double
+            L.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+            L.orc_splitmix64.restype = ctypes.c_uint64
+            L.orc_sgld_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_uint64, ctypes.c_int]
             L.orc_armbox_pivot.argtypes = [ctypes.POINTER(_ArmBox), ctypes.c_double, _dp, _dp]
             L.orc_armbox_qdd.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, _dp, _dp]
             L.orc_armbox_inertia.argtypes = [ctypes.POINTER(_ArmBox), _dp, _dp]
@@ -296,6 +303,36 @@ def max_threads() -> int:
 # --------------------------------------------------------------------------
 # SVGD
 # --------------------------------------------------------------------------
+def splitmix64(seed: int, index: int) -> int:
+    """Output `index` (1-based) of the SplitMix64 sequence from `seed`."""
+    return lib().orc_splitmix64(int(seed), int(index))
+
+
+def langevin_normal(seed: int, k: int) -> float:
+    """The SGLD noise generator's standard normal number k for `seed`."""
+    return lib().orc_langevin_normal(int(seed), int(k))
+
+
+class SgldState:
+    """Step count of the oracle's SGLD chains (one chain per particle)."""
+
+    def __init__(self, N, P, lo, hi, a=1e-4, b=1.0, gamma=0.55, seed=0, clamp=True):
+        self.N, self.P = N, P
+        self.M = len(lo)
+        self.lo = np.ascontiguousarray(lo, dtype=np.float64)
+        self.hi = np.ascontiguousarray(hi, dtype=np.float64)
+        self.t = ctypes.c_int(0)
+        self.a, self.b, self.gamma, self.seed, self.clamp = a, b, gamma, seed, clamp
+
+    def step(self, particles, grad):
+        """In-place SGLD update of particles [N][P] with gradient [N][P]."""
+        assert particles.dtype == np.float64 and particles.flags.c_contiguous
+        g, gp = _d(grad)
+        lib().orc_sgld_step(self.N, self.M, self.P, self.lo.ctypes.data_as(_dp), self.hi.ctypes.data_as(_dp),
+                            particles.ctypes.data_as(_dp), gp, ctypes.byref(self.t), float(self.a), float(self.b),
+                            float(self.gamma), int(self.seed), int(self.clamp))
+
+
 class CsvgdState:
     """Adam moments and step count of the oracle's constrained SVGD update
     (Algorithm 1): particles [N][Pc] with Pc = M + n_shoot + n_def + M."""
