@@ -337,6 +337,8 @@ def run_pds(args):
         extra["serving"]["other_rates"] = [run_serving(api, dev, stream, rate=r, brief=True) for r in (5.0, 200.0)]
     if rank == 0 and world == 1 and not args.no_csvgd:
         extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
+    if rank == 0 and world == 1 and not args.no_sgld:
+        extra["sgld"] = run_sgld(api, dev, stream, wl, obs, x0, flush)
     if rank == 0 and world == 1 and not args.no_trajset:
         extra["trajectory_set"] = run_trajset(api, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_metrics:
@@ -480,6 +482,54 @@ def run_csvgd(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
             "nonfinite_particles_after": nonfinite}
 
 
+def run_sgld(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
+    """SGLD chains (the other estimator of Sec. V-B) on the multiple-shooting
+    likelihood of the benchmark workload: per iteration log p + gradient of
+    every particle, then one Langevin step of every chain."""
+    import torch
+    N, P = wl.N, wl.P
+    prob = api.Problem.from_workload(wl, obs, stream=stream, checkpoint_stride=K_CKPT, fast_math=FAST_MATH)
+    prob.reserve(N)
+    sg = api.Sgld(N, wl.M, P, wl.lo, wl.hi, a=1e-7, b=1.0, gamma=0.55, seed=2021, stream=stream)
+    X = torch.from_numpy(np.ascontiguousarray(x0.T, dtype=np.float32)).to(dev)
+    logp = torch.empty(N, device=dev)
+    G = torch.empty((P, N), device=dev)
+    L = api.lib()
+
+    def lg():
+        api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), None), "sgld loglik")
+
+    def up():
+        api._check(L.pds_sgld_step(sg.handle, api._ptr(X), api._ptr(G), None), "sgld step")
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lg()
+            up()
+    stream.synchronize()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(iters)]
+    with torch.cuda.stream(stream):
+        for k in range(iters):
+            flush.zero_()
+            evs[k][0].record(stream)
+            lg()
+            evs[k][1].record(stream)
+            up()
+            evs[k][2].record(stream)
+    stream.synchronize()
+    tot = sum(e[0].elapsed_time(e[2]) for e in evs) / iters
+    lgt = sum(e[0].elapsed_time(e[1]) for e in evs) / iters
+    step_ms = tot - lgt
+    nonfinite = int((~torch.isfinite(X)).any(dim=0).sum().item())
+    sg.close()
+    prob.close()
+    return {"workload": f"SGLD on the chain5 workload, N={N} chains, T={wl.T}, W={wl.W}, K={K_CKPT}, "
+                        f"eps_t = 1e-7 (1 + t)^-0.55",
+            "value": N * wl.T / (tot / 1e3), "unit": UNIT, "ms_per_iter": tot, "loglik_grad_ms": lgt,
+            "sgld_step_ms": step_ms, "sgld_step_gbs": 12.0 * P * N / (step_ms / 1e3) / 1e9, "iters": iters,
+            "nonfinite_chains_after": nonfinite}
+
+
 def run_trajset(api, dev, stream, flush, N=8192, R=2, iters=10, warmup=3):
     """Likelihood of a set of R trajectories (Sec. IV-C, the equally weighted
     mixture) on the chain5 system: R trajectories from R parameter draws and
@@ -604,6 +654,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-problems measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-csvgd", action="store_true", help="skip the constrained-SVGD measurement")
+    ap.add_argument("--no-sgld", action="store_true", help="skip the SGLD measurement")
     ap.add_argument("--no-trajset", action="store_true", help="skip the trajectory-set measurement")
     ap.add_argument("--no-metrics", action="store_true", help="skip the posterior-metric timing")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")

@@ -97,6 +97,7 @@ typedef struct pds_armbox_desc {
 
 typedef struct pds_problem* pds_problem_t;
 typedef struct pds_svgd* pds_svgd_t;
+typedef struct pds_sgld* pds_sgld_t;
 
 /* Create a multiple-shooting inference problem (Sec. IV-C).
  *  dt, T      : time step and number of steps of the measured trajectory.
@@ -397,6 +398,31 @@ int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_
  * nothing and returns after queuing its kernels. */
 int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo,
                           const float* theta_hi, float* bandwidth_out, void* cuda_stream);
+
+/* ---- Stochastic gradient Langevin dynamics (Welling and Teh 2011), the
+ * other estimator run with the multiple-shooting likelihood in Sec. V-B.
+ * Each particle is an independent chain; one step moves, in place,
+ *   theta rows r < M:  u = (theta - lo) / (hi - lo),
+ *                      u += (eps_t / 2) (hi - lo) g + sqrt(eps_t) xi,
+ *                      clipped to [0, 1] if clamp, theta = lo + u (hi - lo);
+ *   rows r >= M:       x += (eps_t / 2) g + sqrt(eps_t) xi;
+ * with g = d log p / d particles, eps_t = a (b + t)^(-gamma) for the step
+ * count t = 1, 2, ... (incremented by every step, zeroed by reset), and
+ * xi ~ N(0, 1) from a counter-based generator: SplitMix64 from `seed`,
+ * outputs 2k + 1 and 2k + 2 with k = (t - 1) P N + r N + i, combined by the
+ * Box-Muller transform with u1 = (z1 >> 11 + 1) 2^-53, u2 = (z2 >> 11) 2^-53
+ * (computed in fp32).  The draws depend on (seed, t, r, i) only.
+ *  pds_sgld_create: 1 <= N <= 65536, 0 <= M <= 16, M <= P <= 65535,
+ *    theta_lo/hi host [M] (may be NULL when M = 0), a > 0, gamma >= 0,
+ *    b > -1; allocates nothing on the device.
+ *  pds_sgld_step: particles device [P][N] float (read and written), grad
+ *    device [P][N] float; eps_out host float or NULL (receives eps_t).
+ *    One kernel launch queued on the state's stream. */
+int pds_sgld_create(int N, int M, int P, const float* theta_lo, const float* theta_hi, double a, double b,
+                    double gamma, unsigned long long seed, int clamp, void* cuda_stream, pds_sgld_t* out);
+int pds_sgld_destroy(pds_sgld_t s);
+int pds_sgld_reset(pds_sgld_t s);
+int pds_sgld_step(pds_sgld_t s, float* particles, const float* grad, float* eps_out);
 
 /* ---- Posterior metrics (Sec. IV: Eq. knn-kl and the maximum mean
  * discrepancy).  Sample sets are device arrays [d][n] float (coordinate-

@@ -114,6 +114,11 @@ EXPORTS = {
     "pds_server_result": ([_vp, ctypes.c_longlong, _fp, _fp], ctypes.c_int),
     "pds_server_cancel": ([_vp, ctypes.c_longlong], ctypes.c_int),
     "pds_server_stats": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pds_sgld_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, ctypes.c_double,
+                         ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_sgld_destroy": ([_vp], ctypes.c_int),
+    "pds_sgld_reset": ([_vp], ctypes.c_int),
+    "pds_sgld_step": ([_vp, _vp, _vp, _fp], ctypes.c_int),
     "pds_bandwidth_noalloc": ([_vp, ctypes.c_int, ctypes.c_int, _fp, _fp, _vp, _vp], ctypes.c_int),
     "pds_last_launch_count": ([], ctypes.c_int),
     "pds_strerror": ([ctypes.c_int], ctypes.c_char_p),
@@ -395,6 +400,52 @@ class Svgd:
         phi = torch.empty((self.M, self.N), device=particles.device, dtype=torch.float32) if return_phi else None
         _check(lib().pds_svgd_step(self._h, _ptr(particles), _ptr(grad), _ptr(bw), _ptr(phi)), "pds_svgd_step")
         return bw, phi
+
+
+class Sgld:
+    """Stochastic gradient Langevin dynamics chains (pds_sgld_create): one
+    independent chain per particle, step size a (b + t)^(-gamma), theta rows
+    moved in unit-box coordinates."""
+
+    def __init__(self, N, M, P, lo, hi, a=1e-4, b=1.0, gamma=0.55, seed=0, clamp=True, stream=None):
+        L = lib()
+        lo = np.ascontiguousarray(lo, dtype=np.float32).reshape(-1)
+        hi = np.ascontiguousarray(hi, dtype=np.float32).reshape(-1)
+        assert lo.size == M and hi.size == M
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_sgld_create(int(N), int(M), int(P), lo.ctypes.data_as(_fp), hi.ctypes.data_as(_fp), float(a),
+                                 float(b), float(gamma), int(seed) & (2 ** 64 - 1), int(bool(clamp)), self._stream_h,
+                                 ctypes.byref(h)), "pds_sgld_create")
+        self._h = h
+        self.N, self.M, self.P = int(N), int(M), int(P)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.pds_sgld_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        _check(lib().pds_sgld_reset(self._h), "pds_sgld_reset")
+
+    def step(self, particles: torch.Tensor, grad: torch.Tensor) -> float:
+        """In-place update of particles [P][N] with gradient [P][N]; returns eps_t."""
+        _need_cuda(particles, torch.float32, "particles")
+        _need_cuda(grad, torch.float32, "grad")
+        assert tuple(particles.shape) == (self.P, self.N) and tuple(grad.shape) == (self.P, self.N)
+        eps = ctypes.c_float()
+        _check(lib().pds_sgld_step(self._h, _ptr(particles), _ptr(grad), ctypes.byref(eps)), "pds_sgld_step")
+        return eps.value
 
 
 def knn_kl(p: torch.Tensor, q: torch.Tensor, k: int = 3, stream=None) -> float:
