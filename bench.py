@@ -335,6 +335,7 @@ def run_pds(args):
     if rank == 0 and world == 1 and not args.no_serving:
         extra["serving"] = run_serving(api, dev, stream)
         extra["serving"]["other_rates"] = [run_serving(api, dev, stream, rate=r, brief=True) for r in (5.0, 200.0)]
+        extra["serving"]["gated"] = run_serving(api, dev, stream, gate=True)
     if rank == 0 and world == 1 and not args.no_csvgd:
         extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
     if rank == 0 and world == 1 and not args.no_sgld:
@@ -495,6 +496,15 @@ def run_sgld(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
     logp = torch.empty(N, device=dev)
     G = torch.empty((P, N), device=dev)
     L = api.lib()
+    # theta rows from the Sobol sequence over the box (App. A-A), on the device
+    api.sobol_box(X[:wl.M], wl.lo, wl.hi, stream=stream)  # first launch loads the module
+    sob = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(2)) for _ in range(5)]
+    for e0, e1 in sob:
+        e0.record(stream)
+        api.sobol_box(X[:wl.M], wl.lo, wl.hi, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    sobol_us = 1e3 * sum(e0.elapsed_time(e1) for e0, e1 in sob) / len(sob)
 
     def lg():
         api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), None), "sgld loglik")
@@ -524,9 +534,10 @@ def run_sgld(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
     sg.close()
     prob.close()
     return {"workload": f"SGLD on the chain5 workload, N={N} chains, T={wl.T}, W={wl.W}, K={K_CKPT}, "
-                        f"eps_t = 1e-7 (1 + t)^-0.55",
+                        f"eps_t = 1e-7 (1 + t)^-0.55; theta initialised from the Sobol sequence over the box",
             "value": N * wl.T / (tot / 1e3), "unit": UNIT, "ms_per_iter": tot, "loglik_grad_ms": lgt,
             "sgld_step_ms": step_ms, "sgld_step_gbs": 12.0 * P * N / (step_ms / 1e3) / 1e9, "iters": iters,
+            "sobol_init_us": sobol_us,
             "nonfinite_chains_after": nonfinite}
 
 
@@ -610,7 +621,7 @@ def run_metrics(api, dev, X, wl, reps=5):
     return out
 
 
-def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False):
+def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, gate=False):
     """Poisson arrivals of jobs from the uneven-problem distribution, each
     run to `iters` SVGD iterations: continuous batching against one job at a
     time with plain launches."""
@@ -627,6 +638,20 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False):
     lat_p, _, wall_p = serve.run_plain(jobs, arrivals, checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH),
                                        stream=stream)
     n_arm = sum(1 for w in wls if hasattr(w, "arm_len"))
+    if gate:
+        # the convergence gate: MMD^2 between theta snapshots 10 iterations
+        # apart (unit-box coordinates, bandwidth 1/6 per coordinate) at or
+        # below 0 retires a job before its iteration cap
+        used = []
+        lat_g, _, wall_g = serve.run_server(jobs, arrivals, mem_budget=64 << 30, stream=stream,
+                                            checkpoint_stride=K_CKPT, fast_math=bool(FAST_MATH),
+                                            gate=(1, 10, 0.0, 1.0 / 6.0), iters_out=used)
+        units_g = sum(w.N * w.T * k for w, k in zip(wls, used))
+        return {"gate": "MMD^2 (unbiased, RBF, bandwidth M/6 in unit-box coordinates) between theta snapshots "
+                        "10 iterations apart <= 0", "rate_per_s": rate,
+                "served": {**serve.percentiles(lat_g), "value": units_g / wall_g, "wall_s": wall_g},
+                "iterations_mean": float(np.mean(used)), "iterations_min": int(np.min(used)),
+                "jobs_at_cap": int(sum(1 for k in used if k >= iters))}
     if brief:
         return {"rate_per_s": rate, "served": {**serve.percentiles(lat_s), "value": units / wall_s},
                 "plain_sequential": {**serve.percentiles(lat_p), "value": units / wall_p}}

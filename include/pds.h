@@ -375,6 +375,29 @@ int pds_server_result(pds_server_t s, long long job_id, float* particles, float*
 int pds_server_cancel(pds_server_t s, long long job_id);
 int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_use);
 
+/* Convergence gate of the server: the posterior metrics of Sec. IV used to
+ * decide when a job has reached its posterior.  With metric != PDS_GATE_NONE,
+ * every `every` iterations of a job the server snapshots its theta particles
+ * in unit-box coordinates u = (theta - lo) / (hi - lo) and, from the second
+ * snapshot on, evaluates between the new snapshot (n live particles) and the
+ * previous one (m live particles):
+ *   PDS_GATE_MMD2:   the unbiased MMD^2 with kernel exp(-||u - u'||^2 / (h M))
+ *                    (as pds_mmd2 with bandwidth h M: h per coordinate);
+ *   PDS_GATE_KNN_KL: the KNN estimate of KL(new || previous) with k = 3 (as
+ *                    pds_knn_kl); terms of coincident points are left out.
+ * Particles with a coordinate that is not finite take no part.  When the
+ * value is <= threshold the job retires at once (its iterations_done is then
+ * below its cap); otherwise it runs on to its iteration count.  Set the gate
+ * before submitting jobs (PDS_ERR_ARG otherwise); h is used by MMD^2 only
+ * (> 0).  pds_server_job_gate reports the number of metric evaluations and
+ * the last value (NaN before the first) of a job that is queued, active or
+ * done and not yet collected. */
+#define PDS_GATE_NONE 0
+#define PDS_GATE_MMD2 1
+#define PDS_GATE_KNN_KL 2
+int pds_server_set_gate(pds_server_t s, int metric, int every, double threshold, double h);
+int pds_server_job_gate(pds_server_t s, long long job_id, int* checks, double* last_value);
+
 /* Median-heuristic bandwidth of N particles without allocating any device
  * memory.  The paper has no counterpart: this entry point exists for callers
  * that cannot call cudaMalloc -- for example code running inside another
@@ -398,6 +421,19 @@ int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_
  * nothing and returns after queuing its kernels. */
 int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo,
                           const float* theta_hi, float* bandwidth_out, void* cuda_stream);
+
+/* ---- Sobol initialisation (App. A-A: particles start from the
+ * deterministic Sobol sequence over the parameter limits).
+ * Writes theta device [M][N] float (e.g. the first M rows of a particle
+ * array): theta[k][i] = lo_k + x_k(skip + i) (hi_k - lo_k), x(n) the n-th
+ * point of the unscrambled Sobol sequence in Gray-code order (point 0 is the
+ * origin), with the direction numbers of Joe and Kuo (2008) for dimensions
+ * 1..16.  x has at most 24 significant bits for indices below 2^24, so it is
+ * exact in fp32.  1 <= N <= 2^24, 1 <= M <= 16, 0 <= skip and
+ * skip + N <= 2^32; theta_lo/hi host [M] with hi > lo.  One kernel launch
+ * queued on cuda_stream. */
+int pds_sobol_box(float* theta, int N, int M, const float* theta_lo, const float* theta_hi, long long skip,
+                  void* cuda_stream);
 
 /* ---- Stochastic gradient Langevin dynamics (Welling and Teh 2011), the
  * other estimator run with the multiple-shooting likelihood in Sec. V-B.

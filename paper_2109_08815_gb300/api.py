@@ -21,6 +21,7 @@ PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
 OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES, OPT_MEDIAN_CUDA_CORES = 1, 2, 3, 4, 5
 COMBINE_SUM, COMBINE_PRODUCT = 0, 1
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
+GATE_NONE, GATE_MMD2, GATE_KNN_KL = 0, 1, 2
 
 _lib = None
 _lock = threading.Lock()
@@ -113,7 +114,10 @@ EXPORTS = {
     "pds_server_status": ([_vp, ctypes.c_longlong, _ip, _ip], ctypes.c_int),
     "pds_server_result": ([_vp, ctypes.c_longlong, _fp, _fp], ctypes.c_int),
     "pds_server_cancel": ([_vp, ctypes.c_longlong], ctypes.c_int),
+    "pds_server_set_gate": ([_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "pds_server_job_gate": ([_vp, ctypes.c_longlong, _ip, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "pds_server_stats": ([_vp, _ip, _ip, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "pds_sobol_box": ([_vp, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_longlong, _vp], ctypes.c_int),
     "pds_sgld_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, ctypes.c_double,
                          ctypes.c_double, ctypes.c_ulonglong, ctypes.c_int, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "pds_sgld_destroy": ([_vp], ctypes.c_int),
@@ -402,6 +406,22 @@ class Svgd:
         return bw, phi
 
 
+def sobol_box(theta: torch.Tensor, lo, hi, skip: int = 0, stream=None) -> torch.Tensor:
+    """Fill theta [M][N] (a contiguous CUDA float32 tensor, e.g. the first M
+    rows of a particle array) with Sobol points scaled to the box
+    (pds_sobol_box); returns theta."""
+    _need_cuda(theta, torch.float32, "theta")
+    assert theta.dim() == 2
+    M, N = theta.shape
+    lo = np.ascontiguousarray(lo, dtype=np.float32).reshape(-1)
+    hi = np.ascontiguousarray(hi, dtype=np.float32).reshape(-1)
+    assert lo.size == M and hi.size == M
+    h, _ = _stream_handle(stream)
+    _check(lib().pds_sobol_box(_ptr(theta), int(N), int(M), lo.ctypes.data_as(_fp), hi.ctypes.data_as(_fp),
+                               int(skip), h), "pds_sobol_box")
+    return theta
+
+
 class Sgld:
     """Stochastic gradient Langevin dynamics chains (pds_sgld_create): one
     independent chain per particle, step size a (b + t)^(-gamma), theta rows
@@ -631,6 +651,19 @@ class Server:
     def cancel(self, job_id):
         _check(lib().pds_server_cancel(self._h, ctypes.c_longlong(job_id)), "pds_server_cancel")
         self._shapes.pop(job_id, None)
+
+    def set_gate(self, metric: int, every: int, threshold: float, h: float = 0.1):
+        """Convergence gate (pds_server_set_gate): retire a job once the metric
+        between successive theta snapshots is <= threshold."""
+        _check(lib().pds_server_set_gate(self._h, int(metric), int(every), float(threshold), float(h)),
+               "pds_server_set_gate")
+
+    def gate(self, job_id):
+        """(number of gate evaluations, last value) of a job."""
+        c, v = ctypes.c_int(), ctypes.c_double()
+        _check(lib().pds_server_job_gate(self._h, ctypes.c_longlong(job_id), ctypes.byref(c), ctypes.byref(v)),
+               "pds_server_job_gate")
+        return c.value, v.value
 
     def stats(self):
         q, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
