@@ -278,6 +278,10 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       delete b;
       return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs the unconstrained one-trajectory method only");
     }
+    if (p->kind != PDS_SYSTEM_PLANAR_CHAIN && p->kind != PDS_SYSTEM_ARM_BOX) {
+      delete b;
+      return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs planar chains and the arm-and-box system");
+    }
     b->probs.push_back(p);
     b->svgds.push_back(s);
     b->X.push_back(particles[j]);

@@ -70,12 +70,16 @@ __global__ void __launch_bounds__(kMetTile) knn_kernel(const float* __restrict__
   }
 }
 
-// sum_i log(nu_i / rho_i) into acc[0] (double).
+// sum_i log(nu_i / rho_i) into acc[0] (double); with skip_nonfinite, terms
+// that are not finite (a query point that is not finite, or a distance 0)
+// are left out.
 __global__ void __launch_bounds__(256) knn_log_ratio_kernel(const float* __restrict__ nu, const float* __restrict__ rho,
-                                                            int n, double* __restrict__ acc) {
+                                                            int n, double* __restrict__ acc, int skip_nonfinite = 0) {
   __shared__ double part[256];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  part[threadIdx.x] = i < n ? log((double)nu[i]) - log((double)rho[i]) : 0.0;
+  double v = i < n ? log((double)nu[i]) - log((double)rho[i]) : 0.0;
+  if (skip_nonfinite && !isfinite(v)) v = 0.0;
+  part[threadIdx.x] = v;
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
     if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
@@ -86,7 +90,7 @@ __global__ void __launch_bounds__(256) knn_log_ratio_kernel(const float* __restr
 
 // sum over pairs (i in A, j in B; i != j when A and B are the same set) of
 // exp(-||a_i - b_j||^2 / h) into acc[0] (double).
-template <int DM>
+template <int DM, bool SKIP_NONFINITE = false>
 __global__ void __launch_bounds__(kMetTile) rbf_sum_kernel(const float* __restrict__ A, int n, const float* __restrict__ B,
                                                            int m, int d, float inv_h, int same,
                                                            double* __restrict__ acc) {
@@ -111,7 +115,7 @@ __global__ void __launch_bounds__(kMetTile) rbf_sum_kernel(const float* __restri
         const float e = x[c] - tile[c][jj];
         s = fmaf(e, e, s);
       }
-      const bool skip = same && (j0 + jj == i);
+      const bool skip = (same && (j0 + jj == i)) || (SKIP_NONFINITE && !(s <= INFINITY));
       s_tile += skip ? 0.f : expf(-s * inv_h);
     }
     s_all += (double)s_tile;
@@ -140,18 +144,43 @@ static cudaError_t knn(const float* q, int n, const float* r, int m, int d, int 
   return launch_knn<64>(q, n, r, m, d, k, self, out, st);
 }
 
-template <int DM>
+template <int DM, bool SKIP>
 static cudaError_t launch_rbf(const float* a, int n, const float* b, int m, int d, float inv_h, int same, double* acc,
                               cudaStream_t st) {
-  rbf_sum_kernel<DM><<<(n + kMetTile - 1) / kMetTile, kMetTile, 0, st>>>(a, n, b, m, d, inv_h, same, acc);
+  rbf_sum_kernel<DM, SKIP><<<(n + kMetTile - 1) / kMetTile, kMetTile, 0, st>>>(a, n, b, m, d, inv_h, same, acc);
   return cudaGetLastError();
 }
 
+template <bool SKIP = false>
 static cudaError_t rbf(const float* a, int n, const float* b, int m, int d, float inv_h, int same, double* acc,
                        cudaStream_t st) {
-  if (d <= 4) return launch_rbf<4>(a, n, b, m, d, inv_h, same, acc, st);
-  if (d <= 16) return launch_rbf<16>(a, n, b, m, d, inv_h, same, acc, st);
-  return launch_rbf<64>(a, n, b, m, d, inv_h, same, acc, st);
+  if (d <= 4) return launch_rbf<4, SKIP>(a, n, b, m, d, inv_h, same, acc, st);
+  if (d <= 16) return launch_rbf<16, SKIP>(a, n, b, m, d, inv_h, same, acc, st);
+  return launch_rbf<64, SKIP>(a, n, b, m, d, inv_h, same, acc, st);
+}
+
+// Asynchronous parts of the metrics for callers inside the library (the
+// server's convergence gate), on sets whose points that are not finite
+// take no part: acc3 receives the three kernel sums of MMD^2 (xx without
+// the diagonal, yy without the diagonal, xy), acc1 the sum of the KNN log
+// ratios; the caller divides by the live counts.
+cudaError_t mmd2_sums_async(const float* x, int n, const float* y, int m, int d, float inv_h, double* acc3,
+                            cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(acc3, 0, 3 * sizeof(double), st)) != cudaSuccess) return e;
+  if ((e = rbf<true>(x, n, x, n, d, inv_h, 1, acc3, st)) != cudaSuccess) return e;
+  if ((e = rbf<true>(y, m, y, m, d, inv_h, 1, acc3 + 1, st)) != cudaSuccess) return e;
+  return rbf<true>(x, n, y, m, d, inv_h, 0, acc3 + 2, st);
+}
+
+cudaError_t knn_log_ratio_async(const float* p, int n, const float* q, int m, int d, int k, float* scratch2n,
+                                double* acc1, cudaStream_t st) {
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(acc1, 0, sizeof(double), st)) != cudaSuccess) return e;
+  if ((e = knn(p, n, q, m, d, k, 0, scratch2n, st)) != cudaSuccess) return e;
+  if ((e = knn(p, n, p, n, d, k, 1, scratch2n + n, st)) != cudaSuccess) return e;
+  knn_log_ratio_kernel<<<(n + 255) / 256, 256, 0, st>>>(scratch2n, scratch2n + n, n, acc1, 1);
+  return cudaGetLastError();
 }
 
 }  // namespace pds

@@ -46,6 +46,15 @@ struct ArmBoxParams {
   const float* base;  // device [T][9]: pivot omega, alpha, (a - g), pivot coordinates
 };
 
+// Rigid double pendulum (kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM; ChainParams
+// then has n = 2, S = 4 and M = the number of estimated parameters).
+constexpr int kRigid2Params = 11;
+struct Rigid2Params {
+  float p[kRigid2Params];          // nominal values [m1, I1, c1x, c1y, b1, l, m2, I2, c2x, c2y, b2]
+  int theta_row[kRigid2Params];    // particle row of each parameter, or -1 (fixed)
+  int theta_param[kRigid2Params];  // parameter of each theta row (first M entries)
+};
+
 // Per-window partial results written by the rollout kernel, reduced over
 // windows by the window-reduction kernel.  All [row][N] slabs.
 struct Partials {
@@ -148,6 +157,10 @@ cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cuda
 int phi_tc_slots(int N);
 int svgd_phi_partials(int N);
 cudaError_t svgd_setup_device();
+cudaError_t mmd2_sums_async(const float* x, int n, const float* y, int m, int d, float inv_h, double* acc3,
+                            cudaStream_t st);
+cudaError_t knn_log_ratio_async(const float* p, int n, const float* q, int m, int d, int k, float* scratch2n,
+                                double* acc1, cudaStream_t st);
 
 // Record an error message for pds_last_error() and return `code`.
 int set_error(int code, const char* msg);
@@ -160,6 +173,7 @@ struct pds_problem {
   int kind = PDS_SYSTEM_PLANAR_CHAIN;
   pds::ChainParams c;
   pds::ArmBoxParams ab{};
+  pds::Rigid2Params r2{};
   float* d_base = nullptr;  // arm-and-box pivot motion table
   cudaStream_t stream;
   float* d_obs = nullptr;

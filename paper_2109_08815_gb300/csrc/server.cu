@@ -8,7 +8,17 @@
 // their iteration count: their particles and last log p are copied to the
 // host and their device memory is released, so waiting jobs can enter on the
 // next tick.  Every job's state stays resident on the device between ticks.
+//
+// Convergence gate (optional, pds_server_set_gate): every `every` iterations
+// the server takes a snapshot of each active job's theta particles in
+// unit-box coordinates and evaluates a posterior metric (Sec. IV: the
+// unbiased RBF MMD^2, or the KNN-KL estimate with k = 3) between this
+// snapshot and the previous one, over the particles that are finite (the
+// MMD kernel's bandwidth is h per coordinate, h M in all).  A job
+// whose metric is at or below the threshold has reached its posterior and
+// retires before its iteration cap.
 #include <cuda_runtime.h>
+#include <math.h>
 #include <string.h>
 
 #include <deque>
@@ -40,9 +50,37 @@ struct Job {
   pds_svgd_t svgd = nullptr;
   float* d_x = nullptr;
   float* d_logp = nullptr;
+  // convergence gate: unit-box snapshots [M][N] (now, previous), KNN
+  // scratch [2N], sums and live counts
+  float* d_u[2] = {nullptr, nullptr};
+  float* d_gscr = nullptr;
+  double* d_acc = nullptr;  // [0..2] metric sums, [3..4] live counts
+  double h_acc[5] = {0, 0, 0, 0, 0};
+  int u_cur = 0, snapshots = 0, gate_checks = 0;
+  bool gate_pending = false;
+  double gate_value = NAN;
   // results
   std::vector<float> x_out, logp_out;
 };
+
+struct GateUnit {
+  float lo[PDS_MAX_THETA], inv_w[PDS_MAX_THETA];
+};
+
+// u[k][i] = (theta[k][i] - lo_k) / (hi_k - lo_k); a particle with a
+// coordinate that is not finite gets NaN in every row and is not counted.
+__global__ void __launch_bounds__(256) gate_unit_kernel(const float* __restrict__ x, int N, int M, GateUnit g,
+                                                        float* __restrict__ u, double* __restrict__ live) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool ok = false;
+  if (i < N) {
+    ok = true;
+    for (int k = 0; k < M; ++k) ok &= isfinite(x[(size_t)k * N + i]);
+    for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = ok ? (x[(size_t)k * N + i] - g.lo[k]) * g.inv_w[k] : NAN;
+  }
+  const unsigned b = __ballot_sync(0xffffffffu, ok);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(live, (double)__popc(b));
+}
 
 }  // namespace
 
@@ -57,6 +95,8 @@ struct pds_server {
   std::map<long long, Job> jobs;
   pds_batch_t batch = nullptr;
   bool batch_dirty = true;
+  int gate_metric = PDS_GATE_NONE, gate_every = 0;
+  double gate_threshold = 0.0, gate_h = 0.1;
 };
 
 // Device bytes a job holds while active (problem workspace and buffers,
@@ -79,6 +119,7 @@ static size_t job_bytes(int n, int M, int T, int W, int D, int N, int K) {
   if (N >= 256) b += phi_tc_floats(N, M) * 4;
   if (N >= 2048) b += median_tc_floats(N, M) * 4 + (size_t)median_tc_work_items(N, nullptr) * 2 * sizeof(int);
   b += P * N * 4 + (size_t)N * 4;                           // particles, log p
+  b += (2 * (size_t)M * N + 2 * (size_t)N) * 4 + 5 * 8;     // convergence-gate snapshots and scratch
   return b + (64u << 10);
 }
 
@@ -87,10 +128,61 @@ static void release(Job& j) {
   if (j.svgd) pds_svgd_destroy(j.svgd);
   cudaFree(j.d_x);
   cudaFree(j.d_logp);
+  cudaFree(j.d_u[0]);
+  cudaFree(j.d_u[1]);
+  cudaFree(j.d_gscr);
+  cudaFree(j.d_acc);
   j.prob = nullptr;
   j.svgd = nullptr;
   j.d_x = nullptr;
   j.d_logp = nullptr;
+  j.d_u[0] = j.d_u[1] = nullptr;
+  j.d_gscr = nullptr;
+  j.d_acc = nullptr;
+}
+
+static int job_theta_count(const Job& j) { return j.kind == PDS_SYSTEM_ARM_BOX ? 4 : j.sys.n_theta; }
+
+// Queue the gate's snapshot and, from the second snapshot on, its metric.
+static cudaError_t gate_enqueue(pds_server* s, Job& j) {
+  const int M = job_theta_count(j), N = j.N;
+  GateUnit g;
+  for (int k = 0; k < M; ++k) {
+    g.lo[k] = j.lo[k];
+    g.inv_w[k] = 1.0f / (j.hi[k] - j.lo[k]);
+  }
+  float* now = j.d_u[j.u_cur];
+  float* prev = j.d_u[j.u_cur ^ 1];
+  double* live_now = j.d_acc + 3 + j.u_cur;
+  cudaError_t e = cudaMemsetAsync(live_now, 0, sizeof(double), s->stream);
+  if (e != cudaSuccess) return e;
+  gate_unit_kernel<<<(N + 255) / 256, 256, 0, s->stream>>>(j.d_x, N, M, g, now, live_now);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (j.snapshots > 0) {
+    if (s->gate_metric == PDS_GATE_MMD2)
+      e = mmd2_sums_async(now, N, prev, N, M, (float)(1.0 / (s->gate_h * M)), j.d_acc, s->stream);
+    else
+      e = knn_log_ratio_async(now, N, prev, N, M, 3, j.d_gscr, j.d_acc, s->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(j.h_acc, j.d_acc, 5 * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return e;
+    j.gate_pending = true;
+  }
+  ++j.snapshots;
+  j.u_cur ^= 1;
+  return cudaSuccess;
+}
+
+// Metric of the last queued check, after the stream has synchronised.
+static double gate_value(const pds_server* s, const Job& j) {
+  const double n_now = j.h_acc[3 + (j.u_cur ^ 1)], n_prev = j.h_acc[3 + j.u_cur];
+  if (s->gate_metric == PDS_GATE_MMD2) {
+    if (n_now < 2 || n_prev < 2) return NAN;
+    return j.h_acc[0] / (n_now * (n_now - 1)) + j.h_acc[1] / (n_prev * (n_prev - 1)) -
+           2.0 * j.h_acc[2] / (n_now * n_prev);
+  }
+  if (n_now < 4 || n_prev < 3) return NAN;
+  return (double)job_theta_count(j) / n_now * j.h_acc[0] + log(n_prev / (n_now - 1));
 }
 
 static int activate(pds_server* s, Job& j) {
@@ -128,6 +220,14 @@ static int activate(pds_server* s, Job& j) {
   }
   e = cudaMemcpyAsync(j.d_x, j.x0.data(), (size_t)j.P * j.N * sizeof(float), cudaMemcpyHostToDevice, s->stream);
   if (e != cudaSuccess) { release(j); return set_error(PDS_ERR_CUDA, "server: particle upload failed"); }
+  const int M_gate = job_theta_count(j);
+  if ((e = cudaMalloc(&j.d_u[0], (size_t)M_gate * j.N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&j.d_u[1], (size_t)M_gate * j.N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&j.d_gscr, 2 * (size_t)j.N * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&j.d_acc, 5 * sizeof(double))) != cudaSuccess) {
+    release(j);
+    return set_error(PDS_ERR_OOM, "server: gate allocation failed");
+  }
   rc = pds_problem_reserve(j.prob, j.N);
   if (rc != PDS_OK) { release(j); return rc; }
   j.x0.clear();
@@ -280,9 +380,27 @@ int pds_server_tick(pds_server_t s, int* n_active, int* n_retired) {
     if (rc != PDS_OK) return rc;
     std::vector<long long> still;
     std::vector<long long> finishing;
+    const bool gate = s->gate_metric != PDS_GATE_NONE;
     for (long long id : s->active) {
       Job& j = s->jobs[id];
-      if (++j.done_iters >= j.iterations) finishing.push_back(id);
+      ++j.done_iters;
+      if (gate && j.done_iters % s->gate_every == 0) {
+        cudaError_t ge = gate_enqueue(s, j);
+        if (ge != cudaSuccess) return set_error(PDS_ERR_CUDA, "server: gate launch failed");
+      }
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "server: tick failed");
+    for (long long id : s->active) {
+      Job& j = s->jobs[id];
+      bool converged = false;
+      if (j.gate_pending) {
+        j.gate_pending = false;
+        j.gate_value = gate_value(s, j);
+        ++j.gate_checks;
+        converged = j.gate_value <= s->gate_threshold;
+      }
+      if (converged || j.done_iters >= j.iterations) finishing.push_back(id);
       else still.push_back(id);
     }
     for (long long id : finishing) {
@@ -293,9 +411,9 @@ int pds_server_tick(pds_server_t s, int* n_active, int* n_retired) {
       cudaMemcpyAsync(j.logp_out.data(), j.d_logp, j.logp_out.size() * sizeof(float), cudaMemcpyDeviceToHost,
                       s->stream);
     }
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "server: tick failed");
     if (!finishing.empty()) {
+      e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) return set_error(PDS_ERR_CUDA, "server: result copy failed");
       for (long long id : finishing) {
         Job& j = s->jobs[id];
         release(j);
@@ -358,6 +476,29 @@ int pds_server_cancel(pds_server_t s, long long job_id) {
     return set_error(PDS_ERR_ARG, "job already finished");
   }
   s->jobs.erase(it);
+  return PDS_OK;
+}
+
+int pds_server_set_gate(pds_server_t s, int metric, int every, double threshold, double h) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  if (metric != PDS_GATE_NONE && metric != PDS_GATE_MMD2 && metric != PDS_GATE_KNN_KL)
+    return set_error(PDS_ERR_ARG, "unknown gate metric");
+  if (metric != PDS_GATE_NONE && (every < 1 || !isfinite(threshold) || (metric == PDS_GATE_MMD2 && !(h > 0.0))))
+    return set_error(PDS_ERR_ARG, "gate needs every >= 1, a finite threshold and h > 0 for MMD^2");
+  if (!s->active.empty() || !s->queue.empty()) return set_error(PDS_ERR_ARG, "set the gate before submitting jobs");
+  s->gate_metric = metric;
+  s->gate_every = every;
+  s->gate_threshold = threshold;
+  s->gate_h = h > 0.0 ? h : 0.1;
+  return PDS_OK;
+}
+
+int pds_server_job_gate(pds_server_t s, long long job_id, int* checks, double* last_value) {
+  if (!s) return set_error(PDS_ERR_ARG, "NULL server");
+  auto it = s->jobs.find(job_id);
+  if (it == s->jobs.end()) return set_error(PDS_ERR_ARG, "unknown job");
+  if (checks) *checks = it->second.gate_checks;
+  if (last_value) *last_value = it->second.gate_value;
   return PDS_OK;
 }
 

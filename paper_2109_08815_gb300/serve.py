@@ -20,12 +20,18 @@ def poisson_arrivals(n_jobs: int, rate: float, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
 
 
-def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, fast_math=True, stream=None):
+def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, fast_math=True, stream=None,
+               gate=None, iters_out=None):
     """Continuous batching: submit each job at its arrival time, tick the
-    server until every job is done.  Returns (latencies [s], results, wall)."""
+    server until every job is done.  Returns (latencies [s], results, wall).
+    ``gate`` = (metric, every, threshold, h) sets the server's convergence
+    gate; ``iters_out`` (a list) receives each job's iterations run."""
     srv = api.Server(mem_budget, max_active=max_active, stream=stream, checkpoint_stride=checkpoint_stride,
                      fast_math=fast_math)
+    if gate is not None:
+        srv.set_gate(*gate)
     n = len(jobs)
+    used = [0] * n
     ids = [None] * n
     done_at = [None] * n
     results = [None] * n
@@ -46,7 +52,7 @@ def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, 
         if retired:
             t = time.perf_counter() - t0
             for k in list(pending):
-                st, _ = srv.status(ids[k])
+                st, used[k] = srv.status(ids[k])
                 if st == api.JOB_DONE:
                     results[k] = srv.result(ids[k])
                     done_at[k] = t
@@ -54,6 +60,8 @@ def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, 
     wall = time.perf_counter() - t0
     srv.close()
     lat = np.array([done_at[k] - arrivals[k] for k in range(n)])
+    if iters_out is not None:
+        iters_out[:] = used
     return lat, results, wall
 
 
