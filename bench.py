@@ -340,6 +340,8 @@ def run_pds(args):
         extra["csvgd"] = run_csvgd(api, dev, stream, wl, obs, x0, flush)
     if rank == 0 and world == 1 and not args.no_sgld:
         extra["sgld"] = run_sgld(api, dev, stream, wl, obs, x0, flush)
+    if rank == 0 and world == 1 and not args.no_rigid:
+        extra["rigid_double_pendulum"] = run_rigid2(api, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_trajset:
         extra["trajectory_set"] = run_trajset(api, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_metrics:
@@ -541,6 +543,56 @@ def run_sgld(api, dev, stream, wl, obs, x0, flush, iters=10, warmup=3):
             "nonfinite_chains_after": nonfinite}
 
 
+def run_rigid2(api, dev, stream, flush, N=16384, iters=10, warmup=3):
+    """The physical double pendulum's 11-parameter rigid-body model (Sec. V,
+    synthetic): per iteration log p + gradient of N particles (the rigid
+    system's reverse sweep) and the SVGD update over the 11 parameters;
+    theta rows start from the Sobol sequence over the limits (App. A-A)."""
+    import torch
+    wl = wlmod.rigid_double_pendulum(N=N)
+    obs = _gen_obs(api, wl, dev, stream)
+    x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
+    prob = api.Problem.from_workload(wl, obs, stream=stream, checkpoint_stride=K_CKPT, fast_math=FAST_MATH)
+    prob.reserve(N)
+    sv = api.Svgd(N, wl.M, wl.P, wl.lo, wl.hi, lr=wl.lr, stream=stream)
+    X = torch.from_numpy(np.ascontiguousarray(x0.T, dtype=np.float32)).to(dev)
+    api.sobol_box(X[:wl.M], wl.lo, wl.hi, stream=stream)
+    logp = torch.empty(N, device=dev)
+    G = torch.empty((wl.P, N), device=dev)
+    L = api.lib()
+
+    def lg():
+        api._check(L.pds_loglik_grad(prob.handle, api._ptr(X), N, api._ptr(logp), api._ptr(G), None), "rigid loglik")
+
+    def up():
+        api._check(L.pds_svgd_step(sv.handle, api._ptr(X), api._ptr(G), None, None), "rigid step")
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            lg()
+            up()
+    stream.synchronize()
+    evs = [tuple(torch.cuda.Event(enable_timing=True) for _ in range(3)) for _ in range(iters)]
+    with torch.cuda.stream(stream):
+        for k in range(iters):
+            flush.zero_()
+            evs[k][0].record(stream)
+            lg()
+            evs[k][1].record(stream)
+            up()
+            evs[k][2].record(stream)
+    stream.synchronize()
+    tot = sum(e[0].elapsed_time(e[2]) for e in evs) / iters
+    lgt = sum(e[0].elapsed_time(e[1]) for e in evs) / iters
+    nonfinite = int((~torch.isfinite(logp)).sum().item())
+    sv.close()
+    prob.close()
+    return {"workload": f"rigid double pendulum, 11 parameters (masses, inertias, COMs, frictions, joint offset), "
+                        f"N={N}, T={wl.T} at 400 Hz, W={wl.W}, K={K_CKPT}; Sobol initialisation",
+            "value": N * wl.T / (tot / 1e3), "unit": UNIT, "ms_per_iter": tot, "loglik_grad_ms": lgt,
+            "svgd_step_ms": tot - lgt, "iters": iters, "nonfinite_particles": nonfinite}
+
+
 def run_trajset(api, dev, stream, flush, N=8192, R=2, iters=10, warmup=3):
     """Likelihood of a set of R trajectories (Sec. IV-C, the equally weighted
     mixture) on the chain5 system: R trajectories from R parameter draws and
@@ -680,6 +732,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-csvgd", action="store_true", help="skip the constrained-SVGD measurement")
     ap.add_argument("--no-sgld", action="store_true", help="skip the SGLD measurement")
+    ap.add_argument("--no-rigid", action="store_true", help="skip the rigid double pendulum measurement")
     ap.add_argument("--no-trajset", action="store_true", help="skip the trajectory-set measurement")
     ap.add_argument("--no-metrics", action="store_true", help="skip the posterior-metric timing")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")

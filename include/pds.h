@@ -43,6 +43,7 @@ extern "C" {
 
 #define PDS_SYSTEM_PLANAR_CHAIN 1
 #define PDS_SYSTEM_ARM_BOX 2
+#define PDS_SYSTEM_RIGID_DOUBLE_PENDULUM 3
 
 #define PDS_PARAM_MASS 0    /* point mass at the tip of a link [kg]          */
 #define PDS_PARAM_LENGTH 1  /* link length [m]                               */
@@ -132,6 +133,35 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
  * gradient comes from tangents propagated forward through each window
  * (theta and the window's start state: 8 directions). */
 int pds_problem_create_armbox(const pds_armbox_desc* sys, double dt, int T, int windows,
+                              const float* obs, int D, const int* obs_index, double sigma_obs,
+                              double sigma_def, const float* s0, const float* theta_lo,
+                              const float* theta_hi, double c_lim, void* cuda_stream,
+                              pds_problem_t* out);
+
+/* Rigid double pendulum with general inertia and centre of mass: the
+ * 11-parameter model of the physical double pendulum of Sec. V's real-world
+ * experiment (App. Table params-ibm-pendulum).  Two rigid links on parallel
+ * revolute joints (axis z); joint 1 at the origin, joint 2 at (0, -l) in link
+ * 1's frame; gravity along -y.  Link k has mass m_k, centre of mass
+ * (ckx, cky) in its frame, rotational inertia I_k about its COM (the inertia
+ * tensor I_k times the identity; only the z component acts) and viscous joint
+ * friction -b_k qd_k.  State s = [q1, q2, qd1, qd2] (q = 0: link frames
+ * aligned with the world; a COM along -y then hangs at rest).  Parameters,
+ * in the table's order:
+ *   0 m1, 1 I1, 2 c1x, 3 c1y, 4 b1, 5 l, 6 m2, 7 I2, 8 c2x, 9 c2y, 10 b2. */
+typedef struct pds_rigid2_desc {
+  double param[11];       /* nominal values; estimated entries are overridden */
+  double gravity;
+  int n_theta;            /* 1..11 estimated parameters                      */
+  const int* theta_param; /* host [n_theta]: distinct indices into param      */
+} pds_rigid2_desc;
+
+/* Create a multiple-shooting problem of the rigid double pendulum; the other
+ * arguments are as for pds_problem_create (S = 4, P = M + (W-1)*4).  The
+ * gradient comes from a hand-written reverse sweep with checkpoints every K
+ * steps, as for the chains.  Constrained SVGD, trajectory sets and batched
+ * execution are not supported for this system (PDS_ERR_UNSUPPORTED). */
+int pds_problem_create_rigid2(const pds_rigid2_desc* sys, double dt, int T, int windows,
                               const float* obs, int D, const int* obs_index, double sigma_obs,
                               double sigma_def, const float* s0, const float* theta_lo,
                               const float* theta_hi, double c_lim, void* cuda_stream,
@@ -385,7 +415,8 @@ int pds_server_stats(pds_server_t s, int* queued, int* active, size_t* bytes_in_
  *                    (as pds_mmd2 with bandwidth h M: h per coordinate);
  *   PDS_GATE_KNN_KL: the KNN estimate of KL(new || previous) with k = 3 (as
  *                    pds_knn_kl); terms of coincident points are left out.
- * Particles with a coordinate that is not finite take no part.  When the
+ * Particles that sit out (last log p or a theta coordinate not finite) take
+ * no part.  When the
  * value is <= threshold the job retires at once (its iterations_done is then
  * below its cap); otherwise it runs on to its iteration count.  Set the gate
  * before submitting jobs (PDS_ERR_ARG otherwise); h is used by MMD^2 only

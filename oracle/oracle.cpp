@@ -1006,6 +1006,177 @@ static double armbox_particle(const ArmBoxProblem& P, const double* x, double* g
   return total;
 }
 
+// ---------------------------------------------------------------------------
+// Rigid double pendulum with general inertia and centre of mass (the
+// 11-parameter physical double pendulum of Sec. V's real-world experiment,
+// App. Table params-ibm-pendulum), by the 6-D articulated-body algorithm.
+// Two rigid links on revolute joints about their frames' z axes; joint 1 at
+// the world origin, joint 2 at (0, -l, 0) in link 1's frame; link k has
+// mass m_k, centre of mass c_k (link frame) and rotational inertia Ic_k (3x3,
+// about the COM); viscous joint friction tau_k = -b_k qd_k; gravity along
+// -y.  State [q1, q2, qd1, qd2]; q = 0 with c_k along -y hangs at rest.
+// The 11 estimated parameters, in the table's order:
+//   [m1, I1, c1x, c1y, b1, l, m2, I2, c2x, c2y, b2]
+// with c_k = (ckx, cky, 0) and Ic_k = I_k times the identity.
+// ---------------------------------------------------------------------------
+struct Rigid2 {
+  double p[11];  // nominal values of all parameters
+  double g;
+};
+
+template <class T>
+static void rigid2_aba(const T* m, const T (*c)[3], const T (*Ic)[3][3], const T* b, const T& l, double g, const T* s,
+                       T* qdd) {
+  T zero3[3] = {T(0.0), T(0.0), T(0.0)};
+  T r2[3] = {T(0.0), -l, T(0.0)};
+  R3<T> Id;
+  for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) Id.a[i][j] = T(i == j ? 1.0 : 0.0);
+  M6<T> Xup[2];
+  Xup[0] = plux<T>(rot_axis<T>(2, s[0]), zero3);
+  Xup[1] = mm6(plux<T>(rot_axis<T>(2, s[1]), zero3), plux<T>(Id, r2));
+  V6<T> S = v6zero<T>();
+  S.a[2] = T(1.0);
+  V6<T> a0 = v6zero<T>();
+  a0.a[4] = T(g);  // base acceleration = -gravity (gravity along -y)
+  V6<T> v[2], cc[2], pA[2], U[2], a[2];
+  M6<T> IA[2];
+  T d[2], u[2];
+  for (int i = 0; i < 2; ++i) {
+    V6<T> vJ = S;
+    for (int k = 0; k < 6; ++k) vJ.a[k] = vJ.a[k] * s[2 + i];
+    v[i] = (i == 0) ? vJ : add6(mul6(Xup[i], v[i - 1]), vJ);
+    cc[i] = crm6(v[i], vJ);
+    T Ick[3][3];
+    for (int r = 0; r < 3; ++r) for (int q = 0; q < 3; ++q) Ick[r][q] = Ic[i][r][q];
+    IA[i] = mcI<T>(m[i], c[i], Ick);
+    pA[i] = crf6(v[i], mul6(IA[i], v[i]));
+  }
+  for (int i = 1; i >= 0; --i) {
+    U[i] = mul6(IA[i], S);
+    d[i] = U[i].a[2];
+    u[i] = -(b[i] * s[2 + i]) - pA[i].a[2];
+    if (i > 0) {
+      M6<T> Ia;
+      for (int r = 0; r < 6; ++r) for (int q = 0; q < 6; ++q) Ia.a[r][q] = IA[i].a[r][q] - U[i].a[r] * U[i].a[q] / d[i];
+      V6<T> pa = mul6(Ia, cc[i]);
+      for (int r = 0; r < 6; ++r) pa.a[r] = pA[i].a[r] + pa.a[r] + U[i].a[r] * u[i] / d[i];
+      IA[i - 1] = madd6(IA[i - 1], mm6(tr6(Xup[i]), mm6(Ia, Xup[i])));
+      pA[i - 1] = add6(pA[i - 1], mul6T(Xup[i], pa));
+    }
+  }
+  for (int i = 0; i < 2; ++i) {
+    a[i] = add6(mul6(Xup[i], i == 0 ? a0 : a[i - 1]), cc[i]);
+    T ua(0.0);
+    for (int k = 0; k < 6; ++k) ua += U[i].a[k] * a[i].a[k];
+    qdd[i] = (u[i] - ua) / d[i];
+    for (int k = 0; k < 6; ++k) a[i].a[k] = a[i].a[k] + S.a[k] * qdd[i];
+  }
+}
+
+// The 11-parameter form: c_k = (ckx, cky, 0), Ic_k = I_k identity.
+template <class T>
+static void rigid2_qdd(const T* p, double g, const T* s, T* qdd) {
+  T m[2] = {p[0], p[6]}, b[2] = {p[4], p[10]};
+  T c[2][3] = {{p[2], p[3], T(0.0)}, {p[8], p[9], T(0.0)}};
+  T Ic[2][3][3];
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) Ic[k][i][j] = (i == j) ? p[k == 0 ? 1 : 7] : T(0.0);
+  rigid2_aba<T>(m, c, Ic, b, p[5], g, s, qdd);
+}
+
+template <class T>
+static void rigid2_step(const T* p, double g, double dt, const T* s, T* sn) {
+  T qdd[2];
+  rigid2_qdd<T>(p, g, s, qdd);
+  for (int i = 0; i < 2; ++i) {
+    T v = s[2 + i] + qdd[i] * T(dt);
+    sn[2 + i] = v;
+    sn[i] = s[i] + v * T(dt);
+  }
+}
+
+struct Rigid2Problem {
+  Rigid2 sys;
+  int M;
+  const int* theta_param;  // [M] indices into the 11 parameters
+  double dt;
+  int T, W, D;
+  const int* obs_index;    // [D] into the state
+  const double* obs;       // [T][D], row t-1 holds x_t
+  double sigma_obs, sigma_def;
+  const double* s0;        // [4]
+  const double* lo;        // [M]
+  const double* hi;        // [M]
+  double c_lim;
+};
+
+template <class T>
+static T rigid2_window(const Rigid2Problem& P, const T* th, const T* s_start, const T* s_next, int w) {
+  T p[11];
+  for (int k = 0; k < 11; ++k) p[k] = T(P.sys.p[k]);
+  for (int k = 0; k < P.M; ++k) p[P.theta_param[k]] = th[k];
+  std::vector<T> s(s_start, s_start + 4), sn(4);
+  const int t0 = (int)(((long long)w * P.T) / P.W), t1 = (int)(((long long)(w + 1) * P.T) / P.W);
+  const double so2 = P.sigma_obs * P.sigma_obs;
+  const double obs_const = -0.5 * P.D * std::log(2.0 * M_PI * so2);
+  T ll(0.0);
+  for (int t = t0 + 1; t <= t1; ++t) {
+    rigid2_step<T>(p, P.sys.g, P.dt, s.data(), sn.data());
+    s.swap(sn);
+    T acc(0.0);
+    for (int k = 0; k < P.D; ++k) {
+      T r = T(P.obs[(size_t)(t - 1) * P.D + k]) - s[P.obs_index[k]];
+      acc += r * r;
+    }
+    ll += acc * T(-0.5 / so2) + T(obs_const);
+  }
+  if (w < P.W - 1) {
+    const double sd2 = P.sigma_def * P.sigma_def;
+    T acc(0.0);
+    for (int k = 0; k < 4; ++k) {
+      T d = s_next[k] - s[k];
+      acc += d * d;
+    }
+    ll += acc * T(-0.5 / sd2) + T(-0.5 * 4 * std::log(2.0 * M_PI * sd2));
+  }
+  return ll;
+}
+
+static double rigid2_particle(const Rigid2Problem& P, const double* x, double* grad) {
+  const int M = P.M, S = 4, W = P.W, Pdim = M + (W - 1) * S;
+  if (grad) std::fill(grad, grad + Pdim, 0.0);
+  double total = 0.0;
+  for (int w = 0; w < W; ++w) {
+    const double* ss = (w == 0) ? P.s0 : x + M + (w - 1) * S;
+    const double* sn = (w < W - 1) ? x + M + w * S : nullptr;
+    if (!grad) {
+      total += rigid2_window<double>(P, x, ss, sn, w);
+      continue;
+    }
+    g_nd = M + 2 * S;
+    std::vector<Dual> th(M), a(S), b(S);
+    for (int k = 0; k < M; ++k) { th[k] = Dual(x[k]); th[k].d[k] = 1.0; }
+    for (int k = 0; k < S; ++k) {
+      a[k] = Dual(ss[k]);
+      if (w > 0) a[k].d[M + k] = 1.0;
+      if (sn) { b[k] = Dual(sn[k]); b[k].d[M + S + k] = 1.0; }
+    }
+    Dual ll = rigid2_window<Dual>(P, th.data(), a.data(), sn ? b.data() : nullptr, w);
+    total += ll.v;
+    for (int k = 0; k < M; ++k) grad[k] += ll.d[k];
+    if (w > 0) for (int k = 0; k < S; ++k) grad[M + (w - 1) * S + k] += ll.d[M + k];
+    if (sn) for (int k = 0; k < S; ++k) grad[M + w * S + k] += ll.d[M + S + k];
+  }
+  for (int k = 0; k < M; ++k) {
+    const double wd = P.hi[k] - P.lo[k];
+    const double u = (x[k] - P.lo[k]) / wd;
+    const double cu = std::min(1.0, std::max(0.0, u));
+    total += -std::log(wd) - 0.5 * P.c_lim * (cu - u) * (cu - u);
+    if (grad) grad[k] += P.c_lim * (cu - u) / wd;
+  }
+  return total;
+}
+
 }  // namespace orc
 
 using namespace orc;
@@ -1312,6 +1483,49 @@ int orc_armbox_loglik_grad(const ArmBoxProblem* prob, const double* particles, i
 #endif
   for (int i = 0; i < N; ++i)
     logp[i] = armbox_particle(P, particles + (size_t)i * Pdim, grad ? grad + (size_t)i * Pdim : nullptr);
+  return 0;
+}
+
+// ---- rigid double pendulum --------------------------------------------------
+// qdd for general COMs c [2][3] and inertias Ic [2][3][3] (row-major).
+int orc_rigid2_qdd_full(const double* m, const double* c, const double* Ic, const double* b, double l, double g,
+                        const double* s, double* qdd) {
+  double cc[2][3], II[2][3][3];
+  for (int k = 0; k < 2; ++k)
+    for (int i = 0; i < 3; ++i) {
+      cc[k][i] = c[3 * k + i];
+      for (int j = 0; j < 3; ++j) II[k][i][j] = Ic[9 * k + 3 * i + j];
+    }
+  rigid2_aba<double>(m, cc, II, b, l, g, s, qdd);
+  return 0;
+}
+
+// qdd of the 11-parameter form.
+int orc_rigid2_qdd(const double* p11, double g, const double* s, double* qdd) {
+  rigid2_qdd<double>(p11, g, s, qdd);
+  return 0;
+}
+
+// f_sim: states [T+1][4] from s0.
+int orc_rigid2_simulate(const double* p11, double g, double dt, int T, const double* s0, double* states) {
+  std::copy(s0, s0 + 4, states);
+  for (int t = 0; t < T; ++t) rigid2_step<double>(p11, g, dt, states + (size_t)t * 4, states + (size_t)(t + 1) * 4);
+  return 0;
+}
+
+int orc_rigid2_loglik_grad(const Rigid2Problem* prob, const double* particles, int N, double* logp, double* grad,
+                           int threads) {
+  const Rigid2Problem& P = *prob;
+  if (P.W < 1 || P.T < P.W || P.M < 1 || P.M > 11 || P.M + 8 > MAXD) return -1;
+  for (int k = 0; k < P.M; ++k)
+    if (P.theta_param[k] < 0 || P.theta_param[k] > 10) return -1;
+  const int Pdim = P.M + (P.W - 1) * 4;
+#ifdef _OPENMP
+  if (threads > 0) omp_set_num_threads(threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int i = 0; i < N; ++i)
+    logp[i] = rigid2_particle(P, particles + (size_t)i * Pdim, grad ? grad + (size_t)i * Pdim : nullptr);
   return 0;
 }
 

@@ -103,6 +103,30 @@ class _ArmBoxProblem(ctypes.Structure):
     ]
 
 
+class _Rigid2(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double * 11), ("g", ctypes.c_double)]
+
+
+class _Rigid2Problem(ctypes.Structure):
+    _fields_ = [
+        ("sys", _Rigid2),
+        ("M", ctypes.c_int),
+        ("theta_param", _ip),
+        ("dt", ctypes.c_double),
+        ("T", ctypes.c_int),
+        ("W", ctypes.c_int),
+        ("D", ctypes.c_int),
+        ("obs_index", _ip),
+        ("obs", _dp),
+        ("sigma_obs", ctypes.c_double),
+        ("sigma_def", ctypes.c_double),
+        ("s0", _dp),
+        ("lo", _dp),
+        ("hi", _dp),
+        ("c_lim", ctypes.c_double),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -143,6 +167,11 @@ def lib():
             L.orc_armbox_qdd.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, _dp, _dp]
             L.orc_armbox_inertia.argtypes = [ctypes.POINTER(_ArmBox), _dp, _dp]
             L.orc_armbox_simulate.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_rigid2_qdd_full.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
+            L.orc_rigid2_qdd.argtypes = [_dp, ctypes.c_double, _dp, _dp]
+            L.orc_rigid2_simulate.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_rigid2_loglik_grad.argtypes = [ctypes.POINTER(_Rigid2Problem), _dp, ctypes.c_int, _dp, _dp,
+                                                 ctypes.c_int]
             L.orc_armbox_loglik_grad.argtypes = [ctypes.POINTER(_ArmBoxProblem), _dp, ctypes.c_int, _dp, _dp,
                                                  ctypes.c_int]
             _lib = L
@@ -487,4 +516,81 @@ class ArmBoxProblem:
                                           g.ctypes.data_as(_dp) if grad else None, int(threads))
         if rc != 0:
             raise RuntimeError("orc_armbox_loglik_grad failed")
+        return (logp, g) if grad else logp
+
+
+# --------------------------------------------------------------------------
+# Rigid double pendulum (11 parameters: [m1, I1, c1x, c1y, b1, l, m2, I2,
+# c2x, c2y, b2]; joints about z, joint 2 at (0, -l, 0) in link 1's frame,
+# gravity along -y; state [q1, q2, qd1, qd2])
+# --------------------------------------------------------------------------
+RIGID2_PARAMS = ("m1", "I1", "c1x", "c1y", "b1", "l", "m2", "I2", "c2x", "c2y", "b2")
+
+
+def rigid2_qdd_full(m, c, Ic, b, l, g, s):
+    """Joint accelerations for general COMs c [2][3] and inertias Ic [2][3][3]."""
+    ma, mp = _d(m)
+    ca, cp = _d(np.asarray(c, dtype=np.float64).reshape(-1))
+    ia, ip = _d(np.asarray(Ic, dtype=np.float64).reshape(-1))
+    ba, bp = _d(b)
+    sa, sp = _d(s)
+    out = np.zeros(2)
+    lib().orc_rigid2_qdd_full(mp, cp, ip, bp, float(l), float(g), sp, out.ctypes.data_as(_dp))
+    return out
+
+
+def rigid2_qdd(p11, g, s):
+    pa, pp = _d(p11)
+    sa, sp = _d(s)
+    out = np.zeros(2)
+    lib().orc_rigid2_qdd(pp, float(g), sp, out.ctypes.data_as(_dp))
+    return out
+
+
+def rigid2_simulate(p11, g, dt, T, s0):
+    pa, pp = _d(p11)
+    sa, sp = _d(s0)
+    out = np.zeros((T + 1, 4))
+    lib().orc_rigid2_simulate(pp, float(g), float(dt), int(T), sp, out.ctypes.data_as(_dp))
+    return out
+
+
+class Rigid2Problem:
+    """Multiple-shooting problem of the rigid double pendulum: theta are the
+    parameters theta_param (indices into the 11), the others fixed at p11."""
+
+    def __init__(self, *, p11, g, theta_param, dt, T, W, obs, obs_index, sigma_obs, sigma_def, s0, lo, hi,
+                 c_lim=1e4):
+        self._keep = []
+
+        def d(x):
+            a, p = _d(x)
+            self._keep.append(a)
+            return p
+
+        def i(x):
+            a, p = _i(x)
+            self._keep.append(a)
+            return p
+
+        obs = np.asarray(obs, dtype=np.float64)
+        self.T, self.W, self.M, self.S = int(T), int(W), len(theta_param), 4
+        self.P = self.M + (self.W - 1) * 4
+        sysc = _Rigid2(g=float(g))
+        for k in range(11):
+            sysc.p[k] = float(p11[k])
+        self.c = _Rigid2Problem(sys=sysc, M=self.M, theta_param=i(theta_param), dt=float(dt), T=self.T, W=self.W,
+                                D=obs.shape[1], obs_index=i(obs_index), obs=d(obs), sigma_obs=float(sigma_obs),
+                                sigma_def=float(sigma_def), s0=d(s0), lo=d(lo), hi=d(hi), c_lim=float(c_lim))
+
+    def loglik_grad(self, particles, grad=True, threads=1):
+        x, xp = _d(np.atleast_2d(particles))
+        N = x.shape[0]
+        assert x.shape[1] == self.P
+        logp = np.zeros(N)
+        g = np.zeros((N, self.P)) if grad else None
+        rc = lib().orc_rigid2_loglik_grad(ctypes.byref(self.c), xp, N, logp.ctypes.data_as(_dp),
+                                          g.ctypes.data_as(_dp) if grad else None, int(threads))
+        if rc != 0:
+            raise RuntimeError("orc_rigid2_loglik_grad failed")
         return (logp, g) if grad else logp

@@ -46,6 +46,15 @@ class _SystemDesc(ctypes.Structure):
     ]
 
 
+class _Rigid2Desc(ctypes.Structure):
+    _fields_ = [
+        ("param", ctypes.c_double * 11),
+        ("gravity", ctypes.c_double),
+        ("n_theta", ctypes.c_int),
+        ("theta_param", _ip),
+    ]
+
+
 class _ArmBoxDesc(ctypes.Structure):
     _fields_ = [
         ("n_arm", ctypes.c_int),
@@ -68,6 +77,9 @@ EXPORTS = {
                             ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
                             _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "pds_problem_create_armbox": ([ctypes.POINTER(_ArmBoxDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
+                                   ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
+                                   ctypes.c_double, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
+    "pds_problem_create_rigid2": ([ctypes.POINTER(_Rigid2Desc), ctypes.c_double, ctypes.c_int, ctypes.c_int, _fp,
                                    ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
                                    ctypes.c_double, _vp, ctypes.POINTER(_vp)], ctypes.c_int),
     "pds_problem_destroy": ([_vp], ctypes.c_int),
@@ -259,9 +271,41 @@ class Problem:
         return self
 
     @classmethod
+    def rigid2(cls, wl, obs, stream=None, checkpoint_stride=None, fast_math=None):
+        """Rigid double pendulum problem (pds_problem_create_rigid2) from a Rigid2Workload."""
+        self = cls.__new__(cls)
+        L = lib()
+        tp = np.ascontiguousarray(wl.theta_param, dtype=np.int32)
+        d = _Rigid2Desc(gravity=float(wl.g), n_theta=int(tp.size), theta_param=tp.ctypes.data_as(_ip))
+        for k in range(11):
+            d.param[k] = float(wl.p11[k])
+        f = [np.ascontiguousarray(x, dtype=np.float32) for x in (obs, wl.s0, wl.lo, wl.hi)]
+        oi = np.ascontiguousarray(wl.obs_index, dtype=np.int32)
+        self._stream_h, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.pds_problem_create_rigid2(ctypes.byref(d), float(wl.dt), int(wl.T), int(wl.W),
+                                           f[0].ctypes.data_as(_fp), f[0].shape[1], oi.ctypes.data_as(_ip),
+                                           float(wl.sigma_obs), float(wl.sigma_def), f[1].ctypes.data_as(_fp),
+                                           f[2].ctypes.data_as(_fp), f[3].ctypes.data_as(_fp), float(wl.c_lim),
+                                           self._stream_h, ctypes.byref(h)), "pds_problem_create_rigid2")
+        self._h = h
+        self._keep = []
+        self.T, self.W, self.n = int(wl.T), int(wl.W), 2
+        M, S, P = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(L.pds_problem_layout(h, ctypes.byref(M), ctypes.byref(S), ctypes.byref(P)), "pds_problem_layout")
+        self.M, self.S, self.P = M.value, S.value, P.value
+        if checkpoint_stride is not None:
+            self.set_checkpoint_stride(checkpoint_stride)
+        if fast_math is not None:
+            self.set_option(OPT_FAST_MATH, int(bool(fast_math)))
+        return self
+
+    @classmethod
     def from_workload(cls, wl, obs, **kw):
         if hasattr(wl, "arm_len"):
             return cls.armbox(wl, obs, **kw)
+        if hasattr(wl, "p11"):
+            return cls.rigid2(wl, obs, **kw)
         return cls(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
                    theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs, obs_index=wl.obs_index,
                    sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo, hi=wl.hi, g=wl.g,

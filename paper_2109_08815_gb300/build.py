@@ -34,7 +34,7 @@ def _nvcc() -> str:
 def _units():
     units = [("pds_api", "pds_api.cu", []), ("reduce", "reduce.cu", []), ("svgd", "svgd.cu", []),
              ("batch", "batch.cu", []), ("server", "server.cu", []), ("armbox", "armbox.cu", []),
-             ("metrics", "metrics.cu", []), ("sgld", "sgld.cu", []), ("sobol", "sobol.cu", []),
+             ("metrics", "metrics.cu", []), ("sgld", "sgld.cu", []), ("sobol", "sobol.cu", []), ("rigid2", "rigid2.cu", []),
              ("svgd_tc", "svgd_tc.cu", []), ("median_tc", "median_tc.cu", [])]
     for nl in range(1, MAX_LINKS + 1):
         units.append((f"rollout_nl{nl}", "rollout_nl.cu", [f"-DPDS_NL={nl}"]))

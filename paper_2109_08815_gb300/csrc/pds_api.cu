@@ -377,9 +377,12 @@ int pds_loglik_grad(pds_problem_t p, const float* particles, int N, float* logp,
   if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
   int rc = ensure_workspace(p, N);
   if (rc != PDS_OK) return rc;
-  cudaError_t e = (p->kind == PDS_SYSTEM_ARM_BOX)
-                      ? launch_armbox_rollout(p->c, p->ab, particles, N, p->parts, grad != nullptr, status, p->stream)
-                      : launch_rollout(p->c, particles, N, p->parts, grad != nullptr, status, p->stream);
+  cudaError_t e =
+      (p->kind == PDS_SYSTEM_ARM_BOX)
+          ? launch_armbox_rollout(p->c, p->ab, particles, N, p->parts, grad != nullptr, status, p->stream)
+      : (p->kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM)
+          ? launch_rigid2_rollout(p->c, p->r2, particles, N, p->parts, grad != nullptr, status, p->stream)
+          : launch_rollout(p->c, particles, N, p->parts, grad != nullptr, status, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
   e = launch_window_reduce(p->c, particles, N, p->parts, logp, grad, status, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "window reduce launch");
@@ -392,7 +395,9 @@ int pds_simulate(pds_problem_t p, const float* theta, int N, float* states) {
   if (!p || !theta || !states) return fail(PDS_ERR_ARG, "NULL argument");
   if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
   cudaError_t e = (p->kind == PDS_SYSTEM_ARM_BOX) ? launch_armbox_simulate(p->c, p->ab, theta, N, states, p->stream)
-                                                  : launch_simulate(p->c, theta, N, states, p->stream);
+                   : (p->kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM)
+                       ? launch_rigid2_simulate(p->c, p->r2, theta, N, states, p->stream)
+                       : launch_simulate(p->c, theta, N, states, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "simulate launch");
   g_launches = 1;
   return PDS_OK;

@@ -92,6 +92,10 @@ cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, co
 cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st);
 cudaError_t launch_armbox_rollout(const ChainParams& c, const ArmBoxParams& ab, const float* X, int N,
                                   const Partials& parts, int grad, int32_t* status, cudaStream_t st);
+cudaError_t launch_rigid2_rollout(const ChainParams& c, const Rigid2Params& r, const float* X, int N,
+                                  const Partials& parts, int grad, int32_t* status, cudaStream_t st);
+cudaError_t launch_rigid2_simulate(const ChainParams& c, const Rigid2Params& r, const float* theta, int N,
+                                   float* states, cudaStream_t st);
 cudaError_t launch_armbox_simulate(const ChainParams& c, const ArmBoxParams& ab, const float* theta, int N,
                                    float* states, cudaStream_t st);
 

@@ -18,6 +18,9 @@ Workloads (synthetic stand-ins; the paper's real datasets are not available):
 * ``chain5`` -- a 5-link planar chain with point masses at the link tips and
   viscous joint damping, theta = 5 masses + 5 damping coefficients, 1000 steps
   at dt = 0.005, angles and velocities observed with sigma 0.02, 20 windows.
+* ``rigid_double_pendulum`` -- the physical double pendulum's 11-parameter
+  rigid-body model (masses, inertias, centres of mass, joint frictions, the
+  second joint's offset) at 400 Hz, 1000 steps, 10 windows.
 """
 from __future__ import annotations
 
@@ -373,6 +376,85 @@ def arm_box(N: int = 2048, seed: int = 3000, T: int = 2000, W: int = 40, n_arm: 
                           theta_true=theta_true, lo=lo, hi=hi, dt=0.002, T=T, W=W, obs_index=obs_index,
                           sigma_obs=0.01, sigma_def=SIGMA_DEF, s0=np.zeros(4), noise=noise, theta_init=theta_init,
                           seed=seed)
+
+
+RIGID2_PARAMS = ("m1", "I1", "c1x", "c1y", "b1", "l", "m2", "I2", "c2x", "c2y", "b2")
+# parameter limits of the physical double pendulum's table (link 1: mass,
+# inertia, COM x, COM y, joint friction; link 2: length, mass, inertia, COM x,
+# COM y, joint friction)
+RIGID2_LO = np.array([0.05, 0.002, -0.2, -0.2, 0.0, 0.08, 0.05, 0.002, -0.2, -0.2, 0.0])
+RIGID2_HI = np.array([0.5, 1.0, 0.2, 0.2, 0.5, 0.3, 0.5, 1.0, 0.2, 0.2, 0.5])
+
+
+@dataclasses.dataclass
+class Rigid2Workload:
+    """Rigid double pendulum with general inertia and centre of mass (the
+    11-parameter physical double pendulum, synthetic): parameters
+    [m1, I1, c1x, c1y, b1, l, m2, I2, c2x, c2y, b2]; theta_param selects the
+    estimated ones, the others stay at p11."""
+    name: str
+    p11: np.ndarray            # [11] true values of all parameters
+    theta_param: np.ndarray    # [M] int32 indices into p11
+    theta_true: np.ndarray     # [M]
+    lo: np.ndarray             # [M]
+    hi: np.ndarray             # [M]
+    dt: float
+    T: int
+    W: int
+    obs_index: np.ndarray      # [D] int32 into s = [q1, q2, qd1, qd2]
+    sigma_obs: float
+    sigma_def: float
+    s0: np.ndarray             # [4]
+    noise: np.ndarray          # [T][D]
+    theta_init: np.ndarray     # [N][M]
+    g: float = GRAVITY
+    c_lim: float = C_LIM
+    lr: float = 1e-2
+    iterations: int = 2000
+    seed: int = 0
+    n: int = 2
+    S: int = 4
+
+    @property
+    def M(self) -> int:
+        return len(self.theta_param)
+
+    @property
+    def D(self) -> int:
+        return len(self.obs_index)
+
+    @property
+    def N(self) -> int:
+        return self.theta_init.shape[0]
+
+    @property
+    def P(self) -> int:
+        return self.M + (self.W - 1) * self.S
+
+    def window_start(self, w: int) -> int:
+        return (w * self.T) // self.W
+
+
+def rigid_double_pendulum(N: int = 100, seed: int = 7000, T: int = 1000, W: int = 10,
+                          theta_param=tuple(range(11))) -> Rigid2Workload:
+    """All 11 true parameters ~ U over the middle half of the table's limits;
+    recorded at 400 Hz (dt = 0.0025), T = 1000 steps (2.5 s), 10 windows;
+    q0 ~ U(-pi/2, pi/2) at rest; both angles and both velocities observed with
+    sigma 0.02 (velocities of the physical data come from finite differences);
+    initial particles uniform in the limits of the estimated parameters."""
+    rng = np.random.default_rng(seed)
+    w = RIGID2_HI - RIGID2_LO
+    p11 = rng.uniform(RIGID2_LO + 0.25 * w, RIGID2_HI - 0.25 * w)
+    tp = np.asarray(theta_param, dtype=np.int32)
+    lo, hi = RIGID2_LO[tp].copy(), RIGID2_HI[tp].copy()
+    q0 = rng.uniform(-math.pi / 2, math.pi / 2, size=2)
+    D = 4
+    noise = rng.standard_normal((T, D))
+    theta_init = rng.uniform(lo, hi, size=(N, len(tp)))
+    return Rigid2Workload(name="rigid_double_pendulum", p11=p11, theta_param=tp, theta_true=p11[tp].copy(), lo=lo,
+                          hi=hi, dt=0.0025, T=T, W=W, obs_index=np.arange(4, dtype=np.int32), sigma_obs=0.02,
+                          sigma_def=SIGMA_DEF, s0=np.concatenate([q0, np.zeros(2)]), noise=noise,
+                          theta_init=theta_init, seed=seed)
 
 
 def serving_mix(n_jobs: int, seed: int = 5000, armbox_fraction: float = 0.1, armbox_N: int = 512):
