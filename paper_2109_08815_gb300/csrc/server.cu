@@ -13,8 +13,8 @@
 // the server takes a snapshot of each active job's theta particles in
 // unit-box coordinates and evaluates a posterior metric (Sec. IV: the
 // unbiased RBF MMD^2, or the KNN-KL estimate with k = 3) between this
-// snapshot and the previous one, over the particles that are finite (the
-// MMD kernel's bandwidth is h per coordinate, h M in all).  A job
+// snapshot and the previous one, over the live particles (finite theta and
+// last log p; the MMD kernel's bandwidth is h per coordinate, h M in all).  A job
 // whose metric is at or below the threshold has reached its posterior and
 // retires before its iteration cap.
 #include <cuda_runtime.h>
@@ -67,14 +67,16 @@ struct GateUnit {
   float lo[PDS_MAX_THETA], inv_w[PDS_MAX_THETA];
 };
 
-// u[k][i] = (theta[k][i] - lo_k) / (hi_k - lo_k); a particle with a
-// coordinate that is not finite gets NaN in every row and is not counted.
-__global__ void __launch_bounds__(256) gate_unit_kernel(const float* __restrict__ x, int N, int M, GateUnit g,
-                                                        float* __restrict__ u, double* __restrict__ live) {
+// u[k][i] = (theta[k][i] - lo_k) / (hi_k - lo_k); a particle that sits out
+// (its last log p or a theta coordinate not finite) gets NaN in every row and
+// is not counted.
+__global__ void __launch_bounds__(256) gate_unit_kernel(const float* __restrict__ x, const float* __restrict__ logp,
+                                                        int N, int M, GateUnit g, float* __restrict__ u,
+                                                        double* __restrict__ live) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool ok = false;
   if (i < N) {
-    ok = true;
+    ok = isfinite(logp[i]);
     for (int k = 0; k < M; ++k) ok &= isfinite(x[(size_t)k * N + i]);
     for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = ok ? (x[(size_t)k * N + i] - g.lo[k]) * g.inv_w[k] : NAN;
   }
@@ -156,7 +158,7 @@ static cudaError_t gate_enqueue(pds_server* s, Job& j) {
   double* live_now = j.d_acc + 3 + j.u_cur;
   cudaError_t e = cudaMemsetAsync(live_now, 0, sizeof(double), s->stream);
   if (e != cudaSuccess) return e;
-  gate_unit_kernel<<<(N + 255) / 256, 256, 0, s->stream>>>(j.d_x, N, M, g, now, live_now);
+  gate_unit_kernel<<<(N + 255) / 256, 256, 0, s->stream>>>(j.d_x, j.d_logp, N, M, g, now, live_now);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (j.snapshots > 0) {
     if (s->gate_metric == PDS_GATE_MMD2)
