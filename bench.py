@@ -714,9 +714,9 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
             "unit": UNIT, "time_to_posterior": "arrival to final particles on the host"}
 
 
-# dram bytes per rollout launch from the committed ncu capture of this kernel
-# (None until a capture of the current kernel exists)
-TRAFFIC_BYTES_PER_LAUNCH = None
+# dram bytes (read + write) per full-size rollout launch, from the committed
+# ncu capture of this kernel (set to None when the kernel changes)
+TRAFFIC_BYTES_PER_LAUNCH = 13307904 + 117263104
 
 
 def main():
