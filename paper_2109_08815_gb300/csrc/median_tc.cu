@@ -318,7 +318,7 @@ int median_tc_work_items(int N, int* out) {
 
 size_t median_tc_floats(int N, int M) {
   const size_t nt = (size_t)(N + kMtRows - 1) / kMtRows;
-  const int MM = M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 10 ? 10 : 16;
+  const int MM = M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 10 ? 10 : M <= 12 ? 12 : 16;
   const int KA = ((MM + 2 + 7) / 8) * 8;  // as MtDims<MM>
   return 2 * nt * (size_t)(2 * kMtRows * KA);
 }
@@ -376,6 +376,7 @@ cudaError_t launch_median_tc(int N, int M, const float* u, float* img, const int
   if (M <= 4) return median_tc_mm<4>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
   if (M <= 8) return median_tc_mm<8>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
   if (M <= 10) return median_tc_mm<10>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
+  if (M <= 12) return median_tc_mm<12>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
   return median_tc_mm<16>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
 }
 

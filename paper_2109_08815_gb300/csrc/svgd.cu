@@ -759,6 +759,7 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
   if (sp.M <= 4) return launch_svgd_mm<4>(sp, w, X, G, bw_out, phi_out, st, launches);
   if (sp.M <= 8) return launch_svgd_mm<8>(sp, w, X, G, bw_out, phi_out, st, launches);
   if (sp.M <= 10) return launch_svgd_mm<10>(sp, w, X, G, bw_out, phi_out, st, launches);
+  if (sp.M <= 12) return launch_svgd_mm<12>(sp, w, X, G, bw_out, phi_out, st, launches);
   return launch_svgd_mm<16>(sp, w, X, G, bw_out, phi_out, st, launches);
 }
 

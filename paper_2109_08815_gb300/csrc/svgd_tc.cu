@@ -443,7 +443,7 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_
 
 size_t phi_tc_floats(int N, int M) {
   const size_t Npad = (size_t)(N + kTcRows - 1) / kTcRows * kTcRows;
-  const int MM = M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 10 ? 10 : 16;
+  const int MM = M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 10 ? 10 : M <= 12 ? 12 : 16;
   const int KA = ((MM + 2 + 7) / 8) * 8, NV = ((4 * MM + 1 + 15) / 16) * 16;  // as TcDims<MM>
   return Npad * (4 * (size_t)KA + (size_t)NV / 2);  // a, b (tf32 hi, lo) and v (fp16) per particle
 }
@@ -453,6 +453,7 @@ cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cuda
   if (M <= 4) return launch_phi_tc_mm<4>(N, M, w, slots_used, st);
   if (M <= 8) return launch_phi_tc_mm<8>(N, M, w, slots_used, st);
   if (M <= 10) return launch_phi_tc_mm<10>(N, M, w, slots_used, st);
+  if (M <= 12) return launch_phi_tc_mm<12>(N, M, w, slots_used, st);
   return launch_phi_tc_mm<16>(N, M, w, slots_used, st);
 }
 

@@ -59,7 +59,7 @@ def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2, fast=False):
 
 @pytest.mark.parametrize("fast", [False, True])
 @pytest.mark.parametrize("N,M,P", [(2, 1, 1), (3, 2, 5), (100, 4, 76), (129, 10, 30), (1000, 7, 7), (257, 16, 40),
-                                   (600, 3, 9), (1031, 9, 9)])
+                                   (600, 3, 9), (1031, 9, 9), (700, 11, 47), (2100, 12, 12)])
 def test_svgd_step_matches_oracle(N, M, P, fast):
     _compare(N, M, P, seed=N + 10 * M, fast=fast)
 
@@ -173,7 +173,8 @@ def test_sampled_bracket_median_equals_full_passes(kind):
         assert abs(b_full - med / np.log(N)) <= 1e-6 * med / np.log(N)
 
 
-@pytest.mark.parametrize("N,M", [(256, 1), (300, 4), (1000, 10), (777, 16), (4096, 10), (2500, 8)])
+@pytest.mark.parametrize("N,M", [(256, 1), (300, 4), (1000, 10), (777, 16), (4096, 10), (2500, 8), (1500, 11),
+                                 (2049, 12)])
 def test_tensor_core_phi_matches_cuda_cores(N, M):
     """phi's kernel-matrix products on tcgen05 (split tf32 operands, fp32
     accumulation; the kernel values themselves rounded to tf32) against the
@@ -194,7 +195,7 @@ def test_tensor_core_phi_matches_cuda_cores(N, M):
     assert np.max(np.abs(tcp - ref)) <= 1e-3 * np.max(np.abs(ref)), np.max(np.abs(tcp - ref)) / np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("N,M", [(2048, 2), (3001, 10), (4096, 16)])
+@pytest.mark.parametrize("N,M", [(2048, 2), (3001, 10), (4096, 16), (2600, 11), (4100, 12)])
 def test_tensor_core_median_matches_cuda_cores(N, M):
     """Pair distances of the median passes from tensor-core products against
     the CUDA-core distances: the same bandwidth within 1e-5."""
