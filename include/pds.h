@@ -159,8 +159,9 @@ typedef struct pds_rigid2_desc {
 /* Create a multiple-shooting problem of the rigid double pendulum; the other
  * arguments are as for pds_problem_create (S = 4, P = M + (W-1)*4).  The
  * gradient comes from a hand-written reverse sweep with checkpoints every K
- * steps, as for the chains.  Constrained SVGD, trajectory sets and batched
- * execution are not supported for this system (PDS_ERR_UNSUPPORTED). */
+ * steps, as for the chains.  Constrained SVGD and trajectory sets are not
+ * supported for this system (PDS_ERR_UNSUPPORTED); batched execution and the
+ * server run it on its own branch, like the arm-and-box system. */
 int pds_problem_create_rigid2(const pds_rigid2_desc* sys, double dt, int T, int windows,
                               const float* obs, int D, const int* obs_index, double sigma_obs,
                               double sigma_def, const float* s0, const float* theta_lo,
@@ -388,6 +389,12 @@ int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int
                       double sigma_def, const float* s0, const float* theta_lo,
                       const float* theta_hi, double c_lim, int N, const float* particles,
                       double lr, int iterations, long long* job_id);
+/* Same for a rigid double pendulum job (arguments as pds_problem_create_rigid2). */
+int pds_server_submit_rigid2(pds_server_t s, const pds_rigid2_desc* sys, double dt, int T, int windows,
+                             const float* obs, int D, const int* obs_index, double sigma_obs,
+                             double sigma_def, const float* s0, const float* theta_lo,
+                             const float* theta_hi, double c_lim, int N, const float* particles,
+                             double lr, int iterations, long long* job_id);
 /* Same for an arm-and-box job (arguments as pds_problem_create_armbox). */
 int pds_server_submit_armbox(pds_server_t s, const pds_armbox_desc* sys, double dt, int T,
                              int windows, const float* obs, int D, const int* obs_index,

@@ -118,6 +118,10 @@ EXPORTS = {
                            ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp, ctypes.c_double,
                            ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong)],
                           ctypes.c_int),
+    "pds_server_submit_rigid2": ([_vp, ctypes.POINTER(_Rigid2Desc), ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                  _fp, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
+                                  ctypes.c_double, ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int,
+                                  ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
     "pds_server_submit_armbox": ([_vp, ctypes.POINTER(_ArmBoxDesc), ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                   _fp, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double, _fp, _fp, _fp,
                                   ctypes.c_double, ctypes.c_int, _fp, ctypes.c_double, ctypes.c_int,
@@ -650,7 +654,16 @@ class Server:
         obs = np.ascontiguousarray(obs, dtype=np.float32)
         x = np.ascontiguousarray(np.asarray(particles).T, dtype=np.float32)  # [P][N]
         jid = ctypes.c_longlong()
-        if hasattr(wl, "arm_len"):
+        if hasattr(wl, "p11"):
+            rd = _Rigid2Desc(gravity=float(wl.g), n_theta=len(wl.theta_param), theta_param=i(wl.theta_param))
+            for k in range(11):
+                rd.param[k] = float(wl.p11[k])
+            _check(lib().pds_server_submit_rigid2(self._h, ctypes.byref(rd), float(wl.dt), int(wl.T), int(wl.W),
+                                                  f(obs), obs.shape[1], i(wl.obs_index), float(wl.sigma_obs),
+                                                  float(wl.sigma_def), f(wl.s0), f(wl.lo), f(wl.hi),
+                                                  float(wl.c_lim), x.shape[1], f(x), float(wl.lr), int(iterations),
+                                                  ctypes.byref(jid)), "pds_server_submit_rigid2")
+        elif hasattr(wl, "arm_len"):
             ad = _ArmBoxDesc(n_arm=len(wl.arm_len), arm_len=d(wl.arm_len), amp=d(wl.amp), freq=d(wl.freq),
                              phase=d(wl.phase), box_mass=wl.box_mass, box_side=wl.box_side,
                              box_com_depth=wl.box_com_depth, weight_mass=(ctypes.c_double * 2)(*wl.weight_mass),

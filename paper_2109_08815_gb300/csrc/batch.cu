@@ -186,6 +186,9 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
       // not part of the chain-length groups: its own rollout on the branch
       if ((e = launch_armbox_rollout(p->c, p->ab, b->X[j], N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
       ++n;
+    } else if (p->kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM) {
+      if ((e = launch_rigid2_rollout(p->c, p->r2, b->X[j], N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
+      ++n;
     }
     if ((e = launch_window_reduce(p->c, b->X[j], N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess)
       return e;
@@ -214,7 +217,7 @@ static int rebuild(pds_batch* b) {
     if (rc != PDS_OK) return rc;
   }
   for (size_t j = 0; j < b->probs.size(); ++j) {
-    if (b->probs[j]->kind != PDS_SYSTEM_ARM_BOX) continue;
+    if (b->probs[j]->kind == PDS_SYSTEM_PLANAR_CHAIN) continue;
     int rc = ensure_workspace(b->probs[j], b->svgds[j]->sp.N);
     if (rc == PDS_OK) rc = ensure_iter_buffers(b->probs[j], b->svgds[j]->sp.N);
     if (rc != PDS_OK) return rc;
@@ -278,9 +281,10 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       delete b;
       return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs the unconstrained one-trajectory method only");
     }
-    if (p->kind != PDS_SYSTEM_PLANAR_CHAIN && p->kind != PDS_SYSTEM_ARM_BOX) {
+    if (p->kind != PDS_SYSTEM_PLANAR_CHAIN && p->kind != PDS_SYSTEM_ARM_BOX &&
+        p->kind != PDS_SYSTEM_RIGID_DOUBLE_PENDULUM) {
       delete b;
-      return set_error(PDS_ERR_UNSUPPORTED, "batched execution runs planar chains and the arm-and-box system");
+      return set_error(PDS_ERR_UNSUPPORTED, "unknown system kind in the batch");
     }
     b->probs.push_back(p);
     b->svgds.push_back(s);

@@ -38,6 +38,8 @@ struct Job {
   // creation arguments (host copies)
   pds_system_desc sys{};
   pds_armbox_desc arm{};
+  pds_rigid2_desc r2{};
+  std::vector<int> theta_param;
   std::vector<double> arm_len, amp, freq, phase;
   std::vector<double> mass, length, damping;
   std::vector<int> theta_kind, theta_link, obs_index;
@@ -143,7 +145,9 @@ static void release(Job& j) {
   j.d_acc = nullptr;
 }
 
-static int job_theta_count(const Job& j) { return j.kind == PDS_SYSTEM_ARM_BOX ? 4 : j.sys.n_theta; }
+static int job_theta_count(const Job& j) {
+  return j.kind == PDS_SYSTEM_ARM_BOX ? 4 : j.kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM ? j.r2.n_theta : j.sys.n_theta;
+}
 
 // Queue the gate's snapshot and, from the second snapshot on, its metric.
 static cudaError_t gate_enqueue(pds_server* s, Job& j) {
@@ -190,7 +194,13 @@ static double gate_value(const pds_server* s, const Job& j) {
 static int activate(pds_server* s, Job& j) {
   int rc;
   int M = 4;
-  if (j.kind == PDS_SYSTEM_ARM_BOX) {
+  if (j.kind == PDS_SYSTEM_RIGID_DOUBLE_PENDULUM) {
+    pds_rigid2_desc r = j.r2;
+    r.theta_param = j.theta_param.data();
+    M = r.n_theta;
+    rc = pds_problem_create_rigid2(&r, j.dt, j.T, j.W, j.obs.data(), j.D, j.obs_index.data(), j.sigma_obs,
+                                   j.sigma_def, j.s0.data(), j.lo.data(), j.hi.data(), j.c_lim, s->stream, &j.prob);
+  } else if (j.kind == PDS_SYSTEM_ARM_BOX) {
     pds_armbox_desc a = j.arm;
     a.arm_len = j.arm_len.data();
     a.amp = j.amp.data();
@@ -296,6 +306,41 @@ int pds_server_submit(pds_server_t s, const pds_system_desc* sys, double dt, int
   j.lo.assign(theta_lo, theta_lo + M);
   j.hi.assign(theta_hi, theta_hi + M);
   j.dt = dt; j.T = T; j.W = windows; j.D = D; j.N = N; j.P = M + (windows - 1) * 2 * n;
+  j.sigma_obs = sigma_obs; j.sigma_def = sigma_def; j.c_lim = c_lim; j.lr = lr; j.iterations = iterations;
+  j.x0.assign(particles, particles + (size_t)j.P * N);
+  j.bytes = bytes;
+  j.state = PDS_JOB_QUEUED;
+  *job_id = j.id;
+  s->queue.push_back(j.id);
+  s->jobs.emplace(j.id, std::move(j));
+  return PDS_OK;
+}
+
+int pds_server_submit_rigid2(pds_server_t s, const pds_rigid2_desc* sys, double dt, int T, int windows,
+                             const float* obs, int D, const int* obs_index, double sigma_obs, double sigma_def,
+                             const float* s0, const float* theta_lo, const float* theta_hi, double c_lim, int N,
+                             const float* particles, double lr, int iterations, long long* job_id) {
+  if (!s || !sys || !sys->theta_param || !obs || !obs_index || !s0 || !theta_lo || !theta_hi || !particles ||
+      !job_id)
+    return set_error(PDS_ERR_ARG, "NULL argument");
+  *job_id = 0;
+  const int M = sys->n_theta;
+  if (M < 1 || M > 11 || T < 1 || windows < 1 || windows > T || D < 1 || D > 4 || N < 1 || N > 65536 ||
+      iterations < 1 || !(lr > 0.0))
+    return set_error(PDS_ERR_ARG, "job outside the supported sizes");
+  const size_t bytes = job_bytes(2, M, T, windows, D, N, s->K);
+  if (bytes > s->budget) return set_error(PDS_ERR_BUDGET, "job needs more device memory than the server budget");
+  Job j;
+  j.id = s->next_id++;
+  j.kind = PDS_SYSTEM_RIGID_DOUBLE_PENDULUM;
+  j.r2 = *sys;
+  j.theta_param.assign(sys->theta_param, sys->theta_param + M);
+  j.obs_index.assign(obs_index, obs_index + D);
+  j.obs.assign(obs, obs + (size_t)T * D);
+  j.s0.assign(s0, s0 + 4);
+  j.lo.assign(theta_lo, theta_lo + M);
+  j.hi.assign(theta_hi, theta_hi + M);
+  j.dt = dt; j.T = T; j.W = windows; j.D = D; j.N = N; j.P = M + (windows - 1) * 4;
   j.sigma_obs = sigma_obs; j.sigma_def = sigma_def; j.c_lim = c_lim; j.lr = lr; j.iterations = iterations;
   j.x0.assign(particles, particles + (size_t)j.P * N);
   j.bytes = bytes;

@@ -5,16 +5,17 @@ through the C ABI.
 Covers: f_sim; log p and its gradient (hand-written reverse sweep against
 the oracle's dual numbers) for all 11 parameters and for an unordered subset,
 with particles partly outside the box, several checkpoint strides, exact and
-fast math, ragged N; an SVGD iteration on the problem; the configurations
-the system does not support.
+fast math, ragged N; an SVGD iteration on the problem; batched execution and
+the server with rigid pendulum jobs beside chains (equal to each job run
+alone); the configurations the system does not support.
 """
 import numpy as np
 import pytest
 import torch
 
-from helpers import assert_grad_close
+from helpers import assert_grad_close, f32_workload, observations, particles
 from oracle import pds_oracle as orc
-from paper_2109_08815_gb300 import api
+from paper_2109_08815_gb300 import api, serve
 from paper_2109_08815_gb300 import workloads as wlmod
 
 pytestmark = pytest.mark.gpu
@@ -112,12 +113,59 @@ def test_unsupported_configurations_are_rejected():
     prob = api.Problem.from_workload(wl, obs)
     with pytest.raises(api.PdsError):
         prob.set_csvgd(True, 1.0)
-    sv = api.Svgd(16, wl.M, prob.P, wl.lo, wl.hi)
-    X = _gpu(_particles(wl, obs))
     with pytest.raises(api.PdsError):
-        api.Batch([prob], [sv], [X])
-    sv.close()
+        prob.set_trajectories(np.stack([obs, obs]), np.stack([wl.s0, wl.s0]).astype(np.float32))
     prob.close()
     bad = wlmod.rigid_double_pendulum(N=4, T=40, W=2, theta_param=(1, 1))
     with pytest.raises(api.PdsError):
         api.Problem.from_workload(bad, obs)
+
+
+def _mixed_jobs():
+    """Two rigid pendulum problems (all 11 and 4 parameters) beside two chains."""
+    out = []
+    for tp, N, seed in ((tuple(range(11)), 300, 7000), ((5, 0, 6, 9), 200, 7001)):
+        wl, obs = _workload(N=N, T=120, W=4, theta_param=tp, seed=seed)
+        wl.lr = 1e-3
+        out.append((wl, obs, _particles(wl, obs)))
+    for wl in wlmod.batched_problems(n_jobs=2, seed=91, T_range=(40, 90), W_range=(2, 5), N_range=(100, 300)):
+        wl = f32_workload(wl)
+        o = observations(wl)
+        out.append((wl, o, particles(wl, o, seed=3)))
+    return out
+
+
+def test_batch_with_rigid_pendulums_equals_alone():
+    jobs = _mixed_jobs()
+    iters = 3
+    alone = []
+    for wl, obs, x in jobs:
+        prob = api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=0)
+        sv = api.Svgd(x.shape[0], wl.M, prob.P, wl.lo, wl.hi, lr=wl.lr)
+        X = _gpu(x)
+        api.iterate(prob, sv, X, iters)
+        torch.cuda.synchronize()
+        alone.append(X.cpu().numpy())
+        sv.close()
+        prob.close()
+    probs = [api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=0) for wl, obs, _ in jobs]
+    svgds = [api.Svgd(x.shape[0], wl.M, p.P, wl.lo, wl.hi, lr=wl.lr) for (wl, _, x), p in zip(jobs, probs)]
+    Xs = [_gpu(x) for _, _, x in jobs]
+    b = api.Batch(probs, svgds, Xs)
+    b.iterate(iters)
+    torch.cuda.synchronize()
+    for j, (wl, _, _) in enumerate(jobs):
+        width = np.concatenate([wl.hi - wl.lo, np.ones(wl.P - wl.M)])[:, None]
+        dx = np.max(np.abs(Xs[j].cpu().numpy() - alone[j]) / width)
+        assert dx <= 1e-5, (j, dx)
+    b.close()
+
+
+def test_server_runs_rigid_pendulum_jobs():
+    jobs = [(wl, obs, x, 4) for wl, obs, x in _mixed_jobs()]
+    lat, res, _ = serve.run_server(jobs, np.array([0.0, 0.0, 0.01, 0.02]), mem_budget=8 << 30, fast_math=False)
+    _, ref, _ = serve.run_plain(jobs, np.zeros(len(jobs)), fast_math=False)
+    for k, (wl, _, _, _) in enumerate(jobs):
+        width = np.concatenate([wl.hi - wl.lo, np.ones(wl.P - wl.M)])
+        assert np.max(np.abs(res[k][0] - ref[k][0]) / width) <= 1e-5, k
+    assert np.all(lat >= 0)
