@@ -630,22 +630,24 @@ static double bandwidth_from_median(int N, double med) {
 
 // phi_i = 1/N sum_j [ k(u_j,u_i) g_j + grad_{u_j} k(u_j,u_i) ],
 // k(a,b) = exp(-||a-b||^2 / bw), grad_{u_j} k(u_j,u_i) = (2/bw)(u_i-u_j) k.
-static void svgd_phi(int N, int M, const double* u, const double* g, double bw, double* phi) {
-  for (int i = 0; i < N; ++i) {
-    for (int k = 0; k < M; ++k) phi[(size_t)i * M + k] = 0.0;
-    for (int j = 0; j < N; ++j) {
-      double d = 0.0;
-      for (int k = 0; k < M; ++k) {
-        const double e = u[(size_t)i * M + k] - u[(size_t)j * M + k];
-        d += e * e;
-      }
-      const double kij = std::exp(-d / bw);
-      for (int k = 0; k < M; ++k)
-        phi[(size_t)i * M + k] += kij * g[(size_t)j * M + k] +
-                                  (2.0 / bw) * (u[(size_t)i * M + k] - u[(size_t)j * M + k]) * kij;
+// phi of particle i (Eq. 1): (1/N) sum_j k_ij [g_j + (2/bw)(u_i - u_j)].
+static void svgd_phi_row(int i, int N, int M, const double* u, const double* g, double bw, double* phi_i) {
+  for (int k = 0; k < M; ++k) phi_i[k] = 0.0;
+  for (int j = 0; j < N; ++j) {
+    double d = 0.0;
+    for (int k = 0; k < M; ++k) {
+      const double e = u[(size_t)i * M + k] - u[(size_t)j * M + k];
+      d += e * e;
     }
-    for (int k = 0; k < M; ++k) phi[(size_t)i * M + k] /= N;
+    const double kij = std::exp(-d / bw);
+    for (int k = 0; k < M; ++k)
+      phi_i[k] += kij * g[(size_t)j * M + k] + (2.0 / bw) * (u[(size_t)i * M + k] - u[(size_t)j * M + k]) * kij;
   }
+  for (int k = 0; k < M; ++k) phi_i[k] /= N;
+}
+
+static void svgd_phi(int N, int M, const double* u, const double* g, double bw, double* phi) {
+  for (int i = 0; i < N; ++i) svgd_phi_row(i, N, M, u, g, bw, phi + (size_t)i * M);
 }
 
 // Particles that sit out an SVGD step: any unit-box coordinate or gradient
@@ -1287,6 +1289,16 @@ double orc_bandwidth(int N, double med) { return bandwidth_from_median(N, med); 
 
 int orc_svgd_phi(int N, int M, const double* u, const double* g, double bw, double* phi) {
   svgd_phi(N, M, u, g, bw, phi);
+  return 0;
+}
+
+// phi of the listed particles only: phi [n_rows][M] for rows[r].
+int orc_svgd_phi_rows(int N, int M, const double* u, const double* g, double bw, const int* rows, int n_rows,
+                      double* phi) {
+  for (int r = 0; r < n_rows; ++r) {
+    if (rows[r] < 0 || rows[r] >= N) return -1;
+    svgd_phi_row(rows[r], N, M, u, g, bw, phi + (size_t)r * M);
+  }
   return 0;
 }
 

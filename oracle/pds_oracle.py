@@ -167,6 +167,8 @@ def lib():
             L.orc_armbox_qdd.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, _dp, _dp]
             L.orc_armbox_inertia.argtypes = [ctypes.POINTER(_ArmBox), _dp, _dp]
             L.orc_armbox_simulate.argtypes = [ctypes.POINTER(_ArmBox), _dp, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_svgd_phi_rows.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, ctypes.c_double, _ip, ctypes.c_int,
+                                            _dp]
             L.orc_rigid2_qdd_full.argtypes = [_dp, _dp, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _dp]
             L.orc_rigid2_qdd.argtypes = [_dp, ctypes.c_double, _dp, _dp]
             L.orc_rigid2_simulate.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
@@ -406,6 +408,18 @@ def svgd_phi(u, g, bw):
     g, gp = _d(g)
     out = np.zeros_like(u)
     lib().orc_svgd_phi(u.shape[0], u.shape[1], up, gp, float(bw), out.ctypes.data_as(_dp))
+    return out
+
+
+def svgd_phi_rows(u, g, bw, rows):
+    """phi (Eq. 1) of the particles `rows` only, [len(rows)][M]."""
+    u, up = _d(u)
+    g, gp = _d(g)
+    r, rp = _i(rows)
+    out = np.zeros((len(r), u.shape[1]))
+    rc = lib().orc_svgd_phi_rows(u.shape[0], u.shape[1], up, gp, float(bw), rp, len(r), out.ctypes.data_as(_dp))
+    if rc != 0:
+        raise ValueError("row index out of range")
     return out
 
 

@@ -137,6 +137,32 @@ def test_full_size_chain5_sampled_particles(fast):
     assert_grad_close(g[idx], g_ref, wl.M)
 
 
+def test_maximum_particle_count_and_window_length():
+    """The largest call the API accepts: N = 2^20 particles (2-link chain,
+    T = 24, W = 3; 64 sampled particles, the first and last included), and a
+    window of PDS_MAX_WINDOW_STEPS = 4096 steps (W = 1, 8 particles of a
+    damped single pendulum, whose FP32 and FP64 rollouts stay close over
+    4096 steps, unlike a chaotic double pendulum)."""
+    N = 1 << 20
+    wl = f32_workload(wlmod.random_chain(2, N, seed=77, T=24, W=3))
+    obs = observations(wl)
+    x = particles(wl, obs)
+    lp, g, st = _run(wl, obs, x, K=5)
+    assert np.all(st == 0)
+    rng = np.random.default_rng(9)
+    idx = np.sort(rng.choice(N, 64, replace=False))
+    idx[0], idx[-1] = 0, N - 1
+    lp_ref, g_ref = oracle_problem(wl, obs).loglik_grad(x[idx], threads=16)
+    assert_logp_close(lp[idx], lp_ref)
+    assert_grad_close(g[idx], g_ref, wl.M)
+    wl = f32_workload(wlmod.random_chain(1, 8, seed=78, T=4096, W=1, dt=0.001))
+    obs = observations(wl)
+    _check(wl, obs, particles(wl, obs), K=64)
+    bad = f32_workload(wlmod.random_chain(1, 8, seed=78, T=4097, W=1, dt=0.001))
+    with pytest.raises(api.PdsError):
+        api.Problem.from_workload(bad, np.zeros((bad.T, bad.D), np.float32))
+
+
 def test_deterministic_bitwise():
     wl = f32_workload(wlmod.chain5(N=300, T=100, W=5))
     obs = observations(wl)

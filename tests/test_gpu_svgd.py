@@ -128,6 +128,35 @@ def test_full_size_bandwidth_and_phi():
     assert np.max(np.abs(phi[idx] - full[idx])) <= 2e-3 * scale
 
 
+def test_maximum_size_step():
+    """N = 65536 (the largest SVGD state) and M = 16 (the largest theta):
+    2.1e9 pairs, just under 2^31.  The exact lower median is checked by its
+    rank among 4e5 sampled pairs (within 4 standard deviations of the
+    middle); phi of 32 sampled particles (the last one included) against the
+    oracle's phi of those rows with the GPU's bandwidth."""
+    N, M, P = 65536, 16, 18
+    lo, hi, x, g = _case(N, M, P, seed=21)
+    sv = api.Svgd(N, M, P, lo, hi)
+    bw, phi = sv.step(_gpu(x), _gpu(g), return_phi=True)
+    torch.cuda.synchronize()
+    bw = bw.item()
+    u = (x[:, :M] - lo) / (hi - lo)
+    rng = np.random.default_rng(5)
+    n_s = 400000
+    i = rng.integers(0, N, n_s)
+    j = rng.integers(0, N - 1, n_s)
+    j[j >= i] += 1
+    d = ((u[i] - u[j]) ** 2).sum(axis=1)
+    frac = np.mean(d < bw * np.log(N))
+    assert abs(frac - 0.5) < 4 * 0.5 / np.sqrt(n_s), frac
+    rows = rng.choice(N, 32, replace=False)
+    rows[-1] = N - 1
+    ref = orc.svgd_phi_rows(u, g[:, :M] * (hi - lo), bw, rows)
+    got = phi.cpu().numpy().T[rows]
+    assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(ref))
+    sv.close()
+
+
 def test_svgd_rejects_bad_sizes():
     with pytest.raises(api.PdsError):
         api.Svgd(0, 2, 2, [0, 0], [1, 1])
