@@ -347,7 +347,7 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
 int pds_batch_destroy(pds_batch_t b);
 
 /* Autotuner: for every chain length present, time the batched rollout for
- * checkpoint strides K in {5, 10, 25, 50}, exact or (allow_fast_math) fast
+ * checkpoint strides K in {1, 5, 10, 25, 50}, exact or (allow_fast_math) fast
  * math, and the two largest persistent grid sizes, and keep the fastest.
  * choices: NULL or [4 * number of chain lengths] ints receiving
  * (links, K, fast_math, grid blocks) per chain length.  Synchronises. */

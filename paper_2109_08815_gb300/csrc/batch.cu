@@ -330,7 +330,7 @@ int pds_batch_autotune(pds_batch_t b, int allow_fast_math, int* choices) {
   cudaEvent_t t0, t1;
   cudaEventCreate(&t0);
   cudaEventCreate(&t1);
-  const int Ks[] = {5, 10, 25, 50};
+  const int Ks[] = {1, 5, 10, 25, 50};
   int gi = 0;
   for (Group& g : b->groups) {
     int best_K = g.K, best_fast = g.fast, best_blocks = 0;

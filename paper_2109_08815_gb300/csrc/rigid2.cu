@@ -233,7 +233,32 @@ __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c
   R2ConstBar kb;
   kb.A = kb.J2 = kb.Kx = kb.Ky = kb.P1x = kb.P1y = kb.Lg = kb.P2x = kb.P2y = kb.b1 = kb.b2 = 0.f;
   const int h = t1 - t0;
-  const int nseg = (h + K - 1) / K;
+  if (K == 1) {
+    // every pre-step state is on the tape; the state of step j-1 is loaded
+    // while step j is reversed
+    float x[4], xn[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* c0 = ck + (size_t)(h - 1) * 4 * U + u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) x[q] = c0[(size_t)q * U];
+    for (int j = h - 1; j >= 0; --j) {
+      if (j > 0) {
+        const float* cj = ck + (size_t)(j - 1) * 4 * U + u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xn[q] = cj[(size_t)q * U];
+      }
+      const R2Fwd f = r2_forward<FAST>(k, x);
+      float xa[4] = {x[0], x[1], x[2], x[3]};
+      r2_apply(f, c.dt, xa);
+      const float* row = c.obs + (size_t)(t0 + j) * c.D;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c.obs_col[q] >= 0) a[q] = fmaf(c.inv_so2, __ldg(row + c.obs_col[q]) - xa[q], a[q]);
+      r2_reverse(k, f, x, c.dt, a, kb);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) x[q] = xn[q];
+    }
+  }
+  const int nseg = K == 1 ? 0 : (h + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int ta = sg * K, tb = min(h, ta + K);
     // recompute the segment's pre-step states

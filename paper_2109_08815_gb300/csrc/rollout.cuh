@@ -522,7 +522,28 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   float qh[NL], vh[NL];  // state s_{k+1} (output of the step being reversed)
 #pragma unroll
   for (int j = 0; j < NL; ++j) { qh[j] = q[j]; vh[j] = v[j]; }
-  const int nseg = (h + K - 1) / K;
+  if (K == 1) {
+    // Every pre-step state is on the tape: no recomputation.  The state of
+    // step k-1 is loaded while step k is reversed, so the load's latency
+    // hides behind the step's adjoint.
+    float qs[NL], vs[NL], qn[NL] = {}, vn[NL] = {};
+    tape_load<NL>(ckpt, h - 1, U, u, qs, vs);
+    for (int k = h - 1; k >= 0; --k) {
+      if (k > 0) tape_load<NL>(ckpt, k - 1, U, u, qn, vn);
+      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
+      if constexpr (CS) {
+        StepTape<NL> F;
+        chain_step_recompute<NL, FAST>(qs, vs, P, F);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
+      } else {
+        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
+      }
+#pragma unroll
+      for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; qs[j] = qn[j]; vs[j] = vn[j]; }
+    }
+  }
+  const int nseg = K == 1 ? 0 : (h + K - 1) / K;
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int a = sg * K;
     const int e = min(a + K, h);

@@ -2,12 +2,12 @@
 at a time (for example under ``ncu -k``), on seeded synthetic inputs.
 
     python -m paper_2109_08815_gb300.profile_cases rollout [--n 4096] [--calls 2]
-        pds_loglik_grad on the 5-link damped chain (T = 1000, W = 20, K = 5,
+        pds_loglik_grad on the 5-link damped chain (T = 1000, W = 20, K = 1,
         fast math) with N particles: ``--calls`` launches of rollout_kernel
         and window_reduce_kernel.
 
     python -m paper_2109_08815_gb300.profile_cases csvgd [--n 16384] [--steps 3]
-        constrained SVGD (Sec. IV-E) on the same chain: --steps iterations of
+        constrained SVGD (Sec. IV-E) on the same chain (K = 1): --steps iterations of
         pds_loglik_grad (two adjoints) and pds_svgd_step, multipliers from 0.
 
     python -m paper_2109_08815_gb300.profile_cases svgd [--n 16384] [--m 10] [--steps 3]
@@ -17,7 +17,7 @@ at a time (for example under ``ncu -k``), on seeded synthetic inputs.
 
     python -m paper_2109_08815_gb300.profile_cases rigid2 [--n 4096] [--calls 2]
         pds_loglik_grad on the 11-parameter rigid double pendulum (T = 1000
-        at 400 Hz, W = 10, K = 5, fast math): rigid2_rollout_kernel and
+        at 400 Hz, W = 10, K = 1, fast math): rigid2_rollout_kernel and
         window_reduce_kernel.
 
     python -m paper_2109_08815_gb300.profile_cases sgld [--n 16384] [--steps 3]
@@ -48,7 +48,7 @@ def rollout_case(n: int, calls: int) -> float:
     gen.close()
     x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
     X = torch.from_numpy(np.ascontiguousarray(x0.T, dtype=np.float32)).to(dev)
-    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=1)
+    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=1, fast_math=1)
     logp = torch.empty(n, device=dev)
     G = torch.empty_like(X)
     for _ in range(calls):
@@ -69,7 +69,7 @@ def csvgd_case(n: int, steps: int) -> float:
     obs = wlmod.observations(wl, states[:, :, 0].cpu().numpy().astype(np.float64)).astype(np.float32)
     gen.close()
     x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
-    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=1)
+    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=1, fast_math=1)
     prob.set_csvgd(True, 1.0)
     sv = api.Svgd(n, wl.M, prob.P, wl.lo, wl.hi, lr=wl.lr)
     sv.set_csvgd(wl.W - 1)
@@ -99,7 +99,7 @@ def rigid2_case(n: int, calls: int) -> float:
     gen.close()
     x0 = wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=1)
     X = torch.from_numpy(np.ascontiguousarray(x0.T, dtype=np.float32)).to(dev)
-    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=5, fast_math=1)
+    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=1, fast_math=1)
     logp = torch.empty(n, device=dev)
     G = torch.empty_like(X)
     for _ in range(calls):

@@ -78,7 +78,7 @@ def test_batch_autotuned_iteration_matches_oracle():
     choices = b.autotune(allow_fast_math=True)
     assert len(choices) == len({w.n for w in wls})
     for links, K, fast, blocks in choices:
-        assert K in (5, 10, 25, 50) and fast in (0, 1) and blocks > 0
+        assert K in (1, 5, 10, 25, 50) and fast in (0, 1) and blocks > 0
     b.iterate(1)
     torch.cuda.synchronize()
     for j, w in enumerate(wls):
