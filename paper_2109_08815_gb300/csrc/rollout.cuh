@@ -386,6 +386,16 @@ __device__ __forceinline__ float obs_residual(const ChainParams& c, const float*
   return acc;
 }
 
+// Asynchronous 4-byte copy global -> shared (cp.async), its group commit,
+// and the wait for all but the two newest groups.
+__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src_global) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src_global)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+
 template <int NL>
 __device__ __forceinline__ void tape_store(float* __restrict__ tape, size_t slot, size_t U, size_t u,
                                            const float (&q)[NL], const float (&v)[NL]) {
@@ -522,7 +532,40 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   float qh[NL], vh[NL];  // state s_{k+1} (output of the step being reversed)
 #pragma unroll
   for (int j = 0; j < NL; ++j) { qh[j] = q[j]; vh[j] = v[j]; }
-  if (K == 1) {
+  if (K == 1 && seg) {
+    // Every pre-step state is on the tape: no recomputation.  Each state is
+    // copied into a ring of three shared-memory slots two steps ahead
+    // (cp.async, no registers held), so its load's latency hides behind two
+    // steps' adjoints.
+    auto fetch = [&](int k) {
+      if (k >= 0) {
+        const float* src = ckpt + (size_t)k * (2 * NL) * U + u;
+        float* dst = seg + (size_t)(k % 3) * (2 * NL) * sstride;
+#pragma unroll
+        for (int j = 0; j < 2 * NL; ++j) cp_async4(dst + (size_t)j * sstride, src + (size_t)j * U);
+      }
+      cp_async_commit();
+    };
+    fetch(h - 1);
+    fetch(h - 2);
+    for (int k = h - 1; k >= 0; --k) {
+      fetch(k - 2);
+      cp_async_wait2();  // the group of state k (two groups older than the newest)
+      float qs[NL], vs[NL];
+      tape_load<NL>(seg, (size_t)(k % 3), sstride, 0, qs, vs);
+      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
+      if constexpr (CS) {
+        StepTape<NL> F;
+        chain_step_recompute<NL, FAST>(qs, vs, P, F);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
+        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
+      } else {
+        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
+      }
+#pragma unroll
+      for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
+    }
+  } else if (K == 1) {
     // Every pre-step state is on the tape: no recomputation.  The state of
     // step k-1 is loaded while step k is reversed, so the load's latency
     // hides behind the step's adjoint.
@@ -712,9 +755,10 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
                               int32_t* status, cudaStream_t st) {
   const size_t U = (size_t)N * c.W * c.R;
   const unsigned blocks = (unsigned)((U + 127) / 128);
-  // the reverse sweep's K recomputed states in shared memory when they fit
-  // in the default 48 KB of a block
-  const size_t seg_bytes = (size_t)c.K * 2 * NL * 128 * sizeof(float);
+  // the reverse sweep's K recomputed states (K = 1: a ring of three
+  // prefetched states) in shared memory when they fit in the default 48 KB of
+  // a block
+  const size_t seg_bytes = (size_t)(c.K == 1 ? 3 : c.K) * 2 * NL * 128 * sizeof(float);
   const int seg_smem = (grad && seg_bytes <= 48 * 1024) ? 1 : 0;
   const size_t smem = seg_smem ? seg_bytes : 0;
   if (c.csvgd) {
