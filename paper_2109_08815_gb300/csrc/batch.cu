@@ -17,16 +17,16 @@
 namespace pds {
 
 cudaError_t launch_batch_rollout(int NL, const BatchJob* jobs, const WorkItem* items, int n_items,
-                                 unsigned int* counter, int grad, int fast, int blocks, cudaStream_t st) {
+                                 unsigned int* counter, int grad, int fast, int blocks, int ring, cudaStream_t st) {
   switch (NL) {
-    case 1: return launch_batch_rollout_nl<1>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 2: return launch_batch_rollout_nl<2>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 3: return launch_batch_rollout_nl<3>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 4: return launch_batch_rollout_nl<4>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 5: return launch_batch_rollout_nl<5>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 6: return launch_batch_rollout_nl<6>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 7: return launch_batch_rollout_nl<7>(jobs, items, n_items, counter, grad, fast, blocks, st);
-    case 8: return launch_batch_rollout_nl<8>(jobs, items, n_items, counter, grad, fast, blocks, st);
+    case 1: return launch_batch_rollout_nl<1>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 2: return launch_batch_rollout_nl<2>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 3: return launch_batch_rollout_nl<3>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 4: return launch_batch_rollout_nl<4>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 5: return launch_batch_rollout_nl<5>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 6: return launch_batch_rollout_nl<6>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 7: return launch_batch_rollout_nl<7>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 8: return launch_batch_rollout_nl<8>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -161,7 +161,8 @@ static int build_group(pds_batch* b, Group& g) {
 static cudaError_t launch_group_rollout(Group& g, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
-  return launch_batch_rollout(g.NL, g.d_jobs, g.d_items, g.n_items, g.d_counter, 1, g.fast, g.blocks, st);
+  return launch_batch_rollout(g.NL, g.d_jobs, g.d_items, g.n_items, g.d_counter, 1, g.fast, g.blocks, g.K == 1 ? 1 : 0,
+                              st);
 }
 
 // One iteration of every problem, queued on b->stream with per-problem

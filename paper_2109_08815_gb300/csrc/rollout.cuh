@@ -687,7 +687,9 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_ker
                                                                               const WorkItem* __restrict__ items,
                                                                               int n_items,
                                                                               unsigned int* __restrict__ counter,
-                                                                              int grad) {
+                                                                              int grad, int ring) {
+  // ring: dynamic shared memory holds the K = 1 prefetch ring (three states per thread)
+  extern __shared__ float ring_sh[];
   __shared__ ChainParams cs;
   __shared__ int item;
   constexpr int kWords = sizeof(ChainParams) / sizeof(int);
@@ -705,7 +707,8 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_ker
     __syncthreads();
     const size_t u = (size_t)wi.unit0 + threadIdx.x;
     const int N = job->N;
-    if (u < (size_t)N * cs.W) rollout_unit<NL, FAST>(cs, job->X, N, job->parts, grad, job->status, u);
+    float* seg = (ring && cs.K == 1) ? ring_sh + threadIdx.x : nullptr;
+    if (u < (size_t)N * cs.W) rollout_unit<NL, FAST>(cs, job->X, N, job->parts, grad, job->status, u, seg, blockDim.x);
     __syncthreads();
   }
 }
@@ -722,11 +725,12 @@ int batch_rollout_blocks_per_sm_nl(int fast) {
 
 template <int NL>
 cudaError_t launch_batch_rollout_nl(const BatchJob* jobs, const WorkItem* items, int n_items, unsigned int* counter,
-                                    int grad, int fast, int blocks, cudaStream_t st) {
+                                    int grad, int fast, int blocks, int ring, cudaStream_t st) {
+  const size_t smem = ring ? (size_t)3 * 2 * NL * 128 * sizeof(float) : 0;
   if (fast)
-    batch_rollout_kernel<NL, true><<<blocks, 128, 0, st>>>(jobs, items, n_items, counter, grad);
+    batch_rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(jobs, items, n_items, counter, grad, ring);
   else
-    batch_rollout_kernel<NL, false><<<blocks, 128, 0, st>>>(jobs, items, n_items, counter, grad);
+    batch_rollout_kernel<NL, false><<<blocks, 128, smem, st>>>(jobs, items, n_items, counter, grad, ring);
   return cudaGetLastError();
 }
 
