@@ -175,9 +175,11 @@ int pds_problem_destroy(pds_problem_t p);
  * pds_problem_set_csvgd / pds_problem_set_trajectories change it). */
 int pds_problem_layout(pds_problem_t p, int* M, int* S, int* P);
 
-/* Adjoint checkpoint stride K (default 10): the reverse sweep keeps one
+/* Adjoint checkpoint stride K (default 1): the reverse sweep keeps one
  * state every K steps and recomputes the states in between (the gradient is
- * the same for every K up to rounding).  1 <= K <= PDS_MAX_WINDOW_STEPS. */
+ * the same for every K up to rounding).  K = 1 keeps every state
+ * (T x 2n x N floats of device memory per problem) and recomputes nothing;
+ * larger K trades recomputation for memory.  1 <= K <= PDS_MAX_WINDOW_STEPS. */
 int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
 
 /* Tuning options of a problem (pds_problem_set_option / _get_option):
@@ -379,7 +381,7 @@ typedef struct pds_server* pds_server_t;
 int pds_server_create(size_t mem_budget_bytes, int max_active, void* cuda_stream, pds_server_t* out);
 int pds_server_destroy(pds_server_t s);
 /* Checkpoint stride and math variant of the rollouts of jobs admitted from
- * now on (defaults 5 and fast math). */
+ * now on (defaults 1 and fast math). */
 int pds_server_set_rollout_options(pds_server_t s, int checkpoint_stride, int fast_math);
 /* Arguments as pds_problem_create plus N particles (host [P][N], copied),
  * the Adam learning rate and the number of SVGD iterations.  Fails with

@@ -616,7 +616,7 @@ class Server:
                "pds_server_create")
         self._h = h
         if checkpoint_stride is not None or fast_math is not None:
-            _check(L.pds_server_set_rollout_options(h, int(checkpoint_stride or 5), int(1 if fast_math is None
+            _check(L.pds_server_set_rollout_options(h, int(checkpoint_stride or 1), int(1 if fast_math is None
                                                                                          else bool(fast_math))),
                    "pds_server_set_rollout_options")
         self._shapes = {}

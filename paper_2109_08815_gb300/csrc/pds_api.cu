@@ -185,7 +185,7 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
   ChainParams c;
   memset(&c, 0, sizeof(c));
   c.n = n; c.M = M; c.T = T; c.W = windows; c.D = D; c.S = 2 * n; c.P = M + (windows - 1) * 2 * n;
-  c.K = 10;
+  c.K = 1;
   c.dt = (float)dt;
   c.g = (float)sys->gravity;
   c.inv_so2 = (float)(1.0 / (sigma_obs * sigma_obs));

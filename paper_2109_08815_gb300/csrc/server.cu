@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(256) gate_unit_kernel(const float* __restrict_
 struct pds_server {
   size_t budget = 0, in_use = 0;
   int max_active = 0;
-  int K = 5, fast = 1;
+  int K = 1, fast = 1;
   cudaStream_t stream = nullptr;
   long long next_id = 1;
   std::deque<long long> queue;

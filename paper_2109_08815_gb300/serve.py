@@ -20,7 +20,7 @@ def poisson_arrivals(n_jobs: int, rate: float, seed: int) -> np.ndarray:
     return np.cumsum(rng.exponential(1.0 / rate, size=n_jobs))
 
 
-def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, fast_math=True, stream=None,
+def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=1, fast_math=True, stream=None,
                gate=None, iters_out=None):
     """Continuous batching: submit each job at its arrival time, tick the
     server until every job is done.  Returns (latencies [s], results, wall).
@@ -65,7 +65,7 @@ def run_server(jobs, arrivals, mem_budget, max_active=256, checkpoint_stride=5, 
     return lat, results, wall
 
 
-def run_plain(jobs, arrivals, checkpoint_stride=5, fast_math=True, stream=None):
+def run_plain(jobs, arrivals, checkpoint_stride=1, fast_math=True, stream=None):
     """Baseline: one job at a time in arrival order, one kernel launch
     sequence per iteration (pds_iterate), no graph and no cross-job batching."""
     n = len(jobs)
