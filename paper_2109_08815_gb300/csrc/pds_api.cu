@@ -429,6 +429,7 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   cudaError_t e = cudaSuccess;
   if ((s->w.cand_cap && (e = cudaMalloc(&s->w.cand, s->w.cand_cap * sizeof(float))) != cudaSuccess) ||
       (s->w.cand_cap && (e = cudaMalloc(&s->w.samp, svgd_sample_size() * sizeof(float))) != cudaSuccess) ||
+      (s->w.cand_cap && (e = cudaMalloc(&s->w.cbuf, svgd_cbin_capacity() * sizeof(float))) != cudaSuccess) ||
       (N >= 256 && (e = cudaMalloc(&s->w.tc, phi_tc_floats(N, M) * sizeof(float))) != cudaSuccess) ||
       (N >= 2048 && (e = cudaMalloc(&s->w.mimg, median_tc_floats(N, M) * sizeof(float))) != cudaSuccess) ||
       (e = cudaMalloc(&s->w.u, MN * sizeof(float))) != cudaSuccess ||
@@ -484,6 +485,7 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaStreamSynchronize(s->stream);
   cudaFree(s->w.cand);
   cudaFree(s->w.samp);
+  cudaFree(s->w.cbuf);
   cudaFree(s->w.tc);
   cudaFree(s->w.mimg);
   cudaFree(s->w.mwork);

@@ -127,6 +127,10 @@ struct SvgdCtl {
   unsigned int gmax[16];     // max |g_u| per component (float bits); reset at the end of each step
   unsigned int n_live;       // particles with finite coordinates and gradient (the others sit out the step)
   unsigned int live_blocks;  // blocks of the liveness pass that have finished
+  // candidate selection: keys are bit patterns relative to the bracket's
+  // lower end, lob; bins are key >> cshift; cbin the median's bin, ccount
+  // the candidates in it
+  unsigned int lob, cshift, cbin, ccount;
 };
 
 struct SvgdWork {
@@ -137,6 +141,7 @@ struct SvgdWork {
   float* samp;     // sampled pair distances (bracket estimate)
   float* cand;     // candidate distances inside the sampled bracket
   unsigned long long cand_cap;
+  float* cbuf;     // candidates of the median's bin (svgd_cbin_capacity floats)
   float* u;        // [M][N] unit-box coordinates
   float* gu;       // [M][N] gradient in unit-box coordinates
   float* phi_part; // [chunks][M][N] partial phi sums
@@ -150,6 +155,7 @@ cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, 
                              float* phi_out, cudaStream_t st, int* launches);
 int svgd_phi_chunks(int N);
 unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
+int svgd_cbin_capacity();
 int svgd_sample_size();
 size_t phi_tc_floats(int N, int M);
 size_t median_tc_floats(int N, int M);

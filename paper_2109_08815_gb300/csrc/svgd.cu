@@ -367,6 +367,13 @@ __global__ void __launch_bounds__(kSampleThreads) median_sample_sort_kernel(cons
   if (threadIdx.x == 0) {
     ctl->lo = __uint_as_float(prefix[0]);
     ctl->hi = __uint_as_float(prefix[1]);
+    // candidates are max(d, 0) in [max(lo, 0), hi]: keys relative to the
+    // lower end span at most 2^32; 2048 bins of key >> cshift cover them
+    const unsigned int lob = __float_as_uint(fmaxf(__uint_as_float(prefix[0]), 0.f));
+    const unsigned int span = prefix[1] >= lob ? prefix[1] - lob : 0u;
+    const int bits = 32 - __clz(span);
+    ctl->lob = lob;
+    ctl->cshift = bits > 11 ? (unsigned int)(bits - 11) : 0u;
   }
 }
 
@@ -513,6 +520,176 @@ __global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __re
   for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
     const unsigned int h = hist[b];
     if (h) atomicAdd(&ctl->hist[b], h);
+  }
+}
+
+// ---- selection among the candidates by keys relative to the bracket ------
+// One histogram pass of key >> cshift (2048 bins), the bin that holds the
+// rank, a compaction of that bin's candidates, and an exact radix select
+// over the remaining cshift low bits in one block.  The same median as three
+// radix passes over the candidates' full bit patterns.
+constexpr int kCbinCap = 1 << 20;  // compacted candidates of the median's bin (floats)
+
+int svgd_cbin_capacity() { return kCbinCap; }
+
+__device__ __forceinline__ unsigned int cand_key(float v, unsigned int lob) { return __float_as_uint(v) - lob; }
+
+__global__ void __launch_bounds__(256) median_cand_key_hist_kernel(const float* __restrict__ cand,
+                                                                   SvgdCtl* __restrict__ ctl) {
+  __shared__ unsigned int hist[kHistBins];
+  if (ctl->mode != 0) return;
+  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hist[b] = 0u;
+  __syncthreads();
+  const unsigned long long n = ctl->inside;
+  const unsigned int lob = ctl->lob, sh = ctl->cshift;
+  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long n4 = n / 4;
+  const float4* c4 = reinterpret_cast<const float4*>(cand);
+  auto add = [&](float v) { atomicAdd(&hist[min(cand_key(v, lob) >> sh, (unsigned int)kHistBins - 1u)], 1u); };
+  unsigned long long k = tid;
+  for (; k + stride < n4; k += 2 * stride) {
+    const float4 a = __ldg(c4 + k), b = __ldg(c4 + k + stride);
+    add(a.x); add(a.y); add(a.z); add(a.w);
+    add(b.x); add(b.y); add(b.z); add(b.w);
+  }
+  if (k < n4) {
+    const float4 a = __ldg(c4 + k);
+    add(a.x); add(a.y); add(a.z); add(a.w);
+  }
+  for (unsigned long long e = 4 * n4 + tid; e < n; e += stride) add(__ldg(cand + e));
+  __syncthreads();
+  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
+    const unsigned int h = hist[b];
+    if (h) atomicAdd(&ctl->hist[b], h);
+  }
+}
+
+// The bin holding the rank (one warp); clears the histogram and the bin count.
+__global__ void median_cand_bin_kernel(SvgdCtl* __restrict__ ctl) {
+  if (ctl->mode != 0) return;
+  const int lane = threadIdx.x;
+  unsigned int local = 0u;
+  for (int b = 0; b < 64; ++b) local += ctl->hist[lane * 64 + b];
+  unsigned int incl = local;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += o;
+  }
+  const unsigned int excl = incl - local;
+  const unsigned int rank = ctl->rank;
+  __syncwarp();
+  if (rank >= excl && rank < incl) {
+    unsigned int cum = excl;
+    int bin = lane * 64;
+    for (int b = 0; b < 64; ++b) {
+      const unsigned int h = ctl->hist[lane * 64 + b];
+      if (rank < cum + h) { bin = lane * 64 + b; break; }
+      cum += h;
+    }
+    ctl->cbin = (unsigned int)bin;
+    ctl->rank = rank - cum;
+    ctl->ccount = 0u;
+  }
+  __syncwarp();
+  for (int b = 0; b < 64; ++b) ctl->hist[lane * 64 + b] = 0u;
+}
+
+// Candidates of the median's bin into cbuf (up to its capacity; ccount
+// counts them all).
+__global__ void __launch_bounds__(256) median_cand_compact_kernel(const float* __restrict__ cand,
+                                                                  SvgdCtl* __restrict__ ctl,
+                                                                  float* __restrict__ cbuf) {
+  if (ctl->mode != 0) return;
+  const unsigned long long n = ctl->inside;
+  const unsigned int lob = ctl->lob, sh = ctl->cshift, bin = ctl->cbin;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  const unsigned long long n_up = (n + 31) / 32 * 32;  // whole warps in the loop
+  const int lane = threadIdx.x & 31;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_up;
+       e += stride) {
+    const bool in = e < n;
+    const float v = in ? __ldg(cand + e) : 0.f;
+    const bool mine = in && min(cand_key(v, lob) >> sh, (unsigned int)kHistBins - 1u) == bin;
+    const unsigned int ballot = __ballot_sync(0xffffffffu, mine);
+    if (ballot) {
+      unsigned int base = 0u;
+      if (lane == 0) base = atomicAdd(&ctl->ccount, (unsigned int)__popc(ballot));
+      base = __shfl_sync(0xffffffffu, base, 0);
+      const unsigned int pos = base + (unsigned int)__popc(ballot & ((1u << lane) - 1u));
+      if (mine && pos < (unsigned int)kCbinCap) cbuf[pos] = v;
+    }
+  }
+}
+
+// Exact rank-th smallest key of the median's bin: radix passes of up to 11
+// bits over the cshift low bits, in one block; reads the compacted bin, or
+// (if it overflowed cbuf) filters all candidates.  Sets the median and the
+// bandwidth over the live particles.
+constexpr int kFinalThreads = 1024;
+__global__ void __launch_bounds__(kFinalThreads) median_cand_final_kernel(const float* __restrict__ cand,
+                                                                          const float* __restrict__ cbuf,
+                                                                          SvgdCtl* __restrict__ ctl) {
+  __shared__ unsigned int hist[kHistBins];
+  __shared__ unsigned int s_prefix, s_rank;
+  if (ctl->mode != 0) return;
+  const unsigned int lob = ctl->lob, sh = ctl->cshift, bin = ctl->cbin;
+  const unsigned int cnt = ctl->ccount;
+  const bool compact = cnt <= (unsigned int)kCbinCap;
+  const float* src = compact ? cbuf : cand;
+  const unsigned long long n = compact ? (unsigned long long)cnt : ctl->inside;
+  if (threadIdx.x == 0) {
+    s_prefix = 0u;
+    s_rank = ctl->rank;
+  }
+  int done = 0;  // low bits resolved so far
+  while (done < (int)sh) {
+    const int d = min(11, (int)sh - done);  // digit width
+    const int lowsh = (int)sh - done - d;   // shift of this digit within the key
+    for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    const unsigned int prefix = s_prefix;
+    for (unsigned long long e = threadIdx.x; e < n; e += blockDim.x) {
+      const unsigned int key = cand_key(__ldg(src + e), lob);
+      if (min(key >> sh, (unsigned int)kHistBins - 1u) != bin) continue;
+      const unsigned int low = key & ((sh < 32 ? (1u << sh) : 0u) - 1u);
+      if ((low >> (lowsh + d)) != prefix) continue;
+      atomicAdd(&hist[(low >> lowsh) & ((1u << d) - 1u)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      unsigned int local = 0u;
+      for (int b = 0; b < 64; ++b) local += hist[lane * 64 + b];
+      unsigned int incl = local;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      const unsigned int excl = incl - local;
+      const unsigned int rank = s_rank;
+      if (rank >= excl && rank < incl) {
+        unsigned int cum = excl;
+        int digit = lane * 64;
+        for (int b = 0; b < 64; ++b) {
+          if (rank < cum + hist[lane * 64 + b]) { digit = lane * 64 + b; break; }
+          cum += hist[lane * 64 + b];
+        }
+        s_rank = rank - cum;
+        s_prefix = (prefix << d) | (unsigned int)digit;
+      }
+    }
+    __syncthreads();
+    done += d;
+  }
+  if (threadIdx.x == 0) {
+    const unsigned int key = (bin << sh) | s_prefix;
+    const float med = __uint_as_float(lob + key);
+    ctl->med = med;
+    const unsigned int nl = ctl->n_live;
+    ctl->bw = (med > 0.f && nl > 1) ? med / logf((float)nl) : 1.0f;
   }
 }
 
@@ -702,10 +879,19 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
       }
       median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);
       n += 1;
-      for (int pass = 0; pass < 3; ++pass) {
-        median_cand_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, pass);
-        median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 0);
-        n += 2;
+      if (w.cbuf) {
+        // one pass of keys relative to the bracket, then the median's bin
+        median_cand_key_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl);
+        median_cand_bin_kernel<<<1, 32, 0, st>>>(w.ctl);
+        median_cand_compact_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, w.cbuf);
+        median_cand_final_kernel<<<1, kFinalThreads, 0, st>>>(w.cand, w.cbuf, w.ctl);
+        n += 4;
+      } else {
+        for (int pass = 0; pass < 3; ++pass) {
+          median_cand_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, pass);
+          median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 0);
+          n += 2;
+        }
       }
     }
     // full passes over all pairs: always for small N or when asked, otherwise
