@@ -597,7 +597,8 @@ __global__ void median_cand_bin_kernel(SvgdCtl* __restrict__ ctl) {
 }
 
 // Candidates of the median's bin into cbuf (up to its capacity; ccount
-// counts them all).
+// counts them all).  Each thread takes 4 consecutive candidates (one float4)
+// per iteration; a warp reserves its slots with one atomic.
 __global__ void __launch_bounds__(256) median_cand_compact_kernel(const float* __restrict__ cand,
                                                                   SvgdCtl* __restrict__ ctl,
                                                                   float* __restrict__ cbuf) {
@@ -605,20 +606,44 @@ __global__ void __launch_bounds__(256) median_cand_compact_kernel(const float* _
   const unsigned long long n = ctl->inside;
   const unsigned int lob = ctl->lob, sh = ctl->cshift, bin = ctl->cbin;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long n_up = (n + 31) / 32 * 32;  // whole warps in the loop
+  const unsigned long long groups = (n + 3) / 4;
+  const unsigned long long groups_up = (groups + 31) / 32 * 32;  // whole warps in the loop
   const int lane = threadIdx.x & 31;
-  for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < n_up;
-       e += stride) {
-    const bool in = e < n;
-    const float v = in ? __ldg(cand + e) : 0.f;
-    const bool mine = in && min(cand_key(v, lob) >> sh, (unsigned int)kHistBins - 1u) == bin;
-    const unsigned int ballot = __ballot_sync(0xffffffffu, mine);
-    if (ballot) {
+  const float4* c4 = reinterpret_cast<const float4*>(cand);
+  const unsigned long long n4 = n / 4;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < groups_up; g += stride) {
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (g < n4) {
+      const float4 a = __ldg(c4 + g);
+      v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if (g < groups) {
+      for (int q = 0; q < 4; ++q)
+        if (4 * g + q < n) v[q] = __ldg(cand + 4 * g + q);
+    }
+    unsigned int mask = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (g < groups && 4 * g + q < n && min(cand_key(v[q], lob) >> sh, (unsigned int)kHistBins - 1u) == bin)
+        mask |= 1u << q;
+    const unsigned int mine = __popc(mask);
+    unsigned int incl = mine;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
+      if (lane >= off) incl += o;
+    }
+    const unsigned int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (total) {
       unsigned int base = 0u;
-      if (lane == 0) base = atomicAdd(&ctl->ccount, (unsigned int)__popc(ballot));
-      base = __shfl_sync(0xffffffffu, base, 0);
-      const unsigned int pos = base + (unsigned int)__popc(ballot & ((1u << lane) - 1u));
-      if (mine && pos < (unsigned int)kCbinCap) cbuf[pos] = v;
+      if (lane == 31) base = atomicAdd(&ctl->ccount, total);
+      base = __shfl_sync(0xffffffffu, base, 31);
+      unsigned int pos = base + incl - mine;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (mask & (1u << q)) {
+          if (pos < (unsigned int)kCbinCap) cbuf[pos] = v[q];
+          ++pos;
+        }
     }
   }
 }
