@@ -472,57 +472,6 @@ __global__ void median_resolve_kernel(SvgdCtl* __restrict__ ctl, unsigned long l
   }
 }
 
-// Radix pass over the candidates (mode 0 only).  The candidates all lie in
-// the bracket, so runs of them share a bin (in the first pass nearly all of
-// them): each thread counts a run of equal bins in a register and adds it to
-// the shared histogram once.  Loads are float4, two in flight per thread.
-__global__ void __launch_bounds__(256) median_cand_hist_kernel(const float* __restrict__ cand,
-                                                               SvgdCtl* __restrict__ ctl, int pass) {
-  __shared__ unsigned int hist[kHistBins];
-  if (ctl->mode != 0) return;
-  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hist[b] = 0u;
-  __syncthreads();
-  const unsigned long long n = ctl->inside;
-  const unsigned int prefix = ctl->prefix;
-  unsigned int run_bin = 0u, run = 0u;
-  auto add = [&](float v) {
-    const unsigned int bits = __float_as_uint(v);
-    unsigned int bin;
-    if (pass == 0) bin = bits >> 21;
-    else if (pass == 1) bin = ((bits >> 21) == prefix) ? ((bits >> 10) & 2047u) : 0xFFFFFFFFu;
-    else bin = ((bits >> 10) == prefix) ? (bits & 1023u) : 0xFFFFFFFFu;
-    if (bin == 0xFFFFFFFFu) return;
-    if (run && bin == run_bin) {
-      ++run;
-    } else {
-      if (run) atomicAdd(&hist[run_bin], run);
-      run_bin = bin;
-      run = 1u;
-    }
-  };
-  const unsigned long long tid = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long n4 = n / 4;
-  const float4* c4 = reinterpret_cast<const float4*>(cand);
-  unsigned long long k = tid;
-  for (; k + stride < n4; k += 2 * stride) {
-    const float4 a = __ldg(c4 + k), b = __ldg(c4 + k + stride);
-    add(a.x); add(a.y); add(a.z); add(a.w);
-    add(b.x); add(b.y); add(b.z); add(b.w);
-  }
-  if (k < n4) {
-    const float4 a = __ldg(c4 + k);
-    add(a.x); add(a.y); add(a.z); add(a.w);
-  }
-  for (unsigned long long e = 4 * n4 + tid; e < n; e += stride) add(__ldg(cand + e));
-  if (run) atomicAdd(&hist[run_bin], run);
-  __syncthreads();
-  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) {
-    const unsigned int h = hist[b];
-    if (h) atomicAdd(&ctl->hist[b], h);
-  }
-}
-
 // ---- selection among the candidates by keys relative to the bracket ------
 // One histogram pass of key >> cshift (2048 bins), the bin that holds the
 // rank, a compaction of that bin's candidates, and an exact radix select
@@ -872,7 +821,7 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
                                   float* phi_out, cudaStream_t st, int* launches) {
   const int N = sp.N, M = sp.M;
   int n = 0;
-  const bool bracket = (N >= 2) && w.cand && w.cand_cap > 0;
+  const bool bracket = (N >= 2) && w.cand && w.cbuf && w.cand_cap > 0;
   {
     const int total = (M * N > kHistBins) ? M * N : kHistBins;
     svgd_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
@@ -903,21 +852,12 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
         n += 1;
       }
       median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);
-      n += 1;
-      if (w.cbuf) {
-        // one pass of keys relative to the bracket, then the median's bin
-        median_cand_key_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl);
-        median_cand_bin_kernel<<<1, 32, 0, st>>>(w.ctl);
-        median_cand_compact_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, w.cbuf);
-        median_cand_final_kernel<<<1, kFinalThreads, 0, st>>>(w.cand, w.cbuf, w.ctl);
-        n += 4;
-      } else {
-        for (int pass = 0; pass < 3; ++pass) {
-          median_cand_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, pass);
-          median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 0);
-          n += 2;
-        }
-      }
+      // one pass of keys relative to the bracket, then the median's bin
+      median_cand_key_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl);
+      median_cand_bin_kernel<<<1, 32, 0, st>>>(w.ctl);
+      median_cand_compact_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, w.cbuf);
+      median_cand_final_kernel<<<1, kFinalThreads, 0, st>>>(w.cand, w.cbuf, w.ctl);
+      n += 5;
     }
     // full passes over all pairs: always for small N or when asked, otherwise
     // only if the bracket missed (the kernels return at once in that case)
