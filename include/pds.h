@@ -278,7 +278,9 @@ int pds_svgd_destroy(pds_svgd_t s);
  * if the bracket misses); 1 = always three radix passes over all pairs.
  * Both give the same exact median.  PDS_OPT_PHI_CUDA_CORES 0 (default) = for
  * N >= 256 the kernel-matrix products of phi run on the tensor cores
- * (tcgen05, tf32 with split operands, fp32 accumulation); 1 = CUDA cores. */
+ * (tcgen05: the exponent product in tf32 with split operands, the product of
+ * the kernel values with the gradients and coordinates in fp16 with split
+ * operands; fp32 accumulation); 1 = CUDA cores. */
 #define PDS_OPT_MEDIAN_FULL_PASSES 3
 #define PDS_OPT_PHI_CUDA_CORES 4
 /* PDS_OPT_MEDIAN_CUDA_CORES 0 (default) = for N >= 2048 the pair distances of
