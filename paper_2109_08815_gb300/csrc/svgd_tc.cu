@@ -16,16 +16,19 @@
 //
 // The kernel is persistent and warp-specialised: one CTA per SM takes the
 // contiguous run [b T / G, (b+1) T / G) of the T = (N/128)^2 tiles (row tile
-// I, column tile J) in row-major order.  An issuer warp streams the column
-// tiles' operands through three shared-memory stages (bulk async copies),
-// issues the exponent product of tile k+1 into one of two TMEM exponent
-// buffers while sixteen exponent warps turn tile k into kernel values in the
-// other, and then issues the second product of tile k into one of two TMEM
-// output accumulators.  When a CTA's run leaves a row tile, four of the
-// exponent warps read that row's accumulator and write its partial phi to
-// the slot (CTA index - first CTA of the row); the last CTA of a row zeroes
-// the slots no CTA used, and the Adam kernel adds the slots in a fixed
-// order, so the result is deterministic.
+// I, column tile J) in row-major order.  A producer warp streams the column
+// tiles' operands through up to six shared-memory stages (bulk async copies);
+// an issuer warp issues the exponent product of tile k+1 into one of the TMEM
+// exponent buffers while sixteen exponent warps turn tile k into kernel
+// values in another, and then issues the second product of tile k into one
+// of two TMEM output accumulators.  The issuer does nothing else: one thread
+// issues every instruction of the tensor pipe, so its own latency sets the
+// pace (row and column of a tile are counted on, never divided out, and the
+// descriptors are offsets from one base).  When a CTA's run leaves a row
+// tile, four of the exponent warps read that row's accumulator and write its
+// partial phi to the slot (CTA index - first CTA of the row); the last CTA of
+// a row zeroes the slots no CTA used, and the Adam kernel adds the slots in a
+// fixed order, so the result is deterministic.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -72,7 +75,11 @@ struct TcSmem {
   static constexpr int kA = kTcRows * KA * 4;     // one operand tile (128 rows x KA), bytes
   static constexpr int kV = NV * kTcRows * 2;  // one v^T tile in fp16 (high and low parts), bytes
   static constexpr int kStage = 2 * kA + kV;  // b (hi, lo) + v^T of one column tile
-  static constexpr int kStages = (2 * 2 * kA + 3 * kStage + 256 <= 220 * 1024) ? 3 : 2;
+  // as many stages as fit (at most 6): the copy of tile k + S - 1 starts when
+  // the second product of tile k - 1 frees its stage, so S >= 4 hides its
+  // latency behind at least two tiles of work
+  static constexpr int kFit = (220 * 1024 - 2 * 2 * kA - 256) / kStage;
+  static constexpr int kStages = kFit > 6 ? 6 : (kFit < 2 ? 2 : kFit);
   static constexpr int kBytes = 2 * 2 * kA + kStages * kStage + 256;  // two a slots, the stages, barriers
 };
 
@@ -148,8 +155,10 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
   for (int c = 4 * MM + 1; c < NV; ++c) V[kmajor_offset16(c, r, kTcRows) >> 1] = __float2half_rn(0.f);
 }
 
-constexpr int kPhiExpWarps = 16;                    // 4 lane quarters x 4 column quarters
-constexpr int kPhiThreads = 32 * (kPhiExpWarps + 1);  // + the issuer warp
+constexpr int kPhiExpWarps = 16;                      // 4 lane quarters x 4 column quarters
+constexpr int kPhiIssuer = kPhiExpWarps;              // warp issuing the products
+constexpr int kPhiProducer = kPhiExpWarps + 1;        // warp streaming the operands
+constexpr int kPhiThreads = 32 * (kPhiExpWarps + 2);
 constexpr int kPhiEpiWarp0 = 12;                      // warps 12..15 (column quarter 3) read the outputs
 
 // First CTA whose run [b T / G, (b+1) T / G) contains tile x.
@@ -172,13 +181,15 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
   unsigned char* sA = smem;                       // two a slots (hi | lo), by row parity
   unsigned char* sStage = smem + 2 * 2 * SM::kA;  // S stages of (b hi | b lo | v hi | v lo)
   uint64_t* bars = (uint64_t*)(sStage + S * SM::kStage);
-  uint64_t* full = bars;         // [S]   operands of a tile landed
-  uint64_t* g_done = bars + 3;   // [NE]  exponent product done
-  uint64_t* p_ready = bars + 6;  // [NE]  kernel values written (16 warps)
-  uint64_t* pv_done = bars + 9;  // [NE]  second product done
-  uint64_t* o_ready = bars + 12; // [2]   a row segment's outputs complete
-  uint64_t* o_free = bars + 14;  // [2]   a row segment's outputs read (4 warps)
-  uint32_t* tslot = (uint32_t*)(bars + 16);
+  uint64_t* full = bars;             // [S]   operands of a tile landed
+  uint64_t* s_free = full + S;       // [S]   a stage's second product done (the stage may be refilled)
+  uint64_t* g_done = s_free + S;     // [NE]  exponent product done
+  uint64_t* p_ready = g_done + NE;   // [NE]  kernel values written (16 warps)
+  uint64_t* pv_done = p_ready + NE;  // [NE]  second product done
+  uint64_t* o_ready = pv_done + NE;  // [2]   a row segment's outputs complete
+  uint64_t* o_free = o_ready + 2;    // [2]   a row segment's outputs read (4 warps)
+  uint32_t* tslot = (uint32_t*)(o_free + 2);
+  static_assert((2 * 6 + 3 * 3 + 4) * 8 + 4 <= 256, "barriers exceed their 256 bytes");
 
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int nt = Npad / kTcRows;
@@ -187,9 +198,18 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
   const int f0 = (int)(((long long)blockIdx.x * T) / G);
   const int f1 = (int)(((long long)(blockIdx.x + 1) * T) / G);
   const int nk = f1 - f0;
+  const int I0 = f0 / nt, J0 = f0 % nt;  // first tile's row and column; later tiles are counted on
+  // Stages in use.  The copy of a row's first tile rewrites the a slot of the
+  // row two back; the ring orders that copy after the products of tile
+  // (that tile - Se + 1), which cover every tile of the row two back when
+  // Se <= nt + 2.
+  const int Se = S < nt + 2 ? S : nt + 2;
 
   if (t == 0) {
-    for (int b = 0; b < S; ++b) tc::mbar_init(full + b, 1);
+    for (int b = 0; b < S; ++b) {
+      tc::mbar_init(full + b, 1);
+      tc::mbar_init(s_free + b, 1);
+    }
     for (int b = 0; b < NE; ++b) {
       tc::mbar_init(g_done + b, 1);
       tc::mbar_init(p_ready + b, kPhiExpWarps);
@@ -206,68 +226,98 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
   tc::fence_after();
   const uint32_t tbase = *tslot;
   bool ok = true;
+  // waits that are usually already complete test the barrier first
+  auto wait = [&](uint64_t* bar, uint32_t parity) {
+    return tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
+  };
 
-  if (warp == kPhiExpWarps) {
+  if (warp == kPhiProducer) {
+    // ------------------------------------------------------------ producer
+    // operands of tile k into stage k mod Se once the second product of tile
+    // k - Se left it (a with the row's first tile)
+    if (lane == 0 && nk > 0) {
+      int I = I0, J = J0, st = 0, last = -1;
+      uint32_t ph = 0;  // parity of this use of stage st: (k / Se) & 1
+      for (int k = 0; k < nk; ++k) {
+        if (k >= Se && !wait(s_free + st, ph ^ 1u)) {
+          ok = false;
+          break;
+        }
+        const bool needA = (k == 0) || (J == 0);
+        tc::mbar_expect_tx(full + st, SM::kStage + (needA ? 2 * SM::kA : 0));
+        if (needA)
+          tc::bulk_g2s(sA + ((I - I0) & 1) * 2 * SM::kA, imgA + (size_t)I * (2 * SM::kA / 4), 2 * SM::kA, full + st);
+        tc::bulk_g2s(sStage + st * SM::kStage, imgBV + (size_t)J * (SM::kStage / 4), SM::kStage, full + st);
+        last = k;
+        if (++J == nt) {
+          J = 0;
+          ++I;
+        }
+        if (++st == Se) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (!ok) {
+        ctl->tc_error = 1;
+        // let the copies in flight land (bounded) before shared memory is released
+        for (int k = last - Se + 1 > 0 ? last - Se + 1 : 0; k <= last; ++k)
+          tc::mbar_wait(full + k % Se, (uint32_t)(k / Se) & 1u, kLimit);
+      }
+    }
+  } else if (warp == kPhiIssuer) {
     // ------------------------------------------------------------ issuer
     if (lane == 0 && nk > 0) {
-      const int I0 = f0 / nt;
-      int next_load = 0, last_g = -1, last_pv = -1;
-      auto load = [&](int k) {  // operands of tile f0 + k into stage k % S (a with the row's first tile)
-        const int f = f0 + k, I = f / nt, J = f % nt;
-        unsigned char* stg = sStage + (k % S) * SM::kStage;
-        const bool needA = (k == 0) || (f % nt == 0);
-        tc::mbar_expect_tx(full + k % S, SM::kStage + (needA ? 2 * SM::kA : 0));
-        if (needA)
-          tc::bulk_g2s(sA + ((I - I0) & 1) * 2 * SM::kA, imgA + (size_t)I * (2 * SM::kA / 4), 2 * SM::kA, full + k % S);
-        tc::bulk_g2s(stg, imgBV + (size_t)J * (SM::kStage / 4), SM::kStage, full + k % S);
-        next_load = k + 1;
-      };
-      auto gram = [&](int k) {  // E[k % NE] = a b^T (three split products)
-        const int f = f0 + k, I = f / nt;
+      // shared-memory descriptors: the descriptor of offset 0 plus offset / 16
+      // (shared addresses stay below 2^18, so the 14-bit field never carries)
+      const uint32_t s0 = tc::smem_u32(smem);
+      const uint64_t dG = tc::smem_desc(s0, 128, 32 * KA);       // exponent product operands
+      const uint64_t dV = tc::smem_desc(s0, 128, 16 * kTcRows);  // v^T
+      constexpr uint32_t oA = 0, oS = 2 * 2 * SM::kA;            // offsets of the a slots and the stages
+      int last_g = -1, last_pv = -1;
+      // next exponent product's tile: stage, parity of its copy, a slot, column
+      int gst = 0, gslot = 0, gJ = J0;
+      uint32_t gph = 0;
+      auto gram = [&](int k) {  // E[k % NE] = a b^T (three split products), tile k
         tc::fence_after();
         constexpr uint32_t id = tc::idesc_tf32(128, 128);
-        const uint32_t sbo = 32 * KA;
-        const uint32_t a_h = tc::smem_u32(sA + ((I - I0) & 1) * 2 * SM::kA), a_l = a_h + SM::kA;
-        const uint32_t b_h = tc::smem_u32(sStage + (k % S) * SM::kStage), b_l = b_h + SM::kA;
-        const uint32_t Aop[3] = {a_h, a_h, a_l};
-        const uint32_t Bop[3] = {b_h, b_l, b_h};
+        const uint64_t a_h = dG + ((oA + gslot * 2 * SM::kA) >> 4), a_l = a_h + (SM::kA >> 4);
+        const uint64_t b_h = dG + ((oS + gst * SM::kStage) >> 4), b_l = b_h + (SM::kA >> 4);
+        const uint64_t Aop[3] = {a_h, a_h, a_l};
+        const uint64_t Bop[3] = {b_h, b_l, b_h};
 #pragma unroll
         for (int p = 0; p < 3; ++p)
 #pragma unroll
           for (int ks = 0; ks < KA / 8; ++ks)
-            tc::mma_ss(tbase + 128 * (k % NE), tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
-                       tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
+            tc::mma_ss(tbase + 128 * (k % NE), Aop[p] + ks * 16, Bop[p] + ks * 16, id, (p > 0 || ks > 0) ? 1u : 0u);
         tc::mma_commit(g_done + k % NE);
         last_g = k;
+        if (++gJ == nt) {
+          gJ = 0;
+          gslot ^= 1;
+        }
+        if (++gst == Se) {
+          gst = 0;
+          gph ^= 1u;
+        }
       };
-      // waits that are usually already complete test the barrier first
-      auto wait = [&](uint64_t* bar, uint32_t parity) {
-        return tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
-      };
-      for (int k = 0; k < S && k < nk; ++k) load(k);
       ok = wait(full + 0, 0u);
       if (ok) gram(0);
-      int seg = 0;  // row segment of tile k within this CTA's run
+      int pst = 0, pJ = J0, seg = 0;  // second product's tile: stage, column, row segment
       for (int k = 0; k < nk && ok; ++k) {
-        const int f = f0 + k;
-        if (k > 0 && f % nt == 0) ++seg;
-        // (a) exponent product of tile k+1: its exponent buffer was last read
-        // by the second product of tile k+1-NE (already waited for in (c)
-        // when NE = 3), its operands by now landed
+        if (k > 0 && pJ == 0) ++seg;
+        // (a) exponent product of tile k+1 into buffer (k+1) % NE, last read
+        // by the second product of tile k+1-NE
         if (k + 1 < nk) {
-          if (NE == 2 && k >= 1) ok = wait(pv_done + (k - 1) % NE, (uint32_t)((k - 1) / NE) & 1u);
-          if (ok && next_load == k + 1) {  // fewer stages than needed to prefetch
-            if (k + 1 - S >= 0) ok = wait(pv_done + (k + 1 - S) % NE, (uint32_t)((k + 1 - S) / NE) & 1u);
-            if (ok) load(k + 1);
-          }
-          if (ok) ok = wait(full + (k + 1) % S, (uint32_t)((k + 1) / S) & 1u);
+          if (k + 1 - NE >= 0) ok = wait(pv_done + (k + 1 - NE) % NE, (uint32_t)((k + 1 - NE) / NE) & 1u);
+          if (ok) ok = wait(full + gst, gph);
           if (ok) gram(k + 1);
         }
         // (b) second product of tile k once every exponent warp wrote its
         // kernel values (and the output set was read for segment seg - 2)
         if (ok) ok = wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u);
-        const bool first = (k == 0) || (f % nt == 0);
-        const bool last = (k == nk - 1) || ((f + 1) % nt == 0);
+        const bool first = (k == 0) || (pJ == 0);
+        const bool last = (k == nk - 1) || (pJ == nt - 1);
         if (ok && first && seg >= 2) ok = wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u);
         if (!ok) break;
         tc::fence_after();
@@ -276,29 +326,22 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
           // j; the kernel values of j = 16 ks .. 16 ks + 15 sit packed in
           // columns 32 (ks / 2) + 8 (ks % 2) of the exponent buffer
           constexpr uint32_t id = tc::idesc_f16(128, NV);
-          const uint32_t sbo = 16 * kTcRows;
-          const uint32_t v_h = tc::smem_u32(sStage + (k % S) * SM::kStage + 2 * SM::kA);
+          const uint64_t v_h = dV + ((oS + pst * SM::kStage + 2 * SM::kA) >> 4);
           const uint32_t tE = tbase + 128 * (k % NE), tO = tbase + TcAcc<MM>::kOcol + NV * (seg & 1);
 #pragma unroll
           for (int ks = 0; ks < kTcRows / 16; ++ks)
-            tc::mma_ts_f16(tO, tE + 32 * (ks >> 1) + 8 * (ks & 1), tc::smem_desc(v_h + ks * 256, 128, sbo), id,
-                           (!first || ks > 0) ? 1u : 0u);
+            tc::mma_ts_f16(tO, tE + 32 * (ks >> 1) + 8 * (ks & 1), v_h + ks * 16, id, (!first || ks > 0) ? 1u : 0u);
           tc::mma_commit(pv_done + k % NE);
+          tc::mma_commit(s_free + pst);
           if (last) tc::mma_commit(o_ready + (seg & 1));
           last_pv = k;
         }
-        // (c) the second product of tile k-1 frees exponent buffer (k-1) % NE
-        // and stage (k-1) % S, which takes tile k-1+S
-        if (k >= 1) {
-          ok = wait(pv_done + (k - 1) % NE, (uint32_t)((k - 1) / NE) & 1u);
-          if (ok && next_load == k - 1 + S && k - 1 + S < nk) load(k - 1 + S);
-        }
+        if (++pJ == nt) pJ = 0;
+        if (++pst == Se) pst = 0;
       }
       if (!ok) {
         ctl->tc_error = 1;
-        // let the copies and products already issued finish (bounded) before
-        // shared memory and TMEM are released
-        for (int k = last_pv + 1; k < next_load; ++k) tc::mbar_wait(full + k % S, (uint32_t)(k / S) & 1u, kLimit);
+        // let the products already issued finish (bounded) before TMEM is released
         if (last_g >= 0) tc::mbar_wait(g_done + last_g % NE, (uint32_t)(last_g / NE) & 1u, kLimit);
         if (last_pv >= 0) tc::mbar_wait(pv_done + last_pv % NE, (uint32_t)(last_pv / NE) & 1u, kLimit);
       }
@@ -308,10 +351,9 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
     const int quarter = warp & 3, cq = warp >> 2;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     const bool epi = warp >= kPhiEpiWarp0;
-    int seg = 0;
+    int seg = 0, I = I0, J = J0;  // tile k's row segment, row and column
     for (int k = 0; k < nk; ++k) {
-      const int f = f0 + k;
-      if (k > 0 && f % nt == 0) ++seg;
+      if (k > 0 && J == 0) ++seg;
       const bool w = tc::mbar_wait(g_done + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
       ok = __all_sync(0xffffffffu, w) != 0;
       if (!ok) break;
@@ -334,7 +376,8 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
       tc::fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(p_ready + k % NE);
-      const bool last = (k == nk - 1) || ((f + 1) % nt == 0);
+      const bool row_end = J == nt - 1;
+      const bool last = (k == nk - 1) || row_end;
       if (epi && last) {
         // this row segment's outputs: wait for its last second product, then read them
         const bool w2 = tc::mbar_wait(o_ready + (seg & 1), (uint32_t)(seg >> 1) & 1u, kLimit);
@@ -355,12 +398,10 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(o_free + (seg & 1));
-        const int I = f / nt;
         const int i = I * kTcRows + quarter * 32 + lane;
         // slot of this CTA in row I; the row's last CTA zeroes the unused ones
         const int b0 = phi_tc_first_cta((long long)I * nt, T, G);
         const int slot = blockIdx.x - b0;
-        const bool row_end = (f + 1) % nt == 0;
         if (i < N) {
           const float two_over_bw = 2.0f / ctl->bw;
           const float o1s = o[2 * MM];
@@ -377,6 +418,10 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
             for (int sl = slot + 1; sl < slots; ++sl)
               for (int c = 0; c < M; ++c) phi_part[((size_t)sl * M + c) * N + i] = 0.f;
         }
+      }
+      if (++J == nt) {
+        J = 0;
+        ++I;
       }
     }
     if (!ok && lane == 0) ctl->tc_error = 1;
