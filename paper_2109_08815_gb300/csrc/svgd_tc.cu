@@ -17,14 +17,17 @@
 // The kernel is persistent and warp-specialised: one CTA per SM takes the
 // contiguous run [b T / G, (b+1) T / G) of the T = (N/128)^2 tiles (row tile
 // I, column tile J) in row-major order.  A producer warp streams the column
-// tiles' operands through up to six shared-memory stages (bulk async copies);
-// an issuer warp issues the exponent product of tile k+1 into one of the TMEM
-// exponent buffers while sixteen exponent warps turn tile k into kernel
-// values in another, and then issues the second product of tile k into one
-// of two TMEM output accumulators.  The issuer does nothing else: one thread
-// issues every instruction of the tensor pipe, so its own latency sets the
-// pace (row and column of a tile are counted on, never divided out, and the
-// descriptors are offsets from one base).  When a CTA's run leaves a row
+// tiles' operands through up to six shared-memory stages (bulk async copies).
+// One issuer warp issues the exponent products into the TMEM exponent
+// buffers, running ahead of the sixteen exponent warps that turn them into
+// kernel values in place; a second issuer warp issues each tile's second
+// product into one of two TMEM output accumulators once its kernel values
+// are written.  The products are tiny (tens of cycles of tensor work each),
+// so the issue latency sets the pace: the two issuers work side by side, each
+// runs as a whole converged warp (operands in uniform registers, one lane
+// elected per instruction), and they neither divide nor rebuild descriptors
+// (a tile's row and column are counted on; descriptors are offsets from one
+// base).  When a CTA's run leaves a row
 // tile, four of the exponent warps read that row's accumulator and write its
 // partial phi to the slot (CTA index - first CTA of the row); the last CTA of
 // a row zeroes the slots no CTA used, and the Adam kernel adds the slots in a
@@ -156,9 +159,10 @@ __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restri
 }
 
 constexpr int kPhiExpWarps = 16;                      // 4 lane quarters x 4 column quarters
-constexpr int kPhiIssuer = kPhiExpWarps;              // warp issuing the products
-constexpr int kPhiProducer = kPhiExpWarps + 1;        // warp streaming the operands
-constexpr int kPhiThreads = 32 * (kPhiExpWarps + 2);
+constexpr int kPhiGramWarp = kPhiExpWarps;            // warp issuing the exponent products
+constexpr int kPhiPvWarp = kPhiExpWarps + 1;          // warp issuing the second products
+constexpr int kPhiProducer = kPhiExpWarps + 2;        // warp streaming the operands
+constexpr int kPhiThreads = 32 * (kPhiExpWarps + 3);
 constexpr int kPhiEpiWarp0 = 12;                      // warps 12..15 (column quarter 3) read the outputs
 
 // First CTA whose run [b T / G, (b+1) T / G) contains tile x.
@@ -199,11 +203,12 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
   const int f1 = (int)(((long long)(blockIdx.x + 1) * T) / G);
   const int nk = f1 - f0;
   const int I0 = f0 / nt, J0 = f0 % nt;  // first tile's row and column; later tiles are counted on
-  // Stages in use.  The copy of a row's first tile rewrites the a slot of the
-  // row two back; the ring orders that copy after the products of tile
-  // (that tile - Se + 1), which cover every tile of the row two back when
-  // Se <= nt + 2.
-  const int Se = S < nt + 2 ? S : nt + 2;
+  // Stages in use.  The copy of a row's first tile j rewrites the a slot of
+  // the row two back.  The ring orders that copy after the second product of
+  // tile j - Se, which was issued only once the exponent products of tiles
+  // <= j - Se had completed; the row two back ends at tile j - nt - 1 or
+  // earlier, so Se <= nt + 1 keeps the slot until its last reader is done.
+  const int Se = S < nt + 1 ? S : nt + 1;
 
   if (t == 0) {
     for (int b = 0; b < S; ++b) {
@@ -265,85 +270,84 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
           tc::mbar_wait(full + k % Se, (uint32_t)(k / Se) & 1u, kLimit);
       }
     }
-  } else if (warp == kPhiIssuer) {
-    // ------------------------------------------------------------ issuer
-    if (lane == 0 && nk > 0) {
-      // shared-memory descriptors: the descriptor of offset 0 plus offset / 16
-      // (shared addresses stay below 2^18, so the 14-bit field never carries)
-      const uint32_t s0 = tc::smem_u32(smem);
-      const uint64_t dG = tc::smem_desc(s0, 128, 32 * KA);       // exponent product operands
-      const uint64_t dV = tc::smem_desc(s0, 128, 16 * kTcRows);  // v^T
-      constexpr uint32_t oA = 0, oS = 2 * 2 * SM::kA;            // offsets of the a slots and the stages
-      int last_g = -1, last_pv = -1;
-      // next exponent product's tile: stage, parity of its copy, a slot, column
-      int gst = 0, gslot = 0, gJ = J0;
-      uint32_t gph = 0;
-      auto gram = [&](int k) {  // E[k % NE] = a b^T (three split products), tile k
-        tc::fence_after();
-        constexpr uint32_t id = tc::idesc_tf32(128, 128);
-        const uint64_t a_h = dG + ((oA + gslot * 2 * SM::kA) >> 4), a_l = a_h + (SM::kA >> 4);
-        const uint64_t b_h = dG + ((oS + gst * SM::kStage) >> 4), b_l = b_h + (SM::kA >> 4);
-        const uint64_t Aop[3] = {a_h, a_h, a_l};
-        const uint64_t Bop[3] = {b_h, b_l, b_h};
-#pragma unroll
-        for (int p = 0; p < 3; ++p)
-#pragma unroll
-          for (int ks = 0; ks < KA / 8; ++ks)
-            tc::mma_ss(tbase + 128 * (k % NE), Aop[p] + ks * 16, Bop[p] + ks * 16, id, (p > 0 || ks > 0) ? 1u : 0u);
-        tc::mma_commit(g_done + k % NE);
-        last_g = k;
-        if (++gJ == nt) {
-          gJ = 0;
-          gslot ^= 1;
-        }
-        if (++gst == Se) {
-          gst = 0;
-          gph ^= 1u;
-        }
+  } else if (warp == kPhiGramWarp || warp == kPhiPvWarp) {
+    // ------------------------------------------------------------ issuers
+    if (nk > 0) {
+      auto wait = [&](uint64_t* bar, uint32_t parity) {
+        const bool w = tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
+        return __all_sync(0xffffffffu, w) != 0;
       };
-      ok = wait(full + 0, 0u);
-      if (ok) gram(0);
-      int pst = 0, pJ = J0, seg = 0;  // second product's tile: stage, column, row segment
-      for (int k = 0; k < nk && ok; ++k) {
-        if (k > 0 && pJ == 0) ++seg;
-        // (a) exponent product of tile k+1 into buffer (k+1) % NE, last read
-        // by the second product of tile k+1-NE
-        if (k + 1 < nk) {
-          if (k + 1 - NE >= 0) ok = wait(pv_done + (k + 1 - NE) % NE, (uint32_t)((k + 1 - NE) / NE) & 1u);
-          if (ok) ok = wait(full + gst, gph);
-          if (ok) gram(k + 1);
+      const uint32_t s0 = tc::smem_u32(smem);
+      constexpr uint32_t oA = 0, oS = 2 * 2 * SM::kA;  // offsets of the a slots and the stages
+      int last = -1;
+      if (warp == kPhiGramWarp) {
+        // exponent product of tile k into buffer k % NE once the second
+        // product of tile k - NE left it and the operands landed
+        const uint64_t dG = tc::smem_desc(s0, 128, 32 * KA);
+        int st = 0, slot = 0, J = J0;
+        uint32_t ph = 0;
+        for (int k = 0; k < nk; ++k) {
+          if (k >= NE) ok = wait(pv_done + (k - NE) % NE, (uint32_t)((k - NE) / NE) & 1u);
+          if (ok) ok = wait(full + st, ph);
+          if (!ok) break;
+          tc::fence_after();
+          constexpr uint32_t id = tc::idesc_tf32(128, 128);
+          const uint64_t a_h = dG + ((oA + slot * 2 * SM::kA) >> 4), a_l = a_h + (SM::kA >> 4);
+          const uint64_t b_h = dG + ((oS + st * SM::kStage) >> 4), b_l = b_h + (SM::kA >> 4);
+          const uint64_t Aop[3] = {a_h, a_h, a_l};
+          const uint64_t Bop[3] = {b_h, b_l, b_h};
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int ks = 0; ks < KA / 8; ++ks)
+              tc::mma_ss_el(tbase + 128 * (k % NE), Aop[p] + ks * 16, Bop[p] + ks * 16, id,
+                            (p > 0 || ks > 0) ? 1u : 0u);
+          tc::mma_commit_el(g_done + k % NE);
+          last = k;
+          if (++J == nt) {
+            J = 0;
+            slot ^= 1;
+          }
+          if (++st == Se) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
-        // (b) second product of tile k once every exponent warp wrote its
-        // kernel values (and the output set was read for segment seg - 2)
-        if (ok) ok = wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u);
-        const bool first = (k == 0) || (pJ == 0);
-        const bool last = (k == nk - 1) || (pJ == nt - 1);
-        if (ok && first && seg >= 2) ok = wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u);
-        if (!ok) break;
-        tc::fence_after();
-        {
-          // O[seg & 1] (+)= K v in fp16: one instruction per 16-deep slice of
-          // j; the kernel values of j = 16 ks .. 16 ks + 15 sit packed in
-          // columns 32 (ks / 2) + 8 (ks % 2) of the exponent buffer
+        if (!ok) {
+          if (lane == 0) ctl->tc_error = 1;
+          if (last >= 0) tc::mbar_wait(g_done + last % NE, (uint32_t)(last / NE) & 1u, kLimit);
+        }
+      } else {
+        // second product of tile k once every exponent warp wrote its kernel
+        // values (and the output set was read for segment seg - 2)
+        const uint64_t dV = tc::smem_desc(s0, 128, 16 * kTcRows);
+        int st = 0, J = J0, seg = 0;
+        for (int k = 0; k < nk; ++k) {
+          if (k > 0 && J == 0) ++seg;
+          const bool first = (k == 0) || (J == 0);
+          const bool lst = (k == nk - 1) || (J == nt - 1);
+          ok = wait(p_ready + k % NE, (uint32_t)(k / NE) & 1u);
+          if (ok && first && seg >= 2) ok = wait(o_free + (seg & 1), (uint32_t)((seg - 2) >> 1) & 1u);
+          if (!ok) break;
+          tc::fence_after();
           constexpr uint32_t id = tc::idesc_f16(128, NV);
-          const uint64_t v_h = dV + ((oS + pst * SM::kStage + 2 * SM::kA) >> 4);
+          const uint64_t v_h = dV + ((oS + st * SM::kStage + 2 * SM::kA) >> 4);
           const uint32_t tE = tbase + 128 * (k % NE), tO = tbase + TcAcc<MM>::kOcol + NV * (seg & 1);
 #pragma unroll
           for (int ks = 0; ks < kTcRows / 16; ++ks)
-            tc::mma_ts_f16(tO, tE + 32 * (ks >> 1) + 8 * (ks & 1), v_h + ks * 16, id, (!first || ks > 0) ? 1u : 0u);
-          tc::mma_commit(pv_done + k % NE);
-          tc::mma_commit(s_free + pst);
-          if (last) tc::mma_commit(o_ready + (seg & 1));
-          last_pv = k;
+            tc::mma_ts_f16_el(tO, tE + 32 * (ks >> 1) + 8 * (ks & 1), v_h + ks * 16, id,
+                              (!first || ks > 0) ? 1u : 0u);
+          tc::mma_commit_el(pv_done + k % NE);
+          tc::mma_commit_el(s_free + st);
+          if (lst) tc::mma_commit_el(o_ready + (seg & 1));
+          last = k;
+          if (++J == nt) J = 0;
+          if (++st == Se) st = 0;
         }
-        if (++pJ == nt) pJ = 0;
-        if (++pst == Se) pst = 0;
-      }
-      if (!ok) {
-        ctl->tc_error = 1;
-        // let the products already issued finish (bounded) before TMEM is released
-        if (last_g >= 0) tc::mbar_wait(g_done + last_g % NE, (uint32_t)(last_g / NE) & 1u, kLimit);
-        if (last_pv >= 0) tc::mbar_wait(pv_done + last_pv % NE, (uint32_t)(last_pv / NE) & 1u, kLimit);
+        if (!ok) {
+          if (lane == 0) ctl->tc_error = 1;
+          if (last >= 0) tc::mbar_wait(pv_done + last % NE, (uint32_t)(last / NE) & 1u, kLimit);
+        }
       }
     }
   } else {
