@@ -15,11 +15,15 @@
 // [b T / G, (b+1) T / G) of the T upper-triangle tiles in row-major order,
 // so every CTA gets the same number of tiles to within one.  Two shared-memory
 // stages hold (row tile A, column tile B); A is copied only when the row
-// changes.  Two TMEM accumulators let the product of tile k+1 run while
-// tile k is read.  Eight warps read a tile: warp w owns TMEM lanes
+// changes.  Two TMEM accumulators let the products of tiles k+1 and k+2 run
+// while tile k is read.  Eight warps read a tile: warp w owns TMEM lanes
 // 32 (w mod 4) .. + 31 (its rows) and column half w / 4, and releases the
-// accumulator through an mbarrier as soon as its loads are done, so warps
-// never wait for one another except through the accumulators.  In the
+// accumulator through an mbarrier as soon as its loads are done.  No warp
+// is set apart to feed the pipeline: the first warp past product k copies
+// tile k+2 into the stage product k has left, and the last warp to release
+// accumulator k mod 2 issues the product of tile k+2 into it (a shared
+// counter elects each; the mbarriers order them), so every product is
+// issued as early as its operands and accumulator allow.  In the
 // bracket pass each warp appends its candidates to its own shared buffer
 // and flushes it to global memory with one atomic when full.
 #include <math.h>
@@ -101,6 +105,9 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   float* cbuf = (float*)(smem + 2 * D::kStage);  // per-warp candidates, or the histogram in radix modes
   uint64_t* bars = (uint64_t*)(smem + 2 * D::kStage + D::kCand);  // full[2], mma[2], free[2]
   uint32_t* tslot = (uint32_t*)(bars + 6);
+  uint32_t* passed = tslot + 1;    // [2] warps past product k, per stage (elects the copy's issuer)
+  uint32_t* released = tslot + 3;  // [2] warps done reading accumulator s (elects the product's issuer)
+  uint32_t* failed = tslot + 5;    // a warp gave up
 
   if (only_in_fallback && ctl->mode != 1) return;  // uniform: the bracket held the median
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
@@ -123,6 +130,7 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
     for (int b = 0; b < 4; ++b) tc::mbar_init(bars + b, 1);
     tc::mbar_init(bars + 4, kMtWarps);
     tc::mbar_init(bars + 5, kMtWarps);
+    for (int b = 0; b < 5; ++b) passed[b] = 0u;
   }
   if (warp == 0) tc::tmem_alloc(tslot, 256);
   tc::fence_before();
@@ -130,23 +138,21 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   tc::fence_after();
   const uint32_t tbase = *tslot;
 
-  // producer state (thread 0): row tile held by each stage, last tile
-  // loaded and last product issued
-  int a_row0 = -1, a_row1 = -1;
-  int last_loaded = -1, last_issued = -1;
-  auto load = [&](int k) {  // tile f0 + k into stage k & 1
+  // Copies and products are issued by whichever warp can first do so (one
+  // elected lane; operands warp-uniform).  Each thread remembers its latest
+  // copy and product: in flight there is at most one copy per stage and one
+  // product per accumulator, each the latest of the thread that issued it.
+  int my_load = -1, my_mma = -1;
+  auto load = [&](int k, int2 tj, bool needA) {  // tile f0 + k, coordinates tj, into stage k & 1
     const int s = k & 1;
     unsigned char* stg = smem + s * D::kStage;
-    const int2 tj = tiles[f0 + k];
-    const bool needA = (s ? a_row1 : a_row0) != tj.x;
     tc::mbar_expect_tx(bars + s, needA ? 2 * D::kTile : D::kTile);
     if (needA) tc::bulk_g2s(stg, imgA + (size_t)tj.x * (D::kTile / 4), D::kTile, bars + s);
     tc::bulk_g2s(stg + D::kTile, imgB + (size_t)tj.y * (D::kTile / 4), D::kTile, bars + s);
-    if (s) a_row1 = tj.x;
-    else a_row0 = tj.x;
-    last_loaded = k;
+    my_load = k;
   };
-  auto issue = [&](int k) {  // product of tile k into accumulator k & 1
+  // product of tile k into accumulator k & 1, issued by a whole warp
+  auto issue = [&](int k) {
     const int s = k & 1;
     tc::fence_after();
     constexpr uint32_t id = tc::idesc_tf32(128, 128);
@@ -159,19 +165,28 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
     for (int p = 0; p < 3; ++p)
 #pragma unroll
       for (int ks = 0; ks < KA / 8; ++ks)
-        tc::mma_ss(tbase + 128 * s, tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
-                   tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
-    tc::mma_commit(bars + 2 + s);
-    last_issued = k;
+        tc::mma_ss_el(tbase + 128 * s, tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
+                      tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
+    tc::mma_commit_el(bars + 2 + s);
+    my_mma = k;
   };
 
   bool ok = true;
   if (t == 0 && nk > 0) {
-    load(0);
-    if (nk > 1) load(1);
-    ok = tc::mbar_wait(bars + 0, 0, kLimit);
-    if (ok) issue(0);
+    load(0, tiles[f0], true);
+    if (nk > 1) load(1, tiles[f0 + 1], true);
   }
+  if (warp == 0 && nk > 0) {
+    // the first two products (both accumulators start free)
+    ok = __all_sync(0xffffffffu, tc::mbar_wait(bars + 0, 0, kLimit)) != 0;
+    if (ok) issue(0);
+    if (ok && nk > 1) {
+      ok = __all_sync(0xffffffffu, tc::mbar_wait(bars + 1, 0, kLimit)) != 0;
+      if (ok) issue(1);
+    }
+  }
+  // tile coordinates ahead of their use: this tile's, and the next copy's
+  int2 tj = nk > 0 ? tiles[f0] : make_int2(0, 0);
 
   unsigned int below = 0u;  // pairs below the bracket (this thread)
   unsigned int cnt = 0u;    // candidates in this warp's buffer (warp-uniform)
@@ -189,19 +204,14 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
 
   for (int k = 0; k < nk; ++k) {
     const int s = k & 1;
-    if (t == 0 && ok && k + 1 < nk) {
-      // next product: its tile is loaded and accumulator (k+1) & 1 has been
-      // read by every warp (tile k - 1)
-      const int s1 = (k + 1) & 1;
-      ok = tc::mbar_wait(bars + s1, (uint32_t)((k + 1) >> 1) & 1u, kLimit);
-      if (ok && k >= 1) ok = tc::mbar_wait(bars + 4 + s1, (uint32_t)((k - 1) >> 1) & 1u, kLimit);
-      if (ok) issue(k + 1);
-    }
+    const int2 tl = (lane == 0 && k + 2 < nk) ? tiles[f0 + k + 2] : make_int2(0, 0);
     bool w = ok && tc::mbar_wait(bars + 2 + s, (uint32_t)(k >> 1) & 1u, kLimit);
     ok = __all_sync(0xffffffffu, w) != 0;
     if (!ok) break;
     tc::fence_after();
-    if (t == 0 && k + 2 < nk) load(k + 2);  // stage s is free: product k is done
+    // product k is done, so stage s is free: the first warp past it copies
+    // tile k + 2 there (the row tile only when the row changes)
+    if (lane == 0 && k + 2 < nk && atomicAdd(passed + s, 1u) % kMtWarps == 0u) load(k + 2, tl, tl.x != tj.x);
 
     uint32_t r0[32], r1[32];
     tc::tmem_ld32(tbase + lane_off + 128 * s + c0, r0);
@@ -210,8 +220,20 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
     tc::fence_before();
     __syncwarp();
     if (lane == 0) tc::mbar_arrive(bars + 4 + s);
-
-    const int2 tj = tiles[f0 + k];
+    const int2 tj_next = k + 1 < nk ? tiles[f0 + k + 1] : tj;
+    // the last warp to release accumulator s issues the product of tile
+    // k + 2 into it, once the release barrier (every warp's loads) and the
+    // copy have completed
+    uint32_t rel = 0u;
+    if (lane == 0 && k + 2 < nk) rel = atomicAdd(released + s, 1u);
+    rel = __shfl_sync(0xffffffffu, rel, 0);
+    if (k + 2 < nk && rel % kMtWarps == kMtWarps - 1) {
+      bool w2 = tc::mbar_wait(bars + 4 + s, (uint32_t)(k >> 1) & 1u, kLimit);
+      if (w2) w2 = tc::mbar_wait(bars + s, (uint32_t)((k + 2) >> 1) & 1u, kLimit);
+      ok = __all_sync(0xffffffffu, w2) != 0;
+      if (!ok) break;
+      issue(k + 2);
+    }
     const int i = tj.x * kMtRows + quarter * 32 + lane;
     const bool diag = tj.x == tj.y;
     const bool full = !diag && (tj.y + 1) * kMtRows <= N && (tj.x + 1) * kMtRows <= N;
@@ -275,8 +297,12 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
         }
       }
     }
+    tj = tj_next;
   }
-  if (!ok && lane == 0) ctl->tc_error = 1;
+  if (!ok && lane == 0) {
+    ctl->tc_error = 1;
+    *failed = 1u;
+  }
 
   if (mode == 0) {
     if (cnt) flush();
@@ -284,12 +310,12 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
     for (int off = 16; off > 0; off >>= 1) below += __shfl_xor_sync(0xffffffffu, below, off);
     if (lane == 0 && below) atomicAdd(&ctl->below, (unsigned long long)below);
   }
-  if (t == 0 && !ok) {
-    // gave up: let the copies and products already issued finish (bounded)
+  __syncthreads();
+  if (*failed) {
+    // a warp gave up: let the copies and products in flight finish (bounded)
     // before the shared memory and TMEM are released
-    for (int k = last_issued + 1; k <= last_loaded; ++k)
-      tc::mbar_wait(bars + (k & 1), (uint32_t)(k >> 1) & 1u, kLimit);
-    if (last_issued >= 0) tc::mbar_wait(bars + 2 + (last_issued & 1), (uint32_t)(last_issued >> 1) & 1u, kLimit);
+    if (my_load >= 0) tc::mbar_wait(bars + (my_load & 1), (uint32_t)(my_load >> 1) & 1u, kLimit);
+    if (my_mma >= 0) tc::mbar_wait(bars + 2 + (my_mma & 1), (uint32_t)(my_mma >> 1) & 1u, kLimit);
   }
   __syncthreads();
   if (mode != 0) {
