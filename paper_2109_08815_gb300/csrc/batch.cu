@@ -79,7 +79,12 @@ struct pds_batch {
   int launches_per_iter = 0;
 };
 
-static constexpr int kSideStreams = 8;
+// Parallel graph branches for the problems' reductions and SVGD steps: one
+// per problem up to this many.  A small problem's step is a chain of short
+// launches that leave most of the GPU idle, so more branches overlap more of
+// them (64 uneven problems: 4.56 ms per iteration with 8 branches, 3.59 ms
+// with 32).
+static constexpr int kMaxSideStreams = 64;
 
 static void free_group(Group& g) {
   cudaFree(g.d_jobs);
@@ -175,12 +180,13 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     ++n;
   }
   if ((e = cudaEventRecord(b->ev[0], b->stream)) != cudaSuccess) return e;
-  for (int s = 0; s < kSideStreams; ++s)
+  const int n_side = (int)b->side.size();
+  for (int s = 0; s < n_side; ++s)
     if ((e = cudaStreamWaitEvent(b->side[s], b->ev[0], 0)) != cudaSuccess) return e;
   for (size_t j = 0; j < b->probs.size(); ++j) {
     pds_problem* p = b->probs[j];
     pds_svgd* s = b->svgds[j];
-    cudaStream_t st = b->side[j % kSideStreams];
+    cudaStream_t st = b->side[j % n_side];
     const int N = s->sp.N;
     float* lp = b->logp[j] ? b->logp[j] : p->d_logp;
     if (p->kind == PDS_SYSTEM_ARM_BOX) {
@@ -201,7 +207,7 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     if ((e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k)) != cudaSuccess) return e;
     n += 1 + k;
   }
-  for (int s = 0; s < kSideStreams; ++s) {
+  for (int s = 0; s < n_side; ++s) {
     if ((e = cudaEventRecord(b->ev[1 + s], b->side[s])) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(b->stream, b->ev[1 + s], 0)) != cudaSuccess) return e;
   }
@@ -303,9 +309,16 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       b->groups.push_back(g);
     }
   }
-  b->side.resize(kSideStreams);
-  b->ev.resize(1 + kSideStreams);
-  for (int s = 0; s < kSideStreams; ++s) cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking);
+  const int n_side = n_jobs < kMaxSideStreams ? n_jobs : kMaxSideStreams;
+  b->side.resize(n_side);
+  b->ev.resize(1 + n_side);
+  for (int s = 0; s < n_side; ++s)
+    if (cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking) != cudaSuccess) {
+      b->side.resize(s);
+      b->ev.clear();
+      pds_batch_destroy(b);
+      return set_error(PDS_ERR_CUDA, "batch: stream creation failed");
+    }
   for (auto& e : b->ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
   *out = b;
   return PDS_OK;
