@@ -71,6 +71,9 @@ struct pds_batch {
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;    // [0] fork, [1..] joins
+  std::vector<cudaStream_t> gstream;  // one branch per chain-length group's rollout
+  std::vector<cudaEvent_t> gdone;     // that rollout finished
+  std::vector<int> group_of;          // problem -> its group (-1: rolled out on its own branch)
   cudaGraphExec_t exec = nullptr;
   cudaGraph_t graph = nullptr;
   bool dirty = true;              // tables or settings changed since the graph was captured
@@ -170,16 +173,21 @@ static cudaError_t launch_group_rollout(Group& g, cudaStream_t st) {
                               st);
 }
 
-// One iteration of every problem, queued on b->stream with per-problem
-// branches on the side streams.
+// One iteration of every problem: the chain-length groups' rollouts on
+// branches of their own (persistent kernels that take work from a counter,
+// so concurrent groups fill one another's tails), each problem's reduction
+// and SVGD step on a side branch that waits only for its own group.
 static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
   int n = 0;
   cudaError_t e;
-  for (Group& g : b->groups) {
-    if ((e = launch_group_rollout(g, b->stream)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(b->ev[0], b->stream)) != cudaSuccess) return e;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    cudaStream_t gs = b->gstream[gi];
+    if ((e = cudaStreamWaitEvent(gs, b->ev[0], 0)) != cudaSuccess) return e;
+    if ((e = launch_group_rollout(b->groups[gi], gs)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(b->gdone[gi], gs)) != cudaSuccess) return e;
     ++n;
   }
-  if ((e = cudaEventRecord(b->ev[0], b->stream)) != cudaSuccess) return e;
   const int n_side = (int)b->side.size();
   for (int s = 0; s < n_side; ++s)
     if ((e = cudaStreamWaitEvent(b->side[s], b->ev[0], 0)) != cudaSuccess) return e;
@@ -187,6 +195,7 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     pds_problem* p = b->probs[j];
     pds_svgd* s = b->svgds[j];
     cudaStream_t st = b->side[j % n_side];
+    if (b->group_of[j] >= 0 && (e = cudaStreamWaitEvent(st, b->gdone[b->group_of[j]], 0)) != cudaSuccess) return e;
     const int N = s->sp.N;
     float* lp = b->logp[j] ? b->logp[j] : p->d_logp;
     if (p->kind == PDS_SYSTEM_ARM_BOX) {
@@ -211,6 +220,8 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     if ((e = cudaEventRecord(b->ev[1 + s], b->side[s])) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(b->stream, b->ev[1 + s], 0)) != cudaSuccess) return e;
   }
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    if ((e = cudaStreamWaitEvent(b->stream, b->gdone[gi], 0)) != cudaSuccess) return e;
   if (launches) *launches = n;
   return cudaSuccess;
 }
@@ -309,6 +320,23 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
       b->groups.push_back(g);
     }
   }
+  b->group_of.assign(n_jobs, -1);
+  for (size_t gi = 0; gi < b->groups.size(); ++gi)
+    for (int j : b->groups[gi].jobs) b->group_of[j] = (int)gi;
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ge = nullptr;
+    if (cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking) != cudaSuccess) {
+      pds_batch_destroy(b);
+      return set_error(PDS_ERR_CUDA, "batch: stream creation failed");
+    }
+    b->gstream.push_back(gs);
+    if (cudaEventCreateWithFlags(&ge, cudaEventDisableTiming) != cudaSuccess) {
+      pds_batch_destroy(b);
+      return set_error(PDS_ERR_CUDA, "batch: event creation failed");
+    }
+    b->gdone.push_back(ge);
+  }
   const int n_side = n_jobs < kMaxSideStreams ? n_jobs : kMaxSideStreams;
   b->side.resize(n_side);
   b->ev.resize(1 + n_side);
@@ -331,6 +359,8 @@ int pds_batch_destroy(pds_batch_t b) {
   for (Group& g : b->groups) free_group(g);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
+  for (auto s : b->gstream) cudaStreamDestroy(s);
+  for (auto e : b->gdone) cudaEventDestroy(e);
   cudaEventDestroy(b->ev_in);
   cudaEventDestroy(b->ev_out);
   cudaStreamDestroy(b->stream);
