@@ -69,6 +69,31 @@ def test_batch_equals_each_problem_alone(fast):
     b.close()
 
 
+def test_batch_with_more_problems_than_branches():
+    """70 small problems: the per-problem step branches (at most 64) wrap
+    around, and the chain-length groups' rollouts run on branches of their
+    own; each problem still equals itself run alone."""
+    wls, obs, xs = _mix(70, seed=707, T_range=(20, 40), W_range=(2, 4), N_range=(32, 96))
+    iters = 2
+    alone_x = []
+    probs, svgds = _objects(wls, obs, K=1, fast=1)
+    for w, p, s, x in zip(wls, probs, svgds, xs):
+        X = _gpu(x)
+        api.iterate(p, s, X, iters)
+        torch.cuda.synchronize()
+        alone_x.append(X.cpu().numpy())
+    probs, svgds = _objects(wls, obs, K=1, fast=1)
+    Xs = [_gpu(x) for x in xs]
+    b = api.Batch(probs, svgds, Xs)
+    b.iterate(iters)
+    torch.cuda.synchronize()
+    for j, w in enumerate(wls):
+        width = np.concatenate([w.hi - w.lo, np.ones(w.P - w.M)])[:, None]
+        dx = np.max(np.abs(Xs[j].cpu().numpy() - alone_x[j]) / width)
+        assert dx <= 1e-5, (j, dx)
+    b.close()
+
+
 def test_batch_autotuned_iteration_matches_oracle():
     wls, obs, xs = _mix(5, seed=91, T_range=(40, 200), W_range=(2, 10), N_range=(30, 400))
     probs, svgds = _objects(wls, obs, K=10, fast=0)
