@@ -144,6 +144,28 @@ int pds::ensure_iter_buffers(pds_problem* p, int N) {
   return PDS_OK;
 }
 
+// The chain rollout reads each step's observations in state order, with
+// compile-time offsets and 8-byte loads: a [R][T][S] copy of the [R][T][D]
+// observations, unobserved components 0 (their residuals are skipped).
+static cudaError_t upload_state_ordered_obs(const ChainParams& c, int R, const float* obs, cudaStream_t st,
+                                            float** out) {
+  std::vector<float> h((size_t)R * c.T * c.S, 0.f);
+  for (size_t rt = 0; rt < (size_t)R * c.T; ++rt)
+    for (int j = 0; j < c.S; ++j)
+      if (c.obs_col[j] >= 0) h[rt * c.S + j] = obs[rt * c.D + c.obs_col[j]];
+  float* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, h.size() * sizeof(float));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    cudaFree(d);
+    return e;
+  }
+  *out = d;
+  return cudaSuccess;
+}
+
 extern "C" {
 
 const char* pds_strerror(int code) {
@@ -220,6 +242,7 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
     if (idx < 0 || idx >= 2 * n) return fail(PDS_ERR_ARG, "obs_index[%d] = %d out of range", d, idx);
     if (c.obs_col[idx] >= 0) return fail(PDS_ERR_ARG, "obs_index repeats state %d", idx);
     c.obs_col[idx] = d;
+    c.obs_mask |= 1u << idx;
   }
   for (int j = 0; j < 2 * n; ++j) c.s0[j] = s0[j];
   c.R = 1;
@@ -242,6 +265,9 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) { cudaFree(p->d_obs); delete p; return cuda_fail(e, "copy obs"); }
   p->c.obs = p->d_obs;
+  e = upload_state_ordered_obs(p->c, 1, obs, p->stream, &p->d_obs_s);
+  if (e != cudaSuccess) { cudaFree(p->d_obs); delete p; return cuda_fail(e, "copy obs (state order)"); }
+  p->c.obs_s = p->d_obs_s;
   *out = p;
   return PDS_OK;
 }
@@ -251,6 +277,7 @@ int pds_problem_destroy(pds_problem_t p) {
   cudaStreamSynchronize(p->stream);
   free_parts(p->parts);
   cudaFree(p->d_obs);
+  cudaFree(p->d_obs_s);
   cudaFree(p->d_base);
   cudaFree(p->d_grad);
   cudaFree(p->d_logp);
@@ -334,9 +361,17 @@ int pds_problem_set_trajectories(pds_problem_t p, int R, const float* obs, const
     cudaFree(d);
     return cuda_fail(e, "copy observations");
   }
+  float* ds = nullptr;
+  if ((e = upload_state_ordered_obs(c, R, obs, p->stream, &ds)) != cudaSuccess) {
+    cudaFree(d);
+    return cuda_fail(e, "copy observations (state order)");
+  }
   cudaFree(p->d_obs);
+  cudaFree(p->d_obs_s);
   p->d_obs = d;
+  p->d_obs_s = ds;
   c.obs = d;
+  c.obs_s = ds;
   for (int r = 0; r < R; ++r)
     for (int j = 0; j < c.S; ++j) c.s0[r * kMaxState + j] = s0[(size_t)r * c.S + j];
   c.R = R;

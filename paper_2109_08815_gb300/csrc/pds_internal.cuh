@@ -35,6 +35,8 @@ struct ChainParams {
   float s0[kMaxTraj * kMaxState];  // start state of trajectory r at s0[r * kMaxState]
   float lo[kMaxTheta], hi[kMaxTheta];
   const float* obs;        // device [R][T][D]
+  const float* obs_s;      // device [R][T][S]: the same observations in state order, unobserved components 0
+  unsigned int obs_mask;   // bit j: state component j is observed
   int R;                   // trajectories (each with its own shooting states)
   int combine;             // R > 1: 0 equally weighted mixture (sum), 1 product
 };
@@ -187,6 +189,7 @@ struct pds_problem {
   float* d_base = nullptr;  // arm-and-box pivot motion table
   cudaStream_t stream;
   float* d_obs = nullptr;
+  float* d_obs_s = nullptr;  // the observations in state order (chain rollouts)
   int cap_N = 0;          // workspace capacity in particles
   int cap_K = 0;          // checkpoint stride the tape was sized for
   int cap_cs = 0;         // workspace has the constrained-SVGD partials

@@ -364,23 +364,50 @@ __device__ __forceinline__ void load_params(const ChainParams& c, const float* _
 // Observation residual terms of one step: returns sum of r^2 over observed
 // components of state (q, v) at time t (1-based), and if seed != nullptr adds
 // d/ds [-r^2 / (2 sigma^2)] = r / sigma^2 to the state adjoint.
-template <int NL>
+//   EVERY (every state component observed): obs is the trajectory's
+//     observations in state order, [T][2 NL], read in 8-byte pairs at
+//     compile-time offsets with no per-component test;
+//   otherwise obs is [T][D] and each component looks up its column.
+// The test and the column lookup of the general form, run twice per step,
+// cost about 7 % of the chain benchmark's likelihood.
+template <int NL, bool EVERY>
 __device__ __forceinline__ float obs_residual(const ChainParams& c, const float* __restrict__ obs, int t,
                                               const float (&q)[NL], const float (&v)[NL], float (&qb)[NL],
                                               float (&vb)[NL], bool seed) {
-  const float* row = obs + (size_t)(t - 1) * c.D;
   float acc = 0.f;
+  if constexpr (EVERY) {
+    const float2* row = reinterpret_cast<const float2*>(obs + (size_t)(t - 1) * (2 * NL));
+    auto term = [&](int comp, float o) {  // comp: 0..NL-1 angles, NL..2NL-1 velocities
+      if (comp < NL) {
+        const float r = o - q[comp];
+        acc += r * r;
+        if (seed) qb[comp] += r * c.inv_so2;
+      } else {
+        const float r = o - v[comp - NL];
+        acc += r * r;
+        if (seed) vb[comp - NL] += r * c.inv_so2;
+      }
+    };
 #pragma unroll
-  for (int j = 0; j < NL; ++j) {
-    if (c.obs_col[j] >= 0) {
-      const float r = __ldg(row + c.obs_col[j]) - q[j];
-      acc += r * r;
-      if (seed) qb[j] += r * c.inv_so2;
+    for (int j = 0; j < NL; ++j) {
+      const float2 o = __ldg(row + j);
+      term(2 * j, o.x);
+      term(2 * j + 1, o.y);
     }
-    if (c.obs_col[NL + j] >= 0) {
-      const float r = __ldg(row + c.obs_col[NL + j]) - v[j];
-      acc += r * r;
-      if (seed) vb[j] += r * c.inv_so2;
+  } else {
+    const float* row = obs + (size_t)(t - 1) * c.D;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      if (c.obs_col[j] >= 0) {
+        const float r = __ldg(row + c.obs_col[j]) - q[j];
+        acc += r * r;
+        if (seed) qb[j] += r * c.inv_so2;
+      }
+      if (c.obs_col[NL + j] >= 0) {
+        const float r = __ldg(row + c.obs_col[NL + j]) - v[j];
+        acc += r * r;
+        if (seed) vb[j] += r * c.inv_so2;
+      }
     }
   }
   return acc;
@@ -432,7 +459,7 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
 // -dPsi/ds_end = 2 (lam + c g) (s^s_{w+1} - s_end) / sigma_def^2, runs
 // through the same recomputed steps: th2 receives its theta part, start the
 // sum of both adjoints, next the direct -dPsi/ds^s_{w+1}, gdef the value g.
-template <int NL, bool FAST, bool CS = false>
+template <int NL, bool FAST, bool CS = false, bool EVERY = false>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
                                              size_t u, float* seg = nullptr, size_t seg_stride = 0) {
@@ -441,7 +468,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   const int wg = (int)(u / N);
   const int i = (int)(u - (size_t)wg * N);
   const int r = wg / c.W, w = wg - r * c.W;
-  const float* obs = c.obs + (size_t)r * c.T * c.D;
+  const float* obs = EVERY ? c.obs_s + (size_t)r * c.T * (2 * NL) : c.obs + (size_t)r * c.T * c.D;
   const int shoot0 = c.M + r * (c.W - 1) * 2 * NL;  // first shooting-state row of trajectory r
   // the window-reduction kernel (next on the stream) ORs in non-finite flags
   if (status && wg == 0) status[i] = 0;
@@ -473,7 +500,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   for (int k = 0; k < h; ++k) {
     if (grad && (k % K) == 0) tape_store<NL>(ckpt, k / K, U, u, q, v);
     chain_step<NL, FAST>(q, v, P, c.dt);
-    rss += obs_residual<NL>(c, obs, t0 + k + 1, q, v, qb, vb, false);
+    rss += obs_residual<NL, EVERY>(c, obs, t0 + k + 1, q, v, qb, vb, false);
   }
   float lp = -0.5f * c.inv_so2 * rss + (float)h * c.obs_const;
 
@@ -553,7 +580,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       cp_async_wait2();  // the group of state k (two groups older than the newest)
       float qs[NL], vs[NL];
       tape_load<NL>(seg, (size_t)(k % 3), sstride, 0, qs, vs);
-      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
+      obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       if constexpr (CS) {
         StepTape<NL> F;
         chain_step_recompute<NL, FAST>(qs, vs, P, F);
@@ -573,7 +600,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     tape_load<NL>(ckpt, h - 1, U, u, qs, vs);
     for (int k = h - 1; k >= 0; --k) {
       if (k > 0) tape_load<NL>(ckpt, k - 1, U, u, qn, vn);
-      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
+      obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       if constexpr (CS) {
         StepTape<NL> F;
         chain_step_recompute<NL, FAST>(qs, vs, P, F);
@@ -599,7 +626,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     }
     for (int k = e - 1; k >= a; --k) {
       // observation at time t0+k+1 depends on s_{k+1}
-      obs_residual<NL>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
+      obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
       if constexpr (CS) {
         StepTape<NL> F;
@@ -645,8 +672,9 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 }
 
 // seg_smem: the reverse sweep's recomputed segment states live in dynamic
-// shared memory (K x 2 NL x blockDim floats), else in the tape.
-template <int NL, bool FAST>
+// shared memory (K x 2 NL x blockDim floats), else in the tape.  EVERY:
+// the problem observes every state component.
+template <int NL, bool FAST, bool EVERY>
 __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(const ChainParams c, const float* __restrict__ X,
                                                                         int N, Partials parts, int grad,
                                                                         int32_t* __restrict__ status, int seg_smem) {
@@ -655,9 +683,9 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
-    rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+    rollout_unit<NL, FAST, false, EVERY>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
   else
-    rollout_unit<NL, FAST>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, false, EVERY>(c, X, N, parts, grad, status, u);
 }
 
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
@@ -708,7 +736,15 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_ker
     const size_t u = (size_t)wi.unit0 + threadIdx.x;
     const int N = job->N;
     float* seg = (ring && cs.K == 1) ? ring_sh + threadIdx.x : nullptr;
-    if (u < (size_t)N * cs.W) rollout_unit<NL, FAST>(cs, job->X, N, job->parts, grad, job->status, u, seg, blockDim.x);
+    // a problem that observes every state component takes the residual
+    // form without per-component tests, as its single-problem launch does
+    constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
+    if (u < (size_t)N * cs.W) {
+      if ((cs.obs_mask & kAll) == kAll)
+        rollout_unit<NL, FAST, false, true>(cs, job->X, N, job->parts, grad, job->status, u, seg, blockDim.x);
+      else
+        rollout_unit<NL, FAST, false, false>(cs, job->X, N, job->parts, grad, job->status, u, seg, blockDim.x);
+    }
     __syncthreads();
   }
 }
@@ -770,10 +806,18 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
       rollout_cs_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
     else
       rollout_cs_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
-  } else if (c.fast_math) {
-    rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
   } else {
-    rollout_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    // the same residual form as the batched kernel takes for the problem
+    constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
+    const bool every = (c.obs_mask & kAll) == kAll;
+    if (c.fast_math && every)
+      rollout_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else if (c.fast_math)
+      rollout_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else if (every)
+      rollout_kernel<NL, false, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else
+      rollout_kernel<NL, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
   }
   return cudaGetLastError();
 }
