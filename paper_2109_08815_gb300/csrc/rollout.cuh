@@ -420,6 +420,11 @@ __device__ __forceinline__ void cp_async4(float* dst_smem, const float* src_glob
                "l"(src_global)
                : "memory");
 }
+__device__ __forceinline__ void cp_async8(float2* dst_smem, const float2* src_global) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src_global)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
@@ -443,6 +448,44 @@ __device__ __forceinline__ void tape_load(const float* __restrict__ tape, size_t
     q[j] = p[(size_t)j * U];
     v[j] = p[(size_t)(NL + j) * U];
   }
+}
+
+// The checkpoint tape is thread-contiguous, [slot][U][2 NL]: a unit's state
+// (q, v) is 2 NL consecutive floats, moved as NL 8-byte pairs at immediate
+// offsets (a warp still covers 32 x 8 NL contiguous bytes per slot).  Pair j
+// holds state components 2j and 2j+1 (angles 0..NL-1, then velocities).
+template <int NL>
+__device__ __forceinline__ float state_comp(const float (&q)[NL], const float (&v)[NL], int comp) {
+  return comp < NL ? q[comp] : v[comp - NL];
+}
+template <int NL>
+__device__ __forceinline__ void set_comp(float (&q)[NL], float (&v)[NL], int comp, float x) {
+  if (comp < NL) q[comp] = x;
+  else v[comp - NL] = x;
+}
+template <int NL>
+__device__ __forceinline__ void ckpt_store(float* __restrict__ tape, size_t slot, size_t U, size_t u,
+                                           const float (&q)[NL], const float (&v)[NL]) {
+  float2* p = reinterpret_cast<float2*>(tape) + (slot * U + u) * NL;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) p[j] = make_float2(state_comp<NL>(q, v, 2 * j), state_comp<NL>(q, v, 2 * j + 1));
+}
+// pairs of one state at p[j * stride] (stride 1: the tape; the block size:
+// the shared-memory ring)
+template <int NL>
+__device__ __forceinline__ void pairs_load(const float2* __restrict__ p, size_t stride, float (&q)[NL],
+                                           float (&v)[NL]) {
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    const float2 x = p[(size_t)j * stride];
+    set_comp<NL>(q, v, 2 * j, x.x);
+    set_comp<NL>(q, v, 2 * j + 1, x.y);
+  }
+}
+template <int NL>
+__device__ __forceinline__ void ckpt_load(const float* __restrict__ tape, size_t slot, size_t U, size_t u,
+                                          float (&q)[NL], float (&v)[NL]) {
+  pairs_load<NL>(reinterpret_cast<const float2*>(tape) + (slot * U + u) * NL, 1, q, v);
 }
 
 // One thread per unit u = w * N + i (window w, particle i): the window's
@@ -498,7 +541,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   float qb[NL], vb[NL];  // unused in the forward pass
   float rss = 0.f;
   for (int k = 0; k < h; ++k) {
-    if (grad && (k % K) == 0) tape_store<NL>(ckpt, k / K, U, u, q, v);
+    if (grad && (k % K) == 0) ckpt_store<NL>(ckpt, k / K, U, u, q, v);
     chain_step<NL, FAST>(q, v, P, c.dt);
     rss += obs_residual<NL, EVERY>(c, obs, t0 + k + 1, q, v, qb, vb, false);
   }
@@ -563,13 +606,16 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     // Every pre-step state is on the tape: no recomputation.  Each state is
     // copied into a ring of three shared-memory slots two steps ahead
     // (cp.async, no registers held), so its load's latency hides behind two
-    // steps' adjoints.
+    // steps' adjoints.  The ring is pair-major, [3][NL][block] float2, in
+    // the same shared memory (seg is this thread's float of a [..][block]
+    // layout, seg_stride the block size).
+    float2* ring = reinterpret_cast<float2*>(seg - threadIdx.x) + threadIdx.x;
     auto fetch = [&](int k) {
       if (k >= 0) {
-        const float* src = ckpt + (size_t)k * (2 * NL) * U + u;
-        float* dst = seg + (size_t)(k % 3) * (2 * NL) * sstride;
+        const float2* src = reinterpret_cast<const float2*>(ckpt) + ((size_t)k * U + u) * NL;
+        float2* dst = ring + (size_t)(k % 3) * NL * sstride;
 #pragma unroll
-        for (int j = 0; j < 2 * NL; ++j) cp_async4(dst + (size_t)j * sstride, src + (size_t)j * U);
+        for (int j = 0; j < NL; ++j) cp_async8(dst + (size_t)j * sstride, src + j);
       }
       cp_async_commit();
     };
@@ -579,7 +625,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       fetch(k - 2);
       cp_async_wait2();  // the group of state k (two groups older than the newest)
       float qs[NL], vs[NL];
-      tape_load<NL>(seg, (size_t)(k % 3), sstride, 0, qs, vs);
+      pairs_load<NL>(ring + (size_t)(k % 3) * NL * sstride, sstride, qs, vs);
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       if constexpr (CS) {
         StepTape<NL> F;
@@ -597,9 +643,9 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     // step k-1 is loaded while step k is reversed, so the load's latency
     // hides behind the step's adjoint.
     float qs[NL], vs[NL], qn[NL] = {}, vn[NL] = {};
-    tape_load<NL>(ckpt, h - 1, U, u, qs, vs);
+    ckpt_load<NL>(ckpt, h - 1, U, u, qs, vs);
     for (int k = h - 1; k >= 0; --k) {
-      if (k > 0) tape_load<NL>(ckpt, k - 1, U, u, qn, vn);
+      if (k > 0) ckpt_load<NL>(ckpt, k - 1, U, u, qn, vn);
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       if constexpr (CS) {
         StepTape<NL> F;
@@ -618,7 +664,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     const int a = sg * K;
     const int e = min(a + K, h);
     float qs[NL], vs[NL];
-    tape_load<NL>(ckpt, sg, U, u, qs, vs);
+    ckpt_load<NL>(ckpt, sg, U, u, qs, vs);
     // recompute s_a .. s_{e-1} into the segment buffer
     for (int k = a; k < e; ++k) {
       tape_store<NL>(segbuf, k - a, sstride, 0, qs, vs);
