@@ -540,8 +540,13 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   // ---------------- forward
   float qb[NL], vb[NL];  // unused in the forward pass
   float rss = 0.f;
+  int kk = 0, slot = 0;  // step within the checkpoint stride, checkpoint slot (no division per step)
   for (int k = 0; k < h; ++k) {
-    if (grad && (k % K) == 0) ckpt_store<NL>(ckpt, k / K, U, u, q, v);
+    if (grad && kk == 0) ckpt_store<NL>(ckpt, slot, U, u, q, v);
+    if (++kk == K) {
+      kk = 0;
+      ++slot;
+    }
     chain_step<NL, FAST>(q, v, P, c.dt);
     rss += obs_residual<NL, EVERY>(c, obs, t0 + k + 1, q, v, qb, vb, false);
   }
@@ -610,22 +615,24 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     // the same shared memory (seg is this thread's float of a [..][block]
     // layout, seg_stride the block size).
     float2* ring = reinterpret_cast<float2*>(seg - threadIdx.x) + threadIdx.x;
-    auto fetch = [&](int k) {
+    auto fetch = [&](int k, int rs) {  // state k into ring slot rs = k mod 3
       if (k >= 0) {
         const float2* src = reinterpret_cast<const float2*>(ckpt) + ((size_t)k * U + u) * NL;
-        float2* dst = ring + (size_t)(k % 3) * NL * sstride;
+        float2* dst = ring + (size_t)rs * NL * sstride;
 #pragma unroll
         for (int j = 0; j < NL; ++j) cp_async8(dst + (size_t)j * sstride, src + j);
       }
       cp_async_commit();
     };
-    fetch(h - 1);
-    fetch(h - 2);
+    int rs = (h - 1) % 3;  // ring slot of state k, counted down with k
+    fetch(h - 1, rs);
+    fetch(h - 2, rs == 0 ? 2 : rs - 1);
     for (int k = h - 1; k >= 0; --k) {
-      fetch(k - 2);
+      fetch(k - 2, rs == 2 ? 0 : rs + 1);  // (k - 2) mod 3 = (k + 1) mod 3
       cp_async_wait2();  // the group of state k (two groups older than the newest)
       float qs[NL], vs[NL];
-      pairs_load<NL>(ring + (size_t)(k % 3) * NL * sstride, sstride, qs, vs);
+      pairs_load<NL>(ring + (size_t)rs * NL * sstride, sstride, qs, vs);
+      rs = rs == 0 ? 2 : rs - 1;
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       if constexpr (CS) {
         StepTape<NL> F;
