@@ -173,9 +173,41 @@ __device__ __forceinline__ void load_rigid2_params(const Rigid2Params& r, const 
     p[k] = r.theta_row[k] >= 0 ? __ldg(X + (size_t)r.theta_row[k] * N + i) : r.p[k];
 }
 
+// Observation residual of row t (the observation of the state after step t)
+// against state x: returns r^2 summed over the observed components and, if
+// seed, adds r / sigma^2 to a.  EVERY (all four components observed): one
+// 16-byte load of the state-ordered row, no per-component test; otherwise
+// each component looks up its column.
+template <bool EVERY>
+__device__ __forceinline__ float r2_residual(const ChainParams& c, int t, const float (&x)[4], float (&a)[4],
+                                             bool seed) {
+  float acc = 0.f;
+  if constexpr (EVERY) {
+    const float4 o = __ldg(reinterpret_cast<const float4*>(c.obs_s) + t);
+    const float e[4] = {o.x - x[0], o.y - x[1], o.z - x[2], o.w - x[3]};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      acc = fmaf(e[q], e[q], acc);
+      if (seed) a[q] = fmaf(c.inv_so2, e[q], a[q]);
+    }
+  } else {
+    const float* row = c.obs + (size_t)t * c.D;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (c.obs_col[q] >= 0) {
+        const float e = __ldg(row + c.obs_col[q]) - x[q];
+        acc = fmaf(e, e, acc);
+        if (seed) a[q] = fmaf(c.inv_so2, e, a[q]);
+      }
+  }
+  return acc;
+}
+
 }  // namespace
 
-template <bool FAST>
+// The checkpoint tape is thread-contiguous, [slot][U] of float4 (one 16-byte
+// access per state); the K > 1 segment buffer stays [K][4][U].
+template <bool FAST, bool EVERY>
 __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c, const Rigid2Params r,
                                                              const float* __restrict__ X, int N, Partials parts,
                                                              int grad, int32_t* __restrict__ status) {
@@ -194,24 +226,20 @@ __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c
   const int t0 = (int)(((long long)w * c.T) / c.W);
   const int t1 = (int)(((long long)(w + 1) * c.T) / c.W);
   const int K = c.K;
-  float* ck = parts.tape;                                  // [max_seg][4][U]
+  float4* ck = reinterpret_cast<float4*>(parts.tape);     // [max_seg][U]
   float* seg = parts.tape + (size_t)c.max_seg * 4 * U;     // [K][4][U]
   float rss = 0.f;
+  float unused[4];
+  int kk = 0, slot = 0;  // step within the checkpoint stride, checkpoint slot
   for (int t = t0; t < t1; ++t) {
-    if (grad && (t - t0) % K == 0) {
-      float* o = ck + (size_t)((t - t0) / K) * 4 * U + u;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) o[(size_t)q * U] = s[q];
+    if (grad && kk == 0) ck[(size_t)slot * U + u] = make_float4(s[0], s[1], s[2], s[3]);
+    if (++kk == K) {
+      kk = 0;
+      ++slot;
     }
     const R2Fwd f = r2_forward<FAST>(k, s);
     r2_apply(f, c.dt, s);
-    const float* row = c.obs + (size_t)t * c.D;  // observation x_{t+1}
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (c.obs_col[q] >= 0) {
-        const float e = __ldg(row + c.obs_col[q]) - s[q];
-        rss = fmaf(e, e, rss);
-      }
+    rss += r2_residual<EVERY>(c, t, s, unused, false);  // observation x_{t+1}
   }
   float lp = -0.5f * c.inv_so2 * rss + (float)(t1 - t0) * c.obs_const;
   float a[4] = {0.f, 0.f, 0.f, 0.f};
@@ -237,22 +265,17 @@ __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c
     // every pre-step state is on the tape; the state of step j-1 is loaded
     // while step j is reversed
     float x[4], xn[4] = {0.f, 0.f, 0.f, 0.f};
-    const float* c0 = ck + (size_t)(h - 1) * 4 * U + u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = c0[(size_t)q * U];
+    float4 v4 = ck[(size_t)(h - 1) * U + u];
+    x[0] = v4.x; x[1] = v4.y; x[2] = v4.z; x[3] = v4.w;
     for (int j = h - 1; j >= 0; --j) {
       if (j > 0) {
-        const float* cj = ck + (size_t)(j - 1) * 4 * U + u;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) xn[q] = cj[(size_t)q * U];
+        v4 = ck[(size_t)(j - 1) * U + u];
+        xn[0] = v4.x; xn[1] = v4.y; xn[2] = v4.z; xn[3] = v4.w;
       }
       const R2Fwd f = r2_forward<FAST>(k, x);
       float xa[4] = {x[0], x[1], x[2], x[3]};
       r2_apply(f, c.dt, xa);
-      const float* row = c.obs + (size_t)(t0 + j) * c.D;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c.obs_col[q] >= 0) a[q] = fmaf(c.inv_so2, __ldg(row + c.obs_col[q]) - xa[q], a[q]);
+      r2_residual<EVERY>(c, t0 + j, xa, a, true);
       r2_reverse(k, f, x, c.dt, a, kb);
 #pragma unroll
       for (int q = 0; q < 4; ++q) x[q] = xn[q];
@@ -262,10 +285,8 @@ __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int ta = sg * K, tb = min(h, ta + K);
     // recompute the segment's pre-step states
-    float x[4];
-    const float* ci = ck + (size_t)sg * 4 * U + u;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) x[q] = ci[(size_t)q * U];
+    const float4 v4 = ck[(size_t)sg * U + u];
+    float x[4] = {v4.x, v4.y, v4.z, v4.w};
     for (int j = 0; j < tb - ta; ++j) {
       float* o = seg + (size_t)j * 4 * U + u;
 #pragma unroll
@@ -283,10 +304,7 @@ __global__ void __launch_bounds__(128) rigid2_rollout_kernel(const ChainParams c
       float xn[4] = {x[0], x[1], x[2], x[3]};
       r2_apply(f, c.dt, xn);
       // observation seed of the state after the step
-      const float* row = c.obs + (size_t)(t0 + ta + j) * c.D;
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-        if (c.obs_col[q] >= 0) a[q] = fmaf(c.inv_so2, __ldg(row + c.obs_col[q]) - xn[q], a[q]);
+      r2_residual<EVERY>(c, t0 + ta + j, xn, a, true);
       r2_reverse(k, f, x, c.dt, a, kb);
     }
   }
@@ -332,10 +350,15 @@ cudaError_t launch_rigid2_rollout(const ChainParams& c, const Rigid2Params& r, c
                                   const Partials& parts, int grad, int32_t* status, cudaStream_t st) {
   const size_t U = (size_t)N * c.W;
   const unsigned blocks = (unsigned)((U + 127) / 128);
-  if (c.fast_math)
-    rigid2_rollout_kernel<true><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
+  const bool every = (c.obs_mask & 0xFu) == 0xFu;
+  if (c.fast_math && every)
+    rigid2_rollout_kernel<true, true><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
+  else if (c.fast_math)
+    rigid2_rollout_kernel<true, false><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
+  else if (every)
+    rigid2_rollout_kernel<false, true><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
   else
-    rigid2_rollout_kernel<false><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
+    rigid2_rollout_kernel<false, false><<<blocks, 128, 0, st>>>(c, r, X, N, parts, grad, status);
   return cudaGetLastError();
 }
 
