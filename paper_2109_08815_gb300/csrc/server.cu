@@ -114,7 +114,7 @@ static size_t job_bytes(int n, int M, int T, int W, int D, int N, int K) {
   }
   const size_t segs = (size_t)((hmax + K - 1) / K);
   size_t b = 0;
-  b += (size_t)T * D * 4;                                   // observations
+  b += (size_t)T * (D + S) * 4;                             // observations, and their state-ordered copy
   b += (size_t)W * (1 + M + 2 * S) * N * 4;                 // per-window partials
   b += (segs + (size_t)K) * S * U * 4;                      // adjoint tape
   b += (2 * P * N + N) * 4;                                 // iteration buffers (grad, x, logp)
