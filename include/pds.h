@@ -331,8 +331,9 @@ int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int i
  * window) units -- work items ordered longest window first and taken through
  * an atomic counter -- each on a CUDA-graph branch of its own, and each
  * problem's window reduction and SVGD update on a branch of its own (up to
- * 64) that waits only for its chain length's rollout.  The iteration is captured once into a
- * CUDA graph (on the first pds_batch_iterate after creation or autotuning)
+ * 64) that waits only for its chain length's rollout.  The iteration is
+ * captured once into a CUDA graph (on the first pds_batch_iterate after
+ * creation or autotuning)
  * and replayed (the first iteration after creation or autotuning runs with
  * plain launches).  Results equal those of running each problem alone with the
  * same settings, up to rounding.  No counterpart in the paper, which runs one
