@@ -742,7 +742,7 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
 }
 
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
-template <int NL, bool FAST>
+template <int NL, bool FAST, bool EVERY>
 __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
                                                                            const float* __restrict__ X, int N,
                                                                            Partials parts, int grad,
@@ -752,9 +752,9 @@ __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, true>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+    rollout_unit<NL, FAST, true, EVERY>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
   else
-    rollout_unit<NL, FAST, true>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, true, EVERY>(c, X, N, parts, grad, status, u);
 }
 
 // Persistent rollout over several problems with the same chain length
@@ -854,15 +854,17 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
   const size_t seg_bytes = (size_t)(c.K == 1 ? 3 : c.K) * 2 * NL * 128 * sizeof(float);
   const int seg_smem = (grad && seg_bytes <= 48 * 1024) ? 1 : 0;
   const size_t smem = seg_smem ? seg_bytes : 0;
+  constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
+  const bool every = (c.obs_mask & kAll) == kAll;
   if (c.csvgd) {
-    if (c.fast_math)
-      rollout_cs_kernel<NL, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    if (c.fast_math && every)
+      rollout_cs_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else if (c.fast_math)
+      rollout_cs_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
     else
-      rollout_cs_kernel<NL, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+      rollout_cs_kernel<NL, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
   } else {
     // the same residual form as the batched kernel takes for the problem
-    constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
-    const bool every = (c.obs_mask & kAll) == kAll;
     if (c.fast_math && every)
       rollout_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
     else if (c.fast_math)
