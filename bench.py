@@ -325,9 +325,13 @@ def run_pds(args):
         orc.build()
         threads = os.cpu_count() or 1
         rate, secs = oracle_rate(wl, obs, x0, args.ref_sample_baseline, threads)
+        # the same oracle on one thread, on a smaller sample
+        rate1, secs1 = oracle_rate(wl, obs, x0, 64, 1)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.ref_sample_baseline} particles x T={wl.T} log p + gradient (FP64, forward-mode "
-                         f"duals), {secs:.1f} s on {threads} threads"}
+                         f"duals), {secs:.1f} s on {threads} threads",
+               "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                 "sample": f"64 particles x T={wl.T}, {secs1:.1f} s on 1 thread"}}
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_batched:
