@@ -590,7 +590,8 @@ class Batch:
 
     def autotune(self, allow_fast_math=True):
         """Returns [(links, K, fast_math, grid_blocks)] per chain length."""
-        ch = (ctypes.c_int * (4 * 8))()
+        ng, _ = self.info()
+        ch = (ctypes.c_int * (4 * max(ng, 1)))()
         _check(lib().pds_batch_autotune(self._h, int(bool(allow_fast_math)), ch), "pds_batch_autotune")
         ng, _ = self.info()
         return [tuple(ch[4 * g:4 * g + 4]) for g in range(ng)]
