@@ -627,6 +627,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     int rs = (h - 1) % 3;  // ring slot of state k, counted down with k
     fetch(h - 1, rs);
     fetch(h - 2, rs == 0 ? 2 : rs - 1);
+#pragma unroll 2
     for (int k = h - 1; k >= 0; --k) {
       fetch(k - 2, rs == 2 ? 0 : rs + 1);  // (k - 2) mod 3 = (k + 1) mod 3
       cp_async_wait2();  // the group of state k (two groups older than the newest)
