@@ -720,7 +720,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
 
 # dram bytes (read + write) per full-size rollout launch, from the committed
 # ncu capture of this kernel (set to None when the kernel changes)
-TRAFFIC_BYTES_PER_LAUNCH = 274358528 + 659719936
+TRAFFIC_BYTES_PER_LAUNCH = 279944192 + 659641856
 
 
 def main():

@@ -502,7 +502,10 @@ __device__ __forceinline__ void ckpt_load(const float* __restrict__ tape, size_t
 // -dPsi/ds_end = 2 (lam + c g) (s^s_{w+1} - s_end) / sigma_def^2, runs
 // through the same recomputed steps: th2 receives its theta part, start the
 // sum of both adjoints, next the direct -dPsi/ds^s_{w+1}, gdef the value g.
-template <int NL, bool FAST, bool CS = false, bool EVERY = false>
+// RU: unroll factor of the K = 1 reverse loop (2 in the single-problem
+// kernel; the batched kernel, which holds both observation forms, runs
+// slower unrolled).
+template <int NL, bool FAST, bool CS = false, bool EVERY = false, int RU = 1>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
                                              size_t u, float* seg = nullptr, size_t seg_stride = 0) {
@@ -627,7 +630,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     int rs = (h - 1) % 3;  // ring slot of state k, counted down with k
     fetch(h - 1, rs);
     fetch(h - 2, rs == 0 ? 2 : rs - 1);
-#pragma unroll 2
+#pragma unroll RU
     for (int k = h - 1; k >= 0; --k) {
       fetch(k - 2, rs == 2 ? 0 : rs + 1);  // (k - 2) mod 3 = (k + 1) mod 3
       cp_async_wait2();  // the group of state k (two groups older than the newest)
@@ -737,9 +740,9 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, false, EVERY>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+    rollout_unit<NL, FAST, false, EVERY, 2>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
   else
-    rollout_unit<NL, FAST, false, EVERY>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, false, EVERY, 2>(c, X, N, parts, grad, status, u);
 }
 
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
