@@ -186,7 +186,8 @@ int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
  *  PDS_OPT_CHECKPOINT_STRIDE: K as in pds_problem_set_checkpoint_stride.
  *  PDS_OPT_FAST_MATH: 0 (default) = CUDA's sinf/cosf and IEEE division in the
  *    rollout; 1 = the hardware approximations __sincosf / __fdividef (results
- *    stay within the tolerances the parity tests state). */
+ *    stay within the same parity tolerances against the FP64 oracle:
+ *    relative 1e-4 on log p, 1e-3 on the gradient). */
 #define PDS_OPT_CHECKPOINT_STRIDE 1
 #define PDS_OPT_FAST_MATH 2
 int pds_problem_set_option(pds_problem_t p, int option, int value);

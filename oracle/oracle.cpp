@@ -25,7 +25,7 @@
 //     the defect and limit constraints, their MDMM gradient with the
 //     per-particle multipliers held fixed, and the MDMM update.
 //
-// Readings taken where the paper is silent (all documented in the design doc):
+// Readings taken where the paper is silent (the GPU path takes the same ones):
 //   window w covers steps t_w+1 .. t_{w+1}, t_w = floor(w*T/W); window 0
 //   starts at the known s_0, window w>0 at the shooting state s^s_w; every
 //   observation x_1..x_T is compared once; Gaussian constants are included;
