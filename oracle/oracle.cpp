@@ -1302,10 +1302,34 @@ int orc_svgd_phi_rows(int N, int M, const double* u, const double* g, double bw,
   return 0;
 }
 
+// The update of one Algorithm 1 iteration, given its directions: theta rows
+// move by Adam ascent in unit-box coordinates on phi [N][M] (then clipped to
+// the box if clamp), the shooting-state rows by Adam ascent on their own
+// gradient rows grad[i][M..P-1].  adam_m, adam_v [N][P] hold theta moments in
+// unit-box coordinates and shooting-state moments in state units; *t is the
+// step count (incremented).  A particle that sat out has NaN in phi and
+// stays NaN, like the step written out below.
+int orc_svgd_update(int N, int M, int P, const double* lo, const double* hi, double* particles,
+                    const double* phi, const double* grad, double* adam_m, double* adam_v, int* t, double lr,
+                    double b1, double b2, double eps, int clamp) {
+  *t += 1;
+  for (int i = 0; i < N; ++i) {
+    for (int k = 0; k < M; ++k) {
+      double x = (particles[(size_t)i * P + k] - lo[k]) / (hi[k] - lo[k]);
+      adam_ascent(x, adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k], phi[(size_t)i * M + k], *t, lr, b1, b2, eps);
+      if (clamp) x = std::min(1.0, std::max(0.0, x));
+      particles[(size_t)i * P + k] = lo[k] + x * (hi[k] - lo[k]);
+    }
+    for (int k = M; k < P; ++k)
+      adam_ascent(particles[(size_t)i * P + k], adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k],
+                  grad[(size_t)i * P + k], *t, lr, b1, b2, eps);
+  }
+  return 0;
+}
+
 // One SVGD + Adam iteration on particles [N][P] (first M entries theta,
-// the rest shooting states), given grad = d log p / d x [N][P].
-// adam_m, adam_v [N][P] hold theta moments in unit-box coordinates and
-// shooting-state moments in state units; *t is the step count (incremented).
+// the rest shooting states), given grad = d log p / d x [N][P]: phi of
+// Eq. 1 in unit-box coordinates, then the update above.
 // phi_out [N][M] (unit-box coordinates) and bw_out may be NULL.
 int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
                   double* particles, const double* grad, double* adam_m, double* adam_v, int* t,
@@ -1320,18 +1344,7 @@ int orc_svgd_step(int N, int M, int P, const double* lo, const double* hi,
     }
   double bw = 1.0;
   live_step_phi(N, M, u.data(), gu.data(), phi.data(), &bw);
-  *t += 1;
-  for (int i = 0; i < N; ++i) {
-    for (int k = 0; k < M; ++k) {
-      double x = u[(size_t)i * M + k];
-      adam_ascent(x, adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k], phi[(size_t)i * M + k], *t, lr, b1, b2, eps);
-      if (clamp) x = std::min(1.0, std::max(0.0, x));
-      particles[(size_t)i * P + k] = lo[k] + x * (hi[k] - lo[k]);
-    }
-    for (int k = M; k < P; ++k)
-      adam_ascent(particles[(size_t)i * P + k], adam_m[(size_t)i * P + k], adam_v[(size_t)i * P + k],
-                  grad[(size_t)i * P + k], *t, lr, b1, b2, eps);
-  }
+  orc_svgd_update(N, M, P, lo, hi, particles, phi.data(), grad, adam_m, adam_v, t, lr, b1, b2, eps, clamp);
   if (phi_out) std::copy(phi.begin(), phi.end(), phi_out);
   if (bw_out) *bw_out = bw;
   return 0;

@@ -151,6 +151,9 @@ def lib():
             L.orc_svgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp,
                                         ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp, _dp]
+            L.orc_svgd_update.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp, _dp,
+                                          ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_int]
             L.orc_csvgd_loglik_grad.argtypes = [ctypes.POINTER(_Problem), ctypes.c_double, _dp, ctypes.c_int, _dp,
                                                 _dp, ctypes.c_int]
             L.orc_csvgd_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp,
@@ -447,6 +450,18 @@ class SvgdState:
                             self.v.ctypes.data_as(_dp), ctypes.byref(self.t), self.lr, self.beta1, self.beta2,
                             self.eps, int(self.clamp), phi.ctypes.data_as(_dp), ctypes.byref(bw))
         return phi, bw.value
+
+    def update(self, particles, phi, grad):
+        """The update half of ``step`` with given directions: Adam ascent of
+        the theta rows on phi [N][M] (unit-box coordinates) and of the
+        shooting-state rows on grad [N][P] (Algorithm 1)."""
+        assert particles.dtype == np.float64 and particles.flags.c_contiguous
+        ph, pp = _d(phi)
+        g, gp = _d(grad)
+        lib().orc_svgd_update(self.N, self.M, self.P, self.lo.ctypes.data_as(_dp), self.hi.ctypes.data_as(_dp),
+                              particles.ctypes.data_as(_dp), pp, gp, self.m.ctypes.data_as(_dp),
+                              self.v.ctypes.data_as(_dp), ctypes.byref(self.t), self.lr, self.beta1, self.beta2,
+                              self.eps, int(self.clamp))
 
 
 # --------------------------------------------------------------------------

@@ -107,3 +107,44 @@ def test_particles_that_are_not_finite_sit_out_the_step():
     np.testing.assert_array_equal(phi[live], phi_l)
     np.testing.assert_array_equal(xa[live], xl)
     assert np.all(np.isnan(phi[dead]))
+
+
+def test_update_with_given_directions_is_the_update_half_of_a_step():
+    """The update alone, fed the step's own phi and gradient, moves the
+    particles and the Adam moments exactly as the whole step does (Algorithm
+    1: the direction, then the Adam ascent); and its Adam arithmetic is the
+    textbook one: after two steps with directions d1, d2 the move of an entry
+    is lr (m2 / (1 - b1^2)) / (sqrt(v2 / (1 - b2^2)) + eps) on top of the
+    first step's lr sign(d1)."""
+    rng = np.random.default_rng(8)
+    N, M, P = 30, 3, 7
+    lo, hi = rng.uniform(-1, 0, M), rng.uniform(1, 2, M)
+    x0 = np.ascontiguousarray(np.concatenate([rng.uniform(lo, hi, (N, M)), rng.normal(size=(N, P - M))], 1))
+    g1, g2 = rng.normal(size=(N, P)), rng.normal(size=(N, P))
+    lr, b1, b2, eps = 0.05, 0.9, 0.999, 1e-8
+    whole = orc.SvgdState(N, P, lo, hi, lr=lr, clamp=False)
+    half = orc.SvgdState(N, P, lo, hi, lr=lr, clamp=False)
+    xw, xh = x0.copy(), x0.copy()
+    phis = []
+    for g in (g1, g2):
+        phi, _ = whole.step(xw, g)
+        half.update(xh, phi, g)
+        phis.append(phi)
+    np.testing.assert_array_equal(xh, xw)
+    np.testing.assert_array_equal(half.m, whole.m)
+    np.testing.assert_array_equal(half.v, whole.v)
+    # Kingma and Ba's bias-corrected update, written out, on the shooting rows
+    d1, d2 = g1[:, M:], g2[:, M:]
+    m2 = b1 * (1 - b1) * d1 + (1 - b1) * d2
+    v2 = b2 * (1 - b2) * d1 ** 2 + (1 - b2) * d2 ** 2
+    step1 = lr * ((1 - b1) * d1 / (1 - b1)) / (np.sqrt((1 - b2) * d1 ** 2 / (1 - b2)) + eps)
+    step2 = lr * (m2 / (1 - b1 ** 2)) / (np.sqrt(v2 / (1 - b2 ** 2)) + eps)
+    np.testing.assert_allclose(xh[:, M:], x0[:, M:] + step1 + step2, rtol=0, atol=1e-13)
+    # theta rows: the same two moves in unit-box coordinates, on phi
+    p1, p2 = phis
+    m2u = b1 * (1 - b1) * p1 + (1 - b1) * p2
+    v2u = b2 * (1 - b2) * p1 ** 2 + (1 - b2) * p2 ** 2
+    u0 = (x0[:, :M] - lo) / (hi - lo)
+    u2 = u0 + lr * np.sign(p1) * np.abs(p1) / (np.abs(p1) + eps) + lr * (m2u / (1 - b1 ** 2)) / (
+        np.sqrt(v2u / (1 - b2 ** 2)) + eps)
+    np.testing.assert_allclose(xh[:, :M], lo + u2 * (hi - lo), rtol=0, atol=1e-12)
