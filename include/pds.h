@@ -37,7 +37,8 @@ extern "C" {
 #define PDS_ERR_ARG (-1)         /* invalid argument (NULL, size out of range) */
 #define PDS_ERR_CUDA (-2)        /* a CUDA runtime call or launch failed       */
 #define PDS_ERR_OOM (-3)         /* device allocation failed                   */
-#define PDS_ERR_NONFINITE (-4)   /* reserved: non-finite result reported       */
+#define PDS_ERR_NONFINITE (-4)   /* an SVGD step found no finite particle      */
+#define PDS_ERR_TIMEOUT (-5)     /* a bounded device wait ran out              */
 #define PDS_ERR_BUDGET (-6)      /* job larger than the server's memory budget */
 #define PDS_ERR_UNSUPPORTED (-7) /* configuration outside the compiled range   */
 
@@ -288,6 +289,15 @@ int pds_svgd_destroy(pds_svgd_t s);
  * the median passes come from tensor-core products (split tf32, fp32
  * accumulation, clamped at 0); 1 = CUDA cores. */
 #define PDS_OPT_MEDIAN_CUDA_CORES 5
+/* PDS_OPT_WAIT_LIMIT (value >= 0, default 2^24): how many times a warp of a
+ * tensor-core pass polls an mbarrier for the copy or product it needs before
+ * it gives up; 0 tests the barrier once and never waits.  A pass that gives
+ * up lets the copies and products it has in flight finish (with the default
+ * limit), frees its tensor memory and returns; the step then completes with
+ * results that are not valid, and PDS_ERR_TIMEOUT is reported as below.  The
+ * default is far above any wait a healthy pass makes (a few microseconds);
+ * small values exist to exercise that path. */
+#define PDS_OPT_WAIT_LIMIT 6
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);
 
 /* Constrained SVGD update (Algorithm 1) for particles laid out as
@@ -306,9 +316,23 @@ int pds_svgd_set_csvgd(pds_svgd_t s, int enable, int n_def);
  *  particles    : device [P][N] float (read and written).
  *  grad         : device [P][N] float, d log p / d particles.
  *  bandwidth_out: device float scalar or NULL (the bandwidth bw used).
- *  phi_out      : device [M][N] float or NULL (phi in u coordinates). */
+ *  phi_out      : device [M][N] float or NULL (phi in u coordinates).
+ * Two conditions are found by the device while a step runs, after the call
+ * that queued it has returned: a tensor-core pass that gave up waiting
+ * (PDS_ERR_TIMEOUT; that step's particles are not valid) and a step in which
+ * no particle had finite coordinates and gradient (PDS_ERR_NONFINITE; every
+ * particle then sits out and keeps NaN).  The kernel writes them to a word of
+ * mapped host memory; the next pds_svgd_step or pds_iterate on the state
+ * returns the code (TIMEOUT first) instead of queuing work, and clears it.
+ * pds_svgd_status synchronises the state's stream and returns it at once;
+ * pds_iterate_host returns it after its final synchronisation. */
 int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad,
                   float* bandwidth_out, float* phi_out);
+
+/* Synchronise the state's stream, then return and clear the status the
+ * device reported for the steps run so far: PDS_OK, PDS_ERR_TIMEOUT or
+ * PDS_ERR_NONFINITE (see pds_svgd_step). */
+int pds_svgd_status(pds_svgd_t s);
 
 /* Reset Adam moments and the step count to zero. */
 int pds_svgd_reset(pds_svgd_t s);
@@ -449,21 +473,29 @@ int pds_server_job_gate(pds_server_t s, long long job_id, int* checks, double* l
  * framework's allocator or memory-pool callback, or a process whose device
  * memory is fully reserved up front -- and so cannot create the workspace
  * that pds_svgd_create allocates.  It computes the same bandwidth as
- * pds_svgd_step (lower median of the pairwise squared distances of the
- * unit-box coordinates, divided by log N; 1 if N < 2 or the median is 0).
+ * pds_svgd_step with a zero gradient (lower median of the pairwise squared
+ * distances of the unit-box coordinates over the live particles, divided by
+ * log of their number; 1 if fewer than 2 are live or the median is 0).  A
+ * particle with a coordinate that is not finite sits out, as in
+ * pds_svgd_step.
  *  theta        : device [M][N] float (e.g. the first M rows of a particle array).
  *  theta_lo/hi  : host [M] box.
  *  bandwidth_out: device float scalar (written).
  *  cuda_stream  : cudaStream_t the work is queued on (NULL = legacy default).
  * Its scratch is one file-scope device array of 16 KiB + 4 MiB that every GPU
- * loading the library holds until the process exits; N * M must not exceed
- * 1048576 (PDS_ERR_ARG otherwise, with a message) and 1 <= M <= 16.  The
- * first call on each device looks up that array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one array and clears what must start at zero, so calls
- * whose work overlaps on the GPU (different streams, or several host
- * threads) race and must be serialised by the caller.  The call allocates
- * nothing and returns after queuing its kernels. */
+ * loading the library holds until the process exits; 1 <= N <= 65536 (pair
+ * counts are 32-bit, as in pds_svgd_create), N * M <= 1048576 and
+ * 1 <= M <= 16 (PDS_ERR_ARG otherwise, with a message).  The first call on
+ * each device looks up that array's device address (with that device
+ * current); make that first call before any stream capture.  With lazy
+ * module loading (CUDA's default) that first call, or the first launch of
+ * any SVGD kernel of the library on the device, also loads the library's
+ * device code and reserves the array, which allocates device memory: make
+ * the first call at start-up, outside the context that cannot allocate.
+ * Every call shares the one array and clears what must start at zero, so
+ * calls whose work overlaps on the GPU (different streams, or several host
+ * threads) race and must be serialised by the caller.  After that first call
+ * the entry point allocates nothing and returns after queuing its kernels. */
 int pds_bandwidth_noalloc(const float* theta, int N, int M, const float* theta_lo,
                           const float* theta_hi, float* bandwidth_out, void* cuda_stream);
 

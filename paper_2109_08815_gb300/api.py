@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_PKG, "libpds.so")
 PDS_SYSTEM_PLANAR_CHAIN = 1
 PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
 OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES, OPT_MEDIAN_CUDA_CORES = 1, 2, 3, 4, 5
+OPT_WAIT_LIMIT = 6
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_BUDGET, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 COMBINE_SUM, COMBINE_PRODUCT = 0, 1
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2
 GATE_NONE, GATE_MMD2, GATE_KNN_KL = 0, 1, 2
@@ -101,6 +103,7 @@ EXPORTS = {
     "pds_svgd_destroy": ([_vp], ctypes.c_int),
     "pds_svgd_step": ([_vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "pds_svgd_reset": ([_vp], ctypes.c_int),
+    "pds_svgd_status": ([_vp], ctypes.c_int),
     "pds_svgd_set_option": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_svgd_set_csvgd": ([_vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "pds_iterate": ([_vp, _vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
@@ -147,7 +150,12 @@ EXPORTS = {
 
 
 class PdsError(RuntimeError):
-    pass
+    """A failed call; ``code`` is its PDS_ERR_* status (0 when the binding
+    itself refused the call)."""
+
+    def __init__(self, msg: str, code: int = 0):
+        super().__init__(msg)
+        self.code = code
 
 
 def lib():
@@ -170,7 +178,7 @@ def lib():
 def _check(rc: int, what: str):
     if rc != 0:
         L = lib()
-        raise PdsError(f"{what}: {L.pds_strerror(rc).decode()} ({rc}): {L.pds_last_error().decode()}")
+        raise PdsError(f"{what}: {L.pds_strerror(rc).decode()} ({rc}): {L.pds_last_error().decode()}", rc)
 
 
 def last_launch_count() -> int:
@@ -436,6 +444,12 @@ class Svgd:
 
     def reset(self):
         _check(lib().pds_svgd_reset(self._h), "pds_svgd_reset")
+
+    def status(self) -> int:
+        """pds_svgd_status: synchronise the state's stream and return (and
+        clear) what the device reported for the steps run so far: 0,
+        ERR_TIMEOUT or ERR_NONFINITE."""
+        return int(lib().pds_svgd_status(self._h))
 
     def set_option(self, option: int, value: int):
         _check(lib().pds_svgd_set_option(self._h, int(option), int(value)), "pds_svgd_set_option")

@@ -97,10 +97,12 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
                                                                   const int2* __restrict__ tiles, int n_tiles,
                                                                   SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
                                                                   unsigned long long cap, int mode,
-                                                                  int only_in_fallback) {
+                                                                  int only_in_fallback, int wait_limit) {
   using D = MtDims<MM>;
   constexpr int KA = D::KA;
-  constexpr int kLimit = 1 << 24;  // mbarrier polls before giving up
+  // wait_limit: mbarrier polls before a wait gives up (the kernel then
+  // flags ctl->tc_error); the waits that let copies and products in flight
+  // finish before shared memory and TMEM are released take kDrainLimit
   extern __shared__ __align__(1024) unsigned char smem[];
   float* cbuf = (float*)(smem + 2 * D::kStage);  // per-warp candidates, or the histogram in radix modes
   uint64_t* bars = (uint64_t*)(smem + 2 * D::kStage + D::kCand);  // full[2], mma[2], free[2]
@@ -139,17 +141,19 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   const uint32_t tbase = *tslot;
 
   // Copies and products are issued by whichever warp can first do so (one
-  // elected lane; operands warp-uniform).  Each thread remembers its latest
-  // copy and product: in flight there is at most one copy per stage and one
-  // product per accumulator, each the latest of the thread that issued it.
-  int my_load = -1, my_mma = -1;
+  // elected lane; operands warp-uniform).  In flight there is at most one
+  // copy per stage and one product per accumulator (stage s is refilled only
+  // once the product that read it is done, accumulator s only once every
+  // warp has read it), so each thread remembers, per stage and accumulator,
+  // the latest copy and product it issued there.
+  int my_load[2] = {-1, -1}, my_mma[2] = {-1, -1};
   auto load = [&](int k, int2 tj, bool needA) {  // tile f0 + k, coordinates tj, into stage k & 1
     const int s = k & 1;
     unsigned char* stg = smem + s * D::kStage;
     tc::mbar_expect_tx(bars + s, needA ? 2 * D::kTile : D::kTile);
     if (needA) tc::bulk_g2s(stg, imgA + (size_t)tj.x * (D::kTile / 4), D::kTile, bars + s);
     tc::bulk_g2s(stg + D::kTile, imgB + (size_t)tj.y * (D::kTile / 4), D::kTile, bars + s);
-    my_load = k;
+    my_load[s] = k;
   };
   // product of tile k into accumulator k & 1, issued by a whole warp
   auto issue = [&](int k) {
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
         tc::mma_ss_el(tbase + 128 * s, tc::smem_desc(Aop[p] + ks * 256, 128, sbo),
                       tc::smem_desc(Bop[p] + ks * 256, 128, sbo), id, (p > 0 || ks > 0) ? 1u : 0u);
     tc::mma_commit_el(bars + 2 + s);
-    my_mma = k;
+    my_mma[s] = k;
   };
 
   bool ok = true;
@@ -178,10 +182,10 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   }
   if (warp == 0 && nk > 0) {
     // the first two products (both accumulators start free)
-    ok = __all_sync(0xffffffffu, tc::mbar_wait(bars + 0, 0, kLimit)) != 0;
+    ok = __all_sync(0xffffffffu, tc::mbar_test(bars + 0, 0) || tc::mbar_wait(bars + 0, 0, wait_limit)) != 0;
     if (ok) issue(0);
     if (ok && nk > 1) {
-      ok = __all_sync(0xffffffffu, tc::mbar_wait(bars + 1, 0, kLimit)) != 0;
+      ok = __all_sync(0xffffffffu, tc::mbar_test(bars + 1, 0) || tc::mbar_wait(bars + 1, 0, wait_limit)) != 0;
       if (ok) issue(1);
     }
   }
@@ -205,7 +209,8 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   for (int k = 0; k < nk; ++k) {
     const int s = k & 1;
     const int2 tl = (lane == 0 && k + 2 < nk) ? tiles[f0 + k + 2] : make_int2(0, 0);
-    bool w = ok && tc::mbar_wait(bars + 2 + s, (uint32_t)(k >> 1) & 1u, kLimit);
+    bool w = ok && (tc::mbar_test(bars + 2 + s, (uint32_t)(k >> 1) & 1u) ||
+                    tc::mbar_wait(bars + 2 + s, (uint32_t)(k >> 1) & 1u, wait_limit));
     ok = __all_sync(0xffffffffu, w) != 0;
     if (!ok) break;
     tc::fence_after();
@@ -228,8 +233,11 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
     if (lane == 0 && k + 2 < nk) rel = atomicAdd(released + s, 1u);
     rel = __shfl_sync(0xffffffffu, rel, 0);
     if (k + 2 < nk && rel % kMtWarps == kMtWarps - 1) {
-      bool w2 = tc::mbar_wait(bars + 4 + s, (uint32_t)(k >> 1) & 1u, kLimit);
-      if (w2) w2 = tc::mbar_wait(bars + s, (uint32_t)((k + 2) >> 1) & 1u, kLimit);
+      bool w2 = tc::mbar_test(bars + 4 + s, (uint32_t)(k >> 1) & 1u) ||
+                tc::mbar_wait(bars + 4 + s, (uint32_t)(k >> 1) & 1u, wait_limit);
+      if (w2)
+        w2 = tc::mbar_test(bars + s, (uint32_t)((k + 2) >> 1) & 1u) ||
+             tc::mbar_wait(bars + s, (uint32_t)((k + 2) >> 1) & 1u, wait_limit);
       ok = __all_sync(0xffffffffu, w2) != 0;
       if (!ok) break;
       issue(k + 2);
@@ -314,8 +322,11 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
   if (*failed) {
     // a warp gave up: let the copies and products in flight finish (bounded)
     // before the shared memory and TMEM are released
-    if (my_load >= 0) tc::mbar_wait(bars + (my_load & 1), (uint32_t)(my_load >> 1) & 1u, kLimit);
-    if (my_mma >= 0) tc::mbar_wait(bars + 2 + (my_mma & 1), (uint32_t)(my_mma >> 1) & 1u, kLimit);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (my_load[s] >= 0) tc::mbar_wait(bars + s, (uint32_t)(my_load[s] >> 1) & 1u, kDrainLimit);
+      if (my_mma[s] >= 0) tc::mbar_wait(bars + 2 + s, (uint32_t)(my_mma[s] >> 1) & 1u, kDrainLimit);
+    }
   }
   __syncthreads();
   if (mode != 0) {
@@ -352,7 +363,7 @@ size_t median_tc_floats(int N, int M) {
 template <int MM>
 static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const int* work, int n_work, SvgdCtl* ctl,
                                 float* cand, unsigned long long cap, int mode, int only_in_fallback, bool prep,
-                                cudaStream_t st) {
+                                int wait_limit, cudaStream_t st) {
   using D = MtDims<MM>;
   const int Npad = (N + kMtRows - 1) / kMtRows * kMtRows;
   const int nt = Npad / kMtRows;
@@ -391,19 +402,20 @@ static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const 
   const int grid = n_work < grid_of[dev] ? n_work : grid_of[dev];
   if (grid < 1) return cudaSuccess;
   median_tc_kernel<MM><<<grid, kMtThreads, D::kBytes, st>>>(N, imgA, imgB, reinterpret_cast<const int2*>(work),
-                                                           n_work, ctl, cand, cap, mode, only_in_fallback);
+                                                           n_work, ctl, cand, cap, mode, only_in_fallback,
+                                                           wait_limit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_median_tc(int N, int M, const float* u, float* img, const int* work, int n_work, SvgdCtl* ctl,
                              float* cand, unsigned long long cap, int mode, int only_in_fallback, bool prep,
-                             cudaStream_t st) {
-  if (M <= 2) return median_tc_mm<2>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
-  if (M <= 4) return median_tc_mm<4>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
-  if (M <= 8) return median_tc_mm<8>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
-  if (M <= 10) return median_tc_mm<10>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
-  if (M <= 12) return median_tc_mm<12>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
-  return median_tc_mm<16>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, st);
+                             int wait_limit, cudaStream_t st) {
+  if (M <= 2) return median_tc_mm<2>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
+  if (M <= 4) return median_tc_mm<4>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
+  if (M <= 8) return median_tc_mm<8>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
+  if (M <= 10) return median_tc_mm<10>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
+  if (M <= 12) return median_tc_mm<12>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
+  return median_tc_mm<16>(N, M, u, img, work, n_work, ctl, cand, cap, mode, only_in_fallback, prep, wait_limit, st);
 }
 
 }  // namespace pds

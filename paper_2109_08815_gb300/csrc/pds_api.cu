@@ -175,6 +175,7 @@ const char* pds_strerror(int code) {
     case PDS_ERR_CUDA: return "CUDA error";
     case PDS_ERR_OOM: return "out of device memory";
     case PDS_ERR_NONFINITE: return "non-finite value";
+    case PDS_ERR_TIMEOUT: return "device wait timed out";
     case PDS_ERR_BUDGET: return "over the memory budget";
     case PDS_ERR_UNSUPPORTED: return "unsupported configuration";
     default: return "unknown status";
@@ -472,10 +473,14 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
       (e = cudaMalloc(&s->w.phi_part, (size_t)s->w.chunks * MN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.adam_m, PN * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->w.adam_v, PN * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&s->w.ctl, sizeof(SvgdCtl))) != cudaSuccess) {
+      (e = cudaMalloc(&s->w.ctl, sizeof(SvgdCtl))) != cudaSuccess ||
+      (e = cudaHostAlloc(&s->h_status, sizeof(int), cudaHostAllocMapped)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&s->w.status_flags, s->h_status, 0)) != cudaSuccess) {
     pds_svgd_destroy(s);
     return cuda_fail(e, "svgd allocation");
   }
+  *(volatile int*)s->h_status = 0;
+  s->w.wait_limit = kWaitLimitDefault;
   if (N >= 2048) {
     const int n_items = median_tc_work_items(N, nullptr);
     std::vector<int> items(2 * (size_t)n_items);
@@ -494,6 +499,11 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
 
 int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
   if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
+  if (option == PDS_OPT_WAIT_LIMIT) {
+    if (value < 0) return fail(PDS_ERR_ARG, "wait limit %d < 0", value);
+    s->w.wait_limit = value;
+    return PDS_OK;
+  }
   if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "option value must be 0 or 1");
   switch (option) {
     case PDS_OPT_FAST_MATH: s->sp.fast_math = value; return PDS_OK;
@@ -530,13 +540,37 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaFree(s->w.adam_m);
   cudaFree(s->w.adam_v);
   cudaFree(s->w.ctl);
+  if (s->h_status) cudaFreeHost(s->h_status);
   delete s;
   return PDS_OK;
+}
+
+// Status that the device reported for steps already run (the mapped host
+// word, cleared by reading): PDS_ERR_TIMEOUT before PDS_ERR_NONFINITE.
+static int take_status(pds_svgd* s) {
+  if (!s->h_status) return PDS_OK;
+  volatile int* h = s->h_status;
+  const int f = *h;
+  if (!f) return PDS_OK;
+  *h = 0;
+  if (f & kStatusTimeout)
+    return fail(PDS_ERR_TIMEOUT, "a tensor-core pass of an SVGD step gave up waiting for its copies or products; "
+                                 "that step's particles are not valid");
+  return fail(PDS_ERR_NONFINITE, "an SVGD step found no particle with finite coordinates and gradient");
+}
+
+int pds_svgd_status(pds_svgd_t s) {
+  if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
+  const cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "svgd status");
+  return take_status(s);
 }
 
 int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* bandwidth_out, float* phi_out) {
   g_launches = 0;
   if (!s || !particles || !grad) return fail(PDS_ERR_ARG, "NULL argument");
+  const int st = take_status(s);  // reported by a step already run: this one is not queued
+  if (st != PDS_OK) return st;
   int n = 0;
   SvgdWork w = s->w;
   if (s->full_passes) w.cand_cap = 0;
@@ -591,7 +625,9 @@ int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int i
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "copy results to host");
   g_launches = launches;
-  return PDS_OK;
+  if (s->stream != p->stream && (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+    return cuda_fail(e, "svgd stream");
+  return take_status(s);
 }
 
 }  // extern "C"

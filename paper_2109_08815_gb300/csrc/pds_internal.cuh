@@ -151,7 +151,15 @@ struct SvgdWork {
   float* adam_v;   // [P][N]
   SvgdCtl* ctl;
   int chunks;
+  int wait_limit;     // mbarrier polls before a tensor-core pass gives up (0: test once, never wait)
+  int* status_flags;  // device alias of a mapped host word: kStatus* bits of the steps since the host last read it
 };
+
+// Bits of SvgdWork::status_flags, set by the last kernel of a step.
+constexpr int kStatusTimeout = 1;    // a tensor-core pass gave up waiting (the step's results are not valid)
+constexpr int kStatusNoneLive = 2;   // no particle had finite coordinates and gradient
+constexpr int kWaitLimitDefault = 1 << 24;
+constexpr int kDrainLimit = 1 << 24;  // polls of the waits that let copies and products in flight finish
 
 cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
                              float* phi_out, cudaStream_t st, int* launches);
@@ -164,7 +172,7 @@ size_t median_tc_floats(int N, int M);
 int median_tc_work_items(int N, int* out);
 cudaError_t launch_median_tc(int N, int M, const float* u, float* img, const int* work, int n_work, SvgdCtl* ctl,
                              float* cand, unsigned long long cap, int mode, int only_in_fallback, bool prep,
-                             cudaStream_t st);
+                             int wait_limit, cudaStream_t st);
 cudaError_t launch_phi_tc(int N, int M, const SvgdWork& w, int* slots_used, cudaStream_t st);
 int phi_tc_slots(int N);
 int svgd_phi_partials(int N);
@@ -205,6 +213,7 @@ struct pds_problem {
 struct pds_svgd {
   pds::SvgdParams sp;
   pds::SvgdWork w{};
+  int* h_status = nullptr;  // mapped host word behind w.status_flags
   cudaStream_t stream;
   int full_passes = 0;
   int phi_cuda_cores = 0;

@@ -38,6 +38,7 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     ctl->mode = mode;
     ctl->n_live = 0u;
     ctl->live_blocks = 0u;
+    ctl->tc_error = 0;
   }
   const int total = sp.M * sp.N;
   const int k = idx < total ? idx / sp.N : -1;
@@ -754,13 +755,23 @@ __global__ void __launch_bounds__(kTile) svgd_phi_kernel(int N, int M, const flo
   }
 }
 
+// The step's last kernel.  It also reports, into the mapped host word
+// status (may be NULL), a tensor-core pass of this step that gave up waiting
+// and a step in which no particle was live.
 __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float* __restrict__ X,
                                  const float* __restrict__ G, const float* __restrict__ phi_part, int chunks,
                                  float* __restrict__ am, float* __restrict__ av, float* __restrict__ bw_out,
-                                 float* __restrict__ phi_out) {
+                                 float* __restrict__ phi_out, int* __restrict__ status) {
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t total = (size_t)sp.P * sp.N;
   if (idx == 0 && bw_out) *bw_out = ctl->bw;
+  if (idx == 0 && status) {
+    const int f = (ctl->tc_error ? kStatusTimeout : 0) | (ctl->n_live == 0u ? kStatusNoneLive : 0);
+    if (f) {
+      volatile int* h = status;
+      *h = *h | f;
+    }
+  }
   if (idx < 16) ctl->gmax[idx] = 0u;  // for the next step's prep kernel
   if (idx >= total) return;
   const int r = (int)(idx / sp.N);
@@ -843,7 +854,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
       median_sample_sort_kernel<<<1, kSampleThreads, 0, st>>>(w.samp, w.ctl);
       n += 2;
       if (tcm) {
-        e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, w.cand, w.cand_cap, 0, 0, true, st);
+        e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, w.cand, w.cand_cap, 0, 0, true,
+                             w.wait_limit, st);
         if (e != cudaSuccess) return e;
         prepped = true;
         n += 2;
@@ -864,7 +876,7 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     for (int pass = 0; pass < 3; ++pass) {
       if (tcm) {
         cudaError_t e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, nullptr, 0ull, pass + 1,
-                                         bracket ? 1 : 0, !prepped, st);
+                                         bracket ? 1 : 0, !prepped, w.wait_limit, st);
         if (e != cudaSuccess) return e;
         n += prepped ? 1 : 2;
         prepped = true;
@@ -897,7 +909,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     }
     const size_t total = (size_t)sp.P * N;
     svgd_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, w.ctl, X, G, w.phi_part, chunks_used,
-                                                                      w.adam_m, w.adam_v, bw_out, phi_out);
+                                                                      w.adam_m, w.adam_v, bw_out, phi_out,
+                                                                      w.status_flags);
     n += 2;
   }
   if (launches) *launches += n;
@@ -934,6 +947,7 @@ namespace pds {
 
 constexpr int kNoAllocCtlFloats = 4096;        // control block, padded to 16 KiB
 constexpr int kNoAllocMaxElems = 1 << 20;      // N * M <= 1,048,576 (4 MiB of coordinates)
+constexpr int kNoAllocMaxN = 65536;
 static_assert(sizeof(SvgdCtl) <= kNoAllocCtlFloats * sizeof(float), "control block does not fit");
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocCtlFloats + kNoAllocMaxElems];
@@ -949,17 +963,50 @@ __global__ void noalloc_prep_kernel(int N, int M, NoAllocBox box, const float* _
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < kHistBins) ctl->hist[idx] = 0u;
   if (idx == 0) {
-    const unsigned long long pairs = (unsigned long long)N * (unsigned long long)(N - 1) / 2ull;
     ctl->prefix = 0u;
-    ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
+    ctl->rank = 0u;
     ctl->bw = 1.0f;
     ctl->med = 0.0f;
     ctl->mode = 1;
-    ctl->n_live = (unsigned int)N;
+    ctl->n_live = 0u;
+    ctl->live_blocks = 0u;
   }
   if (idx < M * N) {
     const int k = idx / N;
     u[idx] = (theta[idx] - box.lo[k]) / (box.hi[k] - box.lo[k]);
+  }
+}
+
+// As pds_svgd_step's liveness pass, on the coordinates alone: a particle
+// with a coordinate that is not finite sits out (its u becomes NaN, so its
+// pairs are skipped), the live particles are counted, and the last block
+// sets the median's rank over the live pairs.
+__global__ void __launch_bounds__(256) noalloc_live_kernel(int N, int M, SvgdCtl* __restrict__ ctl,
+                                                           float* __restrict__ u) {
+  __shared__ unsigned int blk;
+  __shared__ bool last;
+  if (threadIdx.x == 0) blk = 0u;
+  __syncthreads();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < N) {
+    bool live = true;
+    for (int k = 0; k < M; ++k) live &= isfinite(u[(size_t)k * N + i]);
+    if (live) atomicAdd(&blk, 1u);
+    else
+      for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (blk) atomicAdd(&ctl->n_live, blk);
+    __threadfence();
+    last = atomicAdd(&ctl->live_blocks, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long nl = atomicAdd(&ctl->n_live, 0u);
+    const unsigned long long pairs = nl * (nl > 0 ? nl - 1ull : 0ull) / 2ull;
+    ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
   }
 }
 
@@ -972,6 +1019,7 @@ static cudaError_t noalloc_bandwidth_mm(int N, int M, const NoAllocBox& box, con
   float* u = scratch + kNoAllocCtlFloats;
   const int total = (M * N > kHistBins) ? M * N : kHistBins;
   noalloc_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(N, M, box, theta, ctl, u);
+  noalloc_live_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, M, ctl, u);
   if (N >= 2) {
     const int nt = (N + kSpan - 1) / kSpan;
     const long long all_tiles = (long long)nt * nt;
@@ -997,6 +1045,10 @@ extern "C" int pds_bandwidth_noalloc(const float* theta, int N, int M, const flo
   if (M < 1 || M > kMaxTheta) return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: M outside 1..16");
   if (N < 1 || (long long)N * M > kNoAllocMaxElems)
     return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: N * M must be in 1..1048576 (static scratch limit)");
+  // the radix histogram and the median's rank count pairs in 32 bits
+  // (N (N - 1) / 2 < 2^31 for N <= 65536), as in pds_svgd_create
+  if (N > kNoAllocMaxN)
+    return set_error(PDS_ERR_ARG, "pds_bandwidth_noalloc: N must be at most 65536 (32-bit pair counts)");
   NoAllocBox box;
   for (int k = 0; k < kMaxTheta; ++k) { box.lo[k] = 0.f; box.hi[k] = 1.f; }
   for (int k = 0; k < M; ++k) {

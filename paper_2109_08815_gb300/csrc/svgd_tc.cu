@@ -175,12 +175,14 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
                                                                 const float* __restrict__ imgBV,
                                                                 const float* __restrict__ u,
                                                                 SvgdCtl* __restrict__ ctl, float* __restrict__ phi_part,
-                                                                int slots) {
+                                                                int slots, int wait_limit) {
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   using SM = TcSmem<MM>;
   constexpr int S = SM::kStages;
   constexpr int NE = TcAcc<MM>::NE;
-  constexpr int kLimit = 1 << 24;  // mbarrier polls before giving up
+  // wait_limit: mbarrier polls before a wait gives up (the kernel then
+  // flags ctl->tc_error); the waits that let copies and products in flight
+  // finish before shared memory and TMEM are released take kDrainLimit
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* sA = smem;                       // two a slots (hi | lo), by row parity
   unsigned char* sStage = smem + 2 * 2 * SM::kA;  // S stages of (b hi | b lo | v hi | v lo)
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
   bool ok = true;
   // waits that are usually already complete test the barrier first
   auto wait = [&](uint64_t* bar, uint32_t parity) {
-    return tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
+    return tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, wait_limit);
   };
 
   if (warp == kPhiProducer) {
@@ -267,14 +269,14 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         ctl->tc_error = 1;
         // let the copies in flight land (bounded) before shared memory is released
         for (int k = last - Se + 1 > 0 ? last - Se + 1 : 0; k <= last; ++k)
-          tc::mbar_wait(full + k % Se, (uint32_t)(k / Se) & 1u, kLimit);
+          tc::mbar_wait(full + k % Se, (uint32_t)(k / Se) & 1u, kDrainLimit);
       }
     }
   } else if (warp == kPhiGramWarp || warp == kPhiPvWarp) {
     // ------------------------------------------------------------ issuers
     if (nk > 0) {
       auto wait = [&](uint64_t* bar, uint32_t parity) {
-        const bool w = tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, kLimit);
+        const bool w = tc::mbar_test(bar, parity) || tc::mbar_wait(bar, parity, wait_limit);
         return __all_sync(0xffffffffu, w) != 0;
       };
       const uint32_t s0 = tc::smem_u32(smem);
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         }
         if (!ok) {
           if (lane == 0) ctl->tc_error = 1;
-          if (last >= 0) tc::mbar_wait(g_done + last % NE, (uint32_t)(last / NE) & 1u, kLimit);
+          if (last >= 0) tc::mbar_wait(g_done + last % NE, (uint32_t)(last / NE) & 1u, kDrainLimit);
         }
       } else {
         // second product of tile k once every exponent warp wrote its kernel
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
         }
         if (!ok) {
           if (lane == 0) ctl->tc_error = 1;
-          if (last >= 0) tc::mbar_wait(pv_done + last % NE, (uint32_t)(last / NE) & 1u, kLimit);
+          if (last >= 0) tc::mbar_wait(pv_done + last % NE, (uint32_t)(last / NE) & 1u, kDrainLimit);
         }
       }
     }
@@ -358,7 +360,8 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
     int seg = 0, I = I0, J = J0;  // tile k's row segment, row and column
     for (int k = 0; k < nk; ++k) {
       if (k > 0 && J == 0) ++seg;
-      const bool w = tc::mbar_wait(g_done + k % NE, (uint32_t)(k / NE) & 1u, kLimit);
+      const bool w = tc::mbar_test(g_done + k % NE, (uint32_t)(k / NE) & 1u) ||
+                     tc::mbar_wait(g_done + k % NE, (uint32_t)(k / NE) & 1u, wait_limit);
       ok = __all_sync(0xffffffffu, w) != 0;
       if (!ok) break;
       tc::fence_after();
@@ -384,7 +387,8 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
       const bool last = (k == nk - 1) || row_end;
       if (epi && last) {
         // this row segment's outputs: wait for its last second product, then read them
-        const bool w2 = tc::mbar_wait(o_ready + (seg & 1), (uint32_t)(seg >> 1) & 1u, kLimit);
+        const bool w2 = tc::mbar_test(o_ready + (seg & 1), (uint32_t)(seg >> 1) & 1u) ||
+                        tc::mbar_wait(o_ready + (seg & 1), (uint32_t)(seg >> 1) & 1u, wait_limit);
         ok = __all_sync(0xffffffffu, w2) != 0;
         if (!ok) break;
         tc::fence_after();
@@ -485,7 +489,8 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  phi_tc_kernel<MM><<<G, kPhiThreads, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, slots);
+  phi_tc_kernel<MM><<<G, kPhiThreads, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, slots,
+                                                  w.wait_limit);
   *slots_used = slots;
   return cudaGetLastError();
 }

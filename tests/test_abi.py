@@ -36,6 +36,8 @@ def test_status_strings_without_gpu():
     lib.pds_strerror.restype = ctypes.c_char_p
     assert lib.pds_strerror(0) == b"ok"
     assert lib.pds_strerror(-1) == b"invalid argument"
+    assert lib.pds_strerror(-4) == b"non-finite value"
+    assert lib.pds_strerror(-5) == b"device wait timed out"
 
 
 def test_create_rejects_null_without_touching_the_gpu():

@@ -56,6 +56,54 @@ def test_noalloc_bandwidth_matches_svgd_step_on_two_calls_in_a_row():
         sv.close()
 
 
+def _noalloc(X, N, M, lo, hi, out):
+    L = api.lib()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return L.pds_bandwidth_noalloc(ctypes.c_void_p(X.data_ptr()), N, M, lo.ctypes.data_as(api._fp),
+                                   hi.ctypes.data_as(api._fp), ctypes.c_void_p(out.data_ptr()), stream)
+
+
+def test_noalloc_call_allocates_no_device_memory():
+    """After a first call (which loads the module and reserves the array), a
+    call on a new particle count leaves the device's free memory unchanged."""
+    M = 6
+    lo, hi, X1, _ = _particles(2000, M, M, 3)
+    _, _, X2, _ = _particles(2900, M, M, 4)
+    out = torch.empty(1, device="cuda", dtype=torch.float32)
+    assert _noalloc(X1, 2000, M, lo, hi, out) == 0
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert _noalloc(X2, 2900, M, lo, hi, out) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.isfinite(out.item()) and out.item() > 0
+
+
+def test_noalloc_particles_that_are_not_finite_sit_out():
+    """Particles with a non-finite coordinate take no part, as in
+    pds_svgd_step (checked against its bandwidth for the same particles with
+    a zero gradient); all particles but one non-finite gives bandwidth 1."""
+    N, M = 1200, 5
+    lo, hi, X, _ = _particles(N, M, M, 5)
+    X[1, 7] = float("nan")
+    X[0, 100] = float("inf")
+    X[4, N - 1] = float("-inf")
+    out = torch.empty(1, device="cuda", dtype=torch.float32)
+    assert _noalloc(X, N, M, lo, hi, out) == 0
+    torch.cuda.synchronize()
+    sv = api.Svgd(N, M, M, lo, hi)
+    bw_ref, _ = sv.step(X.clone(), torch.zeros_like(X))
+    torch.cuda.synchronize()
+    ref = float(bw_ref.item())
+    assert abs(float(out.item()) - ref) <= BW_RTOL * ref, (float(out.item()), ref)
+    sv.close()
+    Y = X.clone()
+    Y[2, 1:] = float("nan")
+    assert _noalloc(Y, N, M, lo, hi, out) == 0
+    torch.cuda.synchronize()
+    assert float(out.item()) == 1.0
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     L = api.lib()
     lo = np.zeros(16, np.float32)
@@ -67,3 +115,8 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
                                  hi.ctypes.data_as(api._fp), ctypes.c_void_p(out.data_ptr()), None)
     assert rc == -1
     assert b"1048576" in L.pds_last_error()
+    # N = 65537 with M = 1 fits the array but not the 32-bit pair counts
+    rc = L.pds_bandwidth_noalloc(ctypes.c_void_p(X.data_ptr()), 65537, 1, lo.ctypes.data_as(api._fp),
+                                 hi.ctypes.data_as(api._fp), ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == -1
+    assert b"65536" in L.pds_last_error()
