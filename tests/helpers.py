@@ -4,8 +4,15 @@ CUDA library, and compare their results with the stated tolerances.
 Tolerances (FP32 GPU path vs FP64 oracle on identical FP32-representable
 inputs):
   * log p: |dlogp| <= 1e-4 * |logp_ref| per particle.
-  * gradient: per particle and per block (theta rows; shooting-state rows),
-    max_k |g_k - g_ref_k| <= 1e-3 * max_k |g_ref_k|.
+  * gradient, per component k of a particle:
+        |g_k - g_ref_k| <= 1e-3 * |g_ref_k| + GRAD_FLOOR * max_{k' in B} |g_ref_k'|,
+    B the component's block (theta rows, or shooting-state rows).  The
+    floor is the absolute error of FP32 arithmetic: the adjoint sums
+    O(h) products whose magnitudes are those of the block's largest
+    component, each carrying relative rounding of 2^-24 times the growth of
+    a window's rollout, so a component far below the block's largest one is
+    known to that absolute accuracy only.
+  * phi (Eq. 1): |phi - phi_ref| <= PHI_TOL * max |phi_ref| per entry.
 """
 from __future__ import annotations
 
@@ -16,6 +23,8 @@ from paper_2109_08815_gb300 import workloads as wlmod
 
 LOGP_RTOL = 1e-4
 GRAD_RTOL = 1e-3
+GRAD_FLOOR = 1e-5
+PHI_TOL = 5e-4
 
 
 def physical(wl, theta):
@@ -56,13 +65,42 @@ def assert_logp_close(lp, lp_ref, rtol=LOGP_RTOL):
     return rel.max()
 
 
-def assert_grad_close(g, g_ref, M, rtol=GRAD_RTOL):
-    worst = 0.0
-    blocks = [slice(0, M)] + ([slice(M, g.shape[1])] if g.shape[1] > M else [])
+def grad_tolerance(g_ref, M, rtol=GRAD_RTOL, floor=GRAD_FLOOR):
+    """Per-entry tolerance of a gradient [N][P] (see the module docstring)."""
+    tol = np.empty_like(g_ref)
+    blocks = [slice(0, M)] + ([slice(M, g_ref.shape[1])] if g_ref.shape[1] > M else [])
     for blk in blocks:
-        a, r = g[:, blk], g_ref[:, blk]
-        scale = np.max(np.abs(r), axis=1)
-        err = np.max(np.abs(a - r), axis=1) / np.maximum(scale, 1e-30)
-        worst = max(worst, err.max())
-        assert np.all(err <= rtol), f"max grad err {err.max():.3e} (block {blk}) at particle {int(err.argmax())}"
-    return worst
+        r = np.abs(g_ref[:, blk])
+        tol[:, blk] = rtol * r + floor * np.max(r, axis=1, keepdims=True)
+    return tol
+
+
+def assert_grad_close(g, g_ref, M, rtol=GRAD_RTOL, floor=GRAD_FLOOR):
+    """Every component within its tolerance; returns the largest error in
+    units of the tolerance."""
+    tol = grad_tolerance(g_ref, M, rtol, floor)
+    ratio = np.abs(g - g_ref) / np.maximum(tol, 1e-300)
+    i, k = np.unravel_index(int(np.argmax(ratio)), ratio.shape)
+    assert ratio[i, k] <= 1.0, (f"grad component {k} of particle {i}: {g[i, k]:.7g} vs {g_ref[i, k]:.7g} "
+                                f"({ratio[i, k]:.2f} x its tolerance)")
+    return float(ratio.max())
+
+
+def phi_tolerance(u, g_u, bw, g_tol_u):
+    """Per-entry tolerance [N][M] of phi (Eq. 1) computed from a gradient
+    that is itself known to g_tol_u (unit-box coordinates, e.g. the GPU's
+    FP32 gradient against the oracle's): PHI_TOL * max |phi| for phi's own
+    arithmetic, plus (1/N) sum_j k_ij g_tol_j, the most the gradient error
+    can move the kernel-weighted sum (the repulsion term does not involve
+    the gradient)."""
+    phi = orc.svgd_phi(u, g_u, bw)
+    rep = orc.svgd_phi(u, np.zeros_like(g_u), bw)
+    carried = orc.svgd_phi(u, g_tol_u, bw) - rep
+    return PHI_TOL * np.max(np.abs(phi)) + carried
+
+
+def update_tolerance(x, width):
+    """FP32 Adam update of an entry against the FP64 update with the same
+    directions: x (and, for theta, u = (theta - lo) / w and back) rounded to
+    2^-24 relative a few times, the step lr m^/(sqrt(v^) + eps) to a few ulp."""
+    return 4e-7 * (np.abs(x) + width)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import LOGP_RTOL, f32_workload, observations, oracle_problem, particles
+from helpers import LOGP_RTOL, f32_workload, grad_tolerance, observations, oracle_problem, particles, phi_tolerance
 from oracle import pds_oracle as orc
 from paper_2109_08815_gb300 import api
 from paper_2109_08815_gb300 import workloads as wlmod
@@ -111,14 +111,22 @@ def test_batch_autotuned_iteration_matches_oracle():
         lp = lps[j].cpu().numpy().astype(np.float64)
         assert np.all(np.abs(lp - lp_ref) <= LOGP_RTOL * np.abs(lp_ref)), j
         x_ref = np.ascontiguousarray(xs[j].copy())
-        orc.SvgdState(w.N, w.P, w.lo, w.hi, lr=w.lr).step(x_ref, g_ref)
+        phi_ref, bw_ref = orc.SvgdState(w.N, w.P, w.lo, w.hi, lr=w.lr).step(x_ref, g_ref)
         width = np.concatenate([w.hi - w.lo, np.ones(w.P - w.M)])
         dx = np.abs(Xs[j].cpu().numpy().T - x_ref) / width
-        # Adam's first step moves each entry by about lr * sign(direction):
-        # entries agree to rounding except where the FP32 and FP64 directions
-        # straddle zero, which must stay rare.
-        assert np.mean(dx > 1e-4) <= 1e-3, (j, np.mean(dx > 1e-4))
+        # Adam's first step moves each entry by lr * sign(direction): entries
+        # agree to rounding except where the oracle's direction is within
+        # the GPU direction's tolerance of zero (phi from the FP32 gradient
+        # for theta, the gradient itself for the shooting states)
+        u = (xs[j][:, :w.M] - w.lo) / (w.hi - w.lo)
+        gtol = grad_tolerance(g_ref, w.M)
+        near0 = np.zeros_like(dx, dtype=bool)
+        near0[:, :w.M] = np.abs(phi_ref) <= phi_tolerance(u, g_ref[:, :w.M] * (w.hi - w.lo), bw_ref,
+                                                          gtol[:, :w.M] * (w.hi - w.lo))
+        near0[:, w.M:] = np.abs(g_ref[:, w.M:]) <= gtol[:, w.M:]
+        assert np.all(dx[~near0] <= 1e-4), (j, np.max(dx[~near0]))
         assert dx.max() <= 2.5 * w.lr, (j, dx.max())
+        assert np.mean(near0) <= 2e-2, (j, np.mean(near0))
     b.close()
 
 

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import LOGP_RTOL, f32_workload, observations, oracle_problem, particles
+from helpers import GRAD_FLOOR, LOGP_RTOL, PHI_TOL, f32_workload, observations, oracle_problem, particles
 from oracle import pds_oracle as orc
 from paper_2109_08815_gb300 import api
 from paper_2109_08815_gb300 import workloads as wlmod
@@ -78,9 +78,11 @@ def _check(wl, obs, x, c, K=None, fast=None, rtol=1e-3):
             err = np.max(np.abs(a - r))
             assert err <= 1e-6, (name, err)
         else:
-            scale = np.maximum(np.max(np.abs(r), axis=1), 1e-30)
-            err = np.max(np.abs(a - r), axis=1) / scale
-            assert err.max() <= rtol, (name, err.max(), int(err.argmax()))
+            # per component, as the unconstrained gradient (helpers)
+            tol = rtol * np.abs(r) + GRAD_FLOOR * np.max(np.abs(r), axis=1, keepdims=True)
+            ratio = np.abs(a - r) / np.maximum(tol, 1e-300)
+            err = ratio.max()
+            assert err <= 1.0, (name, err, np.unravel_index(int(ratio.argmax()), ratio.shape))
         worst[name] = float(np.max(err))
     prob.close()
     return worst
@@ -144,17 +146,24 @@ def test_update_matches_oracle():
     phi_ref, bw_ref = st.step(xo, g64)
     assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref
     phi = phi.cpu().numpy().T
-    assert np.max(np.abs(phi - phi_ref)) <= 2e-3 * np.max(np.abs(phi_ref))
+    assert np.max(np.abs(phi - phi_ref)) <= PHI_TOL * np.max(np.abs(phi_ref))
     xg = X.cpu().numpy().T.astype(np.float64)
     lam0 = wl.M + (wl.W - 1) * 2 * wl.n
     # multipliers: lam + lr g (float32 arithmetic against float64)
     np.testing.assert_allclose(xg[:, lam0:], xo[:, lam0:], rtol=1e-6, atol=1e-7)
-    # theta and shooting states: first Adam step moves each entry by about
-    # lr * sign(direction); entries agree except rare straddles of zero
+    # theta and shooting states: the first Adam step moves each entry by
+    # lr * sign(direction).  Both sides have the same gradient, so the
+    # shooting states agree to rounding; a theta entry may take the other
+    # sign only where its direction, phi plus the constraint direction, lies
+    # within phi's tolerance of zero
     width = np.concatenate([wl.hi - wl.lo, np.ones(lam0 - wl.M)])
     dx = np.abs(xg[:, :lam0] - xo[:, :lam0]) / width
-    assert np.mean(dx > 1e-4) <= 2e-3, np.mean(dx > 1e-4)
+    direction = phi_ref + g64[:, prob.P:prob.P + wl.M] * (wl.hi - wl.lo)
+    near0 = np.zeros_like(dx, dtype=bool)
+    near0[:, :wl.M] = np.abs(direction) <= PHI_TOL * np.max(np.abs(phi_ref))
+    assert np.all(dx[~near0] <= 1e-4), np.max(dx[~near0])
     assert dx.max() <= 2.5e-2
+    assert np.mean(near0) <= 2e-2
     # theta is not clipped to the box in the constrained method
     assert np.any(xg[:, wl.M - 1] > wl.hi[wl.M - 1])
     sv.close()

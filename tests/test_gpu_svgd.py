@@ -2,14 +2,19 @@
 Eq. 1's phi, Adam update) against the FP64 oracle, through the C ABI.
 
 Tolerances: bandwidth rel 1e-5 (the median of FP32 distances is within
-rounding of the FP64 median); phi per particle max-norm rel 2e-3 of the
-largest |phi| (FP32 sums of N kernel-weighted terms); updated particles
-abs 1e-4 of the box width (one Adam step moves at most lr).
+rounding of the FP64 median); phi within PHI_TOL of the largest |phi| (FP32
+sums of N kernel-weighted terms); the update, fed the GPU's own phi and the
+gradient, within FP32 rounding of the oracle's Adam (update_tolerance); the
+particles of independent runs within 1e-4 of the box width per step, except
+theta entries whose phi lies within its tolerance of zero, where FP32 and
+FP64 may take opposite signs and Adam's first step lr sign(phi) then differs
+by 2 lr.
 """
 import numpy as np
 import pytest
 import torch
 
+from helpers import PHI_TOL, update_tolerance
 from oracle import pds_oracle as orc
 from paper_2109_08815_gb300 import api
 
@@ -35,26 +40,34 @@ def _compare(N, M, P, seed, steps=1, spread=1.0, lr=1e-2, fast=False):
     lo, hi, x, g = _case(N, M, P, seed, spread)
     sv = api.Svgd(N, M, P, lo, hi, lr=lr, fast_math=fast)
     X, G = _gpu(x), _gpu(g)
-    ost = orc.SvgdState(N, P, lo, hi, lr=lr)
+    ost = orc.SvgdState(N, P, lo, hi, lr=lr)  # independent run
+    fed = orc.SvgdState(N, P, lo, hi, lr=lr)  # driven by the GPU's phi
     xo = np.ascontiguousarray(x.copy())
+    width = np.concatenate([hi - lo, np.ones(P - M)])
+    near0 = np.zeros((N, P), dtype=bool)
     for _ in range(steps):
+        xk = X.cpu().numpy().T.astype(np.float64)
         bw, phi = sv.step(X, G, return_phi=True)
         phi_ref, bw_ref = ost.step(xo, g)
-    torch.cuda.synchronize()
+        near0[:, :M] |= np.abs(phi_ref) <= PHI_TOL * np.max(np.abs(phi_ref))
+        torch.cuda.synchronize()
+        ph = phi.cpu().numpy().T.astype(np.float64)
+        xf = np.ascontiguousarray(xk)
+        fed.update(xf, ph, g)
+        xg = X.cpu().numpy().T.astype(np.float64)
+        assert np.all(np.abs(xg - xf) <= update_tolerance(xf, width)), \
+            np.max(np.abs(xg - xf) / update_tolerance(xf, width))
     # after several steps the two particle sets differ by the rare sign flips
     # below, which moves the median slightly
     assert abs(bw.item() - bw_ref) <= (1e-5 if steps == 1 else 1e-3) * bw_ref, (bw.item(), bw_ref)
-    phi = phi.cpu().numpy().T
     scale = np.max(np.abs(phi_ref))
-    assert np.max(np.abs(phi - phi_ref)) <= 2e-3 * scale, np.max(np.abs(phi - phi_ref)) / scale
-    xg = X.cpu().numpy().T
-    width = np.concatenate([hi - lo, np.ones(P - M)])
+    if steps == 1:
+        assert np.max(np.abs(ph - phi_ref)) <= PHI_TOL * scale, np.max(np.abs(ph - phi_ref)) / scale
     dx = np.abs(xg - xo) / width
-    # Adam's first steps move each entry by about lr * sign(direction): entries
-    # agree to rounding except where the FP32 and FP64 directions straddle
-    # zero, which must stay rare
-    assert np.mean(dx > 1e-4 * steps) <= 2e-3, np.mean(dx > 1e-4 * steps)
-    assert dx.max() <= 2.5 * lr * steps, dx.max()
+    far = ~near0
+    assert np.all(dx[far] <= 1e-4 * steps), np.max(dx[far])
+    assert np.all(dx <= 2.5 * lr * steps), dx.max()
+    assert np.mean(near0) <= 2e-2
 
 
 @pytest.mark.parametrize("fast", [False, True])
@@ -125,7 +138,7 @@ def test_full_size_bandwidth_and_phi():
     full = orc.svgd_phi(u, gu, bw_ref)
     phi = phi.cpu().numpy().T
     scale = np.max(np.abs(full))
-    assert np.max(np.abs(phi[idx] - full[idx])) <= 2e-3 * scale
+    assert np.max(np.abs(phi[idx] - full[idx])) <= PHI_TOL * scale
 
 
 def test_maximum_size_step():
@@ -153,7 +166,7 @@ def test_maximum_size_step():
     rows[-1] = N - 1
     ref = orc.svgd_phi_rows(u, g[:, :M] * (hi - lo), bw, rows)
     got = phi.cpu().numpy().T[rows]
-    assert np.max(np.abs(got - ref)) <= 2e-3 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= PHI_TOL * np.max(np.abs(ref))
     sv.close()
 
 
@@ -275,6 +288,6 @@ def test_particles_that_are_not_finite_sit_out(N, M, phi_cc, med_cc, full):
     assert abs(bw.item() - bw_ref) <= 1e-5 * bw_ref, (bw.item(), bw_ref)
     phi = phi.cpu().numpy().T
     assert np.all(np.isfinite(phi[live]))
-    assert np.max(np.abs(phi[live] - phi_ref[live])) <= 2e-3 * np.max(np.abs(phi_ref[live]))
+    assert np.max(np.abs(phi[live] - phi_ref[live])) <= PHI_TOL * np.max(np.abs(phi_ref[live]))
     assert np.all(np.isnan(phi[dead]))
     sv.close()
