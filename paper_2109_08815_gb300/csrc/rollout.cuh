@@ -31,11 +31,19 @@
 // textbook one written in link frames; the oracle runs the general spatial
 // algorithm, so the two agree only through the dynamics.
 //
-// The adjoint of one step is the exact reverse-mode derivative of the same
-// arithmetic (Appendix B-A: gradients through f_step by the chain rule /
-// adjoint method), written by hand statement by statement in reverse order.
-// cos / sin of the absolute angles are built by composing the joint
-// rotations; their adjoint is taken with respect to phi_i directly.
+// The adjoint of one step (Appendix B-A: gradients through f_step by the
+// chain rule / adjoint method) differentiates the implicit relation
+// ID(q, qd, qdd) = tau instead of the recursion: one solve with the same
+// rank-1 articulated inertias gives mu = H^-1 abar, and the gradient of
+// mu^T ID for point masses is a closed-form sum over the links (see
+// chain_step_vjp).  The reverse step therefore never re-runs the forward
+// recursion; it needs only the step's input state and output velocity,
+// which the tape holds.
+//
+// Every fused multiply-add is written out as fmaf and the file is compiled
+// with -fmad=false, so the arithmetic is the same in the single-problem and
+// the batched kernels whatever the compiler's context: the two give the
+// same results bit for bit.
 #pragma once
 
 #include "pds_internal.cuh"
@@ -91,14 +99,15 @@ __device__ __forceinline__ void joint_trig(const float (&q)[NL], float (&sq)[NL]
 // Forward step in place.
 template <int NL, bool FAST>
 __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const Links<NL>& P, float dt) {
-  float sq[NL], cq[NL], S[NL], C[NL], w[NL], tau[NL];
+  float sq[NL], cq[NL], S[NL], C[NL], o2[NL], w[NL], tau[NL];
   joint_trig<NL, FAST>(q, sq, cq, S, C);
   {
     float om = 0.f;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
       om += v[i];
-      w[i] = om * om * P.l[i];
+      o2[i] = om * om;
+      w[i] = o2[i] * P.l[i];
       tau[i] = -P.b[i] * v[i];
     }
   }
@@ -106,7 +115,7 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
   float Bce = 0.f, Bcp = 0.f, kc = 0.f;
 #pragma unroll
   for (int i = NL - 1; i >= 0; --i) {
-    const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
+    const float dtau = (i + 1 < NL) ? fmaf(-P.b[i], v[i], -tau[i + 1]) : tau[i];
     float Be = 0.f, Bp = 0.f, h = P.m[i], y = 0.f, z = P.m[i];
     if (i + 1 < NL) {
       const float s1 = sq[i + 1], c1 = cq[i + 1];
@@ -118,9 +127,9 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
       z = fmaf(kc * c1, c1, P.m[i]);
     }
     const float ih = rcp<FAST>(h);
-    const float be = Be - w[i] * z - P.mg[i] * C[i];
-    const float bp = Bp - w[i] * y + P.mg[i] * S[i];
-    const float ft = (dtau * P.il[i] - bp) * ih;
+    const float be = fmaf(-P.mg[i], C[i], fmaf(-w[i], z, Be));
+    const float bp = fmaf(P.mg[i], S[i], fmaf(-w[i], y, Bp));
+    const float ft = fmaf(dtau, P.il[i], -bp) * ih;
     f[i] = ft;
     x[i] = y * ih;
     Bce = fmaf(ft, y, be);
@@ -137,7 +146,7 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
     }
     const float An = fmaf(-x[i], ae, f[i]);
     const float al = (An - ap) * P.il[i];
-    Ae = ae - w[i];
+    Ae = fmaf(-o2[i], P.l[i], ae);
     Ap = An;
     const float qdd = al - alp;
     alp = al;
@@ -146,205 +155,125 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
   }
 }
 
-// Forward intermediates of one step that its reverse needs.
-template <int NL>
-struct StepTape {
-  float sq[NL], cq[NL], S[NL], C[NL], om[NL], tau[NL];
-  float kc[NL], ih[NL], y[NL], f[NL], num[NL], Be[NL], Bp[NL], ae[NL], ap[NL];
-  float v[NL];
-};
-
-// Recompute the forward intermediates of the step at (q, v).
+// Reverse of one step.  On entry (qb, vb) is the adjoint of the step's
+// output state (q', v'); on exit it is the adjoint of its input state
+// (q, v), and the adjoints of the link parameters are accumulated into
+// mb, lb, bb.  v2 = v' is the step's output velocity.
+//
+// Euler (q' = q + v' dt, v' = v + qdd dt) hands the joint accelerations the
+// adjoint abar = (vb + qb dt) dt.  For the dynamics qdd = FD(q, v; m, l, b)
+// the reverse uses the inverse-dynamics identity instead of the derivative
+// of the articulated-body recursion: FD is the solution of
+// ID(q, v, qdd; m, l) + b o v = 0 for the actual qdd, with ID's Jacobian in
+// qdd the mass matrix H (symmetric), so
+//   abar^T dqdd/dx = -d/dx [ mu^T (ID(q, v, qdd) + b o v) ],  mu = H^-1 abar,
+// with mu and qdd held fixed (the adjoint method applied to the implicit
+// relation, Appendix B-A).  mu comes from the same rank-1 articulated
+// recursion as the forward step with no velocity, gravity or damping terms
+// and abar as the joint torques.  For point masses at the link tips,
+//   mu^T ID = sum_k m_k (A_k + g y) . delta_k,
+//   A_k = sum_{j<=k} l_j (alpha_j p_j - omega_j^2 e_j),   (tip acceleration)
+//   delta_k = sum_{j<=k} l_j Lambda_j p_j,                (tip motion under mu)
+// with e_j = (sin phi_j, -cos phi_j), p_j = (cos phi_j, sin phi_j), phi,
+// omega, alpha and Lambda the partial sums of q, v, qdd and mu over the
+// joints up to j.  With the suffix sums F_j = sum_{k>=j} m_k (A_k + g y) and
+// D_j = sum_{k>=j} m_k delta_k its gradient is, link by link,
+//   d/dm_k   = (A_k + g y) . delta_k
+//   d/dl_j   = alpha_j p_j.D_j - omega_j^2 e_j.D_j + Lambda_j p_j.F_j
+//   d/domega_j = -2 omega_j l_j e_j.D_j
+//   d/dphi_j = l_j (-alpha_j e_j.D_j - omega_j^2 p_j.D_j - Lambda_j e_j.F_j)
+// and d/dq_i, d/dv_i are the suffix sums over j >= i of d/dphi_j and
+// d/domega_j (plus mu_i b_i for v_i); the damping term gives d/db_i = mu_i v_i.
+// qdd is recovered from the taped velocities as (v' - v) / dt: its FP32
+// error, half an ulp of v' over dt, stays far below the gradient tolerance.
 template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step_recompute(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P,
-                                                     StepTape<NL>& F) {
-  // ---- recompute the forward intermediates at (q, v)
-  float (&sq)[NL] = F.sq, (&cq)[NL] = F.cq, (&S)[NL] = F.S, (&C)[NL] = F.C, (&om)[NL] = F.om, (&tau)[NL] = F.tau;
+__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const float (&v2)[NL],
+                                               const Links<NL>& P, float g, float dt, float idt, float (&qb)[NL],
+                                               float (&vb)[NL], float (&mb)[NL], float (&lb)[NL], float (&bb)[NL]) {
+  // ---- Euler: vb' += qb dt (qb passes through unchanged); abar = vb' dt
+#pragma unroll
+  for (int i = 0; i < NL; ++i) vb[i] = fmaf(qb[i], dt, vb[i]);
+  float sq[NL], cq[NL], S[NL], C[NL];
   joint_trig<NL, FAST>(q, sq, cq, S, C);
+  // ---- mu = H^-1 abar: inward pass (the articulated inertias k_i) ...
+  float f[NL], x[NL];
   {
-    float o = 0.f;
-#pragma unroll
-    for (int i = 0; i < NL; ++i) {
-      o += v[i];
-      om[i] = o;
-      tau[i] = -P.b[i] * v[i];
-    }
-  }
-  float (&kc)[NL] = F.kc, (&ih)[NL] = F.ih, (&y)[NL] = F.y, (&f)[NL] = F.f, (&num)[NL] = F.num;
-  float (&Be)[NL] = F.Be, (&Bp)[NL] = F.Bp, (&ae)[NL] = F.ae, (&ap)[NL] = F.ap;
-#pragma unroll
-  for (int i = 0; i < NL; ++i) F.v[i] = v[i];
-  {
-    float Bce = 0.f, Bcp = 0.f, k = 0.f;
+    float Bce = 0.f, Bcp = 0.f, kc = 0.f;
 #pragma unroll
     for (int i = NL - 1; i >= 0; --i) {
-      const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
-      const float w = om[i] * om[i] * P.l[i];
-      float h = P.m[i], yi = 0.f, z = P.m[i];
-      Be[i] = 0.f;
-      Bp[i] = 0.f;
+      const float dtau = ((i + 1 < NL) ? vb[i] - vb[i + 1] : vb[i]) * dt;  // abar_i - abar_{i+1}
+      float Be = 0.f, Bp = 0.f, h = P.m[i], y = 0.f;
       if (i + 1 < NL) {
         const float s1 = sq[i + 1], c1 = cq[i + 1];
-        Be[i] = fmaf(Bce, c1, -Bcp * s1);
-        Bp[i] = fmaf(Bce, s1, Bcp * c1);
-        const float ks = k * s1;
+        Be = fmaf(Bce, c1, -Bcp * s1);
+        Bp = fmaf(Bce, s1, Bcp * c1);
+        const float ks = kc * s1;
         h = fmaf(ks, s1, P.m[i]);
-        yi = ks * c1;
-        z = fmaf(k * c1, c1, P.m[i]);
+        y = ks * c1;
       }
-      kc[i] = k;
-      ih[i] = rcp<FAST>(h);
-      y[i] = yi;
-      const float be = Be[i] - w * z - P.mg[i] * C[i];
-      const float bp = Bp[i] - w * yi + P.mg[i] * S[i];
-      num[i] = dtau * P.il[i] - bp;
-      f[i] = num[i] * ih[i];
-      Bce = fmaf(f[i], yi, be);
+      const float ih = rcp<FAST>(h);
+      const float ft = fmaf(dtau, P.il[i], -Bp) * ih;
+      f[i] = ft;
+      x[i] = y * ih;
+      Bce = fmaf(ft, y, Be);
       Bcp = dtau * P.il[i];
-      k = P.m[i] * (P.m[i] + k) * ih[i];
+      kc = P.m[i] * (P.m[i] + kc) * ih;
     }
-    float Ae = 0.f, Ap = 0.f;
+  }
+  // ... outward pass (Lambda = absolute angular accelerations of the
+  // solution), with the prefix sums A_k + g y and delta_k
+  float Lam[NL], om[NL], al[NL], Gx[NL], Gy[NL], dx[NL], dy[NL];
+  {
+    float Ae = 0.f, Ap = 0.f, o = 0.f, a = 0.f, Ax = 0.f, Ay = 0.f, ddx = 0.f, ddy = 0.f;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      ae[i] = 0.f;
-      ap[i] = 0.f;
+      float ae = 0.f, ap = 0.f;
       if (i > 0) {
-        ae[i] = fmaf(cq[i], Ae, sq[i] * Ap);
-        ap[i] = fmaf(cq[i], Ap, -sq[i] * Ae);
+        ae = fmaf(cq[i], Ae, sq[i] * Ap);
+        ap = fmaf(cq[i], Ap, -sq[i] * Ae);
       }
-      Ap = fmaf(-y[i] * ih[i], ae[i], f[i]);
-      Ae = ae[i] - om[i] * om[i] * P.l[i];
+      const float An = fmaf(-x[i], ae, f[i]);
+      Lam[i] = (An - ap) * P.il[i];
+      Ae = ae;
+      Ap = An;
+      o += v[i];
+      a = fmaf(v2[i] - v[i], idt, a);
+      om[i] = o;
+      al[i] = a;
+      const float o2 = o * o;
+      const float ux = fmaf(a, C[i], -o2 * S[i]), uy = fmaf(a, S[i], o2 * C[i]);
+      Ax = fmaf(P.l[i], ux, Ax);
+      Ay = fmaf(P.l[i], uy, Ay);
+      const float ll = P.l[i] * Lam[i];
+      ddx = fmaf(ll, C[i], ddx);
+      ddy = fmaf(ll, S[i], ddy);
+      Gx[i] = Ax;
+      Gy[i] = Ay + g;
+      dx[i] = ddx;
+      dy[i] = ddy;
     }
   }
-}
-
-// Reverse of one step from its intermediates.  On entry (qb, vb) is the
-// adjoint of the step's output state; on exit it is the adjoint of the input
-// state.  The adjoints of the link parameters are accumulated into mb, lb, bb.
-template <int NL>
-__device__ __forceinline__ void chain_step_reverse(const StepTape<NL>& F, const Links<NL>& P, float g, float dt,
-                                                   float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
-                                                   float (&lb)[NL], float (&bb)[NL]) {
-  const float (&sq)[NL] = F.sq, (&cq)[NL] = F.cq, (&S)[NL] = F.S, (&C)[NL] = F.C, (&om)[NL] = F.om, (&tau)[NL] = F.tau;
-  const float (&kc)[NL] = F.kc, (&ih)[NL] = F.ih, (&y)[NL] = F.y, (&f)[NL] = F.f, (&num)[NL] = F.num;
-  const float (&Be)[NL] = F.Be, (&Bp)[NL] = F.Bp, (&ae)[NL] = F.ae, (&ap)[NL] = F.ap;
-  const float (&v)[NL] = F.v;
-  // ---- Euler: qd' = qd + qdd dt, q' = q + qd' dt
-#pragma unroll
-  for (int i = 0; i < NL; ++i) vb[i] = fmaf(qb[i], dt, vb[i]);  // qb passes through unchanged
-  // qdd_i = alpha_i - alpha_{i-1}  =>  alpha_i receives qdd_b[i] - qdd_b[i+1]
-  float alb[NL];
-#pragma unroll
-  for (int i = 0; i < NL; ++i) alb[i] = (vb[i] - ((i + 1 < NL) ? vb[i + 1] : 0.f)) * dt;
-
-  // ---- reverse of the outward pass
-  float fb[NL], xb[NL], wb[NL], ilb[NL];
-  {
-    float Aeb = 0.f, Apb = 0.f;
-#pragma unroll
-    for (int i = NL - 1; i >= 0; --i) {
-      const float x = y[i] * ih[i];
-      // Ae = ae - w
-      float aeb = Aeb;
-      wb[i] = -Aeb;
-      // alpha = (An - ap) / l
-      const float ai = alb[i] * P.il[i];
-      const float Anb = Apb + ai;
-      const float apb = -ai;
-      const float An = fmaf(-x, ae[i], f[i]);
-      ilb[i] = alb[i] * (An - ap[i]);
-      // An = f - x ae
-      fb[i] = Anb;
-      xb[i] = -Anb * ae[i];
-      aeb = fmaf(-Anb, x, aeb);
-      if (i > 0) {
-        // (ae, ap) = a_{i-1} turned by -q_i
-        qb[i] += aeb * ap[i] - apb * ae[i];
-        Aeb = fmaf(cq[i], aeb, -sq[i] * apb);
-        Apb = fmaf(sq[i], aeb, cq[i] * apb);
-      }
-    }
-  }
-
-  // ---- reverse of the inward pass (parent to child)
-  float taub[NL], phib[NL], omb[NL];
-#pragma unroll
-  for (int i = 0; i < NL; ++i) taub[i] = 0.f;
-  {
-    float Beob = 0.f, Bpob = 0.f, kob = 0.f;  // adjoints of link i's outputs B_i, k_i
-#pragma unroll
-    for (int i = 0; i < NL; ++i) {
-      const float m = P.m[i];
-      const float dtau = (i + 1 < NL) ? tau[i] - tau[i + 1] : tau[i];
-      const float w = om[i] * om[i] * P.l[i];
-      // k_i = m (m + k_{i+1}) / h
-      float mbi = kob * (2.f * m + kc[i]) * ih[i];
-      float kcb = kob * m * ih[i];
-      float ihb = kob * m * (m + kc[i]);
-      // B_i = (be + f y, dtau / l)
-      const float beb = Beob;
-      const float ftb = fmaf(Beob, y[i], fb[i]);
-      float yb = Beob * f[i];
-      // f = (dtau / l - bp) / h
-      const float gg = ftb * ih[i];
-      const float dtaub = (Bpob + gg) * P.il[i];
-      const float ilbi = fmaf(Bpob + gg, dtau, ilb[i]);
-      const float bpb = -gg;
-      ihb = fmaf(ftb, num[i], ihb);
-      // bp = Bp - w y + m g S ; be = Be - w z - m g C
-      float z = m;
-      if (i + 1 < NL) z = fmaf(kc[i] * cq[i + 1], cq[i + 1], m);
-      const float wbi = wb[i] - bpb * y[i] - beb * z;
-      yb = fmaf(-bpb, w, yb);
-      const float mgb = bpb * S[i] - beb * C[i];
-      const float Sb = bpb * P.mg[i], Cb = -beb * P.mg[i];
-      const float zb = -beb * w;
-      mbi += zb;
-      // x = y / h
-      yb = fmaf(xb[i], ih[i], yb);
-      ihb = fmaf(xb[i], y[i], ihb);
-      const float hb = -ihb * ih[i] * ih[i];
-      mbi += hb;
-      taub[i] += dtaub;
-      if (i + 1 < NL) {
-        const float s1 = sq[i + 1], c1 = cq[i + 1], k = kc[i];
-        // z = m + k c^2, y = k s c, h = m + k s^2
-        kcb += zb * c1 * c1 + yb * s1 * c1 + hb * s1 * s1;
-        const float c1b = 2.f * zb * k * c1 + yb * k * s1;
-        const float s1b = yb * k * c1 + 2.f * hb * k * s1;
-        // (Be, Bp) = B_{i+1} turned by q_{i+1}
-        qb[i + 1] += s1b * c1 - c1b * s1 - beb * Bp[i] + bpb * Be[i];
-        Beob = fmaf(beb, c1, bpb * s1);
-        Bpob = fmaf(bpb, c1, -beb * s1);
-        kob = kcb;
-        taub[i + 1] -= dtaub;
-      }
-      mb[i] += fmaf(mgb, g, mbi);
-      omb[i] = wbi * 2.f * om[i] * P.l[i];
-      lb[i] += wbi * om[i] * om[i] - ilbi * P.il[i] * P.il[i];
-      phib[i] = Sb * C[i] - Cb * S[i];
-    }
-  }
-  // tau_i = -b_i v_i ; phi_i = sum_{j<=i} q_j ; omega_i = sum_{j<=i} v_j
-  float sphi = 0.f, som = 0.f;
+  // ---- the gradient of -mu^T (ID + b o v), suffix sums from the tip
+  float Fx = 0.f, Fy = 0.f, Dx = 0.f, Dy = 0.f, sphi = 0.f, som = 0.f;
 #pragma unroll
   for (int i = NL - 1; i >= 0; --i) {
-    sphi += phib[i];
-    som += omb[i];
-    bb[i] = fmaf(-taub[i], v[i], bb[i]);
-    qb[i] += sphi;
-    vb[i] += fmaf(-taub[i], P.b[i], som);
+    const float m = P.m[i];
+    Fx = fmaf(m, Gx[i], Fx);
+    Fy = fmaf(m, Gy[i], Fy);
+    Dx = fmaf(m, dx[i], Dx);
+    Dy = fmaf(m, dy[i], Dy);
+    const float eD = fmaf(S[i], Dx, -C[i] * Dy), pD = fmaf(C[i], Dx, S[i] * Dy);
+    const float eF = fmaf(S[i], Fx, -C[i] * Fy), pF = fmaf(C[i], Fx, S[i] * Fy);
+    const float o2 = om[i] * om[i];
+    const float mu = (i > 0) ? Lam[i] - Lam[i - 1] : Lam[0];
+    mb[i] -= fmaf(Gx[i], dx[i], Gy[i] * dy[i]);
+    lb[i] -= fmaf(al[i], pD, fmaf(-o2, eD, Lam[i] * pF));
+    bb[i] = fmaf(-mu, v[i], bb[i]);
+    som = fmaf(-2.f * om[i] * P.l[i], eD, som);
+    sphi = fmaf(P.l[i], fmaf(-al[i], eD, fmaf(-o2, pD, -Lam[i] * eF)), sphi);
+    qb[i] -= sphi;
+    vb[i] -= fmaf(mu, P.b[i], som);
   }
-}
-
-// Reverse of one step (recompute, then reverse).
-template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const Links<NL>& P, float g,
-                                               float dt, float (&qb)[NL], float (&vb)[NL], float (&mb)[NL],
-                                               float (&lb)[NL], float (&bb)[NL]) {
-  StepTape<NL> F;
-  chain_step_recompute<NL, FAST>(q, v, P, F);
-  chain_step_reverse<NL>(F, P, g, dt, qb, vb, mb, lb, bb);
 }
 
 // Load the physical parameters of particle i (defaults overridden by theta).
@@ -380,12 +309,12 @@ __device__ __forceinline__ float obs_residual(const ChainParams& c, const float*
     auto term = [&](int comp, float o) {  // comp: 0..NL-1 angles, NL..2NL-1 velocities
       if (comp < NL) {
         const float r = o - q[comp];
-        acc += r * r;
-        if (seed) qb[comp] += r * c.inv_so2;
+        acc = fmaf(r, r, acc);
+        if (seed) qb[comp] = fmaf(r, c.inv_so2, qb[comp]);
       } else {
         const float r = o - v[comp - NL];
-        acc += r * r;
-        if (seed) vb[comp - NL] += r * c.inv_so2;
+        acc = fmaf(r, r, acc);
+        if (seed) vb[comp - NL] = fmaf(r, c.inv_so2, vb[comp - NL]);
       }
     };
 #pragma unroll
@@ -400,17 +329,34 @@ __device__ __forceinline__ float obs_residual(const ChainParams& c, const float*
     for (int j = 0; j < NL; ++j) {
       if (c.obs_col[j] >= 0) {
         const float r = __ldg(row + c.obs_col[j]) - q[j];
-        acc += r * r;
-        if (seed) qb[j] += r * c.inv_so2;
+        acc = fmaf(r, r, acc);
+        if (seed) qb[j] = fmaf(r, c.inv_so2, qb[j]);
       }
       if (c.obs_col[NL + j] >= 0) {
         const float r = __ldg(row + c.obs_col[NL + j]) - v[j];
-        acc += r * r;
-        if (seed) vb[j] += r * c.inv_so2;
+        acc = fmaf(r, r, acc);
+        if (seed) vb[j] = fmaf(r, c.inv_so2, vb[j]);
       }
     }
   }
   return acc;
+}
+
+// The observation seed of one reverse step from a row already loaded (state
+// order, pairs): qb, vb += (x_t - s_t) / sigma_obs^2.
+template <int NL>
+__device__ __forceinline__ void obs_seed_pairs(const ChainParams& c, const float2 (&o)[NL], const float (&q)[NL],
+                                               const float (&v)[NL], float (&qb)[NL], float (&vb)[NL]) {
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const int comp = 2 * j + e;
+      const float ov = e ? o[j].y : o[j].x;
+      if (comp < NL) qb[comp] = fmaf(ov - q[comp], c.inv_so2, qb[comp]);
+      else vb[comp - NL] = fmaf(ov - v[comp - NL], c.inv_so2, vb[comp - NL]);
+    }
+  }
 }
 
 // Asynchronous 4-byte copy global -> shared (cp.async), its group commit,
@@ -426,7 +372,21 @@ __device__ __forceinline__ void cp_async8(float2* dst_smem, const float2* src_gl
                : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
+template <int A>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(A) : "memory"); }
+
+// The K = 1 reverse sweep prefetches each taped state kRingAhead steps
+// before its use into a ring of kRingAhead + 1 shared-memory slots per
+// thread.
+#ifndef PDS_RING_AHEAD
+#define PDS_RING_AHEAD 2
+#endif
+constexpr int kRingAhead = PDS_RING_AHEAD;
+constexpr int kRingSlots = kRingAhead + 1;
+// Unroll factor of the single-problem kernel's K = 1 reverse loop.
+#ifndef PDS_ROLLOUT_RU
+#define PDS_ROLLOUT_RU 2
+#endif
 
 template <int NL>
 __device__ __forceinline__ void tape_store(float* __restrict__ tape, size_t slot, size_t U, size_t u,
@@ -553,7 +513,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     chain_step<NL, FAST>(q, v, P, c.dt);
     rss += obs_residual<NL, EVERY>(c, obs, t0 + k + 1, q, v, qb, vb, false);
   }
-  float lp = -0.5f * c.inv_so2 * rss + (float)h * c.obs_const;
+  float lp = fmaf(-0.5f * c.inv_so2, rss, (float)h * c.obs_const);
 
   // defect term against the next window's shooting state
   float nb[2 * NL];
@@ -568,12 +528,13 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     for (int j = 0; j < NL; ++j) {
       dd[j] = __ldg(xs + (size_t)j * N) - q[j];
       dd[NL + j] = __ldg(xs + (size_t)(NL + j) * N) - v[j];
-      dss += dd[j] * dd[j] + dd[NL + j] * dd[NL + j];
+      dss = fmaf(dd[j], dd[j], dss);
+      dss = fmaf(dd[NL + j], dd[NL + j], dss);
     }
     if constexpr (CS) {
       const float g = dss * c.inv_sd2;
       const float lam = __ldg(X + (size_t)(c.M + (c.W - 1) * 2 * NL + w) * N + i);
-      const float kap2 = 2.f * (lam + c.c_mdmm * g) * c.inv_sd2;
+      const float kap2 = 2.f * fmaf(c.c_mdmm, g, lam) * c.inv_sd2;
 #pragma unroll
       for (int j = 0; j < NL; ++j) {
         qb2[j] = kap2 * dd[j];  // -dPsi/ds_end
@@ -590,7 +551,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
         nb[j] = -dd[j] * c.inv_sd2;  // d/ds^s_{w+1}
         nb[NL + j] = -dd[NL + j] * c.inv_sd2;
       }
-      lp += -0.5f * c.inv_sd2 * dss + c.def_const;
+      lp += fmaf(-0.5f * c.inv_sd2, dss, c.def_const);
     }
   } else {
 #pragma unroll
@@ -603,6 +564,7 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   if (!grad) return;
 
   // ---------------- reverse sweep
+  const float idt = 1.0f / c.dt;
   float mb[NL], lb[NL], bb[NL];
   float mb2[NL], lb2[NL], bb2[NL];  // CS: theta adjoint of -Psi_def
 #pragma unroll
@@ -612,13 +574,14 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   for (int j = 0; j < NL; ++j) { qh[j] = q[j]; vh[j] = v[j]; }
   if (K == 1 && seg) {
     // Every pre-step state is on the tape: no recomputation.  Each state is
-    // copied into a ring of three shared-memory slots two steps ahead
-    // (cp.async, no registers held), so its load's latency hides behind two
-    // steps' adjoints.  The ring is pair-major, [3][NL][block] float2, in
-    // the same shared memory (seg is this thread's float of a [..][block]
-    // layout, seg_stride the block size).
+    // copied into a ring of kRingSlots shared-memory slots kRingAhead steps
+    // ahead (cp.async, no registers held), so its load's latency hides
+    // behind that many steps' adjoints.  The ring is pair-major,
+    // [kRingSlots][NL][block] float2, in the same shared memory (seg is this
+    // thread's float of a [..][block] layout, seg_stride the block size).
+    constexpr int RS = kRingSlots;
     float2* ring = reinterpret_cast<float2*>(seg - threadIdx.x) + threadIdx.x;
-    auto fetch = [&](int k, int rs) {  // state k into ring slot rs = k mod 3
+    auto fetch = [&](int k, int rs) {  // state k into ring slot rs = k mod RS
       if (k >= 0) {
         const float2* src = reinterpret_cast<const float2*>(ckpt) + ((size_t)k * U + u) * NL;
         float2* dst = ring + (size_t)rs * NL * sstride;
@@ -627,25 +590,44 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       }
       cp_async_commit();
     };
-    int rs = (h - 1) % 3;  // ring slot of state k, counted down with k
-    fetch(h - 1, rs);
-    fetch(h - 2, rs == 0 ? 2 : rs - 1);
+    // Every component observed: the observation row of the next step to
+    // reverse is loaded one step ahead, into registers
+    [[maybe_unused]] float2 onx[NL];
+    const float2* orow = reinterpret_cast<const float2*>(obs) + (size_t)t0 * NL;  // row t0 + k + 1 at orow + k NL
+    if constexpr (EVERY) {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) onx[j] = __ldg(orow + (size_t)(h - 1) * NL + j);
+    }
+    int rs = (h - 1) % RS;  // ring slot of state k, counted down with k
+    {
+      int r = rs;
+#pragma unroll
+      for (int a = 1; a <= kRingAhead; ++a) {
+        fetch(h - a, r);
+        r = r == 0 ? RS - 1 : r - 1;
+      }
+    }
 #pragma unroll RU
     for (int k = h - 1; k >= 0; --k) {
-      fetch(k - 2, rs == 2 ? 0 : rs + 1);  // (k - 2) mod 3 = (k + 1) mod 3
-      cp_async_wait2();  // the group of state k (two groups older than the newest)
+      fetch(k - kRingAhead, rs == RS - 1 ? 0 : rs + 1);  // (k - kRingAhead) mod RS = (k + 1) mod RS
+      cp_async_wait<kRingAhead>();  // the group of state k (kRingAhead groups older than the newest)
       float qs[NL], vs[NL];
       pairs_load<NL>(ring + (size_t)rs * NL * sstride, sstride, qs, vs);
-      rs = rs == 0 ? 2 : rs - 1;
-      obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
-      if constexpr (CS) {
-        StepTape<NL> F;
-        chain_step_recompute<NL, FAST>(qs, vs, P, F);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
+      rs = rs == 0 ? RS - 1 : rs - 1;
+      if constexpr (EVERY) {
+        float2 ocur[NL];
+#pragma unroll
+        for (int j = 0; j < NL; ++j) ocur[j] = onx[j];
+        if (k > 0) {
+#pragma unroll
+          for (int j = 0; j < NL; ++j) onx[j] = __ldg(orow + (size_t)(k - 1) * NL + j);
+        }
+        obs_seed_pairs<NL>(c, ocur, qh, vh, qb, vb);
       } else {
-        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
+        obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       }
+      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -658,14 +640,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     for (int k = h - 1; k >= 0; --k) {
       if (k > 0) ckpt_load<NL>(ckpt, k - 1, U, u, qn, vn);
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
-      if constexpr (CS) {
-        StepTape<NL> F;
-        chain_step_recompute<NL, FAST>(qs, vs, P, F);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
-      } else {
-        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
-      }
+      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; qs[j] = qn[j]; vs[j] = vn[j]; }
     }
@@ -685,14 +661,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
-      if constexpr (CS) {
-        StepTape<NL> F;
-        chain_step_recompute<NL, FAST>(qs, vs, P, F);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb, vb, mb, lb, bb);
-        chain_step_reverse<NL>(F, P, c.g, c.dt, qb2, vb2, mb2, lb2, bb2);
-      } else {
-        chain_step_vjp<NL, FAST>(qs, vs, P, c.g, c.dt, qb, vb, mb, lb, bb);
-      }
+      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -740,9 +710,10 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, false, EVERY, 2>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x,
+                                                          blockDim.x);
   else
-    rollout_unit<NL, FAST, false, EVERY, 2>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u);
 }
 
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
@@ -773,7 +744,7 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_ker
                                                                               int n_items,
                                                                               unsigned int* __restrict__ counter,
                                                                               int grad, int ring) {
-  // ring: dynamic shared memory holds the K = 1 prefetch ring (three states per thread)
+  // ring: dynamic shared memory holds the K = 1 prefetch ring (kRingSlots states per thread)
   extern __shared__ float ring_sh[];
   __shared__ ChainParams cs;
   __shared__ int item;
@@ -819,7 +790,7 @@ int batch_rollout_blocks_per_sm_nl(int fast) {
 template <int NL>
 cudaError_t launch_batch_rollout_nl(const BatchJob* jobs, const WorkItem* items, int n_items, unsigned int* counter,
                                     int grad, int fast, int blocks, int ring, cudaStream_t st) {
-  const size_t smem = ring ? (size_t)3 * 2 * NL * 128 * sizeof(float) : 0;
+  const size_t smem = ring ? (size_t)kRingSlots * 2 * NL * 128 * sizeof(float) : 0;
   if (fast)
     batch_rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(jobs, items, n_items, counter, grad, ring);
   else
@@ -852,10 +823,10 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
                               int32_t* status, cudaStream_t st) {
   const size_t U = (size_t)N * c.W * c.R;
   const unsigned blocks = (unsigned)((U + 127) / 128);
-  // the reverse sweep's K recomputed states (K = 1: a ring of three
+  // the reverse sweep's K recomputed states (K = 1: the ring of kRingSlots
   // prefetched states) in shared memory when they fit in the default 48 KB of
   // a block
-  const size_t seg_bytes = (size_t)(c.K == 1 ? 3 : c.K) * 2 * NL * 128 * sizeof(float);
+  const size_t seg_bytes = (size_t)(c.K == 1 ? kRingSlots : c.K) * 2 * NL * 128 * sizeof(float);
   const int seg_smem = (grad && seg_bytes <= 48 * 1024) ? 1 : 0;
   const size_t smem = seg_smem ? seg_bytes : 0;
   constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
