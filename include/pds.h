@@ -298,6 +298,17 @@ int pds_svgd_destroy(pds_svgd_t s);
  * default is far above any wait a healthy pass makes (a few microseconds);
  * small values exist to exercise that path. */
 #define PDS_OPT_WAIT_LIMIT 6
+/* PDS_OPT_GRAPH 1 (default): a step's kernels (about 25) are captured into a
+ * CUDA graph on the second pds_svgd_step call with the same particles, grad,
+ * bandwidth_out and phi_out pointers and the same options, and every later
+ * call with them replays the graph, which saves the gaps between the
+ * launches.  Calls with other pointers or options launch directly and
+ * re-capture on their second use.  The state's stream must not be the
+ * legacy or per-thread default stream, and if the caller is capturing that
+ * stream already the kernels go into the caller's graph instead.  The first
+ * call with new pointers also does the kernels' one-time set-up.  0: launch
+ * every kernel every time. */
+#define PDS_OPT_GRAPH 7
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);
 
 /* Constrained SVGD update (Algorithm 1) for particles laid out as

@@ -497,11 +497,24 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   return pds_svgd_reset(s);
 }
 
+// Forget the captured SVGD step (its graph and the calls counted towards a capture).
+static void drop_graph(pds_svgd* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->gkey_calls = 0;
+}
+
 int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
   if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
   if (option == PDS_OPT_WAIT_LIMIT) {
     if (value < 0) return fail(PDS_ERR_ARG, "wait limit %d < 0", value);
     s->w.wait_limit = value;
+    return PDS_OK;
+  }
+  if (option == PDS_OPT_GRAPH) {
+    if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "option value must be 0 or 1");
+    if (!value) drop_graph(s);
+    s->use_graph = value;
     return PDS_OK;
   }
   if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "option value must be 0 or 1");
@@ -541,6 +554,7 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaFree(s->w.adam_v);
   cudaFree(s->w.ctl);
   if (s->h_status) cudaFreeHost(s->h_status);
+  drop_graph(s);
   delete s;
   return PDS_OK;
 }
@@ -566,19 +580,91 @@ int pds_svgd_status(pds_svgd_t s) {
   return take_status(s);
 }
 
+// The ~25 kernels of one step, launched one by one.
+static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out, int* n) {
+  SvgdWork w = s->w;
+  if (s->full_passes) w.cand_cap = 0;
+  if (s->phi_cuda_cores) w.tc = nullptr;
+  if (s->median_cuda_cores) w.mimg = nullptr;
+  return launch_svgd_step(s->sp, w, X, G, bw_out, phi_out, s->stream, n);
+}
+
+// A stream whose work can be captured by this library: not the legacy or
+// per-thread default stream, and not already being captured by the caller
+// (whose own graph then takes the kernels).
+static bool capturable(cudaStream_t st) {
+  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return false;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+  return cs == cudaStreamCaptureStatusNone;
+}
+
 int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* bandwidth_out, float* phi_out) {
   g_launches = 0;
   if (!s || !particles || !grad) return fail(PDS_ERR_ARG, "NULL argument");
   const int st = take_status(s);  // reported by a step already run: this one is not queued
   if (st != PDS_OK) return st;
   int n = 0;
-  SvgdWork w = s->w;
-  if (s->full_passes) w.cand_cap = 0;
-  if (s->phi_cuda_cores) w.tc = nullptr;
-  if (s->median_cuda_cores) w.mimg = nullptr;
-  cudaError_t e = launch_svgd_step(s->sp, w, particles, grad, bandwidth_out, phi_out, s->stream, &n);
+  cudaError_t e = cudaSuccess;
+  if (!s->use_graph || !capturable(s->stream)) {
+    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
+    g_launches = n;
+    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
+    return PDS_OK;
+  }
+  SvgdGraphKey k;
+  memset(&k, 0, sizeof(k));
+  k.X = particles;
+  k.G = grad;
+  k.bw_out = bandwidth_out;
+  k.phi_out = phi_out;
+  k.full_passes = s->full_passes;
+  k.phi_cuda_cores = s->phi_cuda_cores;
+  k.median_cuda_cores = s->median_cuda_cores;
+  k.wait_limit = s->w.wait_limit;
+  k.sp = s->sp;
+  if (memcmp(&k, &s->gkey, sizeof(k)) != 0) {
+    drop_graph(s);
+    s->gkey = k;
+  }
+  if (s->gexec) {
+    e = cudaGraphLaunch(s->gexec, s->stream);
+    g_launches = s->glaunches;
+    if (e != cudaSuccess) return cuda_fail(e, "svgd graph launch");
+    return PDS_OK;
+  }
+  if (s->gkey_calls++ == 0) {
+    // first call with these buffers: launch directly (it also does each
+    // kernel's one-time set-up, which is not captured)
+    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
+    g_launches = n;
+    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
+    return PDS_OK;
+  }
+  // second call: capture the step once, then replay it
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    const cudaError_t el = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
+    e = cudaStreamEndCapture(s->stream, &g);
+    if (e == cudaSuccess) e = el;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    // capture refused: keep launching directly for this key
+    cudaGetLastError();
+    s->gexec = nullptr;
+    s->use_graph = 0;
+    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
+    g_launches = n;
+    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
+    return PDS_OK;
+  }
+  s->glaunches = n;
+  e = cudaGraphLaunch(s->gexec, s->stream);
   g_launches = n;
-  if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
+  if (e != cudaSuccess) return cuda_fail(e, "svgd graph launch");
   return PDS_OK;
 }
 

@@ -210,10 +210,27 @@ struct pds_problem {
   float* d_x = nullptr;
 };
 
+// What a captured SVGD step depends on besides the state's own buffers.
+struct SvgdGraphKey {
+  float* X;
+  const float* G;
+  float* bw_out;
+  float* phi_out;
+  int full_passes, phi_cuda_cores, median_cuda_cores, wait_limit;
+  pds::SvgdParams sp;
+};
+
 struct pds_svgd {
   pds::SvgdParams sp;
   pds::SvgdWork w{};
   int* h_status = nullptr;  // mapped host word behind w.status_flags
+  // the step replayed from a CUDA graph (PDS_OPT_GRAPH): captured on the
+  // second call with the same key, replayed while the key stays the same
+  int use_graph = 1;
+  SvgdGraphKey gkey{};
+  int gkey_calls = 0;            // calls made with gkey
+  cudaGraphExec_t gexec = nullptr;
+  int glaunches = 0;             // kernels inside the graph
   cudaStream_t stream;
   int full_passes = 0;
   int phi_cuda_cores = 0;
