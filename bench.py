@@ -3,8 +3,8 @@
 
 Workload: the 5-link damped planar chain (theta = 5 masses + 5 damping
 coefficients), T = 1000 steps at dt = 0.005, W = 20 shooting windows,
-N = 16384 particles, adjoint checkpoint stride K = 10 -- the largest particle
-count of the chain workload.  A step is log p + gradient of every particle
+N = 16384 particles, adjoint checkpoint stride K = 1 (every pre-step state on
+the tape) -- the largest particle count of the chain workload.  A step is log p + gradient of every particle
 (rollout + adjoint + window reduction) followed by the SVGD + Adam update
 (median bandwidth, phi, Adam).  Metric: particle-step-gradients per second =
 N * T / step time (one unit = one particle x one time step, forward and
@@ -46,14 +46,14 @@ FP32_LANES_PER_SM = 128
 
 def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
     """Algorithmic FP32 flops of one time step (FMA = 2; sincos and
-    reciprocals run on the MUFU and are not counted): forward step with its
-    observation term, and the reverse (adjoint) step, counted from the
-    arithmetic of the rank-1 link-frame articulated-body recursion and its
-    hand-written reverse.  No recomputation of any kind is counted: the
-    checkpoint segment recompute and the re-forward inside the reverse step
-    are implementation costs."""
+    reciprocals run on the MUFU and are not counted): the forward step with
+    its observation term (the rank-1 link-frame articulated-body recursion
+    and semi-implicit Euler), and the reverse step (Euler's adjoint, one
+    solve mu = H^-1 abar with the same rank-1 recursion, the closed-form
+    gradient of mu^T ID, and the observation seed).  The checkpoint segment
+    recompute of K > 1 is an implementation cost and is not counted."""
     fwd = 58 * n + 3 * D - 25
-    rev = 130 * n + 3 * D - 51
+    rev = 109 * n + 3 * D - 44
     return fwd, rev
 
 
@@ -136,18 +136,89 @@ def make_problem_inputs(N: int):
     return wl
 
 
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
 def oracle_rate(wl, obs, x, sample: int, threads: int):
-    """FP64 oracle: log p + gradient of `sample` particles (full T)."""
+    """FP64 oracle: log p + gradient of `sample` particles (full T), on the
+    FP32 values of every input (those the GPU sees).  Returns the rate, the
+    seconds taken, and the oracle's log p and gradient."""
     from oracle import pds_oracle as orc
+    op = orc.Problem(mass=_f32(wl.mass), length=_f32(wl.length), damping=_f32(wl.damping),
+                     theta_kind=wl.theta_kind, theta_link=wl.theta_link, dt=float(np.float32(wl.dt)), T=wl.T,
+                     W=wl.W, obs=obs.astype(np.float64), obs_index=wl.obs_index, sigma_obs=wl.sigma_obs,
+                     sigma_def=wl.sigma_def, s0=_f32(wl.s0), lo=_f32(wl.lo), hi=_f32(wl.hi),
+                     g=float(np.float32(wl.g)), c_lim=wl.c_lim)
+    xs = np.ascontiguousarray(_f32(x[:sample]))
+    t0 = time.perf_counter()
+    lp, g = op.loglik_grad(xs, threads=threads)
+    dt = time.perf_counter() - t0
+    return sample * wl.T / dt, dt, lp, g
+
+
+def grad_error_in_tolerances(g, g_ref, M):
+    """Largest |g - g_ref| over the per-component tolerance the parity tests
+    use, 1e-3 |g_ref| + 1e-5 x the largest |g_ref| of the component's block
+    (theta rows; shooting-state rows), per particle."""
+    worst = 0.0
+    for blk in (slice(0, M), slice(M, g.shape[1])):
+        r = np.abs(g_ref[:, blk])
+        tol = 1e-3 * r + 1e-5 * np.max(r, axis=1, keepdims=True)
+        worst = max(worst, float(np.max(np.abs(g[:, blk] - g_ref[:, blk]) / np.maximum(tol, 1e-300))))
+    return worst
+
+
+def c0_posterior(api, dev, threads: int, iters: int = 100):
+    """The double-pendulum configuration (N = 100, 100 iterations): the GPU's
+    pds_iterate against the FP64 oracle's loop from the same particles.
+    Returns the oracle's rate and the errors of the GPU's final theta
+    moments."""
+    import torch
+    from oracle import metrics_oracle as mo
+    from oracle import pds_oracle as orc
+    wl = wlmod.double_pendulum(N=100)
+    for name in ("mass", "length", "damping", "lo", "hi", "s0", "theta_true", "theta_init"):
+        setattr(wl, name, _f32(getattr(wl, name)))
+    wl.dt, wl.g = float(np.float32(wl.dt)), float(np.float32(wl.g))
+    st = orc.simulate(wl.mass, wl.length, wl.damping, wl.s0, wl.dt, wl.T, g=wl.g)
+    obs = wlmod.observations(wl, st).astype(np.float32)
+    x = _f32(wlmod.initial_particles(wl, obs.astype(np.float64), rng_seed=7))
+    prob = api.Problem.from_workload(wl, obs)
+    sv = api.Svgd(wl.N, wl.M, wl.P, wl.lo, wl.hi, lr=wl.lr)
+    X = torch.from_numpy(np.ascontiguousarray(x.T, dtype=np.float32)).to(dev)
+    api.iterate(prob, sv, X, iters)
+    torch.cuda.synchronize()
+    xg = X.cpu().numpy().T.astype(np.float64)
+    sv.close()
+    prob.close()
     op = orc.Problem(mass=wl.mass, length=wl.length, damping=wl.damping, theta_kind=wl.theta_kind,
                      theta_link=wl.theta_link, dt=wl.dt, T=wl.T, W=wl.W, obs=obs.astype(np.float64),
                      obs_index=wl.obs_index, sigma_obs=wl.sigma_obs, sigma_def=wl.sigma_def, s0=wl.s0, lo=wl.lo,
                      hi=wl.hi, g=wl.g, c_lim=wl.c_lim)
-    xs = np.ascontiguousarray(x[:sample].astype(np.float64))
+    ost = orc.SvgdState(wl.N, wl.P, wl.lo, wl.hi, lr=wl.lr)
+    xo = np.ascontiguousarray(x.copy())
     t0 = time.perf_counter()
-    op.loglik_grad(xs, threads=threads)
-    dt = time.perf_counter() - t0
-    return sample * wl.T / dt, dt
+    for _ in range(iters):
+        _, g = op.loglik_grad(xo, threads=threads)
+        ost.step(xo, g)
+    secs = time.perf_counter() - t0
+    tg, to = xg[:, :wl.M], xo[:, :wl.M]
+    mu_g, mu_o = tg.mean(0), to.mean(0)
+    cg, co = np.cov(tg.T), np.cov(to.T)
+    sd = np.sqrt(np.diag(co))
+    ug, uo = (tg - wl.lo) / (wl.hi - wl.lo), (to - wl.lo) / (wl.hi - wl.lo)
+    err = {"workload": "double pendulum, N=100, T=200, W=10, 100 SVGD iterations from the same particles",
+           "mean_rel_err_max": float(np.max(np.abs(mu_g - mu_o) / np.abs(mu_o))),
+           "cov_err_max_over_sd_sd": float(np.max(np.abs(cg - co) / np.outer(sd, sd))),
+           "mmd2_unit_box": mo.mmd2_unbiased(ug, uo, orc.median_sqdist(uo)),
+           "particle_max_abs_diff_over_box": float(np.max(np.abs(tg - to) / (wl.hi - wl.lo))),
+           "tolerance": "means relative 5e-2; covariances 5e-2 sd_k sd_l"}
+    rate = {"value": wl.N * wl.T * iters / secs, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "svgd_iters_per_s": iters / secs,
+            "sample": f"the whole double-pendulum configuration: {wl.N} particles x T={wl.T}, {iters} SVGD "
+                      f"iterations (log p + gradient + SVGD step), {secs:.1f} s on {threads} threads"}
+    return rate, err
 
 
 def run_reference(args):
@@ -273,6 +344,10 @@ def run_pds(args):
     stream.synchronize()
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
+    # particles whose log p was not finite in the last timed step (they sit
+    # out the SVGD step), and particles with a non-finite entry after it
+    nonfinite = {"logp_last_step": int((~torch.isfinite(logp)).sum().item()),
+                 "particles_after": int((~torch.isfinite(X)).any(dim=0).sum().item())}
     torch.cuda.synchronize()
     step_ms = [evs[k][0].elapsed_time(evs[k][2]) for k in range(args.steps)]
     lg_ms = [evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)]
@@ -320,18 +395,35 @@ def run_pds(args):
         roofline["frac_at_measured_clock"] = achieved / (sm_count * FP32_LANES_PER_SM * 2 * clocks["sm_mhz"] * 1e6 / 1e12)
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import pds_oracle as orc
         orc.build()
         threads = os.cpu_count() or 1
-        rate, secs = oracle_rate(wl, obs, x0, args.ref_sample_baseline, threads)
+        sample = args.ref_sample_baseline
+        rate, secs, lp_ref, g_ref = oracle_rate(wl, obs, x0, sample, threads)
         # the same oracle on one thread, on a smaller sample
-        rate1, secs1 = oracle_rate(wl, obs, x0, 64, 1)
+        rate1, secs1, _, _ = oracle_rate(wl, obs, x0, 64, 1)
+        c0_rate, c0_err = c0_posterior(api, dev, threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"{args.ref_sample_baseline} particles x T={wl.T} log p + gradient (FP64, forward-mode "
+               "sample": f"{sample} particles x T={wl.T} log p + gradient (FP64, forward-mode "
                          f"duals), {secs:.1f} s on {threads} threads",
                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
-                                 "sample": f"64 particles x T={wl.T}, {secs1:.1f} s on 1 thread"}}
+                                 "sample": f"64 particles x T={wl.T}, {secs1:.1f} s on 1 thread"},
+               "double_pendulum": c0_rate}
+        # the GPU's log p and gradient of the same particles, outside the timed region
+        Xs = torch.from_numpy(np.ascontiguousarray(_f32(x0[:sample]).T, dtype=np.float32)).to(dev)
+        with torch.cuda.stream(stream):
+            lp_s, g_s, _ = prob.loglik_grad(Xs)
+        stream.synchronize()
+        lp_s = lp_s.cpu().numpy().astype(np.float64)
+        g_s = g_s.cpu().numpy().T.astype(np.float64)
+        errors = {"loglik_grad": {"workload": f"the benchmark workload's first {sample} initial particles",
+                                  "logp_rel_err_max": float(np.max(np.abs(lp_s - lp_ref) / np.abs(lp_ref))),
+                                  "logp_tolerance": 1e-4,
+                                  "grad_err_max_in_tolerances": grad_error_in_tolerances(g_s, g_ref, wl.M),
+                                  "grad_tolerance": "1e-3 |g_ref| + 1e-5 max |g_ref| of the block, per component"},
+                  "posterior_double_pendulum": c0_err}
 
     extra = {}
     if rank == 0 and world == 1 and not args.no_batched:
@@ -358,6 +450,7 @@ def run_pds(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": _config(wl, N),
             "svgd_iters_per_sec": 1e3 / ms_per_step, "gpu_launches": launches, "e2e": e2e,
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clocks, "wall_s_timed": t_wall,
+            "error_vs_oracle": errors, "nonfinite_particles": nonfinite,
         }
         line.update(extra)
         print(json.dumps(line))
@@ -720,7 +813,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
 
 # dram bytes (read + write) per full-size rollout launch, from the committed
 # ncu capture of this kernel (set to None when the kernel changes)
-TRAFFIC_BYTES_PER_LAUNCH = 279944192 + 659641856
+TRAFFIC_BYTES_PER_LAUNCH = 271902208 + 648972800
 
 
 def main():
