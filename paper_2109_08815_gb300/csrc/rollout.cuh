@@ -716,6 +716,21 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
     rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u);
 }
 
+// log p alone (no gradient): the forward sweep needs far fewer registers
+// than the reverse, so it runs with more resident blocks.
+#ifndef PDS_FWD_BLOCKS
+#define PDS_FWD_BLOCKS 5
+#endif
+template <int NL, bool FAST, bool EVERY>
+__global__ void __launch_bounds__(128, PDS_FWD_BLOCKS) rollout_fwd_kernel(const ChainParams c,
+                                                                        const float* __restrict__ X, int N,
+                                                                        Partials parts, int32_t* __restrict__ status) {
+  const size_t U = (size_t)N * c.W * c.R;
+  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= U) return;
+  rollout_unit<NL, FAST, false, EVERY>(c, X, N, parts, 0, status, u);
+}
+
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
 template <int NL, bool FAST, bool EVERY>
 __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
@@ -838,6 +853,15 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
       rollout_cs_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
     else
       rollout_cs_kernel<NL, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+  } else if (!grad) {
+    if (c.fast_math && every)
+      rollout_fwd_kernel<NL, true, true><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
+    else if (c.fast_math)
+      rollout_fwd_kernel<NL, true, false><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
+    else if (every)
+      rollout_fwd_kernel<NL, false, true><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
+    else
+      rollout_fwd_kernel<NL, false, false><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
   } else {
     // the same residual form as the batched kernel takes for the problem
     if (c.fast_math && every)

@@ -92,13 +92,24 @@ def test_single_particle_and_ragged_counts():
         _check(wl, obs, particles(wl, obs))
 
 
-def test_logp_only_matches_logp_with_gradient():
-    wl = f32_workload(wlmod.double_pendulum(N=50))
+@pytest.mark.parametrize("case", ["pendulum", "chain5_every_fast", "angles_only_fast"])
+def test_logp_only_matches_logp_with_gradient(case):
+    """log p alone runs a kernel of its own (the forward sweep, fewer
+    registers); it must give the same bits as the forward sweep of the
+    kernel that also computes the gradient."""
+    if case == "pendulum":
+        wl, K, fast = f32_workload(wlmod.double_pendulum(N=50)), None, None
+    elif case == "chain5_every_fast":
+        wl, K, fast = f32_workload(wlmod.chain5(N=300, T=200, W=4)), 1, 1
+    else:
+        wl, K, fast = f32_workload(wlmod.random_chain(4, 131, seed=8, T=60, W=5, observe_velocity=False)), 1, 1
     obs = observations(wl)
     x = particles(wl, obs)
-    lp1, _, _ = _run(wl, obs, x, grad=False)
-    lp2, _, _ = _run(wl, obs, x, grad=True)
+    lp1, _, st1 = _run(wl, obs, x, K=K, grad=False, fast=fast)
+    lp2, _, st2 = _run(wl, obs, x, K=K, grad=True, fast=fast)
     np.testing.assert_array_equal(lp1, lp2)
+    np.testing.assert_array_equal(st1, st2)
+    assert_logp_close(lp1, oracle_problem(wl, obs).loglik_grad(x, grad=False, threads=8))
 
 
 def test_gradient_matches_fp64_central_differences():
