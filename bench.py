@@ -833,7 +833,7 @@ def main():
     ap.add_argument("--no-trajset", action="store_true", help="skip the trajectory-set measurement")
     ap.add_argument("--no-metrics", action="store_true", help="skip the posterior-metric timing")
     ap.add_argument("--ref-sample", type=int, default=64, help="particles per reference-arm step")
-    ap.add_argument("--ref-sample-baseline", type=int, default=1024, help="particles in the cpu_baseline sample")
+    ap.add_argument("--ref-sample-baseline", type=int, default=4096, help="particles in the cpu_baseline sample")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -303,10 +303,12 @@ int pds_svgd_destroy(pds_svgd_t s);
  * bandwidth_out and phi_out pointers and the same options, and every later
  * call with them replays the graph, which saves the gaps between the
  * launches.  Calls with other pointers or options launch directly and
- * re-capture on their second use.  The state's stream must not be the
- * legacy or per-thread default stream, and if the caller is capturing that
- * stream already the kernels go into the caller's graph instead.  The first
- * call with new pointers also does the kernels' one-time set-up.  0: launch
+ * re-capture on their second use.  On the legacy or per-thread default
+ * stream, which cannot be captured, the graph runs on a stream of the
+ * state's own, ordered after the caller's stream and the caller's stream
+ * after it by two events.  If the caller is capturing the state's stream
+ * already, the kernels go into the caller's graph instead.  The first call
+ * with new pointers also does the kernels' one-time set-up.  0: launch
  * every kernel every time. */
 #define PDS_OPT_GRAPH 7
 int pds_svgd_set_option(pds_svgd_t s, int option, int value);

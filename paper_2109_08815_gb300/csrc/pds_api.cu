@@ -541,6 +541,7 @@ int pds_svgd_reset(pds_svgd_t s) {
 int pds_svgd_destroy(pds_svgd_t s) {
   if (!s) return PDS_OK;
   cudaStreamSynchronize(s->stream);
+  if (s->gstream) cudaStreamSynchronize(s->gstream);
   cudaFree(s->w.cand);
   cudaFree(s->w.samp);
   cudaFree(s->w.cbuf);
@@ -555,6 +556,9 @@ int pds_svgd_destroy(pds_svgd_t s) {
   cudaFree(s->w.ctl);
   if (s->h_status) cudaFreeHost(s->h_status);
   drop_graph(s);
+  if (s->gstream) cudaStreamDestroy(s->gstream);
+  if (s->gev_in) cudaEventDestroy(s->gev_in);
+  if (s->gev_out) cudaEventDestroy(s->gev_out);
   delete s;
   return PDS_OK;
 }
@@ -575,28 +579,62 @@ static int take_status(pds_svgd* s) {
 
 int pds_svgd_status(pds_svgd_t s) {
   if (!s) return fail(PDS_ERR_ARG, "NULL svgd");
-  const cudaError_t e = cudaStreamSynchronize(s->stream);
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e == cudaSuccess && s->gstream) e = cudaStreamSynchronize(s->gstream);
   if (e != cudaSuccess) return cuda_fail(e, "svgd status");
   return take_status(s);
 }
 
-// The ~25 kernels of one step, launched one by one.
-static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out, int* n) {
+// The ~25 kernels of one step, launched one by one on st.
+static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out,
+                                   cudaStream_t st, int* n) {
   SvgdWork w = s->w;
   if (s->full_passes) w.cand_cap = 0;
   if (s->phi_cuda_cores) w.tc = nullptr;
   if (s->median_cuda_cores) w.mimg = nullptr;
-  return launch_svgd_step(s->sp, w, X, G, bw_out, phi_out, s->stream, n);
+  return launch_svgd_step(s->sp, w, X, G, bw_out, phi_out, st, n);
 }
 
-// A stream whose work can be captured by this library: not the legacy or
-// per-thread default stream, and not already being captured by the caller
-// (whose own graph then takes the kernels).
-static bool capturable(cudaStream_t st) {
-  if (st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread) return false;
+static bool default_stream(cudaStream_t st) {
+  return st == nullptr || st == cudaStreamLegacy || st == cudaStreamPerThread;
+}
+
+// The caller is capturing st (its own graph then takes the kernels).
+static bool being_captured(cudaStream_t st) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
-  return cs == cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return true;  // unknown: launch directly
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// The stream the step's graph is captured on and replayed on: the caller's,
+// or (for a default stream, which cannot be captured) the state's own.
+static cudaError_t graph_stream(pds_svgd* s, cudaStream_t* out) {
+  if (!default_stream(s->stream)) {
+    *out = s->stream;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!s->gstream && (e = cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!s->gev_in && (e = cudaEventCreateWithFlags(&s->gev_in, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if (!s->gev_out && (e = cudaEventCreateWithFlags(&s->gev_out, cudaEventDisableTiming)) != cudaSuccess) return e;
+  *out = s->gstream;
+  return cudaSuccess;
+}
+
+// Order gs after the caller's stream (before = true) or the caller's stream
+// after gs; nothing when gs is the caller's stream.
+static cudaError_t join(pds_svgd* s, cudaStream_t gs, bool before) {
+  if (gs == s->stream) return cudaSuccess;
+  cudaError_t e;
+  if (before) {
+    if ((e = cudaEventRecord(s->gev_in, s->stream)) != cudaSuccess) return e;
+    return cudaStreamWaitEvent(gs, s->gev_in, 0);
+  }
+  if ((e = cudaEventRecord(s->gev_out, gs)) != cudaSuccess) return e;
+  return cudaStreamWaitEvent(s->stream, s->gev_out, 0);
 }
 
 int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* bandwidth_out, float* phi_out) {
@@ -606,12 +644,12 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   if (st != PDS_OK) return st;
   int n = 0;
   cudaError_t e = cudaSuccess;
-  if (!s->use_graph || !capturable(s->stream)) {
-    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
+  auto direct = [&]() {
+    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, s->stream, &n);
     g_launches = n;
-    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
-    return PDS_OK;
-  }
+    return e == cudaSuccess ? PDS_OK : cuda_fail(e, "svgd launch");
+  };
+  if (!s->use_graph || being_captured(s->stream)) return direct();
   SvgdGraphKey k;
   memset(&k, 0, sizeof(k));
   k.X = particles;
@@ -627,44 +665,37 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
     drop_graph(s);
     s->gkey = k;
   }
-  if (s->gexec) {
-    e = cudaGraphLaunch(s->gexec, s->stream);
-    g_launches = s->glaunches;
-    if (e != cudaSuccess) return cuda_fail(e, "svgd graph launch");
-    return PDS_OK;
+  // first call with these buffers: launch directly (it also does each
+  // kernel's one-time set-up, which is not captured)
+  if (!s->gexec && s->gkey_calls++ == 0) return direct();
+  cudaStream_t gs = nullptr;
+  if ((e = graph_stream(s, &gs)) != cudaSuccess || (e = join(s, gs, true)) != cudaSuccess)
+    return cuda_fail(e, "svgd graph stream");
+  if (!s->gexec) {
+    // second call: capture the step once, then replay it
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t el = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, gs, &n);
+      e = cudaStreamEndCapture(gs, &g);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      // capture refused: launch directly from now on
+      cudaGetLastError();
+      s->gexec = nullptr;
+      s->use_graph = 0;
+      if ((e = join(s, gs, false)) != cudaSuccess) return cuda_fail(e, "svgd graph stream");
+      return direct();
+    }
+    s->glaunches = n;
   }
-  if (s->gkey_calls++ == 0) {
-    // first call with these buffers: launch directly (it also does each
-    // kernel's one-time set-up, which is not captured)
-    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
-    g_launches = n;
-    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
-    return PDS_OK;
-  }
-  // second call: capture the step once, then replay it
-  cudaGraph_t g = nullptr;
-  e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) {
-    const cudaError_t el = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
-    e = cudaStreamEndCapture(s->stream, &g);
-    if (e == cudaSuccess) e = el;
-  }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    // capture refused: keep launching directly for this key
-    cudaGetLastError();
-    s->gexec = nullptr;
-    s->use_graph = 0;
-    e = svgd_launch_all(s, particles, grad, bandwidth_out, phi_out, &n);
-    g_launches = n;
-    if (e != cudaSuccess) return cuda_fail(e, "svgd launch");
-    return PDS_OK;
-  }
-  s->glaunches = n;
-  e = cudaGraphLaunch(s->gexec, s->stream);
-  g_launches = n;
+  e = cudaGraphLaunch(s->gexec, gs);
+  g_launches = s->glaunches;
   if (e != cudaSuccess) return cuda_fail(e, "svgd graph launch");
+  if ((e = join(s, gs, false)) != cudaSuccess) return cuda_fail(e, "svgd graph stream");
   return PDS_OK;
 }
 

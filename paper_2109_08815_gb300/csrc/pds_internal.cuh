@@ -231,6 +231,11 @@ struct pds_svgd {
   int gkey_calls = 0;            // calls made with gkey
   cudaGraphExec_t gexec = nullptr;
   int glaunches = 0;             // kernels inside the graph
+  // where the graph runs when the caller's stream cannot be captured (the
+  // legacy or per-thread default stream): an own stream, ordered after and
+  // before the caller's stream by two events
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   cudaStream_t stream;
   int full_passes = 0;
   int phi_cuda_cores = 0;

@@ -63,6 +63,38 @@ def test_graph_replay_equals_direct_launches(N, M, P, options):
     _same(a, b)
 
 
+@pytest.mark.parametrize("N,M,P", [(4096, 10, 30), (300, 3, 7)])
+def test_graph_on_the_default_stream_equals_direct_launches(N, M, P):
+    """On torch's default stream (the legacy stream, which cannot be
+    captured) the graph runs on the state's own stream, ordered by events:
+    the same bits, and the caller's next default-stream work sees them."""
+    s = torch.cuda.default_stream()
+    a = _run(N, M, P, N + 1, True, 5, s)
+    b = _run(N, M, P, N + 1, False, 5, s)
+    _same(a, b)
+    # default-stream work right after a replayed step reads its result
+    lo, hi, x, g = _case(N, M, P, N + 2)
+    X = torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
+    G = torch.from_numpy(np.ascontiguousarray(g.T)).cuda()
+    sv = api.Svgd(N, M, P, lo, hi)
+    sums = []
+    for _ in range(4):
+        sv.step(X, G)
+        sums.append(X.double().sum())  # queued on the default stream
+    torch.cuda.synchronize()
+    sv.close()
+    ref = api.Svgd(N, M, P, lo, hi)
+    ref.set_option(api.OPT_GRAPH, 0)
+    Y = torch.from_numpy(np.ascontiguousarray(x.T)).cuda()
+    ref_sums = []
+    for _ in range(4):
+        ref.step(Y, G)
+        ref_sums.append(Y.double().sum())
+    torch.cuda.synchronize()
+    ref.close()
+    assert [float(v) for v in sums] == [float(v) for v in ref_sums]
+
+
 def test_new_buffers_and_options_recapture():
     """Steps alternate between two particle sets (each captured on its second
     use) and switch an option midway; every step equals the direct path."""
