@@ -364,7 +364,8 @@ def run_pds(args):
         lh_t = torch.empty(N, dtype=torch.float32, pin_memory=True)
         xh, lh = xh_t.numpy(), lh_t.numpy()
         xh[...] = X.cpu().numpy()
-        api.iterate_host(prob, svgd, xh, 1, lh)  # warm
+        for _ in range(3):  # warm: the first calls set up and capture the host path's step
+            api.iterate_host(prob, svgd, xh, 1, lh)
         ts = []
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
@@ -813,7 +814,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
 
 # dram bytes (read + write) per full-size rollout launch, from the committed
 # ncu capture of this kernel (set to None when the kernel changes)
-TRAFFIC_BYTES_PER_LAUNCH = 271902208 + 648972800
+TRAFFIC_BYTES_PER_LAUNCH = 272974592 + 649377024
 
 
 def main():

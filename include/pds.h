@@ -359,7 +359,12 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
 /* Same as pds_iterate for host-resident data: copies particles (host [P][N])
  * to the device, runs `iters` iterations, copies the updated particles and
  * the last log p (host [N] or NULL) back, and synchronises the stream.
- * Pinned host memory gives the fastest copies. */
+ * For a single planar-chain trajectory the copy in is made in groups of
+ * windows (theta and the shooting states that the group's windows read),
+ * and each group's rollout starts, on a stream of the problem's own, as
+ * soon as its rows have landed, so that the copy overlaps the first
+ * rollout.  The results are those of pds_iterate bit for bit.  Pinned
+ * host memory gives the fastest copies and the overlap. */
 int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters,
                      float* logp_host);
 

@@ -14,7 +14,8 @@
 
 namespace pds {
 template <int NL>
-cudaError_t launch_rollout_nl(const ChainParams&, const float*, int, const Partials&, int, int32_t*, cudaStream_t);
+cudaError_t launch_rollout_nl(const ChainParams&, const float*, int, const Partials&, int, int32_t*, cudaStream_t, size_t,
+                              size_t);
 template <int NL>
 cudaError_t launch_simulate_nl(const ChainParams&, const float*, int, float*, cudaStream_t);
 
@@ -44,16 +45,16 @@ static int cuda_fail(cudaError_t e, const char* what) {
 }
 
 cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                           int32_t* status, cudaStream_t st) {
+                           int32_t* status, cudaStream_t st, size_t u0, size_t nu) {
   switch (c.n) {
-    case 1: return launch_rollout_nl<1>(c, X, N, parts, grad, status, st);
-    case 2: return launch_rollout_nl<2>(c, X, N, parts, grad, status, st);
-    case 3: return launch_rollout_nl<3>(c, X, N, parts, grad, status, st);
-    case 4: return launch_rollout_nl<4>(c, X, N, parts, grad, status, st);
-    case 5: return launch_rollout_nl<5>(c, X, N, parts, grad, status, st);
-    case 6: return launch_rollout_nl<6>(c, X, N, parts, grad, status, st);
-    case 7: return launch_rollout_nl<7>(c, X, N, parts, grad, status, st);
-    case 8: return launch_rollout_nl<8>(c, X, N, parts, grad, status, st);
+    case 1: return launch_rollout_nl<1>(c, X, N, parts, grad, status, st, u0, nu);
+    case 2: return launch_rollout_nl<2>(c, X, N, parts, grad, status, st, u0, nu);
+    case 3: return launch_rollout_nl<3>(c, X, N, parts, grad, status, st, u0, nu);
+    case 4: return launch_rollout_nl<4>(c, X, N, parts, grad, status, st, u0, nu);
+    case 5: return launch_rollout_nl<5>(c, X, N, parts, grad, status, st, u0, nu);
+    case 6: return launch_rollout_nl<6>(c, X, N, parts, grad, status, st, u0, nu);
+    case 7: return launch_rollout_nl<7>(c, X, N, parts, grad, status, st, u0, nu);
+    case 8: return launch_rollout_nl<8>(c, X, N, parts, grad, status, st, u0, nu);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -276,6 +277,19 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
 int pds_problem_destroy(pds_problem_t p) {
   if (!p) return PDS_OK;
   cudaStreamSynchronize(p->stream);
+  if (p->ov_copy) {
+    cudaStreamSynchronize(p->ov_copy);
+    cudaStreamDestroy(p->ov_copy);
+  }
+  for (int g = 0; g < pds_problem::kCopyGroups; ++g) {
+    if (p->ov_roll[g]) {
+      cudaStreamSynchronize(p->ov_roll[g]);
+      cudaStreamDestroy(p->ov_roll[g]);
+    }
+    if (p->ov_copied[g]) cudaEventDestroy(p->ov_copied[g]);
+    if (p->ov_rolled[g]) cudaEventDestroy(p->ov_rolled[g]);
+  }
+  if (p->ov_start) cudaEventDestroy(p->ov_start);
   free_parts(p->parts);
   cudaFree(p->d_obs);
   cudaFree(p->d_obs_s);
@@ -497,11 +511,14 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   return pds_svgd_reset(s);
 }
 
-// Forget the captured SVGD step (its graph and the calls counted towards a capture).
+// Forget the captured SVGD steps (their graphs and the calls counted towards a capture).
+static void drop_graph_slot(pds_svgd::Graph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g.exec = nullptr;
+  g.calls = 0;
+}
 static void drop_graph(pds_svgd* s) {
-  if (s->gexec) cudaGraphExecDestroy(s->gexec);
-  s->gexec = nullptr;
-  s->gkey_calls = 0;
+  for (auto& g : s->graphs) drop_graph_slot(g);
 }
 
 int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
@@ -661,17 +678,25 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   k.median_cuda_cores = s->median_cuda_cores;
   k.wait_limit = s->w.wait_limit;
   k.sp = s->sp;
-  if (memcmp(&k, &s->gkey, sizeof(k)) != 0) {
-    drop_graph(s);
-    s->gkey = k;
+  pds_svgd::Graph* gr = nullptr;
+  for (auto& g : s->graphs)
+    if (g.calls > 0 && memcmp(&k, &g.key, sizeof(k)) == 0) gr = &g;
+  if (!gr) {
+    // a new key takes the slot used longest ago
+    gr = &s->graphs[0];
+    for (auto& g : s->graphs)
+      if (g.used < gr->used) gr = &g;
+    drop_graph_slot(*gr);
+    gr->key = k;
   }
+  gr->used = ++s->graph_clock;
   // first call with these buffers: launch directly (it also does each
   // kernel's one-time set-up, which is not captured)
-  if (!s->gexec && s->gkey_calls++ == 0) return direct();
+  if (!gr->exec && gr->calls++ == 0) return direct();
   cudaStream_t gs = nullptr;
   if ((e = graph_stream(s, &gs)) != cudaSuccess || (e = join(s, gs, true)) != cudaSuccess)
     return cuda_fail(e, "svgd graph stream");
-  if (!s->gexec) {
+  if (!gr->exec) {
     // second call: capture the step once, then replay it
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
@@ -680,20 +705,20 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
       e = cudaStreamEndCapture(gs, &g);
       if (e == cudaSuccess) e = el;
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->gexec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gr->exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
       // capture refused: launch directly from now on
       cudaGetLastError();
-      s->gexec = nullptr;
+      gr->exec = nullptr;
       s->use_graph = 0;
       if ((e = join(s, gs, false)) != cudaSuccess) return cuda_fail(e, "svgd graph stream");
       return direct();
     }
-    s->glaunches = n;
+    gr->launches = n;
   }
-  e = cudaGraphLaunch(s->gexec, gs);
-  g_launches = s->glaunches;
+  e = cudaGraphLaunch(gr->exec, gs);
+  g_launches = gr->launches;
   if (e != cudaSuccess) return cuda_fail(e, "svgd graph launch");
   if ((e = join(s, gs, false)) != cudaSuccess) return cuda_fail(e, "svgd graph stream");
   return PDS_OK;
@@ -725,17 +750,91 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
   return PDS_OK;
 }
 
+// The copy streams and events of a problem (created on first use).
+static int ensure_copy_streams(pds_problem* p) {
+  if (p->ov_copy) return PDS_OK;
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&p->ov_copy, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&p->ov_start, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "copy streams");
+  for (int g = 0; g < pds_problem::kCopyGroups; ++g)
+    if ((e = cudaStreamCreateWithFlags(&p->ov_roll[g], cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->ov_copied[g], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->ov_rolled[g], cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "copy streams");
+  return PDS_OK;
+}
+
+// The first log p + gradient of pds_iterate_host with its copy in: the
+// particle rows [P][N] go over in groups of windows (theta and the shooting
+// states up to the group's last defect target), and each group's rollout
+// units (contiguous, u = w N + i) start on a stream of their own as soon as
+// their rows have landed, so that the copy hides behind the rollout.  The
+// kernels and their arithmetic are those of pds_loglik_grad.
+static int loglik_grad_copy_in(pds_problem* p, const float* host, int N, int* launches) {
+  const ChainParams& c = p->c;
+  const int G = c.W < pds_problem::kCopyGroups ? c.W : pds_problem::kCopyGroups;
+  cudaError_t e = cudaSuccess;
+  if (int rc = ensure_copy_streams(p)) return rc;
+  // the copies wait for earlier work on the problem's stream (it may still read d_x)
+  if ((e = cudaEventRecord(p->ov_start, p->stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(p->ov_copy, p->ov_start, 0)) != cudaSuccess)
+    return cuda_fail(e, "copy order");
+  size_t row0 = 0;
+  for (int g = 0; g < G; ++g) {
+    const int w0 = (int)(((long long)g * c.W) / G), w1 = (int)(((long long)(g + 1) * c.W) / G);
+    // rows of theta and of the shooting states s^s_1 .. s^s_min(w1, W-1)
+    const size_t row1 = (size_t)c.M + (size_t)c.S * (size_t)(w1 < c.W - 1 ? w1 : c.W - 1);
+    if (row1 > row0) {
+      e = cudaMemcpyAsync(p->d_x + row0 * N, host + row0 * N, (row1 - row0) * N * sizeof(float),
+                          cudaMemcpyHostToDevice, p->ov_copy);
+      if (e != cudaSuccess) return cuda_fail(e, "copy particles to device");
+      row0 = row1;
+    }
+    if ((e = cudaEventRecord(p->ov_copied[g], p->ov_copy)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->ov_roll[g], p->ov_copied[g], 0)) != cudaSuccess)
+      return cuda_fail(e, "copy order");
+    e = launch_rollout(c, p->d_x, N, p->parts, 1, nullptr, p->ov_roll[g], (size_t)w0 * N, (size_t)(w1 - w0) * N);
+    if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
+    if ((e = cudaEventRecord(p->ov_rolled[g], p->ov_roll[g])) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(p->stream, p->ov_rolled[g], 0)) != cudaSuccess)
+      return cuda_fail(e, "copy order");
+  }
+  e = launch_window_reduce(c, p->d_x, N, p->parts, p->d_logp, p->d_grad, nullptr, p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "window reduce launch");
+  *launches = G + 1;
+  return PDS_OK;
+}
+
 int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int iters, float* logp_host) {
   if (!p || !s || !particles_host) return fail(PDS_ERR_ARG, "NULL argument");
+  if (iters < 0) return fail(PDS_ERR_ARG, "iters < 0");
   const int N = s->sp.N;
   int rc = ensure_iter_buffers(p, N);
   if (rc != PDS_OK) return rc;
   const size_t bytes = (size_t)p->c.P * N * sizeof(float);
-  cudaError_t e = cudaMemcpyAsync(p->d_x, particles_host, bytes, cudaMemcpyHostToDevice, p->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "copy particles to device");
-  rc = pds_iterate(p, s, p->d_x, iters, p->d_logp);
-  if (rc != PDS_OK) return rc;
-  const int launches = g_launches;
+  cudaError_t e = cudaSuccess;
+  // the copy in overlaps the first rollout for a single planar-chain
+  // trajectory (the units of a group of windows are contiguous)
+  const bool copy_in = iters >= 1 && s->sp.M == p->c.M && s->sp.P == p->c.P && !s->sp.csvgd && !p->c.csvgd &&
+                       p->kind == PDS_SYSTEM_PLANAR_CHAIN && p->c.R == 1;
+  int launches = 0;
+  if (copy_in) {
+    if ((rc = take_status(s)) != PDS_OK) return rc;
+    if ((rc = ensure_workspace(p, N)) != PDS_OK) return rc;
+    if ((rc = loglik_grad_copy_in(p, particles_host, N, &launches)) != PDS_OK) return rc;
+    if ((rc = pds_svgd_step(s, p->d_x, p->d_grad, nullptr, nullptr)) != PDS_OK) return rc;
+    launches += g_launches;
+    if (iters > 1) {
+      if ((rc = pds_iterate(p, s, p->d_x, iters - 1, p->d_logp)) != PDS_OK) return rc;
+      launches += g_launches;
+    }
+  } else {
+    e = cudaMemcpyAsync(p->d_x, particles_host, bytes, cudaMemcpyHostToDevice, p->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy particles to device");
+    if ((rc = pds_iterate(p, s, p->d_x, iters, p->d_logp)) != PDS_OK) return rc;
+    launches = g_launches;
+  }
   e = cudaMemcpyAsync(particles_host, p->d_x, bytes, cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess && logp_host)
     e = cudaMemcpyAsync(logp_host, p->d_logp, (size_t)N * sizeof(float), cudaMemcpyDeviceToHost, p->stream);

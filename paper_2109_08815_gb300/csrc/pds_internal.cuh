@@ -87,8 +87,9 @@ struct WorkItem {
 };
 
 // Launchers (return cudaGetLastError()).
+// nu = 0: all units; otherwise the gradient kernel on units [u0, u0 + nu).
 cudaError_t launch_rollout(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                           int32_t* status, cudaStream_t st);
+                           int32_t* status, cudaStream_t st, size_t u0 = 0, size_t nu = 0);
 cudaError_t launch_window_reduce(const ChainParams& c, const float* X, int N, const Partials& parts, float* logp,
                                  float* grad, int32_t* status, cudaStream_t st);
 cudaError_t launch_simulate(const ChainParams& c, const float* theta, int N, float* states, cudaStream_t st);
@@ -208,6 +209,14 @@ struct pds_problem {
   float* d_grad = nullptr;
   float* d_logp = nullptr;
   float* d_x = nullptr;
+  // pds_iterate_host: the particles' rows are copied in groups of windows,
+  // each group's rollout starting on a stream of its own as its rows land
+  static constexpr int kCopyGroups = 8;
+  cudaStream_t ov_copy = nullptr;
+  cudaStream_t ov_roll[kCopyGroups] = {};
+  cudaEvent_t ov_start = nullptr;
+  cudaEvent_t ov_copied[kCopyGroups] = {};
+  cudaEvent_t ov_rolled[kCopyGroups] = {};
 };
 
 // What a captured SVGD step depends on besides the state's own buffers.
@@ -225,12 +234,19 @@ struct pds_svgd {
   pds::SvgdWork w{};
   int* h_status = nullptr;  // mapped host word behind w.status_flags
   // the step replayed from a CUDA graph (PDS_OPT_GRAPH): captured on the
-  // second call with the same key, replayed while the key stays the same
+  // second call with the same key and replayed on later ones; the graphs of
+  // the two most recent keys are kept (a caller that alternates two sets of
+  // buffers, such as its own loop and pds_iterate_host, keeps both)
   int use_graph = 1;
-  SvgdGraphKey gkey{};
-  int gkey_calls = 0;            // calls made with gkey
-  cudaGraphExec_t gexec = nullptr;
-  int glaunches = 0;             // kernels inside the graph
+  static constexpr int kGraphs = 2;
+  struct Graph {
+    SvgdGraphKey key{};
+    int calls = 0;                  // calls made with key (0: slot unused)
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;               // kernels inside the graph
+    long long used = 0;             // last use, for replacing the older slot
+  } graphs[kGraphs];
+  long long graph_clock = 0;
   // where the graph runs when the caller's stream cannot be captured (the
   // legacy or per-thread default stream): an own stream, ordered after and
   // before the caller's stream by two events

@@ -701,14 +701,16 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
 // seg_smem: the reverse sweep's recomputed segment states live in dynamic
 // shared memory (K x 2 NL x blockDim floats), else in the tape.  EVERY:
 // the problem observes every state component.
+// Units [u0, u1) of the launch (all N W R units, or those of a group of
+// windows whose particle rows have arrived).
 template <int NL, bool FAST, bool EVERY>
 __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(const ChainParams c, const float* __restrict__ X,
                                                                         int N, Partials parts, int grad,
-                                                                        int32_t* __restrict__ status, int seg_smem) {
+                                                                        int32_t* __restrict__ status, int seg_smem,
+                                                                        size_t u0, size_t u1) {
   extern __shared__ float seg_sh[];
-  const size_t U = (size_t)N * c.W * c.R;
-  const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= U) return;
+  const size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= u1) return;
   if (seg_smem)
     rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x,
                                                           blockDim.x);
@@ -833,11 +835,19 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
   }
 }
 
+// nu = 0: all units; otherwise units [u0, u0 + nu) of the gradient kernel.
 template <int NL>
 cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
-                              int32_t* status, cudaStream_t st) {
+                              int32_t* status, cudaStream_t st, size_t u0, size_t nu) {
   const size_t U = (size_t)N * c.W * c.R;
-  const unsigned blocks = (unsigned)((U + 127) / 128);
+  if (nu == 0) {
+    u0 = 0;
+    nu = U;
+  } else if (!grad || c.csvgd || u0 + nu > U) {
+    return cudaErrorInvalidValue;
+  }
+  const unsigned blocks = (unsigned)((nu + 127) / 128);
+  const size_t u1 = u0 + nu;
   // the reverse sweep's K recomputed states (K = 1: the ring of kRingSlots
   // prefetched states) in shared memory when they fit in the default 48 KB of
   // a block
@@ -865,13 +875,13 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
   } else {
     // the same residual form as the batched kernel takes for the problem
     if (c.fast_math && every)
-      rollout_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+      rollout_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
     else if (c.fast_math)
-      rollout_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+      rollout_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
     else if (every)
-      rollout_kernel<NL, false, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+      rollout_kernel<NL, false, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
     else
-      rollout_kernel<NL, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+      rollout_kernel<NL, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
   }
   return cudaGetLastError();
 }
