@@ -359,13 +359,8 @@ __device__ __forceinline__ void obs_seed_pairs(const ChainParams& c, const float
   }
 }
 
-// Asynchronous 4-byte copy global -> shared (cp.async), its group commit,
-// and the wait for all but the two newest groups.
-__device__ __forceinline__ void cp_async4(float* dst_smem, const float* src_global) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
-               "l"(src_global)
-               : "memory");
-}
+// Asynchronous 8-byte copy global -> shared (cp.async), its group commit,
+// and the wait for all but the A newest groups.
 __device__ __forceinline__ void cp_async8(float2* dst_smem, const float2* src_global) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
                "l"(src_global)

@@ -24,6 +24,9 @@ particles of a seeded workload and compares what the iterations produce:
   its posterior is symmetric under swapping the two weights, so particles
   are compared after ordering each one's weights by x, on the fraction that
   needed the swap (the mode each particle settled in) and the moments.
+* The benchmark's own system (the 5-link damped chain with the fast-math
+  rollout) and the 11-parameter rigid double pendulum: theta's moments and
+  the MMD^2 test after 20-25 iterations.
 * The linear-Gaussian toy (a target with a closed-form posterior) through
   pds_svgd_step on the device: the mean within 0.05 sigma, the covariance
   within 10 % (the oracle pin of the same toy, now on the GPU), and the
@@ -284,3 +287,64 @@ def test_linear_gaussian_toy_on_the_gpu():
             for _ in range(iters):
                 st.step(xo, -(xo - mu) @ Pr)
             _moments_agree(xg, xo)
+
+
+def _run_both(prob, op, wl, x, iters, threads=THREADS):
+    """pds_iterate on the GPU and the oracle's own loop from the same particles."""
+    sv = api.Svgd(wl.N, wl.M, wl.P, wl.lo, wl.hi, lr=wl.lr)
+    X = _gpu(x)
+    api.iterate(prob, sv, X, iters)
+    torch.cuda.synchronize()
+    xg = _host(X)
+    sv.close()
+    ost = orc.SvgdState(wl.N, wl.P, wl.lo, wl.hi, lr=wl.lr)
+    xo = np.ascontiguousarray(x.copy())
+    for _ in range(iters):
+        _, g_ref = op.loglik_grad(xo, threads=threads)
+        ost.step(xo, g_ref)
+    return xg, xo
+
+
+@pytest.mark.slow
+def test_chain5_posterior_with_fast_math():
+    """The benchmark's system (5-link damped chain, theta = 5 masses + 5
+    dampings, T = 1000 at dt = 0.005, 20 windows, angles and velocities
+    observed) with the benchmark's fast-math rollout, N = 256 for 20
+    iterations: theta's moments and the MMD^2 two-sample test against the
+    oracle run from the same particles."""
+    wl = f32_workload(wlmod.chain5(N=256))
+    obs = observations(wl)
+    x = particles(wl, obs)
+    op = oracle_problem(wl, obs)
+    prob = api.Problem.from_workload(wl, obs, checkpoint_stride=1, fast_math=1)
+    xg, xo = _run_both(prob, op, wl, x, 20)
+    prob.close()
+    assert np.all(np.isfinite(xg)) and np.all(np.isfinite(xo))
+    _moments_agree(xg[:, :wl.M], xo[:, :wl.M])
+    ug = (xg[:, :wl.M] - wl.lo) / (wl.hi - wl.lo)
+    uo = (xo[:, :wl.M] - wl.lo) / (wl.hi - wl.lo)
+    h = orc.median_sqdist(uo)
+    m2, p = _mmd_permutation_pvalue(ug, uo, h)
+    assert p > 0.05, (m2, p)
+    # the shooting states too: per-dimension means within 5e-2 of their spread
+    sd = np.std(xo[:, wl.M:], axis=0) + 1e-3
+    assert np.all(np.abs(xg[:, wl.M:].mean(0) - xo[:, wl.M:].mean(0)) <= 5e-2 * sd)
+
+
+@pytest.mark.slow
+def test_rigid_double_pendulum_posterior():
+    """The 11-parameter rigid double pendulum (N = 128, T = 200, W = 5),
+    25 iterations: the same comparison of theta's moments and MMD^2."""
+    import test_gpu_rigid2 as tr
+    wl, obs = tr._workload(N=128, T=200, W=5)
+    x = tr._particles(wl, obs)
+    op = tr._oracle(wl, obs)
+    prob = api.Problem.from_workload(wl, obs)
+    xg, xo = _run_both(prob, op, wl, x, 25)
+    prob.close()
+    assert np.all(np.isfinite(xg))
+    _moments_agree(xg[:, :wl.M], xo[:, :wl.M])
+    ug = (xg[:, :wl.M] - wl.lo) / (wl.hi - wl.lo)
+    uo = (xo[:, :wl.M] - wl.lo) / (wl.hi - wl.lo)
+    m2, p = _mmd_permutation_pvalue(ug, uo, orc.median_sqdist(uo))
+    assert p > 0.05, (m2, p)
