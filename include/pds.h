@@ -277,8 +277,9 @@ int pds_svgd_destroy(pds_svgd_t s);
  * 1 = the hardware approximation __expf.  PDS_OPT_MEDIAN_FULL_PASSES 0
  * (default) = for N >= 2048 bracket the median from a sample of pairs and
  * select among the pairs inside the bracket (falling back to the full passes
- * if the bracket misses); 1 = always three radix passes over all pairs.
- * Both give the same exact median.  PDS_OPT_PHI_CUDA_CORES 0 (default) = for
+ * if the bracket misses), and for N <= 256 select it in one block with every
+ * pair distance in shared memory; 1 = always three radix passes over all
+ * pairs, recomputing the distances in each.  All give the same exact median.  PDS_OPT_PHI_CUDA_CORES 0 (default) = for
  * N >= 256 the kernel-matrix products of phi run on the tensor cores
  * (tcgen05: the exponent product in tf32 with split operands, the product of
  * the kernel values with the gradients and coordinates in fp16 with split

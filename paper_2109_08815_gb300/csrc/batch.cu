@@ -209,7 +209,10 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     if ((e = launch_window_reduce(p->c, b->X[j], N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess)
       return e;
     SvgdWork w = s->w;
-    if (s->full_passes) w.cand_cap = 0;
+    if (s->full_passes) {
+      w.cand_cap = 0;
+      w.small_median = 0;
+    }
     if (s->phi_cuda_cores) w.tc = nullptr;
     if (s->median_cuda_cores) w.mimg = nullptr;
     int k = 0;

@@ -495,6 +495,7 @@ int pds_svgd_create(int N, int M, int P, const float* theta_lo, const float* the
   }
   *(volatile int*)s->h_status = 0;
   s->w.wait_limit = kWaitLimitDefault;
+  s->w.small_median = 1;
   if (N >= 2048) {
     const int n_items = median_tc_work_items(N, nullptr);
     std::vector<int> items(2 * (size_t)n_items);
@@ -606,7 +607,10 @@ int pds_svgd_status(pds_svgd_t s) {
 static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out,
                                    cudaStream_t st, int* n) {
   SvgdWork w = s->w;
-  if (s->full_passes) w.cand_cap = 0;
+  if (s->full_passes) {
+    w.cand_cap = 0;
+    w.small_median = 0;
+  }
   if (s->phi_cuda_cores) w.tc = nullptr;
   if (s->median_cuda_cores) w.mimg = nullptr;
   return launch_svgd_step(s->sp, w, X, G, bw_out, phi_out, st, n);

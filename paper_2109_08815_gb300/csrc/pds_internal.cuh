@@ -152,6 +152,7 @@ struct SvgdWork {
   float* adam_v;   // [P][N]
   SvgdCtl* ctl;
   int chunks;
+  int small_median;   // 1: for N <= kSmallMedianN the median in one block (all pairs in shared memory)
   int wait_limit;     // mbarrier polls before a tensor-core pass gives up (0: test once, never wait)
   int* status_flags;  // device alias of a mapped host word: kStatus* bits of the steps since the host last read it
 };
@@ -160,6 +161,7 @@ struct SvgdWork {
 constexpr int kStatusTimeout = 1;    // a tensor-core pass gave up waiting (the step's results are not valid)
 constexpr int kStatusNoneLive = 2;   // no particle had finite coordinates and gradient
 constexpr int kWaitLimitDefault = 1 << 24;
+constexpr int kSmallMedianN = 256;  // N(N-1)/2 <= 32640 pair distances (128 KB) in shared memory
 constexpr int kDrainLimit = 1 << 24;  // polls of the waits that let copies and products in flight finish
 
 cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,

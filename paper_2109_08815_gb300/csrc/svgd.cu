@@ -264,6 +264,118 @@ __global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N,
   for (int b = 0; b < 64; ++b) ctl->hist[lane * 64 + b] = 0u;
 }
 
+// ---- small N: the whole median in one block --------------------------------
+// For N <= kSmallMedianN every pair distance fits in shared memory (at most
+// 32640 floats).  One block computes them once, with the same arithmetic as
+// median_hist_kernel (sum over the padded coordinates in order, fmaf), and
+// runs the same three radix digits (11, 11, 10 bits) over shared memory
+// instead of over recomputed distances in three launches.  Pairs with a
+// particle that sits out are NaN and skipped; the rank over the live pairs
+// comes from the liveness pass.  The same exact lower median and bandwidth.
+constexpr int kSmallThreads = 512;
+
+template <int MM>
+__global__ void __launch_bounds__(kSmallThreads) median_small_kernel(int N, int M, const float* __restrict__ u,
+                                                                     SvgdCtl* __restrict__ ctl) {
+  extern __shared__ float sm_small[];
+  __shared__ unsigned int hist[kHistBins];
+  __shared__ unsigned int s_prefix, s_rank;
+  __shared__ int s_found;
+  float* us = sm_small;               // [MM][N] coordinates (0 beyond M)
+  float* dist = sm_small + MM * N;    // [N (N - 1) / 2] pair distances, i < j, row by row
+  const int t = threadIdx.x;
+  for (int e = t; e < MM * N; e += blockDim.x) {
+    const int k = e / N;
+    us[e] = k < M ? u[(size_t)k * N + (e - k * N)] : 0.f;
+  }
+  if (t == 0) {
+    s_prefix = 0u;
+    s_rank = ctl->rank;
+    s_found = 1;
+  }
+  __syncthreads();
+  const int pairs = N * (N - 1) / 2;
+  for (int q = t; q < N * N; q += blockDim.x) {
+    const int i = q / N, j = q - i * N;
+    if (j <= i) continue;
+    float d = 0.f;
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+      const float e = us[k * N + i] - us[k * N + j];
+      d = fmaf(e, e, d);
+    }
+    dist[i * N - i * (i + 1) / 2 + (j - i - 1)] = d;
+  }
+  __syncthreads();
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int b = t; b < kHistBins; b += blockDim.x) hist[b] = 0u;
+    __syncthreads();
+    const unsigned int prefix = s_prefix;
+    for (int p = t; p < pairs; p += blockDim.x) {
+      const float d = dist[p];
+      if (!(d == d)) continue;  // a pair with a particle that sits out the step
+      const unsigned int bits = __float_as_uint(d);
+      if (pass == 0) atomicAdd(&hist[bits >> 21], 1u);
+      else if (pass == 1) { if ((bits >> 21) == prefix) atomicAdd(&hist[(bits >> 10) & 2047u], 1u); }
+      else if ((bits >> 10) == prefix) atomicAdd(&hist[bits & 1023u], 1u);
+    }
+    __syncthreads();
+    if (t < 32) {
+      // the bin holding the rank (as median_select_kernel)
+      const int lane = t;
+      unsigned int local = 0u;
+      for (int b = 0; b < 64; ++b) local += hist[lane * 64 + b];
+      unsigned int incl = local;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned int o = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += o;
+      }
+      const unsigned int excl = incl - local;
+      const unsigned int rank = s_rank;
+      const bool any = __shfl_sync(0xffffffffu, incl, 31) > rank;
+      if (lane == 0 && !any) s_found = 0;
+      if (rank >= excl && rank < incl) {
+        unsigned int cum = excl;
+        int bin = lane * 64;
+        for (int b = 0; b < 64; ++b) {
+          const unsigned int h = hist[lane * 64 + b];
+          if (rank < cum + h) { bin = lane * 64 + b; break; }
+          cum += h;
+        }
+        const unsigned int digit_bits = (pass == 2) ? 10u : 11u;
+        s_rank = rank - cum;
+        s_prefix = (prefix << digit_bits) | (unsigned int)bin;
+      }
+    }
+    __syncthreads();
+  }
+  if (t == 0 && s_found) {
+    const float med = __uint_as_float(s_prefix);
+    ctl->med = med;
+    const unsigned int nl = ctl->n_live;
+    ctl->bw = (med > 0.f && nl > 1) ? med / logf((float)nl) : 1.0f;
+  }
+}
+
+template <int MM>
+static cudaError_t launch_median_small(int N, int M, const float* u, SvgdCtl* ctl, cudaStream_t st) {
+  const size_t smem = ((size_t)MM * N + (size_t)N * (N - 1) / 2) * sizeof(float);
+  static bool attr[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    const cudaError_t e = cudaFuncSetAttribute(median_small_kernel<MM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)(((size_t)MM * kSmallMedianN +
+                                                      (size_t)kSmallMedianN * (kSmallMedianN - 1) / 2) *
+                                                     sizeof(float)));
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  median_small_kernel<MM><<<1, kSmallThreads, smem, st>>>(N, M, u, ctl);
+  return cudaGetLastError();
+}
+
 // ---- sampled bracket around the median (large N) -------------------------
 // A sample of kSample ordered pairs (i != j, from a counter-based hash) is
 // sorted in shared memory; the order statistics at ranks kSample/2 -+ 2
@@ -872,8 +984,15 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
       n += 5;
     }
     // full passes over all pairs: always for small N or when asked, otherwise
-    // only if the bracket missed (the kernels return at once in that case)
-    for (int pass = 0; pass < 3; ++pass) {
+    // only if the bracket missed (the kernels return at once in that case);
+    // the smallest N in one block
+    const bool small = !bracket && !tcm && w.small_median && N <= kSmallMedianN;
+    if (small) {
+      cudaError_t e = launch_median_small<MM>(N, M, w.u, w.ctl, st);
+      if (e != cudaSuccess) return e;
+      n += 1;
+    }
+    for (int pass = 0; pass < 3 && !small; ++pass) {
       if (tcm) {
         cudaError_t e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, nullptr, 0ull, pass + 1,
                                          bracket ? 1 : 0, !prepped, w.wait_limit, st);

@@ -291,3 +291,25 @@ def test_particles_that_are_not_finite_sit_out(N, M, phi_cc, med_cc, full):
     assert np.max(np.abs(phi[live] - phi_ref[live])) <= PHI_TOL * np.max(np.abs(phi_ref[live]))
     assert np.all(np.isnan(phi[dead]))
     sv.close()
+
+
+@pytest.mark.parametrize("N,M", [(2, 1), (3, 2), (50, 4), (100, 4), (129, 10), (200, 16), (255, 7), (256, 12)])
+def test_small_median_in_one_block_equals_the_full_passes(N, M):
+    """For N <= 256 the median runs in one block with every pair distance in
+    shared memory; it must give the bandwidth of the three radix passes over
+    recomputed distances bit for bit, also with particles that sit out."""
+    rng = np.random.default_rng(N * 7 + M)
+    lo, hi = np.zeros(M), np.ones(M)
+    x = rng.uniform(size=(N, M)).astype(np.float32).astype(np.float64)
+    for dead in (False, True):
+        if dead and N > 3:
+            x[rng.choice(N, 3, replace=False), rng.integers(0, M)] = np.nan
+        out = [_bw(x, lo, hi, full) for full in (False, True)]
+        assert out[0] == out[1], (out, dead)
+    live = np.all(np.isfinite(x), axis=1)
+    u = x[live]
+    if len(u) >= 2:
+        d = np.sort(((u[:, None, :] - u[None, :, :]) ** 2).sum(-1)[np.triu_indices(len(u), 1)])
+        med = d[(len(d) - 1) // 2]
+        ref = med / np.log(len(u)) if med > 0 else 1.0
+        assert abs(out[0] - ref) <= 1e-5 * ref
