@@ -191,6 +191,15 @@ int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
  *    relative 1e-4 on log p, 1e-3 on the gradient). */
 #define PDS_OPT_CHECKPOINT_STRIDE 1
 #define PDS_OPT_FAST_MATH 2
+/*  PDS_OPT_UNITS_PER_THREAD: rollout units (particle-windows) per GPU thread
+ *    in pds_loglik_grad.  1 = one; 2 = two particles of a window per thread,
+ *    each quantity held as a pair so that the step's FP32 arithmetic issues
+ *    as paired (f32x2) instructions; 0 (default) = two for the chain lengths
+ *    where that measured faster (2, 4 and 5 links), else one.  Two apply only
+ *    to planar chains with K = 1, every state component observed, an even
+ *    particle count and no constrained SVGD; elsewhere one is used.  Both
+ *    give the same results bit for bit. */
+#define PDS_OPT_UNITS_PER_THREAD 8
 int pds_problem_set_option(pds_problem_t p, int option, int value);
 int pds_problem_get_option(pds_problem_t p, int option, int* value);
 

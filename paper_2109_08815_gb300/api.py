@@ -21,6 +21,7 @@ PARAM_MASS, PARAM_LENGTH, PARAM_DAMPING = 0, 1, 2
 OPT_CHECKPOINT_STRIDE, OPT_FAST_MATH, OPT_MEDIAN_FULL_PASSES, OPT_PHI_CUDA_CORES, OPT_MEDIAN_CUDA_CORES = 1, 2, 3, 4, 5
 OPT_WAIT_LIMIT = 6
 OPT_GRAPH = 7
+OPT_UNITS_PER_THREAD = 8
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NONFINITE, ERR_TIMEOUT, ERR_BUDGET, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 COMBINE_SUM, COMBINE_PRODUCT = 0, 1
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE = 0, 1, 2

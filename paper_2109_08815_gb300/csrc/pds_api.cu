@@ -148,12 +148,18 @@ int pds::ensure_iter_buffers(pds_problem* p, int N) {
 // The chain rollout reads each step's observations in state order, with
 // compile-time offsets and 8-byte loads: a [R][T][S] copy of the [R][T][D]
 // observations, unobserved components 0 (their residuals are skipped).
+// The observations in state order, [R][T][S] (unobserved components 0),
+// followed at *out_b (16-byte aligned) by the same values each written twice,
+// [R][T][S] float2, for the kernel that steps two particles per thread.
 static cudaError_t upload_state_ordered_obs(const ChainParams& c, int R, const float* obs, cudaStream_t st,
-                                            float** out) {
-  std::vector<float> h((size_t)R * c.T * c.S, 0.f);
+                                            float** out, float** out_b) {
+  const size_t n = (size_t)R * c.T * c.S;
+  const size_t off = (n + 3) / 4 * 4;
+  std::vector<float> h(off + 2 * n, 0.f);
   for (size_t rt = 0; rt < (size_t)R * c.T; ++rt)
     for (int j = 0; j < c.S; ++j)
       if (c.obs_col[j] >= 0) h[rt * c.S + j] = obs[rt * c.D + c.obs_col[j]];
+  for (size_t k = 0; k < n; ++k) h[off + 2 * k] = h[off + 2 * k + 1] = h[k];
   float* d = nullptr;
   cudaError_t e = cudaMalloc(&d, h.size() * sizeof(float));
   if (e != cudaSuccess) return e;
@@ -164,6 +170,7 @@ static cudaError_t upload_state_ordered_obs(const ChainParams& c, int R, const f
     return e;
   }
   *out = d;
+  *out_b = d + off;
   return cudaSuccess;
 }
 
@@ -267,9 +274,11 @@ int pds_problem_create(const pds_system_desc* sys, double dt, int T, int windows
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) { cudaFree(p->d_obs); delete p; return cuda_fail(e, "copy obs"); }
   p->c.obs = p->d_obs;
-  e = upload_state_ordered_obs(p->c, 1, obs, p->stream, &p->d_obs_s);
+  float* obs_b = nullptr;
+  e = upload_state_ordered_obs(p->c, 1, obs, p->stream, &p->d_obs_s, &obs_b);
   if (e != cudaSuccess) { cudaFree(p->d_obs); delete p; return cuda_fail(e, "copy obs (state order)"); }
   p->c.obs_s = p->d_obs_s;
+  p->c.obs_b = obs_b;
   *out = p;
   return PDS_OK;
 }
@@ -325,6 +334,10 @@ int pds_problem_set_option(pds_problem_t p, int option, int value) {
       if (value != 0 && value != 1) return fail(PDS_ERR_ARG, "fast math must be 0 or 1");
       p->c.fast_math = value;
       return PDS_OK;
+    case PDS_OPT_UNITS_PER_THREAD:
+      if (value < 0 || value > 2) return fail(PDS_ERR_ARG, "units per thread must be 0, 1 or 2");
+      p->c.units_per_thread = value;
+      return PDS_OK;
     default: return fail(PDS_ERR_ARG, "unknown option %d", option);
   }
 }
@@ -334,6 +347,7 @@ int pds_problem_get_option(pds_problem_t p, int option, int* value) {
   switch (option) {
     case PDS_OPT_CHECKPOINT_STRIDE: *value = p->c.K; return PDS_OK;
     case PDS_OPT_FAST_MATH: *value = p->c.fast_math; return PDS_OK;
+    case PDS_OPT_UNITS_PER_THREAD: *value = p->c.units_per_thread; return PDS_OK;
     default: return fail(PDS_ERR_ARG, "unknown option %d", option);
   }
 }
@@ -377,7 +391,8 @@ int pds_problem_set_trajectories(pds_problem_t p, int R, const float* obs, const
     return cuda_fail(e, "copy observations");
   }
   float* ds = nullptr;
-  if ((e = upload_state_ordered_obs(c, R, obs, p->stream, &ds)) != cudaSuccess) {
+  float* dsb = nullptr;
+  if ((e = upload_state_ordered_obs(c, R, obs, p->stream, &ds, &dsb)) != cudaSuccess) {
     cudaFree(d);
     return cuda_fail(e, "copy observations (state order)");
   }
@@ -387,6 +402,7 @@ int pds_problem_set_trajectories(pds_problem_t p, int R, const float* obs, const
   p->d_obs_s = ds;
   c.obs = d;
   c.obs_s = ds;
+  c.obs_b = dsb;
   for (int r = 0; r < R; ++r)
     for (int j = 0; j < c.S; ++j) c.s0[r * kMaxState + j] = s0[(size_t)r * c.S + j];
   c.R = R;

@@ -19,6 +19,7 @@ struct ChainParams {
   int n, M, T, W, D, S, P;
   int K;            // adjoint checkpoint stride
   int fast_math;    // 1: hardware sin/cos and reciprocal approximations
+  int units_per_thread;  // rollout units per thread: 0 automatic, 1, or 2 (where the two-unit kernel applies)
   int max_seg;      // checkpoint slots per unit = ceil(max window length / K)
   float dt, g;
   float inv_so2;    // 1 / sigma_obs^2
@@ -36,6 +37,7 @@ struct ChainParams {
   float lo[kMaxTheta], hi[kMaxTheta];
   const float* obs;        // device [R][T][D]
   const float* obs_s;      // device [R][T][S]: the same observations in state order, unobserved components 0
+  const float* obs_b;      // device [R][T][S] float2: obs_s with each value twice, (x, x)
   unsigned int obs_mask;   // bit j: state component j is observed
   int R;                   // trajectories (each with its own shooting states)
   int combine;             // R > 1: 0 equally weighted mixture (sum), 1 product

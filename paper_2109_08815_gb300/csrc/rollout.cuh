@@ -59,6 +59,30 @@
 
 namespace pds {
 
+// Lane types.  The step arithmetic is written once for a lane type V: a
+// float (one unit per thread) or a float2 holding the same quantity of two
+// units side by side, whose arithmetic issues as the paired FP32
+// instructions of sm_100 and later (__ffma2_rn, __fmul2_rn, __fadd2_rn).
+// Each component of a paired operation rounds exactly as the scalar one, so
+// both lane types give the same bits for a unit.
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ float vmul(float a, float b) { return a * b; }
+__device__ __forceinline__ float vadd(float a, float b) { return a + b; }
+__device__ __forceinline__ float vsub(float a, float b) { return a - b; }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+// a - b is a + (-b) exactly in IEEE arithmetic
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __fadd2_rn(a, vneg(b)); }
+template <class V>
+__device__ __forceinline__ V vsplat(float x);
+template <>
+__device__ __forceinline__ float vsplat<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float2 vsplat<float2>(float x) { return make_float2(x, x); }
+
 // sin/cos and reciprocal: CUDA's accurate functions, or (FAST) the hardware
 // approximations __sincosf / __fdividef, which the parity tests also cover.
 template <bool FAST>
@@ -67,22 +91,30 @@ __device__ __forceinline__ void sc(float x, float* s, float* c) {
   else sincosf(x, s, c);
 }
 template <bool FAST>
+__device__ __forceinline__ void sc(float2 x, float2* s, float2* c) {
+  sc<FAST>(x.x, &s->x, &c->x);
+  sc<FAST>(x.y, &s->y, &c->y);
+}
+template <bool FAST>
 __device__ __forceinline__ float rcp(float x) {
   return FAST ? __fdividef(1.0f, x) : 1.0f / x;
 }
+template <bool FAST>
+__device__ __forceinline__ float2 rcp(float2 x) {
+  return make_float2(rcp<FAST>(x.x), rcp<FAST>(x.y));
+}
 
 // Per-particle link parameters, with the loop-invariant 1 / l and m g.
-template <int NL>
+template <int NL, class V = float>
 struct Links {
-  float m[NL], l[NL], b[NL];
-  float il[NL], mg[NL];
+  V m[NL], l[NL], b[NL];
+  V il[NL], mg[NL];
 };
 
 // Joint rotations (sin q_i, cos q_i) and absolute-angle (sin, cos) by
 // composing them along the chain.
-template <int NL, bool FAST>
-__device__ __forceinline__ void joint_trig(const float (&q)[NL], float (&sq)[NL], float (&cq)[NL], float (&S)[NL],
-                                           float (&C)[NL]) {
+template <int NL, bool FAST, class V>
+__device__ __forceinline__ void joint_trig(const V (&q)[NL], V (&sq)[NL], V (&cq)[NL], V (&S)[NL], V (&C)[NL]) {
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
     sc<FAST>(q[i], &sq[i], &cq[i]);
@@ -90,68 +122,73 @@ __device__ __forceinline__ void joint_trig(const float (&q)[NL], float (&sq)[NL]
       S[0] = sq[0];
       C[0] = cq[0];
     } else {
-      S[i] = fmaf(S[i - 1], cq[i], C[i - 1] * sq[i]);
-      C[i] = fmaf(C[i - 1], cq[i], -S[i - 1] * sq[i]);
+      S[i] = vfma(S[i - 1], cq[i], vmul(C[i - 1], sq[i]));
+      C[i] = vfma(C[i - 1], cq[i], vmul(vneg(S[i - 1]), sq[i]));
     }
   }
 }
 
 // Forward step in place.
-template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const Links<NL>& P, float dt) {
-  float sq[NL], cq[NL], S[NL], C[NL], o2[NL], w[NL], tau[NL];
+template <int NL, bool FAST, class V>
+__device__ __forceinline__ void chain_step(V (&q)[NL], V (&v)[NL], const Links<NL, V>& P, float dt_) {
+  const V dt = vsplat<V>(dt_);
+  const V zero = vsplat<V>(0.f);
+  V sq[NL], cq[NL], S[NL], C[NL], o2[NL], w[NL], tau[NL];
   joint_trig<NL, FAST>(q, sq, cq, S, C);
   {
-    float om = 0.f;
+    V om = zero;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      om += v[i];
-      o2[i] = om * om;
-      w[i] = o2[i] * P.l[i];
-      tau[i] = -P.b[i] * v[i];
+      om = vadd(om, v[i]);
+      o2[i] = vmul(om, om);
+      w[i] = vmul(o2[i], P.l[i]);
+      tau[i] = vmul(vneg(P.b[i]), v[i]);
     }
   }
-  float f[NL], x[NL];
-  float Bce = 0.f, Bcp = 0.f, kc = 0.f;
+  V f[NL], x[NL];
+  V Bce = zero, Bcp = zero, kc = zero;
 #pragma unroll
   for (int i = NL - 1; i >= 0; --i) {
-    const float dtau = (i + 1 < NL) ? fmaf(-P.b[i], v[i], -tau[i + 1]) : tau[i];
-    float Be = 0.f, Bp = 0.f, h = P.m[i], y = 0.f, z = P.m[i];
+    const V dtau = (i + 1 < NL) ? vfma(vneg(P.b[i]), v[i], vneg(tau[i + 1])) : tau[i];
+    V Be = zero, Bp = zero, h = P.m[i], y = zero, z = P.m[i];
     if (i + 1 < NL) {
-      const float s1 = sq[i + 1], c1 = cq[i + 1];
-      Be = fmaf(Bce, c1, -Bcp * s1);
-      Bp = fmaf(Bce, s1, Bcp * c1);
-      const float ks = kc * s1;
-      h = fmaf(ks, s1, P.m[i]);
-      y = ks * c1;
-      z = fmaf(kc * c1, c1, P.m[i]);
+      const V s1 = sq[i + 1], c1 = cq[i + 1];
+      Be = vfma(Bce, c1, vmul(vneg(Bcp), s1));
+      Bp = vfma(Bce, s1, vmul(Bcp, c1));
+      const V ks = vmul(kc, s1);
+      h = vfma(ks, s1, P.m[i]);
+      y = vmul(ks, c1);
+      z = vfma(vmul(kc, c1), c1, P.m[i]);
     }
-    const float ih = rcp<FAST>(h);
-    const float be = fmaf(-P.mg[i], C[i], fmaf(-w[i], z, Be));
-    const float bp = fmaf(P.mg[i], S[i], fmaf(-w[i], y, Bp));
-    const float ft = fmaf(dtau, P.il[i], -bp) * ih;
+    const V ih = rcp<FAST>(h);
+    const V be = vfma(vneg(P.mg[i]), C[i], vfma(vneg(w[i]), z, Be));
+    const V bp = vfma(P.mg[i], S[i], vfma(vneg(w[i]), y, Bp));
+    const V ft = vmul(vfma(dtau, P.il[i], vneg(bp)), ih);
     f[i] = ft;
-    x[i] = y * ih;
-    Bce = fmaf(ft, y, be);
-    Bcp = dtau * P.il[i];
-    kc = P.m[i] * (P.m[i] + kc) * ih;
+    x[i] = vmul(y, ih);
+    Bce = vfma(ft, y, be);
+    Bcp = vmul(dtau, P.il[i]);
+    kc = vmul(vmul(P.m[i], vadd(P.m[i], kc)), ih);
   }
-  float Ae = 0.f, Ap = 0.f, alp = 0.f;
+  V Ae = zero, Ap = zero, alp = zero;
 #pragma unroll
   for (int i = 0; i < NL; ++i) {
-    float ae = 0.f, ap = 0.f;
+    V ae = zero, ap = zero;
     if (i > 0) {
-      ae = fmaf(cq[i], Ae, sq[i] * Ap);
-      ap = fmaf(cq[i], Ap, -sq[i] * Ae);
+      ae = vfma(cq[i], Ae, vmul(sq[i], Ap));
+      ap = vfma(cq[i], Ap, vmul(vneg(sq[i]), Ae));
     }
-    const float An = fmaf(-x[i], ae, f[i]);
-    const float al = (An - ap) * P.il[i];
-    Ae = fmaf(-o2[i], P.l[i], ae);
+    const V An = vfma(vneg(x[i]), ae, f[i]);
+    const V d = vsub(An, ap);
+    const V al = vmul(d, P.il[i]);
+    Ae = vfma(vneg(o2[i]), P.l[i], ae);
     Ap = An;
-    const float qdd = al - alp;
+    // qdd = al - alp with al's product fused: written out, so that every
+    // lane type rounds it the same way whatever the compiler contracts
+    const V qdd = (i > 0) ? vfma(d, P.il[i], vneg(alp)) : al;
     alp = al;
-    v[i] = fmaf(qdd, dt, v[i]);
-    q[i] = fmaf(v[i], dt, q[i]);
+    v[i] = vfma(qdd, dt, v[i]);
+    q[i] = vfma(v[i], dt, q[i]);
   }
 }
 
@@ -186,93 +223,97 @@ __device__ __forceinline__ void chain_step(float (&q)[NL], float (&v)[NL], const
 // d/domega_j (plus mu_i b_i for v_i); the damping term gives d/db_i = mu_i v_i.
 // qdd is recovered from the taped velocities as (v' - v) / dt: its FP32
 // error, half an ulp of v' over dt, stays far below the gradient tolerance.
-template <int NL, bool FAST>
-__device__ __forceinline__ void chain_step_vjp(const float (&q)[NL], const float (&v)[NL], const float (&v2)[NL],
-                                               const Links<NL>& P, float g, float dt, float idt, float (&qb)[NL],
-                                               float (&vb)[NL], float (&mb)[NL], float (&lb)[NL], float (&bb)[NL]) {
+template <int NL, bool FAST, class V>
+__device__ __forceinline__ void chain_step_vjp(const V (&q)[NL], const V (&v)[NL], const V (&v2)[NL],
+                                               const Links<NL, V>& P, float g_, float dt_, float idt_, V (&qb)[NL],
+                                               V (&vb)[NL], V (&mb)[NL], V (&lb)[NL], V (&bb)[NL]) {
+  const V dt = vsplat<V>(dt_), idt = vsplat<V>(idt_), g = vsplat<V>(g_);
+  const V zero = vsplat<V>(0.f);
   // ---- Euler: vb' += qb dt (qb passes through unchanged); abar = vb' dt
 #pragma unroll
-  for (int i = 0; i < NL; ++i) vb[i] = fmaf(qb[i], dt, vb[i]);
-  float sq[NL], cq[NL], S[NL], C[NL];
+  for (int i = 0; i < NL; ++i) vb[i] = vfma(qb[i], dt, vb[i]);
+  V sq[NL], cq[NL], S[NL], C[NL];
   joint_trig<NL, FAST>(q, sq, cq, S, C);
   // ---- mu = H^-1 abar: inward pass (the articulated inertias k_i) ...
-  float f[NL], x[NL];
+  V f[NL], x[NL];
   {
-    float Bce = 0.f, Bcp = 0.f, kc = 0.f;
+    V Bce = zero, Bcp = zero, kc = zero;
 #pragma unroll
     for (int i = NL - 1; i >= 0; --i) {
-      const float dtau = ((i + 1 < NL) ? vb[i] - vb[i + 1] : vb[i]) * dt;  // abar_i - abar_{i+1}
-      float Be = 0.f, Bp = 0.f, h = P.m[i], y = 0.f;
+      const V dtau = vmul((i + 1 < NL) ? vsub(vb[i], vb[i + 1]) : vb[i], dt);  // abar_i - abar_{i+1}
+      V Be = zero, Bp = zero, h = P.m[i], y = zero;
       if (i + 1 < NL) {
-        const float s1 = sq[i + 1], c1 = cq[i + 1];
-        Be = fmaf(Bce, c1, -Bcp * s1);
-        Bp = fmaf(Bce, s1, Bcp * c1);
-        const float ks = kc * s1;
-        h = fmaf(ks, s1, P.m[i]);
-        y = ks * c1;
+        const V s1 = sq[i + 1], c1 = cq[i + 1];
+        Be = vfma(Bce, c1, vmul(vneg(Bcp), s1));
+        Bp = vfma(Bce, s1, vmul(Bcp, c1));
+        const V ks = vmul(kc, s1);
+        h = vfma(ks, s1, P.m[i]);
+        y = vmul(ks, c1);
       }
-      const float ih = rcp<FAST>(h);
-      const float ft = fmaf(dtau, P.il[i], -Bp) * ih;
+      const V ih = rcp<FAST>(h);
+      const V ft = vmul(vfma(dtau, P.il[i], vneg(Bp)), ih);
       f[i] = ft;
-      x[i] = y * ih;
-      Bce = fmaf(ft, y, Be);
-      Bcp = dtau * P.il[i];
-      kc = P.m[i] * (P.m[i] + kc) * ih;
+      x[i] = vmul(y, ih);
+      Bce = vfma(ft, y, Be);
+      Bcp = vmul(dtau, P.il[i]);
+      kc = vmul(vmul(P.m[i], vadd(P.m[i], kc)), ih);
     }
   }
   // ... outward pass (Lambda = absolute angular accelerations of the
   // solution), with the prefix sums A_k + g y and delta_k
-  float Lam[NL], om[NL], al[NL], Gx[NL], Gy[NL], dx[NL], dy[NL];
+  V Lam[NL], mu[NL], om[NL], al[NL], Gx[NL], Gy[NL], dx[NL], dy[NL];
   {
-    float Ae = 0.f, Ap = 0.f, o = 0.f, a = 0.f, Ax = 0.f, Ay = 0.f, ddx = 0.f, ddy = 0.f;
+    V Ae = zero, Ap = zero, o = zero, a = zero, Ax = zero, Ay = zero, ddx = zero, ddy = zero;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      float ae = 0.f, ap = 0.f;
+      V ae = zero, ap = zero;
       if (i > 0) {
-        ae = fmaf(cq[i], Ae, sq[i] * Ap);
-        ap = fmaf(cq[i], Ap, -sq[i] * Ae);
+        ae = vfma(cq[i], Ae, vmul(sq[i], Ap));
+        ap = vfma(cq[i], Ap, vmul(vneg(sq[i]), Ae));
       }
-      const float An = fmaf(-x[i], ae, f[i]);
-      Lam[i] = (An - ap) * P.il[i];
+      const V An = vfma(vneg(x[i]), ae, f[i]);
+      const V d = vsub(An, ap);
+      Lam[i] = vmul(d, P.il[i]);
+      mu[i] = (i > 0) ? vfma(d, P.il[i], vneg(Lam[i - 1])) : Lam[0];  // mu_i = Lambda_i - Lambda_{i-1}, fused
       Ae = ae;
       Ap = An;
-      o += v[i];
-      a = fmaf(v2[i] - v[i], idt, a);
+      o = vadd(o, v[i]);
+      a = vfma(vsub(v2[i], v[i]), idt, a);
       om[i] = o;
       al[i] = a;
-      const float o2 = o * o;
-      const float ux = fmaf(a, C[i], -o2 * S[i]), uy = fmaf(a, S[i], o2 * C[i]);
-      Ax = fmaf(P.l[i], ux, Ax);
-      Ay = fmaf(P.l[i], uy, Ay);
-      const float ll = P.l[i] * Lam[i];
-      ddx = fmaf(ll, C[i], ddx);
-      ddy = fmaf(ll, S[i], ddy);
+      const V o2 = vmul(o, o);
+      const V ux = vfma(a, C[i], vmul(vneg(o2), S[i])), uy = vfma(a, S[i], vmul(o2, C[i]));
+      Ax = vfma(P.l[i], ux, Ax);
+      Ay = vfma(P.l[i], uy, Ay);
+      const V ll = vmul(P.l[i], Lam[i]);
+      ddx = vfma(ll, C[i], ddx);
+      ddy = vfma(ll, S[i], ddy);
       Gx[i] = Ax;
-      Gy[i] = Ay + g;
+      Gy[i] = vadd(Ay, g);
       dx[i] = ddx;
       dy[i] = ddy;
     }
   }
   // ---- the gradient of -mu^T (ID + b o v), suffix sums from the tip
-  float Fx = 0.f, Fy = 0.f, Dx = 0.f, Dy = 0.f, sphi = 0.f, som = 0.f;
+  const V m2 = vsplat<V>(-2.f);
+  V Fx = zero, Fy = zero, Dx = zero, Dy = zero, sphi = zero, som = zero;
 #pragma unroll
   for (int i = NL - 1; i >= 0; --i) {
-    const float m = P.m[i];
-    Fx = fmaf(m, Gx[i], Fx);
-    Fy = fmaf(m, Gy[i], Fy);
-    Dx = fmaf(m, dx[i], Dx);
-    Dy = fmaf(m, dy[i], Dy);
-    const float eD = fmaf(S[i], Dx, -C[i] * Dy), pD = fmaf(C[i], Dx, S[i] * Dy);
-    const float eF = fmaf(S[i], Fx, -C[i] * Fy), pF = fmaf(C[i], Fx, S[i] * Fy);
-    const float o2 = om[i] * om[i];
-    const float mu = (i > 0) ? Lam[i] - Lam[i - 1] : Lam[0];
-    mb[i] -= fmaf(Gx[i], dx[i], Gy[i] * dy[i]);
-    lb[i] -= fmaf(al[i], pD, fmaf(-o2, eD, Lam[i] * pF));
-    bb[i] = fmaf(-mu, v[i], bb[i]);
-    som = fmaf(-2.f * om[i] * P.l[i], eD, som);
-    sphi = fmaf(P.l[i], fmaf(-al[i], eD, fmaf(-o2, pD, -Lam[i] * eF)), sphi);
-    qb[i] -= sphi;
-    vb[i] -= fmaf(mu, P.b[i], som);
+    const V m = P.m[i];
+    Fx = vfma(m, Gx[i], Fx);
+    Fy = vfma(m, Gy[i], Fy);
+    Dx = vfma(m, dx[i], Dx);
+    Dy = vfma(m, dy[i], Dy);
+    const V eD = vfma(S[i], Dx, vmul(vneg(C[i]), Dy)), pD = vfma(C[i], Dx, vmul(S[i], Dy));
+    const V eF = vfma(S[i], Fx, vmul(vneg(C[i]), Fy)), pF = vfma(C[i], Fx, vmul(S[i], Fy));
+    const V o2 = vmul(om[i], om[i]);
+    mb[i] = vsub(mb[i], vfma(Gx[i], dx[i], vmul(Gy[i], dy[i])));
+    lb[i] = vsub(lb[i], vfma(al[i], pD, vfma(vneg(o2), eD, vmul(Lam[i], pF))));
+    bb[i] = vfma(vneg(mu[i]), v[i], bb[i]);
+    som = vfma(vmul(vmul(m2, om[i]), P.l[i]), eD, som);
+    sphi = vfma(P.l[i], vfma(vneg(al[i]), eD, vfma(vneg(o2), pD, vmul(vneg(Lam[i]), eF))), sphi);
+    qb[i] = vsub(qb[i], sphi);
+    vb[i] = vsub(vb[i], vfma(mu[i], P.b[i], som));
   }
 }
 
@@ -557,6 +598,16 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
   }
   parts.lp[(size_t)wg * N + i] = lp;
   if (!grad) return;
+  {
+    // the defect's gradient in the next shooting state is final here: written
+    // now, it holds no registers through the reverse sweep
+    float* nx = parts.next + (size_t)wg * 2 * NL * N + i;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      nx[(size_t)j * N] = nb[j];
+      nx[(size_t)(NL + j) * N] = nb[NL + j];
+    }
+  }
 
   // ---------------- reverse sweep
   const float idt = 1.0f / c.dt;
@@ -683,14 +734,239 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     for (int j = 0; j < NL; ++j) { qb[j] += qb2[j]; vb[j] += vb2[j]; }
   }
   float* st = parts.start + (size_t)wg * 2 * NL * N + i;
-  float* nx = parts.next + (size_t)wg * 2 * NL * N + i;
 #pragma unroll
   for (int j = 0; j < NL; ++j) {
     st[(size_t)j * N] = qb[j];
     st[(size_t)(NL + j) * N] = vb[j];
-    nx[(size_t)j * N] = nb[j];
-    nx[(size_t)(NL + j) * N] = nb[NL + j];
   }
+}
+
+// Two units per thread: particles i and i + 1 (i even) of one window and
+// trajectory, every quantity held as a float2 (particle i in .x, i + 1 in
+// .y), so that each FP32 operation of both units' steps issues as one paired
+// instruction and the issue slots it frees go to the loads, MUFU and integer
+// work.  The arithmetic of each unit is that of rollout_unit operation for
+// operation, so the results are the same bits.  Taken for K = 1 (every
+// pre-step state on the tape, read back through the shared-memory ring)
+// when every state component is observed, with one adjoint (no constrained
+// SVGD) and an even particle count.
+//   tape: [slot][U / 2][NL] float4, float4 j = components 2j and 2j + 1 of
+//         both units (same bytes per slot as the one-unit layout);
+//   ring: [kRingSlots][NL][rstride] float4 in shared memory, this thread's
+//         column at ring[0];
+//   c.obs_b: each observation twice, [R][T][2 NL] float2 = (x, x), read as
+//         NL float4 per row.
+__device__ __forceinline__ void cp_async16(float4* dst_smem, const float4* src_global) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src_global)
+               : "memory");
+}
+
+template <int NL>
+__device__ __forceinline__ float2 pair_comp(const float2 (&q)[NL], const float2 (&v)[NL], int comp) {
+  return comp < NL ? q[comp] : v[comp - NL];
+}
+
+template <int NL, bool FAST>
+__device__ __forceinline__ void rollout_pair_unit(const ChainParams& c, const float* __restrict__ X, int N,
+                                                  const Partials& parts, int32_t* __restrict__ status, size_t u,
+                                                  float4* ring, int rstride) {
+  using V = float2;
+  const size_t U = (size_t)N * c.W * c.R;
+  const size_t TS = U / 2 * NL;  // float4 per tape slot
+  const int wg = (int)(u / N);
+  const int i = (int)(u - (size_t)wg * N);
+  const int r = wg / c.W, w = wg - r * c.W;
+  const float4* obs4 = reinterpret_cast<const float4*>(c.obs_b) + (size_t)r * c.T * NL;  // row t at (t - 1) NL
+  const int shoot0 = c.M + r * (c.W - 1) * 2 * NL;
+  if (status && wg == 0) *reinterpret_cast<int2*>(status + i) = make_int2(0, 0);
+  auto ld2 = [&](const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); };
+
+  Links<NL, V> P;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    P.m[j] = (c.mass_theta[j] >= 0) ? ld2(X + (size_t)c.mass_theta[j] * N + i) : vsplat<V>(c.mass[j]);
+    P.l[j] = (c.length_theta[j] >= 0) ? ld2(X + (size_t)c.length_theta[j] * N + i) : vsplat<V>(c.length[j]);
+    P.b[j] = (c.damp_theta[j] >= 0) ? ld2(X + (size_t)c.damp_theta[j] * N + i) : vsplat<V>(c.damping[j]);
+    P.il[j] = rcp<FAST>(P.l[j]);
+    P.mg[j] = vmul(P.m[j], vsplat<V>(c.g));
+  }
+  V q[NL], v[NL];
+  if (w == 0) {
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      q[j] = vsplat<V>(c.s0[r * kMaxState + j]);
+      v[j] = vsplat<V>(c.s0[r * kMaxState + NL + j]);
+    }
+  } else {
+    const float* xs = X + (size_t)(shoot0 + (w - 1) * 2 * NL) * N + i;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) { q[j] = ld2(xs + (size_t)j * N); v[j] = ld2(xs + (size_t)(NL + j) * N); }
+  }
+  const int t0 = (int)(((long long)w * c.T) / c.W);
+  const int t1 = (int)(((long long)(w + 1) * c.T) / c.W);
+  const int h = t1 - t0;
+  float4* tape = reinterpret_cast<float4*>(parts.tape) + u / 2 * NL;
+
+  // ---------------- forward
+  V rss = vsplat<V>(0.f);
+  const float4* orow = obs4 + (size_t)t0 * NL;  // row t0 + k + 1
+  for (int k = 0; k < h; ++k, orow += NL) {
+    float4* tp = tape + (size_t)k * TS;
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const V a = pair_comp<NL>(q, v, 2 * j), b = pair_comp<NL>(q, v, 2 * j + 1);
+      tp[j] = make_float4(a.x, a.y, b.x, b.y);
+    }
+    chain_step<NL, FAST>(q, v, P, c.dt);
+    V acc = vsplat<V>(0.f);
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      const float4 o = __ldg(orow + j);
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const V ov = e ? make_float2(o.z, o.w) : make_float2(o.x, o.y);
+        const V rr = vsub(ov, pair_comp<NL>(q, v, 2 * j + e));
+        acc = vfma(rr, rr, acc);
+      }
+    }
+    rss = vadd(rss, acc);
+  }
+  V lp = vfma(vsplat<V>(-0.5f * c.inv_so2), rss, vsplat<V>((float)h * c.obs_const));
+
+  // defect term against the next window's shooting state
+  V nb[2 * NL], qb[NL], vb[NL];
+  const V isd2 = vsplat<V>(c.inv_sd2);
+#pragma unroll
+  for (int j = 0; j < NL; ++j) { qb[j] = vsplat<V>(0.f); vb[j] = vsplat<V>(0.f); }
+  if (w < c.W - 1) {
+    const float* xs = X + (size_t)(shoot0 + w * 2 * NL) * N + i;
+    V dss = vsplat<V>(0.f);
+    V dd[2 * NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      dd[j] = vsub(ld2(xs + (size_t)j * N), q[j]);
+      dd[NL + j] = vsub(ld2(xs + (size_t)(NL + j) * N), v[j]);
+      dss = vfma(dd[j], dd[j], dss);
+      dss = vfma(dd[NL + j], dd[NL + j], dss);
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+      qb[j] = vmul(dd[j], isd2);
+      vb[j] = vmul(dd[NL + j], isd2);
+      nb[j] = vmul(vneg(dd[j]), isd2);
+      nb[NL + j] = vmul(vneg(dd[NL + j]), isd2);
+    }
+    lp = vadd(lp, vfma(vsplat<V>(-0.5f * c.inv_sd2), dss, vsplat<V>(c.def_const)));
+  } else {
+#pragma unroll
+    for (int j = 0; j < 2 * NL; ++j) nb[j] = vsplat<V>(0.f);
+  }
+  *reinterpret_cast<float2*>(parts.lp + (size_t)wg * N + i) = lp;
+  {
+    float* nx = parts.next + (size_t)wg * 2 * NL * N + i;
+#pragma unroll
+    for (int j = 0; j < 2 * NL; ++j) *reinterpret_cast<float2*>(nx + (size_t)j * N) = nb[j];
+  }
+
+  // ---------------- reverse sweep: state k from the ring, kRingAhead steps ahead
+  const float idt = 1.0f / c.dt;
+  const V iso2 = vsplat<V>(c.inv_so2);
+  V mb[NL], lb[NL], bb[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) { mb[j] = vsplat<V>(0.f); lb[j] = vsplat<V>(0.f); bb[j] = vsplat<V>(0.f); }
+  V qh[NL], vh[NL];  // state s_{k+1}
+#pragma unroll
+  for (int j = 0; j < NL; ++j) { qh[j] = q[j]; vh[j] = v[j]; }
+  constexpr int RS = kRingSlots;
+  auto fetch = [&](int k, int rs) {
+    if (k >= 0) {
+      const float4* src = tape + (size_t)k * TS;
+      float4* dst = ring + (size_t)rs * NL * rstride;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) cp_async16(dst + (size_t)j * rstride, src + j);
+    }
+    cp_async_commit();
+  };
+  const float4* orev = obs4 + (size_t)t0 * NL;  // row t0 + k + 1 at orev + k NL
+  float4 onx[NL];
+#pragma unroll
+  for (int j = 0; j < NL; ++j) onx[j] = __ldg(orev + (size_t)(h - 1) * NL + j);
+  int rs = (h - 1) % RS;
+  {
+    int r2 = rs;
+#pragma unroll
+    for (int a = 1; a <= kRingAhead; ++a) {
+      fetch(h - a, r2);
+      r2 = r2 == 0 ? RS - 1 : r2 - 1;
+    }
+  }
+#pragma unroll 1
+  for (int k = h - 1; k >= 0; --k) {
+    fetch(k - kRingAhead, rs == RS - 1 ? 0 : rs + 1);
+    cp_async_wait<kRingAhead>();
+    V qs[NL], vs[NL];
+    {
+      const float4* sl = ring + (size_t)rs * NL * rstride;
+#pragma unroll
+      for (int j = 0; j < NL; ++j) {
+        const float4 x = sl[(size_t)j * rstride];
+        const V a = make_float2(x.x, x.y), b = make_float2(x.z, x.w);
+        if (2 * j < NL) qs[2 * j] = a; else vs[2 * j - NL] = a;
+        if (2 * j + 1 < NL) qs[2 * j + 1] = b; else vs[2 * j + 1 - NL] = b;
+      }
+    }
+    rs = rs == 0 ? RS - 1 : rs - 1;
+    float4 ocur[NL];
+#pragma unroll
+    for (int j = 0; j < NL; ++j) ocur[j] = onx[j];
+    if (k > 0) {
+#pragma unroll
+      for (int j = 0; j < NL; ++j) onx[j] = __ldg(orev + (size_t)(k - 1) * NL + j);
+    }
+#pragma unroll
+    for (int j = 0; j < NL; ++j) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int comp = 2 * j + e;
+        const V ov = e ? make_float2(ocur[j].z, ocur[j].w) : make_float2(ocur[j].x, ocur[j].y);
+        if (comp < NL) qb[comp] = vfma(vsub(ov, qh[comp]), iso2, qb[comp]);
+        else vb[comp - NL] = vfma(vsub(ov, vh[comp - NL]), iso2, vb[comp - NL]);
+      }
+    }
+    chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+#pragma unroll
+    for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
+  }
+
+  // ---------------- write partial gradients
+  auto st2 = [&](float* p, V x) { *reinterpret_cast<float2*>(p) = x; };
+  float* th = parts.th + (size_t)wg * c.M * N + i;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    if (c.mass_theta[j] >= 0) st2(th + (size_t)c.mass_theta[j] * N, mb[j]);
+    if (c.length_theta[j] >= 0) st2(th + (size_t)c.length_theta[j] * N, lb[j]);
+    if (c.damp_theta[j] >= 0) st2(th + (size_t)c.damp_theta[j] * N, bb[j]);
+  }
+  float* st = parts.start + (size_t)wg * 2 * NL * N + i;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) {
+    st2(st + (size_t)j * N, qb[j]);
+    st2(st + (size_t)(NL + j) * N, vb[j]);
+  }
+}
+
+// Units [u0, u1) (both even), two per thread.
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, 2) rollout_pair_kernel(const ChainParams c,
+                                                                          const float* __restrict__ X, int N,
+                                                                          Partials parts,
+                                                                          int32_t* __restrict__ status, size_t u0,
+                                                                          size_t u1) {
+  extern __shared__ float4 ring4_sh[];
+  const size_t u = u0 + 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (u >= u1) return;
+  rollout_pair_unit<NL, FAST>(c, X, N, parts, status, u, ring4_sh + threadIdx.x, blockDim.x);
 }
 
 // seg_smem: the reverse sweep's recomputed segment states live in dynamic
@@ -830,6 +1106,22 @@ __global__ void __launch_bounds__(128) simulate_kernel(const ChainParams c, cons
   }
 }
 
+// The two-units-per-thread kernel can take a gradient launch with K = 1,
+// every state component observed, one adjoint, an even particle count and an
+// even unit range, when its ring fits in 48 KB of shared memory.  It then
+// runs when c.units_per_thread asks for it (2), or by default (0) for the
+// chain lengths where it measured faster on GB300 (2, 4 and 5 links: its 254
+// registers leave 8 warps per SM, against 12 for the one-unit kernel, and
+// longer chains spill).
+template <int NL>
+bool pair_path_applies(const ChainParams& c, int N, size_t u0, size_t nu) {
+  constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
+  const bool can = c.K == 1 && !c.csvgd && (c.obs_mask & kAll) == kAll && c.obs_b != nullptr && N % 2 == 0 &&
+                   u0 % 2 == 0 && nu % 2 == 0 && (size_t)kRingSlots * NL * 128 * sizeof(float4) <= 48 * 1024;
+  if (!can || c.units_per_thread == 1) return false;
+  return c.units_per_thread == 2 || NL == 2 || NL == 4 || NL == 5;
+}
+
 // nu = 0: all units; otherwise units [u0, u0 + nu) of the gradient kernel.
 template <int NL>
 cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const Partials& parts, int grad,
@@ -867,6 +1159,13 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
       rollout_fwd_kernel<NL, false, true><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
     else
       rollout_fwd_kernel<NL, false, false><<<blocks, 128, 0, st>>>(c, X, N, parts, status);
+  } else if (pair_path_applies<NL>(c, N, u0, nu)) {
+    const size_t rsmem = (size_t)kRingSlots * NL * 128 * sizeof(float4);
+    const unsigned pblocks = (unsigned)((nu / 2 + 127) / 128);
+    if (c.fast_math)
+      rollout_pair_kernel<NL, true><<<pblocks, 128, rsmem, st>>>(c, X, N, parts, status, u0, u1);
+    else
+      rollout_pair_kernel<NL, false><<<pblocks, 128, rsmem, st>>>(c, X, N, parts, status, u0, u1);
   } else {
     // the same residual form as the batched kernel takes for the problem
     if (c.fast_math && every)
