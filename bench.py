@@ -387,7 +387,7 @@ def run_pds(args):
     achieved = flops_launch / lg_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                "kernel": "rollout_kernel<5> (+ window_reduce, <1%)",
+                "kernel": "rollout_pair_kernel<5> (two particles per thread; + window_reduce, 3%)",
                 "peak_basis": f"FP32 {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max_mhz:.0f} MHz "
                               "(MEASURED_PEAKS sm_max_mhz)",
                 "flops_per_particle_step": fwd + rev,
@@ -814,7 +814,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
 
 # dram bytes (read + write) per full-size rollout launch, from the committed
 # ncu capture of this kernel (set to None when the kernel changes)
-TRAFFIC_BYTES_PER_LAUNCH = 272974592 + 649377024
+TRAFFIC_BYTES_PER_LAUNCH = 368196608 + 659459072
 
 
 def main():
