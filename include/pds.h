@@ -203,6 +203,20 @@ int pds_problem_set_checkpoint_stride(pds_problem_t p, int K);
 int pds_problem_set_option(pds_problem_t p, int option, int value);
 int pds_problem_get_option(pds_problem_t p, int option, int* value);
 
+/* Autotuner of the likelihood launch (the paper picks no launch shapes;
+ * this is the library's own): times pds_loglik_grad on `particles` (device,
+ * [P][N], the caller's; read only) for the candidates K = 1 with one and
+ * two units per thread (PDS_OPT_UNITS_PER_THREAD) and K = 5, 10, 25, 50
+ * with one, three calls each after a warm-up call, in the problem's math
+ * mode, and keeps the fastest: the problem's K and units per thread are set
+ * to it.  choice (host, 3 ints, may be NULL) receives units per thread, K
+ * and the chosen configuration's time per call in microseconds.  Blocks the
+ * calling thread until the timings are done.  Every candidate gives the
+ * same log p and gradient up to the rounding that K changes (K = 1 with one
+ * or two units per thread: the same bits).  Planar chains only
+ * (PDS_ERR_UNSUPPORTED otherwise); the options are left unchanged on error. */
+int pds_problem_autotune(pds_problem_t p, const float* particles, int N, int* choice);
+
 /* Constrained SVGD (Sec. IV-E, Eq. mdmm-loss, Algorithm 1).  With enable = 1
  * the likelihood is the observation term only, and the defect terms and the
  * parameter limits become equality constraints.  Each particle carries

@@ -98,6 +98,7 @@ EXPORTS = {
     "pds_mmd2": ([_vp, ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                   ctypes.POINTER(ctypes.c_double), _vp], ctypes.c_int),
     "pds_problem_get_option": ([_vp, ctypes.c_int, _ip], ctypes.c_int),
+    "pds_problem_autotune": ([_vp, _vp, ctypes.c_int, _ip], ctypes.c_int),
     "pds_loglik_grad": ([_vp, _vp, ctypes.c_int, _vp, _vp, _vp], ctypes.c_int),
     "pds_simulate": ([_vp, _vp, ctypes.c_int, _vp], ctypes.c_int),
     "pds_svgd_create": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, ctypes.c_double, ctypes.c_double,
@@ -353,6 +354,13 @@ class Problem:
         v = ctypes.c_int()
         _check(lib().pds_problem_get_option(self._h, int(option), ctypes.byref(v)), "pds_problem_get_option")
         return v.value
+
+    def autotune(self, X) -> dict:
+        """pds_problem_autotune on device particles X [P][N]: sets the fastest
+        (units per thread, K) and returns it with its time per call."""
+        ch = (ctypes.c_int * 3)()
+        _check(lib().pds_problem_autotune(self._h, _ptr(X), int(X.shape[1]), ch), "pds_problem_autotune")
+        return {"units_per_thread": ch[0], "K": ch[1], "us_per_call": ch[2]}
 
     def set_csvgd(self, enable: bool = True, c: float = 1.0):
         """Constrained SVGD (pds_problem_set_csvgd): observation likelihood,

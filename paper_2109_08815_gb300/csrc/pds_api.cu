@@ -352,6 +352,68 @@ int pds_problem_get_option(pds_problem_t p, int option, int* value) {
   }
 }
 
+int pds_problem_autotune(pds_problem_t p, const float* particles, int N, int* choice) {
+  g_launches = 0;
+  if (!p || !particles) return fail(PDS_ERR_ARG, "NULL argument");
+  if (N < 1 || N > (1 << 20)) return fail(PDS_ERR_ARG, "N %d outside 1..2^20", N);
+  if (p->kind != PDS_SYSTEM_PLANAR_CHAIN) return fail(PDS_ERR_UNSUPPORTED, "the autotuner is built for planar chains");
+  int rc = ensure_iter_buffers(p, N);
+  if (rc != PDS_OK) return rc;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if ((e = cudaEventCreate(&t0)) != cudaSuccess || (e = cudaEventCreate(&t1)) != cudaSuccess) {
+    if (t0) cudaEventDestroy(t0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  const int K0 = p->c.K, U0 = p->c.units_per_thread;
+  // candidates: K = 1 with one or two units per thread, then larger strides
+  // (one unit); each timed over 3 calls after one that warms up
+  const int cand[][2] = {{1, 1}, {1, 2}, {5, 1}, {10, 1}, {25, 1}, {50, 1}};
+  int best_K = K0, best_U = U0;
+  float best = 1e30f;
+  for (const auto& kc : cand) {
+    if (kc[0] > PDS_MAX_WINDOW_STEPS) continue;
+    p->c.K = kc[0];
+    p->c.units_per_thread = kc[1];
+    update_segments(p->c);
+    float tot = 0.f;
+    for (int r = 0; r < 4 && rc == PDS_OK; ++r) {
+      if ((e = cudaEventRecord(t0, p->stream)) != cudaSuccess) break;
+      rc = pds_loglik_grad(p, particles, N, p->d_logp, p->d_grad, nullptr);
+      if (rc != PDS_OK) break;
+      if ((e = cudaEventRecord(t1, p->stream)) != cudaSuccess || (e = cudaEventSynchronize(t1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, t0, t1);
+      if (r > 0) tot += ms;
+    }
+    if (rc != PDS_OK || e != cudaSuccess) break;
+    if (tot < best) {
+      best = tot;
+      best_K = kc[0];
+      best_U = kc[1];
+    }
+  }
+  cudaEventDestroy(t0);
+  cudaEventDestroy(t1);
+  if (rc == PDS_OK && e != cudaSuccess) rc = cuda_fail(e, "autotune timing");
+  if (rc != PDS_OK) {
+    p->c.K = K0;
+    p->c.units_per_thread = U0;
+    update_segments(p->c);
+    return rc;
+  }
+  p->c.K = best_K;
+  p->c.units_per_thread = best_U;
+  update_segments(p->c);
+  if (choice) {
+    choice[0] = best_U;
+    choice[1] = best_K;
+    choice[2] = (int)(best / 3.f * 1000.f);  // microseconds per call
+  }
+  return PDS_OK;
+}
+
 int pds_problem_set_csvgd(pds_problem_t p, int enable, double c) {
   if (!p) return fail(PDS_ERR_ARG, "NULL problem");
   if (enable != 0 && enable != 1) return fail(PDS_ERR_ARG, "enable must be 0 or 1");

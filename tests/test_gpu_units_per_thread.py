@@ -107,3 +107,28 @@ def test_units_per_thread_option_range():
         with pytest.raises(api.PdsError):
             prob.set_option(api.OPT_UNITS_PER_THREAD, bad)
     prob.close()
+
+
+def test_autotuner_keeps_the_fastest_valid_choice():
+    """pds_problem_autotune times the candidate launches, sets the fastest
+    (units per thread, K), and the likelihood it then computes still matches
+    the FP64 oracle."""
+    wl = f32_workload(wlmod.random_chain(5, 256, seed=315, T=100, W=4))
+    obs = observations(wl)
+    x = particles(wl, obs)
+    prob = api.Problem.from_workload(wl, obs, fast_math=1)
+    X = _gpu(x)
+    ch = prob.autotune(X)
+    assert ch["units_per_thread"] in (1, 2)
+    assert ch["K"] in (1, 5, 10, 25, 50)
+    assert ch["K"] == 1 or ch["units_per_thread"] == 1
+    assert ch["us_per_call"] > 0
+    assert prob.get_option(api.OPT_UNITS_PER_THREAD) == ch["units_per_thread"]
+    assert prob.get_option(api.OPT_CHECKPOINT_STRIDE) == ch["K"]
+    lp, g, st = prob.loglik_grad(X)
+    torch.cuda.synchronize()
+    lp_ref, g_ref = oracle_problem(wl, obs).loglik_grad(x.astype(np.float32).astype(np.float64))
+    assert np.all(st.cpu().numpy() == 0)
+    assert_logp_close(lp.cpu().numpy().astype(np.float64), lp_ref)
+    assert_grad_close(g.cpu().numpy().T.astype(np.float64), g_ref, wl.M)
+    prob.close()
