@@ -520,7 +520,8 @@ def run_batched(api, dev, stream, n_jobs=64, iters=10):
             "particle_steps_per_iter": units, "value": units / t_b, "unit": UNIT, "ms_per_iter": t_b * 1e3,
             "plain_value": units / t_p, "plain_ms_per_iter": t_p * 1e3, "speedup_vs_plain": t_p / t_b,
             "chain_length_groups": ng, "launches_per_iter_in_graph": lpi,
-            "autotune": [{"links": c[0], "K": c[1], "fast_math": c[2], "grid_blocks": c[3]} for c in choices],
+            "autotune": [{"links": c[0], "K": c[1], "fast_math": c[2], "grid_blocks": c[3], "units_per_thread": c[4]}
+                         for c in choices],
             "autotune_s": t_tune}
 
 

@@ -421,9 +421,14 @@ int pds_batch_destroy(pds_batch_t b);
 
 /* Autotuner: for every chain length present, time the batched rollout for
  * checkpoint strides K in {1, 5, 10, 25, 50}, exact or (allow_fast_math) fast
- * math, and the two largest persistent grid sizes, and keep the fastest.
- * choices: NULL or [4 * number of chain lengths] ints receiving
- * (links, K, fast_math, grid blocks) per chain length.  Synchronises. */
+ * math, one or (K = 1, where every problem of that chain length observes
+ * every state component and has an even particle count) two particles per
+ * thread as PDS_OPT_UNITS_PER_THREAD describes, and the two largest
+ * persistent grid sizes, and keep the fastest.  choices: NULL or
+ * [5 * number of chain lengths] ints receiving (links, K, fast_math, grid
+ * blocks, units per thread) per chain length.  Synchronises.  Before any
+ * autotuning a chain length runs with the first problem's K, fast math and
+ * units per thread. */
 int pds_batch_autotune(pds_batch_t b, int allow_fast_math, int* choices);
 
 /* Run `iters` iterations of every problem (graph replays; asynchronous). */

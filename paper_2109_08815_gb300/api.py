@@ -613,12 +613,12 @@ class Batch:
             pass
 
     def autotune(self, allow_fast_math=True):
-        """Returns [(links, K, fast_math, grid_blocks)] per chain length."""
+        """Returns [(links, K, fast_math, grid_blocks, units_per_thread)] per chain length."""
         ng, _ = self.info()
-        ch = (ctypes.c_int * (4 * max(ng, 1)))()
+        ch = (ctypes.c_int * (5 * max(ng, 1)))()
         _check(lib().pds_batch_autotune(self._h, int(bool(allow_fast_math)), ch), "pds_batch_autotune")
         ng, _ = self.info()
-        return [tuple(ch[4 * g:4 * g + 4]) for g in range(ng)]
+        return [tuple(ch[5 * g:5 * g + 5]) for g in range(ng)]
 
     def iterate(self, iters=1):
         _check(lib().pds_batch_iterate(self._h, int(iters)), "pds_batch_iterate")

@@ -17,30 +17,31 @@
 namespace pds {
 
 cudaError_t launch_batch_rollout(int NL, const BatchJob* jobs, const WorkItem* items, int n_items,
-                                 unsigned int* counter, int grad, int fast, int blocks, int ring, cudaStream_t st) {
+                                 unsigned int* counter, int grad, int fast, int blocks, int ring, int upt,
+                                 cudaStream_t st) {
   switch (NL) {
-    case 1: return launch_batch_rollout_nl<1>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 2: return launch_batch_rollout_nl<2>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 3: return launch_batch_rollout_nl<3>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 4: return launch_batch_rollout_nl<4>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 5: return launch_batch_rollout_nl<5>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 6: return launch_batch_rollout_nl<6>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 7: return launch_batch_rollout_nl<7>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
-    case 8: return launch_batch_rollout_nl<8>(jobs, items, n_items, counter, grad, fast, blocks, ring, st);
+    case 1: return launch_batch_rollout_nl<1>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 2: return launch_batch_rollout_nl<2>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 3: return launch_batch_rollout_nl<3>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 4: return launch_batch_rollout_nl<4>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 5: return launch_batch_rollout_nl<5>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 6: return launch_batch_rollout_nl<6>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 7: return launch_batch_rollout_nl<7>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
+    case 8: return launch_batch_rollout_nl<8>(jobs, items, n_items, counter, grad, fast, blocks, ring, upt, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-static int blocks_per_sm(int NL, int fast) {
+static int blocks_per_sm(int NL, int fast, int upt) {
   switch (NL) {
-    case 1: return batch_rollout_blocks_per_sm_nl<1>(fast);
-    case 2: return batch_rollout_blocks_per_sm_nl<2>(fast);
-    case 3: return batch_rollout_blocks_per_sm_nl<3>(fast);
-    case 4: return batch_rollout_blocks_per_sm_nl<4>(fast);
-    case 5: return batch_rollout_blocks_per_sm_nl<5>(fast);
-    case 6: return batch_rollout_blocks_per_sm_nl<6>(fast);
-    case 7: return batch_rollout_blocks_per_sm_nl<7>(fast);
-    case 8: return batch_rollout_blocks_per_sm_nl<8>(fast);
+    case 1: return batch_rollout_blocks_per_sm_nl<1>(fast, upt);
+    case 2: return batch_rollout_blocks_per_sm_nl<2>(fast, upt);
+    case 3: return batch_rollout_blocks_per_sm_nl<3>(fast, upt);
+    case 4: return batch_rollout_blocks_per_sm_nl<4>(fast, upt);
+    case 5: return batch_rollout_blocks_per_sm_nl<5>(fast, upt);
+    case 6: return batch_rollout_blocks_per_sm_nl<6>(fast, upt);
+    case 7: return batch_rollout_blocks_per_sm_nl<7>(fast, upt);
+    case 8: return batch_rollout_blocks_per_sm_nl<8>(fast, upt);
     default: return 1;
   }
 }
@@ -50,6 +51,8 @@ struct Group {
   int NL = 0;
   std::vector<int> jobs;          // indices into the batch
   int K = 10, fast = 0, blocks = 0;
+  int upt = 0;                    // rollout units per thread: 1, 2, or 0 = by chain length (2, 4, 5 links: two)
+  bool pair = false;              // the built tables are for two units per thread
   BatchJob* d_jobs = nullptr;
   WorkItem* d_items = nullptr;
   int n_items = 0;
@@ -108,6 +111,18 @@ static void drop_graph(pds_batch* b) {
 // (Re)build a group's device job table and cost-ordered work list.
 static int build_group(pds_batch* b, Group& g) {
   free_group(g);
+  // two units per thread: asked for (or by default for the chain lengths
+  // where the single-problem kernel measured faster) and possible for every
+  // problem of the group (K = 1, every state component observed, even N)
+  bool pair = g.upt == 2 || (g.upt == 0 && (g.NL == 2 || g.NL == 4 || g.NL == 5));
+  pair = pair && g.K == 1;
+  for (size_t a = 0; a < g.jobs.size() && pair; ++a) {
+    const pds_problem* p = b->probs[g.jobs[a]];
+    const unsigned int all = (1u << (2 * g.NL)) - 1u;
+    pair = (p->c.obs_mask & all) == all && p->c.obs_b != nullptr && !p->c.csvgd &&
+           b->svgds[g.jobs[a]]->sp.N % 2 == 0;
+  }
+  const int span = pair ? 256 : 128;  // units per work item
   std::vector<BatchJob> jobs;
   struct Item { WorkItem w; int cost; };
   std::vector<Item> items;
@@ -136,8 +151,8 @@ static int build_group(pds_batch* b, Group& g) {
     bj.status = nullptr;
     jobs.push_back(bj);
     const long long U = (long long)N * p->c.W;
-    for (long long u0 = 0; u0 < U; u0 += 128) {
-      const long long u1 = std::min(U, u0 + 128) - 1;
+    for (long long u0 = 0; u0 < U; u0 += span) {
+      const long long u1 = std::min(U, u0 + span) - 1;
       int cost = 0;
       for (long long w = u0 / N; w <= u1 / N; ++w) {
         const int h = (int)(((w + 1) * p->c.T) / p->c.W - (w * p->c.T) / p->c.W);
@@ -162,7 +177,8 @@ static int build_group(pds_batch* b, Group& g) {
       (w.size() && (e = cudaMemcpy(g.d_items, w.data(), w.size() * sizeof(WorkItem), cudaMemcpyHostToDevice)) !=
                        cudaSuccess))
     return set_error(PDS_ERR_CUDA, "batch table upload failed");
-  if (g.blocks <= 0) g.blocks = b->sm_count * std::max(1, blocks_per_sm(g.NL, g.fast));
+  g.pair = pair;
+  if (g.blocks <= 0) g.blocks = b->sm_count * std::max(1, blocks_per_sm(g.NL, g.fast, pair ? 2 : 1));
   return PDS_OK;
 }
 
@@ -170,7 +186,7 @@ static cudaError_t launch_group_rollout(Group& g, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(g.d_counter, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return e;
   return launch_batch_rollout(g.NL, g.d_jobs, g.d_items, g.n_items, g.d_counter, 1, g.fast, g.blocks, g.K == 1 ? 1 : 0,
-                              st);
+                              g.pair ? 2 : 1, st);
 }
 
 // One iteration of every problem: the chain-length groups' rollouts on
@@ -320,6 +336,7 @@ int pds_batch_create(int n_jobs, pds_problem_t const* problems, pds_svgd_t const
     if (!g.jobs.empty()) {
       g.K = b->probs[g.jobs[0]]->c.K;
       g.fast = b->probs[g.jobs[0]]->c.fast_math;
+      g.upt = b->probs[g.jobs[0]]->c.units_per_thread;
       b->groups.push_back(g);
     }
   }
@@ -380,44 +397,54 @@ int pds_batch_autotune(pds_batch_t b, int allow_fast_math, int* choices) {
   const int Ks[] = {1, 5, 10, 25, 50};
   int gi = 0;
   for (Group& g : b->groups) {
-    int best_K = g.K, best_fast = g.fast, best_blocks = 0;
+    int best_K = g.K, best_fast = g.fast, best_blocks = 0, best_upt = 1;
     float best = 1e30f;
     for (int fast = 0; fast <= (allow_fast_math ? 1 : 0); ++fast) {
-      const int occ = std::max(1, blocks_per_sm(g.NL, fast));
       for (int K : Ks) {
-        for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
+        // K = 1 also with two units per thread (taken only where every
+        // problem of the group allows it)
+        for (int upt = 1; upt <= (K == 1 ? 2 : 1); ++upt) {
           g.K = K;
           g.fast = fast;
-          g.blocks = b->sm_count * per_sm;
+          g.upt = upt;
+          g.blocks = 0;
           int rc = build_group(b, g);
           if (rc != PDS_OK) return rc;
-          float ms = 0.f, tot = 0.f;
-          for (int r = 0; r < 4; ++r) {
-            cudaEventRecord(t0, b->stream);
-            if (launch_group_rollout(g, b->stream) != cudaSuccess)
-              return set_error(PDS_ERR_CUDA, "autotune launch failed");
-            cudaEventRecord(t1, b->stream);
-            cudaEventSynchronize(t1);
-            cudaEventElapsedTime(&ms, t0, t1);
-            if (r > 0) tot += ms;  // the first run warms up
-          }
-          if (tot < best) {
-            best = tot;
-            best_K = K;
-            best_fast = fast;
-            best_blocks = g.blocks;
+          if (upt == 2 && !g.pair) continue;
+          const int occ = std::max(1, blocks_per_sm(g.NL, fast, upt));
+          for (int per_sm = occ; per_sm >= std::max(1, occ - 1); --per_sm) {
+            g.blocks = b->sm_count * per_sm;
+            float ms = 0.f, tot = 0.f;
+            for (int r = 0; r < 4; ++r) {
+              cudaEventRecord(t0, b->stream);
+              if (launch_group_rollout(g, b->stream) != cudaSuccess)
+                return set_error(PDS_ERR_CUDA, "autotune launch failed");
+              cudaEventRecord(t1, b->stream);
+              cudaEventSynchronize(t1);
+              cudaEventElapsedTime(&ms, t0, t1);
+              if (r > 0) tot += ms;  // the first run warms up
+            }
+            if (tot < best) {
+              best = tot;
+              best_K = K;
+              best_fast = fast;
+              best_blocks = g.blocks;
+              best_upt = upt;
+            }
           }
         }
       }
     }
     g.K = best_K;
     g.fast = best_fast;
+    g.upt = best_upt;
     g.blocks = best_blocks;
     if (choices) {
-      choices[4 * gi + 0] = g.NL;
-      choices[4 * gi + 1] = g.K;
-      choices[4 * gi + 2] = g.fast;
-      choices[4 * gi + 3] = g.blocks;
+      choices[5 * gi + 0] = g.NL;
+      choices[5 * gi + 1] = g.K;
+      choices[5 * gi + 2] = g.fast;
+      choices[5 * gi + 3] = g.blocks;
+      choices[5 * gi + 4] = g.upt;
     }
     ++gi;
   }

@@ -266,8 +266,8 @@ namespace pds {
 int ensure_workspace(pds_problem* p, int N);
 int ensure_iter_buffers(pds_problem* p, int N);
 template <int NL>
-cudaError_t launch_batch_rollout_nl(const BatchJob*, const WorkItem*, int, unsigned int*, int, int, int, int,
+cudaError_t launch_batch_rollout_nl(const BatchJob*, const WorkItem*, int, unsigned int*, int, int, int, int, int,
                                     cudaStream_t);
 template <int NL>
-int batch_rollout_blocks_per_sm_nl(int fast);
+int batch_rollout_blocks_per_sm_nl(int fast, int upt);
 }  // namespace pds

@@ -1065,10 +1065,52 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) batch_rollout_ker
   }
 }
 
+// The persistent batched launch with two units per thread (the two-unit
+// step of rollout_pair_unit): a work item is 256 consecutive units of one
+// problem, whose particle count is even, every state component observed,
+// K = 1.  The batch sets it up only for groups whose problems all qualify.
+template <int NL, bool FAST>
+__global__ void __launch_bounds__(128, 2) batch_rollout_pair_kernel(const BatchJob* __restrict__ jobs,
+                                                                   const WorkItem* __restrict__ items, int n_items,
+                                                                   unsigned int* __restrict__ counter) {
+  extern __shared__ float4 pring_sh[];
+  __shared__ ChainParams cs;
+  __shared__ int item;
+  constexpr int kWords = sizeof(ChainParams) / sizeof(int);
+  for (;;) {
+    if (threadIdx.x == 0) item = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    const int it = item;
+    if (it >= n_items) break;
+    const WorkItem wi = items[it];
+    const BatchJob* job = jobs + wi.job;
+    const int* src = reinterpret_cast<const int*>(&job->c);
+    int* dst = reinterpret_cast<int*>(&cs);
+    for (int k = threadIdx.x; k < kWords; k += blockDim.x) dst[k] = src[k];
+    __syncthreads();
+    const size_t u = (size_t)wi.unit0 + 2 * (size_t)threadIdx.x;
+    const int N = job->N;
+    if (u < (size_t)N * cs.W * cs.R)
+      rollout_pair_unit<NL, FAST>(cs, job->X, N, job->parts, job->status, u, pring_sh + threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+}
+
 template <int NL>
-int batch_rollout_blocks_per_sm_nl(int fast) {
+int batch_rollout_blocks_per_sm_nl(int fast, int upt) {
   int nb = 0;
-  if (fast)
+  const size_t psmem = (size_t)kRingSlots * NL * 128 * sizeof(float4);
+  if (upt == 2) {
+    if (fast)
+      cudaFuncSetAttribute(batch_rollout_pair_kernel<NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+    else
+      cudaFuncSetAttribute(batch_rollout_pair_kernel<NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  }
+  if (upt == 2 && fast)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_pair_kernel<NL, true>, 128, psmem);
+  else if (upt == 2)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_pair_kernel<NL, false>, 128, psmem);
+  else if (fast)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_kernel<NL, true>, 128, 0);
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_rollout_kernel<NL, false>, 128, 0);
@@ -1077,7 +1119,23 @@ int batch_rollout_blocks_per_sm_nl(int fast) {
 
 template <int NL>
 cudaError_t launch_batch_rollout_nl(const BatchJob* jobs, const WorkItem* items, int n_items, unsigned int* counter,
-                                    int grad, int fast, int blocks, int ring, cudaStream_t st) {
+                                    int grad, int fast, int blocks, int ring, int upt, cudaStream_t st) {
+  if (upt == 2) {
+    if (!grad || !ring) return cudaErrorInvalidValue;
+    const size_t psmem = (size_t)kRingSlots * NL * 128 * sizeof(float4);
+    // with the staged ChainParams the block can pass 48 KB: opt in (per device)
+    const cudaError_t e =
+        fast ? cudaFuncSetAttribute(batch_rollout_pair_kernel<NL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)psmem)
+             : cudaFuncSetAttribute(batch_rollout_pair_kernel<NL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)psmem);
+    if (e != cudaSuccess) return e;
+    if (fast)
+      batch_rollout_pair_kernel<NL, true><<<blocks, 128, psmem, st>>>(jobs, items, n_items, counter);
+    else
+      batch_rollout_pair_kernel<NL, false><<<blocks, 128, psmem, st>>>(jobs, items, n_items, counter);
+    return cudaGetLastError();
+  }
   const size_t smem = ring ? (size_t)kRingSlots * 2 * NL * 128 * sizeof(float) : 0;
   if (fast)
     batch_rollout_kernel<NL, true><<<blocks, 128, smem, st>>>(jobs, items, n_items, counter, grad, ring);

@@ -102,8 +102,9 @@ def test_batch_autotuned_iteration_matches_oracle():
     b = api.Batch(probs, svgds, Xs, lps)
     choices = b.autotune(allow_fast_math=True)
     assert len(choices) == len({w.n for w in wls})
-    for links, K, fast, blocks in choices:
+    for links, K, fast, blocks, upt in choices:
         assert K in (1, 5, 10, 25, 50) and fast in (0, 1) and blocks > 0
+        assert upt == 1 or (upt == 2 and K == 1)
     b.iterate(1)
     torch.cuda.synchronize()
     for j, w in enumerate(wls):
@@ -138,3 +139,33 @@ def test_batch_rejects_mismatched_svgd():
         pytest.skip("both problems have the same layout")
     with pytest.raises(api.PdsError):
         api.Batch(probs, wrong, [_gpu(x) for x in xs])
+
+
+def test_batched_two_units_per_thread_equal_one_unit_alone():
+    """Chain-length groups whose problems all allow it (K = 1, every state
+    component observed, even N) run the batched launch with two particles
+    per thread; each problem's log p equals its one-unit single-problem
+    evaluation bit for bit."""
+    wls = [f32_workload(wlmod.random_chain(n, N, seed=500 + n + N, T=T, W=W))
+           for n, N, T, W in ((2, 64, 40, 4), (2, 130, 33, 3), (4, 96, 50, 5), (5, 200, 41, 4), (3, 58, 30, 3))]
+    obs = [observations(w) for w in wls]
+    xs = [particles(w, o, seed=3) for w, o in zip(wls, obs)]
+    alone = []
+    for w, o, x in zip(wls, obs, xs):
+        p = api.Problem.from_workload(w, o, checkpoint_stride=1, fast_math=1)
+        p.set_option(api.OPT_UNITS_PER_THREAD, 1)
+        lp, _, _ = p.loglik_grad(_gpu(x))
+        torch.cuda.synchronize()
+        alone.append(lp.cpu().numpy())
+        p.close()
+    probs, svgds = _objects(wls, obs, K=1, fast=1)
+    for p in probs:
+        p.set_option(api.OPT_UNITS_PER_THREAD, 2)
+    Xs = [_gpu(x) for x in xs]
+    lps = [torch.empty(w.N, device="cuda") for w in wls]
+    b = api.Batch(probs, svgds, Xs, lps)
+    b.iterate(1)
+    torch.cuda.synchronize()
+    for j in range(len(wls)):
+        np.testing.assert_array_equal(lps[j].cpu().numpy(), alone[j])
+    b.close()
