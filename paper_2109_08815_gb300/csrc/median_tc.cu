@@ -59,6 +59,7 @@ __device__ __forceinline__ void mt_split(float x, float& hi, float& lo) {
 template <int MM>
 __global__ void median_tc_prep_kernel(int N, int Npad, int M, const float* __restrict__ u, float* __restrict__ imgA,
                                       float* __restrict__ imgB) {
+  PDS_PDL_ENTRY();
   using D = MtDims<MM>;
   constexpr int KA = D::KA;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(kMtThreads, 2) median_tc_kernel(int N, const f
                                                                   SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
                                                                   unsigned long long cap, int mode,
                                                                   int only_in_fallback, int wait_limit) {
+  PDS_PDL_ENTRY();
   using D = MtDims<MM>;
   constexpr int KA = D::KA;
   // wait_limit: mbarrier polls before a wait gives up (the kernel then
@@ -369,7 +371,7 @@ static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const 
   const int nt = Npad / kMtRows;
   float* imgA = img;
   float* imgB = img + (size_t)nt * (D::kTile / 4);
-  if (prep) median_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, u, imgA, imgB);
+  if (prep) launch_pdl(median_tc_prep_kernel<MM>, dim3((Npad + 127) / 128), dim3(128), 0, st, N, Npad, M, u, imgA, imgB);
   // per device: shared-memory opt-in and the persistent grid (resident CTAs
   // per SM, at most 2: each holds 256 of the SM's 512 TMEM columns)
   static int grid_of[64];
@@ -401,7 +403,7 @@ static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const 
   }
   const int grid = n_work < grid_of[dev] ? n_work : grid_of[dev];
   if (grid < 1) return cudaSuccess;
-  median_tc_kernel<MM><<<grid, kMtThreads, D::kBytes, st>>>(N, imgA, imgB, reinterpret_cast<const int2*>(work),
+  launch_pdl(median_tc_kernel<MM>, dim3(grid), dim3(kMtThreads), D::kBytes, st, N, imgA, imgB, reinterpret_cast<const int2*>(work),
                                                            n_work, ctl, cand, cap, mode, only_in_fallback,
                                                            wait_limit);
   return cudaGetLastError();

@@ -263,6 +263,39 @@ struct pds_svgd {
 };
 
 namespace pds {
+// Programmatic dependent launch (sm_90 and later).  A kernel that
+// launch_pdl starts may be scheduled while the kernel before it on the
+// stream is still finishing; its first statement is PDS_PDL_ENTRY, which
+// waits until that kernel has completed and its writes are visible
+// (griddepcontrol.wait; a no-op when the kernel was launched plainly) and
+// then lets the next kernel be scheduled in turn.  Nothing is read or
+// written before the wait, so the order of all memory effects is that of
+// plain launches; only launch latency and block start-up overlap.
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#define PDS_PDL_ENTRY()          \
+  do {                           \
+    ::pds::pdl_wait();           \
+    ::pds::pdl_launch_dependents(); \
+  } while (0)
+#endif
+template <class... KArgs, class... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
+
 int ensure_workspace(pds_problem* p, int N);
 int ensure_iter_buffers(pds_problem* p, int N);
 template <int NL>

@@ -21,6 +21,7 @@ constexpr int kHistBins = 2048;   // 11-bit radix digits
 __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const float* __restrict__ X,
                                  const float* __restrict__ G, float* __restrict__ u, float* __restrict__ gu,
                                  int mode) {
+  PDS_PDL_ENTRY();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < kHistBins) ctl->hist[idx] = 0u;
   if (idx == 0) {
@@ -68,6 +69,7 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
 // the last block sets the median's rank over the live pairs.
 __global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* __restrict__ ctl,
                                                         float* __restrict__ u, const float* __restrict__ gu) {
+  PDS_PDL_ENTRY();
   __shared__ unsigned int blk;
   __shared__ bool last;
   if (threadIdx.x == 0) blk = 0u;
@@ -176,6 +178,7 @@ template <int MM>
 __global__ void __launch_bounds__(kTile) median_hist_kernel(int N, int M, const float* __restrict__ u,
                                                             SvgdCtl* __restrict__ ctl, int pass,
                                                             int only_in_fallback) {
+  PDS_PDL_ENTRY();
   constexpr int Q = Pad4<MM>::Q;
   __shared__ unsigned int hist[kHistBins];
   __shared__ float4 uj[kSpan][Q];
@@ -227,6 +230,7 @@ __global__ void __launch_bounds__(kTile) median_hist_kernel(int N, int M, const 
 // Resolve one radix digit: find the bin holding the rank-th element, narrow
 // the prefix and the rank, clear the histogram.  One warp.
 __global__ void median_select_kernel(SvgdCtl* __restrict__ ctl, int pass, int N, int required_mode) {
+  PDS_PDL_ENTRY();
   if (required_mode >= 0 && ctl->mode != required_mode) return;
   const int lane = threadIdx.x;  // 32 lanes x 64 bins
   unsigned int local = 0u;
@@ -277,6 +281,7 @@ constexpr int kSmallThreads = 512;
 template <int MM>
 __global__ void __launch_bounds__(kSmallThreads) median_small_kernel(int N, int M, const float* __restrict__ u,
                                                                      SvgdCtl* __restrict__ ctl) {
+  PDS_PDL_ENTRY();
   extern __shared__ float sm_small[];
   __shared__ unsigned int hist[kHistBins];
   __shared__ unsigned int s_prefix, s_rank;
@@ -372,7 +377,7 @@ static cudaError_t launch_median_small(int N, int M, const float* u, SvgdCtl* ct
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  median_small_kernel<MM><<<1, kSmallThreads, smem, st>>>(N, M, u, ctl);
+  launch_pdl(median_small_kernel<MM>, dim3(1), dim3(kSmallThreads), smem, st, N, M, u, ctl);
   return cudaGetLastError();
 }
 
@@ -401,6 +406,7 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
 template <int MM>
 __global__ void __launch_bounds__(256) median_sample_dist_kernel(int N, int M, const float* __restrict__ u,
                                                                  float* __restrict__ samp) {
+  PDS_PDL_ENTRY();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= kSample) return;
   const unsigned long long h = mix64((unsigned long long)s);
@@ -423,6 +429,7 @@ __global__ void __launch_bounds__(256) median_sample_dist_kernel(int N, int M, c
 // resolved together with one histogram each).
 __global__ void __launch_bounds__(kSampleThreads) median_sample_sort_kernel(const float* __restrict__ samp,
                                                                             SvgdCtl* __restrict__ ctl) {
+  PDS_PDL_ENTRY();
   constexpr int kPer = kSample / kSampleThreads;
   __shared__ unsigned int hist[2][kHistBins];
   __shared__ unsigned int prefix[2], rank[2];
@@ -512,6 +519,7 @@ template <int MM>
 __global__ void __launch_bounds__(kTile) median_bracket_kernel(int N, int M, const float* __restrict__ u,
                                                                SvgdCtl* __restrict__ ctl, float* __restrict__ cand,
                                                                unsigned long long cap) {
+  PDS_PDL_ENTRY();
   constexpr int Q = Pad4<MM>::Q;
   __shared__ float4 uj[kSpan][Q];
   __shared__ float buf[kCandBuf];
@@ -575,6 +583,7 @@ __global__ void __launch_bounds__(kTile) median_bracket_kernel(int N, int M, con
 
 // Decide between the candidate path and the full passes.
 __global__ void median_resolve_kernel(SvgdCtl* __restrict__ ctl, unsigned long long cap) {
+  PDS_PDL_ENTRY();
   const unsigned long long rank = ctl->rank;
   const unsigned long long below = ctl->below, inside = ctl->inside;
   if (below <= rank && rank < below + inside && inside <= cap) {
@@ -598,6 +607,7 @@ __device__ __forceinline__ unsigned int cand_key(float v, unsigned int lob) { re
 
 __global__ void __launch_bounds__(256) median_cand_key_hist_kernel(const float* __restrict__ cand,
                                                                    SvgdCtl* __restrict__ ctl) {
+  PDS_PDL_ENTRY();
   __shared__ unsigned int hist[kHistBins];
   if (ctl->mode != 0) return;
   for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) hist[b] = 0u;
@@ -629,6 +639,7 @@ __global__ void __launch_bounds__(256) median_cand_key_hist_kernel(const float* 
 
 // The bin holding the rank (one warp); clears the histogram and the bin count.
 __global__ void median_cand_bin_kernel(SvgdCtl* __restrict__ ctl) {
+  PDS_PDL_ENTRY();
   if (ctl->mode != 0) return;
   const int lane = threadIdx.x;
   unsigned int local = 0u;
@@ -664,6 +675,7 @@ __global__ void median_cand_bin_kernel(SvgdCtl* __restrict__ ctl) {
 __global__ void __launch_bounds__(256) median_cand_compact_kernel(const float* __restrict__ cand,
                                                                   SvgdCtl* __restrict__ ctl,
                                                                   float* __restrict__ cbuf) {
+  PDS_PDL_ENTRY();
   if (ctl->mode != 0) return;
   const unsigned long long n = ctl->inside;
   const unsigned int lob = ctl->lob, sh = ctl->cshift, bin = ctl->cbin;
@@ -718,6 +730,7 @@ constexpr int kFinalThreads = 1024;
 __global__ void __launch_bounds__(kFinalThreads) median_cand_final_kernel(const float* __restrict__ cand,
                                                                           const float* __restrict__ cbuf,
                                                                           SvgdCtl* __restrict__ ctl) {
+  PDS_PDL_ENTRY();
   __shared__ unsigned int hist[kHistBins];
   __shared__ unsigned int s_prefix, s_rank;
   if (ctl->mode != 0) return;
@@ -801,6 +814,7 @@ template <int MM, bool FAST>
 __global__ void __launch_bounds__(kTile) svgd_phi_kernel(int N, int M, const float* __restrict__ u,
                                                          const float* __restrict__ gu, const SvgdCtl* __restrict__ ctl,
                                                          float* __restrict__ phi_part, int chunk_len) {
+  PDS_PDL_ENTRY();
   constexpr int Q = Pad4<MM>::Q;
   __shared__ float4 uj[kTile][Q];
   __shared__ float4 gj[kTile][Q];
@@ -874,6 +888,7 @@ __global__ void svgd_adam_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, float
                                  const float* __restrict__ G, const float* __restrict__ phi_part, int chunks,
                                  float* __restrict__ am, float* __restrict__ av, float* __restrict__ bw_out,
                                  float* __restrict__ phi_out, int* __restrict__ status) {
+  PDS_PDL_ENTRY();
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   const size_t total = (size_t)sp.P * sp.N;
   if (idx == 0 && bw_out) *bw_out = ctl->bw;
@@ -947,8 +962,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
   const bool bracket = (N >= 2) && w.cand && w.cbuf && w.cand_cap > 0;
   {
     const int total = (M * N > kHistBins) ? M * N : kHistBins;
-    svgd_prep_kernel<<<(total + 255) / 256, 256, 0, st>>>(sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
-    svgd_live_kernel<<<(N + 255) / 256, 256, 0, st>>>(N, M, w.ctl, w.u, w.gu);
+    launch_pdl(svgd_prep_kernel, dim3((total + 255) / 256), dim3(256), 0, st, sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
+    launch_pdl(svgd_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, N, M, w.ctl, w.u, w.gu);
     n += 2;
   }
   if (N >= 2) {
@@ -962,8 +977,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     if (bracket) {
       cudaError_t e = svgd_setup_device();
       if (e != cudaSuccess) return e;
-      median_sample_dist_kernel<MM><<<kSample / 256, 256, 0, st>>>(N, M, w.u, w.samp);
-      median_sample_sort_kernel<<<1, kSampleThreads, 0, st>>>(w.samp, w.ctl);
+      launch_pdl(median_sample_dist_kernel<MM>, dim3(kSample / 256), dim3(256), 0, st, N, M, w.u, w.samp);
+      launch_pdl(median_sample_sort_kernel, dim3(1), dim3(kSampleThreads), 0, st, w.samp, w.ctl);
       n += 2;
       if (tcm) {
         e = launch_median_tc(N, M, w.u, w.mimg, w.mwork, w.n_mwork, w.ctl, w.cand, w.cand_cap, 0, 0, true,
@@ -972,15 +987,15 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
         prepped = true;
         n += 2;
       } else {
-        median_bracket_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, w.cand, w.cand_cap);
+        launch_pdl(median_bracket_kernel<MM>, dim3(grid), dim3(kTile), 0, st, N, M, w.u, w.ctl, w.cand, w.cand_cap);
         n += 1;
       }
-      median_resolve_kernel<<<1, 1, 0, st>>>(w.ctl, w.cand_cap);
+      launch_pdl(median_resolve_kernel, dim3(1), dim3(1), 0, st, w.ctl, w.cand_cap);
       // one pass of keys relative to the bracket, then the median's bin
-      median_cand_key_hist_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl);
-      median_cand_bin_kernel<<<1, 32, 0, st>>>(w.ctl);
-      median_cand_compact_kernel<<<152 * 4, 256, 0, st>>>(w.cand, w.ctl, w.cbuf);
-      median_cand_final_kernel<<<1, kFinalThreads, 0, st>>>(w.cand, w.cbuf, w.ctl);
+      launch_pdl(median_cand_key_hist_kernel, dim3(152 * 4), dim3(256), 0, st, w.cand, w.ctl);
+      launch_pdl(median_cand_bin_kernel, dim3(1), dim3(32), 0, st, w.ctl);
+      launch_pdl(median_cand_compact_kernel, dim3(152 * 4), dim3(256), 0, st, w.cand, w.ctl, w.cbuf);
+      launch_pdl(median_cand_final_kernel, dim3(1), dim3(kFinalThreads), 0, st, w.cand, w.cbuf, w.ctl);
       n += 5;
     }
     // full passes over all pairs: always for small N or when asked, otherwise
@@ -1000,10 +1015,10 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
         n += prepped ? 1 : 2;
         prepped = true;
       } else {
-        median_hist_kernel<MM><<<grid, kTile, 0, st>>>(N, M, w.u, w.ctl, pass, bracket ? 1 : 0);
+        launch_pdl(median_hist_kernel<MM>, dim3(grid), dim3(kTile), 0, st, N, M, w.u, w.ctl, pass, bracket ? 1 : 0);
         n += 1;
       }
-      median_select_kernel<<<1, 32, 0, st>>>(w.ctl, pass, N, 1);
+      launch_pdl(median_select_kernel, dim3(1), dim3(32), 0, st, w.ctl, pass, N, 1);
       n += 1;
     }
   }
@@ -1022,12 +1037,12 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     } else {
       dim3 grid((N + kSpan - 1) / kSpan, chunks);
       if (sp.fast_math)
-        svgd_phi_kernel<MM, true><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+        launch_pdl(svgd_phi_kernel<MM, true>, dim3(grid), dim3(kTile), 0, st, N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
       else
-        svgd_phi_kernel<MM, false><<<grid, kTile, 0, st>>>(N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
+        launch_pdl(svgd_phi_kernel<MM, false>, dim3(grid), dim3(kTile), 0, st, N, M, w.u, w.gu, w.ctl, w.phi_part, chunk_len);
     }
     const size_t total = (size_t)sp.P * N;
-    svgd_adam_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(sp, w.ctl, X, G, w.phi_part, chunks_used,
+    launch_pdl(svgd_adam_kernel, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, st, sp, w.ctl, X, G, w.phi_part, chunks_used,
                                                                       w.adam_m, w.adam_v, bw_out, phi_out,
                                                                       w.status_flags);
     n += 2;

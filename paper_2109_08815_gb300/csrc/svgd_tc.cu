@@ -110,6 +110,7 @@ template <int MM>
 __global__ void phi_tc_prep_kernel(int N, int Npad, int M, const float* __restrict__ u, const float* __restrict__ gu,
                                    const SvgdCtl* __restrict__ ctl, float* __restrict__ imgA,
                                    float* __restrict__ imgBV) {
+  PDS_PDL_ENTRY();
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   using SM = TcSmem<MM>;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(kPhiThreads, 1) phi_tc_kernel(int N, int Npad,
                                                                 const float* __restrict__ u,
                                                                 SvgdCtl* __restrict__ ctl, float* __restrict__ phi_part,
                                                                 int slots, int wait_limit) {
+  PDS_PDL_ENTRY();
   constexpr int KA = TcDims<MM>::KA, NV = TcDims<MM>::NV;
   using SM = TcSmem<MM>;
   constexpr int S = SM::kStages;
@@ -474,7 +476,7 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_
   const int G = phi_tc_grid(N);
   const int slots = phi_tc_slots(N);
   if (G <= 0 || slots <= 0 || slots > w.chunks) return cudaErrorInvalidConfiguration;
-  phi_tc_prep_kernel<MM><<<(Npad + 127) / 128, 128, 0, st>>>(N, Npad, M, w.u, w.gu, w.ctl, imgA, imgBV);
+  launch_pdl(phi_tc_prep_kernel<MM>, dim3((Npad + 127) / 128), dim3(128), 0, st, N, Npad, M, w.u, w.gu, w.ctl, imgA, imgBV);
   // at least 116 KB so that two CTAs never share an SM (each allocates all
   // 512 TMEM columns)
   const int smem = SM::kBytes > 116 * 1024 ? SM::kBytes : 116 * 1024;
@@ -489,7 +491,7 @@ static cudaError_t launch_phi_tc_mm(int N, int M, const SvgdWork& w, int* slots_
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  phi_tc_kernel<MM><<<G, kPhiThreads, smem, st>>>(N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, slots,
+  launch_pdl(phi_tc_kernel<MM>, dim3(G), dim3(kPhiThreads), smem, st, N, Npad, M, imgA, imgBV, w.u, w.ctl, w.phi_part, slots,
                                                   w.wait_limit);
   *slots_used = slots;
   return cudaGetLastError();
