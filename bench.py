@@ -45,16 +45,22 @@ FP32_LANES_PER_SM = 128
 
 
 def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
-    """Algorithmic FP32 flops of one time step (FMA = 2; sincos and
-    reciprocals run on the MUFU and are not counted): the forward step with
-    its observation term (the rank-1 link-frame articulated-body recursion
-    and semi-implicit Euler), and the reverse step (Euler's adjoint, one
-    solve mu = H^-1 abar with the same rank-1 recursion, the closed-form
-    gradient of mu^T ID, and the observation seed).  The checkpoint segment
-    recompute of K > 1 is an implementation cost and is not counted."""
-    fwd = 58 * n + 3 * D - 25
-    rev = 109 * n + 3 * D - 44
-    return fwd, rev
+    """Algorithmic FP32 flops of one time step of the n-link chain with D
+    observed components (FMA = 2; sincos and reciprocals run on the MUFU and
+    are not counted; operations on values that are zero by construction, at
+    the ends of the chain, are not counted): the forward step with its
+    observation term (the rank-1 link-frame articulated-body recursion,
+    semi-implicit Euler, the residual and its running sum), and the reverse
+    step (the observation seed, Euler's adjoint, one solve mu = H^-1 abar
+    with the same rank-1 recursion, the closed-form gradient of mu^T ID).
+    The two products that the kernel re-forms inside a fused multiply-add
+    (qdd_i and mu_i, one per link after the first) and the checkpoint
+    segment recompute of K > 1 are implementation costs and are not counted.
+    tests/test_flopcount.py counts these operations by executing the step on
+    a counting scalar that it first pins to the FP64 oracle."""
+    if n == 1:
+        return 19 + 3 * D, 63 + 3 * D
+    return 60 * n - 43 + 3 * D, 107 * n - 54 + 3 * D
 
 
 def _peaks():
