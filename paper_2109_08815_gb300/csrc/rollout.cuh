@@ -139,7 +139,7 @@ __device__ __forceinline__ void chain_step(V (&q)[NL], V (&v)[NL], const Links<N
     V om = zero;
 #pragma unroll
     for (int i = 0; i < NL; ++i) {
-      om = vadd(om, v[i]);
+      om = (i == 0) ? v[0] : vadd(om, v[i]);
       o2[i] = vmul(om, om);
       w[i] = vmul(o2[i], P.l[i]);
       tau[i] = vmul(vneg(P.b[i]), v[i]);
@@ -162,13 +162,15 @@ __device__ __forceinline__ void chain_step(V (&q)[NL], V (&v)[NL], const Links<N
     }
     const V ih = rcp<FAST>(h);
     const V be = vfma(vneg(P.mg[i]), C[i], vfma(vneg(w[i]), z, Be));
-    const V bp = vfma(P.mg[i], S[i], vfma(vneg(w[i]), y, Bp));
+    // the outermost link (i = NL - 1) has y = 0, Be = Bp = 0: the terms on
+    // those zeros are left out (the same values; no instruction spent on them)
+    const V bp = (i + 1 < NL) ? vfma(P.mg[i], S[i], vfma(vneg(w[i]), y, Bp)) : vmul(P.mg[i], S[i]);
     const V ft = vmul(vfma(dtau, P.il[i], vneg(bp)), ih);
     f[i] = ft;
-    x[i] = vmul(y, ih);
-    Bce = vfma(ft, y, be);
+    x[i] = (i + 1 < NL) ? vmul(y, ih) : zero;
+    Bce = (i + 1 < NL) ? vfma(ft, y, be) : be;
     Bcp = vmul(dtau, P.il[i]);
-    kc = vmul(vmul(P.m[i], vadd(P.m[i], kc)), ih);
+    kc = vmul(vmul(P.m[i], (i + 1 < NL) ? vadd(P.m[i], kc) : P.m[i]), ih);
   }
   V Ae = zero, Ap = zero, alp = zero;
 #pragma unroll
@@ -178,8 +180,9 @@ __device__ __forceinline__ void chain_step(V (&q)[NL], V (&v)[NL], const Links<N
       ae = vfma(cq[i], Ae, vmul(sq[i], Ap));
       ap = vfma(cq[i], Ap, vmul(vneg(sq[i]), Ae));
     }
-    const V An = vfma(vneg(x[i]), ae, f[i]);
-    const V d = vsub(An, ap);
+    // the base link (i = 0) has ae = ap = 0
+    const V An = (i > 0) ? vfma(vneg(x[i]), ae, f[i]) : f[0];
+    const V d = (i > 0) ? vsub(An, ap) : An;
     const V al = vmul(d, P.il[i]);
     Ae = vfma(vneg(o2[i]), P.l[i], ae);
     Ap = An;
@@ -253,10 +256,10 @@ __device__ __forceinline__ void chain_step_vjp(const V (&q)[NL], const V (&v)[NL
       const V ih = rcp<FAST>(h);
       const V ft = vmul(vfma(dtau, P.il[i], vneg(Bp)), ih);
       f[i] = ft;
-      x[i] = vmul(y, ih);
-      Bce = vfma(ft, y, Be);
+      x[i] = (i + 1 < NL) ? vmul(y, ih) : zero;
+      Bce = (i + 1 < NL) ? vfma(ft, y, Be) : Be;
       Bcp = vmul(dtau, P.il[i]);
-      kc = vmul(vmul(P.m[i], vadd(P.m[i], kc)), ih);
+      kc = vmul(vmul(P.m[i], (i + 1 < NL) ? vadd(P.m[i], kc) : P.m[i]), ih);
     }
   }
   // ... outward pass (Lambda = absolute angular accelerations of the
@@ -271,13 +274,13 @@ __device__ __forceinline__ void chain_step_vjp(const V (&q)[NL], const V (&v)[NL
         ae = vfma(cq[i], Ae, vmul(sq[i], Ap));
         ap = vfma(cq[i], Ap, vmul(vneg(sq[i]), Ae));
       }
-      const V An = vfma(vneg(x[i]), ae, f[i]);
-      const V d = vsub(An, ap);
+      const V An = (i > 0) ? vfma(vneg(x[i]), ae, f[i]) : f[0];
+      const V d = (i > 0) ? vsub(An, ap) : An;
       Lam[i] = vmul(d, P.il[i]);
       mu[i] = (i > 0) ? vfma(d, P.il[i], vneg(Lam[i - 1])) : Lam[0];  // mu_i = Lambda_i - Lambda_{i-1}, fused
       Ae = ae;
       Ap = An;
-      o = vadd(o, v[i]);
+      o = (i == 0) ? v[0] : vadd(o, v[i]);
       a = vfma(vsub(v2[i], v[i]), idt, a);
       om[i] = o;
       al[i] = a;
