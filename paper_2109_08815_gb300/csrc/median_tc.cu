@@ -57,9 +57,13 @@ __device__ __forceinline__ void mt_split(float x, float& hi, float& lo) {
 // Tile images (hi, lo) of a_i and b_j for every particle; rows N..Npad-1
 // are zero (never counted).
 template <int MM>
+// only_in_fallback: the images are rebuilt only when the full passes run
+// (the second phase of a split step may have taken particles out of u).
 __global__ void median_tc_prep_kernel(int N, int Npad, int M, const float* __restrict__ u, float* __restrict__ imgA,
-                                      float* __restrict__ imgB) {
+                                      float* __restrict__ imgB, const SvgdCtl* __restrict__ ctl,
+                                      int only_in_fallback) {
   PDS_PDL_ENTRY();
+  if (only_in_fallback && ctl->mode != 1) return;
   using D = MtDims<MM>;
   constexpr int KA = D::KA;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,7 +375,9 @@ static cudaError_t median_tc_mm(int N, int M, const float* u, float* img, const 
   const int nt = Npad / kMtRows;
   float* imgA = img;
   float* imgB = img + (size_t)nt * (D::kTile / 4);
-  if (prep) launch_pdl(median_tc_prep_kernel<MM>, dim3((Npad + 127) / 128), dim3(128), 0, st, N, Npad, M, u, imgA, imgB);
+  if (prep)
+    launch_pdl(median_tc_prep_kernel<MM>, dim3((Npad + 127) / 128), dim3(128), 0, st, N, Npad, M, u, imgA, imgB,
+               (const SvgdCtl*)ctl, only_in_fallback);
   // per device: shared-memory opt-in and the persistent grid (resident CTAs
   // per SM, at most 2: each holds 256 of the SM's 512 TMEM columns)
   static int grid_of[64];

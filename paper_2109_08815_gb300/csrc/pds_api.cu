@@ -598,6 +598,9 @@ static void drop_graph_slot(pds_svgd::Graph& g) {
 }
 static void drop_graph(pds_svgd* s) {
   for (auto& g : s->graphs) drop_graph_slot(g);
+  if (s->iter_exec) cudaGraphExecDestroy(s->iter_exec);
+  s->iter_exec = nullptr;
+  s->iter_calls = 0;
 }
 
 int pds_svgd_set_option(pds_svgd_t s, int option, int value) {
@@ -638,6 +641,7 @@ int pds_svgd_destroy(pds_svgd_t s) {
   if (!s) return PDS_OK;
   cudaStreamSynchronize(s->stream);
   if (s->gstream) cudaStreamSynchronize(s->gstream);
+  if (s->side) cudaStreamSynchronize(s->side);
   cudaFree(s->w.cand);
   cudaFree(s->w.samp);
   cudaFree(s->w.cbuf);
@@ -655,6 +659,9 @@ int pds_svgd_destroy(pds_svgd_t s) {
   if (s->gstream) cudaStreamDestroy(s->gstream);
   if (s->gev_in) cudaEventDestroy(s->gev_in);
   if (s->gev_out) cudaEventDestroy(s->gev_out);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   delete s;
   return PDS_OK;
 }
@@ -681,9 +688,8 @@ int pds_svgd_status(pds_svgd_t s) {
   return take_status(s);
 }
 
-// The ~25 kernels of one step, launched one by one on st.
-static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out,
-                                   cudaStream_t st, int* n) {
+// The workspace view of a step under the state's options.
+static SvgdWork svgd_work(const pds_svgd* s) {
   SvgdWork w = s->w;
   if (s->full_passes) {
     w.cand_cap = 0;
@@ -691,7 +697,13 @@ static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float*
   }
   if (s->phi_cuda_cores) w.tc = nullptr;
   if (s->median_cuda_cores) w.mimg = nullptr;
-  return launch_svgd_step(s->sp, w, X, G, bw_out, phi_out, st, n);
+  return w;
+}
+
+// The ~25 kernels of one step (or of one of its phases), launched one by one on st.
+static cudaError_t svgd_launch_all(pds_svgd* s, float* X, const float* G, float* bw_out, float* phi_out,
+                                   cudaStream_t st, int* n, int phase = kSvgdAll) {
+  return launch_svgd_step(s->sp, svgd_work(s), X, G, bw_out, phi_out, st, n, phase);
 }
 
 static bool default_stream(cudaStream_t st) {
@@ -806,6 +818,95 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
   return PDS_OK;
 }
 
+// One SVGD iteration with the step's median phase beside the likelihood.
+// The median needs only the coordinates, which the likelihood does not
+// change, so it runs on a high-priority side stream while the rollout runs
+// (its blocks fill the SMs that the rollout's last wave leaves idle); the
+// step's gradient phase waits for both.  The results are those of
+// pds_loglik_grad followed by pds_svgd_step.
+static bool iterate_overlaps(const pds_problem* p, const pds_svgd* s) {
+  return p->kind == PDS_SYSTEM_PLANAR_CHAIN && s->use_graph && p->stream == s->stream && !default_stream(s->stream) &&
+         svgd_step_splits(s->sp, svgd_work(s));
+}
+
+static cudaError_t iterate_enqueue(pds_problem* p, pds_svgd* s, float* X, float* lp, cudaStream_t st, int* n) {
+  const int N = s->sp.N;
+  cudaError_t e;
+  if ((e = cudaEventRecord(s->ev_fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(s->side, s->ev_fork, 0)) != cudaSuccess)
+    return e;
+  if ((e = svgd_launch_all(s, X, p->d_grad, nullptr, nullptr, s->side, n, kSvgdTheta)) != cudaSuccess) return e;
+  if ((e = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess) return e;
+  if ((e = launch_rollout(p->c, X, N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
+  if ((e = launch_window_reduce(p->c, X, N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess) return e;
+  *n += 2;
+  if ((e = cudaStreamWaitEvent(st, s->ev_join, 0)) != cudaSuccess) return e;
+  return svgd_launch_all(s, X, p->d_grad, nullptr, nullptr, st, n, kSvgdGrad);
+}
+
+static int iterate_overlapped(pds_problem* p, pds_svgd* s, float* X, float* lp) {
+  const int st_rc = take_status(s);  // reported by a step already run: this one is not queued
+  if (st_rc != PDS_OK) return st_rc;
+  cudaError_t e = cudaSuccess;
+  if (!s->side) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if ((e = cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+      return cuda_fail(e, "iteration streams");
+  }
+  pds_svgd::IterKey k;
+  memset(&k, 0, sizeof(k));
+  k.prob = p;
+  k.X = X;
+  k.logp = lp;
+  k.grad = p->d_grad;
+  k.N = s->sp.N;
+  k.c = p->c;
+  k.parts = p->parts;
+  k.step.X = X;
+  k.step.G = p->d_grad;
+  k.step.full_passes = s->full_passes;
+  k.step.phi_cuda_cores = s->phi_cuda_cores;
+  k.step.median_cuda_cores = s->median_cuda_cores;
+  k.step.wait_limit = s->w.wait_limit;
+  k.step.sp = s->sp;
+  if (memcmp(&k, &s->iter_key, sizeof(k)) != 0) {
+    if (s->iter_exec) cudaGraphExecDestroy(s->iter_exec);
+    s->iter_exec = nullptr;
+    s->iter_calls = 0;
+    s->iter_key = k;
+  }
+  int n = 0;
+  if (!s->iter_exec && s->iter_calls++ == 0) {
+    // first iteration with this key: direct launches (they also do each
+    // kernel's one-time set-up, which is not captured)
+    e = iterate_enqueue(p, s, X, lp, s->stream, &n);
+    g_launches = n;
+    return e == cudaSuccess ? PDS_OK : cuda_fail(e, "iteration launch");
+  }
+  if (!s->iter_exec) {
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t el = iterate_enqueue(p, s, X, lp, s->stream, &n);
+      e = cudaStreamEndCapture(s->stream, &g);
+      if (e == cudaSuccess) e = el;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->iter_exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      s->iter_exec = nullptr;
+      return cuda_fail(e, "iteration graph capture");
+    }
+    s->iter_launches = n;
+  }
+  e = cudaGraphLaunch(s->iter_exec, s->stream);
+  g_launches = s->iter_launches;
+  return e == cudaSuccess ? PDS_OK : cuda_fail(e, "iteration graph launch");
+}
+
 int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, float* logp) {
   if (!p || !s || !particles) return fail(PDS_ERR_ARG, "NULL argument");
   if (iters < 0) return fail(PDS_ERR_ARG, "iters < 0");
@@ -819,8 +920,22 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
   rc = ensure_workspace(p, N);
   if (rc != PDS_OK) return rc;
   int total = 0;
+  const bool overlap = iterate_overlaps(p, s) && !being_captured(s->stream);
   for (int it = 0; it < iters; ++it) {
     float* lp = (logp && it == iters - 1) ? logp : p->d_logp;
+    if (overlap) {
+      // log p always into the problem's buffer (the graph's key stays the
+      // same for every iteration), copied out after the last one
+      rc = iterate_overlapped(p, s, particles, p->d_logp);
+      if (rc != PDS_OK) return rc;
+      total += g_launches;
+      if (lp != p->d_logp) {
+        const cudaError_t e =
+            cudaMemcpyAsync(lp, p->d_logp, (size_t)N * sizeof(float), cudaMemcpyDeviceToDevice, s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy log p");
+      }
+      continue;
+    }
     rc = pds_loglik_grad(p, particles, N, lp, p->d_grad, nullptr);
     if (rc != PDS_OK) return rc;
     total += g_launches;

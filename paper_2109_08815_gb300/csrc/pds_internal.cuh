@@ -132,6 +132,10 @@ struct SvgdCtl {
   unsigned int gmax[16];     // max |g_u| per component (float bits); reset at the end of each step
   unsigned int n_live;       // particles with finite coordinates and gradient (the others sit out the step)
   unsigned int live_blocks;  // blocks of the liveness pass that have finished
+  // a step split in two phases (median on the coordinates, then the
+  // gradient): particles whose coordinates are finite but whose gradient is
+  // not, and the blocks of that check that have finished
+  unsigned int gdead, gblocks;
   // candidate selection: keys are bit patterns relative to the bracket's
   // lower end, lob; bins are key >> cshift; cbin the median's bin, ccount
   // the candidates in it
@@ -166,8 +170,14 @@ constexpr int kWaitLimitDefault = 1 << 24;
 constexpr int kSmallMedianN = 256;  // N(N-1)/2 <= 32640 pair distances (128 KB) in shared memory
 constexpr int kDrainLimit = 1 << 24;  // polls of the waits that let copies and products in flight finish
 
+// phase: kSvgdAll, or (where svgd_step_splits holds) kSvgdTheta -- the
+// median bandwidth, which reads only the coordinates -- then kSvgdGrad, the
+// rest, which also reads G.  The two phases in that order give the same
+// results as kSvgdAll.
+constexpr int kSvgdAll = 0, kSvgdTheta = 1, kSvgdGrad = 2;
 cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
-                             float* phi_out, cudaStream_t st, int* launches);
+                             float* phi_out, cudaStream_t st, int* launches, int phase = kSvgdAll);
+bool svgd_step_splits(const SvgdParams& sp, const SvgdWork& w);
 int svgd_phi_chunks(int N);
 unsigned long long svgd_cand_capacity(int N);  // 0 when the bracket path is not used
 int svgd_cbin_capacity();
@@ -260,6 +270,27 @@ struct pds_svgd {
   int full_passes = 0;
   int phi_cuda_cores = 0;
   int median_cuda_cores = 0;
+  // pds_iterate's whole iteration as one graph (planar chains on a stream
+  // that can be captured): the step's median phase on a high-priority side
+  // stream beside the likelihood, both reading only the particles, then the
+  // step's gradient phase.  Captured on the second iteration with the same
+  // key, replayed afterwards.
+  struct IterKey {
+    const void* prob;
+    float* X;
+    float* logp;
+    float* grad;
+    int N;
+    pds::ChainParams c;
+    pds::Partials parts;
+    SvgdGraphKey step;
+  };
+  IterKey iter_key{};
+  int iter_calls = 0;
+  cudaGraphExec_t iter_exec = nullptr;
+  int iter_launches = 0;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace pds {

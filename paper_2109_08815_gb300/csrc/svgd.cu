@@ -18,6 +18,10 @@ namespace pds {
 constexpr int kTile = 128;        // particles per tile (threads per block)
 constexpr int kHistBins = 2048;   // 11-bit radix digits
 
+// Start of a step: the control block, u = (theta - lo) / (hi - lo), and
+// (G != NULL) the gradient in u coordinates with its per-component maximum.
+// A split step passes G = NULL here and computes the gradient's part in
+// svgd_grad_live_kernel.
 __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const float* __restrict__ X,
                                  const float* __restrict__ G, float* __restrict__ u, float* __restrict__ gu,
                                  int mode) {
@@ -40,14 +44,16 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
     ctl->n_live = 0u;
     ctl->live_blocks = 0u;
     ctl->tc_error = 0;
+    ctl->gdead = 0u;
+    ctl->gblocks = 0u;
   }
   const int total = sp.M * sp.N;
   const int k = idx < total ? idx / sp.N : -1;
+  if (idx < total) u[idx] = (X[idx] - sp.lo[k]) / (sp.hi[k] - sp.lo[k]);
+  if (!G) return;
   unsigned int gbits = 0u;
   if (idx < total) {
-    const float width = sp.hi[k] - sp.lo[k];
-    u[idx] = (X[idx] - sp.lo[k]) / width;
-    const float g = G[idx] * width;
+    const float g = G[idx] * (sp.hi[k] - sp.lo[k]);
     gu[idx] = g;
     if (isfinite(g)) gbits = __float_as_uint(fabsf(g));  // particles that are not finite sit out
   }
@@ -62,7 +68,8 @@ __global__ void svgd_prep_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl, const
   }
 }
 
-// Liveness of each particle: a particle whose unit-box coordinates or
+// Liveness of each particle (gu = NULL: of its coordinates only, the first
+// phase of a split step): a particle whose unit-box coordinates or
 // gradient are not all finite sits out this step (its coordinates in u become
 // NaN, so it takes no part in the median's pairs or in the other particles'
 // kernel sums, and its own direction is NaN).  Counts the live particles;
@@ -78,7 +85,7 @@ __global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* _
   if (i < N) {
     // all loads issued together: accumulate without short-circuiting
     bool live = true;
-    for (int k = 0; k < M; ++k) live &= isfinite(u[(size_t)k * N + i]) & isfinite(gu[(size_t)k * N + i]);
+    for (int k = 0; k < M; ++k) live &= isfinite(u[(size_t)k * N + i]) & (!gu || isfinite(gu[(size_t)k * N + i]));
     if (live) atomicAdd(&blk, 1u);
     else
       for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
@@ -95,6 +102,64 @@ __global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* _
     const unsigned long long nl = atomicAdd(&ctl->n_live, 0u);
     const unsigned long long pairs = nl * (nl > 0 ? nl - 1ull : 0ull) / 2ull;
     ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
+  }
+}
+
+// Second phase of a split step: the gradient in u coordinates and its
+// per-component maximum, and the particles whose coordinates are finite (so
+// the first phase's median counted them) but whose gradient is not.  They
+// sit out as in svgd_live_kernel; if there are any, the last block takes
+// them out of the live count, sets the median's rank over the remaining
+// pairs and the full radix passes (mode 1) to compute it again, exactly.
+__global__ void __launch_bounds__(256) svgd_grad_live_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl,
+                                                             const float* __restrict__ G, float* __restrict__ u,
+                                                             float* __restrict__ gu) {
+  PDS_PDL_ENTRY();
+  __shared__ unsigned int blk;
+  __shared__ bool last;
+  if (threadIdx.x == 0) blk = 0u;
+  __syncthreads();
+  const int N = sp.N, M = sp.M;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = i < N;
+  bool ufin = in, gfin = in;
+  for (int k = 0; k < M; ++k) {
+    float g = 0.f;
+    if (in) {
+      g = G[(size_t)k * N + i] * (sp.hi[k] - sp.lo[k]);
+      gu[(size_t)k * N + i] = g;
+      gfin &= isfinite(g);
+      ufin &= isfinite(u[(size_t)k * N + i]);
+    }
+    const unsigned int bits = (in && isfinite(g)) ? __float_as_uint(fabsf(g)) : 0u;
+    const unsigned int m = __reduce_max_sync(0xffffffffu, bits);
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&ctl->gmax[k], m);
+  }
+  if (ufin && !gfin) {
+    for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
+    atomicAdd(&blk, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (blk) atomicAdd(&ctl->gdead, blk);
+    __threadfence();
+    last = atomicAdd(&ctl->gblocks, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const unsigned int dead = atomicAdd(&ctl->gdead, 0u);
+  if (!dead) return;
+  for (int b = threadIdx.x; b < kHistBins; b += blockDim.x) ctl->hist[b] = 0u;
+  if (threadIdx.x == 0) {
+    const unsigned long long nl = ctl->n_live - dead;
+    const unsigned long long pairs = nl * (nl > 0 ? nl - 1ull : 0ull) / 2ull;
+    ctl->n_live = (unsigned int)nl;
+    ctl->rank = pairs ? (unsigned int)((pairs - 1ull) / 2ull) : 0u;
+    ctl->prefix = 0u;
+    ctl->bw = 1.0f;
+    ctl->med = 0.0f;
+    ctl->mode = 1;
   }
 }
 
@@ -956,24 +1021,32 @@ int svgd_phi_partials(int N) {
 
 template <int MM>
 static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
-                                  float* phi_out, cudaStream_t st, int* launches) {
+                                  float* phi_out, cudaStream_t st, int* launches, int phase) {
   const int N = sp.N, M = sp.M;
   int n = 0;
   const bool bracket = (N >= 2) && w.cand && w.cbuf && w.cand_cap > 0;
-  {
+  // with the sampled bracket the step runs as two phases (the second may
+  // follow the first on another stream): the median over the particles with
+  // finite coordinates, then the gradient, which takes out the particles
+  // with a gradient that is not finite and then has the full passes redo
+  // the median exactly
+  const bool split = bracket;
+  if (phase != kSvgdAll && !split) return cudaErrorInvalidValue;
+  const bool doA = phase != kSvgdGrad, doB = phase != kSvgdTheta;
+  // pair distances on the tensor cores (N >= 2048): every pass over the
+  // pairs then sees the same distances
+  const bool tcm = w.mimg && w.mwork && N >= 2048;
+  const int nt = (N + kSpan - 1) / kSpan;
+  const long long all_tiles = (long long)nt * nt;
+  const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
+  bool prepped = false;  // the tensor-core images of u are current
+  if (doA) {
     const int total = (M * N > kHistBins) ? M * N : kHistBins;
-    launch_pdl(svgd_prep_kernel, dim3((total + 255) / 256), dim3(256), 0, st, sp, w.ctl, X, G, w.u, w.gu, bracket ? 0 : 1);
-    launch_pdl(svgd_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, N, M, w.ctl, w.u, w.gu);
+    launch_pdl(svgd_prep_kernel, dim3((total + 255) / 256), dim3(256), 0, st, sp, w.ctl, X, split ? nullptr : G, w.u,
+               w.gu, bracket ? 0 : 1);
+    launch_pdl(svgd_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, N, M, w.ctl, w.u,
+               split ? (const float*)nullptr : (const float*)w.gu);
     n += 2;
-  }
-  if (N >= 2) {
-    const int nt = (N + kSpan - 1) / kSpan;
-    const long long all_tiles = (long long)nt * nt;
-    const int grid = all_tiles < 152 * 8 ? (int)all_tiles : 152 * 8;
-    // pair distances on the tensor cores (N >= 2048): every pass over the
-    // pairs then sees the same distances
-    const bool tcm = w.mimg && w.mwork && N >= 2048;
-    bool prepped = false;
     if (bracket) {
       cudaError_t e = svgd_setup_device();
       if (e != cudaSuccess) return e;
@@ -998,9 +1071,20 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
       launch_pdl(median_cand_final_kernel, dim3(1), dim3(kFinalThreads), 0, st, w.cand, w.cbuf, w.ctl);
       n += 5;
     }
+  }
+  if (!doB) {
+    if (launches) *launches += n;
+    return cudaGetLastError();
+  }
+  if (split) {
+    launch_pdl(svgd_grad_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, sp, w.ctl, G, w.u, w.gu);
+    n += 1;
+    prepped = false;  // the gradient may have taken particles out of u: the full passes rebuild the images
+  }
+  if (N >= 2) {
     // full passes over all pairs: always for small N or when asked, otherwise
-    // only if the bracket missed (the kernels return at once in that case);
-    // the smallest N in one block
+    // only if the bracket missed or the gradient took particles out (the
+    // kernels return at once otherwise); the smallest N in one block
     const bool small = !bracket && !tcm && w.small_median && N <= kSmallMedianN;
     if (small) {
       cudaError_t e = launch_median_small<MM>(N, M, w.u, w.ctl, st);
@@ -1052,13 +1136,17 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
 }
 
 cudaError_t launch_svgd_step(const SvgdParams& sp, const SvgdWork& w, float* X, const float* G, float* bw_out,
-                             float* phi_out, cudaStream_t st, int* launches) {
-  if (sp.M <= 2) return launch_svgd_mm<2>(sp, w, X, G, bw_out, phi_out, st, launches);
-  if (sp.M <= 4) return launch_svgd_mm<4>(sp, w, X, G, bw_out, phi_out, st, launches);
-  if (sp.M <= 8) return launch_svgd_mm<8>(sp, w, X, G, bw_out, phi_out, st, launches);
-  if (sp.M <= 10) return launch_svgd_mm<10>(sp, w, X, G, bw_out, phi_out, st, launches);
-  if (sp.M <= 12) return launch_svgd_mm<12>(sp, w, X, G, bw_out, phi_out, st, launches);
-  return launch_svgd_mm<16>(sp, w, X, G, bw_out, phi_out, st, launches);
+                             float* phi_out, cudaStream_t st, int* launches, int phase) {
+  if (sp.M <= 2) return launch_svgd_mm<2>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+  if (sp.M <= 4) return launch_svgd_mm<4>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+  if (sp.M <= 8) return launch_svgd_mm<8>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+  if (sp.M <= 10) return launch_svgd_mm<10>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+  if (sp.M <= 12) return launch_svgd_mm<12>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+  return launch_svgd_mm<16>(sp, w, X, G, bw_out, phi_out, st, launches, phase);
+}
+
+bool svgd_step_splits(const SvgdParams& sp, const SvgdWork& w) {
+  return sp.N >= 2 && w.cand && w.cbuf && w.cand_cap > 0;
 }
 
 }  // namespace pds
