@@ -843,18 +843,24 @@ static cudaError_t iterate_enqueue(pds_problem* p, pds_svgd* s, float* X, float*
   return svgd_launch_all(s, X, p->d_grad, nullptr, nullptr, st, n, kSvgdGrad);
 }
 
+// The side stream (highest priority) and its two events, created on first use.
+static int ensure_side(pds_svgd* s) {
+  if (s->side) return PDS_OK;
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(e, "iteration streams");
+  return PDS_OK;
+}
+
 static int iterate_overlapped(pds_problem* p, pds_svgd* s, float* X, float* lp) {
   const int st_rc = take_status(s);  // reported by a step already run: this one is not queued
   if (st_rc != PDS_OK) return st_rc;
   cudaError_t e = cudaSuccess;
-  if (!s->side) {
-    int lo = 0, hi = 0;
-    cudaDeviceGetStreamPriorityRange(&lo, &hi);
-    if ((e = cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, hi)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming)) != cudaSuccess)
-      return cuda_fail(e, "iteration streams");
-  }
+  if (int rc = ensure_side(s)) return rc;
   pds_svgd::IterKey k;
   memset(&k, 0, sizeof(k));
   k.prob = p;
@@ -968,7 +974,10 @@ static int ensure_copy_streams(pds_problem* p) {
 // units (contiguous, u = w N + i) start on a stream of their own as soon as
 // their rows have landed, so that the copy hides behind the rollout.  The
 // kernels and their arithmetic are those of pds_loglik_grad.
-static int loglik_grad_copy_in(pds_problem* p, const float* host, int N, int* launches) {
+// s (may be NULL): the SVGD state whose step's median phase starts on its
+// side stream as soon as the first group of rows, which holds theta, has
+// landed; the caller then runs the step's gradient phase after ev_join.
+static int loglik_grad_copy_in(pds_problem* p, const float* host, int N, int* launches, pds_svgd* s) {
   const ChainParams& c = p->c;
   const int G = c.W < pds_problem::kCopyGroups ? c.W : pds_problem::kCopyGroups;
   cudaError_t e = cudaSuccess;
@@ -991,6 +1000,14 @@ static int loglik_grad_copy_in(pds_problem* p, const float* host, int N, int* la
     if ((e = cudaEventRecord(p->ov_copied[g], p->ov_copy)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(p->ov_roll[g], p->ov_copied[g], 0)) != cudaSuccess)
       return cuda_fail(e, "copy order");
+    if (g == 0 && s) {
+      int n = 0;
+      if ((e = cudaStreamWaitEvent(s->side, p->ov_copied[0], 0)) != cudaSuccess ||
+          (e = svgd_launch_all(s, p->d_x, p->d_grad, nullptr, nullptr, s->side, &n, kSvgdTheta)) != cudaSuccess ||
+          (e = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess)
+        return cuda_fail(e, "svgd median phase");
+      *launches += n;
+    }
     e = launch_rollout(c, p->d_x, N, p->parts, 1, nullptr, p->ov_roll[g], (size_t)w0 * N, (size_t)(w1 - w0) * N);
     if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
     if ((e = cudaEventRecord(p->ov_rolled[g], p->ov_roll[g])) != cudaSuccess ||
@@ -999,7 +1016,7 @@ static int loglik_grad_copy_in(pds_problem* p, const float* host, int N, int* la
   }
   e = launch_window_reduce(c, p->d_x, N, p->parts, p->d_logp, p->d_grad, nullptr, p->stream);
   if (e != cudaSuccess) return cuda_fail(e, "window reduce launch");
-  *launches = G + 1;
+  *launches += G + 1;
   return PDS_OK;
 }
 
@@ -1019,9 +1036,21 @@ int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int i
   if (copy_in) {
     if ((rc = take_status(s)) != PDS_OK) return rc;
     if ((rc = ensure_workspace(p, N)) != PDS_OK) return rc;
-    if ((rc = loglik_grad_copy_in(p, particles_host, N, &launches)) != PDS_OK) return rc;
-    if ((rc = pds_svgd_step(s, p->d_x, p->d_grad, nullptr, nullptr)) != PDS_OK) return rc;
-    launches += g_launches;
+    // the step's median phase beside the copies and the rollout (direct
+    // launches), then its gradient phase
+    const bool split = svgd_step_splits(s->sp, svgd_work(s)) && s->stream == p->stream && !being_captured(p->stream);
+    if (split && (rc = ensure_side(s)) != PDS_OK) return rc;
+    if ((rc = loglik_grad_copy_in(p, particles_host, N, &launches, split ? s : nullptr)) != PDS_OK) return rc;
+    if (split) {
+      int n = 0;
+      if ((e = cudaStreamWaitEvent(p->stream, s->ev_join, 0)) != cudaSuccess ||
+          (e = svgd_launch_all(s, p->d_x, p->d_grad, nullptr, nullptr, p->stream, &n, kSvgdGrad)) != cudaSuccess)
+        return cuda_fail(e, "svgd gradient phase");
+      launches += n;
+    } else {
+      if ((rc = pds_svgd_step(s, p->d_x, p->d_grad, nullptr, nullptr)) != PDS_OK) return rc;
+      launches += g_launches;
+    }
     if (iters > 1) {
       if ((rc = pds_iterate(p, s, p->d_x, iters - 1, p->d_logp)) != PDS_OK) return rc;
       launches += g_launches;
