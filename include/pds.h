@@ -377,7 +377,14 @@ int pds_svgd_reset(pds_svgd_t s);
 /* Algorithm 1 loop on the device: `iters` times { log p and gradient of all
  * particles; SVGD + Adam update }.  particles: device [P][N] in/out;
  * logp: device [N] or NULL, receives log p evaluated in the last iteration
- * (before its update).  N must equal the SVGD state's N. */
+ * (before its update).  N must equal the SVGD state's N.  For a planar chain
+ * whose problem and SVGD state share one stream that can be captured (not a
+ * default stream), and whose step takes the sampled median bracket, each
+ * iteration runs as one CUDA graph (captured on the second call with the
+ * same buffers and settings): the step's median bandwidth, which reads only
+ * the coordinates, on a high-priority side stream beside the likelihood,
+ * then the rest of the step.  The results are those of pds_loglik_grad
+ * followed by pds_svgd_step, bit for bit. */
 int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, float* logp);
 
 /* Same as pds_iterate for host-resident data: copies particles (host [P][N])
