@@ -211,6 +211,19 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     pds_problem* p = b->probs[j];
     pds_svgd* s = b->svgds[j];
     cudaStream_t st = b->side[j % n_side];
+    SvgdWork w = s->w;
+    if (s->full_passes) {
+      w.cand_cap = 0;
+      w.small_median = 0;
+    }
+    if (s->phi_cuda_cores) w.tc = nullptr;
+    if (s->median_cuda_cores) w.mimg = nullptr;
+    // a step that takes the sampled median bracket starts its median phase
+    // (coordinates only) before the rollout of its chain length is done
+    const bool split = svgd_step_splits(s->sp, w);
+    int k = 0;
+    if (split && (e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k, kSvgdTheta)) != cudaSuccess)
+      return e;
     if (b->group_of[j] >= 0 && (e = cudaStreamWaitEvent(st, b->gdone[b->group_of[j]], 0)) != cudaSuccess) return e;
     const int N = s->sp.N;
     float* lp = b->logp[j] ? b->logp[j] : p->d_logp;
@@ -224,15 +237,9 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     }
     if ((e = launch_window_reduce(p->c, b->X[j], N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess)
       return e;
-    SvgdWork w = s->w;
-    if (s->full_passes) {
-      w.cand_cap = 0;
-      w.small_median = 0;
-    }
-    if (s->phi_cuda_cores) w.tc = nullptr;
-    if (s->median_cuda_cores) w.mimg = nullptr;
-    int k = 0;
-    if ((e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k)) != cudaSuccess) return e;
+    if ((e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k,
+                              split ? kSvgdGrad : kSvgdAll)) != cudaSuccess)
+      return e;
     n += 1 + k;
   }
   for (int s = 0; s < n_side; ++s) {
