@@ -220,7 +220,7 @@ static cudaError_t enqueue_iteration(pds_batch* b, int* launches) {
     if (s->median_cuda_cores) w.mimg = nullptr;
     // a step that takes the sampled median bracket starts its median phase
     // (coordinates only) before the rollout of its chain length is done
-    const bool split = svgd_step_splits(s->sp, w);
+    const bool split = svgd_step_splits(s->sp, w) && !s->grad_dead_seen;
     int k = 0;
     if (split && (e = launch_svgd_step(s->sp, w, b->X[j], p->d_grad, nullptr, nullptr, st, &k, kSvgdTheta)) != cudaSuccess)
       return e;

@@ -634,6 +634,7 @@ int pds_svgd_reset(pds_svgd_t s) {
       (e = cudaMemsetAsync(s->w.adam_v, 0, PN * sizeof(float), s->stream)) != cudaSuccess ||
       (e = cudaMemsetAsync(s->w.ctl, 0, sizeof(SvgdCtl), s->stream)) != cudaSuccess)
     return cuda_fail(e, "svgd reset");
+  s->grad_dead_seen = 0;
   return PDS_OK;
 }
 
@@ -674,6 +675,8 @@ static int take_status(pds_svgd* s) {
   const int f = *h;
   if (!f) return PDS_OK;
   *h = 0;
+  if (f & kStatusGradDead) s->grad_dead_seen = 1;
+  if (!(f & (kStatusTimeout | kStatusNoneLive))) return PDS_OK;
   if (f & kStatusTimeout)
     return fail(PDS_ERR_TIMEOUT, "a tensor-core pass of an SVGD step gave up waiting for its copies or products; "
                                  "that step's particles are not valid");
@@ -824,9 +827,12 @@ int pds_svgd_step(pds_svgd_t s, float* particles, const float* grad, float* band
 // (its blocks fill the SMs that the rollout's last wave leaves idle); the
 // step's gradient phase waits for both.  The results are those of
 // pds_loglik_grad followed by pds_svgd_step.
-static bool iterate_overlaps(const pds_problem* p, const pds_svgd* s) {
+static bool iterate_overlaps(const pds_problem* p, pds_svgd* s) {
+  // a divergent particle (finite coordinates, gradient not finite) makes the
+  // split step compute the median twice: such a state runs its steps whole
+  if (s->h_status && (*(volatile int*)s->h_status & kStatusGradDead)) s->grad_dead_seen = 1;
   return p->kind == PDS_SYSTEM_PLANAR_CHAIN && s->use_graph && p->stream == s->stream && !default_stream(s->stream) &&
-         svgd_step_splits(s->sp, svgd_work(s));
+         svgd_step_splits(s->sp, svgd_work(s)) && !s->grad_dead_seen;
 }
 
 static cudaError_t iterate_enqueue(pds_problem* p, pds_svgd* s, float* X, float* lp, cudaStream_t st, int* n) {
@@ -926,10 +932,10 @@ int pds_iterate(pds_problem_t p, pds_svgd_t s, float* particles, int iters, floa
   rc = ensure_workspace(p, N);
   if (rc != PDS_OK) return rc;
   int total = 0;
-  const bool overlap = iterate_overlaps(p, s) && !being_captured(s->stream);
+  const bool capturable = !being_captured(s->stream);
   for (int it = 0; it < iters; ++it) {
     float* lp = (logp && it == iters - 1) ? logp : p->d_logp;
-    if (overlap) {
+    if (capturable && iterate_overlaps(p, s)) {
       // log p always into the problem's buffer (the graph's key stays the
       // same for every iteration), copied out after the last one
       rc = iterate_overlapped(p, s, particles, p->d_logp);
@@ -1038,7 +1044,8 @@ int pds_iterate_host(pds_problem_t p, pds_svgd_t s, float* particles_host, int i
     if ((rc = ensure_workspace(p, N)) != PDS_OK) return rc;
     // the step's median phase beside the copies and the rollout (direct
     // launches), then its gradient phase
-    const bool split = svgd_step_splits(s->sp, svgd_work(s)) && s->stream == p->stream && !being_captured(p->stream);
+    const bool split = svgd_step_splits(s->sp, svgd_work(s)) && s->stream == p->stream &&
+                       !being_captured(p->stream) && !s->grad_dead_seen;
     if (split && (rc = ensure_side(s)) != PDS_OK) return rc;
     if ((rc = loglik_grad_copy_in(p, particles_host, N, &launches, split ? s : nullptr)) != PDS_OK) return rc;
     if (split) {

@@ -166,6 +166,10 @@ struct SvgdWork {
 // Bits of SvgdWork::status_flags, set by the last kernel of a step.
 constexpr int kStatusTimeout = 1;    // a tensor-core pass gave up waiting (the step's results are not valid)
 constexpr int kStatusNoneLive = 2;   // no particle had finite coordinates and gradient
+// (not an error) the second phase of a split step found particles with finite
+// coordinates but a gradient that is not finite, and had the median computed
+// again by the full passes; the state then stops splitting its steps
+constexpr int kStatusGradDead = 4;
 constexpr int kWaitLimitDefault = 1 << 24;
 constexpr int kSmallMedianN = 256;  // N(N-1)/2 <= 32640 pair distances (128 KB) in shared memory
 constexpr int kDrainLimit = 1 << 24;  // polls of the waits that let copies and products in flight finish
@@ -287,6 +291,7 @@ struct pds_svgd {
   };
   IterKey iter_key{};
   int iter_calls = 0;
+  int grad_dead_seen = 0;  // kStatusGradDead seen: steps are no longer split (until pds_svgd_reset)
   cudaGraphExec_t iter_exec = nullptr;
   int iter_launches = 0;
   cudaStream_t side = nullptr;

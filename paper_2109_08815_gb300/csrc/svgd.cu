@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(256) svgd_live_kernel(int N, int M, SvgdCtl* _
 // pairs and the full radix passes (mode 1) to compute it again, exactly.
 __global__ void __launch_bounds__(256) svgd_grad_live_kernel(SvgdParams sp, SvgdCtl* __restrict__ ctl,
                                                              const float* __restrict__ G, float* __restrict__ u,
-                                                             float* __restrict__ gu) {
+                                                             float* __restrict__ gu, int* __restrict__ status) {
   PDS_PDL_ENTRY();
   __shared__ unsigned int blk;
   __shared__ bool last;
@@ -160,6 +160,10 @@ __global__ void __launch_bounds__(256) svgd_grad_live_kernel(SvgdParams sp, Svgd
     ctl->bw = 1.0f;
     ctl->med = 0.0f;
     ctl->mode = 1;
+    if (status) {
+      volatile int* h = status;
+      *h = *h | kStatusGradDead;
+    }
   }
 }
 
@@ -1025,13 +1029,14 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
   const int N = sp.N, M = sp.M;
   int n = 0;
   const bool bracket = (N >= 2) && w.cand && w.cbuf && w.cand_cap > 0;
-  // with the sampled bracket the step runs as two phases (the second may
-  // follow the first on another stream): the median over the particles with
-  // finite coordinates, then the gradient, which takes out the particles
-  // with a gradient that is not finite and then has the full passes redo
-  // the median exactly
-  const bool split = bracket;
-  if (phase != kSvgdAll && !split) return cudaErrorInvalidValue;
+  // with the sampled bracket the step can run as two phases (kSvgdTheta
+  // then kSvgdGrad, the second after the first on another stream): the
+  // median over the particles with finite coordinates, then the gradient,
+  // which takes out the particles with a gradient that is not finite and
+  // then has the full passes redo the median exactly.  kSvgdAll takes the
+  // gradient's liveness first and the bracket once.
+  const bool split = bracket && phase != kSvgdAll;
+  if (phase != kSvgdAll && !bracket) return cudaErrorInvalidValue;
   const bool doA = phase != kSvgdGrad, doB = phase != kSvgdTheta;
   // pair distances on the tensor cores (N >= 2048): every pass over the
   // pairs then sees the same distances
@@ -1077,7 +1082,8 @@ static cudaError_t launch_svgd_mm(const SvgdParams& sp, const SvgdWork& w, float
     return cudaGetLastError();
   }
   if (split) {
-    launch_pdl(svgd_grad_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, sp, w.ctl, G, w.u, w.gu);
+    launch_pdl(svgd_grad_live_kernel, dim3((N + 255) / 256), dim3(256), 0, st, sp, w.ctl, G, w.u, w.gu,
+               w.status_flags);
     n += 1;
     prepped = false;  // the gradient may have taken particles out of u: the full passes rebuild the images
   }
