@@ -117,10 +117,12 @@ __global__ void __launch_bounds__(256) svgd_grad_live_kernel(SvgdParams sp, Svgd
   PDS_PDL_ENTRY();
   __shared__ unsigned int blk;
   __shared__ bool last;
+  __shared__ unsigned int wmax[8][16];  // per warp and component: max |g_u| bits
   if (threadIdx.x == 0) blk = 0u;
   __syncthreads();
   const int N = sp.N, M = sp.M;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int wid = threadIdx.x >> 5;
   const bool in = i < N;
   bool ufin = in, gfin = in;
   for (int k = 0; k < M; ++k) {
@@ -133,7 +135,14 @@ __global__ void __launch_bounds__(256) svgd_grad_live_kernel(SvgdParams sp, Svgd
     }
     const unsigned int bits = (in && isfinite(g)) ? __float_as_uint(fabsf(g)) : 0u;
     const unsigned int m = __reduce_max_sync(0xffffffffu, bits);
-    if ((threadIdx.x & 31) == 0 && m) atomicMax(&ctl->gmax[k], m);
+    if ((threadIdx.x & 31) == 0) wmax[wid][k] = m;
+  }
+  __syncthreads();
+  // one atomic per block and component
+  if (threadIdx.x < M) {
+    unsigned int m = 0u;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = max(m, wmax[q][threadIdx.x]);
+    if (m) atomicMax(&ctl->gmax[threadIdx.x], m);
   }
   if (ufin && !gfin) {
     for (int k = 0; k < M; ++k) u[(size_t)k * N + i] = __int_as_float(0x7fc00000);
