@@ -44,7 +44,7 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
 
-def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
+def flops_per_particle_step(n: int, D: int, lengths: bool = True) -> tuple[int, int]:
     """Algorithmic FP32 flops of one time step of the n-link chain with D
     observed components (FMA = 2; sincos and reciprocals run on the MUFU and
     are not counted; operations on values that are zero by construction, at
@@ -56,11 +56,14 @@ def flops_per_particle_step(n: int, D: int) -> tuple[int, int]:
     The two products that the kernel re-forms inside a fused multiply-add
     (qdd_i and mu_i, one per link after the first) and the checkpoint
     segment recompute of K > 1 are implementation costs and are not counted.
+    With lengths=False (no link length among the parameters) the reverse
+    step leaves out the length adjoint, 8 flops per link.
     tests/test_flopcount.py counts these operations by executing the step on
     a counting scalar that it first pins to the FP64 oracle."""
+    drop = 0 if lengths else 8 * n
     if n == 1:
-        return 19 + 3 * D, 63 + 3 * D
-    return 60 * n - 43 + 3 * D, 107 * n - 54 + 3 * D
+        return 19 + 3 * D, 63 + 3 * D - drop
+    return 60 * n - 43 + 3 * D, 107 * n - 54 + 3 * D - drop
 
 
 def _peaks():
@@ -408,13 +411,13 @@ def run_pds(args):
     sm_count = props.multi_processor_count
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = sm_count * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
-    fwd, rev = flops_per_particle_step(wl.n, wl.D)
+    fwd, rev = flops_per_particle_step(wl.n, wl.D, lengths=bool(np.any(wl.theta_kind == wlmod.PARAM_LENGTH)))
     flops_launch = N * wl.T * (fwd + rev)
     lg_s = statistics.mean(lg_ms) / 1e3
     achieved = flops_launch / lg_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                "kernel": "rollout_pair_kernel<5> (two particles per thread; + window_reduce, 3%)",
+                "kernel": "rollout_pair_kernel<5> (two particles per thread, no length adjoint; + window_reduce, 3%)",
                 "peak_basis": f"FP32 {sm_count} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max_mhz:.0f} MHz "
                               "(MEASURED_PEAKS sm_max_mhz)",
                 "flops_per_particle_step": fwd + rev,
@@ -845,7 +848,7 @@ def run_serving(api, dev, stream, n_jobs=48, rate=50.0, iters=300, brief=False, 
 
 # dram bytes (read + write) per full-size rollout launch, from the committed
 # ncu capture of this kernel (set to None when the kernel changes)
-TRAFFIC_BYTES_PER_LAUNCH = 368196608 + 659459072
+TRAFFIC_BYTES_PER_LAUNCH = 362851328 + 655211776
 
 
 def main():

@@ -226,7 +226,10 @@ __device__ __forceinline__ void chain_step(V (&q)[NL], V (&v)[NL], const Links<N
 // d/domega_j (plus mu_i b_i for v_i); the damping term gives d/db_i = mu_i v_i.
 // qdd is recovered from the taped velocities as (v' - v) / dt: its FP32
 // error, half an ulp of v' over dt, stays far below the gradient tolerance.
-template <int NL, bool FAST, class V>
+// LEN = false leaves out d/dl (p_j.F_j and the length adjoint lb), for
+// problems with no link length among the parameters; every other output is
+// the same bits.
+template <int NL, bool FAST, bool LEN = true, class V>
 __device__ __forceinline__ void chain_step_vjp(const V (&q)[NL], const V (&v)[NL], const V (&v2)[NL],
                                                const Links<NL, V>& P, float g_, float dt_, float idt_, V (&qb)[NL],
                                                V (&vb)[NL], V (&mb)[NL], V (&lb)[NL], V (&bb)[NL]) {
@@ -308,10 +311,13 @@ __device__ __forceinline__ void chain_step_vjp(const V (&q)[NL], const V (&v)[NL
     Dx = vfma(m, dx[i], Dx);
     Dy = vfma(m, dy[i], Dy);
     const V eD = vfma(S[i], Dx, vmul(vneg(C[i]), Dy)), pD = vfma(C[i], Dx, vmul(S[i], Dy));
-    const V eF = vfma(S[i], Fx, vmul(vneg(C[i]), Fy)), pF = vfma(C[i], Fx, vmul(S[i], Fy));
+    const V eF = vfma(S[i], Fx, vmul(vneg(C[i]), Fy));
     const V o2 = vmul(om[i], om[i]);
     mb[i] = vsub(mb[i], vfma(Gx[i], dx[i], vmul(Gy[i], dy[i])));
-    lb[i] = vsub(lb[i], vfma(al[i], pD, vfma(vneg(o2), eD, vmul(Lam[i], pF))));
+    if constexpr (LEN) {
+      const V pF = vfma(C[i], Fx, vmul(S[i], Fy));
+      lb[i] = vsub(lb[i], vfma(al[i], pD, vfma(vneg(o2), eD, vmul(Lam[i], pF))));
+    }
     bb[i] = vfma(vneg(mu[i]), v[i], bb[i]);
     som = vfma(vmul(vmul(m2, om[i]), P.l[i]), eD, som);
     sphi = vfma(P.l[i], vfma(vneg(al[i]), eD, vfma(vneg(o2), pD, vmul(vneg(Lam[i]), eF))), sphi);
@@ -504,7 +510,7 @@ __device__ __forceinline__ void ckpt_load(const float* __restrict__ tape, size_t
 // RU: unroll factor of the K = 1 reverse loop (2 in the single-problem
 // kernel; the batched kernel, which holds both observation forms, runs
 // slower unrolled).
-template <int NL, bool FAST, bool CS = false, bool EVERY = false, int RU = 1>
+template <int NL, bool FAST, bool CS = false, bool EVERY = false, int RU = 1, bool LEN = true>
 __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                              const Partials& parts, int grad, int32_t* __restrict__ status,
                                              size_t u, float* seg = nullptr, size_t seg_stride = 0) {
@@ -675,8 +681,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       } else {
         obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       }
-      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
-      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
+      chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -689,8 +695,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
     for (int k = h - 1; k >= 0; --k) {
       if (k > 0) ckpt_load<NL>(ckpt, k - 1, U, u, qn, vn);
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
-      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
-      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
+      chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; qs[j] = qn[j]; vs[j] = vn[j]; }
     }
@@ -710,8 +716,8 @@ __device__ __forceinline__ void rollout_unit(const ChainParams& c, const float* 
       // observation at time t0+k+1 depends on s_{k+1}
       obs_residual<NL, EVERY>(c, obs, t0 + k + 1, qh, vh, qb, vb, true);
       tape_load<NL>(segbuf, k - a, sstride, 0, qs, vs);
-      chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
-      if constexpr (CS) chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
+      chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+      if constexpr (CS) chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb2, vb2, mb2, lb2, bb2);
 #pragma unroll
       for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
     }
@@ -770,7 +776,7 @@ __device__ __forceinline__ float2 pair_comp(const float2 (&q)[NL], const float2 
   return comp < NL ? q[comp] : v[comp - NL];
 }
 
-template <int NL, bool FAST>
+template <int NL, bool FAST, bool LEN = true>
 __device__ __forceinline__ void rollout_pair_unit(const ChainParams& c, const float* __restrict__ X, int N,
                                                   const Partials& parts, int32_t* __restrict__ status, size_t u,
                                                   float4* ring, int rstride) {
@@ -937,7 +943,7 @@ __device__ __forceinline__ void rollout_pair_unit(const ChainParams& c, const fl
         else vb[comp - NL] = vfma(vsub(ov, vh[comp - NL]), iso2, vb[comp - NL]);
       }
     }
-    chain_step_vjp<NL, FAST>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
+    chain_step_vjp<NL, FAST, LEN>(qs, vs, vh, P, c.g, c.dt, idt, qb, vb, mb, lb, bb);
 #pragma unroll
     for (int j = 0; j < NL; ++j) { qh[j] = qs[j]; vh[j] = vs[j]; }
   }
@@ -960,7 +966,7 @@ __device__ __forceinline__ void rollout_pair_unit(const ChainParams& c, const fl
 }
 
 // Units [u0, u1) (both even), two per thread.
-template <int NL, bool FAST>
+template <int NL, bool FAST, bool LEN = true>
 __global__ void __launch_bounds__(128, 2) rollout_pair_kernel(const ChainParams c,
                                                                           const float* __restrict__ X, int N,
                                                                           Partials parts,
@@ -969,7 +975,7 @@ __global__ void __launch_bounds__(128, 2) rollout_pair_kernel(const ChainParams 
   extern __shared__ float4 ring4_sh[];
   const size_t u = u0 + 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (u >= u1) return;
-  rollout_pair_unit<NL, FAST>(c, X, N, parts, status, u, ring4_sh + threadIdx.x, blockDim.x);
+  rollout_pair_unit<NL, FAST, LEN>(c, X, N, parts, status, u, ring4_sh + threadIdx.x, blockDim.x);
 }
 
 // seg_smem: the reverse sweep's recomputed segment states live in dynamic
@@ -977,7 +983,7 @@ __global__ void __launch_bounds__(128, 2) rollout_pair_kernel(const ChainParams 
 // the problem observes every state component.
 // Units [u0, u1) of the launch (all N W R units, or those of a group of
 // windows whose particle rows have arrived).
-template <int NL, bool FAST, bool EVERY>
+template <int NL, bool FAST, bool EVERY, bool LEN = true>
 __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(const ChainParams c, const float* __restrict__ X,
                                                                         int N, Partials parts, int grad,
                                                                         int32_t* __restrict__ status, int seg_smem,
@@ -986,10 +992,10 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
   const size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= u1) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x,
+    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU, LEN>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x,
                                                           blockDim.x);
   else
-    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU, LEN>(c, X, N, parts, grad, status, u);
 }
 
 // log p alone (no gradient): the forward sweep needs far fewer registers
@@ -1204,6 +1210,11 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
   const size_t smem = seg_smem ? seg_bytes : 0;
   constexpr unsigned int kAll = (1u << (2 * NL)) - 1u;
   const bool every = (c.obs_mask & kAll) == kAll;
+  // no link length among the parameters: the adjoint step leaves out the
+  // length adjoint (the same bits for everything else)
+  bool lengths = false;
+#pragma unroll
+  for (int j = 0; j < NL; ++j) lengths |= c.length_theta[j] >= 0;
   if (c.csvgd) {
     if (c.fast_math && every)
       rollout_cs_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
@@ -1223,13 +1234,19 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
   } else if (pair_path_applies<NL>(c, N, u0, nu)) {
     const size_t rsmem = (size_t)kRingSlots * NL * 128 * sizeof(float4);
     const unsigned pblocks = (unsigned)((nu / 2 + 127) / 128);
-    if (c.fast_math)
+    if (c.fast_math && !lengths)
+      rollout_pair_kernel<NL, true, false><<<pblocks, 128, rsmem, st>>>(c, X, N, parts, status, u0, u1);
+    else if (c.fast_math)
       rollout_pair_kernel<NL, true><<<pblocks, 128, rsmem, st>>>(c, X, N, parts, status, u0, u1);
     else
       rollout_pair_kernel<NL, false><<<pblocks, 128, rsmem, st>>>(c, X, N, parts, status, u0, u1);
   } else {
     // the same residual form as the batched kernel takes for the problem
-    if (c.fast_math && every)
+    if (c.fast_math && every && !lengths)
+      rollout_kernel<NL, true, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
+    else if (c.fast_math && !lengths)
+      rollout_kernel<NL, true, false, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
+    else if (c.fast_math && every)
       rollout_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);
     else if (c.fast_math)
       rollout_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem, u0, u1);

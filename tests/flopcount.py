@@ -179,9 +179,11 @@ def obs_seed(obs, q, v, qb, vb, iso2):
     return qb, vb
 
 
-def chain_step_vjp(q, v, v2, m, l, b, il, g, dt, idt, qb, vb, mb, lb, bb):
+def chain_step_vjp(q, v, v2, m, l, b, il, g, dt, idt, qb, vb, mb, lb, bb, lengths=True):
     """Reverse of one step: (qb, vb) the adjoint of the output state in, that
-    of the input state out; mb, lb, bb accumulate the parameter adjoints."""
+    of the input state out; mb, lb, bb accumulate the parameter adjoints.
+    lengths=False: no link length is a parameter, and the length adjoint
+    (p_j.F_j and lb) is not computed; lb comes back unchanged."""
     n = len(q)
     c = q[0].c
     zero = S(0.0, c, True)
@@ -244,10 +246,11 @@ def chain_step_vjp(q, v, v2, m, l, b, il, g, dt, idt, qb, vb, mb, lb, bb):
         eD = fma(Sa[i], Dx, (-Ca[i]) * Dy)
         pD = fma(Ca[i], Dx, Sa[i] * Dy)
         eF = fma(Sa[i], Fx, (-Ca[i]) * Fy)
-        pF = fma(Ca[i], Fx, Sa[i] * Fy)
         o2 = om[i] * om[i]
         mb[i] = mb[i] - fma(Gx[i], dx[i], Gy[i] * dy[i])
-        lb[i] = lb[i] - fma(al[i], pD, fma(-o2, eD, Lam[i] * pF))
+        if lengths:
+            pF = fma(Ca[i], Fx, Sa[i] * Fy)
+            lb[i] = lb[i] - fma(al[i], pD, fma(-o2, eD, Lam[i] * pF))
         bb[i] = fma(-mu[i], v[i], bb[i])
         som = fma((m2 * om[i]) * l[i], eD, som)
         sphi = fma(l[i], fma(-al[i], eD, fma(-o2, pD, (-Lam[i]) * eF)), sphi)

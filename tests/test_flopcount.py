@@ -9,7 +9,8 @@ oracle's semi-implicit Euler step of the articulated-body dynamics, and the
 reverse step equals central differences of it -- and then check that the
 count per particle-step agrees with the closed form that bench.py divides
 by the measured time (60n + 3D - 43 forward and 107n + 3D - 54 reverse for
-n >= 2; 19 + 3D and 63 + 3D for one link), once the 2(n - 1) flops of the
+n >= 2; 19 + 3D and 63 + 3D for one link; 8n less in the reverse when no
+link length is a parameter), once the 2(n - 1) flops of the
 two re-formed products are taken out (qdd_i and mu_i are each formed as one
 fused multiply-add of a product's factors; the count credits the product
 once).  Operations on values that are zero by construction are not
@@ -58,24 +59,28 @@ def test_transcribed_forward_step_equals_the_oracle_step(n):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
-def _reverse(m, l, b, q, v, v2, dt, cq, cv, c):
+def _reverse(m, l, b, q, v, v2, dt, cq, cv, c, lengths=True):
     M, L, B = _S(m, c), _S(l, c), _S(b, c)
     IL = [fc.rcp(x) for x in L]
     zero = [fc.zero(c)] * len(m)
     c.flops = 0
     return fc.chain_step_vjp(_S(q, c), _S(v, c), _S(v2, c), M, L, B, IL, fc.S(G, c), fc.S(dt, c),
-                             fc.S(1.0 / dt, c), _S(cq, c), _S(cv, c), zero, zero, zero)
+                             fc.S(1.0 / dt, c), _S(cq, c), _S(cv, c), zero, zero, zero, lengths=lengths)
 
 
+@pytest.mark.parametrize("lengths", [True, False])
 @pytest.mark.parametrize("n", [1, 2, 3, 5, 8])
-def test_transcribed_reverse_step_equals_central_differences_of_the_oracle(n):
+def test_transcribed_reverse_step_equals_central_differences_of_the_oracle(n, lengths):
     m, l, b, q, v = _chain(n, 20 + n)
     dt = 0.005
     rng = np.random.default_rng(30 + n)
     cq, cv = rng.standard_normal(n), rng.standard_normal(n)
     s2 = orc.step(m, l, b, np.concatenate([q, v]), dt, g=G)
     c = fc.Counter()
-    qb, vb, mb, lb, bb = _reverse(m, l, b, q, v, s2[n:], dt, cq, cv, c)
+    qb, vb, mb, lb, bb = _reverse(m, l, b, q, v, s2[n:], dt, cq, cv, c, lengths=lengths)
+    if not lengths:
+        # the length adjoint is left out: lb comes back as the zeros passed in
+        assert all(x.z and x.v == 0.0 for x in lb)
     got = np.array([x.v for x in qb + vb + mb + lb + bb])
 
     def L(m_, l_, b_, q_, v_):
@@ -94,12 +99,13 @@ def test_transcribed_reverse_step_equals_central_differences_of_the_oracle(n):
             am[k][i] -= h
             d[i] = (L(*ap) - L(*am)) / (2 * h)
         fd[name] = d
-    ref = np.concatenate([fd["q"], fd["v"], fd["m"], fd["l"], fd["b"]])
+    ref = np.concatenate([fd["q"], fd["v"], fd["m"], fd["l"] if lengths else np.zeros(n), fd["b"]])
     np.testing.assert_allclose(got, ref, rtol=1e-6, atol=1e-7 * np.abs(ref).max())
 
 
+@pytest.mark.parametrize("lengths", [True, False])
 @pytest.mark.parametrize("n", range(1, 9))
-def test_count_per_particle_step_matches_the_roofline_numerator(n):
+def test_count_per_particle_step_matches_the_roofline_numerator(n, lengths):
     from bench import flops_per_particle_step
 
     D = 2 * n  # the benchmark observes every state component
@@ -117,9 +123,9 @@ def test_count_per_particle_step_matches_the_roofline_numerator(n):
     qb, vb = fc.obs_seed(_S(obs, c2), _S([x.v for x in q2], c2), _S([x.v for x in v2], c2),
                          _S(np.ones(n), c2), _S(np.ones(n), c2), fc.S(1.0, c2))
     seed = c2.flops
-    _reverse(m, l, b, q, v, [x.v for x in v2], dt, [x.v for x in qb], [x.v for x in vb], c2)
+    _reverse(m, l, b, q, v, [x.v for x in v2], dt, [x.v for x in qb], [x.v for x in vb], c2, lengths=lengths)
     rev = seed + c2.flops
-    fwd_ref, rev_ref = flops_per_particle_step(n, D)
+    fwd_ref, rev_ref = flops_per_particle_step(n, D, lengths=lengths)
     refs = n - 1  # one re-formed product per link after the first, in each direction
     assert fwd - refs == fwd_ref, (n, fwd, fwd_ref)
     assert rev - refs == rev_ref, (n, rev, rev_ref)

@@ -20,7 +20,8 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import assert_grad_close, assert_logp_close, f32_workload, observations, oracle_problem, particles
+from helpers import (assert_grad_close, assert_logp_close, f32_workload, logp_constant, observations, oracle_problem,
+                     particles)
 from paper_2109_08815_gb300 import api
 from paper_2109_08815_gb300 import workloads as wlmod
 
@@ -62,6 +63,28 @@ def test_two_units_per_thread_are_bit_identical_to_one(n, fast):
     assert np.all(st1 == 0) and np.all(st2 == 0)
     assert np.array_equal(lp1, lp2)
     assert np.array_equal(g1, g2)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_without_length_parameters_both_kernels_match_the_oracle(n):
+    # masses and dampings only: the adjoint step leaves out the length
+    # adjoint (the kernels specialised for it, fast math, K = 1)
+    wl = f32_workload(wlmod.random_chain(n, 130, seed=330 + n, T=47, W=5,
+                                         kinds=(wlmod.PARAM_MASS, wlmod.PARAM_DAMPING)))
+    assert not np.any(wl.theta_kind == wlmod.PARAM_LENGTH)
+    obs = observations(wl)
+    x = particles(wl, obs)
+    lp1, g1, st1 = _run(wl, obs, x, 1, 1)
+    lp2, g2, st2 = _run(wl, obs, x, 2, 1)
+    assert np.all(st1 == 0) and np.all(st2 == 0)
+    assert np.array_equal(lp1, lp2)
+    assert np.array_equal(g1, g2)
+    lp_ref, g_ref = oracle_problem(wl, obs).loglik_grad(x.astype(np.float32).astype(np.float64))
+    # some of these 130 random particles have log p near zero (their residual
+    # terms cancel the normalising constants): log p is compared relative to
+    # the larger of |log p| and the constants' sum
+    assert_logp_close(lp1.astype(np.float64), lp_ref, const=logp_constant(wl))
+    assert_grad_close(g1.T.astype(np.float64), g_ref, wl.M)
 
 
 @pytest.mark.parametrize("fast", [0, 1])

@@ -95,6 +95,20 @@ def test_noise_free_truth_gives_normalising_constants():
     assert abs(got - ref) <= 1e-10 * abs(ref)
 
 
+@pytest.mark.parametrize("n", [2, 5])
+def test_logp_constant_is_the_noise_free_log_p(n):
+    # the constant part that the GPU tests' log p tolerance is scaled by
+    # (tests/helpers.py) is the oracle's log p at the noise-free truth
+    from helpers import logp_constant
+    wl = wlmod.random_chain(n, 1, seed=90 + n, T=47, W=5, kinds=(wlmod.PARAM_MASS, wlmod.PARAM_DAMPING))
+    m, l, b = _physical(wl, wl.theta_true)
+    st = orc.simulate(m, l, b, wl.s0, wl.dt, wl.T, g=wl.g)
+    obs = st[1:, wl.obs_index]
+    x = np.concatenate([wl.theta_true] + [st[wl.window_start(w)] for w in range(1, wl.W)])
+    got = _problem(wl, obs).loglik_grad(x[None, :], grad=False)[0]
+    assert abs(got - logp_constant(wl)) <= 1e-10 * abs(got)
+
+
 def test_defect_term_is_gaussian_in_the_gap():
     """Moving one shooting state by delta changes only its window's start and
     the previous window's defect; with W=2 and an unobserved-free check via
