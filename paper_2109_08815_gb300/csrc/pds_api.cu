@@ -838,11 +838,14 @@ static bool iterate_overlaps(const pds_problem* p, pds_svgd* s) {
 static cudaError_t iterate_enqueue(pds_problem* p, pds_svgd* s, float* X, float* lp, cudaStream_t st, int* n) {
   const int N = s->sp.N;
   cudaError_t e;
-  if ((e = cudaEventRecord(s->ev_fork, st)) != cudaSuccess || (e = cudaStreamWaitEvent(s->side, s->ev_fork, 0)) != cudaSuccess)
-    return e;
+  // the rollout goes first, so that its first wave takes every SM; the
+  // median phase's blocks (highest priority) then take the slots that the
+  // rollout's blocks free, and fill its last, part-empty wave
+  if ((e = cudaEventRecord(s->ev_fork, st)) != cudaSuccess) return e;
+  if ((e = launch_rollout(p->c, X, N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamWaitEvent(s->side, s->ev_fork, 0)) != cudaSuccess) return e;
   if ((e = svgd_launch_all(s, X, p->d_grad, nullptr, nullptr, s->side, n, kSvgdTheta)) != cudaSuccess) return e;
   if ((e = cudaEventRecord(s->ev_join, s->side)) != cudaSuccess) return e;
-  if ((e = launch_rollout(p->c, X, N, p->parts, 1, nullptr, st)) != cudaSuccess) return e;
   if ((e = launch_window_reduce(p->c, X, N, p->parts, lp, p->d_grad, nullptr, st)) != cudaSuccess) return e;
   *n += 2;
   if ((e = cudaStreamWaitEvent(st, s->ev_join, 0)) != cudaSuccess) return e;
