@@ -1014,7 +1014,7 @@ __global__ void __launch_bounds__(128, PDS_FWD_BLOCKS) rollout_fwd_kernel(const 
 }
 
 // Constrained-SVGD variant of rollout_kernel (two adjoints per unit).
-template <int NL, bool FAST, bool EVERY>
+template <int NL, bool FAST, bool EVERY, bool LEN = true>
 __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
                                                                            const float* __restrict__ X, int N,
                                                                            Partials parts, int grad,
@@ -1024,9 +1024,9 @@ __global__ void __launch_bounds__(128, 2) rollout_cs_kernel(const ChainParams c,
   const size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= U) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, true, EVERY>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
+    rollout_unit<NL, FAST, true, EVERY, 1, LEN>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x, blockDim.x);
   else
-    rollout_unit<NL, FAST, true, EVERY>(c, X, N, parts, grad, status, u);
+    rollout_unit<NL, FAST, true, EVERY, 1, LEN>(c, X, N, parts, grad, status, u);
 }
 
 // Persistent rollout over several problems with the same chain length
@@ -1216,7 +1216,9 @@ cudaError_t launch_rollout_nl(const ChainParams& c, const float* X, int N, const
 #pragma unroll
   for (int j = 0; j < NL; ++j) lengths |= c.length_theta[j] >= 0;
   if (c.csvgd) {
-    if (c.fast_math && every)
+    if (c.fast_math && every && !lengths)
+      rollout_cs_kernel<NL, true, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
+    else if (c.fast_math && every)
       rollout_cs_kernel<NL, true, true><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
     else if (c.fast_math)
       rollout_cs_kernel<NL, true, false><<<blocks, 128, smem, st>>>(c, X, N, parts, grad, status, seg_smem);
