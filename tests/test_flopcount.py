@@ -129,3 +129,15 @@ def test_count_per_particle_step_matches_the_roofline_numerator(n, lengths):
     refs = n - 1  # one re-formed product per link after the first, in each direction
     assert fwd - refs == fwd_ref, (n, fwd, fwd_ref)
     assert rev - refs == rev_ref, (n, rev, rev_ref)
+
+
+def test_benchmark_workload_counts_no_length_adjoint():
+    # the benchmark's chain estimates masses and dampings only, so its
+    # rollout leaves out the length adjoint and the numerator is 287 + 471
+    from bench import flops_per_particle_step
+    from paper_2109_08815_gb300 import workloads as wlmod
+
+    wl = wlmod.chain5(N=4)
+    assert not np.any(wl.theta_kind == wlmod.PARAM_LENGTH)
+    assert flops_per_particle_step(wl.n, wl.D, lengths=False) == (287, 471)
+    assert flops_per_particle_step(wl.n, wl.D) == (287, 511)
