@@ -8,13 +8,14 @@ that transcription to the FP64 oracle -- the forward step equals the
 oracle's semi-implicit Euler step of the articulated-body dynamics, and the
 reverse step equals central differences of it -- and then check that the
 count per particle-step agrees with the closed form that bench.py divides
-by the measured time (60n + 3D - 43 forward and 107n + 3D - 54 reverse for
-n >= 2; 19 + 3D and 63 + 3D for one link; 8n less in the reverse when no
+by the measured time (60n + 3D - 43 forward and 110n + 3D - 54 reverse for
+n >= 2; 19 + 3D and 66 + 3D for one link; 9n less in the reverse when no
 link length is a parameter), once the 2(n - 1) flops of the
 two re-formed products are taken out (qdd_i and mu_i are each formed as one
 fused multiply-add of a product's factors; the count credits the product
 once).  Operations on values that are zero by construction are not
-counted.
+counted; the parameter adjoints, which the reverse step adds to over a
+window's steps, are running sums and count in full.
 """
 import numpy as np
 import pytest
@@ -59,13 +60,15 @@ def test_transcribed_forward_step_equals_the_oracle_step(n):
     np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
 
 
-def _reverse(m, l, b, q, v, v2, dt, cq, cv, c, lengths=True):
+def _reverse(m, l, b, q, v, v2, dt, cq, cv, c, lengths=True, acc=None):
     M, L, B = _S(m, c), _S(l, c), _S(b, c)
     IL = [fc.rcp(x) for x in L]
-    zero = [fc.zero(c)] * len(m)
+    # the parameter adjoints are running sums over a window's steps (zero
+    # only before its first reverse step, not by construction), like rss
+    acc = acc if acc is not None else [[fc.S(0.0, c) for _ in m] for _ in range(3)]
     c.flops = 0
     return fc.chain_step_vjp(_S(q, c), _S(v, c), _S(v2, c), M, L, B, IL, fc.S(G, c), fc.S(dt, c),
-                             fc.S(1.0 / dt, c), _S(cq, c), _S(cv, c), zero, zero, zero, lengths=lengths)
+                             fc.S(1.0 / dt, c), _S(cq, c), _S(cv, c), *acc, lengths=lengths)
 
 
 @pytest.mark.parametrize("lengths", [True, False])
@@ -77,10 +80,11 @@ def test_transcribed_reverse_step_equals_central_differences_of_the_oracle(n, le
     cq, cv = rng.standard_normal(n), rng.standard_normal(n)
     s2 = orc.step(m, l, b, np.concatenate([q, v]), dt, g=G)
     c = fc.Counter()
-    qb, vb, mb, lb, bb = _reverse(m, l, b, q, v, s2[n:], dt, cq, cv, c, lengths=lengths)
+    acc = [[fc.S(0.0, c) for _ in range(n)] for _ in range(3)]
+    qb, vb, mb, lb, bb = _reverse(m, l, b, q, v, s2[n:], dt, cq, cv, c, lengths=lengths, acc=acc)
     if not lengths:
-        # the length adjoint is left out: lb comes back as the zeros passed in
-        assert all(x.z and x.v == 0.0 for x in lb)
+        # the length adjoint is left out: lb comes back as the accumulators passed in
+        assert all(x is y for x, y in zip(lb, acc[1]))
     got = np.array([x.v for x in qb + vb + mb + lb + bb])
 
     def L(m_, l_, b_, q_, v_):
@@ -133,11 +137,11 @@ def test_count_per_particle_step_matches_the_roofline_numerator(n, lengths):
 
 def test_benchmark_workload_counts_no_length_adjoint():
     # the benchmark's chain estimates masses and dampings only, so its
-    # rollout leaves out the length adjoint and the numerator is 287 + 471
+    # rollout leaves out the length adjoint and the numerator is 287 + 481
     from bench import flops_per_particle_step
     from paper_2109_08815_gb300 import workloads as wlmod
 
     wl = wlmod.chain5(N=4)
     assert not np.any(wl.theta_kind == wlmod.PARAM_LENGTH)
-    assert flops_per_particle_step(wl.n, wl.D, lengths=False) == (287, 471)
-    assert flops_per_particle_step(wl.n, wl.D) == (287, 511)
+    assert flops_per_particle_step(wl.n, wl.D, lengths=False) == (287, 481)
+    assert flops_per_particle_step(wl.n, wl.D) == (287, 526)
