@@ -992,8 +992,8 @@ __global__ void __launch_bounds__(128, PDS_ROLLOUT_BLOCKS(NL)) rollout_kernel(co
   const size_t u = u0 + (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (u >= u1) return;
   if (seg_smem)
-    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU, LEN>(c, X, N, parts, grad, status, u, seg_sh + threadIdx.x,
-                                                          blockDim.x);
+    rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU, LEN>(c, X, N, parts, grad, status, u,
+                                                               seg_sh + threadIdx.x, blockDim.x);
   else
     rollout_unit<NL, FAST, false, EVERY, PDS_ROLLOUT_RU, LEN>(c, X, N, parts, grad, status, u);
 }
